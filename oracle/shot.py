@@ -1,0 +1,100 @@
+"""Analytic bispectrum shot noise (oracle; test infrastructure only).  Global line of sight.
+
+Notation: X_0 = compensated interlaced FKP spectrum; N_0(q) = compensated interlaced spectrum of
+the w^2 N-field (Sec. 5.2, Eq. generic_noise definitions); F_l^w(q) = L_l(qhat . los) N_0(q);
+S = three-point self term (sum_g w^3 - alpha^3 sum_r w^3).  Shell averages <.>_k are over the
+modes of a k-bin.  Self-pair term S_l(k) = S <L_l(qhat . los)>_k (the C_shot/W^2 factor of Sec. 5.4
+is taken as 1 for interlaced meshes; reading).
+
+* H_l(k) = <Re X_0 F_l^{w*}>_k - S_l(k)            (Eq. H_ell)
+* Q_l(k) = <Re X_l N_0^*>_k - S_l(k), X_l = L_l X_0  (Eq. Q_ell, by the addition theorem)
+
+Scoccimarro, l on leg 1 (Sec. 5.4.1, built from Lemma 1's ring average Eq. I_l0l):
+  N^(l)(i,j,k) = (2l+1)/I33 [ delta_l0 S + Q_l(k_i) + L_l(c12) H_l(k_j) + L_l(c13) H_l(k_k) ]
+with the cosines between legs from bin centres, c12 = (c_k^2 - c_i^2 - c_j^2)/(2 c_i c_j),
+c13 = (c_j^2 - c_i^2 - c_k^2)/(2 c_i c_k) (reading: the paper does not say which k is used).
+
+Compressed B_l0l (Sec. 5.4.3, boxed result), t = c_i/c_j:
+  N(i,j) = (2l+1)/I33 [ delta_l0 S + (-1)^l g_l(t) H_l(k_i) + (-1)^l g_l(1/t) H_l(k_j)
+                        + sum_m w_m Q_l(k_m) / sum_m w_m ]
+over shells m of width dk centred at (m+1/2) dk with centre in [|c_i - c_j| + dk/2, c_i + c_j - dk/2]
+and weight w_m = N_mode(m)/c_m.  Readings: the printed i=j=k term omits the 1/I that the Sugiyama
+form carries (kept here); the printed i=j!=k term divides a mode-averaged Q by sum N_mode/k3,
+which is not dimensionally consistent, so the mode count is applied to the averaged Q as the
+V_ring V_dot ~ 1/k3 derivation of Sec. 5.4.2 requires.
+
+Parity unpinned as an exact reference: these are thin-shell approximations (Sec. 5.3).  The tests
+check them statistically against Poisson catalogues (the subtracted monopole averages to zero and
+the raw monopole averages to the full shot noise) and check the g_l factors separately.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import harmonics as H
+from . import mesh as M
+
+
+def _mu(spec):
+    (kx, ky, kz), _ = M.kvectors(spec["n"], spec["box"])
+    d = np.asarray(spec["los_dir"], dtype=np.float64)
+    d = d / np.linalg.norm(d)
+    kk = np.sqrt(kx * kx + ky * ky + kz * kz)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        return np.where(kk > 0, (kx * d[0] + ky * d[1] + kz * d[2]) / np.where(kk > 0, kk, 1.0), 0.0)
+
+
+def shell_terms(spec, X0, N0, kbins, ell, s3):
+    """(H_l, Q_l, N_mode) on the given bins."""
+    b, _ = M.bin_index(spec["n"], spec["box"], *kbins)
+    nb = kbins[2]
+    lmu = H.legendre(ell, _mu(spec))
+    cross, cnt = M.bin_average(lmu * np.real(X0 * np.conj(N0)), b, nb)
+    lavg, _ = M.bin_average(lmu, b, nb)
+    hval = cross - s3 * lavg
+    return hval, hval.copy(), cnt
+
+
+def qgrid(kbins):
+    """Shells [m dk, (m+1) dk) covering 0 .. 2 k_max for the compressed i=j!=k term."""
+    kmin, dk, nb = kbins
+    kmax = kmin + nb * dk
+    nq = int(np.ceil(2.0 * kmax / dk)) + 1
+    return (0.0, dk, nq)
+
+
+def analytic_shot_noise(spec, X0, N0, kbins, tri, prs, sc, scoc_ells, tripo_ells):
+    kmin, dk, nb = kbins
+    c = np.array([kmin + (b + 0.5) * dk for b in range(nb)])
+    i33, s3 = sc["I33"], sc["S3"]
+    qb = qgrid(kbins)
+    cq = np.array([(m + 0.5) * dk for m in range(qb[2])])
+    shot_B, shot_BB, parts = {}, {}, {}
+    for ell in sorted(set(scoc_ells) | set(tripo_ells)):
+        hl, ql, _ = shell_terms(spec, X0, N0, kbins, ell, s3)
+        hq, qq, nq = shell_terms(spec, X0, N0, qb, ell, s3)
+        parts[ell] = dict(H=hl, Q=ql, Qq=qq, Nq=nq)
+        if ell in scoc_ells:
+            out = np.empty(len(tri))
+            for t, (i, j, k) in enumerate(tri):
+                c12 = (c[k] ** 2 - c[i] ** 2 - c[j] ** 2) / (2.0 * c[i] * c[j])
+                c13 = (c[j] ** 2 - c[i] ** 2 - c[k] ** 2) / (2.0 * c[i] * c[k])
+                v = (s3 if ell == 0 else 0.0) + ql[i]
+                v += float(H.legendre(ell, c12)) * hl[j] + float(H.legendre(ell, c13)) * hl[k]
+                out[t] = (2 * ell + 1) / i33 * v
+            shot_B[ell] = out
+        if ell in tripo_ells:
+            out = np.empty(len(prs))
+            sgn = (-1.0) ** ell
+            for t, (i, j) in enumerate(prs):
+                v = (s3 if ell == 0 else 0.0)
+                v += sgn * H.g_ell(ell, c[i] / c[j]) * hl[i]
+                v += sgn * H.g_ell(ell, c[j] / c[i]) * hl[j]
+                lo = abs(c[i] - c[j]) + 0.5 * dk
+                hi = c[i] + c[j] - 0.5 * dk
+                sel = (cq >= lo - 1e-9 * dk) & (cq <= hi + 1e-9 * dk) & (nq > 0)
+                wts = nq[sel] / cq[sel]
+                v += np.sum(wts * qq[sel]) / np.sum(wts) if wts.size else 0.0
+                out[t] = (2 * ell + 1) / i33 * v
+            shot_BB[ell] = out
+    return shot_B, shot_BB, parts

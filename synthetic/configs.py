@@ -1,0 +1,30 @@
+"""Workload definitions (sizes and geometry only) for the measured configurations.
+
+Each entry names a workload by what it is.  ``seed`` follows seed = 1000*index + mock.
+"""
+from __future__ import annotations
+
+WORKLOADS = {
+    # Plain FP64 Yamamoto P0,P2,P4 on a 64^3 CIC mesh, survey geometry, unit weights.
+    "p024_fp64_64": dict(
+        kind="power", n=64, box=1000.0, distance=1500.0, assign=2, interlace=0, n_gal=50_000,
+        n_ran=500_000, n_gen=64, fkp_p0=None, kmin=0.0, dk=0.01, nbins=20, ells=(0, 2, 4),
+        modified=(), precision="fp64", seed=0,
+    ),
+    # Yamamoto P0,P2,P4 + modified P4b,P6b,P8b, 512^3 TSC interlaced, FKP weights, mixed precision.
+    "p024b_mixed_512": dict(
+        kind="power", n=512, box=2000.0, distance=2500.0, assign=3, interlace=1, n_gal=2_000_000,
+        n_ran=20_000_000, n_gen=256, fkp_p0=1.0e4, kmin=0.0, dk=0.01, nbins=80, ells=(0, 2, 4),
+        modified=(4, 6, 8), precision="mixed", seed=1000,
+    ),
+    # Scoccimarro B0,B2 + compressed B_000, B_202 with analytic shot noise, periodic 256^3 TSC.
+    "bispec_256": dict(
+        kind="bispec", n=256, box=1000.0, assign=3, interlace=1, n_gal=1_000_000, n_gen=256,
+        kmin=0.01, dk=0.01, nbins=19, scoc_ells=(0, 2), tripo_ells=(0, 2), precision="mixed",
+        seed=2000,
+    ),
+}
+
+
+def workload(name):
+    return dict(WORKLOADS[name])

@@ -1,0 +1,155 @@
+"""Pins for oracle.bispec / oracle.shot."""
+from math import pi
+from types import SimpleNamespace
+
+import numpy as np
+import pytest
+
+from oracle import bispec as B
+from oracle import mesh as M
+from oracle import power as P
+from synthetic import make_periodic_catalog, make_survey_catalogs
+
+
+def _periodic_spec(n, box, assign=3, interlace=1):
+    return dict(n=n, box=box, origin=(0.0, 0.0, 0.0), assign=assign, interlace=interlace,
+                los="global", los_dir=(0.0, 0.0, 1.0), periodic=1)
+
+
+@pytest.fixture(scope="module")
+def tiny_periodic():
+    cat = make_periodic_catalog(4000, 300.0, 16, seed=11)
+    spec = _periodic_spec(24, 300.0)
+    sc = P.catalog_scalars(cat, None, 300.0)
+    meshes = P.fkp_meshes(spec, cat, None, sc)
+    fields, _ = P.fields_plain(spec, meshes, [0])
+    return spec, cat, sc, fields[0]
+
+
+def test_triangle_count_for_19_bins():
+    """19 bins of 0.01 from 0.01 with the centre closure rule give 805 of 1330 ordered triples."""
+    tri = B.triangles((0.01, 0.01, 19))
+    assert len(tri) == 805
+    assert np.all(tri[:, 0] <= tri[:, 1]) and np.all(tri[:, 1] <= tri[:, 2])
+
+
+def test_fft_closure_equals_brute_force(tiny_periodic):
+    spec, cat, sc, X0 = tiny_periodic
+    kb = (0.02, 0.02, 5)  # k_max = 0.12 < k_N/2 = 0.126: no aliasing of the closure
+    tri = B.triangles(kb)
+    X2 = B.los_field(spec, X0, 2)
+    Bfft, nt, raw = B.scoccimarro_fft(spec, X0, {2: X2}, kb, tri, sc["I33"], (0, 2))
+    s0, c0 = B.scoccimarro_brute(spec, X0, X0, kb, tri)
+    s2, _ = B.scoccimarro_brute(spec, X0, X2, kb, tri)
+    np.testing.assert_allclose(nt, c0, rtol=1e-12, atol=1e-9)
+    scale = np.max(np.abs(s0))
+    np.testing.assert_allclose(raw[0], np.real(s0), atol=1e-12 * scale)
+    np.testing.assert_allclose(raw[2], np.real(s2), atol=1e-12 * scale)
+    assert np.max(np.abs(np.imag(s0))) < 1e-9 * scale
+    ok = c0 > 0
+    np.testing.assert_allclose(Bfft[0][ok], np.real(s0[ok]) / (sc["I33"] * c0[ok]), rtol=1e-10)
+
+
+def test_compressed_fft_equals_pair_enumeration(tiny_periodic):
+    spec, cat, sc, X0 = tiny_periodic
+    kb = (0.02, 0.03, 3)
+    prs = B.pairs(kb)
+    X2 = B.los_field(spec, X0, 2)
+    _, s, cnt = B.compressed_fft(spec, X0, X2, kb, prs, sc["I33"], 2)
+    n = spec["n"]
+    _, lists = B._mode_lists(spec, kb)
+    for t, (i, j) in enumerate(prs):
+        q1, q2 = lists[i], lists[j]
+        q3 = (-(q1[:, None, :] + q2[None, :, :])) % n
+        i1, i2 = q1 % n, q2 % n
+        v = (X0[i1[:, 0], i1[:, 1], i1[:, 2]][:, None] * X0[i2[:, 0], i2[:, 1], i2[:, 2]][None, :]
+             * X2[q3[..., 0], q3[..., 1], q3[..., 2]])
+        assert abs(np.sum(v) - s[t]) < 1e-11 * np.sum(np.abs(v))
+        assert cnt[i] == len(q1) and cnt[j] == len(q2)
+
+
+def test_compression_identity(tiny_periodic):
+    """sum_k N_T(i,j,k) B^(leg 3)(i,j,k) over k3 bins covering [0, k_i + k_j] = N_i N_j B_l0l(i,j)
+    (pre-shot), Sec. 4: the compressed estimator is the Scoccimarro one summed along k3."""
+    spec, cat, sc, X0 = tiny_periodic
+    dk = 0.02
+    kb = (0.0, dk, 12)
+    X2 = B.los_field(spec, X0, 2)
+    f0 = B.shell_fields(spec, X0, kb)
+    f2 = B.shell_fields(spec, X2, kb)
+    n = spec["n"]
+    _, _, cnt = B.compressed_fft(spec, X0, X2, kb, np.array([[1, 2]]), sc["I33"], 2)
+    for (i, j) in [(1, 1), (1, 2), (2, 3)]:
+        lhs = sum(np.sum(f0[i] * f0[j] * f2[k]) for k in range(kb[2])) / n**3
+        val, s, _ = B.compressed_fft(spec, X0, X2, kb, np.array([[i, j]]), sc["I33"], 2)
+        assert abs(lhs - s[0]) < 1e-10 * (abs(lhs) + abs(s[0]) + 1e-30)
+        assert val[0] == pytest.approx(5 * s[0] / (sc["I33"] * cnt[i] * cnt[j]), rel=1e-12)
+
+
+def test_compressed_collapse_matches_explicit_3j():
+    """The collapsed B_l0l (Fourier-space Yamamoto F_l at the k3 leg) equals the definition with the
+    explicit (m1, M) sum and Wigner 3j symbols, endpoint line of sight (survey geometry)."""
+    g, r, origin = make_survey_catalogs(1500, 12000, 600.0, 900.0, 12, seed=21, fkp_p0=1e4)
+    spec = dict(n=20, box=600.0, origin=tuple(origin), assign=2, interlace=0, los="endpoint",
+                observer=(0.0, 0.0, 0.0))
+    sc = P.catalog_scalars(g, r)
+    meshes = P.fkp_meshes(spec, g, r, sc)
+    fields, _ = P.fields_plain(spec, meshes, [0, 2])
+    kb = (0.011, 0.0135, 3)  # k_max = 0.0515 < k_N/2 = 0.052
+    prs = B.pairs(kb)
+    val, _, _ = B.compressed_fft(spec, fields[0], fields[2], kb, prs, sc["I33"], 2)
+    exp = B.compressed_explicit(spec, meshes, kb, prs, sc["I33"], 2)
+    assert np.max(np.abs(np.imag(exp))) < 1e-9 * np.max(np.abs(val))
+    np.testing.assert_allclose(np.real(exp), val, rtol=1e-9, atol=1e-12 * np.max(np.abs(val)))
+
+
+def test_triangle_count_thin_shell_limit():
+    """N_T -> V_T / k_f^6 = 8 pi^2 c1 c2 c3 dk^3 / k_f^6 (Sec. 5.2, Appendix I) for triangles away
+    from the closure boundary and the smallest shells (k_max < k_N/2: no aliasing)."""
+    n, box = 64, 1000.0
+    kf = 2 * pi / box
+    spec = _periodic_spec(n, box, 2, 0)
+    kb = (4 * kf, 2 * kf, 6)
+    tri = B.triangles(kb)
+    ind = B.shell_fields(spec, None, kb, ones=True)
+    c = B.bin_centres(kb)
+    ratios = []
+    for i, j, k in tri:
+        if c[i] + c[j] - c[k] >= 1.5 * kb[1] and i >= 2:
+            nt = np.sum(ind[i] * ind[j] * ind[k]) / n**3
+            vt = 8 * pi**2 * c[i] * c[j] * c[k] * kb[1] ** 3 / kf**6
+            ratios.append(nt / vt)
+    ratios = np.array(ratios)
+    assert ratios.size >= 10
+    assert np.all(np.abs(ratios - 1) < 0.06)
+
+
+@pytest.mark.slow
+def test_poisson_shot_noise_is_subtracted():
+    """Uniform Poisson catalogues (no clustering): the raw monopole B_0 averages to the analytic
+    shot noise, and B_l - N^(l), B_l0l - N_l0l average to zero within the sample scatter (Sec. 5.1:
+    B_shot = sum P/n + 1/n^2)."""
+    n, box, npart, nseed = 32, 400.0, 6000, 12
+    kb = (0.03, 0.03, 3)  # k_max = 0.12 < k_N/2 = 0.126
+    rows = {k: [] for k in ("B0", "N0", "B2", "N2", "BB0", "NB0", "BB2", "NB2")}
+    for seed in range(nseed):
+        rng = np.random.default_rng(4000 + seed)
+        pos = rng.random((npart, 3)) * box
+        cat = SimpleNamespace(pos=pos, w=np.ones(npart), nbar=np.full(npart, npart / box**3))
+        spec = _periodic_spec(n, box)
+        res = B.bispectrum(spec, cat, None, kb, (0, 2), (0, 2), shot=True)
+        rows["B0"].append(res["B"][0])
+        rows["N0"].append(res["shot_B"][0])
+        rows["B2"].append(res["B"][2])
+        rows["N2"].append(res["shot_B"][2])
+        rows["BB0"].append(res["BB"][0])
+        rows["NB0"].append(res["shot_BB"][0])
+        rows["BB2"].append(res["BB"][2])
+        rows["NB2"].append(res["shot_BB"][2])
+    r = {k: np.array(v) for k, v in rows.items()}
+    level = (box**3 / npart) ** 2
+    for sig, noi in (("B0", "N0"), ("B2", "N2"), ("BB0", "NB0"), ("BB2", "NB2")):
+        d = r[sig] - r[noi]
+        se = d.std(axis=0, ddof=1) / np.sqrt(nseed)
+        assert np.all(np.abs(d.mean(axis=0)) < 4 * se + 0.02 * level), sig
+    assert np.all(np.abs(r["N0"].mean(axis=0) / level - 1) < 0.1)
