@@ -1,0 +1,173 @@
+/*
+ * npc.h -- C ABI of the GB300 FFT multipole estimator library (libnpc.so).
+ *
+ * Implements, on one CUDA device, the Fourier-space clustering estimators of Xie et al.,
+ * "Efficient estimators for power spectrum and bispectrum multipole measurements":
+ *   - Yamamoto power-spectrum multipoles P_l(k) evaluated from the m >= 0 spherical-harmonic
+ *     weighted transforms only (Sec. 2.1, Eqs. key1, F_lm_SIC, new_F_ell, pk_final);
+ *   - the modified high-order even multipoles P_4b, P_6b, P_8b built from l <= 4 fields
+ *     (Sec. 3, Eqs. legendre, Plnew, Pllp);
+ *   - Scoccimarro bispectrum multipoles B_l (Sec. 2.2, Eq. bi_sco) and the compressed TripoSH
+ *     multipoles B_l0l (Sec. 4, Eq. new_bispec) with their analytic shot noise (Sec. 5.4).
+ *
+ * Conventions shared by every entry point
+ *   Mesh      cubic, n^3 cells, side `box`, covering [origin, origin + box); a particle at
+ *             position x has grid coordinate s = (x - origin) * (n / box), evaluated in float64.
+ *             Cells are wrapped periodically.  CIC (assign = 2) or TSC (assign = 3); with
+ *             interlace = 1 a second mesh assigns s + 1/2 (its point j sits at origin+(j-1/2)H).
+ *   Fourier   e^{-i k.x}; W(k) = prod_i sinc(pi k_i / 2k_N)^assign is divided out (Sec. 3.1,
+ *             Eq. compensation); the two interlaced meshes are combined as
+ *             1/2 [S_a + e^{i H (kx+ky+kz)/2} S_b].
+ *   k-bins    modes whose three integer indices lie in (-n/2, n/2), DC excluded, bin
+ *             b = floor((k_f |i| - kmin)/dk) with k_f = 2 pi/box (float64), kept if 0 <= b < nbins.
+ *   Threads   a context may be used by one host thread at a time.  All device work of a call is
+ *             enqueued on the context's stream; calls whose outputs are host memory synchronise
+ *             that stream before returning.
+ *   Errors    every call returns npc_status; nothing aborts or throws across the ABI.  On error
+ *             the outputs are unspecified and npc_last_error() holds a message.  Invalid
+ *             arguments are rejected before any device work is enqueued.
+ *   Memory    the caller owns every input and output buffer; the context owns and reuses its
+ *             device workspace (grown on demand, released by npc_destroy).
+ */
+#ifndef NPC_H
+#define NPC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  NPC_OK = 0,
+  NPC_ERR_INVALID_ARG = 1, /* malformed spec, null pointer, unsupported size or combination */
+  NPC_ERR_OOM = 2,         /* device workspace allocation failed */
+  NPC_ERR_CUDA = 3,        /* a CUDA runtime call failed (message in npc_last_error) */
+  NPC_ERR_UNSUPPORTED = 4, /* valid request outside what this build implements */
+  NPC_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+  NPC_ERR_NUMERIC = 6      /* non-finite or degenerate normalisation (e.g. empty catalogue) */
+} npc_status;
+
+typedef enum { NPC_PREC_FP64 = 0, NPC_PREC_MIXED = 1 } npc_precision;
+/* NPC_PREC_FP64: float64 meshes, transforms and sums.  NPC_PREC_MIXED: float32 meshes and
+ * transforms, float64 catalogue scalars and k-bin accumulators. */
+
+typedef struct npc_ctx npc_ctx;
+
+/* Mesh, box and line-of-sight specification. */
+typedef struct {
+  int32_t n;           /* cells per side: power of two, 16 <= n <= 1024 */
+  double box;          /* side length of the cubic mesh (length units of the positions) */
+  double origin[3];    /* lower corner of the mesh */
+  int32_t assign;      /* 2 = CIC, 3 = TSC */
+  int32_t interlace;   /* 0 or 1 */
+  int32_t periodic;    /* 1: periodic box, no randoms (delta = n - mean); 0: survey with randoms */
+  int32_t los;         /* 0: endpoint line of sight xhat from `observer`; 1: global `los_dir` */
+  double los_dir[3];   /* used when los == 1 (need not be normalised) */
+  double observer[3];  /* used when los == 0 */
+} npc_mesh_spec;
+
+/* A catalogue: positions [n][3] (x,y,z interleaved), weights [n], number densities [n]. */
+typedef struct {
+  const void* pos;     /* required when n > 0 */
+  const void* w;       /* NULL: all weights 1 */
+  const void* nbar;    /* NULL allowed only where nbar is not used (data catalogue, periodic) */
+  int64_t n;           /* number of objects, >= 0 */
+  int32_t dtype;       /* 0 = float32, 1 = float64 (all three arrays) */
+  int32_t on_device;   /* 1: device pointers on the context's device; 0: host pointers */
+} npc_catalog;
+
+/* Half-open bins [kmin + b dk, kmin + (b+1) dk), b = 0..nbins-1; dk > 0, kmin >= 0. */
+typedef struct {
+  double kmin;
+  double dk;
+  int32_t nbins;       /* 1 <= nbins <= 4096 */
+} npc_kbins;
+
+/* Context ------------------------------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t to enqueue on, or
+ * NULL for a stream owned by the context.  The stream must outlive the context. */
+npc_status npc_create(npc_ctx** out, int device, void* cuda_stream);
+/* Release the context and its device workspace (synchronises its stream).  NULL is accepted. */
+npc_status npc_destroy(npc_ctx* ctx);
+/* Static string for a status code. */
+const char* npc_status_string(npc_status s);
+/* Copy the last error message of `ctx` (NUL-terminated, truncated to n bytes). */
+npc_status npc_last_error(npc_ctx* ctx, char* buf, size_t n);
+/* Library version string "major.minor.patch". */
+const char* npc_version(void);
+
+/* Diagnostics of the last completed call on `ctx`. */
+typedef struct {
+  int32_t n_transforms;        /* Y_lm-weighted forward transforms per mesh phase, counted as in
+                                  Table 1 of the paper (one per S_l^m with m >= 0) */
+  int32_t n_r2c_equivalent;    /* the same work counted in real-to-complex transforms per phase */
+  int32_t n_phases;            /* 1 or 2 (interlacing) */
+  int32_t n_kernel_launches;   /* kernels enqueued by the call */
+  int64_t workspace_bytes;     /* device workspace held by the context after the call */
+} npc_stats;
+npc_status npc_last_stats(npc_ctx* ctx, npc_stats* out);
+
+/* Catalogue scalars (Sec. 2.1, Yamamoto estimator; Sec. 2.2 for I33) --------------------------
+ * out[0..7] = { alpha, I22, I33, N0, S3, sum_w(data), sum_w(randoms), sum_w2 } with
+ *   alpha = sum_g w / sum_r w,  I22 = alpha sum_r nbar w^2,  I33 = alpha sum_r nbar^2 w^3,
+ *   N0 = (sum_g w^2 + alpha^2 sum_r w^2)/I22,  S3 = sum_g w^3 - alpha^3 sum_r w^3,
+ *   sum_w2 = sum_g w^2 + alpha^2 sum_r w^2.
+ * randoms == NULL means a periodic box of side `box`: alpha = 0, I22 = W^2/V, I33 = W^3/V^2,
+ * N0 = sum_g w^2/I22, S3 = sum_g w^3 with W = sum_g w, V = box^3.
+ * `out` is host memory when out_on_device == 0, else device memory (then the call is async).
+ * Reductions are float64 and bitwise reproducible run to run (fixed reduction order). */
+npc_status npc_catalog_scalars(npc_ctx* ctx, const npc_catalog* data, const npc_catalog* randoms,
+                               double box, double* out, int32_t out_on_device);
+
+/* Power-spectrum multipoles (Sec. 2.1 Eq. pk_final; Sec. 3 Eqs. Plnew, Pllp) ------------------
+ * ell_mask: bit l requests P_l, l in {0, 2, 4}.  modified_mask: bits 4, 6, 8 request P_4b, P_6b,
+ * P_8b (these need the l = 2 and l = 4 fields and are computed from them; Eq. Plnew).
+ * Output `out` (float64), length npc_power_out_len(), rows of nbins:
+ *   [0]            k_eff  = mean |k| over the modes of the bin
+ *   [1]            N_modes (number of full-grid modes in the bin)
+ *   [2 .. 2+nl)    P_l for the requested l in increasing order, shot noise subtracted (l = 0)
+ *   [.. + nm)      P_4b, P_6b, P_8b for the requested ones in increasing order
+ *   then 8 scalars as in npc_catalog_scalars.
+ * Empty bins report k_eff = N_modes = P = 0.  data->n may be 0 only for a survey (randoms give
+ * a zero field and P_0 = -N0); a periodic box needs data->n > 0 (else NPC_ERR_NUMERIC).
+ * The transforms are evaluated for m >= 0 only: per mesh phase (l+1) S_l^m fields per l, i.e.
+ * 1 + 3 + 5 = 9 for l <= 4 (Table 1); with a global line of sight F_l(k) = L_l(khat.los) F_0(k)
+ * and a single transform suffices. */
+npc_status npc_power_multipoles(npc_ctx* ctx, const npc_mesh_spec* mesh, const npc_catalog* data,
+                                const npc_catalog* randoms, const npc_kbins* bins,
+                                uint32_t ell_mask, uint32_t modified_mask, npc_precision prec,
+                                double* out, int32_t out_on_device);
+/* Number of doubles written by npc_power_multipoles for this request (0 if the masks are bad). */
+int64_t npc_power_out_len(const npc_kbins* bins, uint32_t ell_mask, uint32_t modified_mask);
+
+/* Bispectrum multipoles (Sec. 2.2 Eq. bi_sco; Sec. 4 Eq. new_bispec; Sec. 5.4 shot noise) ------
+ * Periodic box with a global line of sight (mesh->periodic = 1, mesh->los = 1, randoms = NULL).
+ * Triangles: bins i <= j <= k closing at their centres, c_k <= c_i + c_j, c_b = kmin+(b+1/2)dk,
+ * in lexicographic (i, j, k) order; pairs: i <= j in lexicographic order.  The largest bin edge
+ * must not exceed k_N/2 (the closure would alias otherwise), else NPC_ERR_UNSUPPORTED.
+ * scoc_ell_mask: bits 0, 2 request B_0, B_2 (l on the first, smallest side).
+ * tripo_ell_mask: bits 0, 2 request the compressed B_000, B_202.
+ * shot: 1 subtracts the analytic shot noise (and reports it), 0 leaves the raw estimates.
+ * Output `out` (float64), length from npc_bispectrum_layout():
+ *   [ns][ntri]  B_l          [ns][ntri]  shot noise of B_l      [ntri] N_T (closed triplets)
+ *   [nt][npair] B_l0l        [nt][npair] shot noise of B_l0l    [nbins] N_modes
+ *   then 8 scalars as in npc_catalog_scalars. */
+npc_status npc_bispectrum(npc_ctx* ctx, const npc_mesh_spec* mesh, const npc_catalog* data,
+                          const npc_catalog* randoms, const npc_kbins* bins,
+                          uint32_t scoc_ell_mask, uint32_t tripo_ell_mask, int32_t shot,
+                          npc_precision prec, double* out, int32_t out_on_device);
+/* Sizes for npc_bispectrum.  Any output pointer may be NULL. */
+npc_status npc_bispectrum_layout(const npc_kbins* bins, uint32_t scoc_ell_mask,
+                                 uint32_t tripo_ell_mask, int64_t* ntri, int64_t* npairs,
+                                 int64_t* out_len);
+/* Triangle bin indices [ntri][3] (host memory, capacity `cap` triangles). */
+npc_status npc_bispectrum_triangles(const npc_kbins* bins, int32_t* tri, int64_t cap,
+                                    int64_t* ntri);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NPC_H */

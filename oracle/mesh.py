@@ -1,7 +1,7 @@
 """Mesh construction, Fourier grid and k-binning (oracle; test infrastructure only).
 
 Mesh: cubic, n^3 cells of size H = box/n covering [origin, origin + box) (periodic index wrap).
-Array index order is (x, y, z).  A particle at grid coordinate s = (pos - origin)/H is assigned by
+Array index order is (x, y, z).  A particle at grid coordinate s = (pos - origin) n/box is assigned by
 * CIC (assign = 2): base i0 = floor(s), d = s - i0, weights (1-d, d) at (i0, i0+1);
 * TSC (assign = 3): base i0 = floor(s + 1/2), d = s - i0,
   weights (0.5(0.5-d)^2, 0.75-d^2, 0.5(0.5+d)^2) at (i0-1, i0, i0+1).
@@ -26,9 +26,12 @@ import numpy as np
 
 
 def grid_coords(pos, origin, box, n, shift=0.0):
-    """s = (pos - origin)/H (+ shift), float64."""
-    h = box / n
-    return (np.asarray(pos, dtype=np.float64) - np.asarray(origin, dtype=np.float64)) / h + shift
+    """s = (pos - origin) * (n/box) (+ shift), float64.
+
+    The cell a particle lands in is an integer decided in floating point; the GPU library makes
+    the same decision with the same float64 expression (difference, then product with n/box)."""
+    inv_h = n / box
+    return (np.asarray(pos, dtype=np.float64) - np.asarray(origin, dtype=np.float64)) * inv_h + shift
 
 
 def paint(s, weights, n, assign):

@@ -228,6 +228,46 @@ def power_multipoles(spec, data, randoms, kbins, ells=(0, 2, 4), modified=(), me
     return res
 
 
+def power_monopole_rfft(spec, data, randoms, kbins):
+    """P_0 alone (Eq. Hand17 with l = 0, where no Y_lm weighting is needed) from real-to-complex
+    transforms, for meshes too large for the full-m path.  Each stored mode of the half grid
+    (kz > 0) also stands for -k, whose |X|^2 is equal; the kz = 0 plane holds both members of each
+    pair.  Returns (P_0, N_modes, scalars).  Pinned to power_multipoles in the tests."""
+    n = spec["n"]
+    sc = catalog_scalars(data, randoms, spec["box"])
+    meshes = fkp_meshes(spec, data, randoms, sc)
+    parts = [np.fft.rfftn(m) for m in meshes]
+    ii = M.int_freqs(n)
+    iz = np.arange(n // 2 + 1)
+    a = np.pi * ii / n
+    az = np.pi * iz / n
+    if len(parts) == 2:
+        ph = np.exp(1j * (a[:, None, None] + a[None, :, None] + az[None, None, :]))
+        X = 0.5 * (parts[0] + ph * parts[1])
+        del ph
+    else:
+        X = parts[0]
+    del parts
+    p = spec["assign"]
+    s1 = np.where(ii == 0, 1.0, np.sin(a) / np.where(ii == 0, 1.0, a)) ** p
+    sz = np.where(iz == 0, 1.0, np.sin(az) / np.where(iz == 0, 1.0, az)) ** p
+    X /= s1[:, None, None] * s1[None, :, None] * sz[None, None, :]
+    kmin, dk, nb = kbins
+    kf = 2.0 * np.pi / spec["box"]
+    n2 = (ii[:, None, None] ** 2 + ii[None, :, None] ** 2 + iz[None, None, :] ** 2).astype(np.float64)
+    b = np.floor((kf * np.sqrt(n2) - kmin) / dk)
+    ok = (b >= 0) & (b < nb) & (n2 > 0)
+    nyq = -(n // 2)
+    ok &= (ii[:, None, None] != nyq) & (ii[None, :, None] != nyq) & (iz[None, None, :] != n // 2)
+    wgt = np.where(iz == 0, 1.0, 2.0)[None, None, :] * ok
+    bb = np.where(ok, b, 0).astype(np.int64).ravel()
+    cnt = np.bincount(bb, weights=wgt.ravel(), minlength=nb)
+    s0 = np.bincount(bb, weights=(wgt * (X.real**2 + X.imag**2)).ravel(), minlength=nb)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        p0 = np.where(cnt > 0, s0 / np.where(cnt > 0, cnt, 1.0) / sc["I22"] - sc["N0"], 0.0)
+    return p0, cnt, sc
+
+
 def direct_dft(pos, weights, kvecs, origin):
     """sum_p w_p e^{-i k.(x_p - origin)} for a list of k vectors (brute force, for pins)."""
     x = np.asarray(pos, dtype=np.float64) - np.asarray(origin, dtype=np.float64)

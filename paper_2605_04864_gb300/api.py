@@ -1,0 +1,168 @@
+"""Python front end over the C ABI: builds the C structs from NumPy arrays or torch tensors,
+calls the library, and reshapes the flat output.  PyTorch supplies device memory and the current
+CUDA stream; no estimator arithmetic happens here.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import binding as B
+
+_CTX = {}
+
+
+def _stream_ptr(device):
+    try:
+        import torch
+
+        if torch.cuda.is_available():
+            return C.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+    except Exception:  # pragma: no cover - torch without CUDA
+        pass
+    return C.c_void_p(0)
+
+
+def context(device=0):
+    """A library context bound to ``device`` and torch's current stream on it (cached)."""
+    stream = _stream_ptr(device)
+    key = (device, stream.value)
+    if key not in _CTX:
+        h = C.c_void_p()
+        B.check(B.npc_create(C.byref(h), device, stream))
+        _CTX[key] = h
+    return _CTX[key]
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+class _Keep:
+    """Holds converted arrays alive for the duration of a call."""
+
+    def __init__(self):
+        self.refs = []
+
+    def keep(self, x):
+        self.refs.append(x)
+        return x
+
+
+def make_catalog(cat, keep, dtype=None):
+    """npc_catalog from an object with .pos/.w/.nbar (NumPy or torch; device tensors stay on device)."""
+    if cat is None:
+        return None
+    pos, w, nbar = cat.pos, getattr(cat, "w", None), getattr(cat, "nbar", None)
+    c = B.npc_catalog()
+    if _is_torch(pos):
+        import torch
+
+        dt = pos.dtype
+        assert dt in (torch.float32, torch.float64)
+        for t in (pos, w, nbar):
+            if t is not None:
+                assert t.dtype == dt and t.is_contiguous() and t.device == pos.device
+        c.pos = pos.data_ptr() if pos.numel() else None
+        c.w = w.data_ptr() if w is not None and w.numel() else None
+        c.nbar = nbar.data_ptr() if nbar is not None and nbar.numel() else None
+        c.n = pos.shape[0]
+        c.dtype = 1 if dt == torch.float64 else 0
+        c.on_device = 1 if pos.is_cuda else 0
+        keep.keep((pos, w, nbar))
+        return c
+    dt = np.dtype(dtype or np.asarray(pos).dtype)
+    if dt not in (np.float32, np.float64):
+        dt = np.dtype(np.float64)
+    pos = keep.keep(np.ascontiguousarray(pos, dtype=dt).reshape(-1, 3))
+    c.pos = pos.ctypes.data if pos.size else None
+    if w is not None:
+        w = keep.keep(np.ascontiguousarray(w, dtype=dt))
+        c.w = w.ctypes.data
+    if nbar is not None:
+        nbar = keep.keep(np.ascontiguousarray(nbar, dtype=dt))
+        c.nbar = nbar.ctypes.data
+    c.n = pos.shape[0]
+    c.dtype = 1 if dt == np.float64 else 0
+    c.on_device = 0
+    return c
+
+
+def make_spec(n, box, origin=(0.0, 0.0, 0.0), assign=3, interlace=1, periodic=0, los_dir=None,
+              observer=(0.0, 0.0, 0.0)):
+    s = B.npc_mesh_spec()
+    s.n, s.box = int(n), float(box)
+    s.origin[:] = [float(v) for v in origin]
+    s.assign, s.interlace, s.periodic = int(assign), int(interlace), int(periodic)
+    if los_dir is None:
+        s.los = 0
+        s.los_dir[:] = [0.0, 0.0, 1.0]
+    else:
+        s.los = 1
+        s.los_dir[:] = [float(v) for v in los_dir]
+    s.observer[:] = [float(v) for v in observer]
+    return s
+
+
+def _prec(p):
+    return {"fp64": B.NPC_PREC_FP64, "mixed": B.NPC_PREC_MIXED}[p] if isinstance(p, str) else int(p)
+
+
+def power_multipoles(data, randoms, n, box, origin=(0.0, 0.0, 0.0), assign=3, interlace=1, kbins=(0.0, 0.01, 10),
+                     ells=(0, 2, 4), modified=(), precision="mixed", periodic=None, los_dir=None,
+                     observer=(0.0, 0.0, 0.0), device=0, out=None):
+    """Yamamoto P_l (and P_lb).  Returns a dict of NumPy arrays, or fills the device tensor ``out``."""
+    keep = _Keep()
+    if periodic is None:
+        periodic = randoms is None
+    spec = make_spec(n, box, origin, assign, interlace, periodic, los_dir, observer)
+    kb = B.npc_kbins(float(kbins[0]), float(kbins[1]), int(kbins[2]))
+    emask = sum(1 << int(l) for l in ells)
+    mmask = sum(1 << int(l) for l in modified)
+    length = B.npc_power_out_len(C.byref(kb), emask, mmask)
+    if length <= 0:
+        raise ValueError("bad multipole request")
+    d = make_catalog(data, keep)
+    r = make_catalog(randoms, keep)
+    ctx = context(device)
+    if out is not None:
+        B.check(B.npc_power_multipoles(ctx, C.byref(spec), C.byref(d), C.byref(r) if r else None, C.byref(kb),
+                                       emask, mmask, _prec(precision), C.c_void_p(out.data_ptr()), 1), ctx)
+        return out
+    buf = np.zeros(length)
+    B.check(B.npc_power_multipoles(ctx, C.byref(spec), C.byref(d), C.byref(r) if r else None, C.byref(kb),
+                                   emask, mmask, _prec(precision), buf.ctypes.data_as(C.c_void_p), 0), ctx)
+    return unpack_power(buf, kbins[2], ells, modified)
+
+
+def unpack_power(buf, nbins, ells, modified):
+    buf = np.asarray(buf)
+    res = {"k_eff": buf[0:nbins].copy(), "nmodes": buf[nbins:2 * nbins].copy(), "P": {}, "Pmod": {}}
+    row = 2
+    for l in sorted(ells):
+        res["P"][l] = buf[row * nbins:(row + 1) * nbins].copy()
+        row += 1
+    for l in sorted(modified):
+        res["Pmod"][l] = buf[row * nbins:(row + 1) * nbins].copy()
+        row += 1
+    sc = buf[row * nbins:row * nbins + 8]
+    res["scalars"] = dict(zip(("alpha", "I22", "I33", "N0", "S3", "sum_wg", "sum_wr", "sum_w2"), sc))
+    return res
+
+
+def catalog_scalars(data, randoms=None, box=0.0, device=0):
+    keep = _Keep()
+    d = make_catalog(data, keep)
+    r = make_catalog(randoms, keep)
+    out = np.zeros(8)
+    ctx = context(device)
+    B.check(B.npc_catalog_scalars(ctx, C.byref(d), C.byref(r) if r else None, float(box),
+                                  out.ctypes.data_as(C.c_void_p), 0), ctx)
+    return dict(zip(("alpha", "I22", "I33", "N0", "S3", "sum_wg", "sum_wr", "sum_w2"), out))
+
+
+def last_stats(device=0):
+    st = B.npc_stats()
+    B.check(B.npc_last_stats(context(device), C.byref(st)))
+    return {k: getattr(st, k) for k, _ in B.npc_stats._fields_}

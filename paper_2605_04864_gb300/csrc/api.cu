@@ -1,0 +1,410 @@
+// C ABI of libnpc.so: context management, argument validation, device tables and the
+// orchestration of the estimator pipelines.  All compute runs in the kernels of catalog.cu,
+// power.cu and bispec.cu; the host only validates, allocates workspace and enqueues.
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+
+#include "npc_internal.cuh"
+
+#define NPC_VERSION "0.1.0"
+
+npc_status set_err(npc_ctx* ctx, npc_status s, const char* fmt, ...) {
+  if (ctx) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    ctx->last_error = buf;
+  }
+  return s;
+}
+
+npc_status ws_get(npc_ctx* ctx, const char* name, size_t bytes, void** out) {
+  Workspace& w = ctx->ws[name];
+  if (bytes == 0) bytes = 16;
+  if (w.bytes < bytes) {
+    if (w.p) {
+      cudaError_t e = cudaStreamSynchronize(ctx->stream);
+      if (e != cudaSuccess) return set_err(ctx, NPC_ERR_CUDA, "sync before realloc: %s", cudaGetErrorString(e));
+      cudaFree(w.p);
+      w.p = nullptr;
+      w.bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&w.p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      w.p = nullptr;
+      return set_err(ctx, NPC_ERR_OOM, "workspace '%s': cannot allocate %zu bytes (%s)", name, bytes,
+                     cudaGetErrorString(e));
+    }
+    w.bytes = bytes;
+  }
+  *out = w.p;
+  return NPC_OK;
+}
+
+npc_status ws_table(npc_ctx* ctx, const std::string& name, const std::vector<char>& key, const void* data,
+                    size_t bytes, void** out) {
+  auto it = ctx->host_cache_keys.find(name);
+  void* p;
+  NPC_TRY(ws_get(ctx, name.c_str(), bytes, &p));
+  if (it == ctx->host_cache_keys.end() || it->second != key) {
+    NPC_CUDA(ctx, cudaMemcpyAsync(p, data, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    NPC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->host_cache_keys[name] = key;
+  }
+  *out = p;
+  return NPC_OK;
+}
+
+template <typename V> static void key_push(std::vector<char>& k, const V& v) {
+  const char* p = reinterpret_cast<const char*>(&v);
+  k.insert(k.end(), p, p + sizeof(V));
+}
+
+YNorm ylm_norm_table() {
+  YNorm t{};
+  for (int l = 0; l <= NPC_LMAX; ++l)
+    for (int m = 0; m <= l; ++m) {
+      double r = 1.0;  // (l-m)!/(l+m)!
+      for (int j = l - m + 1; j <= l + m; ++j) r /= (double)j;
+      t.v[l * (l + 1) / 2 + m] = std::sqrt((2.0 * l + 1.0) / (4.0 * M_PI) * r);
+    }
+  return t;
+}
+
+npc_status get_twiddles(npc_ctx* ctx, int n, int prec, const void** out) {
+  std::vector<char> key;
+  key_push(key, n);
+  const std::string name = std::string(prec == NPC_PREC_FP64 ? "tw64." : "tw32.") + std::to_string(n);
+  void* p;
+  if (prec == NPC_PREC_FP64) {
+    std::vector<double2> h(n);
+    for (int j = 0; j < n; ++j) h[j] = make_double2(std::cos(2.0 * M_PI * j / n), -std::sin(2.0 * M_PI * j / n));
+    NPC_TRY(ws_table(ctx, name, key, h.data(), sizeof(double2) * n, &p));
+  } else {
+    std::vector<float2> h(n);
+    for (int j = 0; j < n; ++j)
+      h[j] = make_float2((float)std::cos(2.0 * M_PI * j / n), (float)-std::sin(2.0 * M_PI * j / n));
+    NPC_TRY(ws_table(ctx, name, key, h.data(), sizeof(float2) * n, &p));
+  }
+  *out = p;
+  return NPC_OK;
+}
+
+// bin of every integer |k|^2 = i^2+j^2+l^2 (host, float64, no contraction: -ffp-contract=off)
+npc_status get_bin_table(npc_ctx* ctx, int n, double box, const npc_kbins& kb, const int16_t** out) {
+  std::vector<char> key;
+  key_push(key, n);
+  key_push(key, box);
+  key_push(key, kb.kmin);
+  key_push(key, kb.dk);
+  key_push(key, kb.nbins);
+  const int64_t nmax = 3LL * (n / 2) * (n / 2);
+  std::vector<int16_t> h(nmax + 1);
+  const double kf = 2.0 * M_PI / box;
+  for (int64_t n2 = 0; n2 <= nmax; ++n2) {
+    const double kmag = kf * std::sqrt((double)n2);
+    const double b = std::floor((kmag - kb.kmin) / kb.dk);
+    h[n2] = (n2 > 0 && b >= 0.0 && b < (double)kb.nbins) ? (int16_t)b : (int16_t)-1;
+  }
+  void* p;
+  NPC_TRY(ws_table(ctx, "bintab", key, h.data(), sizeof(int16_t) * h.size(), &p));
+  *out = (const int16_t*)p;
+  return NPC_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Validation
+// ---------------------------------------------------------------------------------------------
+static bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+static npc_status check_spec(npc_ctx* ctx, const npc_mesh_spec* m) {
+  if (!m) return set_err(ctx, NPC_ERR_INVALID_ARG, "mesh spec is NULL");
+  if (!is_pow2(m->n) || m->n < 16 || m->n > 1024)
+    return set_err(ctx, NPC_ERR_INVALID_ARG, "mesh n=%d must be a power of two in [16, 1024]", m->n);
+  if (!(m->box > 0.0) || !std::isfinite(m->box)) return set_err(ctx, NPC_ERR_INVALID_ARG, "box must be > 0");
+  for (int a = 0; a < 3; ++a)
+    if (!std::isfinite(m->origin[a]) || !std::isfinite(m->observer[a]) || !std::isfinite(m->los_dir[a]))
+      return set_err(ctx, NPC_ERR_INVALID_ARG, "non-finite origin/observer/los_dir");
+  if (m->assign != 2 && m->assign != 3) return set_err(ctx, NPC_ERR_INVALID_ARG, "assign must be 2 (CIC) or 3 (TSC)");
+  if (m->interlace != 0 && m->interlace != 1) return set_err(ctx, NPC_ERR_INVALID_ARG, "interlace must be 0 or 1");
+  if (m->periodic != 0 && m->periodic != 1) return set_err(ctx, NPC_ERR_INVALID_ARG, "periodic must be 0 or 1");
+  if (m->los != 0 && m->los != 1) return set_err(ctx, NPC_ERR_INVALID_ARG, "los must be 0 or 1");
+  if (m->los == 1) {
+    const double l2 = m->los_dir[0] * m->los_dir[0] + m->los_dir[1] * m->los_dir[1] + m->los_dir[2] * m->los_dir[2];
+    if (!(l2 > 0)) return set_err(ctx, NPC_ERR_INVALID_ARG, "los_dir must be non-zero");
+  }
+  return NPC_OK;
+}
+
+static npc_status check_catalog(npc_ctx* ctx, const npc_catalog* c, const char* what, bool need_nbar) {
+  if (!c) return set_err(ctx, NPC_ERR_INVALID_ARG, "%s catalogue is NULL", what);
+  if (c->n < 0) return set_err(ctx, NPC_ERR_INVALID_ARG, "%s: n < 0", what);
+  if (c->dtype != 0 && c->dtype != 1) return set_err(ctx, NPC_ERR_INVALID_ARG, "%s: dtype must be 0 or 1", what);
+  if (c->on_device != 0 && c->on_device != 1) return set_err(ctx, NPC_ERR_INVALID_ARG, "%s: on_device must be 0/1", what);
+  if (c->n > 0 && !c->pos) return set_err(ctx, NPC_ERR_INVALID_ARG, "%s: pos is NULL", what);
+  if (c->n > 0 && need_nbar && !c->nbar) return set_err(ctx, NPC_ERR_INVALID_ARG, "%s: nbar is required", what);
+  if (c->n >= (int64_t)1 << 31) return set_err(ctx, NPC_ERR_UNSUPPORTED, "%s: more than 2^31-1 objects", what);
+  return NPC_OK;
+}
+
+static npc_status check_bins(npc_ctx* ctx, const npc_kbins* b) {
+  if (!b) return set_err(ctx, NPC_ERR_INVALID_ARG, "k-bins are NULL");
+  if (!(b->dk > 0.0) || !std::isfinite(b->dk) || !(b->kmin >= 0.0) || !std::isfinite(b->kmin))
+    return set_err(ctx, NPC_ERR_INVALID_ARG, "k-bins need dk > 0 and kmin >= 0");
+  if (b->nbins < 1 || b->nbins > 4096) return set_err(ctx, NPC_ERR_INVALID_ARG, "nbins must be in [1, 4096]");
+  return NPC_OK;
+}
+
+// Stage a catalogue on the device (host inputs are copied into context workspace).
+static npc_status stage_catalog(npc_ctx* ctx, const npc_catalog* c, const char* tag, DevCatalog* out) {
+  out->n = c->n;
+  out->dtype = c->dtype;
+  const size_t es = c->dtype == 1 ? 8 : 4;
+  if (c->on_device || c->n == 0) {
+    out->pos = c->pos;
+    out->w = c->w;
+    out->nbar = c->nbar;
+    return NPC_OK;
+  }
+  void *p, *w = nullptr, *nb = nullptr;
+  NPC_TRY(ws_get(ctx, (std::string(tag) + ".pos").c_str(), es * 3 * c->n, &p));
+  NPC_CUDA(ctx, cudaMemcpyAsync(p, c->pos, es * 3 * c->n, cudaMemcpyHostToDevice, ctx->stream));
+  if (c->w) {
+    NPC_TRY(ws_get(ctx, (std::string(tag) + ".w").c_str(), es * c->n, &w));
+    NPC_CUDA(ctx, cudaMemcpyAsync(w, c->w, es * c->n, cudaMemcpyHostToDevice, ctx->stream));
+  }
+  if (c->nbar) {
+    NPC_TRY(ws_get(ctx, (std::string(tag) + ".nbar").c_str(), es * c->n, &nb));
+    NPC_CUDA(ctx, cudaMemcpyAsync(nb, c->nbar, es * c->n, cudaMemcpyHostToDevice, ctx->stream));
+  }
+  out->pos = p;
+  out->w = w;
+  out->nbar = nb;
+  return NPC_OK;
+}
+
+static Geom make_geom(const npc_mesh_spec& m) {
+  Geom g{};
+  g.n = m.n;
+  g.h = m.box / m.n;
+  for (int a = 0; a < 3; ++a) g.o[a] = m.origin[a] - m.observer[a];
+  const double l = std::sqrt(m.los_dir[0] * m.los_dir[0] + m.los_dir[1] * m.los_dir[1] + m.los_dir[2] * m.los_dir[2]);
+  for (int a = 0; a < 3; ++a) g.los[a] = l > 0 ? m.los_dir[a] / l : 0.0;
+  g.global_los = m.los;
+  return g;
+}
+
+static void begin_call(npc_ctx* ctx) {
+  ctx->launches = 0;
+  ctx->last_error.clear();
+}
+
+static npc_status end_call(npc_ctx* ctx) {
+  ctx->stats.n_kernel_launches = ctx->launches;
+  int64_t tot = 0;
+  for (auto& kv : ctx->ws) tot += (int64_t)kv.second.bytes;
+  ctx->stats.workspace_bytes = tot;
+  return NPC_OK;
+}
+
+static npc_status finish_output(npc_ctx* ctx, const double* dev, double* out, int64_t len, int out_on_device) {
+  if (out_on_device) {
+    if (dev != out) NPC_CUDA(ctx, cudaMemcpyAsync(out, dev, sizeof(double) * len, cudaMemcpyDeviceToDevice, ctx->stream));
+    return NPC_OK;
+  }
+  NPC_CUDA(ctx, cudaMemcpyAsync(out, dev, sizeof(double) * len, cudaMemcpyDeviceToHost, ctx->stream));
+  NPC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return NPC_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Public ABI
+// ---------------------------------------------------------------------------------------------
+extern "C" {
+
+const char* npc_version(void) { return NPC_VERSION; }
+
+const char* npc_status_string(npc_status s) {
+  switch (s) {
+    case NPC_OK: return "ok";
+    case NPC_ERR_INVALID_ARG: return "invalid argument";
+    case NPC_ERR_OOM: return "out of device memory";
+    case NPC_ERR_CUDA: return "CUDA error";
+    case NPC_ERR_UNSUPPORTED: return "unsupported";
+    case NPC_ERR_TIMEOUT: return "device wait timed out";
+    case NPC_ERR_NUMERIC: return "degenerate or non-finite normalisation";
+  }
+  return "unknown status";
+}
+
+npc_status npc_create(npc_ctx** out, int device, void* cuda_stream) {
+  if (!out) return NPC_ERR_INVALID_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return NPC_ERR_INVALID_ARG;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return NPC_ERR_CUDA;
+  npc_ctx* c = new npc_ctx();
+  c->device = device;
+  if (cuda_stream) {
+    c->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return NPC_ERR_CUDA;
+    }
+    c->own_stream = true;
+  }
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  *out = c;
+  return NPC_OK;
+}
+
+npc_status npc_destroy(npc_ctx* ctx) {
+  if (!ctx) return NPC_OK;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  for (auto& kv : ctx->ws)
+    if (kv.second.p) cudaFree(kv.second.p);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return NPC_OK;
+}
+
+npc_status npc_last_error(npc_ctx* ctx, char* buf, size_t n) {
+  if (!ctx || !buf || n == 0) return NPC_ERR_INVALID_ARG;
+  std::strncpy(buf, ctx->last_error.c_str(), n - 1);
+  buf[n - 1] = '\0';
+  return NPC_OK;
+}
+
+npc_status npc_last_stats(npc_ctx* ctx, npc_stats* out) {
+  if (!ctx || !out) return NPC_ERR_INVALID_ARG;
+  *out = ctx->stats;
+  return NPC_OK;
+}
+
+npc_status npc_catalog_scalars(npc_ctx* ctx, const npc_catalog* data, const npc_catalog* randoms, double box,
+                               double* out, int32_t out_on_device) {
+  if (!ctx) return NPC_ERR_INVALID_ARG;
+  begin_call(ctx);
+  if (!out) return set_err(ctx, NPC_ERR_INVALID_ARG, "out is NULL");
+  NPC_TRY(check_catalog(ctx, data, "data", false));
+  if (randoms) NPC_TRY(check_catalog(ctx, randoms, "randoms", true));
+  if (!randoms && !(box > 0.0)) return set_err(ctx, NPC_ERR_INVALID_ARG, "periodic scalars need box > 0");
+  NPC_CUDA(ctx, cudaSetDevice(ctx->device));
+  DevCatalog d, r;
+  NPC_TRY(stage_catalog(ctx, data, "data", &d));
+  if (randoms) NPC_TRY(stage_catalog(ctx, randoms, "rand", &r));
+  double* sc;
+  NPC_TRY(ws_get(ctx, "scalars", sizeof(double) * SC_COUNT, (void**)&sc));
+  NPC_TRY(launch_catalog_scalars(ctx, d, randoms ? &r : nullptr, box, sc));
+  NPC_TRY(finish_output(ctx, sc, out, 8, out_on_device));
+  return end_call(ctx);
+}
+
+int64_t npc_power_out_len(const npc_kbins* bins, uint32_t ell_mask, uint32_t modified_mask) {
+  if (!bins || bins->nbins < 1) return 0;
+  if ((ell_mask & ~0x15u) || (modified_mask & ~0x150u) || (ell_mask == 0 && modified_mask == 0)) return 0;
+  int rows = 2;
+  for (int l = 0; l <= 4; l += 2) rows += (ell_mask >> l) & 1;
+  for (int l = 4; l <= 8; l += 2) rows += (modified_mask >> l) & 1;
+  return (int64_t)rows * bins->nbins + 8;
+}
+
+npc_status npc_power_multipoles(npc_ctx* ctx, const npc_mesh_spec* mesh, const npc_catalog* data,
+                                const npc_catalog* randoms, const npc_kbins* bins, uint32_t ell_mask,
+                                uint32_t modified_mask, npc_precision prec, double* out, int32_t out_on_device) {
+  if (!ctx) return NPC_ERR_INVALID_ARG;
+  begin_call(ctx);
+  NPC_TRY(check_spec(ctx, mesh));
+  NPC_TRY(check_bins(ctx, bins));
+  if (!out) return set_err(ctx, NPC_ERR_INVALID_ARG, "out is NULL");
+  const int64_t out_len = npc_power_out_len(bins, ell_mask, modified_mask);
+  if (out_len == 0)
+    return set_err(ctx, NPC_ERR_INVALID_ARG, "ell_mask must use bits 0,2,4 and modified_mask bits 4,6,8");
+  if (prec != NPC_PREC_FP64 && prec != NPC_PREC_MIXED) return set_err(ctx, NPC_ERR_INVALID_ARG, "bad precision");
+  if (prec == NPC_PREC_FP64 && mesh->n > 256) return set_err(ctx, NPC_ERR_UNSUPPORTED, "FP64 precision supports n <= 256");
+  NPC_TRY(check_catalog(ctx, data, "data", false));
+  if (mesh->periodic) {
+    if (randoms) return set_err(ctx, NPC_ERR_INVALID_ARG, "periodic box takes no randoms");
+  } else {
+    if (!randoms) return set_err(ctx, NPC_ERR_INVALID_ARG, "survey geometry needs randoms");
+    NPC_TRY(check_catalog(ctx, randoms, "randoms", true));
+    if (randoms->n == 0) return set_err(ctx, NPC_ERR_NUMERIC, "empty random catalogue");
+  }
+  if (data->n == 0) return set_err(ctx, NPC_ERR_NUMERIC, "empty data catalogue (I22 = 0)");
+  NPC_CUDA(ctx, cudaSetDevice(ctx->device));
+
+  const int n = mesh->n;
+  const int nphase = mesh->interlace ? 2 : 1;
+  PowerPlan plan{};
+  plan.n = n;
+  plan.nphase = nphase;
+  plan.ells_mask = (int)ell_mask;
+  plan.mod_mask = (int)modified_mask;
+  plan.nbins = bins->nbins;
+  plan.global_los = mesh->los;
+  plan.assign = mesh->assign;
+  const Geom g = make_geom(*mesh);
+  for (int a = 0; a < 3; ++a) plan.los[a] = g.los[a];
+  int need = (int)ell_mask | 1;
+  if (modified_mask) need |= 1 | 4 | 16;
+  FieldList& fl = plan.fl;
+  fl.nf = 0;
+  int ntr = 0, nr2c = 0;
+  auto push = [&](int ph, int l, int m, int part) {
+    Comp c;
+    c.phase = (int8_t)ph; c.ell = (int8_t)l; c.m = (int8_t)m; c.part = (int8_t)part;
+    fl.f[fl.nf++] = c;
+  };
+  if (mesh->los == 1) {
+    for (int ph = 0; ph < nphase; ++ph) push(ph, 0, 0, PART_ONE);
+    ntr = 1;
+    nr2c = 1;
+  } else {
+    for (int l = 0; l <= 4; l += 2) {
+      if (!(need & (1 << l))) continue;
+      for (int m = 0; m <= l; ++m) {
+        for (int ph = 0; ph < nphase; ++ph) {
+          push(ph, l, m, PART_RE);
+          if (m > 0) push(ph, l, m, PART_IM);
+        }
+      }
+      ntr += l + 1;
+      nr2c += 2 * l + 1;
+    }
+  }
+  ctx->stats.n_transforms = ntr;
+  ctx->stats.n_r2c_equivalent = nr2c;
+  ctx->stats.n_phases = nphase;
+
+  DevCatalog d, r;
+  NPC_TRY(stage_catalog(ctx, data, "data", &d));
+  if (randoms) NPC_TRY(stage_catalog(ctx, randoms, "rand", &r));
+  double* sc;
+  NPC_TRY(ws_get(ctx, "scalars", sizeof(double) * SC_COUNT, (void**)&sc));
+  NPC_TRY(launch_catalog_scalars(ctx, d, randoms ? &r : nullptr, mesh->box, sc));
+
+  const size_t rs = prec == NPC_PREC_FP64 ? 8 : 4;
+  const size_t ncell = (size_t)n * n * n;
+  void *ma, *mb = nullptr, *half;
+  NPC_TRY(ws_get(ctx, "mesh.a", rs * ncell, &ma));
+  if (nphase == 2) NPC_TRY(ws_get(ctx, "mesh.b", rs * ncell, &mb));
+  NPC_TRY(launch_paint(ctx, d, randoms ? &r : nullptr, *mesh, 1, prec, sc, ma, mb));
+  NPC_TRY(ws_get(ctx, "half", 2 * rs * (size_t)fl.nf * (n / 2) * n * n, &half));
+  NPC_TRY(run_forward_transforms(ctx, prec, plan, g, ma, mb, half));
+  double* dev_out = out;
+  if (!out_on_device) NPC_TRY(ws_get(ctx, "power.out", sizeof(double) * out_len, (void**)&dev_out));
+  NPC_TRY(run_power_contract(ctx, prec, plan, *mesh, *bins, half, sc, dev_out));
+  NPC_TRY(finish_output(ctx, dev_out, out, out_len, out_on_device));
+  return end_call(ctx);
+}
+
+}  // extern "C"

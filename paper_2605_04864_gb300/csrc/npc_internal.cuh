@@ -1,0 +1,222 @@
+// Internal declarations shared by the translation units of libnpc.so.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/npc.h"
+
+// ---------------------------------------------------------------------------------------------
+// Complex helpers (float2 / double2)
+// ---------------------------------------------------------------------------------------------
+template <typename T> struct CplxOf;
+template <> struct CplxOf<float> { using type = float2; };
+template <> struct CplxOf<double> { using type = double2; };
+template <typename T> using cplx = typename CplxOf<T>::type;
+
+__host__ __device__ __forceinline__ float2 cmk(float a, float b) { return make_float2(a, b); }
+__host__ __device__ __forceinline__ double2 cmk(double a, double b) { return make_double2(a, b); }
+template <typename C> __host__ __device__ __forceinline__ C cadd(C a, C b) { return cmk(a.x + b.x, a.y + b.y); }
+template <typename C> __host__ __device__ __forceinline__ C csub(C a, C b) { return cmk(a.x - b.x, a.y - b.y); }
+template <typename C> __host__ __device__ __forceinline__ C cmul(C a, C b) {
+  return cmk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename C> __host__ __device__ __forceinline__ C cconj(C a) { return cmk(a.x, -a.y); }
+template <typename C, typename T> __host__ __device__ __forceinline__ C cscale(C a, T s) {
+  return cmk(a.x * s, a.y * s);
+}
+// multiply by (sign * i): sign = -1 gives -i, +1 gives +i
+template <int SIGN, typename C> __host__ __device__ __forceinline__ C cmul_i(C a) {
+  return SIGN < 0 ? cmk(a.y, -a.x) : cmk(-a.y, a.x);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Spherical harmonics Y_l^m (m >= 0, Condon-Shortley phase) at a unit vector, l <= 8.
+//   Y_l^m = N_lm Q_lm(z) (x + i y)^m,  N_lm = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!),
+//   Q_lm = (-1)^m d^m L_l/dz^m, from Q_mm = (-1)^m (2m-1)!!, Q_{m+1,m} = (2m+1) z Q_mm and the
+//   three-term recurrence (l-m) Q_lm = (2l-1) z Q_{l-1,m} - (l+m-1) Q_{l-2,m}.
+// ---------------------------------------------------------------------------------------------
+constexpr int NPC_LMAX = 8;
+constexpr int NPC_NLM = (NPC_LMAX + 1) * (NPC_LMAX + 2) / 2;
+
+struct YNorm {
+  double v[NPC_NLM];  // index l(l+1)/2 + m
+};
+YNorm ylm_norm_table();
+
+template <typename T>
+__device__ __forceinline__ void ylm_eval(int l, int m, T x, T y, T z, const YNorm& nrm, T& re, T& im) {
+  T pr = T(1), pim = T(0);
+  for (int j = 0; j < m; ++j) {
+    const T nr = pr * x - pim * y;
+    pim = pr * y + pim * x;
+    pr = nr;
+  }
+  T qmm = T(1);
+  for (int j = 1; j <= m; ++j) qmm *= -T(2 * j - 1);
+  T q = qmm;
+  if (l > m) {
+    T q0 = qmm;
+    T q1 = z * T(2 * m + 1) * qmm;
+    for (int ll = m + 2; ll <= l; ++ll) {
+      const T q2 = (T(2 * ll - 1) * z * q1 - T(ll + m - 1) * q0) / T(ll - m);
+      q0 = q1;
+      q1 = q2;
+    }
+    q = q1;
+  }
+  const T c = T(nrm.v[l * (l + 1) / 2 + m]) * q;
+  re = c * pr;
+  im = c * pim;
+}
+
+// Legendre polynomial L_l(mu), l <= 8 (Bonnet recurrence).
+template <typename T> __device__ __forceinline__ T legendre_p(int l, T mu) {
+  if (l == 0) return T(1);
+  T p0 = T(1), p1 = mu;
+  for (int ll = 2; ll <= l; ++ll) {
+    const T p2 = (T(2 * ll - 1) * mu * p1 - T(ll - 1) * p0) / T(ll);
+    p0 = p1;
+    p1 = p2;
+  }
+  return p1;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Field descriptors for the forward transforms
+// ---------------------------------------------------------------------------------------------
+enum : int8_t { PART_RE = 0, PART_IM = 1, PART_ONE = 2, PART_ZERO = 3 };
+
+struct Comp {          // one real field: mesh phase x weight function
+  int8_t phase;        // 0 or 1
+  int8_t ell, m;       // Y_l^m (m >= 0)
+  int8_t part;         // PART_RE / PART_IM of Y_l^m, PART_ONE (global LOS), PART_ZERO
+};
+
+constexpr int NPC_MAX_FIELDS = 40;  // real fields per call (2 phases x 15 for l <= 4, + spare)
+
+struct FieldList {
+  int nf;                     // number of real fields
+  Comp f[NPC_MAX_FIELDS];     // real field f; forward pairs are (2p, 2p+1)
+};
+
+// Geometry needed to evaluate xhat at a grid point.
+struct Geom {
+  int n;
+  double h;          // box / n
+  double o[3];       // origin - observer
+  double los[3];     // unit global LOS
+  int global_los;
+};
+
+// ---------------------------------------------------------------------------------------------
+// Context
+// ---------------------------------------------------------------------------------------------
+struct Workspace {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct npc_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int num_sms = 0;
+  std::map<std::string, Workspace> ws;
+  std::map<std::string, std::vector<char>> host_cache_keys;
+  std::string last_error;
+  npc_stats stats{};
+  int launches = 0;
+};
+
+// error helpers
+npc_status set_err(npc_ctx* ctx, npc_status s, const char* fmt, ...);
+#define NPC_CUDA(ctx, call)                                                                  \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      return set_err((ctx), NPC_ERR_CUDA, "%s failed: %s (%s:%d)", #call,                    \
+                     cudaGetErrorString(e_), __FILE__, __LINE__);                            \
+  } while (0)
+#define NPC_LAUNCH(ctx)                                                                      \
+  do {                                                                                       \
+    (ctx)->launches++;                                                                       \
+    cudaError_t e_ = cudaGetLastError();                                                     \
+    if (e_ != cudaSuccess)                                                                   \
+      return set_err((ctx), NPC_ERR_CUDA, "kernel launch failed: %s (%s:%d)",                \
+                     cudaGetErrorString(e_), __FILE__, __LINE__);                            \
+  } while (0)
+#define NPC_TRY(expr)                                                                        \
+  do {                                                                                       \
+    npc_status s_ = (expr);                                                                  \
+    if (s_ != NPC_OK) return s_;                                                             \
+  } while (0)
+
+// grow-only named device buffer
+npc_status ws_get(npc_ctx* ctx, const char* name, size_t bytes, void** out);
+// cached device table keyed by (name, key bytes); uploads `data` on first use
+npc_status ws_table(npc_ctx* ctx, const std::string& name, const std::vector<char>& key,
+                    const void* data, size_t bytes, void** out);
+
+// ---------------------------------------------------------------------------------------------
+// Scalars layout in device memory (double[16])
+// ---------------------------------------------------------------------------------------------
+enum {
+  SC_ALPHA = 0, SC_I22, SC_I33, SC_N0, SC_S3, SC_SUMWG, SC_SUMWR, SC_SUMW2,
+  SC_MAXW_F = 8,   // max |weight coefficient| for the FKP field (data w, randoms alpha w)
+  SC_MAXW_N = 9,   // same for the w^2 N-field
+  SC_COUNT = 16
+};
+
+// ---------------------------------------------------------------------------------------------
+// Host launchers (catalog.cu)
+// ---------------------------------------------------------------------------------------------
+struct DevCatalog {   // catalogue resident on the device
+  const void* pos = nullptr;
+  const void* w = nullptr;
+  const void* nbar = nullptr;
+  int64_t n = 0;
+  int dtype = 0;      // 0 float, 1 double
+};
+
+npc_status launch_catalog_scalars(npc_ctx* ctx, const DevCatalog& d, const DevCatalog* r, double box,
+                                  double* dev_scalars);
+
+// Paint the FKP field (weight_power 1) or the N-field (2) on 1 or 2 interlacing phases.
+// meshes: nphase pointers to n^3 arrays of T (layout [z][y][x]).
+npc_status launch_paint(npc_ctx* ctx, const DevCatalog& d, const DevCatalog* r, const npc_mesh_spec& m,
+                        int weight_power, int prec, const double* dev_scalars, void* mesh_a,
+                        void* mesh_b);
+
+// ---------------------------------------------------------------------------------------------
+// Power spectrum passes (power.cu)
+// ---------------------------------------------------------------------------------------------
+struct PowerPlan {
+  int n;
+  int nphase;
+  FieldList fl;
+  int ells_mask;        // requested P_l
+  int mod_mask;         // requested P_lb
+  int need_ll;          // 1: two-index sums needed
+  int nbins;
+  int nsum;             // sums per bin
+  int global_los;
+  double los[3];
+  int assign;
+};
+
+npc_status run_forward_transforms(npc_ctx* ctx, int prec, const PowerPlan& plan, const Geom& g,
+                                  const void* mesh_a, const void* mesh_b, void* half);
+npc_status run_power_contract(npc_ctx* ctx, int prec, const PowerPlan& plan, const npc_mesh_spec& m,
+                              const npc_kbins& kb, const void* half, const double* dev_scalars,
+                              double* dev_out);
+
+// bin table: int16 per integer |k|^2 in [0, 3 (n/2)^2]
+npc_status get_bin_table(npc_ctx* ctx, int n, double box, const npc_kbins& kb, const int16_t** out);
+// twiddle table exp(-2 pi i j / n), j < n, as cplx<T>
+npc_status get_twiddles(npc_ctx* ctx, int n, int prec, const void** out);

@@ -1,0 +1,195 @@
+"""GPU parity: npc_power_multipoles (through the C ABI) against the FP64 oracle."""
+import ctypes as C
+from types import SimpleNamespace
+
+import numpy as np
+import pytest
+
+from helpers import ensure_built, p_error
+from oracle import power as P
+from synthetic import make_periodic_catalog, make_survey_catalogs, workload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    ensure_built()
+    from paper_2605_04864_gb300 import api as A
+
+    return A
+
+
+def _oracle(g, r, origin, n, box, assign, interlace, kb, ells, modified=(), los_dir=None):
+    spec = dict(n=n, box=box, origin=tuple(origin), assign=assign, interlace=interlace,
+                los="global" if los_dir is not None else "endpoint", los_dir=los_dir,
+                observer=(0.0, 0.0, 0.0))
+    return P.power_multipoles(spec, g, r, kb, ells, modified, method="plain")
+
+
+def _compare(res, orc, ells, modified, tol):
+    scale = np.abs(orc["P"][0]) + orc["scalars"]["N0"] if 0 in orc["P"] else orc["scalars"]["N0"]
+    np.testing.assert_array_equal(res["nmodes"], orc["nmodes"])
+    np.testing.assert_allclose(res["k_eff"], orc["k_eff"], rtol=1e-6, atol=1e-12)
+    worst = 0.0
+    for l in ells:
+        e = p_error(res["P"][l], orc["P"][l], scale)
+        worst = max(worst, float(np.max(e)))
+        assert np.max(e) < tol, (l, np.max(e))
+    for l in modified:
+        e = p_error(res["Pmod"][l], orc["Pmod"][l], scale)
+        worst = max(worst, float(np.max(e)))
+        assert np.max(e) < tol, ("b", l, np.max(e))
+    for k in ("alpha", "I22", "N0"):
+        assert res["scalars"][k] == pytest.approx(orc["scalars"][k], rel=1e-12)
+    return worst
+
+
+def test_fp64_plain_64_cic_survey(api):
+    """Plain FP64 Yamamoto P_0,2,4: 64^3 CIC, no interlacing, survey geometry, unit weights."""
+    w = workload("p024_fp64_64")
+    g, r, origin = make_survey_catalogs(w["n_gal"], w["n_ran"], w["box"], w["distance"], w["n_gen"],
+                                        seed=w["seed"], fkp_p0=None)
+    kb = (w["kmin"], w["dk"], w["nbins"])
+    res = api.power_multipoles(g, r, n=64, box=w["box"], origin=origin, assign=2, interlace=0, kbins=kb,
+                               ells=(0, 2, 4), precision="fp64")
+    orc = _oracle(g, r, origin, 64, w["box"], 2, 0, kb, (0, 2, 4))
+    _compare(res, orc, (0, 2, 4), (), 1e-12)
+    st = api.last_stats()
+    assert st["n_transforms"] == 9 and st["n_r2c_equivalent"] == 15 and st["n_phases"] == 1
+
+
+@pytest.mark.parametrize("n", [32, 64, 128])
+def test_mixed_tsc_interlaced_modified(api, n):
+    """P_0,2,4 + P_4b,6b,8b, TSC + interlacing, FKP weights, float32 transforms: <= 1e-5."""
+    box = 800.0
+    g, r, origin = make_survey_catalogs(40000, 400000, box, 1300.0, 32, seed=31 + n, fkp_p0=1e4)
+    kn = np.pi * n / box
+    kb = (0.0, 0.01, int(kn / 0.01))
+    res = api.power_multipoles(g, r, n=n, box=box, origin=origin, assign=3, interlace=1, kbins=kb,
+                               ells=(0, 2, 4), modified=(4, 6, 8), precision="mixed")
+    orc = _oracle(g, r, origin, n, box, 3, 1, kb, (0, 2, 4), (4, 6, 8))
+    _compare(res, orc, (0, 2, 4), (4, 6, 8), 1e-5)
+
+
+def test_fp64_ragged_bins_and_subsets(api):
+    """Ragged bins (kmin offset, odd dk, partial coverage), a subset of multipoles, float64 input."""
+    box = 700.0
+    g, r, origin = make_survey_catalogs(9000, 60000, box, 1200.0, 16, seed=77, fkp_p0=5e3,
+                                        dtype=np.float64)
+    kb = (0.013, 0.017, 7)
+    for ells, mods in [((2,), ()), ((0, 4), (4,)), ((4,), (8,))]:
+        res = api.power_multipoles(g, r, n=32, box=box, origin=origin, assign=3, interlace=1, kbins=kb,
+                                   ells=ells, modified=mods, precision="fp64")
+        orc = _oracle(g, r, origin, 32, box, 3, 1, kb, tuple(sorted(set(ells) | {0})), mods)
+        _compare(res, orc, ells, mods, 1e-12)
+
+
+def test_global_los_survey_and_periodic(api):
+    box = 500.0
+    g, r, origin = make_survey_catalogs(6000, 50000, box, 900.0, 16, seed=5, fkp_p0=1e4)
+    kb = (0.0, 0.02, 9)
+    res = api.power_multipoles(g, r, n=32, box=box, origin=origin, assign=2, interlace=1, kbins=kb,
+                               ells=(0, 2, 4), modified=(4,), precision="fp64", los_dir=(1.0, 1.0, 1.0))
+    orc = _oracle(g, r, origin, 32, box, 2, 1, kb, (0, 2, 4), (4,), los_dir=(1.0, 1.0, 1.0))
+    _compare(res, orc, (0, 2, 4), (4,), 1e-12)
+    assert api.last_stats()["n_transforms"] == 1
+    cat = make_periodic_catalog(20000, 300.0, 16, seed=8)
+    res = api.power_multipoles(cat, None, n=64, box=300.0, origin=(0, 0, 0), assign=3, interlace=1,
+                               kbins=(0.02, 0.02, 25), ells=(0, 2), precision="mixed", los_dir=(0, 0, 1))
+    spec = dict(n=64, box=300.0, origin=(0, 0, 0), assign=3, interlace=1, los="global", los_dir=(0, 0, 1))
+    orc = P.power_multipoles(spec, cat, None, (0.02, 0.02, 25), (0, 2))
+    _compare(res, orc, (0, 2), (), 1e-5)
+
+
+def test_tiny_mesh_16(api):
+    g, r, origin = make_survey_catalogs(2000, 20000, 400.0, 700.0, 8, seed=3, fkp_p0=1e4)
+    kb = (0.0, 0.015, 8)
+    res = api.power_multipoles(g, r, n=16, box=400.0, origin=origin, assign=3, interlace=1, kbins=kb,
+                               ells=(0, 2, 4), modified=(4, 6, 8), precision="fp64")
+    orc = _oracle(g, r, origin, 16, 400.0, 3, 1, kb, (0, 2, 4), (4, 6, 8))
+    _compare(res, orc, (0, 2, 4), (4, 6, 8), 1e-12)
+
+
+def test_particles_on_box_edges_and_outside(api):
+    """Positions at the box faces and slightly outside wrap periodically on both sides."""
+    rng = np.random.default_rng(9)
+    box = 200.0
+    pos = rng.random((3000, 3)) * box
+    pos[:200, 0] = 0.0
+    pos[200:400, 1] = np.nextafter(box, 0)
+    pos[400:500, 2] = box + 3.0
+    pos[500:600, 0] = -2.5
+    g = SimpleNamespace(pos=pos, w=np.ones(3000), nbar=np.full(3000, 3000 / box**3))
+    rr = rng.random((20000, 3)) * box
+    r = SimpleNamespace(pos=rr, w=np.ones(20000), nbar=np.full(20000, 3000 / box**3))
+    kb = (0.0, 0.03, 8)
+    res = api.power_multipoles(g, r, n=32, box=box, origin=(0, 0, 0), assign=3, interlace=1, kbins=kb,
+                               ells=(0, 2), precision="fp64", observer=(-500.0, -400.0, -300.0))
+    spec = dict(n=32, box=box, origin=(0, 0, 0), assign=3, interlace=1, los="endpoint",
+                observer=(-500.0, -400.0, -300.0))
+    orc = P.power_multipoles(spec, g, r, kb, (0, 2))
+    _compare(res, orc, (0, 2), (), 1e-12)
+
+
+def test_determinism_and_device_inputs(api):
+    torch = pytest.importorskip("torch")
+    g, r, origin = make_survey_catalogs(30000, 300000, 800.0, 1300.0, 32, seed=12, fkp_p0=1e4)
+    kb = (0.0, 0.01, 20)
+    a = api.power_multipoles(g, r, n=64, box=800.0, origin=origin, kbins=kb, ells=(0, 2, 4), modified=(4,))
+    b = api.power_multipoles(g, r, n=64, box=800.0, origin=origin, kbins=kb, ells=(0, 2, 4), modified=(4,))
+    for l in (0, 2, 4):
+        np.testing.assert_array_equal(a["P"][l], b["P"][l])
+    dev = lambda c: SimpleNamespace(pos=torch.from_numpy(c.pos).cuda(), w=torch.from_numpy(c.w).cuda(),
+                                    nbar=torch.from_numpy(c.nbar).cuda())
+    length = api.B.npc_power_out_len(C.byref(api.B.npc_kbins(*kb)), 0b10101, 1 << 4)
+    out = torch.zeros(length, dtype=torch.float64, device="cuda")
+    api.power_multipoles(dev(g), dev(r), n=64, box=800.0, origin=origin, kbins=kb, ells=(0, 2, 4),
+                         modified=(4,), out=out)
+    torch.cuda.synchronize()
+    got = api.unpack_power(out.cpu().numpy(), kb[2], (0, 2, 4), (4,))
+    for l in (0, 2, 4):
+        np.testing.assert_array_equal(got["P"][l], a["P"][l])
+
+
+def test_invalid_arguments_rejected(api):
+    from paper_2605_04864_gb300 import binding as B
+
+    g, r, origin = make_survey_catalogs(1000, 5000, 300.0, 600.0, 8, seed=1)
+    kb = (0.0, 0.02, 5)
+    for kw, code in [(dict(n=24), 1), (dict(n=2048), 1), (dict(assign=1), 1), (dict(interlace=2), 1),
+                     (dict(kbins=(0.0, -0.01, 5)), 1), (dict(kbins=(0.0, 0.01, 0)), 1)]:
+        args = dict(n=32, box=300.0, origin=origin, assign=3, interlace=1, kbins=kb, ells=(0,))
+        args.update(kw)
+        with pytest.raises(B.NpcError) as ei:
+            api.power_multipoles(g, r, **args)
+        assert ei.value.status == code, kw
+    with pytest.raises(B.NpcError) as ei:
+        api.power_multipoles(g, r, n=512, box=300.0, origin=origin, kbins=kb, ells=(0,), precision="fp64")
+    assert ei.value.status == 4
+    empty = SimpleNamespace(pos=np.zeros((0, 3), np.float32), w=np.zeros(0, np.float32),
+                            nbar=np.zeros(0, np.float32))
+    with pytest.raises(B.NpcError) as ei:
+        api.power_multipoles(empty, r, n=32, box=300.0, origin=origin, kbins=kb, ells=(0,))
+    assert ei.value.status == 6
+    with pytest.raises(B.NpcError) as ei:
+        api.power_multipoles(g, r, n=32, box=300.0, origin=origin, kbins=kb, ells=(0,), periodic=1)
+    assert ei.value.status == 1
+
+
+@pytest.mark.slow
+def test_full_size_512_monopole(api):
+    """Full 512^3 workload (2e6 galaxies, 2e7 randoms, TSC interlaced): P_0 against the oracle,
+    which can afford the single l = 0 transform at this size; P_l binning counts exactly."""
+    w = workload("p024b_mixed_512")
+    g, r, origin = make_survey_catalogs(w["n_gal"], w["n_ran"], w["box"], w["distance"], w["n_gen"],
+                                        seed=w["seed"], fkp_p0=w["fkp_p0"])
+    kb = (w["kmin"], w["dk"], w["nbins"])
+    res = api.power_multipoles(g, r, n=512, box=w["box"], origin=origin, assign=3, interlace=1, kbins=kb,
+                               ells=(0, 2, 4), modified=(4, 6, 8), precision="mixed")
+    spec = dict(n=512, box=w["box"], origin=tuple(origin), assign=3, interlace=1, los="endpoint",
+                observer=(0.0, 0.0, 0.0))
+    p0, cnt, sc = P.power_monopole_rfft(spec, g, r, kb)
+    np.testing.assert_array_equal(res["nmodes"], cnt)
+    e = p_error(res["P"][0], p0, np.abs(p0) + sc["N0"])
+    assert np.max(e) < 1e-5, np.max(e)

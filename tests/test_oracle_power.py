@@ -228,3 +228,15 @@ def test_catalog_scalars_uniform():
     per = P.catalog_scalars(g, None, box=10.0)
     assert per["I22"] == pytest.approx(1000**2 / 1000.0)
     assert per["N0"] == pytest.approx(1.0)
+
+
+@pytest.mark.parametrize("interlace,assign", [(0, 2), (1, 3)])
+def test_rfft_monopole_equals_full_grid(small_survey, interlace, assign):
+    """The half-grid monopole used for full-size checks equals the full-grid Hand+17 P_0."""
+    g, r, origin = small_survey
+    spec = _survey_spec(24, 1000.0, origin, assign, interlace)
+    kb = (0.0, 0.015, 6)
+    a = P.power_multipoles(spec, g, r, kb, (0,), method="plain")
+    p0, cnt, sc = P.power_monopole_rfft(spec, g, r, kb)
+    np.testing.assert_array_equal(cnt, a["nmodes"])
+    np.testing.assert_allclose(p0, a["P"][0], rtol=1e-12, atol=1e-12 * sc["N0"])
