@@ -1,0 +1,358 @@
+"""Benchmark: Yamamoto P_0,2,4 + modified P_4b,6b,8b at 512^3 (catalogue -> multipoles per step).
+
+Workload: 2e6 lognormal galaxies + 2e7 uniform randoms, box 2000 Mpc/h at 2500 Mpc/h from the
+observer, 512^3 TSC + interlacing, FKP weights, 80 bins of 0.01 h/Mpc, float32 transforms with
+float64 bin and normalisation accumulators.  One step = one full measurement through the C ABI
+(catalogue scalars, painting of both interlacing phases, 15 real-field transforms per phase,
+contraction, normalisation).  Metric: P_l meshes/s (measurements per second, whole job).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU: one independent measurement per rank per step (replicas; the estimator has no
+exchange step), launched with torch.distributed.run; value = all ranks' measurements / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "p024b_mixed_512"
+METRIC = "P_l meshes/s @512^3 (P_0,2,4 + P_4b,6b,8b, catalogue to multipoles)"
+UNIT = "meshes/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _src_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2605_04864_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, fn), "rb") as f:
+            h.update(fn.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on the current source."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        rec = d.get(WORKLOAD, {}).get(kernel)
+        if rec and rec.get("src_hash") == _src_hash():
+            return float(rec["bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.idx = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_inputs(w, rank=0):
+    from synthetic import make_survey_catalogs
+
+    g, r, origin = make_survey_catalogs(w["n_gal"], w["n_ran"], w["box"], w["distance"], w["n_gen"],
+                                        seed=w["seed"] + rank, fkp_p0=w["fkp_p0"])
+    return g, r, origin
+
+
+def algorithmic_bytes(w, stage, nf):
+    """Bytes each stage must move at least once (float32 meshes / complex64 half spectra)."""
+    n = w["n"]
+    mesh = 4 * n**3            # one real float32 mesh
+    half = 8 * (n // 2) * n * n  # one complex64 half spectrum = 4 n^3
+    nph = 2 if w["interlace"] else 1
+    ntot = w["n_gal"] + w["n_ran"]
+    if stage == "fft_z_weighted":
+        return nph * mesh + nf * half
+    if stage == "fft_y":
+        return 2 * nf * half
+    if stage == "fft_x_contract":
+        return nf * half
+    tiles = nph * mesh * ((16 + 4) / 16) ** 3   # (bs+4)^3 tiles per bs^3 brick, per phase
+    if stage == "paint_count":      # positions in, brick id + rank out
+        return ntot * (12 + 8)
+    if stage == "paint_scatter":    # positions + weight + brick id + rank in, 16 B records out
+        return ntot * (16 + 8 + 16)
+    if stage == "paint_tiles":      # records in, tiles out
+        return ntot * 16 + tiles
+    if stage == "paint_fold":       # tiles in, meshes out
+        return tiles + nph * mesh
+    return 0
+
+
+def cpu_baseline(w, sample_n=128):
+    """The FP64 oracle as it stands on a bounded sample: same geometry, mesh sample_n^3 and the
+    particle counts scaled by (sample_n/n)^3 (same particles per cell); rate scaled to 512^3 by
+    (n/sample_n)^3 * log(n^3)/log(sample_n^3) (transform-dominated)."""
+    import math
+
+    from oracle import power as P
+    from synthetic import make_survey_catalogs
+
+    f = (sample_n / w["n"]) ** 3
+    g, r, origin = make_survey_catalogs(int(w["n_gal"] * f), int(w["n_ran"] * f), w["box"], w["distance"],
+                                        min(w["n_gen"], sample_n), seed=w["seed"], fkp_p0=w["fkp_p0"])
+    spec = dict(n=sample_n, box=w["box"], origin=tuple(origin), assign=w["assign"], interlace=w["interlace"],
+                los="endpoint", observer=(0.0, 0.0, 0.0))
+    kn = math.pi * sample_n / w["box"]
+    kb = (w["kmin"], w["dk"], min(w["nbins"], int(kn / w["dk"])))
+    t0 = time.perf_counter()
+    P.power_multipoles(spec, g, r, kb, w["ells"], w["modified"], method="plain")
+    dt = time.perf_counter() - t0
+    scale = (w["n"] / sample_n) ** 3 * math.log(w["n"] ** 3) / math.log(sample_n ** 3)
+    return dt, scale, (f"oracle (numpy FP64, Hand+17 full-m) on a {sample_n}^3 mesh with "
+                       f"{len(g.w)} galaxies + {len(r.w)} randoms, same box; time x {scale:.1f} "
+                       f"(cells x log-ratio) to the 512^3 workload")
+
+
+def run_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    times, desc, scale = [], "", 1.0
+    for i in range(args.warmup + args.steps):
+        dt, scale, desc = cpu_baseline(w, sample_n=64)
+        if i >= args.warmup:
+            times.append(dt)
+    per = sum(times) / len(times) * scale
+    value = 1.0 / per
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "mesh": w["n"], "n_gal": w["n_gal"], "n_ran": w["n_ran"],
+                       "global_batch": 1, "parallelism": "replicas"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD, help="power workload name (profiling uses a smaller one)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    from synthetic import workload
+
+    w = workload(args.workload)
+    if args.impl == "reference":
+        run_reference(args, w)
+        return
+
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    if not os.path.exists(os.path.join(ROOT, "paper_2605_04864_gb300", "libnpc.so")):
+        import __graft_entry__
+
+        __graft_entry__.build()
+    from types import SimpleNamespace
+
+    from paper_2605_04864_gb300 import api
+    from paper_2605_04864_gb300 import binding as B
+    import ctypes as C
+
+    g, r, origin = make_inputs(w, rank)
+    dev = lambda c: SimpleNamespace(pos=torch.from_numpy(c.pos).cuda(), w=torch.from_numpy(c.w).cuda(),
+                                    nbar=torch.from_numpy(c.nbar).cuda())
+    gd, rd = dev(g), dev(r)
+    kb = (w["kmin"], w["dk"], w["nbins"])
+    kbs = B.npc_kbins(*kb)
+    emask = sum(1 << l for l in w["ells"])
+    mmask = sum(1 << l for l in w["modified"])
+    out_len = B.npc_power_out_len(C.byref(kbs), emask, mmask)
+    out = torch.zeros(out_len, dtype=torch.float64, device="cuda")
+    kw = dict(n=w["n"], box=w["box"], origin=origin, assign=w["assign"], interlace=w["interlace"], kbins=kb,
+              ells=w["ells"], modified=w["modified"], precision=w["precision"])
+
+    def step_dev():
+        api.power_multipoles(gd, rd, out=out, **kw)
+
+    for _ in range(args.warmup):
+        step_dev()
+    torch.cuda.synchronize()
+    launches = api.last_stats()["n_kernel_launches"]
+    nf = 2 * api.last_stats()["n_r2c_equivalent"] * api.last_stats()["n_phases"] // 2
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    # --- device-resident timed region ---
+    clk = ClockSampler(local)
+    clk.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(args.steps):
+        step_dev()
+    e.record()
+    torch.cuda.synchronize()
+    barrier()
+    clocks = clk.stop()
+    ms = max_over_ranks(s.elapsed_time(e))
+    ms_per_step = ms / args.steps
+    value = world * args.steps / (ms / 1e3)
+
+    # --- per-stage device times (CUDA events recorded by the library on the same stream) ---
+    api.set_profiling(True)
+    acc = {}
+    for _ in range(args.steps):
+        step_dev()
+        for name, t, nl in api.stage_times():
+            a = acc.setdefault(name, [0.0, 0, 0])
+            a[0] += t
+            a[1] += nl
+            a[2] += 1
+    api.set_profiling(False)
+    kernel_stages = {k: v for k, v in acc.items()
+                     if k in ("paint_count", "paint_scatter", "paint_tiles", "paint_fold", "fft_z_weighted",
+                              "fft_y", "fft_x_contract")}
+    dom = max(kernel_stages, key=lambda k: kernel_stages[k][0])
+    tot_ms, tot_launch, nrep = kernel_stages[dom]
+    per_launch_ms = tot_ms / max(tot_launch, 1)
+    launches_per_call = tot_launch / nrep
+    bytes_call = algorithmic_bytes(w, dom, nf)
+    bytes_launch = bytes_call / max(launches_per_call, 1)
+    peak, peak_kind = _peaks()
+    achieved = bytes_launch / (per_launch_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": _traffic(dom), "peak_source": peak_kind,
+                "bytes_per_launch": bytes_launch, "launch_ms": per_launch_ms}
+    stages = {k: round(v[0] / v[2], 4) for k, v in acc.items()}
+
+    # --- end to end through the C ABI with pinned host catalogues and a host result ---
+    pin = lambda c: SimpleNamespace(pos=torch.from_numpy(c.pos).pin_memory(), w=torch.from_numpy(c.w).pin_memory(),
+                                    nbar=torch.from_numpy(c.nbar).pin_memory())
+    gh, rh = pin(g), pin(r)
+    h2d = sum(t.numel() * t.element_size() for c in (gh, rh) for t in (c.pos, c.w, c.nbar))
+    d2h = out_len * 8
+    api.power_multipoles(gh, rh, **kw)
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    s.record()
+    for _ in range(args.steps):
+        res = api.power_multipoles(gh, rh, **kw)
+    e.record()
+    torch.cuda.synchronize()
+    barrier()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e = {"value": world * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+           "ms_per_step": e2e_s / args.steps * 1e3}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 transforms, f64 accumulators", "data": "synthetic",
+            "config": {"workload": args.workload, "mesh": w["n"], "assign": "TSC", "interlace": True,
+                       "n_gal": w["n_gal"], "n_ran": w["n_ran"], "ells": list(w["ells"]),
+                       "modified": list(w["modified"]), "nbins": w["nbins"], "global_batch": world,
+                       "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (catalogues 440 MB, meshes 2x537 MB, spectra 16 GB)"},
+            "roofline": roofline, "stages_ms": stages, "e2e": e2e, "gpu_launches": launches * args.steps,
+            "clocks": clocks}
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        dt, scale, desc = cpu_baseline(w)
+        line["cpu_baseline"] = {"value": 1.0 / (dt * scale), "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": desc, "sample_seconds": dt}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    del res, np
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

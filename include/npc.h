@@ -110,6 +110,14 @@ typedef struct {
 } npc_stats;
 npc_status npc_last_stats(npc_ctx* ctx, npc_stats* out);
 
+/* Stage timing.  With profiling on, every call records CUDA events on the context's stream at its
+ * stage boundaries (a few events per call, no synchronisation).  npc_stage_times() waits for the
+ * stream, then reports the stages of the last call: names[i] (NUL-terminated, 32 bytes each),
+ * ms[i] = device time of stage i and launches[i] = kernels in stage i, for i < *n <= cap. */
+npc_status npc_set_profiling(npc_ctx* ctx, int32_t on);
+npc_status npc_stage_times(npc_ctx* ctx, char* names, double* ms, int32_t* launches, int32_t cap,
+                           int32_t* n);
+
 /* Catalogue scalars (Sec. 2.1, Yamamoto estimator; Sec. 2.2 for I33) --------------------------
  * out[0..7] = { alpha, I22, I33, N0, S3, sum_w(data), sum_w(randoms), sum_w2 } with
  *   alpha = sum_g w / sum_r w,  I22 = alpha sum_r nbar w^2,  I33 = alpha sum_r nbar^2 w^3,

@@ -171,6 +171,8 @@ def n_shot_two_index(ell, ellp, n0):
 def power_from_fields(spec, fields, kbins, ells, scalars, modified=(), fields_kind="F"):
     """Binned P_l (and the modified multipoles) from Fourier fields.
 
+    Bins without modes report 0 for every multipole (convention shared with the GPU library).
+
     fields_kind = "F": fields are F_l (Hand+17 or inverted); "G": fields are G_l and P_l uses
     Re<F_0 G_l^*> (Eq. pk_final) while the two-index spectra use F_l from Eq. F_and_new_G.
     """
@@ -181,10 +183,15 @@ def power_from_fields(spec, fields, kbins, ells, scalars, modified=(), fields_ki
     res = {"P": {}, "Pll": {}, "Pmod": {}}
     kmean, cnt = M.bin_average(kmag, b, nb)
     res["k_eff"], res["nmodes"] = kmean, cnt
-    for ell in ells:
+    empty = cnt == 0
+    internal = sorted(set(ells) | ({0, 2, 4} if modified else set()))
+    pl = {}
+    for ell in internal:
         v = np.real(f0 * np.conj(fields[ell]))
         mean, _ = M.bin_average(v, b, nb)
-        res["P"][ell] = (2 * ell + 1) / i22 * mean - (n0 if ell == 0 else 0.0)
+        pl[ell] = np.where(empty, 0.0, (2 * ell + 1) / i22 * mean - (n0 if ell == 0 else 0.0))
+    for ell in ells:
+        res["P"][ell] = pl[ell]
     if modified:
         if fields_kind == "G":
             ff = {ell: f_from_g(fields[ell], ell) for ell in fields}
@@ -195,13 +202,13 @@ def power_from_fields(spec, fields, kbins, ells, scalars, modified=(), fields_ki
             if a in ff and c in ff:
                 v = np.real(ff[a] * np.conj(ff[c]))
                 mean, _ = M.bin_average(v, b, nb)
-                res["Pll"][(a, c)] = ((2 * (a + c) + 1) / i22 * mean
-                                      - n_shot_two_index(a, c, n0))
+                res["Pll"][(a, c)] = np.where(empty, 0.0, (2 * (a + c) + 1) / i22 * mean
+                                              - n_shot_two_index(a, c, n0))
         for lb in modified:
             acc = 0.0
             for key, coef in PLB_COEFFS[lb].items():
                 if key[0] == 0:
-                    term = res["P"][key[1]]
+                    term = pl[key[1]]
                 else:
                     term = res["Pll"][key]
                 acc = acc + float(coef) * term

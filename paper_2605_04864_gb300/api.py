@@ -18,7 +18,9 @@ def _stream_ptr(device):
         import torch
 
         if torch.cuda.is_available():
-            return C.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+            # torch's default stream is the legacy default stream (handle 0); the library takes
+            # NULL to mean "own stream", so pass cudaStreamLegacy (0x1) explicitly
+            return C.c_void_p(torch.cuda.current_stream(device).cuda_stream or 1)
     except Exception:  # pragma: no cover - torch without CUDA
         pass
     return C.c_void_p(0)
@@ -120,9 +122,7 @@ def power_multipoles(data, randoms, n, box, origin=(0.0, 0.0, 0.0), assign=3, in
     kb = B.npc_kbins(float(kbins[0]), float(kbins[1]), int(kbins[2]))
     emask = sum(1 << int(l) for l in ells)
     mmask = sum(1 << int(l) for l in modified)
-    length = B.npc_power_out_len(C.byref(kb), emask, mmask)
-    if length <= 0:
-        raise ValueError("bad multipole request")
+    length = max(int(B.npc_power_out_len(C.byref(kb), emask, mmask)), 1)  # the library rejects bad requests
     d = make_catalog(data, keep)
     r = make_catalog(randoms, keep)
     ctx = context(device)
@@ -166,3 +166,19 @@ def last_stats(device=0):
     st = B.npc_stats()
     B.check(B.npc_last_stats(context(device), C.byref(st)))
     return {k: getattr(st, k) for k, _ in B.npc_stats._fields_}
+
+
+def set_profiling(on=True, device=0):
+    B.check(B.npc_set_profiling(context(device), 1 if on else 0))
+
+
+def stage_times(device=0, cap=64):
+    """[(name, ms, launches)] for the stages of the last call (waits for the stream)."""
+    ctx = context(device)
+    names = C.create_string_buffer(32 * cap)
+    ms = (C.c_double * cap)()
+    nl = (C.c_int32 * cap)()
+    n = C.c_int32(0)
+    B.check(B.npc_stage_times(ctx, names, ms, nl, cap, C.byref(n)), ctx)
+    raw = names.raw
+    return [(raw[32 * i:32 * i + 32].split(b"\0")[0].decode(), ms[i], nl[i]) for i in range(n.value)]

@@ -1,6 +1,7 @@
 // C ABI of libnpc.so: context management, argument validation, device tables and the
 // orchestration of the estimator pipelines.  All compute runs in the kernels of catalog.cu,
 // power.cu and bispec.cu; the host only validates, allocates workspace and enqueues.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstring>
@@ -45,6 +46,13 @@ npc_status ws_get(npc_ctx* ctx, const char* name, size_t bytes, void** out) {
   return NPC_OK;
 }
 
+static bool table_cached(npc_ctx* ctx, const std::string& name, const std::vector<char>& key, void** out) {
+  auto it = ctx->host_cache_keys.find(name);
+  if (it == ctx->host_cache_keys.end() || it->second != key) return false;
+  *out = ctx->ws[name].p;
+  return *out != nullptr;
+}
+
 npc_status ws_table(npc_ctx* ctx, const std::string& name, const std::vector<char>& key, const void* data,
                     size_t bytes, void** out) {
   auto it = ctx->host_cache_keys.find(name);
@@ -71,6 +79,7 @@ YNorm ylm_norm_table() {
       double r = 1.0;  // (l-m)!/(l+m)!
       for (int j = l - m + 1; j <= l + m; ++j) r /= (double)j;
       t.v[l * (l + 1) / 2 + m] = std::sqrt((2.0 * l + 1.0) / (4.0 * M_PI) * r);
+      t.f[l * (l + 1) / 2 + m] = (float)t.v[l * (l + 1) / 2 + m];
     }
   return t;
 }
@@ -80,6 +89,10 @@ npc_status get_twiddles(npc_ctx* ctx, int n, int prec, const void** out) {
   key_push(key, n);
   const std::string name = std::string(prec == NPC_PREC_FP64 ? "tw64." : "tw32.") + std::to_string(n);
   void* p;
+  if (table_cached(ctx, name, key, &p)) {
+    *out = p;
+    return NPC_OK;
+  }
   if (prec == NPC_PREC_FP64) {
     std::vector<double2> h(n);
     for (int j = 0; j < n; ++j) h[j] = make_double2(std::cos(2.0 * M_PI * j / n), -std::sin(2.0 * M_PI * j / n));
@@ -102,6 +115,11 @@ npc_status get_bin_table(npc_ctx* ctx, int n, double box, const npc_kbins& kb, c
   key_push(key, kb.kmin);
   key_push(key, kb.dk);
   key_push(key, kb.nbins);
+  void* cached;
+  if (table_cached(ctx, "bintab", key, &cached)) {
+    *out = (const int16_t*)cached;
+    return NPC_OK;
+  }
   const int64_t nmax = 3LL * (n / 2) * (n / 2);
   std::vector<int16_t> h(nmax + 1);
   const double kf = 2.0 * M_PI / box;
@@ -198,9 +216,41 @@ static Geom make_geom(const npc_mesh_spec& m) {
   return g;
 }
 
+npc_status stage_begin(npc_ctx* ctx) {
+  ctx->stage_names.clear();
+  ctx->stage_launches.clear();
+  ctx->ev_used = 0;
+  ctx->launches_at_mark = ctx->launches;
+  if (!ctx->profile) return NPC_OK;
+  if (ctx->ev_pool.empty()) {
+    cudaEvent_t e;
+    NPC_CUDA(ctx, cudaEventCreate(&e));
+    ctx->ev_pool.push_back(e);
+  }
+  NPC_CUDA(ctx, cudaEventRecord(ctx->ev_pool[0], ctx->stream));
+  ctx->ev_used = 1;
+  return NPC_OK;
+}
+
+npc_status stage_mark(npc_ctx* ctx, const char* name) {
+  if (!ctx->profile) return NPC_OK;
+  if ((int)ctx->ev_pool.size() <= ctx->ev_used) {
+    cudaEvent_t e;
+    NPC_CUDA(ctx, cudaEventCreate(&e));
+    ctx->ev_pool.push_back(e);
+  }
+  NPC_CUDA(ctx, cudaEventRecord(ctx->ev_pool[ctx->ev_used], ctx->stream));
+  ctx->ev_used++;
+  ctx->stage_names.push_back(name);
+  ctx->stage_launches.push_back(ctx->launches - ctx->launches_at_mark);
+  ctx->launches_at_mark = ctx->launches;
+  return NPC_OK;
+}
+
 static void begin_call(npc_ctx* ctx) {
   ctx->launches = 0;
   ctx->last_error.clear();
+  stage_begin(ctx);
 }
 
 static npc_status end_call(npc_ctx* ctx) {
@@ -272,6 +322,7 @@ npc_status npc_destroy(npc_ctx* ctx) {
   cudaStreamSynchronize(ctx->stream);
   for (auto& kv : ctx->ws)
     if (kv.second.p) cudaFree(kv.second.p);
+  for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
   return NPC_OK;
@@ -287,6 +338,33 @@ npc_status npc_last_error(npc_ctx* ctx, char* buf, size_t n) {
 npc_status npc_last_stats(npc_ctx* ctx, npc_stats* out) {
   if (!ctx || !out) return NPC_ERR_INVALID_ARG;
   *out = ctx->stats;
+  return NPC_OK;
+}
+
+npc_status npc_set_profiling(npc_ctx* ctx, int32_t on) {
+  if (!ctx) return NPC_ERR_INVALID_ARG;
+  ctx->profile = on != 0;
+  return NPC_OK;
+}
+
+npc_status npc_stage_times(npc_ctx* ctx, char* names, double* ms, int32_t* launches, int32_t cap, int32_t* n) {
+  if (!ctx || !n) return NPC_ERR_INVALID_ARG;
+  *n = 0;
+  if (!ctx->profile || ctx->ev_used < 2) return NPC_OK;
+  NPC_CUDA(ctx, cudaSetDevice(ctx->device));
+  NPC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  const int ns = std::min<int>((int)ctx->stage_names.size(), cap);
+  for (int i = 0; i < ns; ++i) {
+    float t = 0.f;
+    NPC_CUDA(ctx, cudaEventElapsedTime(&t, ctx->ev_pool[i], ctx->ev_pool[i + 1]));
+    if (ms) ms[i] = t;
+    if (launches) launches[i] = ctx->stage_launches[i];
+    if (names) {
+      std::strncpy(names + 32 * i, ctx->stage_names[i].c_str(), 31);
+      names[32 * i + 31] = '\0';
+    }
+  }
+  *n = ns;
   return NPC_OK;
 }
 
@@ -373,6 +451,10 @@ npc_status npc_power_multipoles(npc_ctx* ctx, const npc_mesh_spec* mesh, const n
       if (!(need & (1 << l))) continue;
       for (int m = 0; m <= l; ++m) {
         for (int ph = 0; ph < nphase; ++ph) {
+          if (l == 0) {
+            push(ph, 0, 0, PART_ONE);  // F_0 needs no weighting
+            continue;
+          }
           push(ph, l, m, PART_RE);
           if (m > 0) push(ph, l, m, PART_IM);
         }
@@ -390,20 +472,25 @@ npc_status npc_power_multipoles(npc_ctx* ctx, const npc_mesh_spec* mesh, const n
   if (randoms) NPC_TRY(stage_catalog(ctx, randoms, "rand", &r));
   double* sc;
   NPC_TRY(ws_get(ctx, "scalars", sizeof(double) * SC_COUNT, (void**)&sc));
+  NPC_TRY(stage_mark(ctx, "upload"));
   NPC_TRY(launch_catalog_scalars(ctx, d, randoms ? &r : nullptr, mesh->box, sc));
+  NPC_TRY(stage_mark(ctx, "scalars"));
 
   const size_t rs = prec == NPC_PREC_FP64 ? 8 : 4;
   const size_t ncell = (size_t)n * n * n;
   void *ma, *mb = nullptr, *half;
   NPC_TRY(ws_get(ctx, "mesh.a", rs * ncell, &ma));
   if (nphase == 2) NPC_TRY(ws_get(ctx, "mesh.b", rs * ncell, &mb));
-  NPC_TRY(launch_paint(ctx, d, randoms ? &r : nullptr, *mesh, 1, prec, sc, ma, mb));
   NPC_TRY(ws_get(ctx, "half", 2 * rs * (size_t)fl.nf * (n / 2) * n * n, &half));
-  NPC_TRY(run_forward_transforms(ctx, prec, plan, g, ma, mb, half));
   double* dev_out = out;
   if (!out_on_device) NPC_TRY(ws_get(ctx, "power.out", sizeof(double) * out_len, (void**)&dev_out));
+  NPC_TRY(stage_mark(ctx, "alloc"));
+  NPC_TRY(launch_paint(ctx, d, randoms ? &r : nullptr, *mesh, 1, prec, sc, ma, mb));
+  NPC_TRY(stage_mark(ctx, "paint_fold"));
+  NPC_TRY(run_forward_transforms(ctx, prec, plan, g, ma, mb, half));
   NPC_TRY(run_power_contract(ctx, prec, plan, *mesh, *bins, half, sc, dev_out));
   NPC_TRY(finish_output(ctx, dev_out, out, out_len, out_on_device));
+  NPC_TRY(stage_mark(ctx, "download"));
   return end_call(ctx);
 }
 

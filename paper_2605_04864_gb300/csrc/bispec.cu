@@ -1,13 +1,973 @@
-// Bispectrum multipoles (placeholder until the shell-field kernels are in place).
-#include "npc_internal.cuh"
+// Bispectrum multipoles: Scoccimarro B_l (Sec. 2.2, Eq. bi_sco) with l on the first (smallest)
+// side, the compressed TripoSH multipoles B_l0l (Sec. 4, Eq. new_bispec) and their analytic shot
+// noise (Sec. 5.4), for a periodic box with a global line of sight.
+//
+// Pipeline (all bins resident in HBM):
+//   1. forward transforms of the FKP field and of the w^2 N-field (power.cu passes, kz pruned to
+//      the sphere |q| <= 2 k_max that the closure can reach);
+//   2. k_fft_x_combine: last forward pass + interlacing + window compensation -> X_0(q), N_0(q);
+//   3. k_bin_cross: shell sums of Re[X_0 N_0^*] L_l(mu) and of L_l(mu) on the k-bins and on the
+//      unit-width shells of the k_3 compression (shot-noise ingredients H_l, Q_l, N_mode);
+//   4. shell-filtered inverse transforms F_b(x) = sum_{q in b} X(q) e^{iq.x} for F_0 (X_0), F_2
+//      (L_2(mu) X_0), the indicator I_b (1 per mode, for the triangle counts) and the full fields
+//      G^(l) = sum_{|q| <= 2k_max} L_l(mu) X_0(q) e^{iq.x}: x rows only inside the sphere
+//      (k_shell_x), y columns from the compact rows (k_shell_y), z columns of two real fields at
+//      a time as one complex inverse transform (k_shell_z);
+//   5. k_triple: sum_x F_i F_j F_k for every (i <= j, k) and sum_x F_i F_j G^(l) -- float products
+//      over cells staged in shared memory, float64 accumulation per chunk of cells, per-CTA
+//      partials reduced in a fixed order;
+//   6. k_bispec_finalize: normalisation (2l+1)/(I33 N_T) and (2l+1)/(I33 N_i N_j), shot noise.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
 
-extern "C" {
-npc_status npc_bispectrum(npc_ctx* ctx, const npc_mesh_spec*, const npc_catalog*, const npc_catalog*,
-                          const npc_kbins*, uint32_t, uint32_t, int32_t, npc_precision, double*, int32_t) {
-  return set_err(ctx, NPC_ERR_UNSUPPORTED, "bispectrum not built yet");
+#include "fft_core.cuh"
+
+namespace {
+
+constexpr int BT = 256;
+
+template <typename T>
+__device__ __forceinline__ T sinc_p(T a, int p) {
+  const T s = a == T(0) ? T(1) : sin(a) / a;
+  T r = s;
+  for (int i = 1; i < p; ++i) r *= s;
+  return r;
 }
-npc_status npc_bispectrum_layout(const npc_kbins*, uint32_t, uint32_t, int64_t*, int64_t*, int64_t*) {
-  return NPC_ERR_UNSUPPORTED;
+
+// ------------------------------------------------------------------------------------------
+// 2. last forward pass along x with interlacing and compensation
+//    half[f][kz][ky][kx] (KZ planes; fields ordered phase a, phase b per output)
+//    -> X[o][kz][ky][kx] for kz < KZ, |ky| <= KY
+// ------------------------------------------------------------------------------------------
+template <typename T, int N>
+__global__ void __launch_bounds__(BT)
+k_fft_x_combine(const cplx<T>* __restrict__ half, int nout, int nphase, int KZ, int KY, int assign,
+                const cplx<T>* __restrict__ tw_g, cplx<T>* __restrict__ X) {
+  using C = cplx<T>;
+  constexpr int TPF = N / 8;
+  constexpr int G = BT / TPF > 0 ? BT / TPF : 1;
+  constexpr int NP = row_pad_len<N>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  C* phs = tw + N;
+  C* rows = phs + N;
+  const int nf = nout * nphase;
+  T* winv = reinterpret_cast<T*>(rows + (size_t)(nf + G) * NP);
+  const int tid = threadIdx.x;
+  for (int i = tid; i < N; i += blockDim.x) {
+    tw[i] = tw_g[i];
+    const T a = T(M_PI) * T(i - N / 2) / T(N);
+    phs[i] = cmk(cos(a), sin(a));
+  }
+  for (int i = tid; i <= N / 2; i += blockDim.x) winv[i] = T(1) / sinc_p<T>(T(M_PI) * T(i) / T(N), assign);
+  __syncthreads();
+  const int g = tid / TPF, t = tid % TPF;
+  const int nyr = 2 * KY + 1;
+  const int nrows = KZ * nyr;
+  const size_t fstride = (size_t)KZ * N * N;
+  for (int r = blockIdx.x; r < nrows; r += gridDim.x) {
+    const int kz = r / nyr;
+    const int jy = r % nyr - KY;
+    const int ky = jy < 0 ? jy + N : jy;
+    for (int f0 = 0; f0 < nf; f0 += G) {
+      const int f = f0 + g;
+      const bool live = g < G && f < nf;
+      C v[8];
+      if (live) {
+        const C* src = half + (size_t)f * fstride + ((size_t)kz * N + ky) * N;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = src[t + q * TPF];
+      } else {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = cmk(T(0), T(0));
+      }
+      RowView<C> rv{rows + (size_t)(live ? f : nf + (g < G ? g : 0)) * NP};
+      fft_block<N, -1>(v, t, tw, rv);
+      if (live) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) rv.st(t + q * TPF, v[q]);
+      }
+    }
+    __syncthreads();
+    for (int kx = tid; kx < N; kx += blockDim.x) {
+      const int i = kx < N / 2 ? kx : kx - N;
+      const int ai = i < 0 ? -i : i, aj = jy < 0 ? -jy : jy;
+      const T iw = winv[ai] * winv[aj] * winv[kz];
+      const int jp = RowView<C>::idx(kx);
+      for (int o = 0; o < nout; ++o) {
+        C x = rows[(size_t)(o * nphase) * NP + jp];
+        if (nphase == 2) {
+          const C ph = cmul(cmul(phs[i + N / 2], phs[jy + N / 2]), phs[kz + N / 2]);
+          x = cscale(cadd(x, cmul(ph, rows[(size_t)(o * nphase + 1) * NP + jp])), T(0.5));
+        }
+        X[(size_t)o * fstride + ((size_t)kz * N + ky) * N + kx] = cscale(x, iw);
+      }
+    }
+    __syncthreads();
+  }
 }
-npc_status npc_bispectrum_triangles(const npc_kbins*, int32_t*, int64_t, int64_t*) { return NPC_ERR_UNSUPPORTED; }
+
+// ------------------------------------------------------------------------------------------
+// Warp-segmented accumulation of NS sums into per-warp float64 partials (runs of consecutive
+// lanes with equal bin; deterministic for a fixed thread-to-mode map).
+// ------------------------------------------------------------------------------------------
+template <typename T, int NS>
+__device__ __forceinline__ void seg_accumulate(int lane, int bin, const T (&vals)[NS], double* mypart) {
+  const int pb = __shfl_up_sync(0xffffffffu, bin, 1);
+  const bool head = (lane == 0) || (pb != bin);
+  const unsigned heads = __ballot_sync(0xffffffffu, head);
+  const int seg = __popc(heads & (0xffffffffu >> (31 - lane)));
+  unsigned addm = 0;
+#pragma unroll
+  for (int st = 0; st < 5; ++st) {
+    const int off = 1 << st;
+    const int os = __shfl_up_sync(0xffffffffu, seg, off);
+    if (lane >= off && os == seg) addm |= 1u << st;
+  }
+  const bool last = (lane == 31) || ((heads >> (lane + 1)) & 1u);
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    T x = vals[s];
+#pragma unroll
+    for (int st = 0; st < 5; ++st) {
+      const T y = __shfl_up_sync(0xffffffffu, x, 1 << st);
+      if (addm & (1u << st)) x += y;
+    }
+    if (last && bin >= 0) atomicAdd(mypart + (size_t)bin * NS + s, (double)x);
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// 3. shell sums for the shot noise: per bin [sum w Re(X N*), sum w L2 Re(X N*), sum w, sum w L2]
+//    on two bin sets (the k-bins and the unit-width k3 shells), modes with |ky|, kz <= KY.
+// ------------------------------------------------------------------------------------------
+constexpr int NCROSS = 4;
+
+template <typename T, int N>
+__global__ void __launch_bounds__(BT)
+k_bin_cross(const cplx<T>* __restrict__ X0, const cplx<T>* __restrict__ XN, int KZ, int KY, double lx, double ly,
+            double lz, const int16_t* __restrict__ tab_m, int nbm, const int16_t* __restrict__ tab_q, int nbq,
+            int n2max, double* __restrict__ part_m, double* __restrict__ part_q) {
+  using C = cplx<T>;
+  constexpr int NW = BT / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double* pm = part_m + ((size_t)blockIdx.x * NW + warp) * nbm * NCROSS;
+  double* pq = part_q + ((size_t)blockIdx.x * NW + warp) * nbq * NCROSS;
+  const int nyr = 2 * KY + 1;
+  const int nrows = (KY + 1) * nyr;
+  const size_t fstride = (size_t)KZ * N * N;
+  (void)fstride;
+  for (int r = blockIdx.x; r < nrows; r += gridDim.x) {
+    const int kz = r / nyr;
+    const int jy = r % nyr - KY;
+    const int ky = jy < 0 ? jy + N : jy;
+    for (int jb = warp * 32; jb < N; jb += blockDim.x) {
+      const int j = jb + lane;
+      const int i = j < N / 2 ? j : j - N;
+      const int n2 = i * i + jy * jy + kz * kz;
+      int bm = -1, bq = -1;
+      T vals[NCROSS] = {T(0), T(0), T(0), T(0)};
+      if (j < N && n2 > 0 && n2 <= n2max && i != -N / 2 && jy != -N / 2) {
+        bm = tab_m[n2];
+        bq = tab_q[n2];
+        const size_t idx = ((size_t)kz * N + ky) * N + j;
+        const C a = X0[idx], b = XN[idx];
+        const T cr = a.x * b.x + a.y * b.y;
+        const T kk = sqrt(T(n2));
+        const T mu = (T(i) * T(lx) + T(jy) * T(ly) + T(kz) * T(lz)) / kk;
+        const T l2 = T(1.5) * mu * mu - T(0.5);
+        const T w = kz > 0 ? T(2) : T(1);
+        vals[0] = w * cr;
+        vals[1] = w * l2 * cr;
+        vals[2] = w;
+        vals[3] = w * l2;
+      }
+      T vm[NCROSS], vq[NCROSS];
+#pragma unroll
+      for (int s = 0; s < NCROSS; ++s) {
+        vm[s] = bm >= 0 ? vals[s] : T(0);
+        vq[s] = bq >= 0 ? vals[s] : T(0);
+      }
+      seg_accumulate<T, NCROSS>(lane, bm, vm, pm);
+      seg_accumulate<T, NCROSS>(lane, bq, vq, pq);
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// 4. shell-filtered inverse transforms
+// ------------------------------------------------------------------------------------------
+struct ShellField {
+  int8_t src;     // 0: X_0, 1: ones (indicator)
+  int8_t mult;    // 0: 1, 1: L_2(mu)
+  int16_t bin;    // >= 0: modes of this bin; -1: all modes with n2 <= n2cap
+  int K;          // kz <= K, |ky| <= K
+  int64_t off1;   // offset of this field in the x-pass output (complex elements)
+  int64_t off2;   // offset in the y-pass output
+};
+
+// x rows: for every (kz <= Kmax, |ky| <= Kmax) row, every field whose K covers it.
+template <typename T, int N>
+__global__ void __launch_bounds__(BT)
+k_shell_x(const cplx<T>* __restrict__ X0, int KZX, const ShellField* __restrict__ fields, int nfields, int Kmax,
+          const int16_t* __restrict__ tab, int n2cap, double lx, double ly, double lz, const cplx<T>* __restrict__ tw_g,
+          cplx<T>* __restrict__ T1) {
+  using C = cplx<T>;
+  constexpr int TPF = N / 8;
+  constexpr int G = BT / TPF > 0 ? BT / TPF : 1;
+  constexpr int NP = row_pad_len<N>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  C* xrow = tw + N;                  // X_0 row
+  T* l2row = reinterpret_cast<T*>(xrow + N);   // L_2(mu) per kx
+  int* binrow = reinterpret_cast<int*>(l2row + N);  // bin per kx (-1 excluded), n2 per kx
+  int* n2row = binrow + N;
+  C* bufs = reinterpret_cast<C*>(n2row + N);   // G x NP
+  const int tid = threadIdx.x;
+  for (int i = tid; i < N; i += blockDim.x) tw[i] = tw_g[i];
+  const int g = tid / TPF, t = tid % TPF;
+  const int nyr = 2 * Kmax + 1;
+  const int nrows = (Kmax + 1) * nyr;
+  const size_t xstride = (size_t)KZX * N * N;
+  (void)xstride;
+  __syncthreads();
+  for (int r = blockIdx.x; r < nrows; r += gridDim.x) {
+    const int kz = r / nyr;
+    const int jy = r % nyr - Kmax;
+    const int ky = jy < 0 ? jy + N : jy;
+    const int ay = jy < 0 ? -jy : jy;
+    for (int kx = tid; kx < N; kx += blockDim.x) {
+      const int i = kx < N / 2 ? kx : kx - N;
+      const int n2 = i * i + jy * jy + kz * kz;
+      const bool inrange = i != -N / 2 && jy != -N / 2 && n2 <= n2cap;
+      xrow[kx] = (inrange && kz < KZX) ? X0[((size_t)kz * N + ky) * N + kx] : cmk(T(0), T(0));
+      const T kk = sqrt(T(n2));
+      const T mu = n2 > 0 ? (T(i) * T(lx) + T(jy) * T(ly) + T(kz) * T(lz)) / kk : T(0);
+      l2row[kx] = T(1.5) * mu * mu - T(0.5);
+      binrow[kx] = inrange ? tab[n2] : -1;
+      n2row[kx] = inrange ? n2 : -1;
+    }
+    __syncthreads();
+    // fields active on this row
+    for (int f0 = 0; f0 < nfields; f0 += G) {
+      const int f = f0 + g;
+      bool live = g < G && f < nfields;
+      ShellField sf{};
+      if (live) {
+        sf = fields[f];
+        live = kz <= sf.K && ay <= sf.K;
+      }
+      C v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int kx = t + q * TPF;
+        C a = cmk(T(0), T(0));
+        if (live) {
+          const bool in = sf.bin >= 0 ? (binrow[kx] == sf.bin) : (n2row[kx] >= 0);
+          if (in) {
+            a = sf.src == 0 ? xrow[kx] : cmk(T(1), T(0));
+            if (sf.mult) a = cscale(a, l2row[kx]);
+          }
+        }
+        v[q] = a;
+      }
+      fft_block<N, +1>(v, t, tw, RowView<C>{bufs + (size_t)(g < G ? g : 0) * NP});
+      if (live) {
+        C* dst = T1 + sf.off1 + ((size_t)kz * (2 * sf.K + 1) + (jy + sf.K)) * N;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) dst[t + q * TPF] = v[q];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <int N> struct BCol {
+  static constexpr int TX = N >= 512 ? 8 : 16;
+  static constexpr int THREADS = TX * N / 8;
+};
+
+// y columns: plane p = (field, kz) from plane tables; input rows ky' = ky + K (|ky| <= K).
+template <typename T, int N>
+__global__ void __launch_bounds__(BCol<N>::THREADS)
+k_shell_y(const cplx<T>* __restrict__ T1, const ShellField* __restrict__ fields, const int* __restrict__ plane_f,
+          const int* __restrict__ plane_kz, const cplx<T>* __restrict__ tw_g, cplx<T>* __restrict__ T2) {
+  using C = cplx<T>;
+  constexpr int TX = BCol<N>::TX;
+  constexpr int TPF = N / 8;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  C* work = tw + N;
+  const int tid = threadIdx.x;
+  const int c = tid % TX, t = tid / TX;
+  for (int i = tid; i < N; i += blockDim.x) tw[i] = tw_g[i];
+  const int p = blockIdx.y;
+  const ShellField sf = fields[plane_f[p]];
+  const int kz = plane_kz[p];
+  const int x = blockIdx.x * TX + c;
+  const C* src = T1 + sf.off1 + (size_t)kz * (2 * sf.K + 1) * N + x;
+  C v[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int yi = t + q * TPF;
+    const int ky = yi < N / 2 ? yi : yi - N;
+    v[q] = (ky >= -sf.K && ky <= sf.K) ? src[(size_t)(ky + sf.K) * N] : cmk(T(0), T(0));
+  }
+  __syncthreads();
+  fft_block<N, +1>(v, t, tw, ColView<C>{work + c, TX});
+  C* dst = T2 + sf.off2 + (size_t)kz * N * N + x;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) dst[(size_t)(t + q * TPF) * N] = v[q];
+}
+
+// z columns, two real fields (same K) per complex inverse transform:
+// c(kz) = A(kz) + i B(kz), c(N - kz) = conj(A(kz)) + i conj(B(kz)); Re -> A(z), Im -> B(z).
+template <typename T, int N>
+__global__ void __launch_bounds__(BCol<N>::THREADS)
+k_shell_z(const cplx<T>* __restrict__ T2, const ShellField* __restrict__ fields, const int* __restrict__ pair_a,
+          const int* __restrict__ pair_b, const int* __restrict__ out_a, const int* __restrict__ out_b,
+          const cplx<T>* __restrict__ tw_g, T* __restrict__ R) {
+  using C = cplx<T>;
+  constexpr int TX = BCol<N>::TX;
+  constexpr int TPF = N / 8;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  C* work = tw + N;
+  const int tid = threadIdx.x;
+  const int c = tid % TX, t = tid / TX;
+  for (int i = tid; i < N; i += blockDim.x) tw[i] = tw_g[i];
+  const int p = blockIdx.z;
+  const int fa = pair_a[p], fb = pair_b[p];
+  const ShellField sa = fields[fa];
+  const int K = sa.K;
+  const int y = blockIdx.y, x = blockIdx.x * TX + c;
+  const size_t plane = (size_t)N * N;
+  const C* A = T2 + sa.off2 + (size_t)y * N + x;
+  const C* Bp = fb >= 0 ? T2 + fields[fb].off2 + (size_t)y * N + x : nullptr;
+  C v[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int zi = t + q * TPF;
+    C val = cmk(T(0), T(0));
+    if (zi <= K) {
+      const C a = A[(size_t)zi * plane];
+      const C b = Bp ? Bp[(size_t)zi * plane] : cmk(T(0), T(0));
+      val = cmk(a.x - b.y, a.y + b.x);  // a + i b
+    } else if (N - zi <= K) {
+      const C a = A[(size_t)(N - zi) * plane];
+      const C b = Bp ? Bp[(size_t)(N - zi) * plane] : cmk(T(0), T(0));
+      val = cmk(a.x + b.y, -a.y + b.x);  // conj(a) + i conj(b)
+    }
+    v[q] = val;
+  }
+  __syncthreads();
+  fft_block<N, +1>(v, t, tw, ColView<C>{work + c, TX});
+  const size_t cell0 = (size_t)y * N + x;
+  T* ra = R + (size_t)out_a[p] * N * plane + cell0;
+  T* rb = out_b[p] >= 0 ? R + (size_t)out_b[p] * N * plane + cell0 : nullptr;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const size_t zo = (size_t)(t + q * TPF) * plane;
+    ra[zo] = v[q].x;
+    if (rb) rb[zo] = v[q].y;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// 5. triple products over cells.  Thread = pair (i <= j).  Per cell: p_a = A1_i B_j (and
+//    p_b = A2_i B_j), s[k] += p C_k for every k, g[l] += p_a G_l.  Float sums over a chunk of
+//    cells, float64 accumulation per chunk in shared memory, per-CTA partials.
+// ------------------------------------------------------------------------------------------
+constexpr int TRI_CHUNK = 128;
+constexpr int NB_MAX = 24;
+
+struct TripleArgs {
+  int nb;          // bins
+  int npair;
+  int a1, a2;      // field index base of A1 (and A2, -1 if none) families in R
+  int bb, cb;      // field index base of B and C families
+  int ng;          // G fields (0..2) at index gbase
+  int gbase;
+  int nslots;      // per-pair double slots = nb * (a2 >= 0 ? 2 : 1) + ng
+  int64_t ncell;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_triple(const T* __restrict__ R, const TripleArgs A, const int* __restrict__ pair_ij, double* __restrict__ part) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nb = A.nb;
+  // cell-major staging: for each cell, [A1(nb) | A2(nb) | G(ng)] then B and C families
+  const int stride = 3 * NB_MAX + 2 + 1;
+  T* cells = reinterpret_cast<T*>(smem_raw);
+  double* dacc = reinterpret_cast<double*>(cells + (size_t)TRI_CHUNK * stride);  // [nslots][blockDim]
+  const int tid = threadIdx.x;
+  const bool live = tid < A.npair;
+  const int pij = live ? pair_ij[tid] : 0;
+  const int pi = pij & 0xffff, pj = pij >> 16;
+  for (int s = 0; s < A.nslots; ++s) dacc[(size_t)s * blockDim.x + tid] = 0.0;
+  const int64_t per = (A.ncell + gridDim.x - 1) / gridDim.x;
+  const int64_t beg = (int64_t)blockIdx.x * per;
+  const int64_t end = min(A.ncell, beg + per);
+  const bool same_bc = A.bb == A.cb;
+  for (int64_t c0 = beg; c0 < end; c0 += TRI_CHUNK) {
+    const int nc = (int)min<int64_t>(TRI_CHUNK, end - c0);
+    __syncthreads();
+    // stage: slots 0..nb-1 A1, nb..2nb-1 A2, 2nb..2nb+ng-1 G, then B (and C if different)
+    const int nA = nb * (A.a2 >= 0 ? 2 : 1);
+    const int nload = nA + A.ng + nb + (same_bc ? 0 : nb);
+    for (int idx = tid; idx < nload * TRI_CHUNK; idx += blockDim.x) {
+      const int f = idx / TRI_CHUNK, c = idx % TRI_CHUNK;
+      int src;
+      if (f < nb) src = A.a1 + f;
+      else if (f < nA) src = A.a2 + (f - nb);
+      else if (f < nA + A.ng) src = A.gbase + (f - nA);
+      else if (f < nA + A.ng + nb) src = A.bb + (f - nA - A.ng);
+      else src = A.cb + (f - nA - A.ng - nb);
+      cells[(size_t)c * stride + f] = c < nc ? R[(size_t)src * A.ncell + c0 + c] : T(0);
+    }
+    __syncthreads();
+    T s1[NB_MAX], s2[NB_MAX], sg[2];
+#pragma unroll
+    for (int k = 0; k < NB_MAX; ++k) { s1[k] = T(0); s2[k] = T(0); }
+    sg[0] = sg[1] = T(0);
+    const int ob = nA + A.ng;            // B family offset in a cell row
+    const int oc = same_bc ? ob : ob + nb;
+    for (int c = 0; c < nc; ++c) {
+      const T* row = cells + (size_t)c * stride;
+      const T bj = row[ob + pj];
+      const T p1 = row[pi] * bj;
+      const T p2 = A.a2 >= 0 ? row[nb + pi] * bj : T(0);
+#pragma unroll
+      for (int k = 0; k < NB_MAX; ++k) {
+        if (k < nb) {
+          const T ck = row[oc + k];
+          s1[k] += p1 * ck;
+          s2[k] += p2 * ck;
+        }
+      }
+      if (A.ng > 0) sg[0] += p1 * row[nA];
+      if (A.ng > 1) sg[1] += p1 * row[nA + 1];
+    }
+    if (live) {
+      double* d = dacc + tid;
+#pragma unroll
+      for (int k = 0; k < NB_MAX; ++k)
+        if (k < nb) d[(size_t)k * blockDim.x] += (double)s1[k];
+      if (A.a2 >= 0) {
+#pragma unroll
+        for (int k = 0; k < NB_MAX; ++k)
+          if (k < nb) d[(size_t)(nb + k) * blockDim.x] += (double)s2[k];
+      }
+      for (int l = 0; l < A.ng; ++l) d[(size_t)(nA + l) * blockDim.x] += (double)sg[l];
+    }
+  }
+  __syncthreads();
+  if (live)
+    for (int s = 0; s < A.nslots; ++s)
+      part[((size_t)blockIdx.x * A.npair + tid) * A.nslots + s] = dacc[(size_t)s * blockDim.x + tid];
+}
+
+// ------------------------------------------------------------------------------------------
+// 6. normalisation and analytic shot noise (one thread per triangle / pair)
+// ------------------------------------------------------------------------------------------
+__device__ double g_ell_dev(int l, double t) {
+  // closed forms of g_l(t) for l = 0, 2 (Appendix H, Eqs. g0, g2)
+  if (l == 0) return 1.0;
+  if (t == 0.0) return 0.0;
+  if (t == 1.0) return 0.25;
+  const double lg = log((t + 1.0) / fabs(t - 1.0));
+  return (2.0 * t * (5.0 * t * t - 3.0) + 3.0 * (t * t - 1.0) * (t * t - 1.0) * lg) / (16.0 * t * t * t);
+}
+
+struct FinalArgs {
+  int nb, ntri, npair, nq;
+  int nscoc, scoc_l[2];
+  int ntripo, tripo_l[2];
+  int shot;
+  int nparts;           // CTAs of the triple kernel
+  int slots_main;       // slots per pair in the data launch
+  int slots_nt;         // slots per pair in the indicator launch
+  int64_t ncell;
+  double kmin, dk;
+  int part_nw_cross;    // partial records of the cross-spectrum kernel
+};
+
+__global__ void k_bispec_finalize(const int* __restrict__ tri, const int* __restrict__ pair_ij,
+                                  const double* __restrict__ part_main, const double* __restrict__ nt_sums,
+                                  const double* __restrict__ cross_m, const double* __restrict__ cross_q,
+                                  const FinalArgs F, const double* __restrict__ sc, double* __restrict__ out) {
+  const int nb = F.nb;
+  const double i33 = sc[SC_I33], s3 = sc[SC_S3];
+  // layout offsets
+  const size_t oB = 0, oSB = (size_t)F.nscoc * F.ntri, oNT = 2 * (size_t)F.nscoc * F.ntri;
+  const size_t oBB = oNT + F.ntri, oSBB = oBB + (size_t)F.ntripo * F.npair;
+  const size_t oNM = oSBB + (size_t)F.ntripo * F.npair, oSC = oNM + nb;
+  auto cross = [&](const double* cr, int b, int s) { return cr[(size_t)b * NCROSS + s]; };
+  auto centre = [&](int b) { return F.kmin + (b + 0.5) * F.dk; };
+  // H_l(k) = <Re X N*> L_l - S3 <L_l> on the k-bins (l = 0, 2); Q_l on the k3 shells (same form)
+  auto Hm = [&](int l, int b) {
+    const double n = cross(cross_m, b, 2);
+    if (n <= 0) return 0.0;
+    return l == 0 ? (cross(cross_m, b, 0) - s3 * n) / n : (cross(cross_m, b, 1) - s3 * cross(cross_m, b, 3)) / n;
+  };
+  auto Hq = [&](int l, int b) {
+    const double n = cross(cross_q, b, 2);
+    if (n <= 0) return 0.0;
+    return l == 0 ? (cross(cross_q, b, 0) - s3 * n) / n : (cross(cross_q, b, 1) - s3 * cross(cross_q, b, 3)) / n;
+  };
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nthreads = gridDim.x * blockDim.x;
+  for (int t = tid; t < F.ntri; t += nthreads) {
+    const int i = tri[3 * t], j = tri[3 * t + 1], k = tri[3 * t + 2];
+    // locate the pair (i, j)
+    int p = 0;
+    for (int a = 0; a < i; ++a) p += nb - a;
+    p += j - i;
+    double s0 = 0, s2 = 0, snt = 0;
+    for (int c = 0; c < F.nparts; ++c) {
+      const double* rec = part_main + ((size_t)c * F.npair + p) * F.slots_main;
+      s0 += rec[k];
+      if (F.slots_main >= 2 * nb) s2 += rec[nb + k];
+    }
+    snt = nt_sums[(size_t)p * nb + k];
+    out[oNT + t] = snt / (double)F.ncell;
+    const double ci = centre(i), cj = centre(j), ck = centre(k);
+    const double c12 = (ck * ck - ci * ci - cj * cj) / (2.0 * ci * cj);
+    const double c13 = (cj * cj - ci * ci - ck * ck) / (2.0 * ci * ck);
+    for (int e = 0; e < F.nscoc; ++e) {
+      const int l = F.scoc_l[e];
+      const double raw = snt > 0 ? (2 * l + 1) * (l == 0 ? s0 : s2) / (i33 * snt) : 0.0;
+      double sn = 0.0;
+      if (F.shot && snt > 0) {
+        const double L12 = l == 0 ? 1.0 : 1.5 * c12 * c12 - 0.5;
+        const double L13 = l == 0 ? 1.0 : 1.5 * c13 * c13 - 0.5;
+        sn = (2 * l + 1) / i33 * ((l == 0 ? s3 : 0.0) + Hm(l, i) + L12 * Hm(l, j) + L13 * Hm(l, k));
+      }
+      out[oB + (size_t)e * F.ntri + t] = raw - sn;
+      out[oSB + (size_t)e * F.ntri + t] = sn;
+    }
+  }
+  for (int p = tid; p < F.npair; p += nthreads) {
+    const int i = pair_ij[p] & 0xffff, j = pair_ij[p] >> 16;
+    const double ni = cross(cross_m, i, 2), nj = cross(cross_m, j, 2);
+    for (int e = 0; e < F.ntripo; ++e) {
+      const int l = F.tripo_l[e];
+      double sg = 0;
+      for (int c = 0; c < F.nparts; ++c) sg += part_main[((size_t)c * F.npair + p) * F.slots_main + F.slots_main - F.ntripo + e];
+      const double raw = (ni > 0 && nj > 0) ? (2 * l + 1) * sg / (i33 * ni * nj * (double)F.ncell) : 0.0;
+      double sn = 0.0;
+      if (F.shot && ni > 0 && nj > 0) {
+        const double ci = centre(i), cj = centre(j);
+        const double sgn = (l % 2) ? -1.0 : 1.0;
+        double v = (l == 0 ? s3 : 0.0);
+        v += sgn * g_ell_dev(l, ci / cj) * Hm(l, i);
+        v += sgn * g_ell_dev(l, cj / ci) * Hm(l, j);
+        const double lo = fabs(ci - cj) + 0.5 * F.dk, hi = ci + cj - 0.5 * F.dk;
+        double num = 0, den = 0;
+        for (int m = 0; m < F.nq; ++m) {
+          const double cm = (m + 0.5) * F.dk;
+          const double nm = cross(cross_q, m, 2);
+          if (cm >= lo - 1e-9 * F.dk && cm <= hi + 1e-9 * F.dk && nm > 0) {
+            num += nm / cm * Hq(l, m);
+            den += nm / cm;
+          }
+        }
+        if (den > 0) v += num / den;
+        sn = (2 * l + 1) / i33 * v;
+      }
+      out[oBB + (size_t)e * F.npair + p] = raw - sn;
+      out[oSBB + (size_t)e * F.npair + p] = sn;
+    }
+  }
+  for (int b = tid; b < nb; b += nthreads) out[oNM + b] = cross(cross_m, b, 2);
+  if (tid < 8) out[oSC + tid] = sc[tid];
+}
+
+// reduce per-warp cross partials into [bin][NCROSS] in a fixed order
+__global__ void k_cross_reduce(const double* __restrict__ part, int nrec, int nb, double* __restrict__ out) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nb * NCROSS; e += gridDim.x * blockDim.x) {
+    double s = 0;
+    for (int r = 0; r < nrec; ++r) s += part[(size_t)r * nb * NCROSS + e];
+    out[e] = s;
+  }
+}
+
+// reduce the indicator-triple partials over CTAs: nt[p][k]
+__global__ void k_nt_reduce(const double* __restrict__ part, int nparts, int npair, int nslots, int nb,
+                            double* __restrict__ nt) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < npair * nb; e += gridDim.x * blockDim.x) {
+    const int p = e / nb, k = e % nb;
+    double s = 0;
+    for (int c = 0; c < nparts; ++c) s += part[((size_t)c * npair + p) * nslots + k];
+    nt[e] = s;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// host helpers
+// ------------------------------------------------------------------------------------------
+struct Tri {
+  std::vector<int> tri;   // [ntri][3]
+  std::vector<int> pij;   // pair (i | j << 16), lexicographic i <= j
+};
+
+// centre closure rule c_k <= c_i + c_j, float64 with a relative slack of 1e-9 dk (the same
+// expression as the test oracle; host code is compiled without floating-point contraction)
+Tri make_triangles(const npc_kbins& kb) {
+  Tri T;
+  const int nb = kb.nbins;
+  std::vector<double> c(nb);
+  for (int b = 0; b < nb; ++b) c[b] = kb.kmin + (b + 0.5) * kb.dk;
+  for (int i = 0; i < nb; ++i)
+    for (int j = i; j < nb; ++j) {
+      T.pij.push_back(i | (j << 16));
+      for (int k = j; k < nb; ++k)
+        if (c[k] <= c[i] + c[j] + 1e-9 * kb.dk) {
+          T.tri.push_back(i);
+          T.tri.push_back(j);
+          T.tri.push_back(k);
+        }
+    }
+  return T;
+}
+
+template <typename T, int N>
+npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb, int scoc_mask, int tripo_mask,
+                       int shot, const DevCatalog& d, double* sc, double* dev_out, int64_t out_len) {
+  using C = cplx<T>;
+  const double kf = 2.0 * M_PI / m.box;
+  const double kmax = kb.kmin + kb.nbins * kb.dk;
+  const int nb = kb.nbins;
+  const int K = (int)std::ceil(kmax / kf) + 1;            // shells
+  const int K2 = std::min((int)std::ceil(2.0 * kmax / kf) + 2, N / 2 - 1);  // G fields, k3 shells
+  const int nq = (int)std::ceil(2.0 * kmax / kb.dk) + 1;
+  const int n2cap = (int)std::floor(std::pow(2.0 * kmax / kf, 2)) + 1;
+  const int KZ = K2 + 1;
+  const int nphase = m.interlace ? 2 : 1;
+  const Geom geo = [&] {
+    Geom g{};
+    g.n = N;
+    g.h = m.box / N;
+    for (int a = 0; a < 3; ++a) g.o[a] = m.origin[a];
+    g.global_los = 1;
+    return g;
+  }();
+  double l3[3] = {m.los_dir[0], m.los_dir[1], m.los_dir[2]};
+  const double ll = std::sqrt(l3[0] * l3[0] + l3[1] * l3[1] + l3[2] * l3[2]);
+  for (double& v : l3) v /= ll;
+
+  // 1. paint + forward transforms of F and N fields
+  const size_t rs = sizeof(T);
+  const size_t ncell = (size_t)N * N * N;
+  void *ma, *mb = nullptr, *half;
+  NPC_TRY(ws_get(ctx, "mesh.a", rs * ncell, &ma));
+  if (nphase == 2) NPC_TRY(ws_get(ctx, "mesh.b", rs * ncell, &mb));
+  PowerPlan plan{};
+  plan.n = N;
+  plan.nphase = nphase;
+  plan.global_los = 1;
+  plan.assign = m.assign;
+  plan.kz_keep = KZ;
+  plan.fl.nf = 0;
+  for (int ph = 0; ph < nphase; ++ph) {
+    Comp c;
+    c.phase = (int8_t)ph; c.ell = 0; c.m = 0; c.part = PART_ONE;
+    plan.fl.f[plan.fl.nf++] = c;
+  }
+  const int prec = sizeof(T) == 8 ? NPC_PREC_FP64 : NPC_PREC_MIXED;
+  const size_t halfbytes = sizeof(C) * (size_t)nphase * KZ * N * N;
+  NPC_TRY(ws_get(ctx, "half", 2 * halfbytes, &half));
+  C* halfF = (C*)half;
+  C* halfN = (C*)((char*)half + halfbytes);
+  NPC_TRY(stage_mark(ctx, "alloc"));
+  NPC_TRY(launch_paint(ctx, d, nullptr, m, 1, prec, sc, ma, mb));
+  NPC_TRY(stage_mark(ctx, "paint_fold"));
+  NPC_TRY(run_forward_transforms(ctx, prec, plan, geo, ma, mb, halfF));
+  if (shot) {
+    NPC_TRY(launch_paint(ctx, d, nullptr, m, 2, prec, sc, ma, mb));
+    NPC_TRY(run_forward_transforms(ctx, prec, plan, geo, ma, mb, halfN));
+  }
+  NPC_TRY(stage_mark(ctx, "forward_yz"));
+
+  const void* twf;
+  NPC_TRY(get_twiddles(ctx, N, prec, &twf));
+  const C* tw = (const C*)twf;
+  // 2. x pass + combine into X0 (and XN)
+  C* X;
+  const int nout = shot ? 2 : 1;
+  const size_t xfs = (size_t)KZ * N * N;
+  NPC_TRY(ws_get(ctx, "bis.X", sizeof(C) * xfs * nout, (void**)&X));
+  {
+    constexpr int TPF = N / 8;
+    constexpr int G = BT / TPF > 0 ? BT / TPF : 1;
+    const int nf = nphase * nout;
+    // F and N halves are separate buffers: combine each
+    for (int o = 0; o < nout; ++o) {
+      const size_t smem = sizeof(C) * (2 * N + (size_t)(nphase + G) * row_pad_len<N>()) + sizeof(T) * (N / 2 + 2);
+      auto kern = k_fft_x_combine<T, N>;
+      NPC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      const int nrows = KZ * (2 * K2 + 1);
+      const int grid = std::min(nrows, ctx->num_sms * 4);
+      kern<<<grid, BT, smem, ctx->stream>>>(o == 0 ? halfF : halfN, 1, nphase, KZ, K2, m.assign, tw, X + (size_t)o * xfs);
+      NPC_LAUNCH(ctx);
+    }
+    (void)nf;
+  }
+  NPC_TRY(stage_mark(ctx, "forward_x_combine"));
+
+  // 3. shell sums for the shot noise
+  const int16_t *tab_m, *tab_q;
+  NPC_TRY(get_bin_table(ctx, N, m.box, kb, &tab_m, 0));
+  npc_kbins qb{0.0, kb.dk, nq};
+  NPC_TRY(get_bin_table(ctx, N, m.box, qb, &tab_q, 1));
+  double *cross_m, *cross_q;
+  NPC_TRY(ws_get(ctx, "bis.cross", sizeof(double) * NCROSS * (nb + nq), (void**)&cross_m));
+  cross_q = cross_m + (size_t)NCROSS * nb;
+  {
+    const int nrows = (K2 + 1) * (2 * K2 + 1);
+    const int grid = std::min(nrows, ctx->num_sms * 2);
+    const int nw = BT / 32;
+    double* part;
+    const size_t np = (size_t)grid * nw;
+    NPC_TRY(ws_get(ctx, "bis.crosspart", sizeof(double) * np * NCROSS * (nb + nq), (void**)&part));
+    NPC_CUDA(ctx, cudaMemsetAsync(part, 0, sizeof(double) * np * NCROSS * (nb + nq), ctx->stream));
+    const C* XN = shot ? X + xfs : X;
+    k_bin_cross<T, N><<<grid, BT, 0, ctx->stream>>>(X, XN, KZ, K2, l3[0], l3[1], l3[2], tab_m, nb, tab_q, nq, n2cap,
+                                                   part, part + np * NCROSS * nb);
+    NPC_LAUNCH(ctx);
+    k_cross_reduce<<<(nb * NCROSS + 127) / 128, 128, 0, ctx->stream>>>(part, (int)np, nb, cross_m);
+    NPC_LAUNCH(ctx);
+    k_cross_reduce<<<(nq * NCROSS + 127) / 128, 128, 0, ctx->stream>>>(part + np * NCROSS * nb, (int)np, nq, cross_q);
+    NPC_LAUNCH(ctx);
+  }
+  NPC_TRY(stage_mark(ctx, "shot_shells"));
+
+  // 4. shell fields
+  const bool want2 = (scoc_mask & 4) != 0;
+  const bool wantG0 = (tripo_mask & 1) != 0, wantG2 = (tripo_mask & 4) != 0;
+  // triangle-count cache keyed by geometry and bins
+  std::vector<char> ntkey(sizeof(int) + 3 * sizeof(double));
+  {
+    int n_ = N;
+    double a[3] = {m.box, kb.kmin, kb.dk};
+    std::memcpy(ntkey.data(), &n_, sizeof(int));
+    std::memcpy(ntkey.data() + sizeof(int), a, 3 * sizeof(double));
+    ntkey.push_back((char)nb);
+  }
+  const Tri tr = make_triangles(kb);
+  const int ntri = (int)tr.tri.size() / 3, npair = (int)tr.pij.size();
+  double* nt_sums;
+  NPC_TRY(ws_get(ctx, "bis.ntsums", sizeof(double) * npair * nb, (void**)&nt_sums));
+  auto it = ctx->host_cache_keys.find("bis.ntsums");
+  const bool need_nt = it == ctx->host_cache_keys.end() || it->second != ntkey;
+
+  std::vector<ShellField> fl;
+  auto add = [&](int src, int mult, int bin, int Kf) {
+    ShellField f{};
+    f.src = (int8_t)src; f.mult = (int8_t)mult; f.bin = (int16_t)bin; f.K = Kf;
+    fl.push_back(f);
+  };
+  for (int b = 0; b < nb; ++b) add(0, 0, b, K);                  // F0_b: R index b
+  if (want2) for (int b = 0; b < nb; ++b) add(0, 1, b, K);       // F2_b: R index nb + b
+  const int iF2 = want2 ? nb : -1;
+  const int iI = (int)fl.size();
+  if (need_nt) for (int b = 0; b < nb; ++b) add(1, 0, b, K);     // I_b
+  const int iG = (int)fl.size();
+  int ng = 0;
+  if (wantG0) { add(0, 0, -1, K2); ng++; }
+  if (wantG2) { add(0, 1, -1, K2); ng++; }
+  const int nfield = (int)fl.size();
+  int64_t o1 = 0, o2 = 0;
+  std::vector<int> plane_f, plane_kz;
+  for (int f = 0; f < nfield; ++f) {
+    fl[f].off1 = o1;
+    fl[f].off2 = o2;
+    o1 += (int64_t)(fl[f].K + 1) * (2 * fl[f].K + 1) * N;
+    o2 += (int64_t)(fl[f].K + 1) * N * N;
+    for (int kz = 0; kz <= fl[f].K; ++kz) {
+      plane_f.push_back(f);
+      plane_kz.push_back(kz);
+    }
+  }
+  // pairs for the z pass: consecutive fields with the same K
+  std::vector<int> za, zb;
+  for (int f = 0; f < nfield;) {
+    if (f + 1 < nfield && fl[f + 1].K == fl[f].K) {
+      za.push_back(f);
+      zb.push_back(f + 1);
+      f += 2;
+    } else {
+      za.push_back(f);
+      zb.push_back(-1);
+      f += 1;
+    }
+  }
+  const int nzp = (int)za.size();
+  // device tables (one upload per call; small)
+  std::vector<char> tables;
+  auto push_bytes = [&](const void* p, size_t n) {
+    const size_t o = tables.size();
+    tables.resize(o + ((n + 15) / 16) * 16);
+    std::memcpy(tables.data() + o, p, n);
+    return o;
+  };
+  const size_t t_fields = push_bytes(fl.data(), sizeof(ShellField) * nfield);
+  const size_t t_pf = push_bytes(plane_f.data(), sizeof(int) * plane_f.size());
+  const size_t t_pk = push_bytes(plane_kz.data(), sizeof(int) * plane_kz.size());
+  const size_t t_za = push_bytes(za.data(), sizeof(int) * nzp);
+  const size_t t_zb = push_bytes(zb.data(), sizeof(int) * nzp);
+  const size_t t_oa = push_bytes(za.data(), sizeof(int) * nzp);  // R index = field index
+  const size_t t_ob = push_bytes(zb.data(), sizeof(int) * nzp);
+  const size_t t_tri = push_bytes(tr.tri.data(), sizeof(int) * tr.tri.size());
+  const size_t t_pij = push_bytes(tr.pij.data(), sizeof(int) * tr.pij.size());
+  char* dtab;
+  NPC_TRY(ws_get(ctx, "bis.tables", tables.size(), (void**)&dtab));
+  NPC_CUDA(ctx, cudaMemcpyAsync(dtab, tables.data(), tables.size(), cudaMemcpyHostToDevice, ctx->stream));
+  const ShellField* dfields = (const ShellField*)(dtab + t_fields);
+  C *T1, *T2;
+  T* R;
+  NPC_TRY(ws_get(ctx, "bis.T1", sizeof(C) * std::max<int64_t>(o1, 1), (void**)&T1));
+  NPC_TRY(ws_get(ctx, "bis.T2", sizeof(C) * std::max<int64_t>(o2, 1), (void**)&T2));
+  NPC_TRY(ws_get(ctx, "bis.R", sizeof(T) * ncell * nfield, (void**)&R));
+  const int16_t* tab_shell;
+  NPC_TRY(get_bin_table(ctx, N, m.box, kb, &tab_shell, 0));
+  {
+    constexpr int TPF = N / 8;
+    constexpr int G = BT / TPF > 0 ? BT / TPF : 1;
+    const size_t smem = sizeof(C) * (2 * N + (size_t)G * row_pad_len<N>()) + sizeof(T) * N + sizeof(int) * 2 * N;
+    auto kern = k_shell_x<T, N>;
+    NPC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int Kmax = std::max(K, ng ? K2 : 0);
+    const int nrows = (Kmax + 1) * (2 * Kmax + 1);
+    kern<<<std::min(nrows, ctx->num_sms * 4), BT, smem, ctx->stream>>>(X, KZ, dfields, nfield, Kmax, tab_shell, n2cap,
+                                                                     l3[0], l3[1], l3[2], tw, T1);
+    NPC_LAUNCH(ctx);
+  }
+  {
+    constexpr int TX = BCol<N>::TX;
+    const size_t smem = sizeof(C) * (N + (size_t)N * TX);
+    auto ky = k_shell_y<T, N>;
+    NPC_CUDA(ctx, cudaFuncSetAttribute(ky, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int npl = (int)plane_f.size();
+    for (int p0 = 0; p0 < npl; p0 += 65535) {
+      const int np_ = std::min(65535, npl - p0);
+      ky<<<dim3(N / TX, np_), BCol<N>::THREADS, smem, ctx->stream>>>(
+          T1, dfields, (const int*)(dtab + t_pf) + p0, (const int*)(dtab + t_pk) + p0, tw, T2);
+      NPC_LAUNCH(ctx);
+    }
+    auto kz = k_shell_z<T, N>;
+    NPC_CUDA(ctx, cudaFuncSetAttribute(kz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kz<<<dim3(N / TX, N, nzp), BCol<N>::THREADS, smem, ctx->stream>>>(
+        T2, dfields, (const int*)(dtab + t_za), (const int*)(dtab + t_zb), (const int*)(dtab + t_oa),
+        (const int*)(dtab + t_ob), tw, R);
+    NPC_LAUNCH(ctx);
+  }
+  NPC_TRY(stage_mark(ctx, "shell_fields"));
+
+  // 5. triple products
+  const int grid = ctx->num_sms * 2;
+  const int tthreads = ((npair + 31) / 32) * 32;
+  if (npair > 1024 || nb > NB_MAX) return set_err(ctx, NPC_ERR_UNSUPPORTED, "at most %d bins", NB_MAX);
+  double* part;
+  TripleArgs ta{};
+  ta.nb = nb;
+  ta.npair = npair;
+  ta.a1 = 0;
+  ta.a2 = want2 ? iF2 : -1;
+  ta.bb = 0;
+  ta.cb = 0;
+  ta.ng = ng;
+  ta.gbase = iG;
+  ta.nslots = nb * (want2 ? 2 : 1) + ng;
+  ta.ncell = (int64_t)ncell;
+  const int stride = 3 * NB_MAX + 2 + 1;
+  const size_t smem_t = sizeof(T) * (size_t)TRI_CHUNK * stride + sizeof(double) * (size_t)(2 * NB_MAX + 2) * tthreads;
+  NPC_TRY(ws_get(ctx, "bis.tripart", sizeof(double) * (size_t)grid * npair * (2 * NB_MAX + 2), (void**)&part));
+  auto kt = k_triple<T>;
+  NPC_CUDA(ctx, cudaFuncSetAttribute(kt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t));
+  if (need_nt) {
+    TripleArgs tn = ta;
+    tn.a1 = iI;
+    tn.a2 = -1;
+    tn.bb = iI;
+    tn.cb = iI;
+    tn.ng = 0;
+    tn.nslots = nb;
+    kt<<<grid, tthreads, smem_t, ctx->stream>>>(R, tn, (const int*)(dtab + t_pij), part);
+    NPC_LAUNCH(ctx);
+    k_nt_reduce<<<(npair * nb + 127) / 128, 128, 0, ctx->stream>>>(part, grid, npair, nb, nb, nt_sums);
+    NPC_LAUNCH(ctx);
+    ctx->host_cache_keys["bis.ntsums"] = ntkey;
+  }
+  kt<<<grid, tthreads, smem_t, ctx->stream>>>(R, ta, (const int*)(dtab + t_pij), part);
+  NPC_LAUNCH(ctx);
+  NPC_TRY(stage_mark(ctx, "triple"));
+
+  // 6. finalize
+  FinalArgs fa{};
+  fa.nb = nb;
+  fa.ntri = ntri;
+  fa.npair = npair;
+  fa.nq = nq;
+  fa.nscoc = 0;
+  for (int l = 0; l <= 2; l += 2)
+    if (scoc_mask & (1 << l)) fa.scoc_l[fa.nscoc++] = l;
+  fa.ntripo = 0;
+  for (int l = 0; l <= 2; l += 2)
+    if (tripo_mask & (1 << l)) fa.tripo_l[fa.ntripo++] = l;
+  fa.shot = shot;
+  fa.nparts = grid;
+  fa.slots_main = ta.nslots;
+  fa.ncell = (int64_t)ncell;
+  fa.kmin = kb.kmin;
+  fa.dk = kb.dk;
+  k_bispec_finalize<<<std::max(1, (std::max(ntri, npair) + 127) / 128), 128, 0, ctx->stream>>>(
+      (const int*)(dtab + t_tri), (const int*)(dtab + t_pij), part, nt_sums, cross_m, cross_q, fa, sc, dev_out);
+  NPC_LAUNCH(ctx);
+  NPC_TRY(stage_mark(ctx, "finalize"));
+  (void)out_len;
+  return NPC_OK;
+}
+
+template <typename T>
+npc_status bispec_dispatch(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb, int sm, int tm, int shot,
+                           const DevCatalog& d, double* sc, double* out, int64_t len) {
+  switch (m.n) {
+    case 16: return bispec_impl<T, 16>(ctx, m, kb, sm, tm, shot, d, sc, out, len);
+    case 32: return bispec_impl<T, 32>(ctx, m, kb, sm, tm, shot, d, sc, out, len);
+    case 64: return bispec_impl<T, 64>(ctx, m, kb, sm, tm, shot, d, sc, out, len);
+    case 128: return bispec_impl<T, 128>(ctx, m, kb, sm, tm, shot, d, sc, out, len);
+    case 256: return bispec_impl<T, 256>(ctx, m, kb, sm, tm, shot, d, sc, out, len);
+  }
+  if constexpr (sizeof(T) == 4) {
+    if (m.n == 512) return bispec_impl<T, 512>(ctx, m, kb, sm, tm, shot, d, sc, out, len);
+  }
+  return set_err(ctx, NPC_ERR_UNSUPPORTED, "bispectrum mesh size %d not supported at this precision", m.n);
+}
+
+}  // namespace
+
+npc_status run_bispectrum(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb, int scoc_mask, int tripo_mask,
+                          int shot, int prec, const DevCatalog& d, double* sc, double* out, int64_t len) {
+  if (prec == NPC_PREC_FP64) return bispec_dispatch<double>(ctx, m, kb, scoc_mask, tripo_mask, shot, d, sc, out, len);
+  return bispec_dispatch<float>(ctx, m, kb, scoc_mask, tripo_mask, shot, d, sc, out, len);
+}
+
+int64_t bispec_counts(const npc_kbins& kb, int64_t* ntri, int64_t* npair) {
+  const Tri t = make_triangles(kb);
+  *ntri = (int64_t)t.tri.size() / 3;
+  *npair = (int64_t)t.pij.size();
+  return 0;
+}
+
+npc_status bispec_triangles(const npc_kbins& kb, int32_t* tri, int64_t cap, int64_t* ntri) {
+  const Tri t = make_triangles(kb);
+  *ntri = (int64_t)t.tri.size() / 3;
+  if (tri) {
+    if (cap < *ntri) return NPC_ERR_INVALID_ARG;
+    for (size_t i = 0; i < t.tri.size(); ++i) tri[i] = t.tri[i];
+  }
+  return NPC_OK;
 }

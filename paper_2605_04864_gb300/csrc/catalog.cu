@@ -18,7 +18,7 @@
 namespace {
 
 constexpr int RED_THREADS = 256;
-constexpr int RED_BLOCKS = 256;
+constexpr int RED_BLOCKS = 1024;
 constexpr int NSUM = 6;  // sum w, w^2, w^3, nbar w^2, nbar^2 w^3, max |w|
 
 template <typename T>
@@ -120,9 +120,29 @@ __global__ void k_brick_count(const P* __restrict__ pos, int64_t n, PaintGeo g, 
     bool ok = true;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const double s = ((double)pos[3 * i + a] - g.o[a]) * g.inv_h;
-      if (!(fabs(s) < 1e15)) { ok = false; bidx[a] = 0; continue; }
-      const long long f = (long long)floor(s);
+      // floor(s) decided in float when s is farther from an integer than a bound on the float
+      // rounding error (three roundings of relative size 2^-24 on |x| n/box, |origin| n/box and
+      // |s|, with a factor 8 of margin), otherwise in float64 exactly as everywhere else
+      const P pa = pos[3 * i + a];
+      long long f;
+      if (sizeof(P) == 4) {
+        const float ih = (float)g.inv_h;
+        const float sf = ((float)pa - (float)g.o[a]) * ih;
+        const float ff = floorf(sf);
+        const float fr = sf - ff;
+        const float tol = 1.0e-6f * ((fabsf((float)pa) + fabsf((float)g.o[a])) * ih + fabsf(sf)) + 1.0e-6f;
+        if (fabsf(sf) < 1.0e6f && fr > tol && fr < 1.0f - tol) {
+          f = (long long)ff;
+        } else {
+          const double s = ((double)pa - g.o[a]) * g.inv_h;
+          if (!(fabs(s) < 1e15)) { ok = false; bidx[a] = 0; continue; }
+          f = (long long)floor(s);
+        }
+      } else {
+        const double s = ((double)pa - g.o[a]) * g.inv_h;
+        if (!(fabs(s) < 1e15)) { ok = false; bidx[a] = 0; continue; }
+        f = (long long)floor(s);
+      }
       bidx[a] = (int)(wrapi(f, g.n) / g.bs);
     }
     if (!ok) { brick[i] = -1; rank[i] = 0; continue; }
@@ -158,12 +178,36 @@ template <typename R> struct RecOf;
 template <> struct RecOf<float> { using type = float4; };
 template <> struct RecOf<double> { using type = double4_32a; };
 
+// Per particle, per axis: the float64 decisions of the oracle are taken here once and stored as
+//   meta bits 8a..8a+4: base cell floor(s) relative to its brick (< 16)
+//   meta bits 8a+5   : phase-a tap centre minus base (TSC floor(s+1/2) - floor(s); CIC 0)
+//   meta bits 8a+6..7: phase-b tap centre minus base (TSC floor((s+1/2)+1/2) - floor(s);
+//                      CIC floor(s+1/2) - floor(s))
+// and the record keeps frac = s - floor(s) (exact in float64, rounded once to R) and the weight.
+template <int ASSIGN>
+__device__ __forceinline__ uint32_t axis_meta(double s, int n, int bs, double* frac) {
+  const double f = floor(s);
+  const long long fb = (long long)f;
+  const double sb = s + 0.5;
+  long long ia, ib;
+  if (ASSIGN == 2) {
+    ia = fb;
+    ib = (long long)floor(sb);
+  } else {
+    ia = (long long)floor(s + 0.5);
+    ib = (long long)floor(sb + 0.5);
+  }
+  *frac = s - f;
+  const uint32_t local = (uint32_t)(wrapi(fb, n) % bs);
+  return local | ((uint32_t)(ia - fb) << 5) | ((uint32_t)(ib - fb) << 6);
+}
+
 // coefficient * w^power per particle; coef_kind: 0 -> 1, 1 -> -alpha, 2 -> +alpha^2
-template <typename P, typename R>
+template <int ASSIGN, typename P, typename R>
 __global__ void k_scatter(const P* __restrict__ pos, const P* __restrict__ w, int64_t n, int power,
-                          int coef_kind, const double* __restrict__ sc, const int* __restrict__ brick,
+                          int coef_kind, const double* __restrict__ sc, PaintGeo g, const int* __restrict__ brick,
                           const int* __restrict__ rank, const int* __restrict__ start,
-                          typename RecOf<R>::type* __restrict__ rec) {
+                          typename RecOf<R>::type* __restrict__ rec, uint32_t* __restrict__ meta) {
   double coef = 1.0;
   if (coef_kind == 1) coef = -sc[SC_ALPHA];
   if (coef_kind == 2) coef = sc[SC_ALPHA] * sc[SC_ALPHA];
@@ -173,28 +217,37 @@ __global__ void k_scatter(const P* __restrict__ pos, const P* __restrict__ w, in
     if (b < 0) continue;
     const double wi = w ? (double)w[i] : 1.0;
     const double wc = coef * (power == 2 ? wi * wi : wi);
+    double fr[3];
+    uint32_t m = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double s = ((double)pos[3 * i + a] - g.o[a]) * g.inv_h;
+      m |= axis_meta<ASSIGN>(s, g.n, g.bs, &fr[a]) << (8 * a);
+    }
     typename RecOf<R>::type r;
-    r.x = (R)pos[3 * i];
-    r.y = (R)pos[3 * i + 1];
-    r.z = (R)pos[3 * i + 2];
+    r.x = (R)fr[0];
+    r.y = (R)fr[1];
+    r.z = (R)fr[2];
     r.w = (R)wc;
-    rec[start[b] + rank[i]] = r;
+    const int dst = start[b] + rank[i];
+    rec[dst] = r;
+    meta[dst] = m;
   }
 }
 
-// Per-axis taps: up to 3 (TSC) or 2 (CIC) cells relative to the tile, with weights.
+// Per-axis taps of one phase: up to 3 (TSC) or 2 (CIC) tile cells with weights, from the
+// stored fraction and decision bits.
 template <int ASSIGN, typename T>
-__device__ __forceinline__ void axis_taps(double s, long long fbase, int tile0, int* idx, T* wt) {
+__device__ __forceinline__ void axis_taps(T frac, uint32_t m8, int phase, int* idx, T* wt) {
+  const int local = (int)(m8 & 31u);
+  const int off = phase ? (int)((m8 >> 6) & 3u) : (int)((m8 >> 5) & 1u);
+  // d = s - centre (phase a) or (s + 1/2) - centre (phase b)
+  const T d = frac + (phase ? T(0.5) : T(0)) - T(off);
+  const int rel = local + off + 1;   // tile index of the centre (tile starts one cell below the brick)
   if (ASSIGN == 2) {
-    const double i0 = floor(s);
-    const T d = (T)(s - i0);
-    const int rel = (int)((long long)i0 - fbase) + tile0;
     idx[0] = rel; wt[0] = T(1) - d;
     idx[1] = rel + 1; wt[1] = d;
   } else {
-    const double i0 = floor(s + 0.5);
-    const T d = (T)(s - i0);
-    const int rel = (int)((long long)i0 - fbase) + tile0;
     const T a = T(0.5) - d, b = T(0.5) + d;
     idx[0] = rel - 1; wt[0] = T(0.5) * a * a;
     idx[1] = rel; wt[1] = T(0.75) - d * d;
@@ -202,109 +255,120 @@ __device__ __forceinline__ void axis_taps(double s, long long fbase, int tile0, 
   }
 }
 
+// Round to the nearest 64-bit integer (ties to even).  The float path splits |v| < 2^62 into
+// 2^32 * hi + lo with both parts exact in float and converts them with 32-bit instructions.
+template <typename T> __device__ __forceinline__ long long to_fixed(T v);
+template <> __device__ __forceinline__ long long to_fixed<float>(float v) {
+  const float a = fabsf(v);
+  const float hi = floorf(a * 2.3283064365386963e-10f);  // a / 2^32, exact
+  const float lo = fmaf(hi, -4294967296.0f, a);            // exact, < 2^32
+  const long long q = ((long long)__float2uint_rz(hi) << 32) + (long long)__float2uint_rn(lo);
+  return v < 0.0f ? -q : q;
+}
+template <> __device__ __forceinline__ long long to_fixed<double>(double v) { return __double2ll_rn(v); }
+
+// 64-bit fixed point back to T times 2^-e; the float path uses two 32-bit conversions.
+template <typename T> __device__ __forceinline__ T from_fixed(long long q, T inv);
+template <> __device__ __forceinline__ float from_fixed<float>(long long q, float inv) {
+  const int hi = (int)(q >> 32);
+  const unsigned lo = (unsigned)(q & 0xffffffffull);
+  return fmaf((float)hi, 4294967296.0f, (float)lo) * inv;
+}
+template <> __device__ __forceinline__ double from_fixed<double>(long long q, double inv) { return (double)q * inv; }
+
+// One CTA per (brick, phase): fixed-point accumulation of all taps in a (bs+4)^3 tile.
 template <int ASSIGN, typename R, typename T>
-__global__ void k_paint_brick(const typename RecOf<R>::type* __restrict__ rec, const int* __restrict__ start,
-                              const int* __restrict__ count, PaintGeo g, int nphase, const double* __restrict__ sc,
-                              int maxw_slot, T* __restrict__ tiles) {
+__global__ void __launch_bounds__(512)
+k_paint_brick(const typename RecOf<R>::type* __restrict__ rec, const uint32_t* __restrict__ meta,
+              const int* __restrict__ start, const int* __restrict__ count, PaintGeo g, int nphase,
+              const double* __restrict__ sc, int maxw_slot, T* __restrict__ tiles) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   long long* acc = reinterpret_cast<long long*>(smem_raw);
   const int ts3 = g.ts * g.ts * g.ts;
-  const int b = blockIdx.x;
-  const int bx = b % g.nb, by = (b / g.nb) % g.nb, bz = b / (g.nb * g.nb);
-  for (int i = threadIdx.x; i < nphase * ts3; i += blockDim.x) acc[i] = 0;
+  const int b = blockIdx.x / nphase, ph = blockIdx.x % nphase;
+  for (int i = threadIdx.x; i < ts3; i += blockDim.x) acc[i] = 0;
   const int cnt = count[b];
   // fixed-point scale 2^e with cnt * max|w| * 2^e < 2^61 (no overflow of the tile sums)
   const double bound = (double)cnt * sc[maxw_slot];
   int ex = 0;
   if (bound > 0) frexp(bound, &ex);
   const int e = 61 - ex;
-  const double scale = ldexp(1.0, e);
+  const T scale = (T)ldexp(1.0, e);
   __syncthreads();
   const int beg = start[b];
   constexpr int NT = ASSIGN == 2 ? 2 : 3;
   for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
     const typename RecOf<R>::type r = rec[beg + k];
-    const double p3[3] = {(double)r.x, (double)r.y, (double)r.z};
-    const int borg[3] = {bx * g.bs, by * g.bs, bz * g.bs};
-    double s[3];
-    long long fb[3];
-    int t0[3];
+    const uint32_t m = meta[beg + k];
+    int ix[NT], iy[NT], iz[NT];
+    T wx[NT], wy[NT], wz[NT];
+    axis_taps<ASSIGN, T>((T)r.x, m & 255u, ph, ix, wx);
+    axis_taps<ASSIGN, T>((T)r.y, (m >> 8) & 255u, ph, iy, wy);
+    axis_taps<ASSIGN, T>((T)r.z, (m >> 16) & 255u, ph, iz, wz);
+    const T wgt = (T)r.w * scale;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      s[a] = (p3[a] - g.o[a]) * g.inv_h;
-      fb[a] = (long long)floor(s[a]);
-      t0[a] = (int)(wrapi(fb[a], g.n) - borg[a]) + 1;
-    }
-    const T wgt = (T)r.w;
-    for (int ph = 0; ph < nphase; ++ph) {
-      int ix[NT], iy[NT], iz[NT];
-      T wx[NT], wy[NT], wz[NT];
-      const double sh = ph ? 0.5 : 0.0;
-      axis_taps<ASSIGN, T>(s[0] + sh, fb[0], t0[0], ix, wx);
-      axis_taps<ASSIGN, T>(s[1] + sh, fb[1], t0[1], iy, wy);
-      axis_taps<ASSIGN, T>(s[2] + sh, fb[2], t0[2], iz, wz);
-      long long* a = acc + ph * ts3;
+    for (int c = 0; c < NT; ++c) {
 #pragma unroll
-      for (int c = 0; c < NT; ++c) {
+      for (int bb = 0; bb < NT; ++bb) {
+        const T wzy = wgt * wz[c] * wy[bb];
+        const int rowoff = (iz[c] * g.ts + iy[bb]) * g.ts;
 #pragma unroll
-        for (int bb = 0; bb < NT; ++bb) {
-          const T wzy = wgt * wz[c] * wy[bb];
-          const int rowoff = (iz[c] * g.ts + iy[bb]) * g.ts;
-#pragma unroll
-          for (int aa = 0; aa < NT; ++aa) {
-            const double v = (double)(wzy * wx[aa]);
-            const long long q = __double2ll_rn(v * scale);
-            // taps stay inside the tile by construction; the guard only protects shared memory
-            if ((unsigned)iz[c] < (unsigned)g.ts && (unsigned)iy[bb] < (unsigned)g.ts &&
-                (unsigned)ix[aa] < (unsigned)g.ts)
-              atomicAdd(reinterpret_cast<unsigned long long*>(a + rowoff + ix[aa]),
-                        static_cast<unsigned long long>(q));
-          }
+        for (int aa = 0; aa < NT; ++aa) {
+          const long long q = to_fixed<T>(wzy * wx[aa]);
+          // taps stay inside the tile by construction; the guard only protects shared memory
+          if ((unsigned)iz[c] < (unsigned)g.ts && (unsigned)iy[bb] < (unsigned)g.ts &&
+              (unsigned)ix[aa] < (unsigned)g.ts)
+            atomicAdd(reinterpret_cast<unsigned long long*>(acc + rowoff + ix[aa]),
+                      static_cast<unsigned long long>(q));
         }
       }
     }
   }
   __syncthreads();
-  const double inv = ldexp(1.0, -e);
-  for (int i = threadIdx.x; i < nphase * ts3; i += blockDim.x) {
-    const int ph = i / ts3, j = i % ts3;
-    tiles[((size_t)b * nphase + ph) * ts3 + j] = (T)((double)acc[i] * inv);
-  }
+  const T inv = (T)ldexp(1.0, -e);
+  T* out = tiles + ((size_t)b * nphase + ph) * ts3;
+  for (int i = threadIdx.x; i < ts3; i += blockDim.x) out[i] = from_fixed<T>(acc[i], inv);
 }
 
-template <typename T>
-__global__ void k_fold(const T* __restrict__ tiles, PaintGeo g, int nphase, const double* __restrict__ sc,
-                       int subtract_mean, T* __restrict__ mesh_a, T* __restrict__ mesh_b) {
-  const int n = g.n;
-  const int64_t ncell = (int64_t)n * n * n;
-  const int ts = g.ts, ts3 = ts * ts * ts;
-  const double mean = subtract_mean ? sc[SC_SUMWG] / (double)ncell : 0.0;
-  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell;
-       c += (int64_t)gridDim.x * blockDim.x) {
-    const int x = (int)(c % n), y = (int)((c / n) % n), z = (int)(c / ((int64_t)n * n));
-    const int cc[3] = {x, y, z};
+// Each cell sums the tiles covering it, in a fixed order (brick offset -1, 0, +1 per axis, z
+// outermost).  One CTA per (brick, phase); the tile of brick B covers cells [BS B - 1, BS B + BS + 2].
+template <typename T, int BS>
+__global__ void __launch_bounds__(256)
+k_fold(const T* __restrict__ tiles, PaintGeo g, int nphase, const double* __restrict__ sc, int subtract_mean,
+       T* __restrict__ mesh_a, T* __restrict__ mesh_b) {
+  constexpr int TS = BS + 4, TS3 = TS * TS * TS;
+  const int n = g.n, nb = g.nb;
+  const int b = blockIdx.x / nphase, ph = blockIdx.x % nphase;
+  const int B[3] = {b % nb, (b / nb) % nb, b / (nb * nb)};
+  int nbm[3], nbp[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    nbm[a] = B[a] == 0 ? nb - 1 : B[a] - 1;
+    nbp[a] = B[a] == nb - 1 ? 0 : B[a] + 1;
+  }
+  const T mean = subtract_mean ? (T)(sc[SC_SUMWG] / ((double)n * n * n)) : T(0);
+  T* mesh = ph ? mesh_b : mesh_a;
+  for (int i = threadIdx.x; i < BS * BS * BS; i += blockDim.x) {
+    const int l[3] = {i % BS, (i / BS) % BS, i / (BS * BS)};
     int nd[3], db[3][2], dt[3][2];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const int B = cc[a] / g.bs, l = cc[a] % g.bs;
       int k = 0;
-      // tile of brick B covers cells [bs*B - 1, bs*B + bs + 2]
-      if (l <= 2) { db[a][k] = (B - 1 + g.nb) % g.nb; dt[a][k] = l + g.bs + 1; ++k; }
-      db[a][k] = B; dt[a][k] = l + 1; ++k;
-      if (l == g.bs - 1 && k < 2) { db[a][k] = (B + 1) % g.nb; dt[a][k] = 0; ++k; }
+      if (l[a] <= 2) { db[a][k] = nbm[a]; dt[a][k] = l[a] + BS + 1; ++k; }
+      db[a][k] = B[a]; dt[a][k] = l[a] + 1; ++k;
+      if (l[a] == BS - 1) { db[a][k] = nbp[a]; dt[a][k] = 0; ++k; }
       nd[a] = k;
     }
-    for (int ph = 0; ph < nphase; ++ph) {
-      double v = 0.0;
-      for (int iz = 0; iz < nd[2]; ++iz)
-        for (int iy = 0; iy < nd[1]; ++iy)
-          for (int ix = 0; ix < nd[0]; ++ix) {
-            const int b = (db[2][iz] * g.nb + db[1][iy]) * g.nb + db[0][ix];
-            const int j = (dt[2][iz] * ts + dt[1][iy]) * ts + dt[0][ix];
-            v += (double)tiles[((size_t)b * nphase + ph) * ts3 + j];
-          }
-      (ph ? mesh_b : mesh_a)[c] = (T)(v - mean);
-    }
+    T v = T(0);
+    for (int iz = 0; iz < nd[2]; ++iz)
+      for (int iy = 0; iy < nd[1]; ++iy)
+        for (int ix = 0; ix < nd[0]; ++ix) {
+          const int nbr = (db[2][iz] * nb + db[1][iy]) * nb + db[0][ix];
+          const int j = (dt[2][iz] * TS + dt[1][iy]) * TS + dt[0][ix];
+          v += tiles[((size_t)nbr * nphase + ph) * TS3 + j];
+        }
+    const size_t c = ((size_t)(B[2] * BS + l[2]) * n + (B[1] * BS + l[1])) * n + (B[0] * BS + l[0]);
+    mesh[c] = v - mean;
   }
 }
 
@@ -318,19 +382,40 @@ npc_status paint_count(npc_ctx* ctx, const DevCatalog& c, const PaintGeo& g, int
   return NPC_OK;
 }
 
-template <typename P, typename R>
+template <int ASSIGN, typename P, typename R>
 npc_status paint_scatter(npc_ctx* ctx, const DevCatalog& c, int power, int coef_kind, const double* sc,
-                         const int* brick, const int* rank, const int* start, void* rec) {
+                         const PaintGeo& g, const int* brick, const int* rank, const int* start, void* rec,
+                         uint32_t* meta) {
   if (c.n == 0) return NPC_OK;
   const int blocks = (int)std::min<int64_t>((c.n + 255) / 256, (int64_t)ctx->num_sms * 16);
-  k_scatter<P, R><<<blocks, 256, 0, ctx->stream>>>((const P*)c.pos, (const P*)c.w, c.n, power, coef_kind,
-                                                   sc, brick, rank, start,
-                                                   (typename RecOf<R>::type*)rec);
+  k_scatter<ASSIGN, P, R><<<blocks, 256, 0, ctx->stream>>>((const P*)c.pos, (const P*)c.w, c.n, power, coef_kind,
+                                                           sc, g, brick, rank, start,
+                                                           (typename RecOf<R>::type*)rec, meta);
   NPC_LAUNCH(ctx);
   return NPC_OK;
 }
 
-template <typename R, typename T>
+template <int ASSIGN, typename R>
+npc_status scatter_cat(npc_ctx* ctx, const DevCatalog& c, int power, int kind, const double* sc, const PaintGeo& g,
+                       const int* brick, const int* rank, const int* start, void* rec, uint32_t* meta) {
+  if (c.dtype == 1) return paint_scatter<ASSIGN, double, R>(ctx, c, power, kind, sc, g, brick, rank, start, rec, meta);
+  return paint_scatter<ASSIGN, float, R>(ctx, c, power, kind, sc, g, brick, rank, start, rec, meta);
+}
+
+template <typename T>
+npc_status launch_fold(npc_ctx* ctx, const void* tiles, const PaintGeo& g, int nphase, const double* sc, int sub,
+                       void* mesh_a, void* mesh_b) {
+  const int grid = g.nb * g.nb * g.nb * nphase;
+  switch (g.bs) {
+    case 4: k_fold<T, 4><<<grid, 64, 0, ctx->stream>>>((const T*)tiles, g, nphase, sc, sub, (T*)mesh_a, (T*)mesh_b); break;
+    case 8: k_fold<T, 8><<<grid, 256, 0, ctx->stream>>>((const T*)tiles, g, nphase, sc, sub, (T*)mesh_a, (T*)mesh_b); break;
+    default: k_fold<T, 16><<<grid, 256, 0, ctx->stream>>>((const T*)tiles, g, nphase, sc, sub, (T*)mesh_a, (T*)mesh_b); break;
+  }
+  NPC_LAUNCH(ctx);
+  return NPC_OK;
+}
+
+template <int ASSIGN, typename R, typename T>
 npc_status paint_impl(npc_ctx* ctx, const DevCatalog& d, const DevCatalog* r, const npc_mesh_spec& m,
                       int weight_power, const double* sc, void* mesh_a, void* mesh_b) {
   PaintGeo g;
@@ -344,6 +429,7 @@ npc_status paint_impl(npc_ctx* ctx, const DevCatalog& d, const DevCatalog* r, co
   const int nbricks = g.nb * g.nb * g.nb;
   const int64_t ntot = d.n + (r ? r->n : 0);
   int *count, *start, *brick, *rank;
+  uint32_t* meta;
   void* rec;
   void* tiles;
   const size_t ts3 = (size_t)g.ts * g.ts * g.ts;
@@ -351,12 +437,12 @@ npc_status paint_impl(npc_ctx* ctx, const DevCatalog& d, const DevCatalog* r, co
   NPC_TRY(ws_get(ctx, "paint.start", sizeof(int) * nbricks, (void**)&start));
   NPC_TRY(ws_get(ctx, "paint.brick", sizeof(int) * std::max<int64_t>(ntot, 1), (void**)&brick));
   NPC_TRY(ws_get(ctx, "paint.rank", sizeof(int) * std::max<int64_t>(ntot, 1), (void**)&rank));
+  NPC_TRY(ws_get(ctx, "paint.meta", sizeof(uint32_t) * std::max<int64_t>(ntot, 1), (void**)&meta));
   NPC_TRY(ws_get(ctx, "paint.rec", sizeof(typename RecOf<R>::type) * std::max<int64_t>(ntot, 1), &rec));
   NPC_TRY(ws_get(ctx, "paint.tiles", sizeof(T) * ts3 * nbricks * nphase, &tiles));
   NPC_CUDA(ctx, cudaMemsetAsync(count, 0, sizeof(int) * nbricks, ctx->stream));
-  const bool dd = d.dtype == 1;
   // counting: data then randoms share the brick counters (ranks continue)
-  if (dd) NPC_TRY(paint_count<double>(ctx, d, g, count, brick, rank));
+  if (d.dtype == 1) NPC_TRY(paint_count<double>(ctx, d, g, count, brick, rank));
   else NPC_TRY(paint_count<float>(ctx, d, g, count, brick, rank));
   if (r) {
     if (r->dtype == 1) NPC_TRY(paint_count<double>(ctx, *r, g, count, brick + d.n, rank + d.n));
@@ -364,35 +450,23 @@ npc_status paint_impl(npc_ctx* ctx, const DevCatalog& d, const DevCatalog* r, co
   }
   k_scan<<<1, 1024, 0, ctx->stream>>>(count, nbricks, start);
   NPC_LAUNCH(ctx);
-  if (dd) NPC_TRY((paint_scatter<double, R>(ctx, d, weight_power, 0, sc, brick, rank, start, rec)));
-  else NPC_TRY((paint_scatter<float, R>(ctx, d, weight_power, 0, sc, brick, rank, start, rec)));
+  NPC_TRY(stage_mark(ctx, "paint_count"));
+  NPC_TRY((scatter_cat<ASSIGN, R>(ctx, d, weight_power, 0, sc, g, brick, rank, start, rec, meta)));
   if (r) {
     const int kind = weight_power == 1 ? 1 : 2;
-    if (r->dtype == 1)
-      NPC_TRY((paint_scatter<double, R>(ctx, *r, weight_power, kind, sc, brick + d.n, rank + d.n, start, rec)));
-    else
-      NPC_TRY((paint_scatter<float, R>(ctx, *r, weight_power, kind, sc, brick + d.n, rank + d.n, start, rec)));
+    NPC_TRY((scatter_cat<ASSIGN, R>(ctx, *r, weight_power, kind, sc, g, brick + d.n, rank + d.n, start, rec, meta)));
   }
-  const size_t smem = sizeof(long long) * ts3 * nphase;
+  NPC_TRY(stage_mark(ctx, "paint_scatter"));
+  const size_t smem = sizeof(long long) * ts3;
   const int slot = weight_power == 1 ? SC_MAXW_F : SC_MAXW_N;
-  if (m.assign == 2) {
-    auto kern = k_paint_brick<2, R, T>;
-    NPC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<nbricks, 256, smem, ctx->stream>>>((const typename RecOf<R>::type*)rec, start, count, g, nphase, sc,
-                                              slot, (T*)tiles);
-  } else {
-    auto kern = k_paint_brick<3, R, T>;
-    NPC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<nbricks, 256, smem, ctx->stream>>>((const typename RecOf<R>::type*)rec, start, count, g, nphase, sc,
-                                              slot, (T*)tiles);
-  }
+  auto kern = k_paint_brick<ASSIGN, R, T>;
+  NPC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kern<<<nbricks * nphase, 512, smem, ctx->stream>>>((const typename RecOf<R>::type*)rec, meta, start, count, g,
+                                                     nphase, sc, slot, (T*)tiles);
   NPC_LAUNCH(ctx);
-  const int64_t ncell = (int64_t)m.n * m.n * m.n;
-  const int fblocks = (int)std::min<int64_t>((ncell + 255) / 256, (int64_t)ctx->num_sms * 32);
+  NPC_TRY(stage_mark(ctx, "paint_tiles"));
   const int sub = (m.periodic && weight_power == 1) ? 1 : 0;
-  k_fold<T><<<fblocks, 256, 0, ctx->stream>>>((const T*)tiles, g, nphase, sc, sub, (T*)mesh_a, (T*)mesh_b);
-  NPC_LAUNCH(ctx);
-  return NPC_OK;
+  return launch_fold<T>(ctx, tiles, g, nphase, sc, sub, mesh_a, mesh_b);
 }
 
 }  // namespace
@@ -425,7 +499,12 @@ npc_status launch_catalog_scalars(npc_ctx* ctx, const DevCatalog& d, const DevCa
 npc_status launch_paint(npc_ctx* ctx, const DevCatalog& d, const DevCatalog* r, const npc_mesh_spec& m,
                         int weight_power, int prec, const double* dev_scalars, void* mesh_a, void* mesh_b) {
   const bool any_double = d.dtype == 1 || (r && r->dtype == 1);
-  if (prec == NPC_PREC_FP64) return paint_impl<double, double>(ctx, d, r, m, weight_power, dev_scalars, mesh_a, mesh_b);
-  if (any_double) return paint_impl<double, float>(ctx, d, r, m, weight_power, dev_scalars, mesh_a, mesh_b);
-  return paint_impl<float, float>(ctx, d, r, m, weight_power, dev_scalars, mesh_a, mesh_b);
+  if (prec == NPC_PREC_FP64) {
+    if (m.assign == 2) return paint_impl<2, double, double>(ctx, d, r, m, weight_power, dev_scalars, mesh_a, mesh_b);
+    return paint_impl<3, double, double>(ctx, d, r, m, weight_power, dev_scalars, mesh_a, mesh_b);
+  }
+  // records keep the fraction s - floor(s) (< 1) in float32 in the mixed path
+  (void)any_double;
+  if (m.assign == 2) return paint_impl<2, float, float>(ctx, d, r, m, weight_power, dev_scalars, mesh_a, mesh_b);
+  return paint_impl<3, float, float>(ctx, d, r, m, weight_power, dev_scalars, mesh_a, mesh_b);
 }

@@ -46,8 +46,12 @@ constexpr int NPC_NLM = (NPC_LMAX + 1) * (NPC_LMAX + 2) / 2;
 
 struct YNorm {
   double v[NPC_NLM];  // index l(l+1)/2 + m
+  float f[NPC_NLM];   // the same, rounded once to float (no float64 work in float kernels)
 };
 YNorm ylm_norm_table();
+template <typename T> __device__ __forceinline__ T ynorm(const YNorm& n, int i);
+template <> __device__ __forceinline__ float ynorm<float>(const YNorm& n, int i) { return n.f[i]; }
+template <> __device__ __forceinline__ double ynorm<double>(const YNorm& n, int i) { return n.v[i]; }
 
 template <typename T>
 __device__ __forceinline__ void ylm_eval(int l, int m, T x, T y, T z, const YNorm& nrm, T& re, T& im) {
@@ -70,7 +74,36 @@ __device__ __forceinline__ void ylm_eval(int l, int m, T x, T y, T z, const YNor
     }
     q = q1;
   }
-  const T c = T(nrm.v[l * (l + 1) / 2 + m]) * q;
+  const T c = ynorm<T>(nrm, l * (l + 1) / 2 + m) * q;
+  re = c * pr;
+  im = c * pim;
+}
+
+// Closed forms of Q_lm for l in {2, 4} (expanded from the recurrence above), falling back to
+// the recurrence otherwise.  (x, y, z) is a unit vector.
+template <typename T>
+__device__ __forceinline__ void ylm_fast(int l, int m, T x, T y, T z, const YNorm& nrm, T& re, T& im) {
+  const T z2 = z * z;
+  T q;
+  switch (l * 16 + m) {
+    case 0x00: re = ynorm<T>(nrm, 0); im = T(0); return;
+    case 0x20: q = T(1.5) * z2 - T(0.5); break;
+    case 0x21: q = T(-3) * z; break;
+    case 0x22: q = T(3); break;
+    case 0x40: q = (T(35) * z2 * z2 - T(30) * z2 + T(3)) * T(0.125); break;
+    case 0x41: q = T(-2.5) * z * (T(7) * z2 - T(3)); break;
+    case 0x42: q = T(7.5) * (T(7) * z2 - T(1)); break;
+    case 0x43: q = T(-105) * z; break;
+    case 0x44: q = T(105); break;
+    default: ylm_eval<T>(l, m, x, y, z, nrm, re, im); return;
+  }
+  T pr = T(1), pim = T(0);
+  for (int j = 0; j < m; ++j) {
+    const T nr = pr * x - pim * y;
+    pim = pr * y + pim * x;
+    pr = nr;
+  }
+  const T c = ynorm<T>(nrm, l * (l + 1) / 2 + m) * q;
   re = c * pr;
   im = c * pim;
 }
@@ -132,7 +165,18 @@ struct npc_ctx {
   std::string last_error;
   npc_stats stats{};
   int launches = 0;
+  // stage profiling (events recorded on `stream` at stage boundaries when enabled)
+  bool profile = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::string> stage_names;
+  std::vector<int> stage_launches;
+  int ev_used = 0;
+  int launches_at_mark = 0;
 };
+
+// Marks the end of a stage named `name` (and the start of the next) when profiling is on.
+npc_status stage_mark(npc_ctx* ctx, const char* name);
+npc_status stage_begin(npc_ctx* ctx);
 
 // error helpers
 npc_status set_err(npc_ctx* ctx, npc_status s, const char* fmt, ...);
@@ -208,6 +252,7 @@ struct PowerPlan {
   int global_los;
   double los[3];
   int assign;
+  int kz_keep;          // forward passes keep kz < kz_keep (0: all, n/2)
 };
 
 npc_status run_forward_transforms(npc_ctx* ctx, int prec, const PowerPlan& plan, const Geom& g,

@@ -37,21 +37,25 @@ template <int N> struct ColCfg {
   static constexpr int THREADS = TX * N / 8;
 };
 
+// Weight of one real field at grid point (x, y, z): F times ReY/ImY of the direction from the
+// observer to the grid point (phase b sits half a cell lower), or F alone (PART_ONE).
 template <typename T>
-__device__ __forceinline__ T comp_value(const Comp cp, const T* tileA, const T* tileB, int z, int c,
-                                        int tx, int x, int y, const Geom& g, const YNorm& nrm) {
+struct ColGeom {
+  T px[2], py[2], oz[2], h;   // per phase: x and y coordinates of this column, z origin
+};
+
+template <typename T>
+__device__ __forceinline__ T comp_value(const Comp cp, const T* tileA, const T* tileB, int z, int c, int tx,
+                                        const ColGeom<T>& cg, const YNorm& nrm) {
   if (cp.part == PART_ZERO) return T(0);
   const T F = (cp.phase ? tileB : tileA)[z * tx + c];
   if (cp.part == PART_ONE) return F;
-  const T sh = cp.phase ? T(0.5) : T(0);
-  const T h = (T)g.h;
-  const T px = (T)g.o[0] + (T(x) - sh) * h;
-  const T py = (T)g.o[1] + (T(y) - sh) * h;
-  const T pz = (T)g.o[2] + (T(z) - sh) * h;
-  const T r2 = px * px + py * py + pz * pz;
-  const T inv = r2 > T(0) ? T(1) / sqrt(r2) : T(0);
+  const int ph = cp.phase;
+  const T pz = cg.oz[ph] + T(z) * cg.h;
+  const T r2 = cg.px[ph] * cg.px[ph] + cg.py[ph] * cg.py[ph] + pz * pz;
+  const T inv = r2 > T(0) ? rsqrt(r2) : T(0);
   T re, im;
-  ylm_eval<T>(cp.ell, cp.m, px * inv, py * inv, pz * inv, nrm, re, im);
+  ylm_fast<T>(cp.ell, cp.m, cg.px[ph] * inv, cg.py[ph] * inv, pz * inv, nrm, re, im);
   return F * (cp.part == PART_RE ? re : im);
 }
 
@@ -59,7 +63,7 @@ __device__ __forceinline__ T comp_value(const Comp cp, const T* tileA, const T* 
 template <typename T, int N>
 __global__ void __launch_bounds__(ColCfg<N>::THREADS)
 k_fwd_z(const T* __restrict__ mesh_a, const T* __restrict__ mesh_b, cplx<T>* __restrict__ half,
-        const FieldList fl, const Geom g, const YNorm nrm, const cplx<T>* __restrict__ tw_g) {
+        const FieldList fl, const Geom g, const YNorm nrm, const cplx<T>* __restrict__ tw_g, int KZ) {
   using C = cplx<T>;
   constexpr int TX = ColCfg<N>::TX;
   constexpr int TPF = N / 8;
@@ -78,9 +82,17 @@ k_fwd_z(const T* __restrict__ mesh_a, const T* __restrict__ mesh_b, cplx<T>* __r
     tileA[i] = mesh_a[gi];
     if (mesh_b) tileB[i] = mesh_b[gi];
   }
+  ColGeom<T> cg;
+  cg.h = (T)g.h;
+  for (int ph = 0; ph < 2; ++ph) {
+    const double sh = ph ? 0.5 : 0.0;
+    cg.px[ph] = (T)(g.o[0] + ((double)(x0 + c) - sh) * g.h);
+    cg.py[ph] = (T)(g.o[1] + ((double)y - sh) * g.h);
+    cg.oz[ph] = (T)(g.o[2] - sh * g.h);
+  }
   __syncthreads();
   const int npairs = (fl.nf + 1) / 2;
-  const size_t fstride = (size_t)(N / 2) * N * N;
+  const size_t fstride = (size_t)KZ * N * N;
   for (int p = 0; p < npairs; ++p) {
     const Comp c0 = fl.f[2 * p];
     Comp c1;
@@ -90,15 +102,15 @@ k_fwd_z(const T* __restrict__ mesh_a, const T* __restrict__ mesh_b, cplx<T>* __r
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int z = t + q * TPF;
-      const T re = comp_value<T>(c0, tileA, tileB, z, c, TX, x0 + c, y, g, nrm);
-      const T im = comp_value<T>(c1, tileA, tileB, z, c, TX, x0 + c, y, g, nrm);
+      const T re = comp_value<T>(c0, tileA, tileB, z, c, TX, cg, nrm);
+      const T im = comp_value<T>(c1, tileA, tileB, z, c, TX, cg, nrm);
       v[q] = cmk(re, im);
     }
     fft_block<N, -1>(v, t, tw, ColView<C>{work + c, TX});
 #pragma unroll
     for (int q = 0; q < 8; ++q) work[(t + q * TPF) * TX + c] = v[q];
     __syncthreads();
-    for (int i = tid; i < (N / 2) * TX; i += blockDim.x) {
+    for (int i = tid; i < KZ * TX; i += blockDim.x) {
       const int kz = i / TX, cc = i % TX;
       const C z1 = work[kz * TX + cc];
       const C z2 = cconj(work[((N - kz) & (N - 1)) * TX + cc]);
@@ -111,6 +123,175 @@ k_fwd_z(const T* __restrict__ mesh_a, const T* __restrict__ mesh_b, cplx<T>* __r
     }
     __syncthreads();
   }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Specialised first pass for the standard interlaced field layout (l in {0, 2, 4}, both phases):
+// pair p is (l, m, kind) known at compile time; kind 0 packs the m = 0 field of phase a (real
+// part) with that of phase b (imaginary part), kind 1/2 is the complex field F Y_l^m of phase
+// a/b whose real and imaginary parts share one Y evaluation.  Pairs are a prefix of
+//   (0,0,0) (2,0,0) (2,1,1) (2,1,2) (2,2,1) (2,2,2) (4,0,0) (4,1,1) (4,1,2) ... (4,4,1) (4,4,2).
+// ---------------------------------------------------------------------------------------------
+template <typename T, int L, int M>
+__device__ __forceinline__ void ylm_ct(T ux, T uy, T uz, const YNorm& nrm, T& re, T& im) {
+  const T z2 = uz * uz;
+  T q;
+  if constexpr (L == 0) q = T(1);
+  else if constexpr (L == 2 && M == 0) q = T(1.5) * z2 - T(0.5);
+  else if constexpr (L == 2 && M == 1) q = T(-3) * uz;
+  else if constexpr (L == 2 && M == 2) q = T(3);
+  else if constexpr (L == 4 && M == 0) q = (T(35) * z2 * z2 - T(30) * z2 + T(3)) * T(0.125);
+  else if constexpr (L == 4 && M == 1) q = T(-2.5) * uz * (T(7) * z2 - T(3));
+  else if constexpr (L == 4 && M == 2) q = T(7.5) * (T(7) * z2 - T(1));
+  else if constexpr (L == 4 && M == 3) q = T(-105) * uz;
+  else q = T(105);
+  T pr = T(1), pi = T(0);
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+    const T nr = pr * ux - pi * uy;
+    pi = pr * uy + pi * ux;
+    pr = nr;
+  }
+  const T c = ynorm<T>(nrm, L * (L + 1) / 2 + M) * q;
+  re = c * pr;
+  im = c * pi;
+}
+
+template <typename T> struct ZGeom {
+  T px[2], py[2], pxy2[2];  // column x, row y per phase and px^2 + py^2
+  T pz0[2];                 // z coordinate of element q = 0 of this thread, per phase
+  T dz;                     // z step between consecutive elements of a thread (TPF cells)
+};
+
+template <typename T, int N, int TX, int L, int M, int KIND>
+__device__ __forceinline__ void std_inputs(cplx<T> (&v)[8], const T* tileA, const T* tileB, int c, int t,
+                                           const ZGeom<T>& zg, const YNorm& nrm) {
+  constexpr int TPF = N / 8;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int z = t + q * TPF;
+    if constexpr (KIND == 0) {
+      const T fa = tileA[z * TX + c], fb = tileB[z * TX + c];
+      if constexpr (L == 0) {
+        v[q] = cmk(fa, fb);
+      } else {
+        T ya, yb, dum;
+        {
+          const T pz = zg.pz0[0] + T(q) * zg.dz;
+          const T inv = rsqrt(zg.pxy2[0] + pz * pz);
+          ylm_ct<T, L, M>(zg.px[0] * inv, zg.py[0] * inv, pz * inv, nrm, ya, dum);
+        }
+        {
+          const T pz = zg.pz0[1] + T(q) * zg.dz;
+          const T inv = rsqrt(zg.pxy2[1] + pz * pz);
+          ylm_ct<T, L, M>(zg.px[1] * inv, zg.py[1] * inv, pz * inv, nrm, yb, dum);
+        }
+        v[q] = cmk(fa * ya, fb * yb);
+      }
+    } else {
+      constexpr int ph = KIND - 1;
+      const T f = (ph ? tileB : tileA)[z * TX + c];
+      const T pz = zg.pz0[ph] + T(q) * zg.dz;
+      const T inv = rsqrt(zg.pxy2[ph] + pz * pz);
+      T re, im;
+      ylm_ct<T, L, M>(zg.px[ph] * inv, zg.py[ph] * inv, pz * inv, nrm, re, im);
+      v[q] = cmk(f * re, f * im);
+    }
+  }
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(ColCfg<N>::THREADS)
+k_fwd_z_std(const T* __restrict__ mesh_a, const T* __restrict__ mesh_b, cplx<T>* __restrict__ half, int npairs,
+            const Geom g, const YNorm nrm, const cplx<T>* __restrict__ tw_g, int KZ) {
+  using C = cplx<T>;
+  constexpr int TX = ColCfg<N>::TX;
+  constexpr int TPF = N / 8;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  C* work = tw + N;
+  T* tileA = reinterpret_cast<T*>(work + N * TX);
+  T* tileB = tileA + N * TX;
+  const int tid = threadIdx.x;
+  const int c = tid % TX, t = tid / TX;
+  const int x0 = blockIdx.x * TX, y = blockIdx.y;
+  for (int i = tid; i < N; i += blockDim.x) tw[i] = tw_g[i];
+  for (int i = tid; i < N * TX; i += blockDim.x) {
+    const int z = i / TX, cc = i % TX;
+    const size_t gi = ((size_t)z * N + y) * N + x0 + cc;
+    tileA[i] = mesh_a[gi];
+    tileB[i] = mesh_b[gi];
+  }
+  ZGeom<T> zg;
+  for (int ph = 0; ph < 2; ++ph) {
+    const double sh = ph ? 0.5 : 0.0;
+    zg.px[ph] = (T)(g.o[0] + ((double)(x0 + c) - sh) * g.h);
+    zg.py[ph] = (T)(g.o[1] + ((double)y - sh) * g.h);
+    zg.pxy2[ph] = zg.px[ph] * zg.px[ph] + zg.py[ph] * zg.py[ph];
+    zg.pz0[ph] = (T)(g.o[2] + ((double)t - sh) * g.h);
+  }
+  zg.dz = (T)(g.h * TPF);
+  __syncthreads();
+  const size_t fstride = (size_t)KZ * N * N;
+  for (int p = 0; p < npairs; ++p) {
+    C v[8];
+    switch (p) {
+      case 0: std_inputs<T, N, TX, 0, 0, 0>(v, tileA, tileB, c, t, zg, nrm); break;
+      case 1: std_inputs<T, N, TX, 2, 0, 0>(v, tileA, tileB, c, t, zg, nrm); break;
+      case 2: std_inputs<T, N, TX, 2, 1, 1>(v, tileA, tileB, c, t, zg, nrm); break;
+      case 3: std_inputs<T, N, TX, 2, 1, 2>(v, tileA, tileB, c, t, zg, nrm); break;
+      case 4: std_inputs<T, N, TX, 2, 2, 1>(v, tileA, tileB, c, t, zg, nrm); break;
+      case 5: std_inputs<T, N, TX, 2, 2, 2>(v, tileA, tileB, c, t, zg, nrm); break;
+      case 6: std_inputs<T, N, TX, 4, 0, 0>(v, tileA, tileB, c, t, zg, nrm); break;
+      case 7: std_inputs<T, N, TX, 4, 1, 1>(v, tileA, tileB, c, t, zg, nrm); break;
+      case 8: std_inputs<T, N, TX, 4, 1, 2>(v, tileA, tileB, c, t, zg, nrm); break;
+      case 9: std_inputs<T, N, TX, 4, 2, 1>(v, tileA, tileB, c, t, zg, nrm); break;
+      case 10: std_inputs<T, N, TX, 4, 2, 2>(v, tileA, tileB, c, t, zg, nrm); break;
+      case 11: std_inputs<T, N, TX, 4, 3, 1>(v, tileA, tileB, c, t, zg, nrm); break;
+      case 12: std_inputs<T, N, TX, 4, 3, 2>(v, tileA, tileB, c, t, zg, nrm); break;
+      case 13: std_inputs<T, N, TX, 4, 4, 1>(v, tileA, tileB, c, t, zg, nrm); break;
+      default: std_inputs<T, N, TX, 4, 4, 2>(v, tileA, tileB, c, t, zg, nrm); break;
+    }
+    fft_block<N, -1>(v, t, tw, ColView<C>{work + c, TX});
+#pragma unroll
+    for (int q = 0; q < 8; ++q) work[(t + q * TPF) * TX + c] = v[q];
+    __syncthreads();
+    for (int i = tid; i < KZ * TX; i += blockDim.x) {
+      const int kz = i / TX, cc = i % TX;
+      const C z1 = work[kz * TX + cc];
+      const C z2 = cconj(work[((N - kz) & (N - 1)) * TX + cc]);
+      const C a = cscale(cadd(z1, z2), T(0.5));
+      const C d = csub(z1, z2);
+      const C b = cmk(T(0.5) * d.y, T(-0.5) * d.x);
+      const size_t gi = ((size_t)kz * N + y) * N + x0 + cc;
+      half[(size_t)(2 * p) * fstride + gi] = a;
+      half[(size_t)(2 * p + 1) * fstride + gi] = b;
+    }
+    __syncthreads();
+  }
+}
+
+// Number of leading standard pairs the field list matches (0 if it does not follow the layout).
+static int std_pairs(const FieldList& fl) {
+  static const int8_t tbl[15][3] = {{0, 0, 0}, {2, 0, 0}, {2, 1, 1}, {2, 1, 2}, {2, 2, 1}, {2, 2, 2}, {4, 0, 0},
+                                    {4, 1, 1}, {4, 1, 2}, {4, 2, 1}, {4, 2, 2}, {4, 3, 1}, {4, 3, 2}, {4, 4, 1},
+                                    {4, 4, 2}};
+  if (fl.nf % 2) return 0;
+  const int np = fl.nf / 2;
+  if (np > 15) return 0;
+  for (int p = 0; p < np; ++p) {
+    const Comp a = fl.f[2 * p], b = fl.f[2 * p + 1];
+    const int l = tbl[p][0], m = tbl[p][1], kind = tbl[p][2];
+    if (a.ell != l || b.ell != l || a.m != m || b.m != m) return 0;
+    if (kind == 0) {
+      const int part = l == 0 ? PART_ONE : PART_RE;
+      if (a.phase != 0 || b.phase != 1 || a.part != part || b.part != part) return 0;
+    } else {
+      const int ph = kind - 1;
+      if (a.phase != ph || b.phase != ph || a.part != PART_RE || b.part != PART_IM) return 0;
+    }
+  }
+  return np;
 }
 
 // Column transform along a strided axis: element j of column (plane, x) at
@@ -137,24 +318,37 @@ k_fft_cols(cplx<T>* __restrict__ data, size_t plane_stride, int row_stride, cons
   for (int q = 0; q < 8; ++q) base[(size_t)(t + q * TPF) * row_stride] = v[q];
 }
 
-struct LogicalField {   // one (l, m, part) with its field index per phase
-  int8_t ell, m, part;
-  int8_t idx0, idx1;    // idx1 = -1 without interlacing
+// Per stored real field: which F_l it feeds, its mesh phase and its k-space coefficient
+// scale * (ReY or ImY)(khat) from the row's Y table (scale = 4 pi/(2l+1) * (m > 0 ? 2 : 1)).
+struct FieldCoef {
+  int8_t acc;    // 0, 1, 2 for F_0, F_2, F_4
+  int8_t phase;  // 0 or 1
+  int8_t yidx;   // row Y-table index, -1 for PART_ONE
+  int8_t part;   // PART_RE / PART_IM / PART_ONE
+  float scale_f;
+  double scale_d;
 };
+template <typename T> __device__ __forceinline__ T coef_scale(const FieldCoef& c);
+template <> __device__ __forceinline__ float coef_scale<float>(const FieldCoef& c) { return c.scale_f; }
+template <> __device__ __forceinline__ double coef_scale<double>(const FieldCoef& c) { return c.scale_d; }
+
+constexpr int MAX_YTAB = 8;
 
 struct ContractParams {
-  int nf;               // stored real fields
-  int nlog;             // logical fields
-  LogicalField lf[NPC_MAX_FIELDS];
+  int nf;
+  FieldCoef fc[NPC_MAX_FIELDS];
+  int ny;                       // Y_lm(khat) per row, l > 0
+  int8_t yl[MAX_YTAB], ym[MAX_YTAB];
+  int nacc;                     // F accumulators (1..3)
   int nphase;
   int nbins, nsum;
-  int nell;             // P_l sums for ell_list
+  int nell;
   int ell_list[3];
-  int nll;              // two-index sums
+  int nll;
   int lla[3], llb[3];
-  int need2, need4;     // F_2, F_4 required
+  int need2, need4;
   int global_los;
-  float los[3];
+  double los[3];
   int assign;
   double kf;
 };
@@ -167,21 +361,34 @@ __device__ __forceinline__ T sinc_pow(T a, int p) {
   return r;
 }
 
+template <int N> struct XCfg {
+  static constexpr int TPF = N / 8;
+  static constexpr int G = CONTRACT_THREADS / TPF > 0 ? CONTRACT_THREADS / TPF : 1;  // rows in flight
+};
+
+// Last pass.  For one (ky, kz) row: every field row is transformed along x and added, with its
+// coefficient, into per-group F_l accumulators (F_l is linear in the fields, so the 30 rows never
+// need to be resident together); then per mode the products Re[F_0 F_l^*], Re[F_l F_l'^*] are
+// binned.  Groups own their accumulators and threads own their modes, so no shared-memory
+// atomics are needed, and the group sum runs in a fixed order.
 template <typename T, int N>
-__global__ void __launch_bounds__(CONTRACT_THREADS)
+__global__ void __launch_bounds__(CONTRACT_THREADS, 2)
 k_fft_x_contract(const cplx<T>* __restrict__ half, const ContractParams P, const YNorm nrm,
                  const int16_t* __restrict__ bintab, const cplx<T>* __restrict__ tw_g, double* __restrict__ part) {
   using C = cplx<T>;
-  constexpr int TPF = N / 8;
-  constexpr int G = CONTRACT_THREADS / TPF > 0 ? CONTRACT_THREADS / TPF : 1;
+  constexpr int TPF = XCfg<N>::TPF;
+  constexpr int G = XCfg<N>::G;
   constexpr int NP = row_pad_len<N>();
   constexpr int NW = CONTRACT_THREADS / 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
-  C* phs = tw + N;                 // e^{i pi a / N}, a = -N/2 .. N/2-1  (index a + N/2)
-  T* winv = reinterpret_cast<T*>(phs + N);   // 1 / sinc(pi a/N)^p, a = 0 .. N/2
-  C* rows = reinterpret_cast<C*>(winv + (N / 2 + 2));
-  C* dummy = rows + (size_t)P.nf * NP;
+  C* phs = tw + N;                          // e^{i pi a/N}, index a + N/2
+  C* ytab = phs + N;                        // [ny][N]
+  C* facc = ytab + (size_t)P.ny * N;        // [G][nacc][N]
+  C* rowbuf = facc + (size_t)G * P.nacc * N;  // [G][NP]
+  T* winv = reinterpret_cast<T*>(rowbuf + (size_t)G * NP);  // 1/sinc^p, a = 0..N/2
+  T* fa = winv + (N / 2 + 2);               // phase-a factor per kx
+  T* fidx = fa + N;                         // signed frequency index of storage position, as T
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
   for (int i = tid; i < N; i += blockDim.x) {
@@ -190,106 +397,150 @@ k_fft_x_contract(const cplx<T>* __restrict__ half, const ContractParams P, const
     phs[i] = cmk(cos(a), sin(a));
   }
   for (int i = tid; i <= N / 2; i += blockDim.x) winv[i] = T(1) / sinc_pow<T>(T(M_PI) * T(i) / T(N), P.assign);
+  for (int i = tid; i < N; i += blockDim.x) fidx[i] = T(i < N / 2 ? i : i - N);
   __syncthreads();
   double* mypart = part + ((size_t)blockIdx.x * NW + warp) * P.nbins * P.nsum;
   const int nrows = (N / 2) * N;
   const int g = tid / TPF, t = tid % TPF;
+  const bool ingroup = g < G;
+  const T half_or_one = P.nphase == 2 ? T(0.5) : T(1);
   for (int r = blockIdx.x; r < nrows; r += gridDim.x) {
     const int kz = r / N, ky = r % N;
+    const int jy = ky < N / 2 ? ky : ky - N;
+    // per-mode window/interlace factor and Y_lm(khat) table; clear the accumulators
+    for (int kx = tid; kx < N; kx += blockDim.x) {
+      const int i = kx < N / 2 ? kx : kx - N;
+      const int ai = i < 0 ? -i : i, aj = jy < 0 ? -jy : jy;
+      fa[kx] = half_or_one * winv[ai] * winv[aj] * winv[kz];
+      if (P.ny > 0) {
+        const T fi = fidx[kx], fj = fidx[ky], fk = fidx[kz];
+        const T r2 = fi * fi + fj * fj + fk * fk;
+        const T inv = r2 > T(0) ? rsqrt(r2) : T(0);
+        const T ux = fi * inv, uy = fj * inv, uz = r2 > T(0) ? fk * inv : T(1);
+        for (int j = 0; j < P.ny; ++j) {
+          T re, im;
+          ylm_fast<T>(P.yl[j], P.ym[j], ux, uy, uz, nrm, re, im);
+          ytab[(size_t)j * N + kx] = cmk(re, im);
+        }
+      }
+      for (int q = 0; q < G * P.nacc; ++q) facc[(size_t)q * N + kx] = cmk(T(0), T(0));
+    }
+    __syncthreads();
+    const C phyz = cmul(phs[jy + N / 2], phs[kz + N / 2]);
+    C v[8], vn[8];
+    const size_t fstride = (size_t)(N / 2) * N * N;
+    const size_t roff = ((size_t)kz * N + ky) * N;
+    if (ingroup && g < P.nf) {
+      const C* src = half + (size_t)g * fstride + roff;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v[q] = src[t + q * TPF];
+    }
     for (int f0 = 0; f0 < P.nf; f0 += G) {
       const int f = f0 + g;
-      C v[8];
-      const bool live = (g < G) && (f < P.nf);
-      if (live) {
-        const C* src = half + (((size_t)f * (N / 2) + kz) * N + ky) * N;
+      const bool live = ingroup && f < P.nf;
+      const int fn = f + G;
+      if (ingroup && fn < P.nf) {
+        const C* src = half + (size_t)fn * fstride + roff;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) v[q] = src[t + q * TPF];
-      } else {
+        for (int q = 0; q < 8; ++q) vn[q] = src[t + q * TPF];
+      }
+      if (!live) {
 #pragma unroll
         for (int q = 0; q < 8; ++q) v[q] = cmk(T(0), T(0));
       }
-      RowView<C> rv{live ? rows + (size_t)f * NP : dummy};
-      fft_block<N, -1>(v, t, tw, rv);
+      fft_block<N, -1>(v, t, tw, RowView<C>{rowbuf + (size_t)(ingroup ? g : 0) * NP});
       if (live) {
+        const FieldCoef c = P.fc[f];
+        C* acc = facc + ((size_t)g * P.nacc + c.acc) * N;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) rv.st(t + q * TPF, v[q]);
+        for (int q = 0; q < 8; ++q) {
+          const int kx = t + q * TPF;
+          T w = coef_scale<T>(c) * fa[kx];
+          if (c.yidx >= 0) {
+            const C y = ytab[(size_t)c.yidx * N + kx];
+            w *= (c.part == PART_RE ? y.x : y.y);
+          }
+          C a = cscale(v[q], w);
+          if (c.phase) {
+            const int i = kx < N / 2 ? kx : kx - N;
+            a = cmul(a, cmul(phs[i + N / 2], phyz));
+          }
+          acc[kx] = cadd(acc[kx], a);
+        }
       }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v[q] = vn[q];
     }
     __syncthreads();
-    const int jy = ky < N / 2 ? ky : ky - N;
+    const T fjy = fidx[(jy + N) % N], fkz = fidx[kz];
     for (int jb = warp * 32; jb < N; jb += blockDim.x) {
       const int j = jb + lane;
       const int i = j < N / 2 ? j : j - N;
       int bin = -1;
       if (j < N && i != -N / 2 && jy != -N / 2 && (i != 0 || jy != 0 || kz != 0)) bin = bintab[i * i + jy * jy + kz * kz];
-      double vals[MAX_SUMS];
+      T vals[MAX_SUMS];
 #pragma unroll
-      for (int s = 0; s < MAX_SUMS; ++s) vals[s] = 0.0;
+      for (int s = 0; s < MAX_SUMS; ++s) vals[s] = T(0);
       if (bin >= 0) {
         const T wgt = kz > 0 ? T(2) : T(1);
-        const int ai = i < 0 ? -i : i, aj = jy < 0 ? -jy : jy;
-        const T iw = winv[ai] * winv[aj] * winv[kz];
-        C ph = cmk(T(1), T(0));
-        if (P.nphase == 2) ph = cmul(cmul(phs[i + N / 2], phs[jy + N / 2]), phs[kz + N / 2]);
-        const T kk = sqrt(T(i * i + jy * jy + kz * kz));
-        const T ux = T(i) / kk, uy = T(jy) / kk, uz = T(kz) / kk;
         C F0 = cmk(T(0), T(0)), F2 = cmk(T(0), T(0)), F4 = cmk(T(0), T(0));
-        const int jp = RowView<C>::idx(j);
-        for (int k = 0; k < P.nlog; ++k) {
-          const LogicalField L = P.lf[k];
-          C a = rows[(size_t)L.idx0 * NP + jp];
-          if (L.idx1 >= 0) a = cscale(cadd(a, cmul(ph, rows[(size_t)L.idx1 * NP + jp])), T(0.5));
-          a = cscale(a, iw);
-          T coef;
-          if (L.part == PART_ONE) {
-            coef = T(1);
-          } else {
-            T re, im;
-            ylm_eval<T>(L.ell, L.m, ux, uy, uz, nrm, re, im);
-            coef = T(4.0 * M_PI) / T(2 * L.ell + 1) * (L.m > 0 ? T(2) : T(1)) * (L.part == PART_RE ? re : im);
-          }
-          const C term = cscale(a, coef);
-          if (L.ell == 0) F0 = cadd(F0, term);
-          else if (L.ell == 2) F2 = cadd(F2, term);
-          else F4 = cadd(F4, term);
+        for (int gg = 0; gg < G; ++gg) {
+          const C* fg = facc + (size_t)gg * P.nacc * N + j;
+          F0 = cadd(F0, fg[0]);
+          if (P.nacc > 1) F2 = cadd(F2, fg[N]);
+          if (P.nacc > 2) F4 = cadd(F4, fg[2 * N]);
         }
+        const T fi = fidx[j];
+        const T kk = sqrt(fi * fi + fjy * fjy + fkz * fkz);
         if (P.global_los) {
-          const T mu = ux * T(P.los[0]) + uy * T(P.los[1]) + uz * T(P.los[2]);
+          const T mu = (fi * T(P.los[0]) + fjy * T(P.los[1]) + fkz * T(P.los[2])) / kk;
           if (P.need2) F2 = cscale(F0, legendre_p<T>(2, mu));
           if (P.need4) F4 = cscale(F0, legendre_p<T>(4, mu));
         }
-        const C Fl[3] = {F0, F2, F4};
-        int s = 0;
-        for (int e = 0; e < P.nell; ++e, ++s) {
-          const C b = Fl[P.ell_list[e] / 2];
-          vals[s] = (double)(wgt * (F0.x * b.x + F0.y * b.y));
+        auto sel = [&](int l) { return l == 0 ? F0 : (l == 2 ? F2 : F4); };
+#pragma unroll
+        for (int s = 0; s < MAX_SUMS; ++s) {
+          T v = T(0);
+          if (s < P.nell) {
+            const C b = sel(P.ell_list[s]);
+            v = wgt * (F0.x * b.x + F0.y * b.y);
+          } else if (s < P.nell + P.nll) {
+            const C a = sel(P.lla[s - P.nell]), b = sel(P.llb[s - P.nell]);
+            v = wgt * (a.x * b.x + a.y * b.y);
+          } else if (s == P.nsum - 2) {
+            v = wgt;
+          } else if (s == P.nsum - 1) {
+            v = wgt * T(P.kf) * kk;
+          }
+          vals[s] = v;
         }
-        for (int e = 0; e < P.nll; ++e, ++s) {
-          const C a = Fl[P.lla[e] / 2], b = Fl[P.llb[e] / 2];
-          vals[s] = (double)(wgt * (a.x * b.x + a.y * b.y));
-        }
-        vals[P.nsum - 2] = (double)wgt;
-        vals[P.nsum - 1] = (double)wgt * P.kf * (double)kk;
       }
-      // warp-segmented inclusive scan over runs of equal bin (|k| is monotone along a warp of
-      // consecutive kx within one half of the row, so equal bins are contiguous for n >= 64)
+      // warp-segmented inclusive scan over runs of consecutive lanes with equal bin; a run is
+      // identified by the number of run heads up to this lane, so runs of the same bin that are
+      // not adjacent (a warp spanning both kx halves when n < 64) stay separate
+      const int pb = __shfl_up_sync(0xffffffffu, bin, 1);
+      const bool head = (lane == 0) || (pb != bin);
+      const unsigned heads = __ballot_sync(0xffffffffu, head);
+      const int seg = __popc(heads & (0xffffffffu >> (31 - lane)));
       unsigned addm = 0;
 #pragma unroll
       for (int st = 0; st < 5; ++st) {
         const int off = 1 << st;
-        const int ob = __shfl_up_sync(0xffffffffu, bin, off);
-        if (lane >= off && ob == bin) addm |= 1u << st;
+        const int os = __shfl_up_sync(0xffffffffu, seg, off);
+        if (lane >= off && os == seg) addm |= 1u << st;
       }
-      const int nb = __shfl_down_sync(0xffffffffu, bin, 1);
-      const bool last = (lane == 31) || (nb != bin);
-      for (int s = 0; s < P.nsum; ++s) {
-        double x = vals[s];
+      const bool last = (lane == 31) || ((heads >> (lane + 1)) & 1u);
+      // run sums over at most 32 modes stay in T; only run ends convert to float64
+#pragma unroll
+      for (int s = 0; s < MAX_SUMS; ++s) {
+        if (s >= P.nsum) break;
+        T x = vals[s];
 #pragma unroll
         for (int st = 0; st < 5; ++st) {
-          const double y = __shfl_up_sync(0xffffffffu, x, 1 << st);
-          if (addm & (1u << st)) x += y;
+          const T yv = __shfl_up_sync(0xffffffffu, x, 1 << st);
+          if (addm & (1u << st)) x += yv;
         }
-        if (last && bin >= 0) atomicAdd(mypart + (size_t)bin * P.nsum + s, x);
+        if (last && bin >= 0) atomicAdd(mypart + (size_t)bin * P.nsum + s, (double)x);
       }
     }
     __syncthreads();
@@ -305,14 +556,29 @@ struct FinalParams {
   int req_mask;          // requested P_l (bits)
 };
 
-__global__ void k_power_finalize(const double* __restrict__ part, const FinalParams F, const double* __restrict__ sc,
-                                 double* __restrict__ out) {
+constexpr int FIN_THREADS = 128;
+
+// one block per bin: the partials are summed with a fixed per-thread stride and a fixed tree
+__global__ void __launch_bounds__(FIN_THREADS)
+k_power_finalize(const double* __restrict__ part, const FinalParams F, const double* __restrict__ sc,
+                 double* __restrict__ out) {
   const int nb = F.nbins;
-  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+  __shared__ double red[MAX_SUMS][FIN_THREADS];
+  for (int b = blockIdx.x; b < nb; b += gridDim.x) {
     double S[MAX_SUMS];
-    for (int s = 0; s < F.nsum; ++s) S[s] = 0.0;
-    for (int p = 0; p < F.nparts; ++p)
+    for (int s = 0; s < MAX_SUMS; ++s) S[s] = 0.0;
+    for (int p = threadIdx.x; p < F.nparts; p += FIN_THREADS)
       for (int s = 0; s < F.nsum; ++s) S[s] += part[((size_t)p * nb + b) * F.nsum + s];
+    for (int s = 0; s < MAX_SUMS; ++s) red[s][threadIdx.x] = S[s];
+    __syncthreads();
+    for (int off = FIN_THREADS / 2; off > 0; off >>= 1) {
+      if (threadIdx.x < off)
+        for (int s = 0; s < MAX_SUMS; ++s) red[s][threadIdx.x] += red[s][threadIdx.x + off];
+      __syncthreads();
+    }
+    for (int s = 0; s < MAX_SUMS; ++s) S[s] = red[s][0];
+    __syncthreads();
+    if (threadIdx.x != 0) continue;
     const double cnt = S[F.nsum - 2];
     const double i22 = sc[SC_I22], n0 = sc[SC_N0];
     const bool ok = cnt > 0;
@@ -355,6 +621,7 @@ __global__ void k_power_finalize(const double* __restrict__ part, const FinalPar
 template <typename T, int N>
 npc_status fwd_impl(npc_ctx* ctx, const PowerPlan& plan, const Geom& g, const void* mesh_a, const void* mesh_b,
                     void* half) {
+  const int KZ = plan.kz_keep > 0 ? std::min(plan.kz_keep, N / 2) : N / 2;
   using C = cplx<T>;
   constexpr int TX = ColCfg<N>::TX;
   const void* twp;
@@ -363,18 +630,27 @@ npc_status fwd_impl(npc_ctx* ctx, const PowerPlan& plan, const Geom& g, const vo
   const YNorm nrm = ylm_norm_table();
   {
     const size_t smem = sizeof(C) * (N + N * TX) + sizeof(T) * 2 * N * TX;
-    auto kern = k_fwd_z<T, N>;
-    NPC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid(N / TX, N);
-    kern<<<grid, ColCfg<N>::THREADS, smem, ctx->stream>>>((const T*)mesh_a, (const T*)mesh_b, (C*)half, plan.fl, g,
-                                                          nrm, tw);
+    const int nstd = mesh_b ? std_pairs(plan.fl) : 0;
+    if (nstd > 0) {
+      auto kern = k_fwd_z_std<T, N>;
+      NPC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      kern<<<grid, ColCfg<N>::THREADS, smem, ctx->stream>>>((const T*)mesh_a, (const T*)mesh_b, (C*)half, nstd, g,
+                                                            nrm, tw, KZ);
+    } else {
+      auto kern = k_fwd_z<T, N>;
+      NPC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      kern<<<grid, ColCfg<N>::THREADS, smem, ctx->stream>>>((const T*)mesh_a, (const T*)mesh_b, (C*)half, plan.fl,
+                                                            g, nrm, tw, KZ);
+    }
     NPC_LAUNCH(ctx);
+    NPC_TRY(stage_mark(ctx, "fft_z_weighted"));
   }
   {
     const size_t smem = sizeof(C) * (N + N * TX);
     auto kern = k_fft_cols<T, N, -1>;
     NPC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int nplanes = plan.fl.nf * (N / 2);
+    const int nplanes = plan.fl.nf * KZ;
     // planes (f, kz) are contiguous N*N blocks; y rows have stride N
     for (int p0 = 0; p0 < nplanes; p0 += 65535) {
       const int np = std::min(65535, nplanes - p0);
@@ -382,6 +658,7 @@ npc_status fwd_impl(npc_ctx* ctx, const PowerPlan& plan, const Geom& g, const vo
       kern<<<grid, ColCfg<N>::THREADS, smem, ctx->stream>>>((C*)half + (size_t)p0 * N * N, (size_t)N * N, N, tw);
       NPC_LAUNCH(ctx);
     }
+    NPC_TRY(stage_mark(ctx, "fft_y"));
   }
   return NPC_OK;
 }
@@ -397,18 +674,31 @@ npc_status contract_impl(npc_ctx* ctx, const PowerPlan& plan, const npc_mesh_spe
   ContractParams P{};
   P.nf = plan.fl.nf;
   P.nphase = plan.nphase;
-  // logical fields: pair up the per-phase copies of each (l, m, part)
-  P.nlog = 0;
+  P.ny = 0;
   for (int f = 0; f < plan.fl.nf; ++f) {
     const Comp c = plan.fl.f[f];
-    if (c.phase != 0 || c.part == PART_ZERO) continue;
-    LogicalField L;
-    L.ell = c.ell; L.m = c.m; L.part = c.part; L.idx0 = (int8_t)f; L.idx1 = -1;
-    for (int f2 = 0; f2 < plan.fl.nf; ++f2) {
-      const Comp d = plan.fl.f[f2];
-      if (d.phase == 1 && d.ell == c.ell && d.m == c.m && d.part == c.part) L.idx1 = (int8_t)f2;
+    FieldCoef fc;
+    fc.acc = (int8_t)(c.ell / 2);
+    fc.phase = c.phase;
+    fc.part = c.part;
+    fc.yidx = -1;
+    fc.scale_d = 1.0;
+    fc.scale_f = 1.0f;
+    if (c.part == PART_RE || c.part == PART_IM) {
+      int j = -1;
+      for (int q = 0; q < P.ny; ++q)
+        if (P.yl[q] == c.ell && P.ym[q] == c.m) j = q;
+      if (j < 0) {
+        if (P.ny >= MAX_YTAB) return set_err(ctx, NPC_ERR_UNSUPPORTED, "too many Y_lm fields");
+        j = P.ny++;
+        P.yl[j] = c.ell;
+        P.ym[j] = c.m;
+      }
+      fc.yidx = (int8_t)j;
+      fc.scale_d = 4.0 * M_PI / (2 * c.ell + 1) * (c.m > 0 ? 2.0 : 1.0);
+      fc.scale_f = (float)fc.scale_d;
     }
-    P.lf[P.nlog++] = L;
+    P.fc[f] = fc;
   }
   P.nbins = kb.nbins;
   P.nell = 0;
@@ -423,13 +713,16 @@ npc_status contract_impl(npc_ctx* ctx, const PowerPlan& plan, const npc_mesh_spe
   P.nsum = P.nell + P.nll + 2;
   P.need2 = (req_internal & 4) ? 1 : 0;
   P.need4 = (req_internal & 16) ? 1 : 0;
+  P.nacc = plan.global_los ? 1 : (P.need4 ? 3 : (P.need2 ? 2 : 1));
   P.global_los = plan.global_los;
-  for (int a = 0; a < 3; ++a) P.los[a] = (float)plan.los[a];
+  for (int a = 0; a < 3; ++a) P.los[a] = plan.los[a];
   P.assign = plan.assign;
   P.kf = 2.0 * M_PI / m.box;
 
   constexpr int NP = row_pad_len<N>();
-  const size_t smem = sizeof(C) * (2 * N) + sizeof(T) * (N / 2 + 2) + sizeof(C) * (size_t)(P.nf + 1) * NP;
+  constexpr int G = XCfg<N>::G;
+  const size_t smem = sizeof(C) * ((size_t)2 * N + (size_t)P.ny * N + (size_t)G * P.nacc * N + (size_t)G * NP) +
+                      sizeof(T) * (N / 2 + 2 + 2 * N);
   auto kern = k_fft_x_contract<T, N>;
   NPC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
@@ -442,9 +735,11 @@ npc_status contract_impl(npc_ctx* ctx, const PowerPlan& plan, const npc_mesh_spe
   double* part;
   NPC_TRY(ws_get(ctx, "power.part", sizeof(double) * nparts * P.nbins * P.nsum, (void**)&part));
   NPC_CUDA(ctx, cudaMemsetAsync(part, 0, sizeof(double) * nparts * P.nbins * P.nsum, ctx->stream));
+  NPC_TRY(stage_mark(ctx, "contract_setup"));
   kern<<<grid, CONTRACT_THREADS, smem, ctx->stream>>>((const C*)half, P, ylm_norm_table(), bintab, (const C*)twp,
                                                       part);
   NPC_LAUNCH(ctx);
+  NPC_TRY(stage_mark(ctx, "fft_x_contract"));
 
   FinalParams F{};
   F.nbins = P.nbins;
@@ -461,9 +756,9 @@ npc_status contract_impl(npc_ctx* ctx, const PowerPlan& plan, const npc_mesh_spe
   for (int l = 0; l <= 4; l += 2) nreq += (plan.ells_mask >> l) & 1;
   F.out_rows = 2 + nreq + F.nmod;
   F.req_mask = plan.ells_mask;
-  const int fb = (P.nbins + 127) / 128;
-  k_power_finalize<<<fb, 128, 0, ctx->stream>>>(part, F, sc, dev_out);
+  k_power_finalize<<<std::min(P.nbins, 1024), FIN_THREADS, 0, ctx->stream>>>(part, F, sc, dev_out);
   NPC_LAUNCH(ctx);
+  NPC_TRY(stage_mark(ctx, "finalize"));
   return NPC_OK;
 }
 

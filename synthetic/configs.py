@@ -17,6 +17,12 @@ WORKLOADS = {
         n_ran=20_000_000, n_gen=256, fkp_p0=1.0e4, kmin=0.0, dk=0.01, nbins=80, ells=(0, 2, 4),
         modified=(4, 6, 8), precision="mixed", seed=1000,
     ),
+    # The 512^3 power workload scaled to 256^3 (1/8 of the objects, same box): profiling size.
+    "p024b_mixed_256": dict(
+        kind="power", n=256, box=2000.0, distance=2500.0, assign=3, interlace=1, n_gal=250_000,
+        n_ran=2_500_000, n_gen=128, fkp_p0=1.0e4, kmin=0.0, dk=0.01, nbins=40, ells=(0, 2, 4),
+        modified=(4, 6, 8), precision="mixed", seed=1000,
+    ),
     # Scoccimarro B0,B2 + compressed B_000, B_202 with analytic shot noise, periodic 256^3 TSC.
     "bispec_256": dict(
         kind="bispec", n=256, box=1000.0, assign=3, interlace=1, n_gal=1_000_000, n_gen=256,
