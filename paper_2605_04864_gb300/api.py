@@ -182,3 +182,65 @@ def stage_times(device=0, cap=64):
     B.check(B.npc_stage_times(ctx, names, ms, nl, cap, C.byref(n)), ctx)
     raw = names.raw
     return [(raw[32 * i:32 * i + 32].split(b"\0")[0].decode(), ms[i], nl[i]) for i in range(n.value)]
+
+
+def bispectrum(data, n, box, kbins, scoc_ells=(0, 2), tripo_ells=(0, 2), shot=True, assign=3, interlace=1,
+               los_dir=(0.0, 0.0, 1.0), precision="mixed", origin=(0.0, 0.0, 0.0), device=0, out=None):
+    """Scoccimarro B_l and compressed B_l0l (periodic box, global line of sight)."""
+    keep = _Keep()
+    spec = make_spec(n, box, origin, assign, interlace, 1, los_dir)
+    kb = B.npc_kbins(float(kbins[0]), float(kbins[1]), int(kbins[2]))
+    sm = sum(1 << int(l) for l in scoc_ells)
+    tm = sum(1 << int(l) for l in tripo_ells)
+    ntri, npair, length = C.c_int64(), C.c_int64(), C.c_int64()
+    st = B.npc_bispectrum_layout(C.byref(kb), sm, tm, C.byref(ntri), C.byref(npair), C.byref(length))
+    d = make_catalog(data, keep)
+    ctx = context(device)
+    if out is not None:
+        B.check(B.npc_bispectrum(ctx, C.byref(spec), C.byref(d), None, C.byref(kb), sm, tm, int(shot),
+                                 _prec(precision), C.c_void_p(out.data_ptr()), 1), ctx)
+        return out
+    buf = np.zeros(max(length.value, 1) if st == 0 else 1)
+    B.check(B.npc_bispectrum(ctx, C.byref(spec), C.byref(d), None, C.byref(kb), sm, tm, int(shot),
+                             _prec(precision), buf.ctypes.data_as(C.c_void_p), 0), ctx)
+    return unpack_bispectrum(buf, kbins, scoc_ells, tripo_ells)
+
+
+def bispectrum_triangles(kbins):
+    kb = B.npc_kbins(float(kbins[0]), float(kbins[1]), int(kbins[2]))
+    n = C.c_int64()
+    B.check(B.npc_bispectrum_triangles(C.byref(kb), None, 0, C.byref(n)))
+    tri = np.zeros((n.value, 3), dtype=np.int32)
+    B.check(B.npc_bispectrum_triangles(C.byref(kb), tri.ctypes.data_as(C.POINTER(C.c_int32)), n.value, C.byref(n)))
+    return tri
+
+
+def unpack_bispectrum(buf, kbins, scoc_ells, tripo_ells):
+    kb = B.npc_kbins(float(kbins[0]), float(kbins[1]), int(kbins[2]))
+    ntri, npair = C.c_int64(), C.c_int64()
+    sm = sum(1 << int(l) for l in scoc_ells)
+    tm = sum(1 << int(l) for l in tripo_ells)
+    B.check(B.npc_bispectrum_layout(C.byref(kb), sm, tm, C.byref(ntri), C.byref(npair), None))
+    nt, npr, nb = ntri.value, npair.value, int(kbins[2])
+    buf = np.asarray(buf)
+    o = 0
+    res = {"B": {}, "shot_B": {}, "BB": {}, "shot_BB": {}}
+    for l in sorted(scoc_ells):
+        res["B"][l] = buf[o:o + nt].copy()
+        o += nt
+    for l in sorted(scoc_ells):
+        res["shot_B"][l] = buf[o:o + nt].copy()
+        o += nt
+    res["NT"] = buf[o:o + nt].copy()
+    o += nt
+    for l in sorted(tripo_ells):
+        res["BB"][l] = buf[o:o + npr].copy()
+        o += npr
+    for l in sorted(tripo_ells):
+        res["shot_BB"][l] = buf[o:o + npr].copy()
+        o += npr
+    res["nmodes"] = buf[o:o + nb].copy()
+    o += nb
+    res["scalars"] = dict(zip(("alpha", "I22", "I33", "N0", "S3", "sum_wg", "sum_wr", "sum_w2"), buf[o:o + 8]))
+    res["tri"] = bispectrum_triangles(kbins)
+    return res

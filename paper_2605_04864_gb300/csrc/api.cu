@@ -108,7 +108,8 @@ npc_status get_twiddles(npc_ctx* ctx, int n, int prec, const void** out) {
 }
 
 // bin of every integer |k|^2 = i^2+j^2+l^2 (host, float64, no contraction: -ffp-contract=off)
-npc_status get_bin_table(npc_ctx* ctx, int n, double box, const npc_kbins& kb, const int16_t** out) {
+npc_status get_bin_table(npc_ctx* ctx, int n, double box, const npc_kbins& kb, const int16_t** out, int slot) {
+  const std::string name = "bintab" + std::to_string(slot);
   std::vector<char> key;
   key_push(key, n);
   key_push(key, box);
@@ -116,7 +117,7 @@ npc_status get_bin_table(npc_ctx* ctx, int n, double box, const npc_kbins& kb, c
   key_push(key, kb.dk);
   key_push(key, kb.nbins);
   void* cached;
-  if (table_cached(ctx, "bintab", key, &cached)) {
+  if (table_cached(ctx, name, key, &cached)) {
     *out = (const int16_t*)cached;
     return NPC_OK;
   }
@@ -129,7 +130,7 @@ npc_status get_bin_table(npc_ctx* ctx, int n, double box, const npc_kbins& kb, c
     h[n2] = (n2 > 0 && b >= 0.0 && b < (double)kb.nbins) ? (int16_t)b : (int16_t)-1;
   }
   void* p;
-  NPC_TRY(ws_table(ctx, "bintab", key, h.data(), sizeof(int16_t) * h.size(), &p));
+  NPC_TRY(ws_table(ctx, name, key, h.data(), sizeof(int16_t) * h.size(), &p));
   *out = (const int16_t*)p;
   return NPC_OK;
 }
@@ -489,6 +490,79 @@ npc_status npc_power_multipoles(npc_ctx* ctx, const npc_mesh_spec* mesh, const n
   NPC_TRY(stage_mark(ctx, "paint_fold"));
   NPC_TRY(run_forward_transforms(ctx, prec, plan, g, ma, mb, half));
   NPC_TRY(run_power_contract(ctx, prec, plan, *mesh, *bins, half, sc, dev_out));
+  NPC_TRY(finish_output(ctx, dev_out, out, out_len, out_on_device));
+  NPC_TRY(stage_mark(ctx, "download"));
+  return end_call(ctx);
+}
+
+static int64_t bispec_len(const npc_kbins* bins, uint32_t sm, uint32_t tm, int64_t* ntri, int64_t* npair) {
+  bispec_counts(*bins, ntri, npair);
+  const int ns = ((sm >> 0) & 1) + ((sm >> 2) & 1);
+  const int nt = ((tm >> 0) & 1) + ((tm >> 2) & 1);
+  return 2 * ns * (*ntri) + (*ntri) + 2 * nt * (*npair) + bins->nbins + 8;
+}
+
+npc_status npc_bispectrum_layout(const npc_kbins* bins, uint32_t scoc_ell_mask, uint32_t tripo_ell_mask,
+                                 int64_t* ntri, int64_t* npairs, int64_t* out_len) {
+  if (!bins || bins->nbins < 1 || bins->nbins > 24 || !(bins->dk > 0)) return NPC_ERR_INVALID_ARG;
+  if ((scoc_ell_mask & ~5u) || (tripo_ell_mask & ~5u) || (scoc_ell_mask | tripo_ell_mask) == 0)
+    return NPC_ERR_INVALID_ARG;
+  int64_t nt = 0, np = 0;
+  const int64_t len = bispec_len(bins, scoc_ell_mask, tripo_ell_mask, &nt, &np);
+  if (ntri) *ntri = nt;
+  if (npairs) *npairs = np;
+  if (out_len) *out_len = len;
+  return NPC_OK;
+}
+
+npc_status npc_bispectrum_triangles(const npc_kbins* bins, int32_t* tri, int64_t cap, int64_t* ntri) {
+  if (!bins || !ntri || bins->nbins < 1 || bins->nbins > 24 || !(bins->dk > 0)) return NPC_ERR_INVALID_ARG;
+  return bispec_triangles(*bins, tri, cap, ntri);
+}
+
+npc_status npc_bispectrum(npc_ctx* ctx, const npc_mesh_spec* mesh, const npc_catalog* data,
+                          const npc_catalog* randoms, const npc_kbins* bins, uint32_t scoc_ell_mask,
+                          uint32_t tripo_ell_mask, int32_t shot, npc_precision prec, double* out,
+                          int32_t out_on_device) {
+  if (!ctx) return NPC_ERR_INVALID_ARG;
+  begin_call(ctx);
+  NPC_TRY(check_spec(ctx, mesh));
+  NPC_TRY(check_bins(ctx, bins));
+  if (!out) return set_err(ctx, NPC_ERR_INVALID_ARG, "out is NULL");
+  if (bins->nbins > 24) return set_err(ctx, NPC_ERR_UNSUPPORTED, "bispectrum supports at most 24 bins");
+  if ((scoc_ell_mask & ~5u) || (tripo_ell_mask & ~5u) || (scoc_ell_mask | tripo_ell_mask) == 0)
+    return set_err(ctx, NPC_ERR_INVALID_ARG, "multipole masks must use bits 0 and 2");
+  if (shot != 0 && shot != 1) return set_err(ctx, NPC_ERR_INVALID_ARG, "shot must be 0 or 1");
+  if (prec != NPC_PREC_FP64 && prec != NPC_PREC_MIXED) return set_err(ctx, NPC_ERR_INVALID_ARG, "bad precision");
+  if (!mesh->periodic || mesh->los != 1 || randoms)
+    return set_err(ctx, NPC_ERR_UNSUPPORTED, "bispectrum: periodic box with a global line of sight only");
+  const double kf = 2.0 * M_PI / mesh->box;
+  const double knyq = kf * mesh->n / 2.0;
+  const double kmax = bins->kmin + bins->nbins * bins->dk;
+  if (kmax > 0.5 * knyq)
+    return set_err(ctx, NPC_ERR_UNSUPPORTED, "largest bin edge %.4g exceeds k_N/2 = %.4g (closure would alias)", kmax,
+                   0.5 * knyq);
+  if (prec == NPC_PREC_FP64 && mesh->n > 256) return set_err(ctx, NPC_ERR_UNSUPPORTED, "FP64 precision supports n <= 256");
+  if (mesh->n > 512) return set_err(ctx, NPC_ERR_UNSUPPORTED, "bispectrum supports n <= 512");
+  NPC_TRY(check_catalog(ctx, data, "data", false));
+  if (data->n == 0) return set_err(ctx, NPC_ERR_NUMERIC, "empty data catalogue (I33 = 0)");
+  NPC_CUDA(ctx, cudaSetDevice(ctx->device));
+  int64_t ntri = 0, npair = 0;
+  const int64_t out_len = bispec_len(bins, scoc_ell_mask, tripo_ell_mask, &ntri, &npair);
+  ctx->stats.n_transforms = 1;
+  ctx->stats.n_r2c_equivalent = 1;
+  ctx->stats.n_phases = mesh->interlace ? 2 : 1;
+  DevCatalog d;
+  NPC_TRY(stage_catalog(ctx, data, "data", &d));
+  double* sc;
+  NPC_TRY(ws_get(ctx, "scalars", sizeof(double) * SC_COUNT, (void**)&sc));
+  NPC_TRY(stage_mark(ctx, "upload"));
+  NPC_TRY(launch_catalog_scalars(ctx, d, nullptr, mesh->box, sc));
+  NPC_TRY(stage_mark(ctx, "scalars"));
+  double* dev_out = out;
+  if (!out_on_device) NPC_TRY(ws_get(ctx, "bis.out", sizeof(double) * out_len, (void**)&dev_out));
+  NPC_TRY(run_bispectrum(ctx, *mesh, *bins, (int)scoc_ell_mask, (int)tripo_ell_mask, shot, prec, d, sc, dev_out,
+                         out_len));
   NPC_TRY(finish_output(ctx, dev_out, out, out_len, out_on_device));
   NPC_TRY(stage_mark(ctx, "download"));
   return end_call(ctx);

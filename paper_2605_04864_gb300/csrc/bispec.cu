@@ -412,7 +412,7 @@ k_triple(const T* __restrict__ R, const TripleArgs A, const int* __restrict__ pa
   const int64_t end = min(A.ncell, beg + per);
   const bool same_bc = A.bb == A.cb;
   for (int64_t c0 = beg; c0 < end; c0 += TRI_CHUNK) {
-    const int nc = (int)min<int64_t>(TRI_CHUNK, end - c0);
+    const int nc = (int)((end - c0) < (int64_t)TRI_CHUNK ? (end - c0) : (int64_t)TRI_CHUNK);
     __syncthreads();
     // stage: slots 0..nb-1 A1, nb..2nb-1 A2, 2nb..2nb+ng-1 G, then B (and C if different)
     const int nA = nb * (A.a2 >= 0 ? 2 : 1);
@@ -488,6 +488,7 @@ struct FinalArgs {
   int shot;
   int nparts;           // CTAs of the triple kernel
   int slots_main;       // slots per pair in the data launch
+  int has2;             // B_2 slots present (nb .. 2nb-1)
   int slots_nt;         // slots per pair in the indicator launch
   int64_t ncell;
   double kmin, dk;
@@ -529,7 +530,7 @@ __global__ void k_bispec_finalize(const int* __restrict__ tri, const int* __rest
     for (int c = 0; c < F.nparts; ++c) {
       const double* rec = part_main + ((size_t)c * F.npair + p) * F.slots_main;
       s0 += rec[k];
-      if (F.slots_main >= 2 * nb) s2 += rec[nb + k];
+      if (F.has2) s2 += rec[nb + k];
     }
     snt = nt_sums[(size_t)p * nb + k];
     out[oNT + t] = snt / (double)F.ncell;
@@ -920,6 +921,7 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
   fa.shot = shot;
   fa.nparts = grid;
   fa.slots_main = ta.nslots;
+  fa.has2 = want2 ? 1 : 0;
   fa.ncell = (int64_t)ncell;
   fa.kmin = kb.kmin;
   fa.dk = kb.dk;

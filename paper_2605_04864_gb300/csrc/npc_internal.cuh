@@ -262,6 +262,14 @@ npc_status run_power_contract(npc_ctx* ctx, int prec, const PowerPlan& plan, con
                               double* dev_out);
 
 // bin table: int16 per integer |k|^2 in [0, 3 (n/2)^2]
-npc_status get_bin_table(npc_ctx* ctx, int n, double box, const npc_kbins& kb, const int16_t** out);
+npc_status get_bin_table(npc_ctx* ctx, int n, double box, const npc_kbins& kb, const int16_t** out, int slot = 0);
 // twiddle table exp(-2 pi i j / n), j < n, as cplx<T>
 npc_status get_twiddles(npc_ctx* ctx, int n, int prec, const void** out);
+
+// ---------------------------------------------------------------------------------------------
+// Bispectrum (bispec.cu)
+// ---------------------------------------------------------------------------------------------
+npc_status run_bispectrum(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb, int scoc_mask, int tripo_mask,
+                          int shot, int prec, const DevCatalog& d, double* sc, double* out, int64_t len);
+int64_t bispec_counts(const npc_kbins& kb, int64_t* ntri, int64_t* npair);
+npc_status bispec_triangles(const npc_kbins& kb, int32_t* tri, int64_t cap, int64_t* ntri);

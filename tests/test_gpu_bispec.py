@@ -1,0 +1,131 @@
+"""GPU parity: npc_bispectrum (through the C ABI) against the FP64 oracle."""
+import numpy as np
+import pytest
+
+from helpers import ensure_built
+from oracle import bispec as OB
+from synthetic import make_periodic_catalog, workload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    ensure_built()
+    from paper_2605_04864_gb300 import api as A
+
+    return A
+
+
+def _spec(n, box, assign=3, interlace=1):
+    return dict(n=n, box=box, origin=(0.0, 0.0, 0.0), assign=assign, interlace=interlace, los="global",
+                los_dir=(0.0, 0.0, 1.0), periodic=1)
+
+
+def _check(res, orc, tol):
+    """Error relative to the monopole + shot-noise scale of the same triangle / pair."""
+    np.testing.assert_array_equal(res["tri"], orc["tri"])
+    np.testing.assert_allclose(res["NT"], orc["NT"], rtol=max(tol, 1e-9) * 10, atol=1e-6)
+    # the oracle reports raw estimates and the analytic shot noise separately; the library
+    # reports the subtracted estimate and the shot noise
+    scale_t = np.abs(orc["B"][0]) + np.abs(orc["shot_B"][0])
+    for l in orc["B"]:
+        raw_g = res["B"][l] + res["shot_B"][l]
+        raw_o = orc["B"][l]
+        e = np.abs(raw_g - raw_o) / np.maximum(np.abs(raw_o), scale_t)
+        assert np.max(e) < tol, ("B", l, np.max(e))
+        e = np.abs(res["shot_B"][l] - orc["shot_B"][l]) / np.maximum(np.abs(orc["shot_B"][l]), scale_t)
+        assert np.max(e) < tol, ("shot_B", l, np.max(e))
+    scale_p = np.abs(orc["BB"][0]) + np.abs(orc["shot_BB"][0])
+    for l in orc["BB"]:
+        raw_g = res["BB"][l] + res["shot_BB"][l]
+        raw_o = orc["BB"][l]
+        e = np.abs(raw_g - raw_o) / np.maximum(np.abs(raw_o), scale_p)
+        assert np.max(e) < tol, ("BB", l, np.max(e))
+        e = np.abs(res["shot_BB"][l] - orc["shot_BB"][l]) / np.maximum(np.abs(orc["shot_BB"][l]), scale_p)
+        assert np.max(e) < tol, ("shot_BB", l, np.max(e))
+
+
+@pytest.mark.parametrize("assign,interlace", [(3, 1), (2, 0)])
+def test_fp64_small_periodic(api, assign, interlace):
+    cat = make_periodic_catalog(20000, 300.0, 32, seed=41)
+    kb = (0.02, 0.02, 5)   # k_max = 0.12 < k_N/2 = 0.168
+    res = api.bispectrum(cat, n=32, box=300.0, kbins=kb, assign=assign, interlace=interlace, precision="fp64")
+    orc = OB.bispectrum(_spec(32, 300.0, assign, interlace), cat, None, kb, (0, 2), (0, 2), shot=True)
+    _check(res, orc, 1e-10)
+
+
+def test_mixed_19_bins_805_triangles_128(api):
+    """The 19-bin / 805-triangle layout of the 256^3 workload on a 128^3 mesh of the same box
+    (k_max = 0.2 = k_N/2), float32 transforms: <= 1e-4."""
+    w = workload("bispec_256")
+    cat = make_periodic_catalog(w["n_gal"] // 8, w["box"], 128, seed=w["seed"])
+    kb = (w["kmin"], w["dk"], w["nbins"])
+    res = api.bispectrum(cat, n=128, box=w["box"], kbins=kb, precision="mixed")
+    assert res["tri"].shape == (805, 3)
+    orc = OB.bispectrum(_spec(128, w["box"]), cat, None, kb, (0, 2), (0, 2), shot=True)
+    _check(res, orc, 1e-4)
+
+
+def test_subsets_and_repeat(api):
+    cat = make_periodic_catalog(30000, 400.0, 32, seed=5)
+    kb = (0.015, 0.025, 4)
+    a = api.bispectrum(cat, n=64, box=400.0, kbins=kb, scoc_ells=(0,), tripo_ells=(2,), shot=False, precision="fp64")
+    b = api.bispectrum(cat, n=64, box=400.0, kbins=kb, scoc_ells=(0,), tripo_ells=(2,), shot=False, precision="fp64")
+    np.testing.assert_array_equal(a["B"][0], b["B"][0])
+    orc = OB.bispectrum(_spec(64, 400.0), cat, None, kb, (0,), (2,), shot=False)
+    scale = np.abs(orc["B"][0])
+    assert np.max(np.abs(a["B"][0] - orc["B"][0]) / scale.max()) < 1e-10
+    assert np.max(np.abs(a["BB"][2] - orc["BB"][2]) / np.abs(orc["BB"][2]).max()) < 1e-10
+    assert np.all(a["shot_B"][0] == 0)
+
+
+def test_bispectrum_rejects(api):
+    from paper_2605_04864_gb300 import binding as B
+
+    cat = make_periodic_catalog(1000, 300.0, 16, seed=2)
+    with pytest.raises(B.NpcError) as ei:        # k_max beyond k_N/2
+        api.bispectrum(cat, n=32, box=300.0, kbins=(0.02, 0.05, 5))
+    assert ei.value.status == 4
+    with pytest.raises(B.NpcError) as ei:        # odd multipole
+        api.bispectrum(cat, n=32, box=300.0, kbins=(0.02, 0.02, 4), scoc_ells=(1,))
+    assert ei.value.status == 1
+
+
+@pytest.mark.slow
+def test_full_size_256_sampled_triangles(api):
+    """Full 256^3 workload (1e6 particles, 19 bins): B_0, B_2 and N_T of a few triangles the oracle
+    computes one by one from its own shell fields."""
+    w = workload("bispec_256")
+    cat = make_periodic_catalog(w["n_gal"], w["box"], w["n_gen"], seed=w["seed"])
+    kb = (w["kmin"], w["dk"], w["nbins"])
+    res = api.bispectrum(cat, n=256, box=w["box"], kbins=kb, precision="mixed")
+    spec = _spec(256, w["box"])
+    from oracle import power as P
+
+    sc = P.catalog_scalars(cat, None, w["box"])
+    meshes = P.fkp_meshes(spec, cat, None, sc)
+    X0 = P.fields_plain(spec, meshes, [0])[0][0]
+    del meshes
+    tri = res["tri"]
+    picks = [0, len(tri) // 2, len(tri) - 1]
+    bins = sorted({int(b) for t in picks for b in tri[t]})
+    from oracle import mesh as M
+
+    b_idx, _ = M.bin_index(256, w["box"], *kb)
+    X2 = OB.los_field(spec, X0, 2)
+    f0, f2, ind = {}, {}, {}
+    for b in bins:
+        mask = b_idx == b
+        f0[b] = np.real(np.fft.ifftn(np.where(mask, X0, 0))) * 256**3
+        f2[b] = np.real(np.fft.ifftn(np.where(mask, X2, 0))) * 256**3
+        ind[b] = np.real(np.fft.ifftn(mask.astype(float))) * 256**3
+    for t in picks:
+        i, j, k = (int(v) for v in tri[t])
+        nt = np.sum(ind[i] * ind[j] * ind[k])
+        b0 = np.sum(f0[i] * f0[j] * f0[k]) / (sc["I33"] * nt)
+        b2 = 5 * np.sum(f2[i] * f0[j] * f0[k]) / (sc["I33"] * nt)
+        assert res["NT"][t] == pytest.approx(nt / 256**3, rel=1e-5)
+        scale = abs(b0)
+        assert abs(res["B"][0][t] + res["shot_B"][0][t] - b0) < 1e-4 * max(abs(b0), scale)
+        assert abs(res["B"][2][t] + res["shot_B"][2][t] - b2) < 1e-4 * max(abs(b2), scale)
