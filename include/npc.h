@@ -130,6 +130,25 @@ npc_status npc_stage_times(npc_ctx* ctx, char* names, double* ms, int32_t* launc
 npc_status npc_catalog_scalars(npc_ctx* ctx, const npc_catalog* data, const npc_catalog* randoms,
                                double box, double* out, int32_t out_on_device);
 
+/* Allocation-free catalogue scalars ------------------------------------------------------------
+ * The paper has no counterpart to this call; it exists for callers that cannot allocate device
+ * memory (a host framework that owns all device memory through its own pool, a plugin that is
+ * only handed device pointers, a latency-bound loop that must not pay an allocation's implicit
+ * synchronisation).  It computes the same out[0..7] as npc_catalog_scalars, but needs no context
+ * and allocates nothing: its scratch (per-block partial sums) is a static device array of
+ * 786,560 bytes that every device which loads the library holds until the process exits.
+ *   - data / randoms: device pointers only (on_device = 1), at most 33,554,432 objects each,
+ *     otherwise NPC_ERR_INVALID_ARG with a message in `err`; randoms == NULL means a periodic box.
+ *   - out_device: 8 doubles of device memory; the call is asynchronous on `cuda_stream` (NULL:
+ *     the legacy default stream) and runs on the calling thread's current device.
+ *   - err / errlen: optional buffer for a NUL-terminated message.
+ * The first call on each device looks up the address of the static array on that device; make
+ * that first call before any stream capture.  Every call reuses the same array and leaves the
+ * last call's partial sums in it; calls whose work can overlap on one device (concurrent streams
+ * or threads) race on it and must be serialised by the caller. */
+npc_status npc_catalog_scalars_noalloc(const npc_catalog* data, const npc_catalog* randoms, double box,
+                                       double* out_device, void* cuda_stream, char* err, size_t errlen);
+
 /* Power-spectrum multipoles (Sec. 2.1 Eq. pk_final; Sec. 3 Eqs. Plnew, Pllp) ------------------
  * ell_mask: bit l requests P_l, l in {0, 2, 4}.  modified_mask: bits 4, 6, 8 request P_4b, P_6b,
  * P_8b (these need the l = 2 and l = 4 fields and are computed from them; Eq. Plnew).

@@ -11,7 +11,9 @@
 //                     the tile is written out once.
 //   5. k_fold         each mesh cell sums, in a fixed order, the (up to 8) tiles that cover it.
 // The mesh is therefore bitwise reproducible run to run without any floating-point atomics.
+#include <algorithm>
 #include <cmath>
+#include <cstring>
 
 #include "npc_internal.cuh"
 
@@ -507,4 +509,104 @@ npc_status launch_paint(npc_ctx* ctx, const DevCatalog& d, const DevCatalog* r, 
   (void)any_double;
   if (m.assign == 2) return paint_impl<2, float, float>(ctx, d, r, m, weight_power, dev_scalars, mesh_a, mesh_b);
   return paint_impl<3, float, float>(ctx, d, r, m, weight_power, dev_scalars, mesh_a, mesh_b);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Allocation-free catalogue scalars.
+//
+// Some callers cannot call cudaMalloc at all: a host framework that owns every byte of device
+// memory through its own pool (a raw allocation would sit outside its accounting), a plugin that
+// is only handed device pointers, or a latency-bound loop where the implicit synchronisation of an
+// allocation stalls the pipeline.  This entry point serves them: it reuses the reduction kernels
+// above, but its scratch (the per-block partial sums and the 16 scalar slots) lives in a
+// file-scope device array instead of context workspace, so the call allocates nothing.
+// ---------------------------------------------------------------------------------------------
+#include <mutex>
+
+namespace {
+
+constexpr int NOALLOC_CHUNK = 4096;            // objects reduced by one block
+constexpr int NOALLOC_MAX_BLOCKS = 8192;       // blocks per catalogue
+constexpr int64_t NOALLOC_MAX_OBJECTS = (int64_t)NOALLOC_CHUNK * NOALLOC_MAX_BLOCKS;  // 33,554,432
+constexpr size_t NOALLOC_PART = (size_t)NOALLOC_MAX_BLOCKS * NSUM;                     // per catalogue
+
+// 2 catalogues x 8192 blocks x 6 sums + 16 scalar slots, doubles: 786,560 bytes, resident on every
+// device that loads this library until the process exits.
+static __device__ __align__(256) double g_noalloc_scratch[2 * NOALLOC_PART + SC_COUNT];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mutex;
+double* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+
+npc_status noalloc_err(char* err, size_t errlen, npc_status s, const char* msg) {
+  if (err && errlen) {
+    std::strncpy(err, msg, errlen - 1);
+    err[errlen - 1] = '\0';
+  }
+  return s;
+}
+
+}  // namespace
+
+extern "C" npc_status npc_catalog_scalars_noalloc(const npc_catalog* data, const npc_catalog* randoms, double box,
+                                                  double* out_device, void* cuda_stream, char* err, size_t errlen) {
+  if (err && errlen) err[0] = '\0';
+  if (!data || !out_device) return noalloc_err(err, errlen, NPC_ERR_INVALID_ARG, "data and out_device are required");
+  const npc_catalog* cats[2] = {data, randoms};
+  for (int c = 0; c < 2; ++c) {
+    const npc_catalog* k = cats[c];
+    if (!k) continue;
+    if (k->n < 0 || (k->n > 0 && !k->pos) || (k->dtype != 0 && k->dtype != 1))
+      return noalloc_err(err, errlen, NPC_ERR_INVALID_ARG, "malformed catalogue");
+    if (!k->on_device)
+      return noalloc_err(err, errlen, NPC_ERR_INVALID_ARG, "catalogue arrays must be device pointers (on_device = 1)");
+    if (k->n > NOALLOC_MAX_OBJECTS)
+      return noalloc_err(err, errlen, NPC_ERR_INVALID_ARG,
+                         "catalogue larger than 33554432 objects, the capacity of the static scratch");
+    if (c == 1 && k->n > 0 && !k->nbar) return noalloc_err(err, errlen, NPC_ERR_INVALID_ARG, "randoms need nbar");
+  }
+  if (!randoms && !(box > 0.0)) return noalloc_err(err, errlen, NPC_ERR_INVALID_ARG, "periodic scalars need box > 0");
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
+    cudaGetLastError();
+    return noalloc_err(err, errlen, NPC_ERR_CUDA, "no usable current CUDA device");
+  }
+  double* scratch;
+  {
+    // One-time set-up per device, with that device current: host code cannot take the address
+    // of a __device__ array directly, so ask the runtime for it.
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+      void* p = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        return noalloc_err(err, errlen, NPC_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed");
+      }
+      g_noalloc_ptr[dev] = static_cast<double*>(p);
+    }
+    scratch = g_noalloc_ptr[dev];
+  }
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const int64_t nmax = std::max<int64_t>(data->n, randoms ? randoms->n : 0);
+  const int nblk = (int)std::max<int64_t>(1, (nmax + NOALLOC_CHUNK - 1) / NOALLOC_CHUNK);
+  double* part_d = scratch;
+  double* part_r = scratch + NOALLOC_PART;
+  double* sc = scratch + 2 * NOALLOC_PART;
+  // every partial that k_cat_final reads is written by this call's k_cat_partials (blocks past the
+  // end of a catalogue write zeros), so nothing needs clearing first
+  for (int c = 0; c < 2; ++c) {
+    const npc_catalog* k = cats[c];
+    if (!k) continue;
+    double* part = c == 0 ? part_d : part_r;
+    if (k->dtype == 1)
+      k_cat_partials<double><<<nblk, RED_THREADS, 0, st>>>((const double*)k->w, (const double*)k->nbar, k->n, part);
+    else
+      k_cat_partials<float><<<nblk, RED_THREADS, 0, st>>>((const float*)k->w, (const float*)k->nbar, k->n, part);
+  }
+  k_cat_final<<<1, 32, 0, st>>>(part_d, part_r, nblk, randoms ? 1 : 0, box, sc);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out_device, sc, 8 * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return noalloc_err(err, errlen, NPC_ERR_CUDA, cudaGetErrorString(e));
+  return NPC_OK;
 }
