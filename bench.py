@@ -194,6 +194,63 @@ def run_reference(args, w):
     print(json.dumps(line), flush=True)
 
 
+def bispec_leg(args, world, rank, barrier, max_over_ranks):
+    """B_l triangles/s at 256^3: 1e6 lognormal particles, periodic, TSC interlaced, 19 bins,
+    805 closed triangles, B_0 and B_2 (plus the compressed B_000, B_202) with analytic shot noise."""
+    import ctypes as C
+    from types import SimpleNamespace
+
+    import torch
+
+    from paper_2605_04864_gb300 import api
+    from paper_2605_04864_gb300 import binding as B
+    from synthetic import make_periodic_catalog, workload
+
+    w = workload("bispec_256")
+    cat = make_periodic_catalog(w["n_gal"], w["box"], w["n_gen"], seed=w["seed"] + rank)
+    cd = SimpleNamespace(pos=torch.from_numpy(cat.pos).cuda(), w=torch.from_numpy(cat.w).cuda(),
+                         nbar=torch.from_numpy(cat.nbar).cuda())
+    kb = (w["kmin"], w["dk"], w["nbins"])
+    kbs = B.npc_kbins(*kb)
+    ntri, npair, length = C.c_int64(), C.c_int64(), C.c_int64()
+    B.check(B.npc_bispectrum_layout(C.byref(kbs), 5, 5, C.byref(ntri), C.byref(npair), C.byref(length)))
+    out = torch.zeros(length.value, dtype=torch.float64, device="cuda")
+    kw = dict(n=w["n"], box=w["box"], kbins=kb, scoc_ells=w["scoc_ells"], tripo_ells=w["tripo_ells"], shot=True,
+              precision=w["precision"], out=out)
+    for _ in range(args.warmup):
+        api.bispectrum(cd, **kw)
+    torch.cuda.synchronize()
+    launches = api.last_stats()["n_kernel_launches"]
+    barrier()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(args.steps):
+        api.bispectrum(cd, **kw)
+    e.record()
+    torch.cuda.synchronize()
+    barrier()
+    ms = max_over_ranks(s.elapsed_time(e)) / args.steps
+    nmult = len(w["scoc_ells"])
+    api.set_profiling(True)
+    acc = {}
+    for _ in range(args.steps):
+        api.bispectrum(cd, **kw)
+        for name, t, nl in api.stage_times():
+            a = acc.setdefault(name, [0.0, 0, 0])
+            a[0] += t
+            a[1] += nl
+            a[2] += 1
+    api.set_profiling(False)
+    stages = {k: round(v[0] / v[2], 4) for k, v in acc.items()}
+    return {"metric": "B_l triangles/s @256^3 (805 closed triangles x B_0, B_2; + B_000, B_202, shot noise)",
+            "value": world * ntri.value * nmult / (ms / 1e3), "unit": "triangles/s", "ms_per_step": ms,
+            "measurements_per_s": world / (ms / 1e3), "triangles": ntri.value, "pairs": npair.value,
+            "config": {"workload": "bispec_256", "mesh": w["n"], "n_gal": w["n_gal"], "nbins": w["nbins"],
+                       "assign": "TSC", "interlace": True},
+            "stages_ms": stages, "gpu_launches": launches * args.steps,
+            "triple_product": "3xTF32 split hi+lo tensor-core products (mma.sync m16n8k8), FP32 within 128-cell chunks, FP64 across chunks"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -202,6 +259,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD, help="power workload name (profiling uses a smaller one)")
+    ap.add_argument("--no-bispec", action="store_true", help="skip the 256^3 bispectrum leg")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -333,6 +391,8 @@ def main():
     e2e = {"value": world * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
            "ms_per_step": e2e_s / args.steps * 1e3}
 
+    secondary = None if args.no_bispec else bispec_leg(args, world, rank, barrier, max_over_ranks)
+
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 transforms, f64 accumulators", "data": "synthetic",
@@ -343,6 +403,9 @@ def main():
                        "l2": "inputs larger than L2 (catalogues 440 MB, meshes 2x537 MB, spectra 16 GB)"},
             "roofline": roofline, "stages_ms": stages, "e2e": e2e, "gpu_launches": launches * args.steps,
             "clocks": clocks}
+    if secondary is not None:
+        line["secondary"] = secondary
+        line["gpu_launches"] += secondary["gpu_launches"]
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         dt, scale, desc = cpu_baseline(w)
         line["cpu_baseline"] = {"value": 1.0 / (dt * scale), "unit": UNIT, "cores": 1, "kind": "oracle",

@@ -375,98 +375,191 @@ k_shell_z(const cplx<T>* __restrict__ T2, const ShellField* __restrict__ fields,
 }
 
 // ------------------------------------------------------------------------------------------
-// 5. triple products over cells.  Thread = pair (i <= j).  Per cell: p_a = A1_i B_j (and
-//    p_b = A2_i B_j), s[k] += p C_k for every k, g[l] += p_a G_l.  Float sums over a chunk of
-//    cells, float64 accumulation per chunk in shared memory, per-CTA partials.
+// 5. triple products over cells as a dense contraction on the tensor cores:
+//      D[row, col] = sum_x P[row, x] C[x, col],  P[row, x] = A_i(x) B_j(x) for the pair (i, j) of the
+//      row (two row families: A = F_0 or A = F_2, B = F_0), C[x, col] = F_0,k(x) for col = k < nb
+//      and G^(l)(x) for the compressed estimator columns.  M = rows (<= 384 per CTA row group), N =
+//      32 columns (4 tiles of 8), K = cells in steps of 8.  Operands are split into TF32 hi + lo
+//      parts and multiplied as hi*hi + hi*lo + lo*hi (mma.sync m16n8k8, FP32 accumulation), which
+//      keeps about 21 bits of each product; FP32 accumulators are added into FP64 every FLUSH
+//      chunks and the per-CTA FP64 partials are reduced in a fixed order by the finalize kernel.
 // ------------------------------------------------------------------------------------------
-constexpr int TRI_CHUNK = 128;
 constexpr int NB_MAX = 24;
+constexpr int TRI_CHUNK = 256;          // cells staged per chunk
+constexpr int TRI_FLUSH = 16;           // chunks between FP64 flushes
+constexpr int TRI_WARPS = 8;
+constexpr int TRI_MT = 3;               // m tiles (16 rows) per warp -> 384 rows per CTA
+constexpr int TRI_NT = 4;               // n tiles (8 cols) -> 32 columns
+constexpr int TRI_ROWS = TRI_WARPS * TRI_MT * 16;
+constexpr int TRI_COLS = TRI_NT * 8;
+constexpr int TRI_SPAD = TRI_CHUNK + 8; // staging row stride (floats)
 
 struct TripleArgs {
-  int nb;          // bins
+  int nrows;        // pair rows over all families (family f, pair p) -> row f * npair + p
   int npair;
-  int a1, a2;      // field index base of A1 (and A2, -1 if none) families in R
-  int bb, cb;      // field index base of B and C families
-  int ng;          // G fields (0..2) at index gbase
-  int gbase;
-  int nslots;      // per-pair double slots = nb * (a2 >= 0 ? 2 : 1) + ng
+  int ncol;         // used columns
+  int nstage;       // distinct fields staged per chunk
+  int stage_field[2 * NB_MAX + 2];  // R index of staged slot s
+  int a_slot[2][NB_MAX];            // staged slot of A_i per family
+  int b_slot[NB_MAX];               // staged slot of B_j
+  int c_slot[TRI_COLS];             // staged slot of column c (-1: zero column)
   int64_t ncell;
 };
 
-template <typename T>
-__global__ void __launch_bounds__(256)
-k_triple(const T* __restrict__ R, const TripleArgs A, const int* __restrict__ pair_ij, double* __restrict__ part) {
+__device__ __forceinline__ uint32_t to_tf32(float v) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+  return r;
+}
+
+__device__ __forceinline__ void split_tf32(float v, uint32_t& hi, uint32_t& lo) {
+  hi = to_tf32(v);
+  lo = to_tf32(v - __uint_as_float(hi));
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// grid = (cell ranges, row groups of TRI_ROWS); block = TRI_WARPS warps.
+// Fragment layouts of m16n8k8 (tf32): A a0 (row g, k t), a1 (g+8, t), a2 (g, t+4), a3 (g+8, t+4);
+// B b0 (k t, col g), b1 (k t+4, col g); D d0, d1 (row g, cols 2t, 2t+1), d2, d3 (row g+8, ...),
+// with g = lane/4 and t = lane%4.
+__global__ void __launch_bounds__(TRI_WARPS * 32, 1)
+k_triple(const float* __restrict__ R, const TripleArgs A, const int* __restrict__ pair_ij, double* __restrict__ part) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int nb = A.nb;
-  // cell-major staging: for each cell, [A1(nb) | A2(nb) | G(ng)] then B and C families
-  const int stride = 3 * NB_MAX + 2 + 1;
-  T* cells = reinterpret_cast<T*>(smem_raw);
-  double* dacc = reinterpret_cast<double*>(cells + (size_t)TRI_CHUNK * stride);  // [nslots][blockDim]
-  const int tid = threadIdx.x;
-  const bool live = tid < A.npair;
-  const int pij = live ? pair_ij[tid] : 0;
-  const int pi = pij & 0xffff, pj = pij >> 16;
-  for (int s = 0; s < A.nslots; ++s) dacc[(size_t)s * blockDim.x + tid] = 0.0;
-  const int64_t per = (A.ncell + gridDim.x - 1) / gridDim.x;
+  float* stage = reinterpret_cast<float*>(smem_raw);                               // [nstage][TRI_SPAD]
+  double* dacc = reinterpret_cast<double*>(stage + (size_t)A.nstage * TRI_SPAD);  // [tid][NACC]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  const int rowbase = blockIdx.y * TRI_ROWS + warp * TRI_MT * 16;
+  int sa[TRI_MT][2], sb[TRI_MT][2];
+#pragma unroll
+  for (int mt = 0; mt < TRI_MT; ++mt)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int r = rowbase + mt * 16 + g + 8 * h;
+      sa[mt][h] = sb[mt][h] = -1;
+      if (r < A.nrows) {
+        const int fam = r / A.npair, p = r % A.npair;
+        const int pij = pair_ij[p];
+        sa[mt][h] = A.a_slot[fam][pij & 0xffff];
+        sb[mt][h] = A.b_slot[pij >> 16];
+      }
+    }
+  int scol[TRI_NT];
+#pragma unroll
+  for (int nt = 0; nt < TRI_NT; ++nt) {
+    const int c = nt * 8 + g;
+    scol[nt] = c < A.ncol ? A.c_slot[c] : -1;
+  }
+  constexpr int NACC = TRI_MT * TRI_NT * 4;
+  double* myacc = dacc + (size_t)tid * NACC;
+  for (int e = 0; e < NACC; ++e) myacc[e] = 0.0;
+  float d[TRI_MT][TRI_NT][4];
+#pragma unroll
+  for (int mt = 0; mt < TRI_MT; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < TRI_NT; ++nt)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) d[mt][nt][q] = 0.f;
+  const int64_t per = ((A.ncell + gridDim.x - 1) / gridDim.x + TRI_CHUNK - 1) / TRI_CHUNK * TRI_CHUNK;
   const int64_t beg = (int64_t)blockIdx.x * per;
   const int64_t end = min(A.ncell, beg + per);
-  const bool same_bc = A.bb == A.cb;
+  int nchunk = 0;
   for (int64_t c0 = beg; c0 < end; c0 += TRI_CHUNK) {
     const int nc = (int)((end - c0) < (int64_t)TRI_CHUNK ? (end - c0) : (int64_t)TRI_CHUNK);
     __syncthreads();
-    // stage: slots 0..nb-1 A1, nb..2nb-1 A2, 2nb..2nb+ng-1 G, then B (and C if different)
-    const int nA = nb * (A.a2 >= 0 ? 2 : 1);
-    const int nload = nA + A.ng + nb + (same_bc ? 0 : nb);
-    for (int idx = tid; idx < nload * TRI_CHUNK; idx += blockDim.x) {
-      const int f = idx / TRI_CHUNK, c = idx % TRI_CHUNK;
-      int src;
-      if (f < nb) src = A.a1 + f;
-      else if (f < nA) src = A.a2 + (f - nb);
-      else if (f < nA + A.ng) src = A.gbase + (f - nA);
-      else if (f < nA + A.ng + nb) src = A.bb + (f - nA - A.ng);
-      else src = A.cb + (f - nA - A.ng - nb);
-      cells[(size_t)c * stride + f] = c < nc ? R[(size_t)src * A.ncell + c0 + c] : T(0);
+    for (int idx = tid; idx < A.nstage * TRI_CHUNK; idx += blockDim.x) {
+      const int sl = idx / TRI_CHUNK, c = idx % TRI_CHUNK;
+      stage[(size_t)sl * TRI_SPAD + c] = c < nc ? R[(size_t)A.stage_field[sl] * A.ncell + c0 + c] : 0.f;
     }
     __syncthreads();
-    T s1[NB_MAX], s2[NB_MAX], sg[2];
+    for (int kk = 0; kk < TRI_CHUNK; kk += 8) {
+      uint32_t bh[TRI_NT][2], bl[TRI_NT][2];
 #pragma unroll
-    for (int k = 0; k < NB_MAX; ++k) { s1[k] = T(0); s2[k] = T(0); }
-    sg[0] = sg[1] = T(0);
-    const int ob = nA + A.ng;            // B family offset in a cell row
-    const int oc = same_bc ? ob : ob + nb;
-    for (int c = 0; c < nc; ++c) {
-      const T* row = cells + (size_t)c * stride;
-      const T bj = row[ob + pj];
-      const T p1 = row[pi] * bj;
-      const T p2 = A.a2 >= 0 ? row[nb + pi] * bj : T(0);
+      for (int nt = 0; nt < TRI_NT; ++nt) {
+        float v0 = 0.f, v1 = 0.f;
+        if (scol[nt] >= 0) {
+          const float* col = stage + (size_t)scol[nt] * TRI_SPAD + kk;
+          v0 = col[t];
+          v1 = col[t + 4];
+        }
+        split_tf32(v0, bh[nt][0], bl[nt][0]);
+        split_tf32(v1, bh[nt][1], bl[nt][1]);
+      }
 #pragma unroll
-      for (int k = 0; k < NB_MAX; ++k) {
-        if (k < nb) {
-          const T ck = row[oc + k];
-          s1[k] += p1 * ck;
-          s2[k] += p2 * ck;
+      for (int mt = 0; mt < TRI_MT; ++mt) {
+        uint32_t ah[4], al[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int h = q & 1;
+          const int kc = kk + t + ((q >> 1) ? 4 : 0);
+          float e = 0.f;
+          if (sa[mt][h] >= 0) e = stage[(size_t)sa[mt][h] * TRI_SPAD + kc] * stage[(size_t)sb[mt][h] * TRI_SPAD + kc];
+          split_tf32(e, ah[q], al[q]);
+        }
+#pragma unroll
+        for (int nt = 0; nt < TRI_NT; ++nt) {
+          mma_tf32(d[mt][nt], ah, bh[nt][0], bh[nt][1]);
+          mma_tf32(d[mt][nt], ah, bl[nt][0], bl[nt][1]);
+          mma_tf32(d[mt][nt], al, bh[nt][0], bh[nt][1]);
         }
       }
-      if (A.ng > 0) sg[0] += p1 * row[nA];
-      if (A.ng > 1) sg[1] += p1 * row[nA + 1];
     }
-    if (live) {
-      double* d = dacc + tid;
+    if (++nchunk == TRI_FLUSH || c0 + TRI_CHUNK >= end) {
+      nchunk = 0;
+      int e = 0;
 #pragma unroll
-      for (int k = 0; k < NB_MAX; ++k)
-        if (k < nb) d[(size_t)k * blockDim.x] += (double)s1[k];
-      if (A.a2 >= 0) {
+      for (int mt = 0; mt < TRI_MT; ++mt)
 #pragma unroll
-        for (int k = 0; k < NB_MAX; ++k)
-          if (k < nb) d[(size_t)(nb + k) * blockDim.x] += (double)s2[k];
-      }
-      for (int l = 0; l < A.ng; ++l) d[(size_t)(nA + l) * blockDim.x] += (double)sg[l];
+        for (int nt = 0; nt < TRI_NT; ++nt)
+#pragma unroll
+          for (int q = 0; q < 4; ++q, ++e) {
+            myacc[e] += (double)d[mt][nt][q];
+            d[mt][nt][q] = 0.f;
+          }
     }
   }
-  __syncthreads();
-  if (live)
-    for (int s = 0; s < A.nslots; ++s)
-      part[((size_t)blockIdx.x * A.npair + tid) * A.nslots + s] = dacc[(size_t)s * blockDim.x + tid];
+  // this CTA's partial sums as part[cta][row][col]
+  int e = 0;
+#pragma unroll
+  for (int mt = 0; mt < TRI_MT; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < TRI_NT; ++nt)
+#pragma unroll
+      for (int q = 0; q < 4; ++q, ++e) {
+        const int r = rowbase + mt * 16 + g + ((q >> 1) ? 8 : 0);
+        const int c = nt * 8 + 2 * t + (q & 1);
+        if (r < A.nrows && c < A.ncol) part[((size_t)blockIdx.x * A.nrows + r) * A.ncol + c] = myacc[e];
+      }
+}
+
+// Float64 path of the same contraction (precision NPC_PREC_FP64): one thread per (row, col)
+// output over a range of cells; slow, exact to float64 rounding, for validation-size meshes.
+__global__ void __launch_bounds__(256)
+k_triple_f64(const double* __restrict__ R, const TripleArgs A, const int* __restrict__ pair_ij,
+             double* __restrict__ part) {
+  const int o = blockIdx.y * blockDim.x + threadIdx.x;
+  if (o >= A.nrows * A.ncol) return;
+  const int r = o / A.ncol, c = o % A.ncol;
+  const int fam = r / A.npair, p = r % A.npair;
+  const int pij = pair_ij[p];
+  const int cs = A.c_slot[c];
+  double acc = 0.0;
+  if (cs >= 0) {
+    const double* fa = R + (size_t)A.stage_field[A.a_slot[fam][pij & 0xffff]] * A.ncell;
+    const double* fb = R + (size_t)A.stage_field[A.b_slot[pij >> 16]] * A.ncell;
+    const double* fc = R + (size_t)A.stage_field[cs] * A.ncell;
+    const int64_t per = (A.ncell + gridDim.x - 1) / gridDim.x;
+    const int64_t beg = (int64_t)blockIdx.x * per, end = min(A.ncell, beg + per);
+    for (int64_t x = beg; x < end; ++x) acc += fa[x] * fb[x] * fc[x];
+  }
+  part[((size_t)blockIdx.x * A.nrows + r) * A.ncol + c] = acc;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -487,9 +580,9 @@ struct FinalArgs {
   int ntripo, tripo_l[2];
   int shot;
   int nparts;           // CTAs of the triple kernel
-  int slots_main;       // slots per pair in the data launch
-  int has2;             // B_2 slots present (nb .. 2nb-1)
-  int slots_nt;         // slots per pair in the indicator launch
+  int nrows;            // rows of the data launch partials (family * npair + pair)
+  int ncol;             // columns of the data launch partials (nb F_0 columns, then G columns)
+  int has2;             // rows npair .. 2 npair - 1 hold the l = 2 family
   int64_t ncell;
   double kmin, dk;
   int part_nw_cross;    // partial records of the cross-spectrum kernel
@@ -528,9 +621,8 @@ __global__ void k_bispec_finalize(const int* __restrict__ tri, const int* __rest
     p += j - i;
     double s0 = 0, s2 = 0, snt = 0;
     for (int c = 0; c < F.nparts; ++c) {
-      const double* rec = part_main + ((size_t)c * F.npair + p) * F.slots_main;
-      s0 += rec[k];
-      if (F.has2) s2 += rec[nb + k];
+      s0 += part_main[((size_t)c * F.nrows + p) * F.ncol + k];
+      if (F.has2) s2 += part_main[((size_t)c * F.nrows + F.npair + p) * F.ncol + k];
     }
     snt = nt_sums[(size_t)p * nb + k];
     out[oNT + t] = snt / (double)F.ncell;
@@ -556,7 +648,7 @@ __global__ void k_bispec_finalize(const int* __restrict__ tri, const int* __rest
     for (int e = 0; e < F.ntripo; ++e) {
       const int l = F.tripo_l[e];
       double sg = 0;
-      for (int c = 0; c < F.nparts; ++c) sg += part_main[((size_t)c * F.npair + p) * F.slots_main + F.slots_main - F.ntripo + e];
+      for (int c = 0; c < F.nparts; ++c) sg += part_main[((size_t)c * F.nrows + p) * F.ncol + nb + e];
       const double raw = (ni > 0 && nj > 0) ? (2 * l + 1) * sg / (i33 * ni * nj * (double)F.ncell) : 0.0;
       double sn = 0.0;
       if (F.shot && ni > 0 && nj > 0) {
@@ -587,22 +679,30 @@ __global__ void k_bispec_finalize(const int* __restrict__ tri, const int* __rest
 }
 
 // reduce per-warp cross partials into [bin][NCROSS] in a fixed order
+// one warp per (bin, sum): strided lane sums then a fixed shuffle tree (reproducible order)
 __global__ void k_cross_reduce(const double* __restrict__ part, int nrec, int nb, double* __restrict__ out) {
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nb * NCROSS; e += gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x / 32;
+  for (int e = blockIdx.x * wpb + (threadIdx.x >> 5); e < nb * NCROSS; e += gridDim.x * wpb) {
     double s = 0;
-    for (int r = 0; r < nrec; ++r) s += part[(size_t)r * nb * NCROSS + e];
-    out[e] = s;
+    for (int r = lane; r < nrec; r += 32) s += part[(size_t)r * nb * NCROSS + e];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if (lane == 0) out[e] = s;
   }
 }
 
 // reduce the indicator-triple partials over CTAs: nt[p][k]
+// Sum_x I_i I_j I_k = ncell * (number of closed wavevector triples q_i + q_j + q_k = 0).  With every
+// shell inside |q| <= k_N/2 no triple aliases across the grid, so the count is an exact integer and
+// the sum is rounded to ncell * round(count): this removes the rounding error of the float shell
+// fields from the normalisation whenever it is below half a triangle.
 __global__ void k_nt_reduce(const double* __restrict__ part, int nparts, int npair, int nslots, int nb,
-                            double* __restrict__ nt) {
+                            double ncell, double* __restrict__ nt) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < npair * nb; e += gridDim.x * blockDim.x) {
     const int p = e / nb, k = e % nb;
     double s = 0;
     for (int c = 0; c < nparts; ++c) s += part[((size_t)c * npair + p) * nslots + k];
-    nt[e] = s;
+    nt[e] = rint(s / ncell) * ncell;
   }
 }
 
@@ -738,9 +838,9 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
     k_bin_cross<T, N><<<grid, BT, 0, ctx->stream>>>(X, XN, KZ, K2, l3[0], l3[1], l3[2], tab_m, nb, tab_q, nq, n2cap,
                                                    part, part + np * NCROSS * nb);
     NPC_LAUNCH(ctx);
-    k_cross_reduce<<<(nb * NCROSS + 127) / 128, 128, 0, ctx->stream>>>(part, (int)np, nb, cross_m);
+    k_cross_reduce<<<(nb * NCROSS + 3) / 4, 128, 0, ctx->stream>>>(part, (int)np, nb, cross_m);
     NPC_LAUNCH(ctx);
-    k_cross_reduce<<<(nq * NCROSS + 127) / 128, 128, 0, ctx->stream>>>(part + np * NCROSS * nb, (int)np, nq, cross_q);
+    k_cross_reduce<<<(nq * NCROSS + 3) / 4, 128, 0, ctx->stream>>>(part + np * NCROSS * nb, (int)np, nq, cross_q);
     NPC_LAUNCH(ctx);
   }
   NPC_TRY(stage_mark(ctx, "shot_shells"));
@@ -868,42 +968,64 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
   NPC_TRY(stage_mark(ctx, "shell_fields"));
 
   // 5. triple products
-  const int grid = ctx->num_sms * 2;
-  const int tthreads = ((npair + 31) / 32) * 32;
-  if (npair > 1024 || nb > NB_MAX) return set_err(ctx, NPC_ERR_UNSUPPORTED, "at most %d bins", NB_MAX);
+  if (nb > NB_MAX) return set_err(ctx, NPC_ERR_UNSUPPORTED, "at most %d bins", NB_MAX);
+  auto setup = [&](TripleArgs& a, bool indicator) {
+    a = TripleArgs{};
+    a.npair = npair;
+    a.ncell = (int64_t)ncell;
+    a.nstage = 0;
+    auto stage_of = [&](int field) {
+      for (int q = 0; q < a.nstage; ++q)
+        if (a.stage_field[q] == field) return q;
+      a.stage_field[a.nstage] = field;
+      return a.nstage++;
+    };
+    for (int q = 0; q < TRI_COLS; ++q) a.c_slot[q] = -1;
+    if (indicator) {
+      for (int b = 0; b < nb; ++b) a.a_slot[0][b] = a.b_slot[b] = a.c_slot[b] = stage_of(iI + b);
+      a.nrows = npair;
+      a.ncol = nb;
+    } else {
+      for (int b = 0; b < nb; ++b) a.a_slot[0][b] = a.b_slot[b] = a.c_slot[b] = stage_of(b);
+      if (want2)
+        for (int b = 0; b < nb; ++b) a.a_slot[1][b] = stage_of(iF2 + b);
+      for (int l = 0; l < ng; ++l) a.c_slot[nb + l] = stage_of(iG + l);
+      a.nrows = npair * (want2 ? 2 : 1);
+      a.ncol = nb + ng;
+    }
+  };
+  TripleArgs ta, tn;
+  setup(ta, false);
+  setup(tn, true);
+  const int ngroups = (ta.nrows + TRI_ROWS - 1) / TRI_ROWS;
+  const int grid = sizeof(T) == 4 ? std::max(1, ctx->num_sms / ngroups) : ctx->num_sms * 4;
   double* part;
-  TripleArgs ta{};
-  ta.nb = nb;
-  ta.npair = npair;
-  ta.a1 = 0;
-  ta.a2 = want2 ? iF2 : -1;
-  ta.bb = 0;
-  ta.cb = 0;
-  ta.ng = ng;
-  ta.gbase = iG;
-  ta.nslots = nb * (want2 ? 2 : 1) + ng;
-  ta.ncell = (int64_t)ncell;
-  const int stride = 3 * NB_MAX + 2 + 1;
-  const size_t smem_t = sizeof(T) * (size_t)TRI_CHUNK * stride + sizeof(double) * (size_t)(2 * NB_MAX + 2) * tthreads;
-  NPC_TRY(ws_get(ctx, "bis.tripart", sizeof(double) * (size_t)grid * npair * (2 * NB_MAX + 2), (void**)&part));
-  auto kt = k_triple<T>;
-  NPC_CUDA(ctx, cudaFuncSetAttribute(kt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t));
-  if (need_nt) {
-    TripleArgs tn = ta;
-    tn.a1 = iI;
-    tn.a2 = -1;
-    tn.bb = iI;
-    tn.cb = iI;
-    tn.ng = 0;
-    tn.nslots = nb;
-    kt<<<grid, tthreads, smem_t, ctx->stream>>>(R, tn, (const int*)(dtab + t_pij), part);
+  NPC_TRY(ws_get(ctx, "bis.tripart", sizeof(double) * (size_t)grid * std::max(ta.nrows, tn.nrows) * TRI_COLS,
+                 (void**)&part));
+  auto launch = [&](const TripleArgs& a) -> npc_status {
+    if constexpr (sizeof(T) == 4) {
+      const size_t smem = sizeof(float) * (size_t)a.nstage * TRI_SPAD +
+                          sizeof(double) * (size_t)TRI_WARPS * 32 * TRI_MT * TRI_NT * 4;
+      NPC_CUDA(ctx, cudaFuncSetAttribute(k_triple, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      const int groups = (a.nrows + TRI_ROWS - 1) / TRI_ROWS;
+      k_triple<<<dim3(grid, groups), TRI_WARPS * 32, smem, ctx->stream>>>((const float*)R, a,
+                                                                          (const int*)(dtab + t_pij), part);
+    } else {
+      const int outs = a.nrows * a.ncol;
+      k_triple_f64<<<dim3(grid, (outs + 255) / 256), 256, 0, ctx->stream>>>((const double*)R, a,
+                                                                             (const int*)(dtab + t_pij), part);
+    }
     NPC_LAUNCH(ctx);
-    k_nt_reduce<<<(npair * nb + 127) / 128, 128, 0, ctx->stream>>>(part, grid, npair, nb, nb, nt_sums);
+    return NPC_OK;
+  };
+  if (need_nt) {
+    NPC_TRY(launch(tn));
+    k_nt_reduce<<<(npair * nb + 127) / 128, 128, 0, ctx->stream>>>(part, grid, npair, nb, nb, (double)ncell,
+                                                                  nt_sums);
     NPC_LAUNCH(ctx);
     ctx->host_cache_keys["bis.ntsums"] = ntkey;
   }
-  kt<<<grid, tthreads, smem_t, ctx->stream>>>(R, ta, (const int*)(dtab + t_pij), part);
-  NPC_LAUNCH(ctx);
+  NPC_TRY(launch(ta));
   NPC_TRY(stage_mark(ctx, "triple"));
 
   // 6. finalize
@@ -920,7 +1042,8 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
     if (tripo_mask & (1 << l)) fa.tripo_l[fa.ntripo++] = l;
   fa.shot = shot;
   fa.nparts = grid;
-  fa.slots_main = ta.nslots;
+  fa.nrows = ta.nrows;
+  fa.ncol = ta.ncol;
   fa.has2 = want2 ? 1 : 0;
   fa.ncell = (int64_t)ncell;
   fa.kmin = kb.kmin;

@@ -56,11 +56,14 @@ k_cat_partials(const T* __restrict__ w, const T* __restrict__ nbar, int64_t n, d
   if (threadIdx.x < NSUM) part[blockIdx.x * NSUM + threadIdx.x] = sh[threadIdx.x][0];
 }
 
+// One warp: lane l sums the partials of blocks l, l+32, ... in order, then a fixed shuffle tree;
+// the reduction order depends only on nblk (bitwise reproducible).
 __global__ void k_cat_final(const double* __restrict__ pd, const double* __restrict__ pr, int nblk,
                             int have_randoms, double box, double* __restrict__ sc) {
-  if (threadIdx.x != 0) return;
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x >= 32) return;
   double g[NSUM] = {0, 0, 0, 0, 0, 0}, r[NSUM] = {0, 0, 0, 0, 0, 0};
-  for (int b = 0; b < nblk; ++b) {
+  for (int b = lane; b < nblk; b += 32) {
     for (int k = 0; k < NSUM - 1; ++k) g[k] += pd[b * NSUM + k];
     g[NSUM - 1] = fmax(g[NSUM - 1], pd[b * NSUM + NSUM - 1]);
     if (have_randoms) {
@@ -68,6 +71,15 @@ __global__ void k_cat_final(const double* __restrict__ pd, const double* __restr
       r[NSUM - 1] = fmax(r[NSUM - 1], pr[b * NSUM + NSUM - 1]);
     }
   }
+  for (int off = 16; off > 0; off >>= 1) {
+    for (int k = 0; k < NSUM - 1; ++k) {
+      g[k] += __shfl_down_sync(0xffffffffu, g[k], off);
+      r[k] += __shfl_down_sync(0xffffffffu, r[k], off);
+    }
+    g[NSUM - 1] = fmax(g[NSUM - 1], __shfl_down_sync(0xffffffffu, g[NSUM - 1], off));
+    r[NSUM - 1] = fmax(r[NSUM - 1], __shfl_down_sync(0xffffffffu, r[NSUM - 1], off));
+  }
+  if (lane != 0) return;
   for (int k = 0; k < SC_COUNT; ++k) sc[k] = 0.0;
   if (have_randoms) {
     const double alpha = g[0] / r[0];
