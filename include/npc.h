@@ -194,6 +194,65 @@ npc_status npc_bispectrum_layout(const npc_kbins* bins, uint32_t scoc_ell_mask,
 npc_status npc_bispectrum_triangles(const npc_kbins* bins, int32_t* tri, int64_t cap,
                                     int64_t* ntri);
 
+/* Mesh-level estimators and their adjoints ------------------------------------------------------
+ * The paper defines its estimators as functions of the density field (Sec. 2.1 Eq. pk_final for
+ * P_l; Sec. 2.2 Eq. bi_sco for B_l) but does not differentiate them.  These calls expose the same
+ * estimators on a caller-owned mesh, and their exact derivatives, so the measurement can sit inside
+ * a gradient-based fit.  Scope: periodic box, global line of sight, one mesh without interlacing
+ * (spec->periodic = 1, spec->los = 1, spec->interlace = 0), else NPC_ERR_UNSUPPORTED.
+ *
+ * Mesh layout: n^3 values of the precision's type (float32 for NPC_PREC_MIXED, float64 for
+ * NPC_PREC_FP64), index (z n + y) n + x, device memory of the context's device.
+ * With X(q) = sum_x delta(x) e^{-iq.x} / W(q) and the bins of npc_power_multipoles:
+ *   P_l(b) = (2l+1)/(I22 N_b) sum_{q in b} L_l(qhat.los) |X(q)|^2 - delta_l0 N0,   l in {0, 2, 4};
+ *   B_0(b) = sum_x F_b(x)^3 / (I33 sum_x I_b(x)^3),  F_b(x) = sum_{q in b} X(q) e^{iq.x},
+ *            I_b(x) = sum_{q in b} e^{iq.x}   (the equilateral triangle (b, b, b) of Eq. bi_sco).
+ * I22, N0 and I33 are inputs (npc_catalog_scalars gives them for a catalogue); they are held fixed
+ * under differentiation.  B_0 needs the largest bin edge <= k_N/2 and nbins <= 32. */
+
+/* Number of doubles npc_mesh_multipoles writes (0 for a bad request). */
+int64_t npc_mesh_multipoles_len(const npc_kbins* bins, uint32_t ell_mask, int32_t b0);
+
+/* Forward values.  ell_mask: bits 0, 2, 4 request P_l; b0 = 1 requests B_0.  Output rows of
+ * nbins: [0] k_eff, [1] N_modes, then P_l for the requested l in increasing order, then (b0) B_0
+ * and N_T (closed wavevector triples of the equilateral bin triangle).  `out` is host memory when
+ * out_on_device == 0 (the call then synchronises), else device memory.  Sums are float64 and
+ * reproducible run to run. */
+npc_status npc_mesh_multipoles(npc_ctx* ctx, const npc_mesh_spec* spec, const void* mesh,
+                               const npc_kbins* bins, uint32_t ell_mask, int32_t b0, double i22,
+                               double n0, double i33, npc_precision prec, double* out,
+                               int32_t out_on_device);
+
+/* Vector-Jacobian product: grad_mesh(x) = dL/ddelta(x) for the loss with cotangents
+ * dl_dp[e][b] = dL/dP_{l_e}(b) (requested l in increasing order) and dl_db0[b] = dL/dB_0(b):
+ *   dL/ddelta(x) = sum_q [2 K(q) X(q) + sum_b c_b Phi_b(q) D_b(q)] / W(q) e^{iq.x},
+ *   K(q) = sum_{l,b} dl_dp (2l+1) Phi_b(q) L_l(qhat.los) / (I22 N_b),
+ *   c_b = 3 dl_db0[b] / (I33 sum_x I_b^3),  D_b(q) = sum_x F_b(x)^2 e^{-iq.x}.
+ * The transforms are recomputed from `mesh` (nothing is kept from the forward call).
+ * Cotangents are host (cotangents_on_device = 0) or device memory; grad_mesh is device memory in
+ * the mesh layout and is overwritten. */
+npc_status npc_mesh_multipoles_vjp(npc_ctx* ctx, const npc_mesh_spec* spec, const void* mesh,
+                                   const npc_kbins* bins, uint32_t ell_mask, int32_t b0,
+                                   double i22, double i33, const double* dl_dp,
+                                   const double* dl_db0, int32_t cotangents_on_device,
+                                   npc_precision prec, void* grad_mesh);
+
+/* Deterministic mass assignment of a periodic catalogue onto one mesh (spec->periodic = 1,
+ * spec->interlace = 0): mesh(c) = sum_p w_p W(c - s_p) - sum_p w_p / n^3, in the mesh layout above
+ * (device memory, overwritten).  The same painting as the estimator calls. */
+npc_status npc_paint_mesh(npc_ctx* ctx, const npc_mesh_spec* spec, const npc_catalog* data,
+                          npc_precision prec, void* mesh);
+
+/* Adjoint of npc_paint_mesh with respect to positions and weights, for a cotangent mesh G:
+ *   grad_pos[p][a] = w_p (n/box) sum_c G(c) dW(c - s_p)/ds_a,   grad_w[p] = sum_c G(c) W(c - s_p),
+ * over the 8 (CIC) or 27 (TSC) taps, with the tap cells decided in float64 as in the forward
+ * assignment (the window is piecewise polynomial; at a cell boundary the one-sided derivative of the
+ * chosen taps is returned).  The catalogue must be on the device; grad_pos ([n][3]) and grad_w ([n],
+ * may be NULL) are device arrays of the catalogue's dtype; grad_mesh has the precision's type. */
+npc_status npc_paint_adjoint(npc_ctx* ctx, const npc_mesh_spec* spec, const npc_catalog* data,
+                             const void* grad_mesh, npc_precision prec, void* grad_pos,
+                             void* grad_w);
+
 #ifdef __cplusplus
 }
 #endif

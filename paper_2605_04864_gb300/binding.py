@@ -66,6 +66,16 @@ _sig = {
     "npc_catalog_scalars_noalloc": (C.c_int, [_P(npc_catalog), _P(npc_catalog), C.c_double, C.c_void_p,
                                               C.c_void_p, C.c_char_p, C.c_size_t]),
     "npc_set_profiling": (C.c_int, [C.c_void_p, C.c_int32]),
+    "npc_mesh_multipoles_len": (C.c_int64, [_P(npc_kbins), C.c_uint32, C.c_int32]),
+    "npc_mesh_multipoles": (C.c_int, [C.c_void_p, _P(npc_mesh_spec), C.c_void_p, _P(npc_kbins), C.c_uint32,
+                                      C.c_int32, C.c_double, C.c_double, C.c_double, C.c_int, C.c_void_p,
+                                      C.c_int32]),
+    "npc_mesh_multipoles_vjp": (C.c_int, [C.c_void_p, _P(npc_mesh_spec), C.c_void_p, _P(npc_kbins), C.c_uint32,
+                                          C.c_int32, C.c_double, C.c_double, C.c_void_p, C.c_void_p, C.c_int32,
+                                          C.c_int, C.c_void_p]),
+    "npc_paint_mesh": (C.c_int, [C.c_void_p, _P(npc_mesh_spec), _P(npc_catalog), C.c_int, C.c_void_p]),
+    "npc_paint_adjoint": (C.c_int, [C.c_void_p, _P(npc_mesh_spec), _P(npc_catalog), C.c_void_p, C.c_int,
+                                    C.c_void_p, C.c_void_p]),
     "npc_stage_times": (C.c_int, [C.c_void_p, C.c_char_p, _P(C.c_double), _P(C.c_int32), C.c_int32,
                                   _P(C.c_int32)]),
 }

@@ -140,7 +140,7 @@ npc_status get_bin_table(npc_ctx* ctx, int n, double box, const npc_kbins& kb, c
 // ---------------------------------------------------------------------------------------------
 static bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
-static npc_status check_spec(npc_ctx* ctx, const npc_mesh_spec* m) {
+npc_status check_spec(npc_ctx* ctx, const npc_mesh_spec* m) {
   if (!m) return set_err(ctx, NPC_ERR_INVALID_ARG, "mesh spec is NULL");
   if (!is_pow2(m->n) || m->n < 16 || m->n > 1024)
     return set_err(ctx, NPC_ERR_INVALID_ARG, "mesh n=%d must be a power of two in [16, 1024]", m->n);
@@ -159,7 +159,7 @@ static npc_status check_spec(npc_ctx* ctx, const npc_mesh_spec* m) {
   return NPC_OK;
 }
 
-static npc_status check_catalog(npc_ctx* ctx, const npc_catalog* c, const char* what, bool need_nbar) {
+npc_status check_catalog(npc_ctx* ctx, const npc_catalog* c, const char* what, bool need_nbar) {
   if (!c) return set_err(ctx, NPC_ERR_INVALID_ARG, "%s catalogue is NULL", what);
   if (c->n < 0) return set_err(ctx, NPC_ERR_INVALID_ARG, "%s: n < 0", what);
   if (c->dtype != 0 && c->dtype != 1) return set_err(ctx, NPC_ERR_INVALID_ARG, "%s: dtype must be 0 or 1", what);
@@ -170,7 +170,7 @@ static npc_status check_catalog(npc_ctx* ctx, const npc_catalog* c, const char* 
   return NPC_OK;
 }
 
-static npc_status check_bins(npc_ctx* ctx, const npc_kbins* b) {
+npc_status check_bins(npc_ctx* ctx, const npc_kbins* b) {
   if (!b) return set_err(ctx, NPC_ERR_INVALID_ARG, "k-bins are NULL");
   if (!(b->dk > 0.0) || !std::isfinite(b->dk) || !(b->kmin >= 0.0) || !std::isfinite(b->kmin))
     return set_err(ctx, NPC_ERR_INVALID_ARG, "k-bins need dk > 0 and kmin >= 0");
@@ -179,7 +179,7 @@ static npc_status check_bins(npc_ctx* ctx, const npc_kbins* b) {
 }
 
 // Stage a catalogue on the device (host inputs are copied into context workspace).
-static npc_status stage_catalog(npc_ctx* ctx, const npc_catalog* c, const char* tag, DevCatalog* out) {
+npc_status stage_catalog(npc_ctx* ctx, const npc_catalog* c, const char* tag, DevCatalog* out) {
   out->n = c->n;
   out->dtype = c->dtype;
   const size_t es = c->dtype == 1 ? 8 : 4;
@@ -206,7 +206,7 @@ static npc_status stage_catalog(npc_ctx* ctx, const npc_catalog* c, const char* 
   return NPC_OK;
 }
 
-static Geom make_geom(const npc_mesh_spec& m) {
+Geom make_geom(const npc_mesh_spec& m) {
   Geom g{};
   g.n = m.n;
   g.h = m.box / m.n;
@@ -248,13 +248,13 @@ npc_status stage_mark(npc_ctx* ctx, const char* name) {
   return NPC_OK;
 }
 
-static void begin_call(npc_ctx* ctx) {
+void begin_call(npc_ctx* ctx) {
   ctx->launches = 0;
   ctx->last_error.clear();
   stage_begin(ctx);
 }
 
-static npc_status end_call(npc_ctx* ctx) {
+npc_status end_call(npc_ctx* ctx) {
   ctx->stats.n_kernel_launches = ctx->launches;
   int64_t tot = 0;
   for (auto& kv : ctx->ws) tot += (int64_t)kv.second.bytes;
@@ -262,7 +262,7 @@ static npc_status end_call(npc_ctx* ctx) {
   return NPC_OK;
 }
 
-static npc_status finish_output(npc_ctx* ctx, const double* dev, double* out, int64_t len, int out_on_device) {
+npc_status finish_output(npc_ctx* ctx, const double* dev, double* out, int64_t len, int out_on_device) {
   if (out_on_device) {
     if (dev != out) NPC_CUDA(ctx, cudaMemcpyAsync(out, dev, sizeof(double) * len, cudaMemcpyDeviceToDevice, ctx->stream));
     return NPC_OK;

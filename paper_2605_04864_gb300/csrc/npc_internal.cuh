@@ -207,6 +207,17 @@ npc_status ws_get(npc_ctx* ctx, const char* name, size_t bytes, void** out);
 npc_status ws_table(npc_ctx* ctx, const std::string& name, const std::vector<char>& key,
                     const void* data, size_t bytes, void** out);
 
+// Shared host helpers of the public entry points (api.cu)
+npc_status check_spec(npc_ctx* ctx, const npc_mesh_spec* m);
+npc_status check_catalog(npc_ctx* ctx, const npc_catalog* c, const char* what, bool need_nbar);
+npc_status check_bins(npc_ctx* ctx, const npc_kbins* b);
+struct DevCatalog;
+npc_status stage_catalog(npc_ctx* ctx, const npc_catalog* c, const char* tag, DevCatalog* out);
+Geom make_geom(const npc_mesh_spec& m);
+void begin_call(npc_ctx* ctx);
+npc_status end_call(npc_ctx* ctx);
+npc_status finish_output(npc_ctx* ctx, const double* dev, double* out, int64_t len, int out_on_device);
+
 // ---------------------------------------------------------------------------------------------
 // Scalars layout in device memory (double[16])
 // ---------------------------------------------------------------------------------------------

@@ -29,6 +29,17 @@ WORKLOADS = {
         kmin=0.01, dk=0.01, nbins=19, scoc_ells=(0, 2), tripo_ells=(0, 2), precision="mixed",
         seed=2000,
     ),
+    # Gradients of P_0,2,4 (global LOS) and of the equilateral B_0 (19 bins) with respect to the
+    # mesh and, through the TSC adjoint, the galaxy positions: periodic 1024^3, 1e7 galaxies.
+    "adjoint_1024": dict(
+        kind="adjoint", n=1024, box=3000.0, assign=3, interlace=0, n_gal=10_000_000, n_gen=256,
+        kmin=0.01, dk=0.01, nbins=19, ells=(0, 2, 4), b0=True, precision="mixed", seed=4000,
+    ),
+    # The same at 32^3 for finite-difference checks (box scaled to keep k_N, 1/32 of the side).
+    "adjoint_32": dict(
+        kind="adjoint", n=32, box=93.75, assign=3, interlace=0, n_gal=2_000, n_gen=32,
+        kmin=0.1, dk=0.1, nbins=4, ells=(0, 2, 4), b0=True, precision="fp64", seed=4001,
+    ),
 }
 
 
