@@ -251,47 +251,61 @@ def bispec_leg(args, world, rank, barrier, max_over_ranks):
             "triple_product": "3xTF32 split hi+lo tensor-core products (mma.sync m16n8k8), FP32 within 128-cell chunks, FP64 across chunks"}
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default=WORKLOAD, help="power workload name (profiling uses a smaller one)")
-    ap.add_argument("--no-bispec", action="store_true", help="skip the 256^3 bispectrum leg")
-    args = ap.parse_args()
-    if args.warmup < 3:
-        args.warmup = 3
-
-    from synthetic import workload
-
-    w = workload(args.workload)
-    if args.impl == "reference":
-        run_reference(args, w)
-        return
-
-    import numpy as np
+def adjoint_leg(args, world, rank, barrier, max_over_ranks):
+    """Gradients/s at 1024^3: 1e7 lognormal galaxies, periodic, TSC; one step = paint -> P_0,2,4
+    (global LOS) and equilateral B_0 on 19 bins -> scalar loss -> backward through the mesh adjoint
+    and the TSC adjoint to the positions (torch.autograd over the library's calls)."""
     import torch
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
+    from paper_2605_04864_gb300 import autograd as AG
+    from synthetic import make_periodic_catalog, workload
 
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    w = workload("adjoint_1024")
+    n, box = w["n"], w["box"]
+    kb = (w["kmin"], w["dk"], w["nbins"])
+    cat = make_periodic_catalog(w["n_gal"], box, w["n_gen"], seed=w["seed"] + rank)
+    pos0 = torch.from_numpy(cat.pos).cuda()
+    i22, n0, i33 = AG.periodic_normalisations(pos0, None, box)
+    g = torch.Generator(device="cuda").manual_seed(7)
+    cp = torch.randn(len(w["ells"]), kb[2], device="cuda", dtype=torch.float64, generator=g)
+    cb = torch.randn(kb[2], device="cuda", dtype=torch.float64, generator=g)
 
-    if not os.path.exists(os.path.join(ROOT, "paper_2605_04864_gb300", "libnpc.so")):
-        import __graft_entry__
+    def step():
+        pos = pos0.detach().requires_grad_(True)
+        mesh = AG.paint(pos, None, n, box, assign=w["assign"], precision=w["precision"])
+        r = AG.mesh_multipoles(mesh, box, kb, w["ells"], True, i22, n0, i33, assign=w["assign"],
+                               precision=w["precision"])
+        loss = (r["P"] * cp).sum() + (r["B0"] * cb).sum()
+        loss.backward()
+        return pos.grad
 
-        __graft_entry__.build()
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(args.steps):
+        step()
+    e.record()
+    torch.cuda.synchronize()
+    barrier()
+    ms = max_over_ranks(s.elapsed_time(e)) / args.steps
+    return {"metric": "gradients/s @1024^3 (dL/dpos of P_0,2,4 + equilateral B_0, 1e7 galaxies)",
+            "value": world / (ms / 1e3), "unit": "gradients/s", "ms_per_step": ms,
+            "config": {"workload": "adjoint_1024", "mesh": n, "n_gal": w["n_gal"], "nbins": w["nbins"],
+                       "assign": "TSC", "interlace": False, "precision": w["precision"]}}
+
+
+def power_leg(args, w, world, local, rank, barrier, max_over_ranks):
+    """The headline leg: catalogue -> P_l measurements at 512^3, device-resident and end to end."""
+    import ctypes as C
     from types import SimpleNamespace
+
+    import torch
 
     from paper_2605_04864_gb300 import api
     from paper_2605_04864_gb300 import binding as B
-    import ctypes as C
 
     g, r, origin = make_inputs(w, rank)
     dev = lambda c: SimpleNamespace(pos=torch.from_numpy(c.pos).cuda(), w=torch.from_numpy(c.w).cuda(),
@@ -314,17 +328,6 @@ def main():
     torch.cuda.synchronize()
     launches = api.last_stats()["n_kernel_launches"]
     nf = 2 * api.last_stats()["n_r2c_equivalent"] * api.last_stats()["n_phases"] // 2
-
-    def barrier():
-        if world > 1:
-            torch.distributed.barrier()
-
-    def max_over_ranks(v):
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
 
     # --- device-resident timed region ---
     clk = ClockSampler(local)
@@ -383,16 +386,13 @@ def main():
     t0 = time.perf_counter()
     s.record()
     for _ in range(args.steps):
-        res = api.power_multipoles(gh, rh, **kw)
+        api.power_multipoles(gh, rh, **kw)
     e.record()
     torch.cuda.synchronize()
     barrier()
     e2e_s = max_over_ranks(time.perf_counter() - t0)
     e2e = {"value": world * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
            "ms_per_step": e2e_s / args.steps * 1e3}
-
-    secondary = None if args.no_bispec else bispec_leg(args, world, rank, barrier, max_over_ranks)
-
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 transforms, f64 accumulators", "data": "synthetic",
@@ -403,16 +403,73 @@ def main():
                        "l2": "inputs larger than L2 (catalogues 440 MB, meshes 2x537 MB, spectra 16 GB)"},
             "roofline": roofline, "stages_ms": stages, "e2e": e2e, "gpu_launches": launches * args.steps,
             "clocks": clocks}
-    if secondary is not None:
-        line["secondary"] = secondary
-        line["gpu_launches"] += secondary["gpu_launches"]
-    if rank == 0 and not args.no_cpu_baseline and world == 1:
+    del gd, rd, gh, rh, out
+    torch.cuda.empty_cache()
+    return line
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD, help="power workload name (profiling uses a smaller one)")
+    ap.add_argument("--no-power", action="store_true", help="skip the headline leg (profiling of the others)")
+    ap.add_argument("--no-bispec", action="store_true", help="skip the 256^3 bispectrum leg")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the 1024^3 gradient leg")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    from synthetic import workload
+
+    w = workload(args.workload)
+    if args.impl == "reference":
+        run_reference(args, w)
+        return
+
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    if not os.path.exists(os.path.join(ROOT, "paper_2605_04864_gb300", "libnpc.so")):
+        import __graft_entry__
+
+        __graft_entry__.build()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    line = {} if args.no_power else power_leg(args, w, world, local, rank, barrier, max_over_ranks)
+    if not args.no_bispec:
+        sec = bispec_leg(args, world, rank, barrier, max_over_ranks)
+        line["secondary"] = sec
+        line["gpu_launches"] = line.get("gpu_launches", 0) + sec["gpu_launches"]
+    if not args.no_adjoint:
+        line["gradient"] = adjoint_leg(args, world, rank, barrier, max_over_ranks)
+    if rank == 0 and not args.no_power and not args.no_cpu_baseline and world == 1:
         dt, scale, desc = cpu_baseline(w)
         line["cpu_baseline"] = {"value": 1.0 / (dt * scale), "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": desc, "sample_seconds": dt}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    del res, np
     if world > 1:
         torch.distributed.destroy_process_group()
 
