@@ -57,7 +57,7 @@ typedef struct npc_ctx npc_ctx;
 
 /* Mesh, box and line-of-sight specification. */
 typedef struct {
-  int32_t n;           /* cells per side: power of two, 16 <= n <= 1024 */
+  int32_t n;           /* cells per side: a power of two in [16, 1024], or 48, 96, 192 (3 * 2^k) */
   double box;          /* side length of the cubic mesh (length units of the positions) */
   double origin[3];    /* lower corner of the mesh */
   int32_t assign;      /* 2 = CIC, 3 = TSC */
@@ -171,7 +171,9 @@ npc_status npc_power_multipoles(npc_ctx* ctx, const npc_mesh_spec* mesh, const n
 int64_t npc_power_out_len(const npc_kbins* bins, uint32_t ell_mask, uint32_t modified_mask);
 
 /* Bispectrum multipoles (Sec. 2.2 Eq. bi_sco; Sec. 4 Eq. new_bispec; Sec. 5.4 shot noise) ------
- * Periodic box with a global line of sight (mesh->periodic = 1, mesh->los = 1, randoms = NULL).
+ * Periodic box (mesh->periodic = 1, randoms = NULL) with a global line of sight (mesh->los = 1) for l = 2;
+ * survey geometry (mesh->periodic = 0, randoms required) for the monopoles B_0 and B_000 only,
+ * which do not depend on the line of sight.
  * Triangles: bins i <= j <= k closing at their centres, c_k <= c_i + c_j, c_b = kmin+(b+1/2)dk,
  * in lexicographic (i, j, k) order; pairs: i <= j in lexicographic order.  The largest bin edge
  * must not exceed k_N/2 (the closure would alias otherwise), else NPC_ERR_UNSUPPORTED.

@@ -490,7 +490,7 @@ k_adj_z(cplx<T>* __restrict__ T2, const AFieldTable* __restrict__ ftp, const int
   const int Kmx = Ka > Kb ? Ka : Kb;
   for (int kz = t; kz <= Kmx; kz += TPF) {
     const C z1 = work[kz * TX + c];
-    const C z2 = cconj(work[((N - kz) & (N - 1)) * TX + c]);
+    const C z2 = cconj(work[((N - kz) % N) * TX + c]);
     if (kz <= Ka) A[(size_t)kz * plane] = cscale(cadd(z1, z2), T(0.5));
     if (kz <= Kb) {
       const C d = csub(z1, z2);
@@ -977,6 +977,7 @@ npc_status check_mesh_call(npc_ctx* ctx, const npc_mesh_spec* m, const npc_kbins
                            uint32_t ell_mask, int32_t b0, npc_precision prec) {
   NPC_TRY(check_spec(ctx, m));
   NPC_TRY(check_bins(ctx, b));
+  if (m->n & (m->n - 1)) return set_err(ctx, NPC_ERR_UNSUPPORTED, "mesh estimators: n must be a power of two");
   if (!mesh) return set_err(ctx, NPC_ERR_INVALID_ARG, "mesh is NULL");
   if (!m->periodic || m->los != 1 || m->interlace != 0)
     return set_err(ctx, NPC_ERR_UNSUPPORTED, "mesh estimators: periodic box, global line of sight, no interlacing");

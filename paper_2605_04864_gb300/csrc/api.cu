@@ -22,10 +22,17 @@ npc_status set_err(npc_ctx* ctx, npc_status s, const char* fmt, ...) {
   return s;
 }
 
+std::string slot_name(const npc_ctx* ctx, const std::string& name) {
+  return ctx->slot_base ? name + "#" + std::to_string(ctx->slot_base) : name;
+}
+
 npc_status ws_get(npc_ctx* ctx, const char* name, size_t bytes, void** out) {
   Workspace& w = ctx->ws[name];
   if (bytes == 0) bytes = 16;
   if (w.bytes < bytes) {
+    if (ctx->capturing)
+      return set_err(ctx, NPC_ERR_INVALID_ARG, "workspace '%s' would grow during graph capture", name);
+    ctx->ws_generation++;
     if (w.p) {
       cudaError_t e = cudaStreamSynchronize(ctx->stream);
       if (e != cudaSuccess) return set_err(ctx, NPC_ERR_CUDA, "sync before realloc: %s", cudaGetErrorString(e));
@@ -46,19 +53,23 @@ npc_status ws_get(npc_ctx* ctx, const char* name, size_t bytes, void** out) {
   return NPC_OK;
 }
 
-static bool table_cached(npc_ctx* ctx, const std::string& name, const std::vector<char>& key, void** out) {
+static bool table_cached(npc_ctx* ctx, const std::string& name0, const std::vector<char>& key, void** out) {
+  const std::string name = slot_name(ctx, name0);
   auto it = ctx->host_cache_keys.find(name);
   if (it == ctx->host_cache_keys.end() || it->second != key) return false;
   *out = ctx->ws[name].p;
   return *out != nullptr;
 }
 
-npc_status ws_table(npc_ctx* ctx, const std::string& name, const std::vector<char>& key, const void* data,
+npc_status ws_table(npc_ctx* ctx, const std::string& name0, const std::vector<char>& key, const void* data,
                     size_t bytes, void** out) {
+  const std::string name = slot_name(ctx, name0);
   auto it = ctx->host_cache_keys.find(name);
   void* p;
   NPC_TRY(ws_get(ctx, name.c_str(), bytes, &p));
   if (it == ctx->host_cache_keys.end() || it->second != key) {
+    if (ctx->capturing)
+      return set_err(ctx, NPC_ERR_INVALID_ARG, "table '%s' would be uploaded during graph capture", name.c_str());
     NPC_CUDA(ctx, cudaMemcpyAsync(p, data, bytes, cudaMemcpyHostToDevice, ctx->stream));
     NPC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     ctx->host_cache_keys[name] = key;
@@ -139,11 +150,13 @@ npc_status get_bin_table(npc_ctx* ctx, int n, double box, const npc_kbins& kb, c
 // Validation
 // ---------------------------------------------------------------------------------------------
 static bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+// mesh sizes with compiled transforms: 2^k for 16 <= n <= 1024, and 3 * 2^k for n = 48, 96, 192
+static bool mesh_size_ok(int n) { return (is_pow2(n) && n >= 16 && n <= 1024) || n == 48 || n == 96 || n == 192; }
 
 npc_status check_spec(npc_ctx* ctx, const npc_mesh_spec* m) {
   if (!m) return set_err(ctx, NPC_ERR_INVALID_ARG, "mesh spec is NULL");
-  if (!is_pow2(m->n) || m->n < 16 || m->n > 1024)
-    return set_err(ctx, NPC_ERR_INVALID_ARG, "mesh n=%d must be a power of two in [16, 1024]", m->n);
+  if (!mesh_size_ok(m->n))
+    return set_err(ctx, NPC_ERR_INVALID_ARG, "mesh n=%d must be a power of two in [16, 1024] or 48, 96, 192", m->n);
   if (!(m->box > 0.0) || !std::isfinite(m->box)) return set_err(ctx, NPC_ERR_INVALID_ARG, "box must be > 0");
   for (int a = 0; a < 3; ++a)
     if (!std::isfinite(m->origin[a]) || !std::isfinite(m->observer[a]) || !std::isfinite(m->los_dir[a]))
@@ -269,6 +282,73 @@ npc_status finish_output(npc_ctx* ctx, const double* dev, double* out, int64_t l
   }
   NPC_CUDA(ctx, cudaMemcpyAsync(out, dev, sizeof(double) * len, cudaMemcpyDeviceToHost, ctx->stream));
   NPC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return NPC_OK;
+}
+
+// The estimator after validation, staging and the catalogue scalars (device output `dev_out`).
+npc_status power_core(npc_ctx* ctx, const npc_mesh_spec& ms, const DevCatalog& d, const DevCatalog* r,
+                      const npc_kbins& kb, uint32_t ell_mask, uint32_t modified_mask, int prec, const double* sc,
+                      double* dev_out) {
+  const npc_mesh_spec* mesh = &ms;
+  const npc_kbins* bins = &kb;
+  const int n = mesh->n;
+  const int nphase = mesh->interlace ? 2 : 1;
+  PowerPlan plan{};
+  plan.n = n;
+  plan.nphase = nphase;
+  plan.ells_mask = (int)ell_mask;
+  plan.mod_mask = (int)modified_mask;
+  plan.nbins = bins->nbins;
+  plan.global_los = mesh->los;
+  plan.assign = mesh->assign;
+  const Geom g = make_geom(*mesh);
+  for (int a = 0; a < 3; ++a) plan.los[a] = g.los[a];
+  int need = (int)ell_mask | 1;
+  if (modified_mask) need |= 1 | 4 | 16;
+  FieldList& fl = plan.fl;
+  fl.nf = 0;
+  int ntr = 0, nr2c = 0;
+  auto push = [&](int ph, int l, int m, int part) {
+    Comp c;
+    c.phase = (int8_t)ph; c.ell = (int8_t)l; c.m = (int8_t)m; c.part = (int8_t)part;
+    fl.f[fl.nf++] = c;
+  };
+  if (mesh->los == 1) {
+    for (int ph = 0; ph < nphase; ++ph) push(ph, 0, 0, PART_ONE);
+    ntr = 1;
+    nr2c = 1;
+  } else {
+    for (int l = 0; l <= 4; l += 2) {
+      if (!(need & (1 << l))) continue;
+      for (int m = 0; m <= l; ++m) {
+        for (int ph = 0; ph < nphase; ++ph) {
+          if (l == 0) {
+            push(ph, 0, 0, PART_ONE);  // F_0 needs no weighting
+            continue;
+          }
+          push(ph, l, m, PART_RE);
+          if (m > 0) push(ph, l, m, PART_IM);
+        }
+      }
+      ntr += l + 1;
+      nr2c += 2 * l + 1;
+    }
+  }
+  ctx->stats.n_transforms = ntr;
+  ctx->stats.n_r2c_equivalent = nr2c;
+  ctx->stats.n_phases = nphase;
+
+  const size_t rs = prec == NPC_PREC_FP64 ? 8 : 4;
+  const size_t ncell = (size_t)n * n * n;
+  void *ma, *mb = nullptr, *half;
+  NPC_TRY(ws_get(ctx, "mesh.a", rs * ncell, &ma));
+  if (nphase == 2) NPC_TRY(ws_get(ctx, "mesh.b", rs * ncell, &mb));
+  NPC_TRY(ws_get(ctx, "half", 2 * rs * (size_t)fl.nf * (n / 2) * n * n, &half));
+  NPC_TRY(stage_mark(ctx, "alloc"));
+  NPC_TRY(launch_paint(ctx, d, r, *mesh, 1, prec, sc, ma, mb));
+  NPC_TRY(stage_mark(ctx, "paint_fold"));
+  NPC_TRY(run_forward_transforms(ctx, prec, plan, g, ma, mb, half));
+  NPC_TRY(run_power_contract(ctx, prec, plan, *mesh, *bins, half, sc, dev_out));
   return NPC_OK;
 }
 
@@ -421,53 +501,6 @@ npc_status npc_power_multipoles(npc_ctx* ctx, const npc_mesh_spec* mesh, const n
   if (data->n == 0) return set_err(ctx, NPC_ERR_NUMERIC, "empty data catalogue (I22 = 0)");
   NPC_CUDA(ctx, cudaSetDevice(ctx->device));
 
-  const int n = mesh->n;
-  const int nphase = mesh->interlace ? 2 : 1;
-  PowerPlan plan{};
-  plan.n = n;
-  plan.nphase = nphase;
-  plan.ells_mask = (int)ell_mask;
-  plan.mod_mask = (int)modified_mask;
-  plan.nbins = bins->nbins;
-  plan.global_los = mesh->los;
-  plan.assign = mesh->assign;
-  const Geom g = make_geom(*mesh);
-  for (int a = 0; a < 3; ++a) plan.los[a] = g.los[a];
-  int need = (int)ell_mask | 1;
-  if (modified_mask) need |= 1 | 4 | 16;
-  FieldList& fl = plan.fl;
-  fl.nf = 0;
-  int ntr = 0, nr2c = 0;
-  auto push = [&](int ph, int l, int m, int part) {
-    Comp c;
-    c.phase = (int8_t)ph; c.ell = (int8_t)l; c.m = (int8_t)m; c.part = (int8_t)part;
-    fl.f[fl.nf++] = c;
-  };
-  if (mesh->los == 1) {
-    for (int ph = 0; ph < nphase; ++ph) push(ph, 0, 0, PART_ONE);
-    ntr = 1;
-    nr2c = 1;
-  } else {
-    for (int l = 0; l <= 4; l += 2) {
-      if (!(need & (1 << l))) continue;
-      for (int m = 0; m <= l; ++m) {
-        for (int ph = 0; ph < nphase; ++ph) {
-          if (l == 0) {
-            push(ph, 0, 0, PART_ONE);  // F_0 needs no weighting
-            continue;
-          }
-          push(ph, l, m, PART_RE);
-          if (m > 0) push(ph, l, m, PART_IM);
-        }
-      }
-      ntr += l + 1;
-      nr2c += 2 * l + 1;
-    }
-  }
-  ctx->stats.n_transforms = ntr;
-  ctx->stats.n_r2c_equivalent = nr2c;
-  ctx->stats.n_phases = nphase;
-
   DevCatalog d, r;
   NPC_TRY(stage_catalog(ctx, data, "data", &d));
   if (randoms) NPC_TRY(stage_catalog(ctx, randoms, "rand", &r));
@@ -476,20 +509,9 @@ npc_status npc_power_multipoles(npc_ctx* ctx, const npc_mesh_spec* mesh, const n
   NPC_TRY(stage_mark(ctx, "upload"));
   NPC_TRY(launch_catalog_scalars(ctx, d, randoms ? &r : nullptr, mesh->box, sc));
   NPC_TRY(stage_mark(ctx, "scalars"));
-
-  const size_t rs = prec == NPC_PREC_FP64 ? 8 : 4;
-  const size_t ncell = (size_t)n * n * n;
-  void *ma, *mb = nullptr, *half;
-  NPC_TRY(ws_get(ctx, "mesh.a", rs * ncell, &ma));
-  if (nphase == 2) NPC_TRY(ws_get(ctx, "mesh.b", rs * ncell, &mb));
-  NPC_TRY(ws_get(ctx, "half", 2 * rs * (size_t)fl.nf * (n / 2) * n * n, &half));
   double* dev_out = out;
   if (!out_on_device) NPC_TRY(ws_get(ctx, "power.out", sizeof(double) * out_len, (void**)&dev_out));
-  NPC_TRY(stage_mark(ctx, "alloc"));
-  NPC_TRY(launch_paint(ctx, d, randoms ? &r : nullptr, *mesh, 1, prec, sc, ma, mb));
-  NPC_TRY(stage_mark(ctx, "paint_fold"));
-  NPC_TRY(run_forward_transforms(ctx, prec, plan, g, ma, mb, half));
-  NPC_TRY(run_power_contract(ctx, prec, plan, *mesh, *bins, half, sc, dev_out));
+  NPC_TRY(power_core(ctx, *mesh, d, randoms ? &r : nullptr, *bins, ell_mask, modified_mask, prec, sc, dev_out));
   NPC_TRY(finish_output(ctx, dev_out, out, out_len, out_on_device));
   NPC_TRY(stage_mark(ctx, "download"));
   return end_call(ctx);
@@ -534,8 +556,18 @@ npc_status npc_bispectrum(npc_ctx* ctx, const npc_mesh_spec* mesh, const npc_cat
     return set_err(ctx, NPC_ERR_INVALID_ARG, "multipole masks must use bits 0 and 2");
   if (shot != 0 && shot != 1) return set_err(ctx, NPC_ERR_INVALID_ARG, "shot must be 0 or 1");
   if (prec != NPC_PREC_FP64 && prec != NPC_PREC_MIXED) return set_err(ctx, NPC_ERR_INVALID_ARG, "bad precision");
-  if (!mesh->periodic || mesh->los != 1 || randoms)
-    return set_err(ctx, NPC_ERR_UNSUPPORTED, "bispectrum: periodic box with a global line of sight only");
+  const bool mono = (scoc_ell_mask & ~1u) == 0 && (tripo_ell_mask & ~1u) == 0;
+  if (mesh->periodic) {
+    if (randoms) return set_err(ctx, NPC_ERR_INVALID_ARG, "periodic box takes no randoms");
+    if (mesh->los != 1 && !mono)
+      return set_err(ctx, NPC_ERR_UNSUPPORTED, "bispectrum: l = 2 needs a global line of sight");
+  } else {
+    // survey geometry: the monopoles B_0 and B_000 do not depend on the line of sight
+    if (!mono) return set_err(ctx, NPC_ERR_UNSUPPORTED, "bispectrum: survey geometry supports l = 0 only");
+    if (!randoms) return set_err(ctx, NPC_ERR_INVALID_ARG, "survey geometry needs randoms");
+    NPC_TRY(check_catalog(ctx, randoms, "randoms", true));
+    if (randoms->n == 0) return set_err(ctx, NPC_ERR_NUMERIC, "empty random catalogue");
+  }
   const double kf = 2.0 * M_PI / mesh->box;
   const double knyq = kf * mesh->n / 2.0;
   const double kmax = bins->kmin + bins->nbins * bins->dk;
@@ -552,17 +584,18 @@ npc_status npc_bispectrum(npc_ctx* ctx, const npc_mesh_spec* mesh, const npc_cat
   ctx->stats.n_transforms = 1;
   ctx->stats.n_r2c_equivalent = 1;
   ctx->stats.n_phases = mesh->interlace ? 2 : 1;
-  DevCatalog d;
+  DevCatalog d, r;
   NPC_TRY(stage_catalog(ctx, data, "data", &d));
+  if (randoms) NPC_TRY(stage_catalog(ctx, randoms, "rand", &r));
   double* sc;
   NPC_TRY(ws_get(ctx, "scalars", sizeof(double) * SC_COUNT, (void**)&sc));
   NPC_TRY(stage_mark(ctx, "upload"));
-  NPC_TRY(launch_catalog_scalars(ctx, d, nullptr, mesh->box, sc));
+  NPC_TRY(launch_catalog_scalars(ctx, d, randoms ? &r : nullptr, mesh->box, sc));
   NPC_TRY(stage_mark(ctx, "scalars"));
   double* dev_out = out;
   if (!out_on_device) NPC_TRY(ws_get(ctx, "bis.out", sizeof(double) * out_len, (void**)&dev_out));
-  NPC_TRY(run_bispectrum(ctx, *mesh, *bins, (int)scoc_ell_mask, (int)tripo_ell_mask, shot, prec, d, sc, dev_out,
-                         out_len));
+  NPC_TRY(run_bispectrum(ctx, *mesh, *bins, (int)scoc_ell_mask, (int)tripo_ell_mask, shot, prec, d,
+                         randoms ? &r : nullptr, sc, dev_out, out_len));
   NPC_TRY(finish_output(ctx, dev_out, out, out_len, out_on_device));
   NPC_TRY(stage_mark(ctx, "download"));
   return end_call(ctx);

@@ -53,7 +53,7 @@ k_fft_x_combine(const cplx<T>* __restrict__ half, int nout, int nphase, int KZ, 
   C* phs = tw + N;
   C* rows = phs + N;
   const int nf = nout * nphase;
-  T* winv = reinterpret_cast<T*>(rows + (size_t)(nf + G) * NP);
+  T* winv = reinterpret_cast<T*>(rows + (size_t)(nf + RowGroups<N, BT>::NBUF) * NP);
   const int tid = threadIdx.x;
   for (int i = tid; i < N; i += blockDim.x) {
     tw[i] = tw_g[i];
@@ -82,7 +82,7 @@ k_fft_x_combine(const cplx<T>* __restrict__ half, int nout, int nphase, int KZ, 
 #pragma unroll
         for (int q = 0; q < 8; ++q) v[q] = cmk(T(0), T(0));
       }
-      RowView<C> rv{rows + (size_t)(live ? f : nf + (g < G ? g : 0)) * NP};
+      RowView<C> rv{rows + (size_t)(live ? f : nf + g) * NP};
       fft_block<N, -1>(v, t, tw, rv);
       if (live) {
 #pragma unroll
@@ -272,7 +272,7 @@ k_shell_x(const cplx<T>* __restrict__ X0, int KZX, const ShellField* __restrict_
         }
         v[q] = a;
       }
-      fft_block<N, +1>(v, t, tw, RowView<C>{bufs + (size_t)(g < G ? g : 0) * NP});
+      fft_block<N, +1>(v, t, tw, RowView<C>{bufs + (size_t)g * NP});
       if (live) {
         C* dst = T1 + sf.off1 + ((size_t)kz * (2 * sf.K + 1) + (jy + sf.K)) * N;
 #pragma unroll
@@ -736,7 +736,8 @@ Tri make_triangles(const npc_kbins& kb) {
 
 template <typename T, int N>
 npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb, int scoc_mask, int tripo_mask,
-                       int shot, const DevCatalog& d, double* sc, double* dev_out, int64_t out_len) {
+                       int shot, const DevCatalog& d, const DevCatalog* r, double* sc, double* dev_out,
+                       int64_t out_len) {
   using C = cplx<T>;
   const double kf = 2.0 * M_PI / m.box;
   const double kmax = kb.kmin + kb.nbins * kb.dk;
@@ -755,9 +756,12 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
     g.global_los = 1;
     return g;
   }();
-  double l3[3] = {m.los_dir[0], m.los_dir[1], m.los_dir[2]};
-  const double ll = std::sqrt(l3[0] * l3[0] + l3[1] * l3[1] + l3[2] * l3[2]);
-  for (double& v : l3) v /= ll;
+  // global line of sight (only the l = 2 terms use it; the monopoles of a survey need none)
+  double l3[3] = {0.0, 0.0, 1.0};
+  if (m.los == 1) {
+    const double ll = std::sqrt(m.los_dir[0] * m.los_dir[0] + m.los_dir[1] * m.los_dir[1] + m.los_dir[2] * m.los_dir[2]);
+    for (int a = 0; a < 3; ++a) l3[a] = m.los_dir[a] / ll;
+  }
 
   // 1. paint + forward transforms of F and N fields
   const size_t rs = sizeof(T);
@@ -783,11 +787,11 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
   C* halfF = (C*)half;
   C* halfN = (C*)((char*)half + halfbytes);
   NPC_TRY(stage_mark(ctx, "alloc"));
-  NPC_TRY(launch_paint(ctx, d, nullptr, m, 1, prec, sc, ma, mb));
+  NPC_TRY(launch_paint(ctx, d, r, m, 1, prec, sc, ma, mb));
   NPC_TRY(stage_mark(ctx, "paint_fold"));
   NPC_TRY(run_forward_transforms(ctx, prec, plan, geo, ma, mb, halfF));
   if (shot) {
-    NPC_TRY(launch_paint(ctx, d, nullptr, m, 2, prec, sc, ma, mb));
+    NPC_TRY(launch_paint(ctx, d, r, m, 2, prec, sc, ma, mb));
     NPC_TRY(run_forward_transforms(ctx, prec, plan, geo, ma, mb, halfN));
   }
   NPC_TRY(stage_mark(ctx, "forward_yz"));
@@ -806,7 +810,8 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
     const int nf = nphase * nout;
     // F and N halves are separate buffers: combine each
     for (int o = 0; o < nout; ++o) {
-      const size_t smem = sizeof(C) * (2 * N + (size_t)(nphase + G) * row_pad_len<N>()) + sizeof(T) * (N / 2 + 2);
+      const size_t smem =
+          sizeof(C) * (2 * N + (size_t)(nphase + RowGroups<N, BT>::NBUF) * row_pad_len<N>()) + sizeof(T) * (N / 2 + 2);
       auto kern = k_fft_x_combine<T, N>;
       NPC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       const int nrows = KZ * (2 * K2 + 1);
@@ -860,8 +865,9 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
   const Tri tr = make_triangles(kb);
   const int ntri = (int)tr.tri.size() / 3, npair = (int)tr.pij.size();
   double* nt_sums;
-  NPC_TRY(ws_get(ctx, "bis.ntsums", sizeof(double) * npair * nb, (void**)&nt_sums));
-  auto it = ctx->host_cache_keys.find("bis.ntsums");
+  const std::string ntname = slot_name(ctx, "bis.ntsums");
+  NPC_TRY(ws_get(ctx, ntname.c_str(), sizeof(double) * npair * nb, (void**)&nt_sums));
+  auto it = ctx->host_cache_keys.find(ntname);
   const bool need_nt = it == ctx->host_cache_keys.end() || it->second != ntkey;
 
   std::vector<ShellField> fl;
@@ -924,8 +930,7 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
   const size_t t_tri = push_bytes(tr.tri.data(), sizeof(int) * tr.tri.size());
   const size_t t_pij = push_bytes(tr.pij.data(), sizeof(int) * tr.pij.size());
   char* dtab;
-  NPC_TRY(ws_get(ctx, "bis.tables", tables.size(), (void**)&dtab));
-  NPC_CUDA(ctx, cudaMemcpyAsync(dtab, tables.data(), tables.size(), cudaMemcpyHostToDevice, ctx->stream));
+  NPC_TRY(ws_table(ctx, "bis.tables", tables, tables.data(), tables.size(), (void**)&dtab));
   const ShellField* dfields = (const ShellField*)(dtab + t_fields);
   C *T1, *T2;
   T* R;
@@ -937,7 +942,8 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
   {
     constexpr int TPF = N / 8;
     constexpr int G = BT / TPF > 0 ? BT / TPF : 1;
-    const size_t smem = sizeof(C) * (2 * N + (size_t)G * row_pad_len<N>()) + sizeof(T) * N + sizeof(int) * 2 * N;
+    const size_t smem = sizeof(C) * (2 * N + (size_t)RowGroups<N, BT>::NBUF * row_pad_len<N>()) + sizeof(T) * N +
+                        sizeof(int) * 2 * N;
     auto kern = k_shell_x<T, N>;
     NPC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int Kmax = std::max(K, ng ? K2 : 0);
@@ -1023,7 +1029,7 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
     k_nt_reduce<<<(npair * nb + 127) / 128, 128, 0, ctx->stream>>>(part, grid, npair, nb, nb, (double)ncell,
                                                                   nt_sums);
     NPC_LAUNCH(ctx);
-    ctx->host_cache_keys["bis.ntsums"] = ntkey;
+    ctx->host_cache_keys[ntname] = ntkey;
   }
   NPC_TRY(launch(ta));
   NPC_TRY(stage_mark(ctx, "triple"));
@@ -1058,16 +1064,19 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
 
 template <typename T>
 npc_status bispec_dispatch(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb, int sm, int tm, int shot,
-                           const DevCatalog& d, double* sc, double* out, int64_t len) {
+                           const DevCatalog& d, const DevCatalog* r, double* sc, double* out, int64_t len) {
   switch (m.n) {
-    case 16: return bispec_impl<T, 16>(ctx, m, kb, sm, tm, shot, d, sc, out, len);
-    case 32: return bispec_impl<T, 32>(ctx, m, kb, sm, tm, shot, d, sc, out, len);
-    case 64: return bispec_impl<T, 64>(ctx, m, kb, sm, tm, shot, d, sc, out, len);
-    case 128: return bispec_impl<T, 128>(ctx, m, kb, sm, tm, shot, d, sc, out, len);
-    case 256: return bispec_impl<T, 256>(ctx, m, kb, sm, tm, shot, d, sc, out, len);
+    case 16: return bispec_impl<T, 16>(ctx, m, kb, sm, tm, shot, d, r, sc, out, len);
+    case 32: return bispec_impl<T, 32>(ctx, m, kb, sm, tm, shot, d, r, sc, out, len);
+    case 64: return bispec_impl<T, 64>(ctx, m, kb, sm, tm, shot, d, r, sc, out, len);
+    case 128: return bispec_impl<T, 128>(ctx, m, kb, sm, tm, shot, d, r, sc, out, len);
+    case 256: return bispec_impl<T, 256>(ctx, m, kb, sm, tm, shot, d, r, sc, out, len);
+    case 48: return bispec_impl<T, 48>(ctx, m, kb, sm, tm, shot, d, r, sc, out, len);
+    case 96: return bispec_impl<T, 96>(ctx, m, kb, sm, tm, shot, d, r, sc, out, len);
+    case 192: return bispec_impl<T, 192>(ctx, m, kb, sm, tm, shot, d, r, sc, out, len);
   }
   if constexpr (sizeof(T) == 4) {
-    if (m.n == 512) return bispec_impl<T, 512>(ctx, m, kb, sm, tm, shot, d, sc, out, len);
+    if (m.n == 512) return bispec_impl<T, 512>(ctx, m, kb, sm, tm, shot, d, r, sc, out, len);
   }
   return set_err(ctx, NPC_ERR_UNSUPPORTED, "bispectrum mesh size %d not supported at this precision", m.n);
 }
@@ -1075,9 +1084,11 @@ npc_status bispec_dispatch(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins
 }  // namespace
 
 npc_status run_bispectrum(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb, int scoc_mask, int tripo_mask,
-                          int shot, int prec, const DevCatalog& d, double* sc, double* out, int64_t len) {
-  if (prec == NPC_PREC_FP64) return bispec_dispatch<double>(ctx, m, kb, scoc_mask, tripo_mask, shot, d, sc, out, len);
-  return bispec_dispatch<float>(ctx, m, kb, scoc_mask, tripo_mask, shot, d, sc, out, len);
+                          int shot, int prec, const DevCatalog& d, const DevCatalog* r, double* sc, double* out,
+                          int64_t len) {
+  if (prec == NPC_PREC_FP64)
+    return bispec_dispatch<double>(ctx, m, kb, scoc_mask, tripo_mask, shot, d, r, sc, out, len);
+  return bispec_dispatch<float>(ctx, m, kb, scoc_mask, tripo_mask, shot, d, r, sc, out, len);
 }
 
 int64_t bispec_counts(const npc_kbins& kb, int64_t* ntri, int64_t* npair) {

@@ -434,7 +434,7 @@ npc_status paint_impl(npc_ctx* ctx, const DevCatalog& d, const DevCatalog* r, co
                       int weight_power, const double* sc, void* mesh_a, void* mesh_b) {
   PaintGeo g;
   g.n = m.n;
-  g.bs = m.n >= 64 ? 16 : m.n / 4;
+  g.bs = (m.n >= 48 && m.n % 16 == 0) ? 16 : m.n / 4;   // 16 for every size >= 48; 4, 8 at n = 16, 32
   g.nb = m.n / g.bs;
   g.ts = g.bs + 4;
   for (int a = 0; a < 3; ++a) g.o[a] = m.origin[a];

@@ -56,23 +56,44 @@ __device__ __forceinline__ void dft8(C (&v)[8]) {
   v[1] = c0; v[3] = c1; v[5] = c2; v[7] = c3;
 }
 
-// Shared-memory views used for the inter-stage exchange.
+// Shared-memory views used for the inter-stage exchange.  sub(off) is the view of the elements
+// from `off` on (off a multiple of 8), used by the sub-transforms of a composite length.
 template <typename C> struct ColView {  // element n of column at p[n*stride]
   C* p;
   int stride;
   __device__ __forceinline__ void st(int n, C v) const { p[n * stride] = v; }
   __device__ __forceinline__ C ld(int n) const { return p[n * stride]; }
+  __device__ __forceinline__ ColView sub(int off) const { return ColView{p + off * stride, stride}; }
 };
 template <typename C> struct RowView {  // element n at p[n + n/8] (one pad slot per 8)
   C* p;
   __device__ __forceinline__ static int idx(int n) { return n + (n >> 3); }
   __device__ __forceinline__ void st(int n, C v) const { p[idx(n)] = v; }
   __device__ __forceinline__ C ld(int n) const { return p[idx(n)]; }
+  __device__ __forceinline__ RowView sub(int off) const { return RowView{p + idx(off)}; }
 };
 template <int N> __host__ __device__ constexpr int row_pad_len() { return N + N / 8; }
 
+// Supported transform lengths: powers of two >= 16, and three times a power of two >= 48.
+template <int N> struct FftLen {
+  static constexpr bool pow2 = (N & (N - 1)) == 0;
+  static constexpr int M = pow2 ? N : N / 3;  // power-of-two factor
+  static_assert(N >= 16 && (M & (M - 1)) == 0 && (pow2 || (N % 3 == 0 && M >= 16)),
+                "transform length must be 2^k >= 16 or 3 * 2^k >= 48");
+};
+
+// Rows of length N transformed side by side by THREADS threads, TPF = N/8 per row: G row groups and
+// the number of exchange buffers, one per group plus one scratch buffer for the leftover threads
+// when TPF does not divide THREADS (they transform zeros so that every thread meets each barrier).
+template <int N, int THREADS> struct RowGroups {
+  static constexpr int TPF = N / 8;
+  static constexpr int G = THREADS / TPF > 0 ? THREADS / TPF : 1;
+  static constexpr int NBUF = (THREADS % TPF) ? G + 1 : G;
+};
+
 // All threads of the block must call this the same number of times (it contains __syncthreads).
-template <int N, int DIR, int Ns, typename C, typename View>
+// TS: stride into the twiddle table (a length-N/TS sub-transform reads every TS-th twiddle of N).
+template <int N, int DIR, int Ns, int TS = 1, typename C, typename View>
 __device__ __forceinline__ void fft_stages(C (&v)[8], const int t, const C* __restrict__ tw,
                                            const View& buf) {
   constexpr int TPF = N / 8;
@@ -88,7 +109,7 @@ __device__ __forceinline__ void fft_stages(C (&v)[8], const int t, const C* __re
 #pragma unroll
       for (int r = 1; r < R; ++r) {
         const int j = r * k * (N / (Ns * R));
-        v[s + r * BPT] = cmul(v[s + r * BPT], twiddle<C, DIR>(tw, j));
+        v[s + r * BPT] = cmul(v[s + r * BPT], twiddle<C, DIR>(tw, j * TS));
       }
     }
     if constexpr (R == 8) {
@@ -111,14 +132,47 @@ __device__ __forceinline__ void fft_stages(C (&v)[8], const int t, const C* __re
 #pragma unroll
     for (int q = 0; q < 8; ++q) v[q] = buf.ld(t + q * TPF);
     __syncthreads();
-    fft_stages<N, DIR, Ns * R>(v, t, tw, buf);
+    fft_stages<N, DIR, Ns * R, TS>(v, t, tw, buf);
   }
 }
 
-// Length-N transform of the elements held in v (thread t of TPF = N/8 threads).
+// Length-N transform of the elements held in v (thread t of TPF = N/8 threads); `tw` is the
+// length-N twiddle table.  For N = 3M (M a power of two) the transform is split by decimation in
+// time: the three length-M transforms of x[3m + r] (r = 0, 1, 2) run side by side, one per third
+// of the threads, then X[k] = A_0[k mod M] + w^k A_1[k mod M] + w^{2k} A_2[k mod M] with
+// w = exp(DIR 2 pi i / N).  Inputs and outputs keep the natural order t + q TPF; the buffer
+// holds N elements and may be reused by the caller as soon as this returns.
 template <int N, int DIR, typename C, typename View>
 __device__ __forceinline__ void fft_block(C (&v)[8], const int t, const C* __restrict__ tw,
                                           const View& buf) {
-  static_assert(N >= 16 && (N & (N - 1)) == 0, "N must be a power of two >= 16");
-  fft_stages<N, DIR, 1>(v, t, tw, buf);
+  using L = FftLen<N>;
+  if constexpr (L::pow2) {
+    fft_stages<N, DIR, 1>(v, t, tw, buf);
+  } else {
+    constexpr int M = L::M;
+    constexpr int TPF = N / 8, SUB = M / 8;
+    const int r = t / SUB, s = t % SUB;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) buf.st(t + q * TPF, v[q]);
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = buf.ld(3 * (s + q * SUB) + r);
+    __syncthreads();
+    const View sb = buf.sub(r * M);
+    fft_stages<M, DIR, 1, 3>(v, s, tw, sb);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) sb.st(s + q * SUB, v[q]);
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int k = t + q * TPF;
+      const int km = k % M;
+      const int k2 = (2 * k) % N;
+      C a = buf.ld(km);
+      a = cadd(a, cmul(buf.ld(M + km), twiddle<C, DIR>(tw, k)));
+      a = cadd(a, cmul(buf.ld(2 * M + km), twiddle<C, DIR>(tw, k2)));
+      v[q] = a;
+    }
+    __syncthreads();
+  }
 }

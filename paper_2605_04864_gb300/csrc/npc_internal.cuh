@@ -172,7 +172,20 @@ struct npc_ctx {
   std::vector<int> stage_launches;
   int ev_used = 0;
   int launches_at_mark = 0;
+  // batches: cached device tables are named per measurement slot so that a captured graph of
+  // many measurements never re-uploads a table; while capturing, workspace growth and table
+  // uploads are errors (the warm-up run sizes everything first)
+  int slot_base = 0;
+  bool capturing = false;
+  uint64_t ws_generation = 0;          // bumped whenever a workspace buffer moves
+  std::vector<npc_ctx*> subs;          // per-branch contexts of the batch executor
+  std::map<std::string, struct BatchGraph*> graphs;
+  int batch_branches = 0;              // 0: not tuned (default 4)
+  std::map<int, int> ytx;              // tuned columns per CTA of the y pass, per (n * 2 + fp64)
 };
+
+// slot-qualified name of a cached table or cache entry
+std::string slot_name(const npc_ctx* ctx, const std::string& name);
 
 // Marks the end of a stage named `name` (and the start of the next) when profiling is on.
 npc_status stage_mark(npc_ctx* ctx, const char* name);
@@ -266,6 +279,11 @@ struct PowerPlan {
   int kz_keep;          // forward passes keep kz < kz_keep (0: all, n/2)
 };
 
+// Catalogue -> P_l after validation, staging and the catalogue scalars `sc` (api.cu).
+npc_status power_core(npc_ctx* ctx, const npc_mesh_spec& ms, const DevCatalog& d, const DevCatalog* r,
+                      const npc_kbins& kb, uint32_t ell_mask, uint32_t modified_mask, int prec, const double* sc,
+                      double* dev_out);
+
 npc_status run_forward_transforms(npc_ctx* ctx, int prec, const PowerPlan& plan, const Geom& g,
                                   const void* mesh_a, const void* mesh_b, void* half);
 npc_status run_power_contract(npc_ctx* ctx, int prec, const PowerPlan& plan, const npc_mesh_spec& m,
@@ -281,6 +299,7 @@ npc_status get_twiddles(npc_ctx* ctx, int n, int prec, const void** out);
 // Bispectrum (bispec.cu)
 // ---------------------------------------------------------------------------------------------
 npc_status run_bispectrum(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb, int scoc_mask, int tripo_mask,
-                          int shot, int prec, const DevCatalog& d, double* sc, double* out, int64_t len);
+                          int shot, int prec, const DevCatalog& d, const DevCatalog* r, double* sc, double* out,
+                          int64_t len);
 int64_t bispec_counts(const npc_kbins& kb, int64_t* ntri, int64_t* npair);
 npc_status bispec_triangles(const npc_kbins& kb, int32_t* tri, int64_t cap, int64_t* ntri);

@@ -113,7 +113,7 @@ k_fwd_z(const T* __restrict__ mesh_a, const T* __restrict__ mesh_b, cplx<T>* __r
     for (int i = tid; i < KZ * TX; i += blockDim.x) {
       const int kz = i / TX, cc = i % TX;
       const C z1 = work[kz * TX + cc];
-      const C z2 = cconj(work[((N - kz) & (N - 1)) * TX + cc]);
+      const C z2 = cconj(work[((N - kz) % N) * TX + cc]);
       const C a = cscale(cadd(z1, z2), T(0.5));
       const C d = csub(z1, z2);
       const C b = cmk(T(0.5) * d.y, T(-0.5) * d.x);
@@ -259,7 +259,7 @@ k_fwd_z_std(const T* __restrict__ mesh_a, const T* __restrict__ mesh_b, cplx<T>*
     for (int i = tid; i < KZ * TX; i += blockDim.x) {
       const int kz = i / TX, cc = i % TX;
       const C z1 = work[kz * TX + cc];
-      const C z2 = cconj(work[((N - kz) & (N - 1)) * TX + cc]);
+      const C z2 = cconj(work[((N - kz) % N) * TX + cc]);
       const C a = cscale(cadd(z1, z2), T(0.5));
       const C d = csub(z1, z2);
       const C b = cmk(T(0.5) * d.y, T(-0.5) * d.x);
@@ -363,7 +363,8 @@ __device__ __forceinline__ T sinc_pow(T a, int p) {
 
 template <int N> struct XCfg {
   static constexpr int TPF = N / 8;
-  static constexpr int G = CONTRACT_THREADS / TPF > 0 ? CONTRACT_THREADS / TPF : 1;  // rows in flight
+  static constexpr int G = RowGroups<N, CONTRACT_THREADS>::G;        // rows in flight
+  static constexpr int NBUF = RowGroups<N, CONTRACT_THREADS>::NBUF;  // exchange buffers
 };
 
 // Last pass.  For one (ky, kz) row: every field row is transformed along x and added, with its
@@ -386,7 +387,7 @@ k_fft_x_contract(const cplx<T>* __restrict__ half, const ContractParams P, const
   C* ytab = phs + N;                        // [ny][N]
   C* facc = ytab + (size_t)P.ny * N;        // [G][nacc][N]
   C* rowbuf = facc + (size_t)G * P.nacc * N;  // [G][NP]
-  T* winv = reinterpret_cast<T*>(rowbuf + (size_t)G * NP);  // 1/sinc^p, a = 0..N/2
+  T* winv = reinterpret_cast<T*>(rowbuf + (size_t)XCfg<N>::NBUF * NP);  // 1/sinc^p, a = 0..N/2
   T* fa = winv + (N / 2 + 2);               // phase-a factor per kx
   T* fidx = fa + N;                         // signed frequency index of storage position, as T
   const int tid = threadIdx.x;
@@ -448,7 +449,7 @@ k_fft_x_contract(const cplx<T>* __restrict__ half, const ContractParams P, const
 #pragma unroll
         for (int q = 0; q < 8; ++q) v[q] = cmk(T(0), T(0));
       }
-      fft_block<N, -1>(v, t, tw, RowView<C>{rowbuf + (size_t)(ingroup ? g : 0) * NP});
+      fft_block<N, -1>(v, t, tw, RowView<C>{rowbuf + (size_t)(ingroup ? g : G) * NP});
       if (live) {
         const FieldCoef c = P.fc[f];
         C* acc = facc + ((size_t)g * P.nacc + c.acc) * N;
@@ -721,7 +722,8 @@ npc_status contract_impl(npc_ctx* ctx, const PowerPlan& plan, const npc_mesh_spe
 
   constexpr int NP = row_pad_len<N>();
   constexpr int G = XCfg<N>::G;
-  const size_t smem = sizeof(C) * ((size_t)2 * N + (size_t)P.ny * N + (size_t)G * P.nacc * N + (size_t)G * NP) +
+  const size_t smem = sizeof(C) * ((size_t)2 * N + (size_t)P.ny * N + (size_t)G * P.nacc * N +
+                                   (size_t)XCfg<N>::NBUF * NP) +
                       sizeof(T) * (N / 2 + 2 + 2 * N);
   auto kern = k_fft_x_contract<T, N>;
   NPC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -762,7 +764,7 @@ npc_status contract_impl(npc_ctx* ctx, const PowerPlan& plan, const npc_mesh_spe
   return NPC_OK;
 }
 
-// float32 transforms for 16 <= n <= 1024; float64 transforms for n <= 256
+// float32 transforms for n = 2^k in [16, 1024] and n = 48, 96, 192; float64 transforms for n <= 256
 template <typename T>
 npc_status fwd_dispatch(npc_ctx* ctx, const PowerPlan& plan, const Geom& g, const void* a, const void* b, void* half) {
   switch (plan.n) {
@@ -771,6 +773,9 @@ npc_status fwd_dispatch(npc_ctx* ctx, const PowerPlan& plan, const Geom& g, cons
     case 64: return fwd_impl<T, 64>(ctx, plan, g, a, b, half);
     case 128: return fwd_impl<T, 128>(ctx, plan, g, a, b, half);
     case 256: return fwd_impl<T, 256>(ctx, plan, g, a, b, half);
+    case 48: return fwd_impl<T, 48>(ctx, plan, g, a, b, half);
+    case 96: return fwd_impl<T, 96>(ctx, plan, g, a, b, half);
+    case 192: return fwd_impl<T, 192>(ctx, plan, g, a, b, half);
   }
   if constexpr (sizeof(T) == 4) {
     if (plan.n == 512) return fwd_impl<T, 512>(ctx, plan, g, a, b, half);
@@ -788,6 +793,9 @@ npc_status contract_dispatch(npc_ctx* ctx, const PowerPlan& plan, const npc_mesh
     case 64: return contract_impl<T, 64>(ctx, plan, m, kb, half, sc, out);
     case 128: return contract_impl<T, 128>(ctx, plan, m, kb, half, sc, out);
     case 256: return contract_impl<T, 256>(ctx, plan, m, kb, half, sc, out);
+    case 48: return contract_impl<T, 48>(ctx, plan, m, kb, half, sc, out);
+    case 96: return contract_impl<T, 96>(ctx, plan, m, kb, half, sc, out);
+    case 192: return contract_impl<T, 192>(ctx, plan, m, kb, half, sc, out);
   }
   if constexpr (sizeof(T) == 4) {
     if (plan.n == 512) return contract_impl<T, 512>(ctx, plan, m, kb, half, sc, out);

@@ -55,6 +55,19 @@ def test_fp64_small_periodic(api, assign, interlace):
     _check(res, orc, 1e-10)
 
 
+@pytest.mark.parametrize("n,prec,tol", [(48, "fp64", 1e-10), (96, "mixed", 1e-4)])
+def test_radix3_meshes(api, n, prec, tol):
+    """Meshes of 3 * 2^k cells through the whole bispectrum path (forward, shell inverses, triple
+    products, shot noise)."""
+    box = 300.0 * n / 32
+    cat = make_periodic_catalog(30000, box, 32, seed=43 + n)
+    kf = 2 * np.pi / box
+    kb = (2 * kf, 1.5 * kf, 5)   # k_max = 9.5 k_f < k_N/2 = n k_f/4
+    res = api.bispectrum(cat, n=n, box=box, kbins=kb, precision=prec)
+    orc = OB.bispectrum(_spec(n, box), cat, None, kb, (0, 2), (0, 2), shot=True)
+    _check(res, orc, tol)
+
+
 def test_mixed_19_bins_805_triangles_128(api):
     """The 19-bin / 805-triangle layout of the 256^3 workload on a 128^3 mesh of the same box
     (k_max = 0.2 = k_N/2), float32 transforms: <= 1e-4."""

@@ -72,6 +72,20 @@ def test_mixed_tsc_interlaced_modified(api, n):
     _compare(res, orc, (0, 2, 4), (4, 6, 8), 1e-5)
 
 
+@pytest.mark.parametrize("n,prec,tol", [(48, "fp64", 1e-12), (96, "mixed", 1e-5), (192, "mixed", 1e-5)])
+def test_radix3_meshes(api, n, prec, tol):
+    """Meshes of 3 * 2^k cells (48, 96, 192: transforms split into three power-of-two transforms
+    and a radix-3 combination), survey geometry, TSC + interlacing, P_0,2,4 + P_4b,6b,8b."""
+    box = 900.0
+    g, r, origin = make_survey_catalogs(30000, 300000, box, 1400.0, 48, seed=300 + n, fkp_p0=1e4)
+    kn = np.pi * n / box
+    kb = (0.0, 0.01, int(kn / 0.01))
+    res = api.power_multipoles(g, r, n=n, box=box, origin=origin, assign=3, interlace=1, kbins=kb,
+                               ells=(0, 2, 4), modified=(4, 6, 8), precision=prec)
+    orc = _oracle(g, r, origin, n, box, 3, 1, kb, (0, 2, 4), (4, 6, 8))
+    _compare(res, orc, (0, 2, 4), (4, 6, 8), tol)
+
+
 def test_fp64_ragged_bins_and_subsets(api):
     """Ragged bins (kmin offset, odd dk, partial coverage), a subset of multipoles, float64 input."""
     box = 700.0
