@@ -297,6 +297,70 @@ def adjoint_leg(args, world, rank, barrier, max_over_ranks):
                        "assign": "TSC", "interlace": False, "precision": w["precision"]}}
 
 
+def batch_leg(args, world, rank, barrier, max_over_ranks):
+    """Mocks/s for 96 survey mocks of uneven size in one batch (32 each at 128^3, 192^3, 256^3):
+    P_0,2,4 and B_0 with analytic shot noise per mock, through npc_batch_run.  The graph form (one
+    graph launch per batch after the first call) and the eager form are both timed; the autotuner
+    picks the y-pass tile per mesh size and the number of concurrent branches first."""
+    from types import SimpleNamespace
+
+    import torch
+
+    from paper_2605_04864_gb300 import api
+    from synthetic import base_catalogues, batch_plan, workload
+
+    w = workload("batch_96")
+    plan = batch_plan(w)
+    gmax = max(m["n_gal"] for m in plan)
+    rmax = max(m["n_ran"] for m in plan)
+    gb, rb = base_catalogues(gmax, rmax, 256, w["seed"] + rank)
+    gb, rb = torch.from_numpy(gb).cuda(), torch.from_numpy(rb).cuda()
+    items = []
+    for m in plan:
+        o = torch.tensor(m["origin"], dtype=torch.float32, device="cuda")
+        cat = lambda base, k: SimpleNamespace(pos=(base[:k] * m["box"] + o).contiguous(),
+                                              w=torch.full((k,), m["weight"], device="cuda"),
+                                              nbar=torch.full((k,), m["nbar"], device="cuda"))
+        items.append(dict(n=m["n"], box=m["box"], origin=m["origin"], assign=w["assign"], interlace=w["interlace"],
+                          data=cat(gb, m["n_gal"]), randoms=cat(rb, m["n_ran"]),
+                          power_bins=(0.0, w["dk"], m["pk_nbins"]),
+                          bispec_bins=(w["bk_kmin"], w["dk"], m["bk_nbins"])))
+    del gb, rb
+    arr, keep = api.make_batch(items)
+    total, _ = api.batch_layout(arr, w["ells"])
+    out = torch.zeros(total, dtype=torch.float64, device="cuda")
+    t0 = time.perf_counter()
+    branches = api.batch_tune(arr, out, w["ells"], precision=w["precision"])
+    tune_s = time.perf_counter() - t0
+
+    def timed(graph):
+        for _ in range(args.warmup):
+            api.batch_run(arr, out, w["ells"], precision=w["precision"], graph=graph)
+        torch.cuda.synchronize()
+        barrier()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        for _ in range(args.steps):
+            api.batch_run(arr, out, w["ells"], precision=w["precision"], graph=graph)
+        e.record()
+        torch.cuda.synchronize()
+        barrier()
+        return max_over_ranks(s.elapsed_time(e)) / args.steps
+
+    ms_graph = timed(True)
+    launches = api.last_stats()["n_kernel_launches"]
+    ms_eager = timed(False)
+    nm = len(plan)
+    del keep, items, arr, out
+    torch.cuda.empty_cache()
+    return {"metric": "mocks/s (96 survey mocks, 32 each at 128^3/192^3/256^3, P_0,2,4 + B_0 with shot noise)",
+            "value": world * nm / (ms_graph / 1e3), "unit": "mocks/s", "ms_per_batch": ms_graph,
+            "eager": {"value": world * nm / (ms_eager / 1e3), "ms_per_batch": ms_eager},
+            "branches": branches, "tune_seconds": tune_s, "kernels_per_batch": launches,
+            "config": {"workload": "batch_96", "mocks": nm, "n_gal_total": sum(m["n_gal"] for m in plan),
+                       "n_ran_total": sum(m["n_ran"] for m in plan), "precision": w["precision"]}}
+
+
 def power_leg(args, w, world, local, rank, barrier, max_over_ranks):
     """The headline leg: catalogue -> P_l measurements at 512^3, device-resident and end to end."""
     import ctypes as C
@@ -419,6 +483,7 @@ def main():
     ap.add_argument("--no-power", action="store_true", help="skip the headline leg (profiling of the others)")
     ap.add_argument("--no-bispec", action="store_true", help="skip the 256^3 bispectrum leg")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the 1024^3 gradient leg")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 96-mock batch leg")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -464,6 +529,8 @@ def main():
         line["gpu_launches"] = line.get("gpu_launches", 0) + sec["gpu_launches"]
     if not args.no_adjoint:
         line["gradient"] = adjoint_leg(args, world, rank, barrier, max_over_ranks)
+    if not args.no_batch:
+        line["batch"] = batch_leg(args, world, rank, barrier, max_over_ranks)
     if rank == 0 and not args.no_power and not args.no_cpu_baseline and world == 1:
         dt, scale, desc = cpu_baseline(w)
         line["cpu_baseline"] = {"value": 1.0 / (dt * scale), "unit": UNIT, "cores": 1, "kind": "oracle",

@@ -196,6 +196,45 @@ npc_status npc_bispectrum_layout(const npc_kbins* bins, uint32_t scoc_ell_mask,
 npc_status npc_bispectrum_triangles(const npc_kbins* bins, int32_t* tri, int64_t cap,
                                     int64_t* ntri);
 
+/* Batches of measurements --------------------------------------------------------------------------
+ * Many mocks of uneven catalogue size and mesh, each measured as npc_power_multipoles (P_l for
+ * ell_mask, no modified multipoles) and, when bispec_bins.nbins > 0, as npc_bispectrum with the
+ * Scoccimarro monopole B_0 and its analytic shot noise (scoc_ell_mask = 1, tripo_ell_mask = 0,
+ * shot = 1; periodic boxes and survey geometry).  The paper measures its estimators mock by mock;
+ * the batch changes only how the work is scheduled, not what is computed: every item's output
+ * equals, bit for bit, the single call on the same inputs.
+ * Items run on concurrent branches (private streams and workspaces of the context); with
+ * NPC_BATCH_GRAPH the first call of a batch shape also captures the whole sequence into a CUDA
+ * graph, and later calls with identical items (same pointers, sizes and specs) and the same
+ * output pointer replay it with one graph launch.  Catalogues must be device memory that stays
+ * valid (and may be refilled in place) while graphs of them are replayed. */
+#define NPC_BATCH_GRAPH 1
+
+typedef struct {
+  npc_mesh_spec mesh;
+  npc_catalog data;          /* device memory, n > 0 */
+  npc_catalog randoms;       /* device memory for a survey; n = 0 for a periodic box */
+  npc_kbins power_bins;
+  npc_kbins bispec_bins;     /* nbins = 0: no bispectrum; else largest edge <= k_N/2, nbins <= 24 */
+} npc_batch_item;
+
+/* Total output length in doubles for the batch (0 for a bad request); offsets[2i] and offsets[2i+1]
+ * (may be NULL) receive the start of item i's P_l block (layout of npc_power_multipoles) and of its
+ * B_0 block (layout of npc_bispectrum with one Scoccimarro multipole and no compressed one), or -1. */
+int64_t npc_batch_layout(int32_t nitems, const npc_batch_item* items, uint32_t ell_mask,
+                         int64_t* offsets);
+/* Run the batch; out_device (device memory, npc_batch_layout() doubles) receives every item's
+ * block.  Asynchronous on the context's stream.  flags: 0 or NPC_BATCH_GRAPH. */
+npc_status npc_batch_run(npc_ctx* ctx, int32_t nitems, const npc_batch_item* items, uint32_t ell_mask,
+                         npc_precision prec, double* out_device, int32_t flags);
+/* Autotuner: times, on this batch, the columns per CTA of the y transform pass for every mesh size
+ * and then the number of concurrent branches (graph replays), keeps the fastest choices in the
+ * context and reports the branch count.  Runs the batch several times (out_device is overwritten). */
+npc_status npc_batch_tune(npc_ctx* ctx, int32_t nitems, const npc_batch_item* items, uint32_t ell_mask,
+                          npc_precision prec, double* out_device, int32_t* branches);
+/* Fix the number of concurrent branches (1..16; 0 restores the default of 4). */
+npc_status npc_batch_set_branches(npc_ctx* ctx, int32_t branches);
+
 /* Mesh-level estimators and their adjoints ------------------------------------------------------
  * The paper defines its estimators as functions of the density field (Sec. 2.1 Eq. pk_final for
  * P_l; Sec. 2.2 Eq. bi_sco for B_l) but does not differentiate them.  These calls expose the same

@@ -185,23 +185,27 @@ def stage_times(device=0, cap=64):
 
 
 def bispectrum(data, n, box, kbins, scoc_ells=(0, 2), tripo_ells=(0, 2), shot=True, assign=3, interlace=1,
-               los_dir=(0.0, 0.0, 1.0), precision="mixed", origin=(0.0, 0.0, 0.0), device=0, out=None):
-    """Scoccimarro B_l and compressed B_l0l (periodic box, global line of sight)."""
+               los_dir=(0.0, 0.0, 1.0), precision="mixed", origin=(0.0, 0.0, 0.0), device=0, out=None,
+               randoms=None):
+    """Scoccimarro B_l and compressed B_l0l: periodic box with a global line of sight, or (with
+    ``randoms``) survey geometry for the monopoles."""
     keep = _Keep()
-    spec = make_spec(n, box, origin, assign, interlace, 1, los_dir)
+    spec = make_spec(n, box, origin, assign, interlace, 1 if randoms is None else 0, los_dir)
     kb = B.npc_kbins(float(kbins[0]), float(kbins[1]), int(kbins[2]))
     sm = sum(1 << int(l) for l in scoc_ells)
     tm = sum(1 << int(l) for l in tripo_ells)
     ntri, npair, length = C.c_int64(), C.c_int64(), C.c_int64()
     st = B.npc_bispectrum_layout(C.byref(kb), sm, tm, C.byref(ntri), C.byref(npair), C.byref(length))
     d = make_catalog(data, keep)
+    r = make_catalog(randoms, keep)
+    rp = C.byref(r) if r is not None else None
     ctx = context(device)
     if out is not None:
-        B.check(B.npc_bispectrum(ctx, C.byref(spec), C.byref(d), None, C.byref(kb), sm, tm, int(shot),
+        B.check(B.npc_bispectrum(ctx, C.byref(spec), C.byref(d), rp, C.byref(kb), sm, tm, int(shot),
                                  _prec(precision), C.c_void_p(out.data_ptr()), 1), ctx)
         return out
     buf = np.zeros(max(length.value, 1) if st == 0 else 1)
-    B.check(B.npc_bispectrum(ctx, C.byref(spec), C.byref(d), None, C.byref(kb), sm, tm, int(shot),
+    B.check(B.npc_bispectrum(ctx, C.byref(spec), C.byref(d), rp, C.byref(kb), sm, tm, int(shot),
                              _prec(precision), buf.ctypes.data_as(C.c_void_p), 0), ctx)
     return unpack_bispectrum(buf, kbins, scoc_ells, tripo_ells)
 
@@ -244,3 +248,52 @@ def unpack_bispectrum(buf, kbins, scoc_ells, tripo_ells):
     res["scalars"] = dict(zip(("alpha", "I22", "I33", "N0", "S3", "sum_wg", "sum_wr", "sum_w2"), buf[o:o + 8]))
     res["tri"] = bispectrum_triangles(kbins)
     return res
+
+
+def make_batch(items):
+    """ctypes array of npc_batch_item from dicts with keys n, box, data, and optionally origin,
+    assign, interlace, randoms, los_dir, observer, power_bins (kmin, dk, nbins), bispec_bins."""
+    keep = _Keep()
+    arr = (B.npc_batch_item * len(items))()
+    for i, it in enumerate(items):
+        rnd = it.get("randoms")
+        a = arr[i]
+        a.mesh = make_spec(it["n"], it["box"], it.get("origin", (0.0, 0.0, 0.0)), it.get("assign", 3),
+                           it.get("interlace", 1), 0 if rnd is not None else 1, it.get("los_dir"),
+                           it.get("observer", (0.0, 0.0, 0.0)))
+        a.data = make_catalog(it["data"], keep)
+        if rnd is not None:
+            a.randoms = make_catalog(rnd, keep)
+        a.power_bins = B.npc_kbins(*[float(v) for v in it["power_bins"][:2]], int(it["power_bins"][2]))
+        bb = it.get("bispec_bins")
+        a.bispec_bins = B.npc_kbins(*[float(v) for v in bb[:2]], int(bb[2])) if bb else B.npc_kbins(0.0, 1.0, 0)
+    return arr, keep
+
+
+def batch_layout(arr, ells=(0, 2, 4)):
+    emask = sum(1 << int(l) for l in ells)
+    offs = (C.c_int64 * (2 * len(arr)))()
+    total = B.npc_batch_layout(len(arr), arr, emask, offs)
+    return int(total), [(offs[2 * i], offs[2 * i + 1]) for i in range(len(arr))]
+
+
+def batch_run(arr, out, ells=(0, 2, 4), precision="mixed", graph=True, device=0):
+    """Runs the batch into the device tensor ``out`` (float64, batch_layout() long)."""
+    emask = sum(1 << int(l) for l in ells)
+    ctx = context(device)
+    B.check(B.npc_batch_run(ctx, len(arr), arr, emask, _prec(precision), C.c_void_p(out.data_ptr()),
+                            B.NPC_BATCH_GRAPH if graph else 0), ctx)
+    return out
+
+
+def batch_tune(arr, out, ells=(0, 2, 4), precision="mixed", device=0):
+    emask = sum(1 << int(l) for l in ells)
+    ctx = context(device)
+    nb = C.c_int32(0)
+    B.check(B.npc_batch_tune(ctx, len(arr), arr, emask, _prec(precision), C.c_void_p(out.data_ptr()),
+                             C.byref(nb)), ctx)
+    return nb.value
+
+
+def batch_set_branches(n, device=0):
+    B.check(B.npc_batch_set_branches(context(device), int(n)))

@@ -38,6 +38,14 @@ class npc_kbins(C.Structure):
     _fields_ = [("kmin", C.c_double), ("dk", C.c_double), ("nbins", C.c_int32)]
 
 
+class npc_batch_item(C.Structure):
+    _fields_ = [("mesh", npc_mesh_spec), ("data", npc_catalog), ("randoms", npc_catalog),
+                ("power_bins", npc_kbins), ("bispec_bins", npc_kbins)]
+
+
+NPC_BATCH_GRAPH = 1
+
+
 class npc_stats(C.Structure):
     _fields_ = [("n_transforms", C.c_int32), ("n_r2c_equivalent", C.c_int32), ("n_phases", C.c_int32),
                 ("n_kernel_launches", C.c_int32), ("workspace_bytes", C.c_int64)]
@@ -66,6 +74,12 @@ _sig = {
     "npc_catalog_scalars_noalloc": (C.c_int, [_P(npc_catalog), _P(npc_catalog), C.c_double, C.c_void_p,
                                               C.c_void_p, C.c_char_p, C.c_size_t]),
     "npc_set_profiling": (C.c_int, [C.c_void_p, C.c_int32]),
+    "npc_batch_layout": (C.c_int64, [C.c_int32, _P(npc_batch_item), C.c_uint32, _P(C.c_int64)]),
+    "npc_batch_run": (C.c_int, [C.c_void_p, C.c_int32, _P(npc_batch_item), C.c_uint32, C.c_int, C.c_void_p,
+                                C.c_int32]),
+    "npc_batch_tune": (C.c_int, [C.c_void_p, C.c_int32, _P(npc_batch_item), C.c_uint32, C.c_int, C.c_void_p,
+                                 _P(C.c_int32)]),
+    "npc_batch_set_branches": (C.c_int, [C.c_void_p, C.c_int32]),
     "npc_mesh_multipoles_len": (C.c_int64, [_P(npc_kbins), C.c_uint32, C.c_int32]),
     "npc_mesh_multipoles": (C.c_int, [C.c_void_p, _P(npc_mesh_spec), C.c_void_p, _P(npc_kbins), C.c_uint32,
                                       C.c_int32, C.c_double, C.c_double, C.c_double, C.c_int, C.c_void_p,

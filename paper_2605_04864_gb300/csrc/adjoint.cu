@@ -136,7 +136,7 @@ k_adj_xfwd(const cplx<T>* __restrict__ H, int K, int assign, const cplx<T>* __re
     const C* src = H + ((size_t)kz * N + ky) * N;
 #pragma unroll
     for (int q = 0; q < 8; ++q) v[q] = live ? src[t + q * TPF] : cmk(T(0), T(0));
-    fft_block<N, -1>(v, t, tw, RowView<C>{bufs + (size_t)g * NP});
+    fft_block<N, -1>(v, t, tw, RowView<C>{bufs + (size_t)g * NP}, RowSync<N, AT>::make(g));
     if (live) {
       const int aj = jy < 0 ? -jy : jy;
       const T wyz = winv[aj] * winv[kz];
@@ -239,24 +239,31 @@ struct GradArgs {
   double los[3];
 };
 
-template <typename T, int N>
+// The shell fields are band-limited (|q_i| <= K per component), so their products F^2, F^3 are
+// too (2K, 3K): sums over cells and the transforms of F^2 restricted to |q| <= K are exact on any
+// grid of NS >= 3K + 1 points per axis, up to the factor (n/NS)^3.  The shell passes therefore run
+// on the smallest supported NS (n itself for the final gradient), reading and writing the
+// compact rows of the n grid.  Row kx' of the NS grid holds the integer frequency
+// i = kx' (kx' < NS/2) or kx' - NS.
+template <typename T, int NS>
 __global__ void __launch_bounds__(AT)
-k_adj_rows_inv(const cplx<T>* __restrict__ X, int KM, const AFieldTable ft, const int16_t* __restrict__ bintab,
-               const GradArgs ga, int assign, const cplx<T>* __restrict__ tw_g, cplx<T>* __restrict__ T1) {
+k_adj_rows_inv(const cplx<T>* __restrict__ X, int KM, int nfine, const AFieldTable ft,
+               const int16_t* __restrict__ bintab, const GradArgs ga, int assign, const cplx<T>* __restrict__ tw_g,
+               cplx<T>* __restrict__ T1) {
   using C = cplx<T>;
-  constexpr int TPF = N / 8;
-  constexpr int G = AT / TPF;
-  constexpr int NP = row_pad_len<N>();
+  constexpr int TPF = NS / 8;
+  constexpr int G = RowGroups<NS, AT>::G;
+  constexpr int NP = row_pad_len<NS>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
-  C* xrow = tw + N;
-  C* grow = xrow + N;
-  C* bufs = grow + N;
-  T* winv = reinterpret_cast<T*>(bufs + (size_t)G * NP);
-  int* binrow = reinterpret_cast<int*>(winv + (N / 2 + 2));
+  C* xrow = tw + NS;
+  C* grow = xrow + NS;
+  C* bufs = grow + NS;
+  int* binrow = reinterpret_cast<int*>(bufs + (size_t)RowGroups<NS, AT>::NBUF * NP);
+  T* winv = reinterpret_cast<T*>(binrow + NS);       // 1/W per |i| of the n grid, |i| <= nfine/2
   const int tid = threadIdx.x;
-  for (int i = tid; i < N; i += blockDim.x) tw[i] = tw_g[i];
-  for (int i = tid; i <= N / 2; i += blockDim.x) winv[i] = T(1) / wsinc<T>(T(M_PI) * T(i) / T(N), assign);
+  for (int i = tid; i < NS; i += blockDim.x) tw[i] = tw_g[i];
+  for (int i = tid; i <= nfine / 2; i += blockDim.x) winv[i] = T(1) / wsinc<T>(T(M_PI) * T(i) / T(nfine), assign);
   const int g = tid / TPF, t = tid % TPF;
   const int nyr = 2 * KM + 1;
   const int nrows = (KM + 1) * nyr;
@@ -267,15 +274,17 @@ k_adj_rows_inv(const cplx<T>* __restrict__ X, int KM, const AFieldTable ft, cons
   for (int r = blockIdx.x; r < nrows; r += gridDim.x) {
     const int kz = r / nyr, jy = r % nyr - KM;
     const int ay = jy < 0 ? -jy : jy;
-    for (int kx = tid; kx < N; kx += blockDim.x) {
-      const int i = kx < N / 2 ? kx : kx - N;
+    for (int kx = tid; kx < NS; kx += blockDim.x) {
+      const int i = kx < NS / 2 ? kx : kx - NS;
+      const bool ok = i != -NS / 2 && i != -nfine / 2;
+      const int fx = i < 0 ? i + nfine : i;       // position in the n-grid row
       const int n2 = i * i + jy * jy + kz * kz;
-      const int bin = (i != -N / 2 && n2 > 0) ? bintab[n2] : -1;
+      const int bin = (ok && n2 > 0) ? bintab[n2] : -1;
       binrow[kx] = bin;
-      const C x = X ? X[(size_t)r * N + kx] : cmk(T(0), T(0));
+      const C x = (X && ok) ? X[(size_t)r * nfine + fx] : cmk(T(0), T(0));
       xrow[kx] = x;
       if (any_grad) {
-        C gv = Y ? Y[(size_t)r * N + kx] : cmk(T(0), T(0));
+        C gv = (Y && ok) ? Y[(size_t)r * nfine + fx] : cmk(T(0), T(0));
         if (ga.coef && bin >= 0) {
           const T kk = sqrt(T(n2));
           const T mu = (T(i) * T(ga.los[0]) + T(jy) * T(ga.los[1]) + T(kz) * T(ga.los[2])) / kk;
@@ -288,14 +297,14 @@ k_adj_rows_inv(const cplx<T>* __restrict__ X, int KM, const AFieldTable ft, cons
           }
           gv = cadd(gv, cscale(x, T(2) * kq));
         }
-        const T w = i == -N / 2 ? T(0) : winv[i < 0 ? -i : i] * winv[ay] * winv[kz];
+        const T w = ok ? winv[i < 0 ? -i : i] * winv[ay] * winv[kz] : T(0);
         grow[kx] = cscale(gv, w);
       }
     }
     __syncthreads();
     for (int f0 = 0; f0 < ft.nf; f0 += G) {
       const int f = f0 + g;
-      bool live = f < ft.nf;
+      bool live = g < G && f < ft.nf;
       AField sf{};
       if (live) {
         sf = ft.f[f];
@@ -312,9 +321,9 @@ k_adj_rows_inv(const cplx<T>* __restrict__ X, int KM, const AFieldTable ft, cons
         }
         v[q] = a;
       }
-      fft_block<N, +1>(v, t, tw, RowView<C>{bufs + (size_t)g * NP});
+      fft_block<NS, +1>(v, t, tw, RowView<C>{bufs + (size_t)g * NP}, RowSync<NS, AT>::make(g));
       if (live) {
-        C* dst = T1 + sf.off1 + ((size_t)kz * (2 * sf.K + 1) + (jy + sf.K)) * N;
+        C* dst = T1 + sf.off1 + ((size_t)kz * (2 * sf.K + 1) + (jy + sf.K)) * NS;
 #pragma unroll
         for (int q = 0; q < 8; ++q) dst[t + q * TPF] = v[q];
       }
@@ -514,46 +523,50 @@ __global__ void k_adj_cube_reduce(const double* __restrict__ cube, size_t nblk, 
   if (threadIdx.x == 0) sums[f] = sh[0];
 }
 
-// Triangle counts: sum_x I_b^3 = ncell * (number of closed (q1, q2, q3) in bin b), an exact integer
-// when no triple aliases (largest bin edge <= k_N/2); rounded to it.
-__global__ void k_adj_nt_store(const double* __restrict__ sums, int first, int nb, double ncell, double* __restrict__ nt) {
+// Triangle counts: on the NS grid sum_x I_b^3 = NS^3 * (number of closed (q1, q2, q3) in bin b), an
+// exact integer when no triple aliases (3 K < NS); rounded to it and stored as the n-grid sum
+// n^3 * count.
+__global__ void k_adj_nt_store(const double* __restrict__ sums, int first, int nb, double ncell_s, double ncell,
+                               double* __restrict__ nt) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b < nb) nt[b] = rint(sums[first + b] / ncell) * ncell;
+  if (b < nb) nt[b] = rint(sums[first + b] / ncell_s) * ncell;
 }
 
-// B_0 = sum F^3 / (I33 sum I^3); N_T = sum I^3 / ncell
+// B_0 = (n/NS)^3 sum_NS F^3 / (I33 sum_n I^3); N_T = sum_n I^3 / n^3
 __global__ void k_adj_b0_final(const double* __restrict__ sums, const double* __restrict__ nt, int nb, double i33,
-                               double ncell, double* __restrict__ out_b0, double* __restrict__ out_nt) {
+                               double scale, double ncell, double* __restrict__ out_b0, double* __restrict__ out_nt) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= nb) return;
-  out_b0[b] = nt[b] > 0 ? sums[b] / (i33 * nt[b]) : 0.0;
+  out_b0[b] = nt[b] > 0 ? scale * sums[b] / (i33 * nt[b]) : 0.0;
   out_nt[b] = nt[b] / ncell;
 }
 
-// c_b = 3 h_b / (I33 sum I_b^3)
+// c_b = 3 h_b / (I33 sum_n I^3), times (n/NS)^3 for transforms of F^2 taken on the NS grid
 __global__ void k_adj_bcoef(const double* __restrict__ nt, const double* __restrict__ h, int nb, double i33,
-                            double* __restrict__ cb) {
+                            double scale, double* __restrict__ cb) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b < nb) cb[b] = nt[b] > 0 ? 3.0 * h[b] / (i33 * nt[b]) : 0.0;
+  if (b < nb) cb[b] = nt[b] > 0 ? 3.0 * scale * h[b] / (i33 * nt[b]) : 0.0;
 }
 
 // Row pass, forward x with accumulation: Y[r][kx] (+)= sum_f c_f Phi_f(q) FFT_x(T1_f row), fields
-// summed per group then over groups in a fixed order.
-template <typename T, int N>
+// summed per group then over groups in a fixed order; rows of the NS grid are mapped back onto the
+// n-grid rows of Y.
+template <typename T, int NS>
 __global__ void __launch_bounds__(AT)
-k_adj_rows_fwd_acc(const cplx<T>* __restrict__ T1, int KM, const AFieldTable ft, const int16_t* __restrict__ bintab,
-                   const double* __restrict__ cb, const cplx<T>* __restrict__ tw_g, cplx<T>* __restrict__ Y) {
+k_adj_rows_fwd_acc(const cplx<T>* __restrict__ T1, int KM, int nfine, const AFieldTable ft,
+                   const int16_t* __restrict__ bintab, const double* __restrict__ cb, const cplx<T>* __restrict__ tw_g,
+                   cplx<T>* __restrict__ Y) {
   using C = cplx<T>;
-  constexpr int TPF = N / 8;
-  constexpr int G = AT / TPF;
-  constexpr int NP = row_pad_len<N>();
+  constexpr int TPF = NS / 8;
+  constexpr int G = RowGroups<NS, AT>::G;
+  constexpr int NP = row_pad_len<NS>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
-  C* acc = tw + N;                      // [G][N]
-  C* bufs = acc + (size_t)G * N;        // [G][NP]
-  int* binrow = reinterpret_cast<int*>(bufs + (size_t)G * NP);
+  C* acc = tw + NS;                     // [G][NS]
+  C* bufs = acc + (size_t)G * NS;       // [NBUF][NP]
+  int* binrow = reinterpret_cast<int*>(bufs + (size_t)RowGroups<NS, AT>::NBUF * NP);
   const int tid = threadIdx.x;
-  for (int i = tid; i < N; i += blockDim.x) tw[i] = tw_g[i];
+  for (int i = tid; i < NS; i += blockDim.x) tw[i] = tw_g[i];
   const int g = tid / TPF, t = tid % TPF;
   const int nyr = 2 * KM + 1;
   const int nrows = (KM + 1) * nyr;
@@ -561,40 +574,45 @@ k_adj_rows_fwd_acc(const cplx<T>* __restrict__ T1, int KM, const AFieldTable ft,
   for (int r = blockIdx.x; r < nrows; r += gridDim.x) {
     const int kz = r / nyr, jy = r % nyr - KM;
     const int ay = jy < 0 ? -jy : jy;
-    for (int kx = tid; kx < N; kx += blockDim.x) {
-      const int i = kx < N / 2 ? kx : kx - N;
+    for (int kx = tid; kx < NS; kx += blockDim.x) {
+      const int i = kx < NS / 2 ? kx : kx - NS;
       const int n2 = i * i + jy * jy + kz * kz;
-      binrow[kx] = (i != -N / 2 && n2 > 0) ? bintab[n2] : -1;
+      binrow[kx] = (i != -NS / 2 && i != -nfine / 2 && n2 > 0) ? bintab[n2] : -1;
     }
-    for (int i = tid; i < G * N; i += blockDim.x) acc[i] = cmk(T(0), T(0));
+    for (int i = tid; i < G * NS; i += blockDim.x) acc[i] = cmk(T(0), T(0));
     __syncthreads();
     for (int f0 = 0; f0 < ft.nf; f0 += G) {
       const int f = f0 + g;
-      bool live = f < ft.nf;
+      bool live = g < G && f < ft.nf;
       AField sf{};
       if (live) {
         sf = ft.f[f];
         live = kz <= sf.K && ay <= sf.K;
       }
       C v[8];
-      const C* src = T1 + (live ? sf.off1 + ((size_t)kz * (2 * sf.K + 1) + (jy + sf.K)) * N : 0);
+      const C* src = T1 + (live ? sf.off1 + ((size_t)kz * (2 * sf.K + 1) + (jy + sf.K)) * NS : 0);
 #pragma unroll
       for (int q = 0; q < 8; ++q) v[q] = live ? src[t + q * TPF] : cmk(T(0), T(0));
-      fft_block<N, -1>(v, t, tw, RowView<C>{bufs + (size_t)g * NP});
+      fft_block<NS, -1>(v, t, tw, RowView<C>{bufs + (size_t)g * NP}, RowSync<NS, AT>::make(g));
       if (live) {
         const T c = (T)cb[sf.bin];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           const int kx = t + q * TPF;
-          if (binrow[kx] == sf.bin) acc[(size_t)g * N + kx] = cadd(acc[(size_t)g * N + kx], cscale(v[q], c));
+          if (binrow[kx] == sf.bin) acc[(size_t)g * NS + kx] = cadd(acc[(size_t)g * NS + kx], cscale(v[q], c));
         }
       }
     }
     __syncthreads();
-    for (int kx = tid; kx < N; kx += blockDim.x) {
-      C s = acc[kx];
-      for (int q = 1; q < G; ++q) s = cadd(s, acc[(size_t)q * N + kx]);
-      Y[(size_t)r * N + kx] = s;
+    for (int kx = tid; kx < nfine; kx += blockDim.x) {
+      const int i = kx < nfine / 2 ? kx : kx - nfine;
+      C s = cmk(T(0), T(0));
+      if (i > -NS / 2 && i < NS / 2) {
+        const int cx = i < 0 ? i + NS : i;
+        s = acc[cx];
+        for (int q = 1; q < G; ++q) s = cadd(s, acc[(size_t)q * NS + cx]);
+      }
+      Y[(size_t)r * nfine + kx] = s;
     }
     __syncthreads();
   }
@@ -707,13 +725,16 @@ npc_status row_grid(npc_ctx* ctx, const void* kern, size_t smem, int nrows, int 
   return NPC_OK;
 }
 
-// Shell pipeline for a field table: inverse x (rows of radius KM), inverse y, then the z pass in
-// `mode`; for SQUARE_FWD also forward y and the accumulating forward x into Y.
-template <typename T, int N>
-npc_status shell_pass(npc_ctx* ctx, const AFieldTable& ft, const std::string& tag, int KM, const cplx<T>* X,
-                      const int16_t* bintab, const GradArgs& ga, int assign, const cplx<T>* tw, int mode,
+// Shell pipeline for a field table on the NS grid: inverse x (rows of radius KM), inverse y, then
+// the z pass in `mode`; for SQUARE_FWD also forward y and the accumulating forward x into Y.
+template <typename T, int NS>
+npc_status shell_pass(npc_ctx* ctx, const AFieldTable& ft, const std::string& tag, int KM, int nfine,
+                      const cplx<T>* X, const int16_t* bintab, const GradArgs& ga, int assign, int mode,
                       double* cube_sums, const double* cb, cplx<T>* Yacc, T* out) {
   using C = cplx<T>;
+  const void* twp;
+  NPC_TRY(get_twiddles(ctx, NS, sizeof(T) == 8 ? NPC_PREC_FP64 : NPC_PREC_MIXED, &twp));
+  const C* tw = (const C*)twp;
   // buffers and plane / pair tables
   int64_t n1 = 0, n2 = 0;
   AFieldTable t = ft;
@@ -722,8 +743,8 @@ npc_status shell_pass(npc_ctx* ctx, const AFieldTable& ft, const std::string& ta
     const int K = t.f[f].K;
     t.f[f].off1 = n1;
     t.f[f].off2 = n2;
-    n1 += (int64_t)(K + 1) * (2 * K + 1) * N;
-    n2 += (int64_t)(K + 1) * N * N;
+    n1 += (int64_t)(K + 1) * (2 * K + 1) * NS;
+    n2 += (int64_t)(K + 1) * NS * NS;
     for (int kz = 0; kz <= K; ++kz) planes.push_back(make_int2(f, kz));
   }
   for (int f = 0; f < t.nf; f += 2) pairs.push_back(make_int2(f, f + 1 < t.nf ? f + 1 : -1));
@@ -741,40 +762,40 @@ npc_status shell_pass(npc_ctx* ctx, const AFieldTable& ft, const std::string& ta
   const int2* dplanes = (const int2*)((char*)dtab + sizeof(AFieldTable));
   const int2* dpairs = dplanes + planes.size();
 
-  constexpr int TPF = N / 8;
-  constexpr int G = AT / TPF;
-  constexpr int NP = row_pad_len<N>();
+  constexpr int G = RowGroups<NS, AT>::G;
+  constexpr int NBUF = RowGroups<NS, AT>::NBUF;
+  constexpr int NP = row_pad_len<NS>();
   const int nrows = (KM + 1) * (2 * KM + 1);
   {
-    const size_t smem = sizeof(C) * (3 * N + (size_t)G * NP) + sizeof(T) * (N / 2 + 2) + sizeof(int) * N;
-    auto kern = k_adj_rows_inv<T, N>;
+    const size_t smem = sizeof(C) * (3 * NS + (size_t)NBUF * NP) + sizeof(int) * NS + sizeof(T) * (nfine / 2 + 2);
+    auto kern = k_adj_rows_inv<T, NS>;
     int grid;
-    NPC_TRY((row_grid<T, N>(ctx, (const void*)kern, smem, nrows, 1, &grid)));
-    kern<<<grid, AT, smem, ctx->stream>>>(X, KM, t, bintab, ga, assign, tw, T1);
+    NPC_TRY((row_grid<T, NS>(ctx, (const void*)kern, smem, nrows, 1, &grid)));
+    kern<<<grid, AT, smem, ctx->stream>>>(X, KM, nfine, t, bintab, ga, assign, tw, T1);
     NPC_LAUNCH(ctx);
   }
   NPC_TRY(stage_mark(ctx, "shell_x_inv"));
-  constexpr int TX = ACol<N>::TX;
-  const size_t csmem = sizeof(C) * (N + (size_t)N * TX);
+  constexpr int TX = ACol<NS>::TX;
+  const size_t csmem = sizeof(C) * (NS + (size_t)NS * TX);
   {
-    auto kern = k_adj_y_inv<T, N>;
+    auto kern = k_adj_y_inv<T, NS>;
     NPC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem));
     for (size_t p0 = 0; p0 < planes.size(); p0 += 65535) {
       const int np = (int)std::min<size_t>(65535, planes.size() - p0);
-      kern<<<dim3(N / TX, np), ACol<N>::THREADS, csmem, ctx->stream>>>(T1, dft, dplanes + p0, tw, T2);
+      kern<<<dim3(NS / TX, np), ACol<NS>::THREADS, csmem, ctx->stream>>>(T1, dft, dplanes + p0, tw, T2);
       NPC_LAUNCH(ctx);
     }
   }
   NPC_TRY(stage_mark(ctx, "shell_y_inv"));
   {
-    const size_t zsmem = csmem + sizeof(double) * 2 * (ACol<N>::THREADS / 32);
-    auto kern = k_adj_z<T, N>;
+    const size_t zsmem = csmem + sizeof(double) * 2 * (ACol<NS>::THREADS / 32);
+    auto kern = k_adj_z<T, NS>;
     NPC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zsmem));
     double* cube = nullptr;
-    const size_t nblk = (size_t)(N / TX) * N;
+    const size_t nblk = (size_t)(NS / TX) * NS;
     if (mode == ZMODE_CUBE) NPC_TRY(ws_get(ctx, "adj.cube", sizeof(double) * nblk * t.nf, (void**)&cube));
-    kern<<<dim3(N / TX, N, (unsigned)pairs.size()), ACol<N>::THREADS, zsmem, ctx->stream>>>(T2, dft, dpairs, mode, tw,
-                                                                                          cube, out);
+    kern<<<dim3(NS / TX, NS, (unsigned)pairs.size()), ACol<NS>::THREADS, zsmem, ctx->stream>>>(T2, dft, dpairs, mode,
+                                                                                             tw, cube, out);
     NPC_LAUNCH(ctx);
     if (mode == ZMODE_CUBE) {
       k_adj_cube_reduce<<<t.nf, 256, 0, ctx->stream>>>(cube, nblk, cube_sums);
@@ -784,25 +805,51 @@ npc_status shell_pass(npc_ctx* ctx, const AFieldTable& ft, const std::string& ta
   NPC_TRY(stage_mark(ctx, mode == ZMODE_WRITE ? "grad_z_inv" : (mode == ZMODE_CUBE ? "shell_z_cube" : "shell_z_sq_fwd")));
   if (mode != ZMODE_SQUARE_FWD) return NPC_OK;
   {
-    auto kern = k_adj_y_fwd<T, N>;
+    auto kern = k_adj_y_fwd<T, NS>;
     NPC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem));
     for (size_t p0 = 0; p0 < planes.size(); p0 += 65535) {
       const int np = (int)std::min<size_t>(65535, planes.size() - p0);
-      kern<<<dim3(N / TX, np), ACol<N>::THREADS, csmem, ctx->stream>>>(T2, dft, dplanes + p0, tw, T1);
+      kern<<<dim3(NS / TX, np), ACol<NS>::THREADS, csmem, ctx->stream>>>(T2, dft, dplanes + p0, tw, T1);
       NPC_LAUNCH(ctx);
     }
   }
   NPC_TRY(stage_mark(ctx, "shell_y_fwd"));
   {
-    const size_t smem = sizeof(C) * (N + (size_t)G * N + (size_t)G * NP) + sizeof(int) * N;
-    auto kern = k_adj_rows_fwd_acc<T, N>;
+    const size_t smem = sizeof(C) * (NS + (size_t)G * NS + (size_t)NBUF * NP) + sizeof(int) * NS;
+    auto kern = k_adj_rows_fwd_acc<T, NS>;
     int grid;
-    NPC_TRY((row_grid<T, N>(ctx, (const void*)kern, smem, nrows, 1, &grid)));
-    kern<<<grid, AT, smem, ctx->stream>>>(T1, KM, t, bintab, cb, tw, Yacc);
+    NPC_TRY((row_grid<T, NS>(ctx, (const void*)kern, smem, nrows, 1, &grid)));
+    kern<<<grid, AT, smem, ctx->stream>>>(T1, KM, nfine, t, bintab, cb, tw, Yacc);
     NPC_LAUNCH(ctx);
   }
   NPC_TRY(stage_mark(ctx, "shell_x_fwd_acc"));
   return NPC_OK;
+}
+
+// the smallest compiled transform length >= need (and <= n; FP64 up to 256)
+int shell_grid(int need, int n, bool fp64) {
+  static const int sizes[] = {16, 32, 48, 64, 96, 128, 192, 256, 384, 512, 1024};
+  for (int s : sizes) {
+    if (s > n || (fp64 && s > 256)) break;
+    if (s >= need) return s;
+  }
+  return n;
+}
+
+template <typename T>
+npc_status shell_dispatch(npc_ctx* ctx, int NS, const AFieldTable& ft, const std::string& tag, int KM, int nfine,
+                          const cplx<T>* X, const int16_t* bintab, const GradArgs& ga, int assign, int mode,
+                          double* cube_sums, const double* cb, cplx<T>* Yacc, T* out) {
+#define NPC_SHELL(S) \
+  case S: return shell_pass<T, S>(ctx, ft, tag, KM, nfine, X, bintab, ga, assign, mode, cube_sums, cb, Yacc, out);
+  switch (NS) {
+    NPC_SHELL(16) NPC_SHELL(32) NPC_SHELL(48) NPC_SHELL(64) NPC_SHELL(96) NPC_SHELL(128) NPC_SHELL(192) NPC_SHELL(256)
+  }
+  if constexpr (sizeof(T) == 4) {
+    switch (NS) { NPC_SHELL(384) NPC_SHELL(512) NPC_SHELL(1024) }
+  }
+#undef NPC_SHELL
+  return set_err(ctx, NPC_ERR_UNSUPPORTED, "shell grid %d not supported at this precision", NS);
 }
 
 template <typename T, int N>
@@ -812,11 +859,16 @@ npc_status mesh_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb, 
   const int nb = kb.nbins;
   const int KM = outer_radius(N, m.box, kb);
   const double ncell = (double)N * N * N;
+  // grid of the B_0 shell passes: every shell lies inside |q_i| <= KB, products up to 3 KB
+  int KB = 1;
+  for (int b = 0; b < nb; ++b) KB = std::max(KB, bin_radius(m.box, kb, b, KM));
+  const int NS = shell_grid(3 * KB + 1, N, sizeof(T) == 8);
+  const double ncell_s = (double)NS * NS * NS;
   const void* twp;
   NPC_TRY(get_twiddles(ctx, N, prec, &twp));
   const C* tw = (const C*)twp;
   const int16_t* bintab;
-  NPC_TRY(get_bin_table(ctx, N, m.box, kb, &bintab));
+  NPC_TRY(get_bin_table(ctx, N, m.box, kb, &bintab, 4));
 
   // 1. forward transform of the mesh on kz <= KM, compact rows, 1/W
   PowerPlan plan{};
@@ -883,14 +935,17 @@ npc_status mesh_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb, 
   // 3. equilateral B_0: bin shells, triangle counts (cached per geometry)
   double* nt = nullptr;
   if (job.want_b0) {
-    NPC_TRY(ws_get(ctx, "adj.nt", sizeof(double) * nb, (void**)&nt));
+    NPC_TRY(ws_get(ctx, slot_name(ctx, "adj.nt").c_str(), sizeof(double) * nb, (void**)&nt));
     std::vector<char> key;
     auto push = [&](const void* p, size_t s) { key.insert(key.end(), (const char*)p, (const char*)p + s); };
     const int nn = N;
     push(&nn, sizeof(nn));
     push(&m.box, sizeof(double));
     push(&kb, sizeof(kb));
-    auto it = ctx->host_cache_keys.find("adj.nt");
+    const int tsize = (int)sizeof(T);   // float and float64 shells round differently
+    push(&tsize, sizeof(tsize));
+    const std::string ntname = slot_name(ctx, "adj.nt");
+    auto it = ctx->host_cache_keys.find(ntname);
     const bool nt_ok = it != ctx->host_cache_keys.end() && it->second == key;
     const bool fwd_b0 = job.want_out != 0;
     double* sums;
@@ -905,16 +960,16 @@ npc_status mesh_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb, 
       if (!nt_ok)
         for (int b = 0; b < nb; ++b) ft.f[ft.nf++] = AField{SRC_ONE, (int16_t)b, bin_radius(m.box, kb, b, KM), 0, 0};
       GradArgs ga{};
-      NPC_TRY((shell_pass<T, N>(ctx, ft, "cube", KM, X, bintab, ga, m.assign, tw, ZMODE_CUBE, sums, nullptr, nullptr,
-                                nullptr)));
+      NPC_TRY(shell_dispatch<T>(ctx, NS, ft, "cube", KM, N, X, bintab, ga, m.assign, ZMODE_CUBE, sums, nullptr,
+                                nullptr, nullptr));
       if (!nt_ok) {
-        k_adj_nt_store<<<(nb + 127) / 128, 128, 0, ctx->stream>>>(sums, first_one, nb, ncell, nt);
+        k_adj_nt_store<<<(nb + 127) / 128, 128, 0, ctx->stream>>>(sums, first_one, nb, ncell_s, ncell, nt);
         NPC_LAUNCH(ctx);
-        ctx->host_cache_keys["adj.nt"] = key;
+        ctx->host_cache_keys[ntname] = key;
       }
       if (fwd_b0) {
         const int rb = 2 + nell;
-        k_adj_b0_final<<<(nb + 127) / 128, 128, 0, ctx->stream>>>(sums, nt, nb, job.i33, ncell,
+        k_adj_b0_final<<<(nb + 127) / 128, 128, 0, ctx->stream>>>(sums, nt, nb, job.i33, ncell / ncell_s, ncell,
                                                                   job.out + (size_t)rb * nb,
                                                                   job.out + (size_t)(rb + 1) * nb);
         NPC_LAUNCH(ctx);
@@ -929,15 +984,15 @@ npc_status mesh_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb, 
   if (job.dldb) {
     double* cb;
     NPC_TRY(ws_get(ctx, "adj.cb", sizeof(double) * nb, (void**)&cb));
-    k_adj_bcoef<<<(nb + 127) / 128, 128, 0, ctx->stream>>>(nt, job.dldb, nb, job.i33, cb);
+    k_adj_bcoef<<<(nb + 127) / 128, 128, 0, ctx->stream>>>(nt, job.dldb, nb, job.i33, ncell / ncell_s, cb);
     NPC_LAUNCH(ctx);
     NPC_TRY(ws_get(ctx, "adj.Y", sizeof(C) * nrows * N, (void**)&Y));
     AFieldTable ft{};
     ft.nf = 0;
     for (int b = 0; b < nb; ++b) ft.f[ft.nf++] = AField{SRC_BIN, (int16_t)b, bin_radius(m.box, kb, b, KM), 0, 0};
     GradArgs ga{};
-    NPC_TRY((shell_pass<T, N>(ctx, ft, "sq", KM, X, bintab, ga, m.assign, tw, ZMODE_SQUARE_FWD, nullptr, cb, Y,
-                              nullptr)));
+    NPC_TRY(shell_dispatch<T>(ctx, NS, ft, "sq", KM, N, X, bintab, ga, m.assign, ZMODE_SQUARE_FWD, nullptr, cb, Y,
+                              nullptr));
   }
   GradArgs ga{};
   ga.Y = Y;
@@ -949,7 +1004,7 @@ npc_status mesh_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb, 
   AFieldTable ft{};
   ft.nf = 1;
   ft.f[0] = AField{SRC_GRAD, -1, KM, 0, 0};
-  NPC_TRY((shell_pass<T, N>(ctx, ft, "grad", KM, X, bintab, ga, m.assign, tw, ZMODE_WRITE, nullptr, nullptr, nullptr,
+  NPC_TRY((shell_pass<T, N>(ctx, ft, "grad", KM, N, X, bintab, ga, m.assign, ZMODE_WRITE, nullptr, nullptr, nullptr,
                             (T*)job.grad)));
   return NPC_OK;
 }

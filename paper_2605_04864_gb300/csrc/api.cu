@@ -401,6 +401,7 @@ npc_status npc_destroy(npc_ctx* ctx) {
   if (!ctx) return NPC_OK;
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
+  destroy_batch_state(ctx);
   for (auto& kv : ctx->ws)
     if (kv.second.p) cudaFree(kv.second.p);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);

@@ -83,7 +83,7 @@ k_fft_x_combine(const cplx<T>* __restrict__ half, int nout, int nphase, int KZ, 
         for (int q = 0; q < 8; ++q) v[q] = cmk(T(0), T(0));
       }
       RowView<C> rv{rows + (size_t)(live ? f : nf + g) * NP};
-      fft_block<N, -1>(v, t, tw, rv);
+      fft_block<N, -1>(v, t, tw, rv, RowSync<N, BT>::make(g));
       if (live) {
 #pragma unroll
         for (int q = 0; q < 8; ++q) rv.st(t + q * TPF, v[q]);
@@ -272,7 +272,7 @@ k_shell_x(const cplx<T>* __restrict__ X0, int KZX, const ShellField* __restrict_
         }
         v[q] = a;
       }
-      fft_block<N, +1>(v, t, tw, RowView<C>{bufs + (size_t)g * NP});
+      fft_block<N, +1>(v, t, tw, RowView<C>{bufs + (size_t)g * NP}, RowSync<N, BT>::make(g));
       if (live) {
         C* dst = T1 + sf.off1 + ((size_t)kz * (2 * sf.K + 1) + (jy + sf.K)) * N;
 #pragma unroll
@@ -825,9 +825,9 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
 
   // 3. shell sums for the shot noise
   const int16_t *tab_m, *tab_q;
-  NPC_TRY(get_bin_table(ctx, N, m.box, kb, &tab_m, 0));
+  NPC_TRY(get_bin_table(ctx, N, m.box, kb, &tab_m, 2));
   npc_kbins qb{0.0, kb.dk, nq};
-  NPC_TRY(get_bin_table(ctx, N, m.box, qb, &tab_q, 1));
+  NPC_TRY(get_bin_table(ctx, N, m.box, qb, &tab_q, 3));
   double *cross_m, *cross_q;
   NPC_TRY(ws_get(ctx, "bis.cross", sizeof(double) * NCROSS * (nb + nq), (void**)&cross_m));
   cross_q = cross_m + (size_t)NCROSS * nb;
@@ -861,6 +861,7 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
     std::memcpy(ntkey.data(), &n_, sizeof(int));
     std::memcpy(ntkey.data() + sizeof(int), a, 3 * sizeof(double));
     ntkey.push_back((char)nb);
+    ntkey.push_back((char)sizeof(T));   // float and float64 shell fields give different rounding
   }
   const Tri tr = make_triangles(kb);
   const int ntri = (int)tr.tri.size() / 3, npair = (int)tr.pij.size();
@@ -898,10 +899,13 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
       plane_kz.push_back(kz);
     }
   }
-  // pairs for the z pass: consecutive fields with the same K
+  // pairs for the z pass: consecutive fields of the same family (F0, F2, I, G) and the same K, so
+  // that the rounding of every field (a pair shares one complex transform) does not depend on
+  // whether the cached indicator fields are recomputed in this call
+  auto family = [&](int f) { return f < nb ? 0 : (f < iI ? 1 : (f < iG ? 2 : 3)); };
   std::vector<int> za, zb;
   for (int f = 0; f < nfield;) {
-    if (f + 1 < nfield && fl[f + 1].K == fl[f].K) {
+    if (f + 1 < nfield && fl[f + 1].K == fl[f].K && family(f + 1) == family(f)) {
       za.push_back(f);
       zb.push_back(f + 1);
       f += 2;
@@ -930,7 +934,8 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
   const size_t t_tri = push_bytes(tr.tri.data(), sizeof(int) * tr.tri.size());
   const size_t t_pij = push_bytes(tr.pij.data(), sizeof(int) * tr.pij.size());
   char* dtab;
-  NPC_TRY(ws_table(ctx, "bis.tables", tables, tables.data(), tables.size(), (void**)&dtab));
+  NPC_TRY(ws_table(ctx, need_nt ? "bis.tables.nt" : "bis.tables", tables, tables.data(), tables.size(),
+                   (void**)&dtab));
   const ShellField* dfields = (const ShellField*)(dtab + t_fields);
   C *T1, *T2;
   T* R;
@@ -938,7 +943,7 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
   NPC_TRY(ws_get(ctx, "bis.T2", sizeof(C) * std::max<int64_t>(o2, 1), (void**)&T2));
   NPC_TRY(ws_get(ctx, "bis.R", sizeof(T) * ncell * nfield, (void**)&R));
   const int16_t* tab_shell;
-  NPC_TRY(get_bin_table(ctx, N, m.box, kb, &tab_shell, 0));
+  NPC_TRY(get_bin_table(ctx, N, m.box, kb, &tab_shell, 2));
   {
     constexpr int TPF = N / 8;
     constexpr int G = BT / TPF > 0 ? BT / TPF : 1;

@@ -346,8 +346,11 @@ k_paint_brick(const typename RecOf<R>::type* __restrict__ rec, const uint32_t* _
 
 // Each cell sums the tiles covering it, in a fixed order (brick offset -1, 0, +1 per axis, z
 // outermost).  One CTA per (brick, phase); the tile of brick B covers cells [BS B - 1, BS B + BS + 2].
+// Thread (x, y) of the CTA owns one column of the brick along z: its x and y options (own tile, the
+// lower neighbour's for the first three cells, the upper neighbour's for the last) are fixed per
+// thread, only the z options change per cell.
 template <typename T, int BS>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(BS * BS)
 k_fold(const T* __restrict__ tiles, PaintGeo g, int nphase, const double* __restrict__ sc, int subtract_mean,
        T* __restrict__ mesh_a, T* __restrict__ mesh_b) {
   constexpr int TS = BS + 4, TS3 = TS * TS * TS;
@@ -362,27 +365,38 @@ k_fold(const T* __restrict__ tiles, PaintGeo g, int nphase, const double* __rest
   }
   const T mean = subtract_mean ? (T)(sc[SC_SUMWG] / ((double)n * n * n)) : T(0);
   T* mesh = ph ? mesh_b : mesh_a;
-  for (int i = threadIdx.x; i < BS * BS * BS; i += blockDim.x) {
-    const int l[3] = {i % BS, (i / BS) % BS, i / (BS * BS)};
-    int nd[3], db[3][2], dt[3][2];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      int k = 0;
-      if (l[a] <= 2) { db[a][k] = nbm[a]; dt[a][k] = l[a] + BS + 1; ++k; }
-      db[a][k] = B[a]; dt[a][k] = l[a] + 1; ++k;
-      if (l[a] == BS - 1) { db[a][k] = nbp[a]; dt[a][k] = 0; ++k; }
-      nd[a] = k;
+  const int lx = threadIdx.x % BS, ly = threadIdx.x / BS;
+  // x and y options: brick coordinate and tile coordinate, lower neighbour first
+  int nx = 0, ny = 0, bx[2], tx[2], by[2], ty[2];
+  if (lx <= 2) { bx[nx] = nbm[0]; tx[nx] = lx + BS + 1; ++nx; }
+  bx[nx] = B[0]; tx[nx] = lx + 1; ++nx;
+  if (lx == BS - 1) { bx[nx] = nbp[0]; tx[nx] = 0; ++nx; }
+  if (ly <= 2) { by[ny] = nbm[1]; ty[ny] = ly + BS + 1; ++ny; }
+  by[ny] = B[1]; ty[ny] = ly + 1; ++ny;
+  if (ly == BS - 1) { by[ny] = nbp[1]; ty[ny] = 0; ++ny; }
+  // per (iy, ix) option: tile base (brick index without z) and in-tile offset without z
+  size_t base_yx[4];
+  int off_yx[4];
+  int nyx = 0;
+  for (int iy = 0; iy < ny; ++iy)
+    for (int ix = 0; ix < nx; ++ix) {
+      base_yx[nyx] = (size_t)by[iy] * nb + bx[ix];
+      off_yx[nyx] = ty[iy] * TS + tx[ix];
+      ++nyx;
     }
+  T* col = mesh + ((size_t)(B[2] * BS) * n + (B[1] * BS + ly)) * n + (B[0] * BS + lx);
+  for (int lz = 0; lz < BS; ++lz) {
+    int nz = 0, bz[2], tz[2];
+    if (lz <= 2) { bz[nz] = nbm[2]; tz[nz] = lz + BS + 1; ++nz; }
+    bz[nz] = B[2]; tz[nz] = lz + 1; ++nz;
+    if (lz == BS - 1) { bz[nz] = nbp[2]; tz[nz] = 0; ++nz; }
     T v = T(0);
-    for (int iz = 0; iz < nd[2]; ++iz)
-      for (int iy = 0; iy < nd[1]; ++iy)
-        for (int ix = 0; ix < nd[0]; ++ix) {
-          const int nbr = (db[2][iz] * nb + db[1][iy]) * nb + db[0][ix];
-          const int j = (dt[2][iz] * TS + dt[1][iy]) * TS + dt[0][ix];
-          v += tiles[((size_t)nbr * nphase + ph) * TS3 + j];
-        }
-    const size_t c = ((size_t)(B[2] * BS + l[2]) * n + (B[1] * BS + l[1])) * n + (B[0] * BS + l[0]);
-    mesh[c] = v - mean;
+    for (int iz = 0; iz < nz; ++iz) {
+      const size_t zb = (size_t)bz[iz] * nb * nb;
+      const int zo = tz[iz] * TS * TS;
+      for (int k = 0; k < nyx; ++k) v += tiles[((zb + base_yx[k]) * nphase + ph) * TS3 + zo + off_yx[k]];
+    }
+    col[(size_t)lz * n * n] = v - mean;
   }
 }
 
@@ -421,8 +435,8 @@ npc_status launch_fold(npc_ctx* ctx, const void* tiles, const PaintGeo& g, int n
                        void* mesh_a, void* mesh_b) {
   const int grid = g.nb * g.nb * g.nb * nphase;
   switch (g.bs) {
-    case 4: k_fold<T, 4><<<grid, 64, 0, ctx->stream>>>((const T*)tiles, g, nphase, sc, sub, (T*)mesh_a, (T*)mesh_b); break;
-    case 8: k_fold<T, 8><<<grid, 256, 0, ctx->stream>>>((const T*)tiles, g, nphase, sc, sub, (T*)mesh_a, (T*)mesh_b); break;
+    case 4: k_fold<T, 4><<<grid, 16, 0, ctx->stream>>>((const T*)tiles, g, nphase, sc, sub, (T*)mesh_a, (T*)mesh_b); break;
+    case 8: k_fold<T, 8><<<grid, 64, 0, ctx->stream>>>((const T*)tiles, g, nphase, sc, sub, (T*)mesh_a, (T*)mesh_b); break;
     default: k_fold<T, 16><<<grid, 256, 0, ctx->stream>>>((const T*)tiles, g, nphase, sc, sub, (T*)mesh_a, (T*)mesh_b); break;
   }
   NPC_LAUNCH(ctx);

@@ -9,6 +9,8 @@
 // (b div Ns)*Ns*R + (b mod Ns) + r*Ns.  DIR = -1 forward (e^{-i k x}), +1 inverse (unscaled).
 #pragma once
 
+#include <type_traits>
+
 #include "npc_internal.cuh"
 
 template <typename C, int DIR>
@@ -91,11 +93,27 @@ template <int N, int THREADS> struct RowGroups {
   static constexpr int NBUF = (THREADS % TPF) ? G + 1 : G;
 };
 
-// All threads of the block must call this the same number of times (it contains __syncthreads).
+// Barrier among the threads that share one transform's exchange buffer: the whole block (the
+// default), one warp (transforms of <= 32 threads packed in a warp), or a named barrier of the
+// group's threads (transforms of 64, 128 ... threads) so that row groups do not wait on each other.
+struct SyncBlock {
+  __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+struct SyncWarp {
+  __device__ __forceinline__ void operator()() const { __syncwarp(); }
+};
+struct SyncNamed {
+  int id, count;
+  __device__ __forceinline__ void operator()() const {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+  }
+};
+
+// All threads that share `buf` must call this the same number of times (it contains barriers).
 // TS: stride into the twiddle table (a length-N/TS sub-transform reads every TS-th twiddle of N).
-template <int N, int DIR, int Ns, int TS = 1, typename C, typename View>
+template <int N, int DIR, int Ns, int TS = 1, typename C, typename View, typename Sync = SyncBlock>
 __device__ __forceinline__ void fft_stages(C (&v)[8], const int t, const C* __restrict__ tw,
-                                           const View& buf) {
+                                           const View& buf, const Sync& sync = Sync()) {
   constexpr int TPF = N / 8;
   constexpr int REM = N / Ns;
   constexpr int R = (REM >= 8) ? 8 : REM;
@@ -128,11 +146,11 @@ __device__ __forceinline__ void fft_stages(C (&v)[8], const int t, const C* __re
 #pragma unroll
       for (int r = 0; r < R; ++r) buf.st(base + r * Ns, v[s + r * BPT]);
     }
-    __syncthreads();
+    sync();
 #pragma unroll
     for (int q = 0; q < 8; ++q) v[q] = buf.ld(t + q * TPF);
-    __syncthreads();
-    fft_stages<N, DIR, Ns * R, TS>(v, t, tw, buf);
+    sync();
+    fft_stages<N, DIR, Ns * R, TS>(v, t, tw, buf, sync);
   }
 }
 
@@ -142,27 +160,27 @@ __device__ __forceinline__ void fft_stages(C (&v)[8], const int t, const C* __re
 // of the threads, then X[k] = A_0[k mod M] + w^k A_1[k mod M] + w^{2k} A_2[k mod M] with
 // w = exp(DIR 2 pi i / N).  Inputs and outputs keep the natural order t + q TPF; the buffer
 // holds N elements and may be reused by the caller as soon as this returns.
-template <int N, int DIR, typename C, typename View>
+template <int N, int DIR, typename C, typename View, typename Sync = SyncBlock>
 __device__ __forceinline__ void fft_block(C (&v)[8], const int t, const C* __restrict__ tw,
-                                          const View& buf) {
+                                          const View& buf, const Sync& sync = Sync()) {
   using L = FftLen<N>;
   if constexpr (L::pow2) {
-    fft_stages<N, DIR, 1>(v, t, tw, buf);
+    fft_stages<N, DIR, 1>(v, t, tw, buf, sync);
   } else {
     constexpr int M = L::M;
     constexpr int TPF = N / 8, SUB = M / 8;
     const int r = t / SUB, s = t % SUB;
 #pragma unroll
     for (int q = 0; q < 8; ++q) buf.st(t + q * TPF, v[q]);
-    __syncthreads();
+    sync();
 #pragma unroll
     for (int q = 0; q < 8; ++q) v[q] = buf.ld(3 * (s + q * SUB) + r);
-    __syncthreads();
+    sync();
     const View sb = buf.sub(r * M);
-    fft_stages<M, DIR, 1, 3>(v, s, tw, sb);
+    fft_stages<M, DIR, 1, 3>(v, s, tw, sb, sync);
 #pragma unroll
     for (int q = 0; q < 8; ++q) sb.st(s + q * SUB, v[q]);
-    __syncthreads();
+    sync();
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int k = t + q * TPF;
@@ -173,6 +191,21 @@ __device__ __forceinline__ void fft_block(C (&v)[8], const int t, const C* __res
       a = cadd(a, cmul(buf.ld(2 * M + km), twiddle<C, DIR>(tw, k2)));
       v[q] = a;
     }
-    __syncthreads();
+    sync();
   }
 }
+
+// The barrier a row kernel with THREADS threads uses for its length-N row transforms (TPF = N/8
+// threads each, group g): named per group when a group is whole warps, the warp when groups pack
+// into warps, else the block.
+template <int N, int THREADS> struct RowSync {
+  static constexpr int TPF = N / 8;
+  static constexpr bool named = (TPF % 32 == 0) && (THREADS % TPF == 0) && (THREADS / TPF <= 15) && (THREADS > TPF);
+  static constexpr bool warp = (32 % TPF == 0) && (THREADS % 32 == 0);
+  using type = typename std::conditional<named, SyncNamed,
+                                         typename std::conditional<warp, SyncWarp, SyncBlock>::type>::type;
+  __device__ __forceinline__ static type make(int g) {
+    if constexpr (named) return SyncNamed{1 + g, TPF};
+    else return type{};
+  }
+};

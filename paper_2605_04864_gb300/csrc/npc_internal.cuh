@@ -182,7 +182,11 @@ struct npc_ctx {
   std::map<std::string, struct BatchGraph*> graphs;
   int batch_branches = 0;              // 0: not tuned (default 4)
   std::map<int, int> ytx;              // tuned columns per CTA of the y pass, per (n * 2 + fp64)
+  cudaStream_t batch_hub = nullptr;    // stream the batch graphs are captured on and launched from
 };
+
+// releases branch contexts, graphs and the batch stream (batch.cu)
+void destroy_batch_state(npc_ctx* ctx);
 
 // slot-qualified name of a cached table or cache entry
 std::string slot_name(const npc_ctx* ctx, const std::string& name);
@@ -284,6 +288,9 @@ npc_status power_core(npc_ctx* ctx, const npc_mesh_spec& ms, const DevCatalog& d
                       const npc_kbins& kb, uint32_t ell_mask, uint32_t modified_mask, int prec, const double* sc,
                       double* dev_out);
 
+// Autotuner of the y pass (columns per CTA) for mesh size n; the choice is kept in ctx->ytx.
+npc_status tune_y_pass(npc_ctx* ctx, int n, int prec, int nplanes);
+
 npc_status run_forward_transforms(npc_ctx* ctx, int prec, const PowerPlan& plan, const Geom& g,
                                   const void* mesh_a, const void* mesh_b, void* half);
 npc_status run_power_contract(npc_ctx* ctx, int prec, const PowerPlan& plan, const npc_mesh_spec& m,
@@ -291,6 +298,7 @@ npc_status run_power_contract(npc_ctx* ctx, int prec, const PowerPlan& plan, con
                               double* dev_out);
 
 // bin table: int16 per integer |k|^2 in [0, 3 (n/2)^2]
+// slots: 0 power spectrum, 2-3 bispectrum, 4 mesh-level adjoint (tables stay cached per slot)
 npc_status get_bin_table(npc_ctx* ctx, int n, double box, const npc_kbins& kb, const int16_t** out, int slot = 0);
 // twiddle table exp(-2 pi i j / n), j < n, as cplx<T>
 npc_status get_twiddles(npc_ctx* ctx, int n, int prec, const void** out);

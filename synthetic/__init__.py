@@ -16,3 +16,4 @@ from .catalogs import (  # noqa: F401
     make_periodic_catalog,
 )
 from .configs import WORKLOADS, workload  # noqa: F401
+from .batch import batch_plan, base_catalogues  # noqa: F401

@@ -29,6 +29,15 @@ WORKLOADS = {
         kmin=0.01, dk=0.01, nbins=19, scoc_ells=(0, 2), tripo_ells=(0, 2), precision="mixed",
         seed=2000,
     ),
+    # 96 survey mocks of uneven size in one batch: 32 each on 128^3, 192^3 and 256^3 meshes, box side
+    # L ~ U[500, 1500], N_g log-uniform in [1e5, 2e6], N_r = 10 N_g, box centre at 1.5 L; P_0,2,4 on
+    # bins of 0.01 up to k_N, B_0 on 19 bins from 0.01 truncated at k_N/2.
+    "batch_96": dict(
+        kind="batch", sizes=(128, 192, 256), per_size=32, box_range=(500.0, 1500.0),
+        n_gal_range=(1e5, 2e6), ran_factor=10, distance_factor=1.5, assign=3, interlace=1,
+        fkp_p0=1.0e4, dk=0.01, pk_nbins_max=80, bk_kmin=0.01, bk_nbins=19, ells=(0, 2, 4),
+        precision="mixed", seed=3000,
+    ),
     # Gradients of P_0,2,4 (global LOS) and of the equilateral B_0 (19 bins) with respect to the
     # mesh and, through the TSC adjoint, the galaxy positions: periodic 1024^3, 1e7 galaxies.
     "adjoint_1024": dict(
