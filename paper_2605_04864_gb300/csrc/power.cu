@@ -295,12 +295,12 @@ static int std_pairs(const FieldList& fl) {
 }
 
 // Column transform along a strided axis: element j of column (plane, x) at
-// data[plane*plane_stride + j*row_stride + x].  grid = (N/TX, nplanes).
-template <typename T, int N, int DIR>
-__global__ void __launch_bounds__(ColCfg<N>::THREADS)
+// data[plane*plane_stride + j*row_stride + x].  grid = (N/TX, nplanes); TX columns per CTA is a
+// tuning parameter (see tune_y_pass).
+template <typename T, int N, int DIR, int TX>
+__global__ void __launch_bounds__(TX * N / 8)
 k_fft_cols(cplx<T>* __restrict__ data, size_t plane_stride, int row_stride, const cplx<T>* __restrict__ tw_g) {
   using C = cplx<T>;
-  constexpr int TX = ColCfg<N>::TX;
   constexpr int TPF = N / 8;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
@@ -388,8 +388,7 @@ k_fft_x_contract(const cplx<T>* __restrict__ half, const ContractParams P, const
   C* facc = ytab + (size_t)P.ny * N;        // [G][nacc][N]
   C* rowbuf = facc + (size_t)G * P.nacc * N;  // [G][NP]
   T* winv = reinterpret_cast<T*>(rowbuf + (size_t)XCfg<N>::NBUF * NP);  // 1/sinc^p, a = 0..N/2
-  T* fa = winv + (N / 2 + 2);               // phase-a factor per kx
-  T* fidx = fa + N;                         // signed frequency index of storage position, as T
+  T* fidx = winv + (N / 2 + 2);             // signed frequency index of storage position, as T
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
   for (int i = tid; i < N; i += blockDim.x) {
@@ -410,9 +409,6 @@ k_fft_x_contract(const cplx<T>* __restrict__ half, const ContractParams P, const
     const int jy = ky < N / 2 ? ky : ky - N;
     // per-mode window/interlace factor and Y_lm(khat) table; clear the accumulators
     for (int kx = tid; kx < N; kx += blockDim.x) {
-      const int i = kx < N / 2 ? kx : kx - N;
-      const int ai = i < 0 ? -i : i, aj = jy < 0 ? -jy : jy;
-      fa[kx] = half_or_one * winv[ai] * winv[aj] * winv[kz];
       if (P.ny > 0) {
         const T fi = fidx[kx], fj = fidx[ky], fk = fidx[kz];
         const T r2 = fi * fi + fj * fj + fk * fk;
@@ -424,10 +420,34 @@ k_fft_x_contract(const cplx<T>* __restrict__ half, const ContractParams P, const
           ytab[(size_t)j * N + kx] = cmk(re, im);
         }
       }
-      for (int q = 0; q < G * P.nacc; ++q) facc[(size_t)q * N + kx] = cmk(T(0), T(0));
     }
     __syncthreads();
-    const C phyz = cmul(phs[jy + N / 2], phs[kz + N / 2]);
+    // this thread's 8 modes kx = t + q TPF: window (and interlacing 1/2) weight of phase-a fields,
+    // and the same times the half-cell phase e^{i pi (i + j + l)/N} for phase-b fields
+    T wa[8];
+    C wb[8];
+    {
+      const C phyz = cmul(phs[jy + N / 2], phs[kz + N / 2]);
+      const int aj = jy < 0 ? -jy : jy;
+      const T wyz = half_or_one * winv[aj] * winv[kz];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int kx = t + q * TPF;
+        const int i = kx < N / 2 ? kx : kx - N;
+        wa[q] = wyz * winv[i < 0 ? -i : i];
+        wb[q] = cscale(cmul(phs[i + N / 2], phyz), wa[q]);
+      }
+    }
+    // F_0, F_2, F_4 accumulators of this thread's modes: registers in float (summed over groups
+    // below), this group's shared-memory rows in float64 (registers would spill)
+    constexpr bool REG_ACC = sizeof(T) == 4;
+    C r0[REG_ACC ? 8 : 1], r1[REG_ACC ? 8 : 1], r2[REG_ACC ? 8 : 1];
+    if constexpr (REG_ACC) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) r0[q] = r1[q] = r2[q] = cmk(T(0), T(0));
+    } else if (ingroup) {
+      for (int q = 0; q < 8 * P.nacc; ++q) facc[((size_t)g * P.nacc + q / 8) * N + t + (q % 8) * TPF] = cmk(T(0), T(0));
+    }
     C v[8], vn[8];
     const size_t fstride = (size_t)(N / 2) * N * N;
     const size_t roff = ((size_t)kz * N + ky) * N;
@@ -449,28 +469,42 @@ k_fft_x_contract(const cplx<T>* __restrict__ half, const ContractParams P, const
 #pragma unroll
         for (int q = 0; q < 8; ++q) v[q] = cmk(T(0), T(0));
       }
-      fft_block<N, -1>(v, t, tw, RowView<C>{rowbuf + (size_t)(ingroup ? g : G) * NP});
+      fft_block<N, -1>(v, t, tw, RowView<C>{rowbuf + (size_t)(ingroup ? g : G) * NP},
+                       RowSync<N, CONTRACT_THREADS>::make(g));
       if (live) {
         const FieldCoef c = P.fc[f];
-        C* acc = facc + ((size_t)g * P.nacc + c.acc) * N;
+        const T cs = coef_scale<T>(c);
+        C* sacc = facc + ((size_t)g * P.nacc + c.acc) * N + t;
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-          const int kx = t + q * TPF;
-          T w = coef_scale<T>(c) * fa[kx];
+          T sc = cs;
           if (c.yidx >= 0) {
-            const C y = ytab[(size_t)c.yidx * N + kx];
-            w *= (c.part == PART_RE ? y.x : y.y);
+            const C y = ytab[(size_t)c.yidx * N + t + q * TPF];
+            sc *= (c.part == PART_RE ? y.x : y.y);
           }
-          C a = cscale(v[q], w);
-          if (c.phase) {
-            const int i = kx < N / 2 ? kx : kx - N;
-            a = cmul(a, cmul(phs[i + N / 2], phyz));
+          const C a = c.phase ? cmul(v[q], cscale(wb[q], sc)) : cscale(v[q], sc * wa[q]);
+          if constexpr (REG_ACC) {
+            if (c.acc == 0) r0[q] = cadd(r0[q], a);
+            else if (c.acc == 1) r1[q] = cadd(r1[q], a);
+            else r2[q] = cadd(r2[q], a);
+          } else {
+            sacc[q * TPF] = cadd(sacc[q * TPF], a);
           }
-          acc[kx] = cadd(acc[kx], a);
         }
       }
 #pragma unroll
       for (int q = 0; q < 8; ++q) v[q] = vn[q];
+    }
+    if constexpr (REG_ACC) {
+      if (ingroup) {
+        C* fg = facc + (size_t)g * P.nacc * N + t;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          fg[q * TPF] = r0[q];
+          if (P.nacc > 1) fg[N + q * TPF] = r1[q];
+          if (P.nacc > 2) fg[2 * N + q * TPF] = r2[q];
+        }
+      }
     }
     __syncthreads();
     const T fjy = fidx[(jy + N) % N], fkz = fidx[kz];
@@ -619,6 +653,85 @@ k_power_finalize(const double* __restrict__ part, const FinalParams F, const dou
 }
 
 // ---------------------------------------------------------------------------------------------
+// y pass with a selectable number of columns per CTA
+// ---------------------------------------------------------------------------------------------
+template <int N> constexpr bool ytx_ok(int tx) { return tx <= N && N % tx == 0 && tx * N / 8 <= 1024; }
+
+int ytx_for(const npc_ctx* ctx, int n, bool fp64) {
+  auto it = ctx->ytx.find(n * 2 + (fp64 ? 1 : 0));
+  if (it != ctx->ytx.end()) return it->second;
+  return n >= 1024 ? 4 : (n >= 512 ? 8 : 16);
+}
+
+template <typename T, int N, int TX>
+npc_status y_pass_tx(npc_ctx* ctx, cplx<T>* data, int nplanes, const cplx<T>* tw) {
+  using C = cplx<T>;
+  if constexpr (!ytx_ok<N>(TX)) {
+    return set_err(ctx, NPC_ERR_INVALID_ARG, "y pass: %d columns per CTA not valid at n = %d", TX, N);
+  } else {
+    const size_t smem = sizeof(C) * (N + N * TX);
+    auto kern = k_fft_cols<T, N, -1, TX>;
+    NPC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    for (int p0 = 0; p0 < nplanes; p0 += 65535) {
+      const int np = std::min(65535, nplanes - p0);
+      kern<<<dim3(N / TX, np), TX * N / 8, smem, ctx->stream>>>(data + (size_t)p0 * N * N, (size_t)N * N, N, tw);
+      NPC_LAUNCH(ctx);
+    }
+    return NPC_OK;
+  }
+}
+
+template <typename T, int N>
+npc_status y_pass(npc_ctx* ctx, cplx<T>* data, int nplanes, const cplx<T>* tw, int tx) {
+  switch (tx) {
+    case 4: return y_pass_tx<T, N, 4>(ctx, data, nplanes, tw);
+    case 8: return y_pass_tx<T, N, 8>(ctx, data, nplanes, tw);
+    case 16: return y_pass_tx<T, N, 16>(ctx, data, nplanes, tw);
+    case 32: return y_pass_tx<T, N, 32>(ctx, data, nplanes, tw);
+  }
+  return set_err(ctx, NPC_ERR_INVALID_ARG, "y pass: unsupported columns per CTA %d", tx);
+}
+
+// Autotuner for the y pass: times every valid columns-per-CTA choice on a scratch buffer of
+// `nplanes` planes (values irrelevant to the timing) and keeps the fastest for (n, precision).
+template <typename T, int N>
+npc_status tune_y_impl(npc_ctx* ctx, int nplanes) {
+  using C = cplx<T>;
+  const void* twp;
+  NPC_TRY(get_twiddles(ctx, N, sizeof(T) == 8 ? NPC_PREC_FP64 : NPC_PREC_MIXED, &twp));
+  C* buf;
+  NPC_TRY(ws_get(ctx, "tune.y", sizeof(C) * (size_t)nplanes * N * N, (void**)&buf));
+  NPC_CUDA(ctx, cudaMemsetAsync(buf, 0, sizeof(C) * (size_t)nplanes * N * N, ctx->stream));
+  cudaEvent_t e0, e1;
+  NPC_CUDA(ctx, cudaEventCreate(&e0));
+  NPC_CUDA(ctx, cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_tx = ytx_for(ctx, N, sizeof(T) == 8);
+  npc_status st = NPC_OK;
+  for (int tx : {4, 8, 16, 32}) {
+    if (!(tx <= N && N % tx == 0 && tx * N / 8 <= 1024)) continue;
+    st = y_pass<T, N>(ctx, buf, nplanes, (const C*)twp, tx);  // warm-up
+    if (st != NPC_OK) break;
+    cudaEventRecord(e0, ctx->stream);
+    for (int rep = 0; rep < 3 && st == NPC_OK; ++rep) st = y_pass<T, N>(ctx, buf, nplanes, (const C*)twp, tx);
+    cudaEventRecord(e1, ctx->stream);
+    if (st != NPC_OK) break;
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      best_tx = tx;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != NPC_OK) return st;
+  ctx->ytx[N * 2 + (sizeof(T) == 8 ? 1 : 0)] = best_tx;
+  return NPC_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
 template <typename T, int N>
 npc_status fwd_impl(npc_ctx* ctx, const PowerPlan& plan, const Geom& g, const void* mesh_a, const void* mesh_b,
                     void* half) {
@@ -647,20 +760,9 @@ npc_status fwd_impl(npc_ctx* ctx, const PowerPlan& plan, const Geom& g, const vo
     NPC_LAUNCH(ctx);
     NPC_TRY(stage_mark(ctx, "fft_z_weighted"));
   }
-  {
-    const size_t smem = sizeof(C) * (N + N * TX);
-    auto kern = k_fft_cols<T, N, -1>;
-    NPC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int nplanes = plan.fl.nf * KZ;
-    // planes (f, kz) are contiguous N*N blocks; y rows have stride N
-    for (int p0 = 0; p0 < nplanes; p0 += 65535) {
-      const int np = std::min(65535, nplanes - p0);
-      dim3 grid(N / TX, np);
-      kern<<<grid, ColCfg<N>::THREADS, smem, ctx->stream>>>((C*)half + (size_t)p0 * N * N, (size_t)N * N, N, tw);
-      NPC_LAUNCH(ctx);
-    }
-    NPC_TRY(stage_mark(ctx, "fft_y"));
-  }
+  // planes (f, kz) are contiguous N*N blocks; y rows have stride N
+  NPC_TRY((y_pass<T, N>(ctx, (C*)half, plan.fl.nf * KZ, tw, ytx_for(ctx, N, sizeof(T) == 8))));
+  NPC_TRY(stage_mark(ctx, "fft_y"));
   return NPC_OK;
 }
 
@@ -724,7 +826,7 @@ npc_status contract_impl(npc_ctx* ctx, const PowerPlan& plan, const npc_mesh_spe
   constexpr int G = XCfg<N>::G;
   const size_t smem = sizeof(C) * ((size_t)2 * N + (size_t)P.ny * N + (size_t)G * P.nacc * N +
                                    (size_t)XCfg<N>::NBUF * NP) +
-                      sizeof(T) * (N / 2 + 2 + 2 * N);
+                      sizeof(T) * (N / 2 + 2 + N);
   auto kern = k_fft_x_contract<T, N>;
   NPC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
@@ -805,6 +907,20 @@ npc_status contract_dispatch(npc_ctx* ctx, const PowerPlan& plan, const npc_mesh
 }
 
 }  // namespace
+
+npc_status tune_y_pass(npc_ctx* ctx, int n, int prec, int nplanes) {
+  const bool d = prec == NPC_PREC_FP64;
+#define NPC_TY(NN)                                                              \
+  case NN:                                                                      \
+    return d ? tune_y_impl<double, NN>(ctx, nplanes) : tune_y_impl<float, NN>(ctx, nplanes);
+  switch (n) {
+    NPC_TY(16) NPC_TY(32) NPC_TY(48) NPC_TY(64) NPC_TY(96) NPC_TY(128) NPC_TY(192) NPC_TY(256)
+    case 512: return d ? set_err(ctx, NPC_ERR_UNSUPPORTED, "FP64 n <= 256") : tune_y_impl<float, 512>(ctx, nplanes);
+    case 1024: return d ? set_err(ctx, NPC_ERR_UNSUPPORTED, "FP64 n <= 256") : tune_y_impl<float, 1024>(ctx, nplanes);
+  }
+#undef NPC_TY
+  return set_err(ctx, NPC_ERR_UNSUPPORTED, "mesh size %d", n);
+}
 
 npc_status run_forward_transforms(npc_ctx* ctx, int prec, const PowerPlan& plan, const Geom& g,
                                   const void* mesh_a, const void* mesh_b, void* half) {
