@@ -232,6 +232,11 @@ npc_status npc_batch_run(npc_ctx* ctx, int32_t nitems, const npc_batch_item* ite
  * context and reports the branch count.  Runs the batch several times (out_device is overwritten). */
 npc_status npc_batch_tune(npc_ctx* ctx, int32_t nitems, const npc_batch_item* items, uint32_t ell_mask,
                           npc_precision prec, double* out_device, int32_t* branches);
+/* Autotuner of the transform passes for mesh size n: times the valid column-tile widths of the
+ * y pass on a scratch buffer and keeps the fastest for (n, prec) in the context; every later call
+ * on the context uses it.  Synchronous; results do not depend on the choice (same arithmetic per
+ * column). */
+npc_status npc_tune_transforms(npc_ctx* ctx, int32_t n, npc_precision prec);
 /* Fix the number of concurrent branches (1..16; 0 restores the default of 4). */
 npc_status npc_batch_set_branches(npc_ctx* ctx, int32_t branches);
 

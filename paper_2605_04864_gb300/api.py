@@ -297,3 +297,9 @@ def batch_tune(arr, out, ells=(0, 2, 4), precision="mixed", device=0):
 
 def batch_set_branches(n, device=0):
     B.check(B.npc_batch_set_branches(context(device), int(n)))
+
+
+def tune_transforms(n, precision="mixed", device=0):
+    """Autotune the transform passes for mesh size n on this context (kept for later calls)."""
+    ctx = context(device)
+    B.check(B.npc_tune_transforms(ctx, int(n), _prec(precision)), ctx)

@@ -80,6 +80,7 @@ _sig = {
     "npc_batch_tune": (C.c_int, [C.c_void_p, C.c_int32, _P(npc_batch_item), C.c_uint32, C.c_int, C.c_void_p,
                                  _P(C.c_int32)]),
     "npc_batch_set_branches": (C.c_int, [C.c_void_p, C.c_int32]),
+    "npc_tune_transforms": (C.c_int, [C.c_void_p, C.c_int32, C.c_int]),
     "npc_mesh_multipoles_len": (C.c_int64, [_P(npc_kbins), C.c_uint32, C.c_int32]),
     "npc_mesh_multipoles": (C.c_int, [C.c_void_p, _P(npc_mesh_spec), C.c_void_p, _P(npc_kbins), C.c_uint32,
                                       C.c_int32, C.c_double, C.c_double, C.c_double, C.c_int, C.c_void_p,

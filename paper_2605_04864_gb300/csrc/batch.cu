@@ -371,13 +371,13 @@ npc_status npc_batch_tune(npc_ctx* ctx, int32_t nitems, const npc_batch_item* it
   float best = 1e30f;
   int best_b = 1;
   npc_status st = NPC_OK;
-  for (int nb : {1, 2, 4, 6, 8, 12}) {
+  for (int nb : {1, 2, 4, 8}) {
     if (nb > nitems || nb > MAX_BRANCHES) break;
     st = batch_exec(ctx, nitems, items, ell_mask, prec, out_device, true, nb);   // warm + capture
     if (st == NPC_OK) st = batch_exec(ctx, nitems, items, ell_mask, prec, out_device, true, nb);  // replay
     if (st != NPC_OK) break;
     cudaEventRecord(e0, ctx->stream);
-    for (int rep = 0; rep < 3 && st == NPC_OK; ++rep)
+    for (int rep = 0; rep < 2 && st == NPC_OK; ++rep)
       st = batch_exec(ctx, nitems, items, ell_mask, prec, out_device, true, nb);
     cudaEventRecord(e1, ctx->stream);
     if (st != NPC_OK) break;
@@ -394,6 +394,16 @@ npc_status npc_batch_tune(npc_ctx* ctx, int32_t nitems, const npc_batch_item* it
   if (st != NPC_OK) return st;
   ctx->batch_branches = best_b;
   if (branches) *branches = best_b;
+  return end_call(ctx);
+}
+
+npc_status npc_tune_transforms(npc_ctx* ctx, int32_t n, npc_precision prec) {
+  if (!ctx) return NPC_ERR_INVALID_ARG;
+  begin_call(ctx);
+  if (prec != NPC_PREC_FP64 && prec != NPC_PREC_MIXED) return set_err(ctx, NPC_ERR_INVALID_ARG, "bad precision");
+  NPC_CUDA(ctx, cudaSetDevice(ctx->device));
+  NPC_TRY(tune_y_pass(ctx, n, prec, std::min(n / 2, 64) * 4));
+  NPC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   return end_call(ctx);
 }
 

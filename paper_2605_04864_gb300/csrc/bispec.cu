@@ -389,10 +389,11 @@ constexpr int TRI_CHUNK = 256;          // cells staged per chunk
 constexpr int TRI_FLUSH = 16;           // chunks between FP64 flushes
 constexpr int TRI_WARPS = 8;
 constexpr int TRI_MT = 3;               // m tiles (16 rows) per warp -> 384 rows per CTA
-constexpr int TRI_NT = 4;               // n tiles (8 cols) -> 32 columns
+constexpr int TRI_NT_MAX = 4;           // n tiles (8 cols) -> up to 32 columns (3 when <= 24 are used)
 constexpr int TRI_ROWS = TRI_WARPS * TRI_MT * 16;
-constexpr int TRI_COLS = TRI_NT * 8;
-constexpr int TRI_SPAD = TRI_CHUNK + 8; // staging row stride (floats)
+constexpr int TRI_COLS = TRI_NT_MAX * 8;
+constexpr int TRI_SPAD = TRI_CHUNK + 4; // staging row stride (floats): 8 rows x 4 cells of an operand
+                                        // fragment fall on 32 distinct banks
 
 struct TripleArgs {
   int nrows;        // pair rows over all families (family f, pair p) -> row f * npair + p
@@ -403,18 +404,16 @@ struct TripleArgs {
   int a_slot[2][NB_MAX];            // staged slot of A_i per family
   int b_slot[NB_MAX];               // staged slot of B_j
   int c_slot[TRI_COLS];             // staged slot of column c (-1: zero column)
+  int nf_cols;                      // columns 0 .. nf_cols-1 are F_k (k = column), the rest G^(l)
   int64_t ncell;
 };
 
-__device__ __forceinline__ uint32_t to_tf32(float v) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
-  return r;
-}
-
+// v = hi + lo with hi = v truncated to the 10 explicit mantissa bits of tf32 (a bit mask) and the
+// exact residual lo, which the tensor core reads truncated to tf32 as well: the product keeps about
+// 21 bits (the error of lo's truncation is below 2^-21 |v|).
 __device__ __forceinline__ void split_tf32(float v, uint32_t& hi, uint32_t& lo) {
-  hi = to_tf32(v);
-  lo = to_tf32(v - __uint_as_float(hi));
+  hi = __float_as_uint(v) & 0xffffe000u;
+  lo = __float_as_uint(v - __uint_as_float(hi));
 }
 
 __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
@@ -425,32 +424,38 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// grid = (cell ranges, row groups of TRI_ROWS); block = TRI_WARPS warps.
+// grid = (cell ranges, row groups of TRI_ROWS); block = TRI_WARPS warps; TRI_NT n tiles of 8
+// columns (3 when the F_k and G^(l) columns fit in 24).  Rows run in the order row_pair (pairs
+// sorted by their larger bin j) and are written back to their pair index.
 // Fragment layouts of m16n8k8 (tf32): A a0 (row g, k t), a1 (g+8, t), a2 (g, t+4), a3 (g+8, t+4);
 // B b0 (k t, col g), b1 (k t+4, col g); D d0, d1 (row g, cols 2t, 2t+1), d2, d3 (row g+8, ...),
 // with g = lane/4 and t = lane%4.
+template <int TRI_NT>
 __global__ void __launch_bounds__(TRI_WARPS * 32, 1)
-k_triple(const float* __restrict__ R, const TripleArgs A, const int* __restrict__ pair_ij, double* __restrict__ part) {
+k_triple(const float* __restrict__ R, const TripleArgs A, const int* __restrict__ pair_ij,
+         const int* __restrict__ row_pair, double* __restrict__ part) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* stage = reinterpret_cast<float*>(smem_raw);                               // [nstage][TRI_SPAD]
   double* dacc = reinterpret_cast<double*>(stage + (size_t)A.nstage * TRI_SPAD);  // [tid][NACC]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = lane >> 2, t = lane & 3;
   const int rowbase = blockIdx.y * TRI_ROWS + warp * TRI_MT * 16;
-  int sa[TRI_MT][2], sb[TRI_MT][2];
+  int sa[TRI_MT][2], sb[TRI_MT][2], orow[TRI_MT][2];
 #pragma unroll
-  for (int mt = 0; mt < TRI_MT; ++mt)
+  for (int mt = 0; mt < TRI_MT; ++mt) {
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int r = rowbase + mt * 16 + g + 8 * h;
-      sa[mt][h] = sb[mt][h] = -1;
+      sa[mt][h] = sb[mt][h] = orow[mt][h] = -1;
       if (r < A.nrows) {
-        const int fam = r / A.npair, p = r % A.npair;
+        const int fam = r / A.npair, p = row_pair[r % A.npair];
         const int pij = pair_ij[p];
         sa[mt][h] = A.a_slot[fam][pij & 0xffff];
         sb[mt][h] = A.b_slot[pij >> 16];
+        orow[mt][h] = fam * A.npair + p;
       }
     }
+  }
   int scol[TRI_NT];
 #pragma unroll
   for (int nt = 0; nt < TRI_NT; ++nt) {
@@ -533,9 +538,9 @@ k_triple(const float* __restrict__ R, const TripleArgs A, const int* __restrict_
     for (int nt = 0; nt < TRI_NT; ++nt)
 #pragma unroll
       for (int q = 0; q < 4; ++q, ++e) {
-        const int r = rowbase + mt * 16 + g + ((q >> 1) ? 8 : 0);
+        const int r = orow[mt][q >> 1];
         const int c = nt * 8 + 2 * t + (q & 1);
-        if (r < A.nrows && c < A.ncol) part[((size_t)blockIdx.x * A.nrows + r) * A.ncol + c] = myacc[e];
+        if (r >= 0 && c < A.ncol) part[((size_t)blockIdx.x * A.nrows + r) * A.ncol + c] = myacc[e];
       }
 }
 
@@ -933,6 +938,14 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
   const size_t t_ob = push_bytes(zb.data(), sizeof(int) * nzp);
   const size_t t_tri = push_bytes(tr.tri.data(), sizeof(int) * tr.tri.size());
   const size_t t_pij = push_bytes(tr.pij.data(), sizeof(int) * tr.pij.size());
+  // triple-product row order: pairs sorted by (j, i)
+  std::vector<int> row_pair(tr.pij.size());
+  for (size_t q = 0; q < row_pair.size(); ++q) row_pair[q] = (int)q;
+  std::stable_sort(row_pair.begin(), row_pair.end(), [&](int a, int b) {
+    const int ja = tr.pij[a] >> 16, jb = tr.pij[b] >> 16;
+    return ja != jb ? ja < jb : (tr.pij[a] & 0xffff) < (tr.pij[b] & 0xffff);
+  });
+  const size_t t_rowp = push_bytes(row_pair.data(), sizeof(int) * row_pair.size());
   char* dtab;
   NPC_TRY(ws_table(ctx, need_nt ? "bis.tables.nt" : "bis.tables", tables, tables.data(), tables.size(),
                    (void**)&dtab));
@@ -992,6 +1005,7 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
       return a.nstage++;
     };
     for (int q = 0; q < TRI_COLS; ++q) a.c_slot[q] = -1;
+    a.nf_cols = nb;
     if (indicator) {
       for (int b = 0; b < nb; ++b) a.a_slot[0][b] = a.b_slot[b] = a.c_slot[b] = stage_of(iI + b);
       a.nrows = npair;
@@ -1015,12 +1029,17 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
                  (void**)&part));
   auto launch = [&](const TripleArgs& a) -> npc_status {
     if constexpr (sizeof(T) == 4) {
-      const size_t smem = sizeof(float) * (size_t)a.nstage * TRI_SPAD +
-                          sizeof(double) * (size_t)TRI_WARPS * 32 * TRI_MT * TRI_NT * 4;
-      NPC_CUDA(ctx, cudaFuncSetAttribute(k_triple, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       const int groups = (a.nrows + TRI_ROWS - 1) / TRI_ROWS;
-      k_triple<<<dim3(grid, groups), TRI_WARPS * 32, smem, ctx->stream>>>((const float*)R, a,
-                                                                          (const int*)(dtab + t_pij), part);
+      auto run = [&](auto kern, int nt) -> npc_status {
+        const size_t smem = sizeof(float) * (size_t)a.nstage * TRI_SPAD +
+                            sizeof(double) * (size_t)TRI_WARPS * 32 * TRI_MT * nt * 4;
+        NPC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kern<<<dim3(grid, groups), TRI_WARPS * 32, smem, ctx->stream>>>(
+            (const float*)R, a, (const int*)(dtab + t_pij), (const int*)(dtab + t_rowp), part);
+        return NPC_OK;
+      };
+      if (a.ncol <= 24) NPC_TRY(run(k_triple<3>, 3));
+      else NPC_TRY(run(k_triple<4>, 4));
     } else {
       const int outs = a.nrows * a.ncol;
       k_triple_f64<<<dim3(grid, (outs + 255) / 256), 256, 0, ctx->stream>>>((const double*)R, a,

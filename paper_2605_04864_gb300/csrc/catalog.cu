@@ -374,27 +374,30 @@ k_fold(const T* __restrict__ tiles, PaintGeo g, int nphase, const double* __rest
   if (ly <= 2) { by[ny] = nbm[1]; ty[ny] = ly + BS + 1; ++ny; }
   by[ny] = B[1]; ty[ny] = ly + 1; ++ny;
   if (ly == BS - 1) { by[ny] = nbp[1]; ty[ny] = 0; ++ny; }
-  // per (iy, ix) option: tile base (brick index without z) and in-tile offset without z
-  size_t base_yx[4];
-  int off_yx[4];
+  // per (iy, ix) option: pointer into the tile of the brick in the same z layer
+  const size_t zstride = (size_t)nb * nb * nphase * TS3;   // between z layers of bricks
+  const T* p_yx[4];
   int nyx = 0;
   for (int iy = 0; iy < ny; ++iy)
     for (int ix = 0; ix < nx; ++ix) {
-      base_yx[nyx] = (size_t)by[iy] * nb + bx[ix];
-      off_yx[nyx] = ty[iy] * TS + tx[ix];
-      ++nyx;
+      const size_t brick = ((size_t)B[2] * nb + by[iy]) * nb + bx[ix];
+      p_yx[nyx++] = tiles + (brick * nphase + ph) * TS3 + ty[iy] * TS + tx[ix];
     }
+  const ptrdiff_t dzm = (ptrdiff_t)(nbm[2] - B[2]) * (ptrdiff_t)zstride;   // to the lower z layer
+  const ptrdiff_t dzp = (ptrdiff_t)(nbp[2] - B[2]) * (ptrdiff_t)zstride;   // to the upper z layer
   T* col = mesh + ((size_t)(B[2] * BS) * n + (B[1] * BS + ly)) * n + (B[0] * BS + lx);
   for (int lz = 0; lz < BS; ++lz) {
-    int nz = 0, bz[2], tz[2];
-    if (lz <= 2) { bz[nz] = nbm[2]; tz[nz] = lz + BS + 1; ++nz; }
-    bz[nz] = B[2]; tz[nz] = lz + 1; ++nz;
-    if (lz == BS - 1) { bz[nz] = nbp[2]; tz[nz] = 0; ++nz; }
     T v = T(0);
-    for (int iz = 0; iz < nz; ++iz) {
-      const size_t zb = (size_t)bz[iz] * nb * nb;
-      const int zo = tz[iz] * TS * TS;
-      for (int k = 0; k < nyx; ++k) v += tiles[((zb + base_yx[k]) * nphase + ph) * TS3 + zo + off_yx[k]];
+    if (lz <= 2) {
+      const ptrdiff_t o = dzm + (ptrdiff_t)(lz + BS + 1) * TS * TS;
+      for (int k = 0; k < nyx; ++k) v += p_yx[k][o];
+    }
+    {
+      const int o = (lz + 1) * TS * TS;
+      for (int k = 0; k < nyx; ++k) v += p_yx[k][o];
+    }
+    if (lz == BS - 1) {
+      for (int k = 0; k < nyx; ++k) v += p_yx[k][dzp];
     }
     col[(size_t)lz * n * n] = v - mean;
   }

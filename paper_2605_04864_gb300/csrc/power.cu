@@ -298,7 +298,7 @@ static int std_pairs(const FieldList& fl) {
 // data[plane*plane_stride + j*row_stride + x].  grid = (N/TX, nplanes); TX columns per CTA is a
 // tuning parameter (see tune_y_pass).
 template <typename T, int N, int DIR, int TX>
-__global__ void __launch_bounds__(TX * N / 8)
+__global__ void __launch_bounds__(TX * N / 8, (TX * N / 8 <= 512 ? 1536 / (TX * N / 8) : 1))
 k_fft_cols(cplx<T>* __restrict__ data, size_t plane_stride, int row_stride, const cplx<T>* __restrict__ tw_g) {
   using C = cplx<T>;
   constexpr int TPF = N / 8;
@@ -388,7 +388,8 @@ k_fft_x_contract(const cplx<T>* __restrict__ half, const ContractParams P, const
   C* facc = ytab + (size_t)P.ny * N;        // [G][nacc][N]
   C* rowbuf = facc + (size_t)G * P.nacc * N;  // [G][NP]
   T* winv = reinterpret_cast<T*>(rowbuf + (size_t)XCfg<N>::NBUF * NP);  // 1/sinc^p, a = 0..N/2
-  T* fidx = winv + (N / 2 + 2);             // signed frequency index of storage position, as T
+  T* fa = winv + (N / 2 + 2);               // phase-a factor per kx
+  T* fidx = fa + N;                         // signed frequency index of storage position, as T
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
   for (int i = tid; i < N; i += blockDim.x) {
@@ -409,6 +410,9 @@ k_fft_x_contract(const cplx<T>* __restrict__ half, const ContractParams P, const
     const int jy = ky < N / 2 ? ky : ky - N;
     // per-mode window/interlace factor and Y_lm(khat) table; clear the accumulators
     for (int kx = tid; kx < N; kx += blockDim.x) {
+      const int i = kx < N / 2 ? kx : kx - N;
+      const int ai = i < 0 ? -i : i, aj = jy < 0 ? -jy : jy;
+      fa[kx] = half_or_one * winv[ai] * winv[aj] * winv[kz];
       if (P.ny > 0) {
         const T fi = fidx[kx], fj = fidx[ky], fk = fidx[kz];
         const T r2 = fi * fi + fj * fj + fk * fk;
@@ -420,34 +424,10 @@ k_fft_x_contract(const cplx<T>* __restrict__ half, const ContractParams P, const
           ytab[(size_t)j * N + kx] = cmk(re, im);
         }
       }
+      for (int q = 0; q < G * P.nacc; ++q) facc[(size_t)q * N + kx] = cmk(T(0), T(0));
     }
     __syncthreads();
-    // this thread's 8 modes kx = t + q TPF: window (and interlacing 1/2) weight of phase-a fields,
-    // and the same times the half-cell phase e^{i pi (i + j + l)/N} for phase-b fields
-    T wa[8];
-    C wb[8];
-    {
-      const C phyz = cmul(phs[jy + N / 2], phs[kz + N / 2]);
-      const int aj = jy < 0 ? -jy : jy;
-      const T wyz = half_or_one * winv[aj] * winv[kz];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int kx = t + q * TPF;
-        const int i = kx < N / 2 ? kx : kx - N;
-        wa[q] = wyz * winv[i < 0 ? -i : i];
-        wb[q] = cscale(cmul(phs[i + N / 2], phyz), wa[q]);
-      }
-    }
-    // F_0, F_2, F_4 accumulators of this thread's modes: registers in float (summed over groups
-    // below), this group's shared-memory rows in float64 (registers would spill)
-    constexpr bool REG_ACC = sizeof(T) == 4;
-    C r0[REG_ACC ? 8 : 1], r1[REG_ACC ? 8 : 1], r2[REG_ACC ? 8 : 1];
-    if constexpr (REG_ACC) {
-#pragma unroll
-      for (int q = 0; q < 8; ++q) r0[q] = r1[q] = r2[q] = cmk(T(0), T(0));
-    } else if (ingroup) {
-      for (int q = 0; q < 8 * P.nacc; ++q) facc[((size_t)g * P.nacc + q / 8) * N + t + (q % 8) * TPF] = cmk(T(0), T(0));
-    }
+    const C phyz = cmul(phs[jy + N / 2], phs[kz + N / 2]);
     C v[8], vn[8];
     const size_t fstride = (size_t)(N / 2) * N * N;
     const size_t roff = ((size_t)kz * N + ky) * N;
@@ -473,38 +453,25 @@ k_fft_x_contract(const cplx<T>* __restrict__ half, const ContractParams P, const
                        RowSync<N, CONTRACT_THREADS>::make(g));
       if (live) {
         const FieldCoef c = P.fc[f];
-        const T cs = coef_scale<T>(c);
-        C* sacc = facc + ((size_t)g * P.nacc + c.acc) * N + t;
+        C* acc = facc + ((size_t)g * P.nacc + c.acc) * N;
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-          T sc = cs;
+          const int kx = t + q * TPF;
+          T w = coef_scale<T>(c) * fa[kx];
           if (c.yidx >= 0) {
-            const C y = ytab[(size_t)c.yidx * N + t + q * TPF];
-            sc *= (c.part == PART_RE ? y.x : y.y);
+            const C y = ytab[(size_t)c.yidx * N + kx];
+            w *= (c.part == PART_RE ? y.x : y.y);
           }
-          const C a = c.phase ? cmul(v[q], cscale(wb[q], sc)) : cscale(v[q], sc * wa[q]);
-          if constexpr (REG_ACC) {
-            if (c.acc == 0) r0[q] = cadd(r0[q], a);
-            else if (c.acc == 1) r1[q] = cadd(r1[q], a);
-            else r2[q] = cadd(r2[q], a);
-          } else {
-            sacc[q * TPF] = cadd(sacc[q * TPF], a);
+          C a = cscale(v[q], w);
+          if (c.phase) {
+            const int i = kx < N / 2 ? kx : kx - N;
+            a = cmul(a, cmul(phs[i + N / 2], phyz));
           }
+          acc[kx] = cadd(acc[kx], a);
         }
       }
 #pragma unroll
       for (int q = 0; q < 8; ++q) v[q] = vn[q];
-    }
-    if constexpr (REG_ACC) {
-      if (ingroup) {
-        C* fg = facc + (size_t)g * P.nacc * N + t;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          fg[q * TPF] = r0[q];
-          if (P.nacc > 1) fg[N + q * TPF] = r1[q];
-          if (P.nacc > 2) fg[2 * N + q * TPF] = r2[q];
-        }
-      }
     }
     __syncthreads();
     const T fjy = fidx[(jy + N) % N], fkz = fidx[kz];
@@ -826,7 +793,7 @@ npc_status contract_impl(npc_ctx* ctx, const PowerPlan& plan, const npc_mesh_spe
   constexpr int G = XCfg<N>::G;
   const size_t smem = sizeof(C) * ((size_t)2 * N + (size_t)P.ny * N + (size_t)G * P.nacc * N +
                                    (size_t)XCfg<N>::NBUF * NP) +
-                      sizeof(T) * (N / 2 + 2 + N);
+                      sizeof(T) * (N / 2 + 2 + 2 * N);
   auto kern = k_fft_x_contract<T, N>;
   NPC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
