@@ -203,13 +203,25 @@ struct PFinal {
 
 // Per bin: fixed-order sum of the warp partials; outputs k_eff, N_modes, P_l; for the adjoint the
 // coefficients coef[e][b] = g_eb (2l+1)/(I22 N_b).
-__global__ void k_adj_pfinal(const double* __restrict__ part, PFinal F, const double* __restrict__ dldp,
-                             double* __restrict__ out, double* __restrict__ coef) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= F.nb) return;
-  double s[ANS] = {0, 0, 0, 0, 0};
-  for (int p = 0; p < F.nparts; ++p)
-    for (int k = 0; k < ANS; ++k) s[k] += part[((size_t)p * F.nb + b) * ANS + k];
+// One CTA per bin: thread t sums partials t, t + 256, ... in order, then a fixed tree.
+__global__ void __launch_bounds__(256)
+k_adj_pfinal(const double* __restrict__ part, PFinal F, const double* __restrict__ dldp,
+             double* __restrict__ out, double* __restrict__ coef) {
+  const int b = blockIdx.x;
+  __shared__ double sh[ANS][256];
+  double a[ANS] = {0, 0, 0, 0, 0};
+  for (int p = threadIdx.x; p < F.nparts; p += blockDim.x)
+    for (int k = 0; k < ANS; ++k) a[k] += part[((size_t)p * F.nb + b) * ANS + k];
+  for (int k = 0; k < ANS; ++k) sh[k][threadIdx.x] = a[k];
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o)
+      for (int k = 0; k < ANS; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  double s[ANS];
+  for (int k = 0; k < ANS; ++k) s[k] = sh[k][0];
   const bool has = s[0] > 0;
   if (F.want_out) {
     out[b] = has ? F.kf * s[1] / s[0] : 0.0;
@@ -927,7 +939,7 @@ npc_status mesh_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb, 
     F.kf = 2.0 * M_PI / m.box;
     F.want_out = job.want_out ? 1 : 0;
     if (job.dldp) NPC_TRY(ws_get(ctx, "adj.coef", sizeof(double) * nell * nb, (void**)&coef));
-    k_adj_pfinal<<<(nb + 127) / 128, 128, 0, ctx->stream>>>(part, F, job.dldp, job.out, coef);
+    k_adj_pfinal<<<nb, 256, 0, ctx->stream>>>(part, F, job.dldp, job.out, coef);
     NPC_LAUNCH(ctx);
     NPC_TRY(stage_mark(ctx, "power_bins"));
   }

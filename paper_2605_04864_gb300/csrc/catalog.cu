@@ -238,14 +238,29 @@ __global__ void k_scatter(const P* __restrict__ pos, const P* __restrict__ w, in
       const double s = ((double)pos[3 * i + a] - g.o[a]) * g.inv_h;
       m |= axis_meta<ASSIGN>(s, g.n, g.bs, &fr[a]) << (8 * a);
     }
-    typename RecOf<R>::type r;
-    r.x = (R)fr[0];
-    r.y = (R)fr[1];
-    r.z = (R)fr[2];
-    r.w = (R)wc;
     const int dst = start[b] + rank[i];
+    typename RecOf<R>::type r;
+    if constexpr (sizeof(R) == 4) {
+      // one 16-byte record: per axis the fraction in 24-bit fixed point (truncated, |error| < 2^-24
+      // of a cell) with that axis's 8 decision bits on top, and the float weight
+      uint32_t u[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const uint32_t q = __float2uint_rz((float)fr[a] * 16777216.0f);
+        u[a] = (q > 0xffffffu ? 0xffffffu : q) | (((m >> (8 * a)) & 255u) << 24);
+      }
+      r.x = __uint_as_float(u[0]);
+      r.y = __uint_as_float(u[1]);
+      r.z = __uint_as_float(u[2]);
+      r.w = (float)wc;
+    } else {
+      r.x = (R)fr[0];
+      r.y = (R)fr[1];
+      r.z = (R)fr[2];
+      r.w = (R)wc;
+      meta[dst] = m;
+    }
     rec[dst] = r;
-    meta[dst] = m;
   }
 }
 
@@ -313,12 +328,20 @@ k_paint_brick(const typename RecOf<R>::type* __restrict__ rec, const uint32_t* _
   constexpr int NT = ASSIGN == 2 ? 2 : 3;
   for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
     const typename RecOf<R>::type r = rec[beg + k];
-    const uint32_t m = meta[beg + k];
     int ix[NT], iy[NT], iz[NT];
     T wx[NT], wy[NT], wz[NT];
-    axis_taps<ASSIGN, T>((T)r.x, m & 255u, ph, ix, wx);
-    axis_taps<ASSIGN, T>((T)r.y, (m >> 8) & 255u, ph, iy, wy);
-    axis_taps<ASSIGN, T>((T)r.z, (m >> 16) & 255u, ph, iz, wz);
+    if constexpr (sizeof(R) == 4) {
+      const uint32_t ux = __float_as_uint(r.x), uy = __float_as_uint(r.y), uz = __float_as_uint(r.z);
+      const float sc24 = 5.9604644775390625e-8f;   // 2^-24
+      axis_taps<ASSIGN, T>((T)((float)(ux & 0xffffffu) * sc24), ux >> 24, ph, ix, wx);
+      axis_taps<ASSIGN, T>((T)((float)(uy & 0xffffffu) * sc24), uy >> 24, ph, iy, wy);
+      axis_taps<ASSIGN, T>((T)((float)(uz & 0xffffffu) * sc24), uz >> 24, ph, iz, wz);
+    } else {
+      const uint32_t m = meta[beg + k];
+      axis_taps<ASSIGN, T>((T)r.x, m & 255u, ph, ix, wx);
+      axis_taps<ASSIGN, T>((T)r.y, (m >> 8) & 255u, ph, iy, wy);
+      axis_taps<ASSIGN, T>((T)r.z, (m >> 16) & 255u, ph, iz, wz);
+    }
     const T wgt = (T)r.w * scale;
 #pragma unroll
     for (int c = 0; c < NT; ++c) {

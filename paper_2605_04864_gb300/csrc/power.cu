@@ -125,6 +125,53 @@ k_fwd_z(const T* __restrict__ mesh_a, const T* __restrict__ mesh_b, cplx<T>* __r
   }
 }
 
+// First pass for a single unweighted real field (global line of sight without interlacing, mesh
+// gradients): two neighbouring x columns share one complex transform, c = F(x) + i F(x+1), and
+// their half spectra follow from c(kz) and conj c(N - kz).  grid = (N / (2 TX), N).
+template <int N> struct SingleCfg {   // column pairs per CTA: 2 TX divides N, TX <= the z-pass TX
+  static constexpr int TX = (ColCfg<N>::TX >= 16 && N % 32 == 0) ? 16
+                          : (ColCfg<N>::TX >= 8 && N % 16 == 0) ? 8 : 4;
+  static constexpr int THREADS = TX * N / 8;
+};
+
+template <typename T, int N>
+__global__ void __launch_bounds__(SingleCfg<N>::THREADS)
+k_fwd_z_single(const T* __restrict__ mesh, cplx<T>* __restrict__ half, const cplx<T>* __restrict__ tw_g, int KZ) {
+  using C = cplx<T>;
+  constexpr int TX = SingleCfg<N>::TX;
+  constexpr int TPF = N / 8;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  C* work = tw + N;
+  const int tid = threadIdx.x;
+  const int c = tid % TX, t = tid / TX;
+  const int x0 = blockIdx.x * 2 * TX, y = blockIdx.y;
+  for (int i = tid; i < N; i += blockDim.x) tw[i] = tw_g[i];
+  C v[8];
+  const T* col = mesh + (size_t)y * N + x0 + 2 * c;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const size_t zoff = (size_t)(t + q * TPF) * N * N;
+    v[q] = cmk(col[zoff], col[zoff + 1]);
+  }
+  __syncthreads();
+  fft_block<N, -1>(v, t, tw, ColView<C>{work + c, TX});
+#pragma unroll
+  for (int q = 0; q < 8; ++q) work[(t + q * TPF) * TX + c] = v[q];
+  __syncthreads();
+  for (int i = tid; i < KZ * TX; i += blockDim.x) {
+    const int kz = i / TX, cc = i % TX;
+    const C z1 = work[kz * TX + cc];
+    const C z2 = cconj(work[((N - kz) % N) * TX + cc]);
+    const C a = cscale(cadd(z1, z2), T(0.5));
+    const C d = csub(z1, z2);
+    const C b = cmk(T(0.5) * d.y, T(-0.5) * d.x);
+    C* dst = half + ((size_t)kz * N + y) * N + x0 + 2 * cc;
+    dst[0] = a;
+    dst[1] = b;
+  }
+}
+
 // ---------------------------------------------------------------------------------------------
 // Specialised first pass for the standard interlaced field layout (l in {0, 2, 4}, both phases):
 // pair p is (l, m, kind) known at compile time; kind 0 packs the m = 0 field of phase a (real
@@ -361,6 +408,9 @@ __device__ __forceinline__ T sinc_pow(T a, int p) {
   return r;
 }
 
+__device__ __forceinline__ void sincospi_t(float x, float* s, float* c) { sincospif(x, s, c); }
+__device__ __forceinline__ void sincospi_t(double x, double* s, double* c) { sincospi(x, s, c); }
+
 template <int N> struct XCfg {
   static constexpr int TPF = N / 8;
   static constexpr int G = RowGroups<N, CONTRACT_THREADS>::G;        // rows in flight
@@ -383,22 +433,16 @@ k_fft_x_contract(const cplx<T>* __restrict__ half, const ContractParams P, const
   constexpr int NW = CONTRACT_THREADS / 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
-  C* phs = tw + N;                          // e^{i pi a/N}, index a + N/2
-  C* ytab = phs + N;                        // [ny][N]
+  C* ytab = tw + N;                         // [ny][N]
   C* facc = ytab + (size_t)P.ny * N;        // [G][nacc][N]
   C* rowbuf = facc + (size_t)G * P.nacc * N;  // [G][NP]
-  T* winv = reinterpret_cast<T*>(rowbuf + (size_t)XCfg<N>::NBUF * NP);  // 1/sinc^p, a = 0..N/2
+  C* fb = rowbuf + (size_t)XCfg<N>::NBUF * NP;  // phase-b factor per kx: fa e^{i pi (i+j+l)/N}
+  T* winv = reinterpret_cast<T*>(fb + N);   // 1/sinc^p, a = 0..N/2
   T* fa = winv + (N / 2 + 2);               // phase-a factor per kx
-  T* fidx = fa + N;                         // signed frequency index of storage position, as T
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
-  for (int i = tid; i < N; i += blockDim.x) {
-    tw[i] = tw_g[i];
-    const T a = T(M_PI) * T(i - N / 2) / T(N);
-    phs[i] = cmk(cos(a), sin(a));
-  }
+  for (int i = tid; i < N; i += blockDim.x) tw[i] = tw_g[i];
   for (int i = tid; i <= N / 2; i += blockDim.x) winv[i] = T(1) / sinc_pow<T>(T(M_PI) * T(i) / T(N), P.assign);
-  for (int i = tid; i < N; i += blockDim.x) fidx[i] = T(i < N / 2 ? i : i - N);
   __syncthreads();
   double* mypart = part + ((size_t)blockIdx.x * NW + warp) * P.nbins * P.nsum;
   const int nrows = (N / 2) * N;
@@ -413,8 +457,17 @@ k_fft_x_contract(const cplx<T>* __restrict__ half, const ContractParams P, const
       const int i = kx < N / 2 ? kx : kx - N;
       const int ai = i < 0 ? -i : i, aj = jy < 0 ? -jy : jy;
       fa[kx] = half_or_one * winv[ai] * winv[aj] * winv[kz];
+      {
+        // interlacing phase e^{i pi (i + j + l)/N}, the argument reduced to (-1, 1] half turns
+        int m = i + jy + kz;
+        m = ((m % (2 * N)) + 2 * N) % (2 * N);
+        if (m > N) m -= 2 * N;
+        T sn, cs;
+        sincospi_t(T(m) / T(N), &sn, &cs);
+        fb[kx] = cmk(cs * fa[kx], sn * fa[kx]);
+      }
       if (P.ny > 0) {
-        const T fi = fidx[kx], fj = fidx[ky], fk = fidx[kz];
+        const T fi = T(i), fj = T(jy), fk = T(kz);
         const T r2 = fi * fi + fj * fj + fk * fk;
         const T inv = r2 > T(0) ? rsqrt(r2) : T(0);
         const T ux = fi * inv, uy = fj * inv, uz = r2 > T(0) ? fk * inv : T(1);
@@ -427,7 +480,6 @@ k_fft_x_contract(const cplx<T>* __restrict__ half, const ContractParams P, const
       for (int q = 0; q < G * P.nacc; ++q) facc[(size_t)q * N + kx] = cmk(T(0), T(0));
     }
     __syncthreads();
-    const C phyz = cmul(phs[jy + N / 2], phs[kz + N / 2]);
     C v[8], vn[8];
     const size_t fstride = (size_t)(N / 2) * N * N;
     const size_t roff = ((size_t)kz * N + ky) * N;
@@ -457,16 +509,12 @@ k_fft_x_contract(const cplx<T>* __restrict__ half, const ContractParams P, const
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           const int kx = t + q * TPF;
-          T w = coef_scale<T>(c) * fa[kx];
+          T w = coef_scale<T>(c);
           if (c.yidx >= 0) {
             const C y = ytab[(size_t)c.yidx * N + kx];
             w *= (c.part == PART_RE ? y.x : y.y);
           }
-          C a = cscale(v[q], w);
-          if (c.phase) {
-            const int i = kx < N / 2 ? kx : kx - N;
-            a = cmul(a, cmul(phs[i + N / 2], phyz));
-          }
+          const C a = c.phase ? cmul(v[q], cscale(fb[kx], w)) : cscale(v[q], w * fa[kx]);
           acc[kx] = cadd(acc[kx], a);
         }
       }
@@ -474,7 +522,7 @@ k_fft_x_contract(const cplx<T>* __restrict__ half, const ContractParams P, const
       for (int q = 0; q < 8; ++q) v[q] = vn[q];
     }
     __syncthreads();
-    const T fjy = fidx[(jy + N) % N], fkz = fidx[kz];
+    const T fjy = T(jy), fkz = T(kz);
     for (int jb = warp * 32; jb < N; jb += blockDim.x) {
       const int j = jb + lane;
       const int i = j < N / 2 ? j : j - N;
@@ -492,7 +540,7 @@ k_fft_x_contract(const cplx<T>* __restrict__ half, const ContractParams P, const
           if (P.nacc > 1) F2 = cadd(F2, fg[N]);
           if (P.nacc > 2) F4 = cadd(F4, fg[2 * N]);
         }
-        const T fi = fidx[j];
+        const T fi = T(i);
         const T kk = sqrt(fi * fi + fjy * fjy + fkz * fkz);
         if (P.global_los) {
           const T mu = (fi * T(P.los[0]) + fjy * T(P.los[1]) + fkz * T(P.los[2])) / kk;
@@ -713,7 +761,16 @@ npc_status fwd_impl(npc_ctx* ctx, const PowerPlan& plan, const Geom& g, const vo
     const size_t smem = sizeof(C) * (N + N * TX) + sizeof(T) * 2 * N * TX;
     dim3 grid(N / TX, N);
     const int nstd = mesh_b ? std_pairs(plan.fl) : 0;
-    if (nstd > 0) {
+    const bool single = !mesh_b && plan.fl.nf == 1 && plan.fl.f[0].part == PART_ONE && plan.fl.f[0].phase == 0;
+    if (single) {
+      constexpr int STX = SingleCfg<N>::TX;
+      static_assert(N % (2 * STX) == 0, "column pairs must tile the mesh");
+      const size_t ssmem = sizeof(C) * (N + N * STX);
+      auto kern = k_fwd_z_single<T, N>;
+      NPC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssmem));
+      kern<<<dim3(N / (2 * STX), N), SingleCfg<N>::THREADS, ssmem, ctx->stream>>>((const T*)mesh_a, (C*)half, tw,
+                                                                                   KZ);
+    } else if (nstd > 0) {
       auto kern = k_fwd_z_std<T, N>;
       NPC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       kern<<<grid, ColCfg<N>::THREADS, smem, ctx->stream>>>((const T*)mesh_a, (const T*)mesh_b, (C*)half, nstd, g,
@@ -791,9 +848,9 @@ npc_status contract_impl(npc_ctx* ctx, const PowerPlan& plan, const npc_mesh_spe
 
   constexpr int NP = row_pad_len<N>();
   constexpr int G = XCfg<N>::G;
-  const size_t smem = sizeof(C) * ((size_t)2 * N + (size_t)P.ny * N + (size_t)G * P.nacc * N +
-                                   (size_t)XCfg<N>::NBUF * NP) +
-                      sizeof(T) * (N / 2 + 2 + 2 * N);
+  const size_t smem = sizeof(C) * ((size_t)N + (size_t)P.ny * N + (size_t)G * P.nacc * N +
+                                   (size_t)XCfg<N>::NBUF * NP + N) +
+                      sizeof(T) * (N / 2 + 2 + N);
   auto kern = k_fft_x_contract<T, N>;
   NPC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
