@@ -207,41 +207,43 @@ struct ShellField {
   int64_t off2;   // offset in the y-pass output
 };
 
-// x rows: for every (kz <= Kmax, |ky| <= Kmax) row, every field whose K covers it.
-template <typename T, int N>
+// x rows: for every (kz <= Kmax, |ky| <= Kmax) row, every field whose K covers it.  The shells and
+// their triple products are band-limited, so they run on a grid of NS <= n points per axis (the
+// smallest with no aliasing of the closed triples); row kx' of the NS grid holds the integer
+// frequency i = kx' (kx' < NS/2) or kx' - NS, read from the n-grid spectrum X0.
+template <typename T, int NS>
 __global__ void __launch_bounds__(BT)
-k_shell_x(const cplx<T>* __restrict__ X0, int KZX, const ShellField* __restrict__ fields, int nfields, int Kmax,
-          const int16_t* __restrict__ tab, int n2cap, double lx, double ly, double lz, const cplx<T>* __restrict__ tw_g,
-          cplx<T>* __restrict__ T1) {
+k_shell_x(const cplx<T>* __restrict__ X0, int KZX, int nfine, const ShellField* __restrict__ fields, int nfields,
+          int Kmax, const int16_t* __restrict__ tab, int n2cap, double lx, double ly, double lz,
+          const cplx<T>* __restrict__ tw_g, cplx<T>* __restrict__ T1) {
   using C = cplx<T>;
-  constexpr int TPF = N / 8;
+  constexpr int TPF = NS / 8;
   constexpr int G = BT / TPF > 0 ? BT / TPF : 1;
-  constexpr int NP = row_pad_len<N>();
+  constexpr int NP = row_pad_len<NS>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
-  C* xrow = tw + N;                  // X_0 row
-  T* l2row = reinterpret_cast<T*>(xrow + N);   // L_2(mu) per kx
-  int* binrow = reinterpret_cast<int*>(l2row + N);  // bin per kx (-1 excluded), n2 per kx
-  int* n2row = binrow + N;
-  C* bufs = reinterpret_cast<C*>(n2row + N);   // G x NP
+  C* xrow = tw + NS;                  // X_0 row
+  T* l2row = reinterpret_cast<T*>(xrow + NS);   // L_2(mu) per kx
+  int* binrow = reinterpret_cast<int*>(l2row + NS);  // bin per kx (-1 excluded), n2 per kx
+  int* n2row = binrow + NS;
+  C* bufs = reinterpret_cast<C*>(n2row + NS);   // NBUF x NP
   const int tid = threadIdx.x;
-  for (int i = tid; i < N; i += blockDim.x) tw[i] = tw_g[i];
+  for (int i = tid; i < NS; i += blockDim.x) tw[i] = tw_g[i];
   const int g = tid / TPF, t = tid % TPF;
   const int nyr = 2 * Kmax + 1;
   const int nrows = (Kmax + 1) * nyr;
-  const size_t xstride = (size_t)KZX * N * N;
-  (void)xstride;
   __syncthreads();
   for (int r = blockIdx.x; r < nrows; r += gridDim.x) {
     const int kz = r / nyr;
     const int jy = r % nyr - Kmax;
-    const int ky = jy < 0 ? jy + N : jy;
+    const int ky = jy < 0 ? jy + nfine : jy;
     const int ay = jy < 0 ? -jy : jy;
-    for (int kx = tid; kx < N; kx += blockDim.x) {
-      const int i = kx < N / 2 ? kx : kx - N;
+    for (int kx = tid; kx < NS; kx += blockDim.x) {
+      const int i = kx < NS / 2 ? kx : kx - NS;
+      const int fx = i < 0 ? i + nfine : i;
       const int n2 = i * i + jy * jy + kz * kz;
-      const bool inrange = i != -N / 2 && jy != -N / 2 && n2 <= n2cap;
-      xrow[kx] = (inrange && kz < KZX) ? X0[((size_t)kz * N + ky) * N + kx] : cmk(T(0), T(0));
+      const bool inrange = i != -NS / 2 && i != -nfine / 2 && jy != -nfine / 2 && n2 <= n2cap;
+      xrow[kx] = (inrange && kz < KZX) ? X0[((size_t)kz * nfine + ky) * nfine + fx] : cmk(T(0), T(0));
       const T kk = sqrt(T(n2));
       const T mu = n2 > 0 ? (T(i) * T(lx) + T(jy) * T(ly) + T(kz) * T(lz)) / kk : T(0);
       l2row[kx] = T(1.5) * mu * mu - T(0.5);
@@ -272,9 +274,9 @@ k_shell_x(const cplx<T>* __restrict__ X0, int KZX, const ShellField* __restrict_
         }
         v[q] = a;
       }
-      fft_block<N, +1>(v, t, tw, RowView<C>{bufs + (size_t)g * NP}, RowSync<N, BT>::make(g));
+      fft_block<NS, +1>(v, t, tw, RowView<C>{bufs + (size_t)g * NP}, RowSync<NS, BT>::make(g));
       if (live) {
-        C* dst = T1 + sf.off1 + ((size_t)kz * (2 * sf.K + 1) + (jy + sf.K)) * N;
+        C* dst = T1 + sf.off1 + ((size_t)kz * (2 * sf.K + 1) + (jy + sf.K)) * NS;
 #pragma unroll
         for (int q = 0; q < 8; ++q) dst[t + q * TPF] = v[q];
       }
@@ -739,6 +741,85 @@ Tri make_triangles(const npc_kbins& kb) {
   return T;
 }
 
+// the smallest compiled transform length >= need (and <= n; float64 up to 256)
+int shell_grid_size(int need, int n, bool fp64) {
+  static const int sizes[] = {16, 32, 48, 64, 96, 128, 192, 256, 512};
+  for (int s : sizes) {
+    if (s > n || (fp64 && s > 256)) break;
+    if (s >= need) return s;
+  }
+  return n;
+}
+
+struct ShellLaunch {
+  const void* X;
+  int KZX, nfine;
+  const ShellField* fields;
+  int nfield, Kmax;
+  const int16_t* tab;
+  int n2cap;
+  double l[3];
+  const int* plane_f;
+  const int* plane_kz;
+  int nplanes;
+  const int *za, *zb, *oa, *ob;
+  int nzp;
+};
+
+// the three shell passes on the NS grid
+template <typename T, int NS>
+npc_status shell_passes(npc_ctx* ctx, const ShellLaunch& sl, cplx<T>* T1, cplx<T>* T2, T* R) {
+  using C = cplx<T>;
+  const void* twp;
+  NPC_TRY(get_twiddles(ctx, NS, sizeof(T) == 8 ? NPC_PREC_FP64 : NPC_PREC_MIXED, &twp));
+  const C* tw = (const C*)twp;
+  {
+    const size_t smem = sizeof(C) * (2 * NS + (size_t)RowGroups<NS, BT>::NBUF * row_pad_len<NS>()) +
+                        sizeof(T) * NS + sizeof(int) * 2 * NS;
+    auto kern = k_shell_x<T, NS>;
+    NPC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int nrows = (sl.Kmax + 1) * (2 * sl.Kmax + 1);
+    kern<<<std::min(nrows, ctx->num_sms * 4), BT, smem, ctx->stream>>>(
+        (const C*)sl.X, sl.KZX, sl.nfine, sl.fields, sl.nfield, sl.Kmax, sl.tab, sl.n2cap, sl.l[0], sl.l[1], sl.l[2],
+        tw, T1);
+    NPC_LAUNCH(ctx);
+  }
+  constexpr int TX = BCol<NS>::TX;
+  const size_t smem = sizeof(C) * (NS + (size_t)NS * TX);
+  auto ky = k_shell_y<T, NS>;
+  NPC_CUDA(ctx, cudaFuncSetAttribute(ky, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  for (int p0 = 0; p0 < sl.nplanes; p0 += 65535) {
+    const int np_ = std::min(65535, sl.nplanes - p0);
+    ky<<<dim3(NS / TX, np_), BCol<NS>::THREADS, smem, ctx->stream>>>(T1, sl.fields, sl.plane_f + p0,
+                                                                     sl.plane_kz + p0, tw, T2);
+    NPC_LAUNCH(ctx);
+  }
+  auto kz = k_shell_z<T, NS>;
+  NPC_CUDA(ctx, cudaFuncSetAttribute(kz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kz<<<dim3(NS / TX, NS, sl.nzp), BCol<NS>::THREADS, smem, ctx->stream>>>(T2, sl.fields, sl.za, sl.zb, sl.oa, sl.ob,
+                                                                          tw, R);
+  NPC_LAUNCH(ctx);
+  return NPC_OK;
+}
+
+template <typename T>
+npc_status shell_dispatch(npc_ctx* ctx, int NS, const ShellLaunch& sl, cplx<T>* T1, cplx<T>* T2, T* R) {
+  switch (NS) {
+    case 16: return shell_passes<T, 16>(ctx, sl, T1, T2, R);
+    case 32: return shell_passes<T, 32>(ctx, sl, T1, T2, R);
+    case 48: return shell_passes<T, 48>(ctx, sl, T1, T2, R);
+    case 64: return shell_passes<T, 64>(ctx, sl, T1, T2, R);
+    case 96: return shell_passes<T, 96>(ctx, sl, T1, T2, R);
+    case 128: return shell_passes<T, 128>(ctx, sl, T1, T2, R);
+    case 192: return shell_passes<T, 192>(ctx, sl, T1, T2, R);
+    case 256: return shell_passes<T, 256>(ctx, sl, T1, T2, R);
+  }
+  if constexpr (sizeof(T) == 4) {
+    if (NS == 512) return shell_passes<T, 512>(ctx, sl, T1, T2, R);
+  }
+  return set_err(ctx, NPC_ERR_UNSUPPORTED, "shell grid %d not supported at this precision", NS);
+}
+
 template <typename T, int N>
 npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb, int scoc_mask, int tripo_mask,
                        int shot, const DevCatalog& d, const DevCatalog* r, double* sc, double* dev_out,
@@ -858,6 +939,18 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
   // 4. shell fields
   const bool want2 = (scoc_mask & 4) != 0;
   const bool wantG0 = (tripo_mask & 1) != 0, wantG2 = (tripo_mask & 4) != 0;
+  // grid of the shell fields and triple products: shells reach |q_i| <= K and the full fields
+  // |q_i| <= K2, so a closed triple sums to at most 3K (2K + K2 with the compressed estimator) per
+  // axis; any grid of more points has no aliasing and gives the same sums up to (n/NS)^3, which
+  // cancels in every normalised result (cell counts are those of the NS grid)
+  // exact radii: shell modes (|q| < k_max) have integer components <= Ks, full-field modes
+  // (|q|^2 <= n2cap) components <= KG
+  const int Ks = std::max(1, (int)std::floor(kmax / kf));
+  const int KG = std::max(1, std::min((int)std::floor(std::sqrt((double)n2cap)), N / 2 - 1));  // no Nyquist
+  const int Kshell = (wantG0 || wantG2) ? std::max(Ks, KG) : Ks;
+  const int need_ns = std::max((wantG0 || wantG2) ? 2 * Ks + KG + 1 : 3 * Ks + 1, 2 * Kshell + 1);
+  const int NS = shell_grid_size(need_ns, N, sizeof(T) == 8);
+  const size_t ncs = (size_t)NS * NS * NS;
   // triangle-count cache keyed by geometry and bins
   std::vector<char> ntkey(sizeof(int) + 3 * sizeof(double));
   {
@@ -867,6 +960,8 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
     std::memcpy(ntkey.data() + sizeof(int), a, 3 * sizeof(double));
     ntkey.push_back((char)nb);
     ntkey.push_back((char)sizeof(T));   // float and float64 shell fields give different rounding
+    const char* nsb = reinterpret_cast<const char*>(&NS);
+    ntkey.insert(ntkey.end(), nsb, nsb + sizeof(int));
   }
   const Tri tr = make_triangles(kb);
   const int ntri = (int)tr.tri.size() / 3, npair = (int)tr.pij.size();
@@ -882,23 +977,23 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
     f.src = (int8_t)src; f.mult = (int8_t)mult; f.bin = (int16_t)bin; f.K = Kf;
     fl.push_back(f);
   };
-  for (int b = 0; b < nb; ++b) add(0, 0, b, K);                  // F0_b: R index b
-  if (want2) for (int b = 0; b < nb; ++b) add(0, 1, b, K);       // F2_b: R index nb + b
+  for (int b = 0; b < nb; ++b) add(0, 0, b, Ks);                 // F0_b: R index b
+  if (want2) for (int b = 0; b < nb; ++b) add(0, 1, b, Ks);      // F2_b: R index nb + b
   const int iF2 = want2 ? nb : -1;
   const int iI = (int)fl.size();
-  if (need_nt) for (int b = 0; b < nb; ++b) add(1, 0, b, K);     // I_b
+  if (need_nt) for (int b = 0; b < nb; ++b) add(1, 0, b, Ks);    // I_b
   const int iG = (int)fl.size();
   int ng = 0;
-  if (wantG0) { add(0, 0, -1, K2); ng++; }
-  if (wantG2) { add(0, 1, -1, K2); ng++; }
+  if (wantG0) { add(0, 0, -1, KG); ng++; }
+  if (wantG2) { add(0, 1, -1, KG); ng++; }
   const int nfield = (int)fl.size();
   int64_t o1 = 0, o2 = 0;
   std::vector<int> plane_f, plane_kz;
   for (int f = 0; f < nfield; ++f) {
     fl[f].off1 = o1;
     fl[f].off2 = o2;
-    o1 += (int64_t)(fl[f].K + 1) * (2 * fl[f].K + 1) * N;
-    o2 += (int64_t)(fl[f].K + 1) * N * N;
+    o1 += (int64_t)(fl[f].K + 1) * (2 * fl[f].K + 1) * NS;
+    o2 += (int64_t)(fl[f].K + 1) * NS * NS;
     for (int kz = 0; kz <= fl[f].K; ++kz) {
       plane_f.push_back(f);
       plane_kz.push_back(kz);
@@ -954,40 +1049,29 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
   T* R;
   NPC_TRY(ws_get(ctx, "bis.T1", sizeof(C) * std::max<int64_t>(o1, 1), (void**)&T1));
   NPC_TRY(ws_get(ctx, "bis.T2", sizeof(C) * std::max<int64_t>(o2, 1), (void**)&T2));
-  NPC_TRY(ws_get(ctx, "bis.R", sizeof(T) * ncell * nfield, (void**)&R));
+  NPC_TRY(ws_get(ctx, "bis.R", sizeof(T) * ncs * nfield, (void**)&R));
   const int16_t* tab_shell;
   NPC_TRY(get_bin_table(ctx, N, m.box, kb, &tab_shell, 2));
   {
-    constexpr int TPF = N / 8;
-    constexpr int G = BT / TPF > 0 ? BT / TPF : 1;
-    const size_t smem = sizeof(C) * (2 * N + (size_t)RowGroups<N, BT>::NBUF * row_pad_len<N>()) + sizeof(T) * N +
-                        sizeof(int) * 2 * N;
-    auto kern = k_shell_x<T, N>;
-    NPC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int Kmax = std::max(K, ng ? K2 : 0);
-    const int nrows = (Kmax + 1) * (2 * Kmax + 1);
-    kern<<<std::min(nrows, ctx->num_sms * 4), BT, smem, ctx->stream>>>(X, KZ, dfields, nfield, Kmax, tab_shell, n2cap,
-                                                                     l3[0], l3[1], l3[2], tw, T1);
-    NPC_LAUNCH(ctx);
-  }
-  {
-    constexpr int TX = BCol<N>::TX;
-    const size_t smem = sizeof(C) * (N + (size_t)N * TX);
-    auto ky = k_shell_y<T, N>;
-    NPC_CUDA(ctx, cudaFuncSetAttribute(ky, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int npl = (int)plane_f.size();
-    for (int p0 = 0; p0 < npl; p0 += 65535) {
-      const int np_ = std::min(65535, npl - p0);
-      ky<<<dim3(N / TX, np_), BCol<N>::THREADS, smem, ctx->stream>>>(
-          T1, dfields, (const int*)(dtab + t_pf) + p0, (const int*)(dtab + t_pk) + p0, tw, T2);
-      NPC_LAUNCH(ctx);
-    }
-    auto kz = k_shell_z<T, N>;
-    NPC_CUDA(ctx, cudaFuncSetAttribute(kz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kz<<<dim3(N / TX, N, nzp), BCol<N>::THREADS, smem, ctx->stream>>>(
-        T2, dfields, (const int*)(dtab + t_za), (const int*)(dtab + t_zb), (const int*)(dtab + t_oa),
-        (const int*)(dtab + t_ob), tw, R);
-    NPC_LAUNCH(ctx);
+    ShellLaunch sl{};
+    sl.X = X;
+    sl.KZX = KZ;
+    sl.nfine = N;
+    sl.fields = dfields;
+    sl.nfield = nfield;
+    sl.Kmax = Kshell;
+    sl.tab = tab_shell;
+    sl.n2cap = n2cap;
+    for (int a = 0; a < 3; ++a) sl.l[a] = l3[a];
+    sl.plane_f = (const int*)(dtab + t_pf);
+    sl.plane_kz = (const int*)(dtab + t_pk);
+    sl.nplanes = (int)plane_f.size();
+    sl.za = (const int*)(dtab + t_za);
+    sl.zb = (const int*)(dtab + t_zb);
+    sl.oa = (const int*)(dtab + t_oa);
+    sl.ob = (const int*)(dtab + t_ob);
+    sl.nzp = nzp;
+    NPC_TRY(shell_dispatch<T>(ctx, NS, sl, T1, T2, R));
   }
   NPC_TRY(stage_mark(ctx, "shell_fields"));
 
@@ -996,7 +1080,7 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
   auto setup = [&](TripleArgs& a, bool indicator) {
     a = TripleArgs{};
     a.npair = npair;
-    a.ncell = (int64_t)ncell;
+    a.ncell = (int64_t)ncs;
     a.nstage = 0;
     auto stage_of = [&](int field) {
       for (int q = 0; q < a.nstage; ++q)
@@ -1050,7 +1134,7 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
   };
   if (need_nt) {
     NPC_TRY(launch(tn));
-    k_nt_reduce<<<(npair * nb + 127) / 128, 128, 0, ctx->stream>>>(part, grid, npair, nb, nb, (double)ncell,
+    k_nt_reduce<<<(npair * nb + 127) / 128, 128, 0, ctx->stream>>>(part, grid, npair, nb, nb, (double)ncs,
                                                                   nt_sums);
     NPC_LAUNCH(ctx);
     ctx->host_cache_keys[ntname] = ntkey;
@@ -1075,7 +1159,7 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
   fa.nrows = ta.nrows;
   fa.ncol = ta.ncol;
   fa.has2 = want2 ? 1 : 0;
-  fa.ncell = (int64_t)ncell;
+  fa.ncell = (int64_t)ncs;
   fa.kmin = kb.kmin;
   fa.dk = kb.dk;
   k_bispec_finalize<<<std::max(1, (std::max(ntri, npair) + 127) / 128), 128, 0, ctx->stream>>>(
