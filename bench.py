@@ -123,6 +123,22 @@ def make_inputs(w, rank=0):
     return g, r, origin
 
 
+def active_row_fraction(w):
+    """Fraction of the half-spectrum rows (ky, kz) that hold a binned mode (ky^2 + kz^2 below the
+    largest bin edge in grid units); the others are neither stored by the y pass nor read by the
+    contraction."""
+    import math
+
+    n = w["n"]
+    r2 = ((w["kmin"] + w["nbins"] * w["dk"]) * w["box"] / (2 * math.pi)) ** 2
+    lim = math.floor(r2) + 1
+    act = 0
+    for kz in range(n // 2):
+        for jy in range(-n // 2, n // 2):
+            act += jy * jy + kz * kz <= lim
+    return act / ((n // 2) * n)
+
+
 def algorithmic_bytes(w, stage, nf):
     """Bytes each stage must move at least once (float32 meshes / complex64 half spectra)."""
     n = w["n"]
@@ -130,12 +146,13 @@ def algorithmic_bytes(w, stage, nf):
     half = 8 * (n // 2) * n * n  # one complex64 half spectrum = 4 n^3
     nph = 2 if w["interlace"] else 1
     ntot = w["n_gal"] + w["n_ran"]
+    act = active_row_fraction(w)
     if stage == "fft_z_weighted":
         return nph * mesh + nf * half
     if stage == "fft_y":
-        return 2 * nf * half
+        return nf * half * (1 + act)
     if stage == "fft_x_contract":
-        return nf * half
+        return nf * half * act
     tiles = nph * mesh * ((16 + 4) / 16) ** 3   # (bs+4)^3 tiles per bs^3 brick, per phase
     if stage == "paint_count":      # positions in, brick id + rank out
         return ntot * (12 + 8)

@@ -303,6 +303,14 @@ npc_status power_core(npc_ctx* ctx, const npc_mesh_spec& ms, const DevCatalog& d
   plan.assign = mesh->assign;
   const Geom g = make_geom(*mesh);
   for (int a = 0; a < 3; ++a) plan.los[a] = g.los[a];
+  {
+    // rows of the half spectrum that hold no binned mode need not be stored by the y pass (the
+    // contraction skips them): a binned mode has k_f |q| < kmin + nbins dk
+    const double kf = 2.0 * M_PI / mesh->box, kmax = bins->kmin + bins->nbins * bins->dk;
+    const double r2 = (kmax / kf) * (kmax / kf);
+    const double full = 3.0 * (n / 2) * (n / 2);
+    plan.row_n2max = r2 >= full ? 0 : (int)std::floor(r2) + 1;
+  }
   int need = (int)ell_mask | 1;
   if (modified_mask) need |= 1 | 4 | 16;
   FieldList& fl = plan.fl;

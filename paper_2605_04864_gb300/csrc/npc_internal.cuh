@@ -281,6 +281,7 @@ struct PowerPlan {
   double los[3];
   int assign;
   int kz_keep;          // forward passes keep kz < kz_keep (0: all, n/2)
+  int row_n2max;        // > 0: the y pass may skip rows (ky, kz) with ky^2 + kz^2 above it
 };
 
 // Catalogue -> P_l after validation, staging and the catalogue scalars `sc` (api.cu).

@@ -346,7 +346,8 @@ static int std_pairs(const FieldList& fl) {
 // tuning parameter (see tune_y_pass).
 template <typename T, int N, int DIR, int TX>
 __global__ void __launch_bounds__(TX * N / 8, (TX * N / 8 <= 512 ? 1536 / (TX * N / 8) : 1))
-k_fft_cols(cplx<T>* __restrict__ data, size_t plane_stride, int row_stride, const cplx<T>* __restrict__ tw_g) {
+k_fft_cols(cplx<T>* __restrict__ data, size_t plane_stride, int row_stride, const cplx<T>* __restrict__ tw_g,
+           int plane0, int kz_planes, int row_n2max) {
   using C = cplx<T>;
   constexpr int TPF = N / 8;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -361,8 +362,14 @@ k_fft_cols(cplx<T>* __restrict__ data, size_t plane_stride, int row_stride, cons
   for (int q = 0; q < 8; ++q) v[q] = base[(size_t)(t + q * TPF) * row_stride];
   __syncthreads();
   fft_block<N, DIR>(v, t, tw, ColView<C>{work + c, TX});
+  // rows (ky, kz) outside every k-bin are never read again: not stored (plane p holds kz = p % kz_planes)
+  const int kz = (plane0 + (int)blockIdx.y) % kz_planes;
 #pragma unroll
-  for (int q = 0; q < 8; ++q) base[(size_t)(t + q * TPF) * row_stride] = v[q];
+  for (int q = 0; q < 8; ++q) {
+    const int yi = t + q * TPF;
+    const int jy = yi < N / 2 ? yi : yi - N;
+    if (jy * jy + kz * kz <= row_n2max) base[(size_t)yi * row_stride] = v[q];
+  }
 }
 
 // Per stored real field: which F_l it feeds, its mesh phase and its k-space coefficient
@@ -389,6 +396,7 @@ struct ContractParams {
   int nacc;                     // F accumulators (1..3)
   int nphase;
   int nbins, nsum;
+  int row_n2max;                // rows (ky, kz) with ky^2 + kz^2 above this hold no binned mode
   int nell;
   int ell_list[3];
   int nll;
@@ -452,6 +460,7 @@ k_fft_x_contract(const cplx<T>* __restrict__ half, const ContractParams P, const
   for (int r = blockIdx.x; r < nrows; r += gridDim.x) {
     const int kz = r / N, ky = r % N;
     const int jy = ky < N / 2 ? ky : ky - N;
+    if (jy * jy + kz * kz > P.row_n2max) continue;   // block-uniform: the whole row is outside the bins
     // per-mode window/interlace factor and Y_lm(khat) table; clear the accumulators
     for (int kx = tid; kx < N; kx += blockDim.x) {
       const int i = kx < N / 2 ? kx : kx - N;
@@ -679,7 +688,7 @@ int ytx_for(const npc_ctx* ctx, int n, bool fp64) {
 }
 
 template <typename T, int N, int TX>
-npc_status y_pass_tx(npc_ctx* ctx, cplx<T>* data, int nplanes, const cplx<T>* tw) {
+npc_status y_pass_tx(npc_ctx* ctx, cplx<T>* data, int nplanes, const cplx<T>* tw, int kz_planes, int row_n2max) {
   using C = cplx<T>;
   if constexpr (!ytx_ok<N>(TX)) {
     return set_err(ctx, NPC_ERR_INVALID_ARG, "y pass: %d columns per CTA not valid at n = %d", TX, N);
@@ -689,7 +698,8 @@ npc_status y_pass_tx(npc_ctx* ctx, cplx<T>* data, int nplanes, const cplx<T>* tw
     NPC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     for (int p0 = 0; p0 < nplanes; p0 += 65535) {
       const int np = std::min(65535, nplanes - p0);
-      kern<<<dim3(N / TX, np), TX * N / 8, smem, ctx->stream>>>(data + (size_t)p0 * N * N, (size_t)N * N, N, tw);
+      kern<<<dim3(N / TX, np), TX * N / 8, smem, ctx->stream>>>(data + (size_t)p0 * N * N, (size_t)N * N, N, tw, p0,
+                                                                kz_planes, row_n2max);
       NPC_LAUNCH(ctx);
     }
     return NPC_OK;
@@ -697,12 +707,13 @@ npc_status y_pass_tx(npc_ctx* ctx, cplx<T>* data, int nplanes, const cplx<T>* tw
 }
 
 template <typename T, int N>
-npc_status y_pass(npc_ctx* ctx, cplx<T>* data, int nplanes, const cplx<T>* tw, int tx) {
+npc_status y_pass(npc_ctx* ctx, cplx<T>* data, int nplanes, const cplx<T>* tw, int tx, int kz_planes = 1,
+                  int row_n2max = 1 << 30) {
   switch (tx) {
-    case 4: return y_pass_tx<T, N, 4>(ctx, data, nplanes, tw);
-    case 8: return y_pass_tx<T, N, 8>(ctx, data, nplanes, tw);
-    case 16: return y_pass_tx<T, N, 16>(ctx, data, nplanes, tw);
-    case 32: return y_pass_tx<T, N, 32>(ctx, data, nplanes, tw);
+    case 4: return y_pass_tx<T, N, 4>(ctx, data, nplanes, tw, kz_planes, row_n2max);
+    case 8: return y_pass_tx<T, N, 8>(ctx, data, nplanes, tw, kz_planes, row_n2max);
+    case 16: return y_pass_tx<T, N, 16>(ctx, data, nplanes, tw, kz_planes, row_n2max);
+    case 32: return y_pass_tx<T, N, 32>(ctx, data, nplanes, tw, kz_planes, row_n2max);
   }
   return set_err(ctx, NPC_ERR_INVALID_ARG, "y pass: unsupported columns per CTA %d", tx);
 }
@@ -785,7 +796,8 @@ npc_status fwd_impl(npc_ctx* ctx, const PowerPlan& plan, const Geom& g, const vo
     NPC_TRY(stage_mark(ctx, "fft_z_weighted"));
   }
   // planes (f, kz) are contiguous N*N blocks; y rows have stride N
-  NPC_TRY((y_pass<T, N>(ctx, (C*)half, plan.fl.nf * KZ, tw, ytx_for(ctx, N, sizeof(T) == 8))));
+  NPC_TRY((y_pass<T, N>(ctx, (C*)half, plan.fl.nf * KZ, tw, ytx_for(ctx, N, sizeof(T) == 8), KZ,
+                        plan.row_n2max > 0 ? plan.row_n2max : (1 << 30))));
   NPC_TRY(stage_mark(ctx, "fft_y"));
   return NPC_OK;
 }
@@ -845,6 +857,12 @@ npc_status contract_impl(npc_ctx* ctx, const PowerPlan& plan, const npc_mesh_spe
   for (int a = 0; a < 3; ++a) P.los[a] = plan.los[a];
   P.assign = plan.assign;
   P.kf = 2.0 * M_PI / m.box;
+  {
+    // a mode is binned only if k_f |q| < kmin + nbins dk; its row has ky^2 + kz^2 <= |q|^2
+    const double kmax = kb.kmin + kb.nbins * kb.dk;
+    const double r2 = std::pow(kmax / P.kf, 2);
+    P.row_n2max = r2 >= 3.0 * (N / 2) * (N / 2) ? 3 * (N / 2) * (N / 2) : (int)std::floor(r2) + 1;
+  }
 
   constexpr int NP = row_pad_len<N>();
   constexpr int G = XCfg<N>::G;
