@@ -397,30 +397,50 @@ k_fold(const T* __restrict__ tiles, PaintGeo g, int nphase, const double* __rest
   if (ly <= 2) { by[ny] = nbm[1]; ty[ny] = ly + BS + 1; ++ny; }
   by[ny] = B[1]; ty[ny] = ly + 1; ++ny;
   if (ly == BS - 1) { by[ny] = nbp[1]; ty[ny] = 0; ++ny; }
-  // per (iy, ix) option: pointer into the tile of the brick in the same z layer
+  // per (iy, ix) option (2 x 2 slots, slot valid when iy < ny and ix < nx): pointer into the tile
+  // of the brick in the same z layer; invalid slots hold a valid address and are predicated off
   const size_t zstride = (size_t)nb * nb * nphase * TS3;   // between z layers of bricks
-  const T* p_yx[4];
-  int nyx = 0;
-  for (int iy = 0; iy < ny; ++iy)
-    for (int ix = 0; ix < nx; ++ix) {
-      const size_t brick = ((size_t)B[2] * nb + by[iy]) * nb + bx[ix];
-      p_yx[nyx++] = tiles + (brick * nphase + ph) * TS3 + ty[iy] * TS + tx[ix];
+  const T* p_yx[2][2];
+  bool ok[2][2];
+#pragma unroll
+  for (int iy = 0; iy < 2; ++iy)
+#pragma unroll
+    for (int ix = 0; ix < 2; ++ix) {
+      ok[iy][ix] = iy < ny && ix < nx;
+      const int yy = ok[iy][ix] ? iy : 0, xx = ok[iy][ix] ? ix : 0;
+      const size_t brick = ((size_t)B[2] * nb + by[yy]) * nb + bx[xx];
+      p_yx[iy][ix] = tiles + (brick * nphase + ph) * TS3 + ty[yy] * TS + tx[xx];
     }
   const ptrdiff_t dzm = (ptrdiff_t)(nbm[2] - B[2]) * (ptrdiff_t)zstride;   // to the lower z layer
   const ptrdiff_t dzp = (ptrdiff_t)(nbp[2] - B[2]) * (ptrdiff_t)zstride;   // to the upper z layer
   T* col = mesh + ((size_t)(B[2] * BS) * n + (B[1] * BS + ly)) * n + (B[0] * BS + lx);
+  // z cells 0..2 also take the lower z layer's tiles, cell BS-1 the upper one's; the loop is unrolled
+  // so that the independent loads of several cells are in flight together
+#pragma unroll
   for (int lz = 0; lz < BS; ++lz) {
     T v = T(0);
     if (lz <= 2) {
       const ptrdiff_t o = dzm + (ptrdiff_t)(lz + BS + 1) * TS * TS;
-      for (int k = 0; k < nyx; ++k) v += p_yx[k][o];
+#pragma unroll
+      for (int iy = 0; iy < 2; ++iy)
+#pragma unroll
+        for (int ix = 0; ix < 2; ++ix)
+          if (ok[iy][ix]) v += p_yx[iy][ix][o];
     }
     {
       const int o = (lz + 1) * TS * TS;
-      for (int k = 0; k < nyx; ++k) v += p_yx[k][o];
+#pragma unroll
+      for (int iy = 0; iy < 2; ++iy)
+#pragma unroll
+        for (int ix = 0; ix < 2; ++ix)
+          if (ok[iy][ix]) v += p_yx[iy][ix][o];
     }
     if (lz == BS - 1) {
-      for (int k = 0; k < nyx; ++k) v += p_yx[k][dzp];
+#pragma unroll
+      for (int iy = 0; iy < 2; ++iy)
+#pragma unroll
+        for (int ix = 0; ix < 2; ++ix)
+          if (ok[iy][ix]) v += p_yx[iy][ix][dzp];
     }
     col[(size_t)lz * n * n] = v - mean;
   }
