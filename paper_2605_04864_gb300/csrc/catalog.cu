@@ -289,10 +289,18 @@ __device__ __forceinline__ void axis_taps(T frac, uint32_t m8, int phase, int* i
 template <typename T> __device__ __forceinline__ long long to_fixed(T v);
 template <> __device__ __forceinline__ long long to_fixed<float>(float v) {
   const float a = fabsf(v);
-  const float hi = floorf(a * 2.3283064365386963e-10f);  // a / 2^32, exact
-  const float lo = fmaf(hi, -4294967296.0f, a);            // exact, < 2^32
-  const long long q = ((long long)__float2uint_rz(hi) << 32) + (long long)__float2uint_rn(lo);
-  return v < 0.0f ? -q : q;
+  const float hf = floorf(a * 2.3283064365386963e-10f);  // a / 2^32, exact
+  const float lf = fmaf(hf, -4294967296.0f, a);            // exact, < 2^32
+  uint32_t hi = __float2uint_rz(hf);
+  uint32_t lo = __float2uint_rn(lf);
+  if (lo == 0u && lf >= 4294967296.0f) { lo = 0u; hi += 1u; }   // lf rounds to 2^32 only at the top
+  if (v < 0.0f) {            // two's complement of (hi, lo) in 32-bit halves
+    lo = ~lo + 1u;
+    hi = ~hi + (lo == 0u ? 1u : 0u);
+  }
+  unsigned long long q;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(q) : "r"(lo), "r"(hi));
+  return (long long)q;
 }
 template <> __device__ __forceinline__ long long to_fixed<double>(double v) { return __double2ll_rn(v); }
 
@@ -450,7 +458,7 @@ template <typename P>
 npc_status paint_count(npc_ctx* ctx, const DevCatalog& c, const PaintGeo& g, int* count, int* brick,
                        int* rank) {
   if (c.n == 0) return NPC_OK;
-  const int blocks = (int)std::min<int64_t>((c.n + 255) / 256, (int64_t)ctx->num_sms * 16);
+  const int blocks = (int)std::min<int64_t>((c.n + 255) / 256, (int64_t)1 << 20);   // one object per thread
   k_brick_count<P><<<blocks, 256, 0, ctx->stream>>>((const P*)c.pos, c.n, g, count, brick, rank);
   NPC_LAUNCH(ctx);
   return NPC_OK;
@@ -461,7 +469,7 @@ npc_status paint_scatter(npc_ctx* ctx, const DevCatalog& c, int power, int coef_
                          const PaintGeo& g, const int* brick, const int* rank, const int* start, void* rec,
                          uint32_t* meta) {
   if (c.n == 0) return NPC_OK;
-  const int blocks = (int)std::min<int64_t>((c.n + 255) / 256, (int64_t)ctx->num_sms * 16);
+  const int blocks = (int)std::min<int64_t>((c.n + 255) / 256, (int64_t)1 << 20);   // one object per thread
   k_scatter<ASSIGN, P, R><<<blocks, 256, 0, ctx->stream>>>((const P*)c.pos, (const P*)c.w, c.n, power, coef_kind,
                                                            sc, g, brick, rank, start,
                                                            (typename RecOf<R>::type*)rec, meta);
