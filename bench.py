@@ -115,6 +115,30 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def rank_collectives(world, device):
+    """Barrier and max-over-ranks for replicas (one measurement per rank, no data-path exchange):
+    the timed region of every leg is bracketed by barriers and the slowest rank's time is reported."""
+    import torch
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    return barrier, max_over_ranks
+
+
+def replica_throughput(world, units_per_rank, max_seconds):
+    """Whole-job throughput of independent replicas: all ranks' units over the slowest rank's time."""
+    return world * units_per_rank / max_seconds
+
+
 def make_inputs(w, rank=0):
     from synthetic import make_survey_catalogs
 
@@ -378,7 +402,7 @@ def batch_leg(args, world, rank, barrier, max_over_ranks):
                        "n_ran_total": sum(m["n_ran"] for m in plan), "precision": w["precision"]}}
 
 
-def plain_gpu_power(gd, rd, origin, w, dev="cuda"):
+def plain_gpu_power(gd, rd, origin, w, dev="cuda", dtype=None):
     """The plain GPU form of the same measurement, timed beside the library: float64 throughout,
     cuFFT through torch.fft, painting with float64 atomics (index_add_), the Hand+17 estimator with
     all 2l+1 real spherical-harmonic fields per multipole (1 + 5 + 9 = 15 real transforms per
@@ -389,7 +413,7 @@ def plain_gpu_power(gd, rd, origin, w, dev="cuda"):
     import torch
 
     n, box, p = w["n"], w["box"], w["assign"]
-    f64 = torch.float64
+    f64 = dtype or torch.float64
     H = box / n
     pg, wg = gd.pos.to(f64), gd.w.to(f64)
     pr, wr, nr = rd.pos.to(f64), rd.w.to(f64), rd.nbar.to(f64)
@@ -468,7 +492,7 @@ def plain_gpu_power(gd, rd, origin, w, dev="cuda"):
             acc = acc * (4 * math.pi / (2 * l + 1))
             F[(ph, l)] = acc
         del mesh
-    phase = torch.exp(1j * math.pi * (KX + KY + KZ) / n)
+    phase = torch.exp(1j * math.pi * (KX + KY + KZ) / n).to(F[(0, 0)].dtype)
     Fl = {l: 0.5 * (F[(0, l)] + phase * F[(1, l)]) / W for l in (0, 2, 4)}
     # bins: half spectrum, kx = 0 and kx = n/2 planes counted once, Nyquist planes excluded
     wgt = torch.full_like(kk, 2.0)
@@ -528,15 +552,21 @@ def power_leg(args, w, world, local, rank, barrier, max_over_ranks):
     barrier()
     torch.cuda.synchronize()
     s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    marks = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     s.record()
-    for _ in range(args.steps):
+    marks[0].record()
+    for k in range(args.steps):
         step_dev()
+        marks[k + 1].record()
     e.record()
     torch.cuda.synchronize()
     barrier()
     clocks = clk.stop()
     ms = max_over_ranks(s.elapsed_time(e))
     ms_per_step = ms / args.steps
+    per_step = sorted(marks[k].elapsed_time(marks[k + 1]) for k in range(args.steps))
+    pct = lambda q: per_step[min(len(per_step) - 1, int(q * (len(per_step) - 1) + 0.5))]
+    step_stats = {"p10": pct(0.1), "median": pct(0.5), "p90": pct(0.9)}
     value = world * args.steps / (ms / 1e3)
 
     # --- per-stage device times (CUDA events recorded by the library on the same stream) ---
@@ -594,7 +624,7 @@ def power_leg(args, w, world, local, rank, barrier, max_over_ranks):
                        "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (catalogues 440 MB, meshes 2x537 MB, spectra 16 GB)"},
             "roofline": roofline, "stages_ms": stages, "e2e": e2e, "gpu_launches": launches * args.steps,
-            "clocks": clocks}
+            "clocks": clocks, "step_ms": step_stats}
     # the plain GPU form (float64 cuFFT, Hand+17 full-m fields, atomic painting) beside it
     if not args.no_plain:
         ours = out.cpu().numpy()
@@ -616,6 +646,20 @@ def power_leg(args, w, world, local, rank, barrier, max_over_ranks):
                              "method": "float64 torch.fft (cuFFT) Hand+17 with 2l+1 real-harmonic fields per l, "
                                        "float64 atomic painting",
                              "max_rel_diff_vs_ours": diff, "speedup_of_ours": value * plain_s / world}
+        del res
+        # the same plain form in float32 (second GPU baseline)
+        res, n0 = plain_gpu_power(gd, rd, origin, w, dtype=torch.float32)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(nrep):
+            res, n0 = plain_gpu_power(gd, rd, origin, w, dtype=torch.float32)
+        torch.cuda.synchronize()
+        plain32_s = (time.perf_counter() - t0) / nrep
+        diff32 = max(float((abs(ours[(2 + e) * nb:(3 + e) * nb] - res[l].double().cpu().numpy()) / scale).max())
+                     for e, l in enumerate((0, 2, 4)))
+        line["plain_gpu_f32"] = {"value": world / plain32_s, "unit": UNIT, "ms_per_step": plain32_s * 1e3,
+                                 "method": "the same plain form in float32 (cuFFT C2C/R2C float, float atomics)",
+                                 "max_rel_diff_vs_ours": diff32, "speedup_of_ours": value * plain32_s / world}
         del res
     del gd, rd, out
     torch.cuda.empty_cache()
@@ -662,16 +706,7 @@ def main():
 
         __graft_entry__.build()
 
-    def barrier():
-        if world > 1:
-            torch.distributed.barrier()
-
-    def max_over_ranks(v):
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+    barrier, max_over_ranks = rank_collectives(world, "cuda")
 
     line = {} if args.no_power else power_leg(args, w, world, local, rank, barrier, max_over_ranks)
     if not args.no_bispec:
