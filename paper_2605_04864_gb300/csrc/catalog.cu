@@ -284,23 +284,21 @@ __device__ __forceinline__ void axis_taps(T frac, uint32_t m8, int phase, int* i
   }
 }
 
-// Round to the nearest 64-bit integer (ties to even).  The float path splits |v| < 2^62 into
-// 2^32 * hi + lo with both parts exact in float and converts them with 32-bit instructions.
+// Round to the nearest 64-bit integer (ties to even).  The float path takes |v| < 2^43 (the tile
+// kernel's scale guarantees it) and needs no conversion instruction: hi = rn(v / 2^22) and the exact
+// remainder lo = v - 2^22 hi, both of magnitude <= 2^21, are rounded to integers by adding 1.5 * 2^23
+// (the float add rounds to nearest even, and the integer sits in the low mantissa bits); since
+// 2^22 hi is an even integer, 2^22 hi + rn(lo) = rn(v).
 template <typename T> __device__ __forceinline__ long long to_fixed(T v);
 template <> __device__ __forceinline__ long long to_fixed<float>(float v) {
-  const float a = fabsf(v);
-  const float hf = floorf(a * 2.3283064365386963e-10f);  // a / 2^32, exact
-  const float lf = fmaf(hf, -4294967296.0f, a);            // exact, < 2^32
-  uint32_t hi = __float2uint_rz(hf);
-  uint32_t lo = __float2uint_rn(lf);
-  if (lo == 0u && lf >= 4294967296.0f) { lo = 0u; hi += 1u; }   // lf rounds to 2^32 only at the top
-  if (v < 0.0f) {            // two's complement of (hi, lo) in 32-bit halves
-    lo = ~lo + 1u;
-    hi = ~hi + (lo == 0u ? 1u : 0u);
-  }
-  unsigned long long q;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(q) : "r"(lo), "r"(hi));
-  return (long long)q;
+  const float magic = 12582912.0f;                         // 1.5 * 2^23
+  const float th = v * 2.384185791015625e-07f + magic;     // rn(v 2^-22) + magic
+  const float hf = th - magic;                             // exact
+  const float lf = fmaf(hf, -4194304.0f, v);               // v - 2^22 hi, exact
+  const float tl = lf + magic;
+  const int hi = __float_as_int(th) - 0x4B400000;
+  const int lo = __float_as_int(tl) - 0x4B400000;
+  return (long long)hi * 4194304LL + (long long)lo;
 }
 template <> __device__ __forceinline__ long long to_fixed<double>(double v) { return __double2ll_rn(v); }
 
@@ -329,12 +327,25 @@ k_paint_brick(const typename RecOf<R>::type* __restrict__ rec, const uint32_t* _
   const double bound = (double)cnt * sc[maxw_slot];
   int ex = 0;
   if (bound > 0) frexp(bound, &ex);
-  const int e = 61 - ex;
+  int e = 61 - ex;
+  if constexpr (sizeof(T) == 4) {
+    // and every tap |w W| 2^e < 2^43, the range of the float conversion
+    int exw = 0;
+    if (sc[maxw_slot] > 0) frexp(sc[maxw_slot], &exw);
+    e = min(e, 43 - exw);
+  }
   const T scale = (T)ldexp(1.0, e);
   __syncthreads();
   const int beg = start[b];
   constexpr int NT = ASSIGN == 2 ? 2 : 3;
-  for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+  // NT adjacent lanes share one object, lane xt taking its x tap: the atomics of one instruction
+  // then hit runs of NT neighbouring cells instead of 32 scattered ones (fewer bank wavefronts)
+  constexpr int OPW = 32 / NT;   // objects per warp and pass
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const int xt = lane % NT, slot = lane / NT;
+  for (int k0 = warp * OPW; k0 < cnt; k0 += nwarp * OPW) {
+    const int k = k0 + slot;
+    if (slot >= OPW || k >= cnt) continue;
     const typename RecOf<R>::type r = rec[beg + k];
     int ix[NT], iy[NT], iz[NT];
     T wx[NT], wy[NT], wz[NT];
@@ -350,22 +361,22 @@ k_paint_brick(const typename RecOf<R>::type* __restrict__ rec, const uint32_t* _
       axis_taps<ASSIGN, T>((T)r.y, (m >> 8) & 255u, ph, iy, wy);
       axis_taps<ASSIGN, T>((T)r.z, (m >> 16) & 255u, ph, iz, wz);
     }
-    const T wgt = (T)r.w * scale;
+    T wxs = wx[0];
+    int ixs = ix[0];
+#pragma unroll
+    for (int a = 1; a < NT; ++a)
+      if (xt == a) { wxs = wx[a]; ixs = ix[a]; }
+    const T wgt = (T)r.w * scale * wxs;
 #pragma unroll
     for (int c = 0; c < NT; ++c) {
 #pragma unroll
       for (int bb = 0; bb < NT; ++bb) {
-        const T wzy = wgt * wz[c] * wy[bb];
-        const int rowoff = (iz[c] * g.ts + iy[bb]) * g.ts;
-#pragma unroll
-        for (int aa = 0; aa < NT; ++aa) {
-          const long long q = to_fixed<T>(wzy * wx[aa]);
-          // taps stay inside the tile by construction; the guard only protects shared memory
-          if ((unsigned)iz[c] < (unsigned)g.ts && (unsigned)iy[bb] < (unsigned)g.ts &&
-              (unsigned)ix[aa] < (unsigned)g.ts)
-            atomicAdd(reinterpret_cast<unsigned long long*>(acc + rowoff + ix[aa]),
-                      static_cast<unsigned long long>(q));
-        }
+        // tap value (w 2^e W_x) W_z W_y, formed once per tap in a fixed order
+        const long long q = to_fixed<T>(wgt * wz[c] * wy[bb]);
+        // taps stay inside the tile by construction; the guard only protects shared memory
+        if ((unsigned)iz[c] < (unsigned)g.ts && (unsigned)iy[bb] < (unsigned)g.ts && (unsigned)ixs < (unsigned)g.ts)
+          atomicAdd(reinterpret_cast<unsigned long long*>(acc + (iz[c] * g.ts + iy[bb]) * g.ts + ixs),
+                    static_cast<unsigned long long>(q));
       }
     }
   }

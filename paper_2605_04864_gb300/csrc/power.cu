@@ -179,19 +179,24 @@ k_fwd_z_single(const T* __restrict__ mesh, cplx<T>* __restrict__ half, const cpl
 // a/b whose real and imaginary parts share one Y evaluation.  Pairs are a prefix of
 //   (0,0,0) (2,0,0) (2,1,1) (2,1,2) (2,2,1) (2,2,2) (4,0,0) (4,1,1) (4,1,2) ... (4,4,1) (4,4,2).
 // ---------------------------------------------------------------------------------------------
+// Polynomial factor Q_lm(uz) of Y_lm = norm_lm Q_lm(uz) (ux + i uy)^m, l <= 4.
+template <typename T, int L, int M>
+__device__ __forceinline__ T ylm_q(T uz) {
+  const T z2 = uz * uz;
+  if constexpr (L == 0) return T(1);
+  else if constexpr (L == 2 && M == 0) return T(1.5) * z2 - T(0.5);
+  else if constexpr (L == 2 && M == 1) return T(-3) * uz;
+  else if constexpr (L == 2 && M == 2) return T(3);
+  else if constexpr (L == 4 && M == 0) return (T(35) * z2 * z2 - T(30) * z2 + T(3)) * T(0.125);
+  else if constexpr (L == 4 && M == 1) return T(-2.5) * uz * (T(7) * z2 - T(3));
+  else if constexpr (L == 4 && M == 2) return T(7.5) * (T(7) * z2 - T(1));
+  else if constexpr (L == 4 && M == 3) return T(-105) * uz;
+  else return T(105);
+}
+
 template <typename T, int L, int M>
 __device__ __forceinline__ void ylm_ct(T ux, T uy, T uz, const YNorm& nrm, T& re, T& im) {
-  const T z2 = uz * uz;
-  T q;
-  if constexpr (L == 0) q = T(1);
-  else if constexpr (L == 2 && M == 0) q = T(1.5) * z2 - T(0.5);
-  else if constexpr (L == 2 && M == 1) q = T(-3) * uz;
-  else if constexpr (L == 2 && M == 2) q = T(3);
-  else if constexpr (L == 4 && M == 0) q = (T(35) * z2 * z2 - T(30) * z2 + T(3)) * T(0.125);
-  else if constexpr (L == 4 && M == 1) q = T(-2.5) * uz * (T(7) * z2 - T(3));
-  else if constexpr (L == 4 && M == 2) q = T(7.5) * (T(7) * z2 - T(1));
-  else if constexpr (L == 4 && M == 3) q = T(-105) * uz;
-  else q = T(105);
+  const T q = ylm_q<T, L, M>(uz);
   T pr = T(1), pi = T(0);
 #pragma unroll
   for (int j = 0; j < M; ++j) {
@@ -386,15 +391,21 @@ template <typename T> __device__ __forceinline__ T coef_scale(const FieldCoef& c
 template <> __device__ __forceinline__ float coef_scale<float>(const FieldCoef& c) { return c.scale_f; }
 template <> __device__ __forceinline__ double coef_scale<double>(const FieldCoef& c) { return c.scale_d; }
 
+// Row Y table: Y_lm(khat) in the fixed order (2,0) (2,1) (2,2) (4,0) (4,1) (4,2) (4,3) (4,4).
 constexpr int MAX_YTAB = 8;
+__host__ __device__ constexpr int ytab_index(int l, int m) { return l == 2 ? m : 3 + m; }
+// Field slots of the x pass: slot[r * G + g] is the field row group g transforms in round r.
+constexpr int MAX_SLOTS = 256;
 
 struct ContractParams {
   int nf;
   FieldCoef fc[NPC_MAX_FIELDS];
-  int ny;                       // Y_lm(khat) per row, l > 0
-  int8_t yl[MAX_YTAB], ym[MAX_YTAB];
+  int ny;                       // Y table rows: 0, 3 (l = 2) or 8 (l = 2 and 4)
   int nacc;                     // F accumulators (1..3)
   int nphase;
+  int nrounds;                  // rounds of G field rows
+  int phase_pure;               // 1: every group sees one mesh phase only (group parity when nphase = 2)
+  int8_t slot[MAX_SLOTS];       // field per (round, group), -1 for none
   int nbins, nsum;
   int row_n2max;                // rows (ky, kz) with ky^2 + kz^2 above this hold no binned mode
   int nell;
@@ -480,28 +491,35 @@ k_fft_x_contract(const cplx<T>* __restrict__ half, const ContractParams P, const
         const T r2 = fi * fi + fj * fj + fk * fk;
         const T inv = r2 > T(0) ? rsqrt(r2) : T(0);
         const T ux = fi * inv, uy = fj * inv, uz = r2 > T(0) ? fk * inv : T(1);
-        for (int j = 0; j < P.ny; ++j) {
-          T re, im;
-          ylm_fast<T>(P.yl[j], P.ym[j], ux, uy, uz, nrm, re, im);
-          ytab[(size_t)j * N + kx] = cmk(re, im);
+        T re, im;
+        ylm_ct<T, 2, 0>(ux, uy, uz, nrm, re, im); ytab[0 * N + kx] = cmk(re, im);
+        ylm_ct<T, 2, 1>(ux, uy, uz, nrm, re, im); ytab[1 * N + kx] = cmk(re, im);
+        ylm_ct<T, 2, 2>(ux, uy, uz, nrm, re, im); ytab[2 * N + kx] = cmk(re, im);
+        if (P.ny > 3) {
+          ylm_ct<T, 4, 0>(ux, uy, uz, nrm, re, im); ytab[3 * N + kx] = cmk(re, im);
+          ylm_ct<T, 4, 1>(ux, uy, uz, nrm, re, im); ytab[4 * N + kx] = cmk(re, im);
+          ylm_ct<T, 4, 2>(ux, uy, uz, nrm, re, im); ytab[5 * N + kx] = cmk(re, im);
+          ylm_ct<T, 4, 3>(ux, uy, uz, nrm, re, im); ytab[6 * N + kx] = cmk(re, im);
+          ylm_ct<T, 4, 4>(ux, uy, uz, nrm, re, im); ytab[7 * N + kx] = cmk(re, im);
         }
       }
       for (int q = 0; q < G * P.nacc; ++q) facc[(size_t)q * N + kx] = cmk(T(0), T(0));
     }
     __syncthreads();
-    C v[8], vn[8];
+    C v[8], vn[8], racc[8];
+    int cur = -1;   // accumulator held in racc
     const size_t fstride = (size_t)(N / 2) * N * N;
     const size_t roff = ((size_t)kz * N + ky) * N;
-    if (ingroup && g < P.nf) {
-      const C* src = half + (size_t)g * fstride + roff;
+    int f = ingroup ? P.slot[g] : -1;
+    if (f >= 0) {
+      const C* src = half + (size_t)f * fstride + roff;
 #pragma unroll
       for (int q = 0; q < 8; ++q) v[q] = src[t + q * TPF];
     }
-    for (int f0 = 0; f0 < P.nf; f0 += G) {
-      const int f = f0 + g;
-      const bool live = ingroup && f < P.nf;
-      const int fn = f + G;
-      if (ingroup && fn < P.nf) {
+    for (int rd = 0; rd < P.nrounds; ++rd) {
+      const bool live = f >= 0;
+      const int fn = (ingroup && rd + 1 < P.nrounds) ? P.slot[(rd + 1) * G + g] : -1;
+      if (fn >= 0) {
         const C* src = half + (size_t)fn * fstride + roff;
 #pragma unroll
         for (int q = 0; q < 8; ++q) vn[q] = src[t + q * TPF];
@@ -514,7 +532,16 @@ k_fft_x_contract(const cplx<T>* __restrict__ half, const ContractParams P, const
                        RowSync<N, CONTRACT_THREADS>::make(g));
       if (live) {
         const FieldCoef c = P.fc[f];
-        C* acc = facc + ((size_t)g * P.nacc + c.acc) * N;
+        if (c.acc != cur) {   // a group's fields come in accumulator order: flush once per change
+          if (cur >= 0) {
+            C* acc = facc + ((size_t)g * P.nacc + cur) * N;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) acc[t + q * TPF] = cadd(acc[t + q * TPF], racc[q]);
+          }
+          cur = c.acc;
+#pragma unroll
+          for (int q = 0; q < 8; ++q) racc[q] = cmk(T(0), T(0));
+        }
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           const int kx = t + q * TPF;
@@ -523,12 +550,20 @@ k_fft_x_contract(const cplx<T>* __restrict__ half, const ContractParams P, const
             const C y = ytab[(size_t)c.yidx * N + kx];
             w *= (c.part == PART_RE ? y.x : y.y);
           }
-          const C a = c.phase ? cmul(v[q], cscale(fb[kx], w)) : cscale(v[q], w * fa[kx]);
-          acc[kx] = cadd(acc[kx], a);
+          // phase-pure groups apply the window and interlacing factors once per mode, at binning
+          const C a = P.phase_pure ? cscale(v[q], w)
+                                   : (c.phase ? cmul(v[q], cscale(fb[kx], w)) : cscale(v[q], w * fa[kx]));
+          racc[q] = cadd(racc[q], a);
         }
       }
 #pragma unroll
       for (int q = 0; q < 8; ++q) v[q] = vn[q];
+      f = fn;
+    }
+    if (cur >= 0) {
+      C* acc = facc + ((size_t)g * P.nacc + cur) * N;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc[t + q * TPF] = cadd(acc[t + q * TPF], racc[q]);
     }
     __syncthreads();
     const T fjy = T(jy), fkz = T(kz);
@@ -543,11 +578,39 @@ k_fft_x_contract(const cplx<T>* __restrict__ half, const ContractParams P, const
       if (bin >= 0) {
         const T wgt = kz > 0 ? T(2) : T(1);
         C F0 = cmk(T(0), T(0)), F2 = cmk(T(0), T(0)), F4 = cmk(T(0), T(0));
-        for (int gg = 0; gg < G; ++gg) {
-          const C* fg = facc + (size_t)gg * P.nacc * N + j;
-          F0 = cadd(F0, fg[0]);
-          if (P.nacc > 1) F2 = cadd(F2, fg[N]);
-          if (P.nacc > 2) F4 = cadd(F4, fg[2 * N]);
+        if (P.phase_pure) {
+          // groups of phase a (even g, or all with one phase) and of phase b (odd g), summed in g order
+          C B0 = cmk(T(0), T(0)), B2 = cmk(T(0), T(0)), B4 = cmk(T(0), T(0));
+          const int gstep = P.nphase == 2 ? 2 : 1;
+          for (int gg = 0; gg < G; gg += gstep) {
+            const C* fg = facc + (size_t)gg * P.nacc * N + j;
+            F0 = cadd(F0, fg[0]);
+            if (P.nacc > 1) F2 = cadd(F2, fg[N]);
+            if (P.nacc > 2) F4 = cadd(F4, fg[2 * N]);
+          }
+          const T faj = fa[j];
+          F0 = cscale(F0, faj);
+          F2 = cscale(F2, faj);
+          F4 = cscale(F4, faj);
+          if (P.nphase == 2) {
+            for (int gg = 1; gg < G; gg += 2) {
+              const C* fg = facc + (size_t)gg * P.nacc * N + j;
+              B0 = cadd(B0, fg[0]);
+              if (P.nacc > 1) B2 = cadd(B2, fg[N]);
+              if (P.nacc > 2) B4 = cadd(B4, fg[2 * N]);
+            }
+            const C fbj = fb[j];
+            F0 = cadd(F0, cmul(B0, fbj));
+            F2 = cadd(F2, cmul(B2, fbj));
+            F4 = cadd(F4, cmul(B4, fbj));
+          }
+        } else {
+          for (int gg = 0; gg < G; ++gg) {
+            const C* fg = facc + (size_t)gg * P.nacc * N + j;
+            F0 = cadd(F0, fg[0]);
+            if (P.nacc > 1) F2 = cadd(F2, fg[N]);
+            if (P.nacc > 2) F4 = cadd(F4, fg[2 * N]);
+          }
         }
         const T fi = T(i);
         const T kk = sqrt(fi * fi + fjy * fjy + fkz * fkz);
@@ -824,20 +887,47 @@ npc_status contract_impl(npc_ctx* ctx, const PowerPlan& plan, const npc_mesh_spe
     fc.scale_d = 1.0;
     fc.scale_f = 1.0f;
     if (c.part == PART_RE || c.part == PART_IM) {
-      int j = -1;
-      for (int q = 0; q < P.ny; ++q)
-        if (P.yl[q] == c.ell && P.ym[q] == c.m) j = q;
-      if (j < 0) {
-        if (P.ny >= MAX_YTAB) return set_err(ctx, NPC_ERR_UNSUPPORTED, "too many Y_lm fields");
-        j = P.ny++;
-        P.yl[j] = c.ell;
-        P.ym[j] = c.m;
-      }
-      fc.yidx = (int8_t)j;
+      if ((c.ell != 2 && c.ell != 4) || c.m < 0 || c.m > c.ell)
+        return set_err(ctx, NPC_ERR_UNSUPPORTED, "Y_%d%d field in the x pass", c.ell, c.m);
+      fc.yidx = (int8_t)ytab_index(c.ell, c.m);
+      P.ny = std::max(P.ny, c.ell == 4 ? 8 : 3);
       fc.scale_d = 4.0 * M_PI / (2 * c.ell + 1) * (c.m > 0 ? 2.0 : 1.0);
       fc.scale_f = (float)fc.scale_d;
     }
     P.fc[f] = fc;
+  }
+  {
+    // field slots: with two phases and an even number of row groups, even groups take the
+    // phase-a fields and odd groups the phase-b fields (in list order), so that a group's
+    // accumulators hold one phase and the window/interlacing factors are applied per mode
+    constexpr int G = XCfg<N>::G;
+    std::vector<int> ph[2];
+    for (int f = 0; f < plan.fl.nf; ++f) ph[plan.fl.f[f].phase ? 1 : 0].push_back(f);
+    P.phase_pure = (P.nphase == 1 || G % 2 == 0) ? 1 : 0;
+    if (P.nphase == 1 && !ph[1].empty()) return set_err(ctx, NPC_ERR_INVALID_ARG, "phase-b field without interlacing");
+    int nrounds;
+    if (P.phase_pure && P.nphase == 2) {
+      const int per = G / 2;
+      nrounds = (int)std::max((ph[0].size() + per - 1) / per, (ph[1].size() + per - 1) / per);
+    } else {
+      nrounds = (plan.fl.nf + G - 1) / G;
+    }
+    if ((size_t)nrounds * G > (size_t)MAX_SLOTS)
+      return set_err(ctx, NPC_ERR_UNSUPPORTED, "x pass: %d fields do not fit %d slots", plan.fl.nf, MAX_SLOTS);
+    P.nrounds = nrounds;
+    for (int r = 0; r < nrounds; ++r)
+      for (int g = 0; g < G; ++g) {
+        int f = -1;
+        if (P.phase_pure && P.nphase == 2) {
+          const size_t i = (size_t)r * (G / 2) + g / 2;
+          const std::vector<int>& l = ph[g & 1];
+          if (i < l.size()) f = l[i];
+        } else {
+          const int i = r * G + g;
+          if (i < plan.fl.nf) f = i;
+        }
+        P.slot[r * G + g] = (int8_t)f;
+      }
   }
   P.nbins = kb.nbins;
   P.nell = 0;
