@@ -193,7 +193,8 @@ def compressed_explicit(spec, meshes, kbins, prs, i33, ell):
 
 
 def bispectrum(spec, data, randoms, kbins, scoc_ells=(0, 2), tripo_ells=(0, 2), shot=True):
-    """Full oracle measurement (global line of sight): B_l, N_T, compressed B_l0l, shot noise."""
+    """Full oracle measurement (global line of sight): B_l, N_T, compressed B_l0l, shot noise
+    (analytic; shot="fft" adds the FFT-method shot noise of B_l as ``shot_B_fft``)."""
     from . import power as P
     from . import shot as S
 
@@ -214,6 +215,9 @@ def bispectrum(spec, data, randoms, kbins, scoc_ells=(0, 2), tripo_ells=(0, 2), 
         nf, _ = P.fields_plain(spec, nmeshes, [0])
         res["shot_B"], res["shot_BB"], res["shot_parts"] = S.analytic_shot_noise(
             spec, X0, nf[0], kbins, tri, prs, sc, scoc_ells, tripo_ells)
+        if shot == "fft":
+            res["shot_B_fft"] = S.fft_method_shot_noise(spec, X0, nf[0], kbins, tri, sc["I33"], sc["S3"],
+                                                        scoc_ells)
     return res
 
 

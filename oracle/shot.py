@@ -26,6 +26,20 @@ V_ring V_dot ~ 1/k3 derivation of Sec. 5.4.2 requires.
 Parity unpinned as an exact reference: these are thin-shell approximations (Sec. 5.3).  The tests
 check them statistically against Poisson catalogues (the subtracted monopole averages to zero and
 the raw monopole averages to the full shot noise) and check the g_l factors separately.
+
+FFT method (Sec. 5.4.2, the exact reference the paper evaluates with extra inverse transforms
+instead of the thin-shell integrals), Scoccimarro B_l with l on leg 1 and a global line of sight.
+Over the closed triplets q1 in b_i, q2 in b_j, q3 in b_k, q1 + q2 + q3 = 0:
+  T23 = sum L_l(mu1) X_0(q1) N_0^*(q1)     (legs 2, 3 from one object)
+  T12 = sum L_l(mu1) X_0(q3) N_0^*(q3)     (legs 1, 2 from one object)
+  T13 = sum L_l(mu1) X_0(q2) N_0^*(q2)     (legs 1, 3 from one object)
+  N_T^(l) = sum L_l(mu1)
+  N^(l)_fft(i,j,k) = (2l+1)/(I33 N_T) Re[T23 + T12 + T13 - 2 S N_T^(l)]
+Each two-object term contains the three-of-one-object part S N_T^(l) once; the pure term adds it
+back once, hence the -2.  ``fft_method_shot_noise`` enumerates the triplets (the definition written
+out; tiny meshes).  Pinned by the exact identity it must satisfy: for uncompensated fields of at
+most two objects every closed triplet draws two legs from one object, so the raw estimator equals
+N_fft; with three objects the difference is the sum over distinct triples (tests).
 """
 from __future__ import annotations
 
@@ -98,3 +112,49 @@ def analytic_shot_noise(spec, X0, N0, kbins, tri, prs, sc, scoc_ells, tripo_ells
                 out[t] = (2 * ell + 1) / i33 * v
             shot_BB[ell] = out
     return shot_B, shot_BB, parts
+
+
+def triplet_shot_terms(spec, X0, N0, kbins, tri, ell):
+    """Per triangle (i, j, k): explicit sums over the closed triplets of the FFT-method terms.
+
+    Returns dict of arrays nt (triplet count), ntl (sum of L_l(mu1)), t23, t12, t13 (complex)."""
+    from .bispec import _mode_lists
+
+    n = spec["n"]
+    kf = 2.0 * np.pi / spec["box"]
+    d = np.asarray(spec["los_dir"], dtype=np.float64)
+    d = d / np.linalg.norm(d)
+    b, lists = _mode_lists(spec, kbins)
+    out = {k: [] for k in ("nt", "ntl", "t23", "t12", "t13")}
+    for i, j, k in tri:
+        q1 = lists[i]
+        q2 = lists[j]
+        q3 = -(q1[:, None, :] + q2[None, :, :])
+        idx3 = q3 % n
+        inb = b[idx3[..., 0], idx3[..., 1], idx3[..., 2]] == k
+        inb &= np.all(np.abs(q3) < n // 2, axis=-1)
+        i1 = q1 % n
+        i2 = q2 % n
+        kk1 = np.sqrt(np.sum((kf * q1) ** 2, axis=1))
+        mu1 = (kf * q1) @ d / kk1
+        l1 = H.legendre(ell, mu1)[:, None] * np.ones(q3.shape[:2])
+        xn1 = (X0 * np.conj(N0))[i1[:, 0], i1[:, 1], i1[:, 2]][:, None]
+        xn2 = (X0 * np.conj(N0))[i2[:, 0], i2[:, 1], i2[:, 2]][None, :]
+        xn3 = (X0 * np.conj(N0))[idx3[..., 0], idx3[..., 1], idx3[..., 2]]
+        out["nt"].append(int(np.sum(inb)))
+        out["ntl"].append(np.sum(np.where(inb, l1, 0.0)))
+        out["t23"].append(np.sum(np.where(inb, l1 * xn1, 0.0)))
+        out["t12"].append(np.sum(np.where(inb, l1 * xn3, 0.0)))
+        out["t13"].append(np.sum(np.where(inb, l1 * xn2, 0.0)))
+    return {k: np.array(v) for k, v in out.items()}
+
+
+def fft_method_shot_noise(spec, X0, N0, kbins, tri, i33, s3, ells):
+    """N^(l)_fft for every triangle and each l in ells (global line of sight)."""
+    res = {}
+    for ell in ells:
+        t = triplet_shot_terms(spec, X0, N0, kbins, tri, ell)
+        tot = np.real(t["t23"] + t["t12"] + t["t13"]) - 2.0 * s3 * t["ntl"]
+        with np.errstate(invalid="ignore", divide="ignore"):
+            res[ell] = np.where(t["nt"] > 0, (2 * ell + 1) * tot / (i33 * np.where(t["nt"] > 0, t["nt"], 1)), 0.0)
+    return res

@@ -31,16 +31,50 @@ k_cat_partials(const T* __restrict__ w, const T* __restrict__ nbar, int64_t n, d
   const int64_t beg = (int64_t)blockIdx.x * chunk;
   const int64_t end = min(n, beg + chunk);
   double a[NSUM] = {0, 0, 0, 0, 0, 0};
-  for (int64_t i = beg + threadIdx.x; i < end; i += blockDim.x) {
-    const double wi = w ? (double)w[i] : 1.0;
-    const double nb = nbar ? (double)nbar[i] : 0.0;
-    const double w2 = wi * wi;
-    a[0] += wi;
-    a[1] += w2;
-    a[2] += w2 * wi;
-    a[3] += nb * w2;
-    a[4] += nb * nb * w2 * wi;
-    a[5] = fmax(a[5], fabs(wi));
+  if constexpr (sizeof(T) == 4) {
+    // float inputs: products and per-thread sums in float-float arithmetic (error-free products by
+    // FMA, two-sum accumulation, about 48 significant bits) instead of the slow FP64 pipe; the
+    // per-thread results are exact in double and enter the same fixed-order tree
+    float hs[NSUM - 1] = {0, 0, 0, 0, 0}, ls[NSUM - 1] = {0, 0, 0, 0, 0};
+    float wmax = 0.0f;
+    // explicit _rn operations: the compiler must not fuse a product into the sums below
+    auto acc = [&](int k, float vh, float vl) {
+      const float s = __fadd_rn(hs[k], vh);
+      const float bb = __fsub_rn(s, hs[k]);
+      const float e = __fadd_rn(__fadd_rn(__fsub_rn(hs[k], __fsub_rn(s, bb)), __fsub_rn(vh, bb)), __fadd_rn(ls[k], vl));
+      hs[k] = __fadd_rn(s, e);
+      ls[k] = __fsub_rn(e, __fsub_rn(hs[k], s));
+    };
+    for (int64_t i = beg + threadIdx.x; i < end; i += blockDim.x) {
+      const float wi = w ? (float)w[i] : 1.0f;
+      const float nb = nbar ? (float)nbar[i] : 0.0f;
+      const float p2 = __fmul_rn(wi, wi), e2 = fmaf(wi, wi, -p2);             // w^2
+      const float p3 = __fmul_rn(p2, wi), e3 = fmaf(p2, wi, -p3) + e2 * wi;   // w^3
+      const float p4 = __fmul_rn(nb, p2), e4 = fmaf(nb, p2, -p4) + nb * e2;   // nbar w^2
+      const float pt = __fmul_rn(nb, p3), et = fmaf(nb, p3, -pt) + nb * e3;   // nbar w^3
+      const float p5 = __fmul_rn(nb, pt), e5 = fmaf(nb, pt, -p5) + nb * et;   // nbar^2 w^3
+      acc(0, wi, 0.0f);
+      acc(1, p2, e2);
+      acc(2, p3, e3);
+      acc(3, p4, e4);
+      acc(4, p5, e5);
+      wmax = fmaxf(wmax, fabsf(wi));
+    }
+#pragma unroll
+    for (int k = 0; k < NSUM - 1; ++k) a[k] = (double)hs[k] + (double)ls[k];
+    a[NSUM - 1] = (double)wmax;
+  } else {
+    for (int64_t i = beg + threadIdx.x; i < end; i += blockDim.x) {
+      const double wi = w ? (double)w[i] : 1.0;
+      const double nb = nbar ? (double)nbar[i] : 0.0;
+      const double w2 = wi * wi;
+      a[0] += wi;
+      a[1] += w2;
+      a[2] += w2 * wi;
+      a[3] += nb * w2;
+      a[4] += nb * nb * w2 * wi;
+      a[5] = fmax(a[5], fabs(wi));
+    }
   }
 #pragma unroll
   for (int k = 0; k < NSUM; ++k) sh[k][threadIdx.x] = a[k];

@@ -153,3 +153,105 @@ def test_poisson_shot_noise_is_subtracted():
         se = d.std(axis=0, ddof=1) / np.sqrt(nseed)
         assert np.all(np.abs(d.mean(axis=0)) < 4 * se + 0.02 * level), sig
     assert np.all(np.abs(r["N0"].mean(axis=0) / level - 1) < 0.1)
+
+
+# --- FFT-method (exact triplet) shot noise ------------------------------------------------------
+
+def _object_fields(spec, pos, w):
+    """Uncompensated transforms of a few point objects: X(q) = sum_p w_p e^{-i q.x_p} and the
+    N-field sum_p w_p^2 e^{-i q.x_p}, on the integer grid of spec."""
+    (kx, ky, kz), _ = M.kvectors(spec["n"], spec["box"])
+    X = np.zeros((spec["n"],) * 3, dtype=np.complex128)
+    N = np.zeros_like(X)
+    for p, wp in zip(pos, w):
+        e = np.exp(-1j * (kx * p[0] + ky * p[1] + kz * p[2]))
+        X += wp * e
+        N += wp * wp * e
+    return X, N
+
+
+def _distinct_triple_part(spec, pos, w, kbins, tri, ell):
+    """(2l+1)/N_T sum over closed triplets of L_l(mu1) sum_{a, b, c distinct} w_a w_b w_c
+    e^{-i(q1.x_a + q2.x_b + q3.x_c)}, by explicit loops over modes (independent of the oracle)."""
+    from oracle import harmonics as Hm
+
+    n, box = spec["n"], spec["box"]
+    kf = 2 * pi / box
+    b, _ = M.bin_index(n, box, *kbins)
+    ii = M.int_freqs(n)
+    modes = [[] for _ in range(kbins[2])]
+    for a in range(n):
+        for c in range(n):
+            for e in range(n):
+                if b[a, c, e] >= 0:
+                    modes[b[a, c, e]].append((ii[a], ii[c], ii[e]))
+    out = []
+    for i, j, k in tri:
+        tot, cnt = 0.0, 0
+        for q1 in modes[i]:
+            l1 = float(Hm.legendre(ell, q1[2] / np.sqrt(q1[0] ** 2 + q1[1] ** 2 + q1[2] ** 2)))
+            for q2 in modes[j]:
+                q3 = (-q1[0] - q2[0], -q1[1] - q2[1], -q1[2] - q2[2])
+                if max(abs(q3[0]), abs(q3[1]), abs(q3[2])) >= n // 2:
+                    continue
+                if b[q3[0] % n, q3[1] % n, q3[2] % n] != k:
+                    continue
+                cnt += 1
+                s = 0.0
+                for xa in range(len(w)):
+                    for xb in range(len(w)):
+                        for xc in range(len(w)):
+                            if len({xa, xb, xc}) < 3:
+                                continue
+                            ph = sum(kf * (q1[d] * pos[xa][d] + q2[d] * pos[xb][d] + q3[d] * pos[xc][d])
+                                     for d in range(3))
+                            s += w[xa] * w[xb] * w[xc] * np.cos(ph)
+                tot += l1 * s
+        out.append((2 * ell + 1) * tot / cnt if cnt else 0.0)
+    return np.array(out)
+
+
+@pytest.mark.parametrize("ell", [0, 2])
+def test_fft_shot_equals_raw_estimator_for_two_objects(ell):
+    """With at most two objects every closed triplet takes two legs from one object, so the raw
+    estimator (no window, I33 = 1) equals the FFT-method shot noise exactly."""
+    from oracle import shot as S
+
+    spec = _periodic_spec(12, 100.0)
+    kf = 2 * pi / 100.0
+    kb = (0.5 * kf, 1.0 * kf, 3)
+    tri = B.triangles(kb)
+    pos = [(13.7, 42.1, 77.3), (61.2, 5.9, 30.4)]
+    w = [0.8, 1.7]
+    X, N = _object_fields(spec, pos, w)
+    Xl = B.los_field(spec, X, ell)
+    sums, counts = B.scoccimarro_brute(spec, X, Xl, kb, tri)
+    raw = (2 * ell + 1) * np.real(sums) / counts
+    s3 = sum(x ** 3 for x in w)
+    sn = S.fft_method_shot_noise(spec, X, N, kb, tri, 1.0, s3, [ell])[ell]
+    scale = np.max(np.abs(raw))
+    assert scale > 0
+    np.testing.assert_allclose(sn, raw, rtol=0, atol=1e-12 * scale)
+
+
+@pytest.mark.parametrize("ell", [0, 2])
+def test_fft_shot_leaves_the_distinct_triples(ell):
+    """With three objects, raw estimator minus FFT-method shot noise is the sum over triples of
+    three distinct objects (evaluated here by explicit loops)."""
+    from oracle import shot as S
+
+    spec = _periodic_spec(10, 100.0)
+    kf = 2 * pi / 100.0
+    kb = (0.5 * kf, 1.0 * kf, 3)
+    tri = B.triangles(kb)
+    pos = [(13.7, 42.1, 77.3), (61.2, 5.9, 30.4), (88.8, 70.2, 12.6)]
+    w = [0.8, 1.7, 1.1]
+    X, N = _object_fields(spec, pos, w)
+    Xl = B.los_field(spec, X, ell)
+    sums, counts = B.scoccimarro_brute(spec, X, Xl, kb, tri)
+    raw = (2 * ell + 1) * np.real(sums) / counts
+    s3 = sum(x ** 3 for x in w)
+    sn = S.fft_method_shot_noise(spec, X, N, kb, tri, 1.0, s3, [ell])[ell]
+    distinct = _distinct_triple_part(spec, pos, w, kb, tri, ell)
+    scale = np.max(np.abs(raw))
+    np.testing.assert_allclose(raw - sn, distinct, rtol=0, atol=1e-11 * scale)
