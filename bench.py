@@ -283,12 +283,27 @@ def bispec_leg(args, world, rank, barrier, max_over_ranks):
             a[2] += 1
     api.set_profiling(False)
     stages = {k: round(v[0] / v[2], 4) for k, v in acc.items()}
+    # the same measurement with the FFT-method (exact triplet) shot noise of B_l
+    kwf = dict(kw, shot="fft")
+    for _ in range(args.warmup):
+        api.bispectrum(cd, **kwf)
+    torch.cuda.synchronize()
+    barrier()
+    s.record()
+    for _ in range(args.steps):
+        api.bispectrum(cd, **kwf)
+    e.record()
+    torch.cuda.synchronize()
+    barrier()
+    ms_fft = max_over_ranks(s.elapsed_time(e)) / args.steps
     return {"metric": "B_l triangles/s @256^3 (805 closed triangles x B_0, B_2; + B_000, B_202, shot noise)",
             "value": world * ntri.value * nmult / (ms / 1e3), "unit": "triangles/s", "ms_per_step": ms,
             "measurements_per_s": world / (ms / 1e3), "triangles": ntri.value, "pairs": npair.value,
             "config": {"workload": "bispec_256", "mesh": w["n"], "n_gal": w["n_gal"], "nbins": w["nbins"],
                        "assign": "TSC", "interlace": True},
             "stages_ms": stages, "gpu_launches": launches * args.steps,
+            "fft_method_shot": {"value": world * ntri.value * nmult / (ms_fft / 1e3), "ms_per_step": ms_fft,
+                                "note": "shot noise of B_l by the FFT method (exact triplet sums)"},
             "triple_product": "3xTF32 split hi+lo tensor-core products (mma.sync m16n8k8), FP32 within 128-cell chunks, FP64 across chunks"}
 
 

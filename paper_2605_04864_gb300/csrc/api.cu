@@ -563,7 +563,7 @@ npc_status npc_bispectrum(npc_ctx* ctx, const npc_mesh_spec* mesh, const npc_cat
   if (bins->nbins > 24) return set_err(ctx, NPC_ERR_UNSUPPORTED, "bispectrum supports at most 24 bins");
   if ((scoc_ell_mask & ~5u) || (tripo_ell_mask & ~5u) || (scoc_ell_mask | tripo_ell_mask) == 0)
     return set_err(ctx, NPC_ERR_INVALID_ARG, "multipole masks must use bits 0 and 2");
-  if (shot != 0 && shot != 1) return set_err(ctx, NPC_ERR_INVALID_ARG, "shot must be 0 or 1");
+  if (shot < 0 || shot > 2) return set_err(ctx, NPC_ERR_INVALID_ARG, "shot must be 0, 1 or 2");
   if (prec != NPC_PREC_FP64 && prec != NPC_PREC_MIXED) return set_err(ctx, NPC_ERR_INVALID_ARG, "bad precision");
   const bool mono = (scoc_ell_mask & ~1u) == 0 && (tripo_ell_mask & ~1u) == 0;
   if (mesh->periodic) {

@@ -199,7 +199,7 @@ k_bin_cross(const cplx<T>* __restrict__ X0, const cplx<T>* __restrict__ XN, int 
 // 4. shell-filtered inverse transforms
 // ------------------------------------------------------------------------------------------
 struct ShellField {
-  int8_t src;     // 0: X_0, 1: ones (indicator)
+  int8_t src;     // 0: X_0, 1: ones (indicator), 2: X_0 N_0^* (FFT-method shot noise)
   int8_t mult;    // 0: 1, 1: L_2(mu)
   int16_t bin;    // >= 0: modes of this bin; -1: all modes with n2 <= n2cap
   int K;          // kz <= K, |ky| <= K
@@ -213,9 +213,9 @@ struct ShellField {
 // frequency i = kx' (kx' < NS/2) or kx' - NS, read from the n-grid spectrum X0.
 template <typename T, int NS>
 __global__ void __launch_bounds__(BT)
-k_shell_x(const cplx<T>* __restrict__ X0, int KZX, int nfine, const ShellField* __restrict__ fields, int nfields,
-          int Kmax, const int16_t* __restrict__ tab, int n2cap, double lx, double ly, double lz,
-          const cplx<T>* __restrict__ tw_g, cplx<T>* __restrict__ T1) {
+k_shell_x(const cplx<T>* __restrict__ X0, const cplx<T>* __restrict__ XN, int KZX, int nfine,
+          const ShellField* __restrict__ fields, int nfields, int Kmax, const int16_t* __restrict__ tab, int n2cap,
+          double lx, double ly, double lz, const cplx<T>* __restrict__ tw_g, cplx<T>* __restrict__ T1) {
   using C = cplx<T>;
   constexpr int TPF = NS / 8;
   constexpr int G = BT / TPF > 0 ? BT / TPF : 1;
@@ -223,7 +223,8 @@ k_shell_x(const cplx<T>* __restrict__ X0, int KZX, int nfine, const ShellField* 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
   C* xrow = tw + NS;                  // X_0 row
-  T* l2row = reinterpret_cast<T*>(xrow + NS);   // L_2(mu) per kx
+  C* xnrow = xrow + NS;               // X_0 N_0^* row (when XN is given)
+  T* l2row = reinterpret_cast<T*>(xnrow + NS);  // L_2(mu) per kx
   int* binrow = reinterpret_cast<int*>(l2row + NS);  // bin per kx (-1 excluded), n2 per kx
   int* n2row = binrow + NS;
   C* bufs = reinterpret_cast<C*>(n2row + NS);   // NBUF x NP
@@ -243,7 +244,9 @@ k_shell_x(const cplx<T>* __restrict__ X0, int KZX, int nfine, const ShellField* 
       const int fx = i < 0 ? i + nfine : i;
       const int n2 = i * i + jy * jy + kz * kz;
       const bool inrange = i != -NS / 2 && i != -nfine / 2 && jy != -nfine / 2 && n2 <= n2cap;
-      xrow[kx] = (inrange && kz < KZX) ? X0[((size_t)kz * nfine + ky) * nfine + fx] : cmk(T(0), T(0));
+      const size_t src = ((size_t)kz * nfine + ky) * nfine + fx;
+      xrow[kx] = (inrange && kz < KZX) ? X0[src] : cmk(T(0), T(0));
+      if (XN) xnrow[kx] = (inrange && kz < KZX) ? cmul(X0[src], cconj(XN[src])) : cmk(T(0), T(0));
       const T kk = sqrt(T(n2));
       const T mu = n2 > 0 ? (T(i) * T(lx) + T(jy) * T(ly) + T(kz) * T(lz)) / kk : T(0);
       l2row[kx] = T(1.5) * mu * mu - T(0.5);
@@ -268,7 +271,7 @@ k_shell_x(const cplx<T>* __restrict__ X0, int KZX, int nfine, const ShellField* 
         if (live) {
           const bool in = sf.bin >= 0 ? (binrow[kx] == sf.bin) : (n2row[kx] >= 0);
           if (in) {
-            a = sf.src == 0 ? xrow[kx] : cmk(T(1), T(0));
+            a = sf.src == 0 ? xrow[kx] : (sf.src == 2 ? xnrow[kx] : cmk(T(1), T(0)));
             if (sf.mult) a = cscale(a, l2row[kx]);
           }
         }
@@ -402,7 +405,7 @@ struct TripleArgs {
   int npair;
   int ncol;         // used columns
   int nstage;       // distinct fields staged per chunk
-  int stage_field[2 * NB_MAX + 2];  // R index of staged slot s
+  int stage_field[3 * NB_MAX + 2];  // R index of staged slot s
   int a_slot[2][NB_MAX];            // staged slot of A_i per family
   int b_slot[NB_MAX];               // staged slot of B_j
   int c_slot[TRI_COLS];             // staged slot of column c (-1: zero column)
@@ -593,12 +596,17 @@ struct FinalArgs {
   int64_t ncell;
   double kmin, dk;
   int part_nw_cross;    // partial records of the cross-spectrum kernel
+  // FFT-method shot noise (shot = 2): partials of sum_x I_a I_b G_c (family 0) and
+  // sum_x I2_a I_b G_c (family 1) in s1, of sum_x I_a I_b G2_c in s2; columns c = 0 .. nb-1
+  int s1_nparts, s1_nrows, s2_nparts, s2_nrows;
 };
 
 __global__ void k_bispec_finalize(const int* __restrict__ tri, const int* __restrict__ pair_ij,
                                   const double* __restrict__ part_main, const double* __restrict__ nt_sums,
                                   const double* __restrict__ cross_m, const double* __restrict__ cross_q,
-                                  const FinalArgs F, const double* __restrict__ sc, double* __restrict__ out) {
+                                  const double* __restrict__ part_s1, const double* __restrict__ part_s2,
+                                  const double* __restrict__ nt2_sums, const FinalArgs F,
+                                  const double* __restrict__ sc, double* __restrict__ out) {
   const int nb = F.nb;
   const double i33 = sc[SC_I33], s3 = sc[SC_S3];
   // layout offsets
@@ -618,14 +626,22 @@ __global__ void k_bispec_finalize(const int* __restrict__ tri, const int* __rest
     if (n <= 0) return 0.0;
     return l == 0 ? (cross(cross_q, b, 0) - s3 * n) / n : (cross(cross_q, b, 1) - s3 * cross(cross_q, b, 3)) / n;
   };
+  auto pair_index = [&](int a, int b) {   // a <= b
+    int p = 0;
+    for (int c = 0; c < a; ++c) p += nb - c;
+    return p + b - a;
+  };
+  // sum over CTAs of an FFT-method partial (family fam, pair p, column c)
+  auto shot_sum = [&](const double* part, int nparts, int nrows, int fam, int p, int c) {
+    double v = 0;
+    for (int q = 0; q < nparts; ++q) v += part[((size_t)q * nrows + fam * F.npair + p) * nb + c];
+    return v;
+  };
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int nthreads = gridDim.x * blockDim.x;
   for (int t = tid; t < F.ntri; t += nthreads) {
     const int i = tri[3 * t], j = tri[3 * t + 1], k = tri[3 * t + 2];
-    // locate the pair (i, j)
-    int p = 0;
-    for (int a = 0; a < i; ++a) p += nb - a;
-    p += j - i;
+    const int p = pair_index(i, j);
     double s0 = 0, s2 = 0, snt = 0;
     for (int c = 0; c < F.nparts; ++c) {
       s0 += part_main[((size_t)c * F.nrows + p) * F.ncol + k];
@@ -640,7 +656,24 @@ __global__ void k_bispec_finalize(const int* __restrict__ tri, const int* __rest
       const int l = F.scoc_l[e];
       const double raw = snt > 0 ? (2 * l + 1) * (l == 0 ? s0 : s2) / (i33 * snt) : 0.0;
       double sn = 0.0;
-      if (F.shot && snt > 0) {
+      if (F.shot == 2 && snt > 0) {
+        // FFT method: two-object terms T23 + T12 + T13 over the closed triplets, minus twice the
+        // three-of-one-object part S N_T^(l) (each two-object term holds it once, the pure term once)
+        const int pik = pair_index(i, k), pjk = pair_index(j, k);
+        double tsum, ntl;
+        if (l == 0) {
+          tsum = shot_sum(part_s1, F.s1_nparts, F.s1_nrows, 0, pjk, i) +
+                 shot_sum(part_s1, F.s1_nparts, F.s1_nrows, 0, p, k) +
+                 shot_sum(part_s1, F.s1_nparts, F.s1_nrows, 0, pik, j);
+          ntl = snt;
+        } else {
+          tsum = shot_sum(part_s2, F.s2_nparts, F.s2_nrows, 0, pjk, i) +
+                 shot_sum(part_s1, F.s1_nparts, F.s1_nrows, 1, p, k) +
+                 shot_sum(part_s1, F.s1_nparts, F.s1_nrows, 1, pik, j);
+          ntl = nt2_sums[(size_t)p * nb + k];
+        }
+        sn = (2 * l + 1) * (tsum - 2.0 * s3 * ntl) / (i33 * snt);
+      } else if (F.shot && snt > 0) {
         const double L12 = l == 0 ? 1.0 : 1.5 * c12 * c12 - 0.5;
         const double L13 = l == 0 ? 1.0 : 1.5 * c13 * c13 - 0.5;
         sn = (2 * l + 1) / i33 * ((l == 0 ? s3 : 0.0) + Hm(l, i) + L12 * Hm(l, j) + L13 * Hm(l, k));
@@ -703,13 +736,14 @@ __global__ void k_cross_reduce(const double* __restrict__ part, int nrec, int nb
 // shell inside |q| <= k_N/2 no triple aliases across the grid, so the count is an exact integer and
 // the sum is rounded to ncell * round(count): this removes the rounding error of the float shell
 // fields from the normalisation whenever it is below half a triangle.
+// (round_count = 0: the Legendre-weighted count sum_x L_2 I_i I_j I_k, not an integer, is kept as is)
 __global__ void k_nt_reduce(const double* __restrict__ part, int nparts, int npair, int nslots, int nb,
-                            double ncell, double* __restrict__ nt) {
+                            double ncell, int round_count, double* __restrict__ nt) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < npair * nb; e += gridDim.x * blockDim.x) {
     const int p = e / nb, k = e % nb;
     double s = 0;
     for (int c = 0; c < nparts; ++c) s += part[((size_t)c * npair + p) * nslots + k];
-    nt[e] = rint(s / ncell) * ncell;
+    nt[e] = round_count ? rint(s / ncell) * ncell : s;
   }
 }
 
@@ -753,6 +787,7 @@ int shell_grid_size(int need, int n, bool fp64) {
 
 struct ShellLaunch {
   const void* X;
+  const void* XN;   // N-field spectrum for src = 2 fields, or null
   int KZX, nfine;
   const ShellField* fields;
   int nfield, Kmax;
@@ -774,14 +809,14 @@ npc_status shell_passes(npc_ctx* ctx, const ShellLaunch& sl, cplx<T>* T1, cplx<T
   NPC_TRY(get_twiddles(ctx, NS, sizeof(T) == 8 ? NPC_PREC_FP64 : NPC_PREC_MIXED, &twp));
   const C* tw = (const C*)twp;
   {
-    const size_t smem = sizeof(C) * (2 * NS + (size_t)RowGroups<NS, BT>::NBUF * row_pad_len<NS>()) +
+    const size_t smem = sizeof(C) * (3 * NS + (size_t)RowGroups<NS, BT>::NBUF * row_pad_len<NS>()) +
                         sizeof(T) * NS + sizeof(int) * 2 * NS;
     auto kern = k_shell_x<T, NS>;
     NPC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int nrows = (sl.Kmax + 1) * (2 * sl.Kmax + 1);
     kern<<<std::min(nrows, ctx->num_sms * 4), BT, smem, ctx->stream>>>(
-        (const C*)sl.X, sl.KZX, sl.nfine, sl.fields, sl.nfield, sl.Kmax, sl.tab, sl.n2cap, sl.l[0], sl.l[1], sl.l[2],
-        tw, T1);
+        (const C*)sl.X, (const C*)sl.XN, sl.KZX, sl.nfine, sl.fields, sl.nfield, sl.Kmax, sl.tab, sl.n2cap, sl.l[0],
+        sl.l[1], sl.l[2], tw, T1);
     NPC_LAUNCH(ctx);
   }
   constexpr int TX = BCol<NS>::TX;
@@ -971,21 +1006,48 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
   auto it = ctx->host_cache_keys.find(ntname);
   const bool need_nt = it == ctx->host_cache_keys.end() || it->second != ntkey;
 
+  // FFT-method shot noise: the l = 2 triplet count sum_x L_2 I_i I_j I_k is cached like N_T
+  const bool fftshot = shot == 2;
+  const bool want_nt2 = fftshot && want2;
+  double* nt2_sums = nullptr;
+  std::vector<char> nt2key = ntkey;
+  nt2key.push_back('2');
+  const std::string nt2name = slot_name(ctx, "bis.nt2sums");
+  bool need_nt2 = false;
+  if (want_nt2) {
+    NPC_TRY(ws_get(ctx, nt2name.c_str(), sizeof(double) * npair * nb, (void**)&nt2_sums));
+    auto it2 = ctx->host_cache_keys.find(nt2name);
+    need_nt2 = it2 == ctx->host_cache_keys.end() || it2->second != nt2key;
+  }
+
   std::vector<ShellField> fl;
-  auto add = [&](int src, int mult, int bin, int Kf) {
+  std::vector<int> ffam;   // field family (z-pass pairs stay within a family)
+  auto add = [&](int src, int mult, int bin, int Kf, int fam) {
     ShellField f{};
     f.src = (int8_t)src; f.mult = (int8_t)mult; f.bin = (int16_t)bin; f.K = Kf;
     fl.push_back(f);
+    ffam.push_back(fam);
   };
-  for (int b = 0; b < nb; ++b) add(0, 0, b, Ks);                 // F0_b: R index b
-  if (want2) for (int b = 0; b < nb; ++b) add(0, 1, b, Ks);      // F2_b: R index nb + b
+  for (int b = 0; b < nb; ++b) add(0, 0, b, Ks, 0);              // F0_b: R index b
+  if (want2) for (int b = 0; b < nb; ++b) add(0, 1, b, Ks, 1);   // F2_b: R index nb + b
   const int iF2 = want2 ? nb : -1;
   const int iI = (int)fl.size();
-  if (need_nt) for (int b = 0; b < nb; ++b) add(1, 0, b, Ks);    // I_b
+  if (need_nt || fftshot) for (int b = 0; b < nb; ++b) add(1, 0, b, Ks, 2);   // I_b
   const int iG = (int)fl.size();
   int ng = 0;
-  if (wantG0) { add(0, 0, -1, KG); ng++; }
-  if (wantG2) { add(0, 1, -1, KG); ng++; }
+  if (wantG0) { add(0, 0, -1, KG, 3); ng++; }
+  if (wantG2) { add(0, 1, -1, KG, 3); ng++; }
+  int iS0 = -1, iS2 = -1, iI2 = -1;
+  if (fftshot) {
+    iS0 = (int)fl.size();
+    for (int b = 0; b < nb; ++b) add(2, 0, b, Ks, 4);            // sum_{q in b} X_0 N_0^* e^{iqx}
+    if (want2) {
+      iS2 = (int)fl.size();
+      for (int b = 0; b < nb; ++b) add(2, 1, b, Ks, 5);          // the same with L_2(mu)
+      iI2 = (int)fl.size();
+      for (int b = 0; b < nb; ++b) add(1, 1, b, Ks, 6);          // L_2(mu) indicators
+    }
+  }
   const int nfield = (int)fl.size();
   int64_t o1 = 0, o2 = 0;
   std::vector<int> plane_f, plane_kz;
@@ -1002,7 +1064,7 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
   // pairs for the z pass: consecutive fields of the same family (F0, F2, I, G) and the same K, so
   // that the rounding of every field (a pair shares one complex transform) does not depend on
   // whether the cached indicator fields are recomputed in this call
-  auto family = [&](int f) { return f < nb ? 0 : (f < iI ? 1 : (f < iG ? 2 : 3)); };
+  auto family = [&](int f) { return ffam[f]; };
   std::vector<int> za, zb;
   for (int f = 0; f < nfield;) {
     if (f + 1 < nfield && fl[f + 1].K == fl[f].K && family(f + 1) == family(f)) {
@@ -1055,6 +1117,7 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
   {
     ShellLaunch sl{};
     sl.X = X;
+    sl.XN = fftshot ? (const void*)(X + xfs) : nullptr;
     sl.KZX = KZ;
     sl.nfine = N;
     sl.fields = dfields;
@@ -1106,12 +1169,45 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
   TripleArgs ta, tn;
   setup(ta, false);
   setup(tn, true);
-  const int ngroups = (ta.nrows + TRI_ROWS - 1) / TRI_ROWS;
-  const int grid = sizeof(T) == 4 ? std::max(1, ctx->num_sms / ngroups) : ctx->num_sms * 4;
+  // FFT-method shot noise products: rows (A_a, I_b) over pairs a <= b, columns over bins
+  auto setup_shot = [&](TripleArgs& a, int fieldA0, int fieldA1, int fieldC) {
+    a = TripleArgs{};
+    a.npair = npair;
+    a.ncell = (int64_t)ncs;
+    a.nstage = 0;
+    auto stage_of = [&](int field) {
+      for (int q = 0; q < a.nstage; ++q)
+        if (a.stage_field[q] == field) return q;
+      a.stage_field[a.nstage] = field;
+      return a.nstage++;
+    };
+    for (int q = 0; q < TRI_COLS; ++q) a.c_slot[q] = -1;
+    for (int b = 0; b < nb; ++b) {
+      a.a_slot[0][b] = stage_of(fieldA0 + b);
+      a.b_slot[b] = stage_of(iI + b);
+      a.c_slot[b] = stage_of(fieldC + b);
+    }
+    if (fieldA1 >= 0)
+      for (int b = 0; b < nb; ++b) a.a_slot[1][b] = stage_of(fieldA1 + b);
+    a.nf_cols = nb;
+    a.nrows = npair * (fieldA1 >= 0 ? 2 : 1);
+    a.ncol = nb;
+  };
+  TripleArgs ts1{}, ts2{}, tn2{};
+  if (fftshot) {
+    setup_shot(ts1, iI, want2 ? iI2 : -1, iS0);   // sum I_a I_b S0_c and sum I2_a I_b S0_c
+    if (want2) setup_shot(ts2, iI, -1, iS2);      // sum I_a I_b S2_c
+    if (want2) setup_shot(tn2, iI2, -1, iI);      // sum I2_a I_b I_c (cached)
+  }
+  auto grid_for = [&](const TripleArgs& a) {
+    const int ng_ = (a.nrows + TRI_ROWS - 1) / TRI_ROWS;
+    return sizeof(T) == 4 ? std::max(1, ctx->num_sms / ng_) : ctx->num_sms * 4;
+  };
+  const int grid = grid_for(ta);
   double* part;
   NPC_TRY(ws_get(ctx, "bis.tripart", sizeof(double) * (size_t)grid * std::max(ta.nrows, tn.nrows) * TRI_COLS,
                  (void**)&part));
-  auto launch = [&](const TripleArgs& a) -> npc_status {
+  auto launch = [&](const TripleArgs& a, int grid, double* part) -> npc_status {
     if constexpr (sizeof(T) == 4) {
       const int groups = (a.nrows + TRI_ROWS - 1) / TRI_ROWS;
       auto run = [&](auto kern, int nt) -> npc_status {
@@ -1133,14 +1229,37 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
     return NPC_OK;
   };
   if (need_nt) {
-    NPC_TRY(launch(tn));
-    k_nt_reduce<<<(npair * nb + 127) / 128, 128, 0, ctx->stream>>>(part, grid, npair, nb, nb, (double)ncs,
+    NPC_TRY(launch(tn, grid, part));
+    k_nt_reduce<<<(npair * nb + 127) / 128, 128, 0, ctx->stream>>>(part, grid, npair, nb, nb, (double)ncs, 1,
                                                                   nt_sums);
     NPC_LAUNCH(ctx);
     ctx->host_cache_keys[ntname] = ntkey;
   }
-  NPC_TRY(launch(ta));
+  if (need_nt2) {
+    const int g2 = grid_for(tn2);
+    double* p2;
+    NPC_TRY(ws_get(ctx, "bis.nt2part", sizeof(double) * (size_t)g2 * tn2.nrows * nb, (void**)&p2));
+    NPC_TRY(launch(tn2, g2, p2));
+    k_nt_reduce<<<(npair * nb + 127) / 128, 128, 0, ctx->stream>>>(p2, g2, npair, nb, nb, (double)ncs, 0,
+                                                                  nt2_sums);
+    NPC_LAUNCH(ctx);
+    ctx->host_cache_keys[nt2name] = nt2key;
+  }
+  NPC_TRY(launch(ta, grid, part));
   NPC_TRY(stage_mark(ctx, "triple"));
+  double *part_s1 = nullptr, *part_s2 = nullptr;
+  int gs1 = 0, gs2 = 0;
+  if (fftshot) {
+    gs1 = grid_for(ts1);
+    NPC_TRY(ws_get(ctx, "bis.s1part", sizeof(double) * (size_t)gs1 * ts1.nrows * nb, (void**)&part_s1));
+    NPC_TRY(launch(ts1, gs1, part_s1));
+    if (want2) {
+      gs2 = grid_for(ts2);
+      NPC_TRY(ws_get(ctx, "bis.s2part", sizeof(double) * (size_t)gs2 * ts2.nrows * nb, (void**)&part_s2));
+      NPC_TRY(launch(ts2, gs2, part_s2));
+    }
+    NPC_TRY(stage_mark(ctx, "shot_triple"));
+  }
 
   // 6. finalize
   FinalArgs fa{};
@@ -1162,8 +1281,13 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
   fa.ncell = (int64_t)ncs;
   fa.kmin = kb.kmin;
   fa.dk = kb.dk;
+  fa.s1_nparts = gs1;
+  fa.s1_nrows = ts1.nrows;
+  fa.s2_nparts = gs2;
+  fa.s2_nrows = ts2.nrows;
   k_bispec_finalize<<<std::max(1, (std::max(ntri, npair) + 127) / 128), 128, 0, ctx->stream>>>(
-      (const int*)(dtab + t_tri), (const int*)(dtab + t_pij), part, nt_sums, cross_m, cross_q, fa, sc, dev_out);
+      (const int*)(dtab + t_tri), (const int*)(dtab + t_pij), part, nt_sums, cross_m, cross_q, part_s1, part_s2,
+      nt2_sums, fa, sc, dev_out);
   NPC_LAUNCH(ctx);
   NPC_TRY(stage_mark(ctx, "finalize"));
   (void)out_len;

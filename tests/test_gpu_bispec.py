@@ -86,6 +86,47 @@ def test_survey_monopoles(api, prec, tol):
     _check(res, orc, tol)
 
 
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 1e-4)])
+def test_fft_method_shot_noise_periodic(api, prec, tol):
+    """shot = "fft": the exact two-object triplet sums (B_0, B_2) against the oracle's explicit
+    enumeration; the raw estimates and the compressed estimator's analytic shot noise are unchanged."""
+    cat = make_periodic_catalog(20000, 300.0, 32, seed=47)
+    kb = (0.02, 0.02, 5)
+    res = api.bispectrum(cat, n=32, box=300.0, kbins=kb, precision=prec, shot="fft")
+    orc = OB.bispectrum(_spec(32, 300.0), cat, None, kb, (0, 2), (0, 2), shot="fft")
+    scale_t = np.abs(orc["B"][0]) + np.abs(orc["shot_B_fft"][0])
+    for l in (0, 2):
+        raw_g = res["B"][l] + res["shot_B"][l]
+        e = np.abs(raw_g - orc["B"][l]) / np.maximum(np.abs(orc["B"][l]), scale_t)
+        assert np.max(e) < tol, ("B", l, np.max(e))
+        e = np.abs(res["shot_B"][l] - orc["shot_B_fft"][l]) / np.maximum(np.abs(orc["shot_B_fft"][l]), scale_t)
+        assert np.max(e) < tol, ("shot_B_fft", l, np.max(e))
+    scale_p = np.abs(orc["BB"][0]) + np.abs(orc["shot_BB"][0])
+    e = np.abs(res["shot_BB"][0] - orc["shot_BB"][0]) / np.maximum(np.abs(orc["shot_BB"][0]), scale_p)
+    assert np.max(e) < tol
+    # the exact and thin-shell forms estimate the same noise: close for the monopole, not equal
+    d = np.abs(orc["shot_B_fft"][0] - orc["shot_B"][0]) / np.abs(orc["shot_B"][0])
+    assert 0 < np.max(d) < 0.2
+
+
+def test_fft_method_shot_noise_survey_monopole(api):
+    """Survey geometry: the FFT-method shot noise of B_0 with randoms (alpha-weighted N-field)."""
+    from synthetic import make_survey_catalogs
+
+    box = 600.0
+    g, r, origin = make_survey_catalogs(20000, 200000, box, 900.0, 32, seed=73, fkp_p0=1e4)
+    kf = 2 * np.pi / box
+    kb = (2 * kf, 1.5 * kf, 3)
+    res = api.bispectrum(g, n=32, box=box, kbins=kb, scoc_ells=(0,), tripo_ells=(), precision="fp64",
+                         origin=origin, randoms=r, shot="fft")
+    spec = dict(n=32, box=box, origin=tuple(origin), assign=3, interlace=1, los="global",
+                los_dir=(0.0, 0.0, 1.0), periodic=0)
+    orc = OB.bispectrum(spec, g, r, kb, (0,), (), shot="fft")
+    scale = np.abs(orc["B"][0]) + np.abs(orc["shot_B_fft"][0])
+    e = np.abs(res["shot_B"][0] - orc["shot_B_fft"][0]) / np.maximum(np.abs(orc["shot_B_fft"][0]), scale)
+    assert np.max(e) < 1e-10
+
+
 def test_mixed_19_bins_805_triangles_128(api):
     """The 19-bin / 805-triangle layout of the 256^3 workload on a 128^3 mesh of the same box
     (k_max = 0.2 = k_N/2), float32 transforms: <= 1e-4."""
