@@ -235,6 +235,31 @@ def power_multipoles(spec, data, randoms, kbins, ells=(0, 2, 4), modified=(), me
     return res
 
 
+def cross_power_multipoles(spec, data_a, randoms_a, data_b, randoms_b, kbins, ells=(0, 2, 4)):
+    """Cross multipoles of two tracers A and B (multi-tracer spectra; the paper's toolkit measures
+    auto and cross spectra, Sec. 7, without printing the cross form).  Readings: the Y_lm weighting
+    (line of sight) sits on tracer B, P_l^AB = (2l+1)/I22^AB <Re F_0^A F_l^B*>_bin with F_l^B the
+    Hand+17 field of B; the normalisation I22^AB = sqrt(I22^A I22^B) (exact when the two
+    selections n w have the same shape); no shot noise is subtracted (disjoint tracers share no
+    object).  Pinned by: the cross spectrum of a tracer with itself equals its auto spectrum plus
+    N_0 (l = 0); with a global line of sight P_l^AB = P_l^BA."""
+    sa = catalog_scalars(data_a, randoms_a, spec["box"])
+    sb = catalog_scalars(data_b, randoms_b, spec["box"])
+    fa, _ = fields_plain(spec, fkp_meshes(spec, data_a, randoms_a, sa), [0])
+    need = sorted(set(ells) | {0})
+    fb, _ = fields_plain(spec, fkp_meshes(spec, data_b, randoms_b, sb), need)
+    kmin, dk, nb = kbins
+    b, kmag = M.bin_index(spec["n"], spec["box"], kmin, dk, nb)
+    i22 = np.sqrt(sa["I22"] * sb["I22"])
+    kmean, cnt = M.bin_average(kmag, b, nb)
+    empty = cnt == 0
+    res = {"P": {}, "k_eff": kmean, "nmodes": cnt, "I22": i22, "scalars_a": sa, "scalars_b": sb}
+    for ell in ells:
+        mean, _ = M.bin_average(np.real(fa[0] * np.conj(fb[ell])), b, nb)
+        res["P"][ell] = np.where(empty, 0.0, (2 * ell + 1) / i22 * mean)
+    return res
+
+
 def power_monopole_rfft(spec, data, randoms, kbins):
     """P_0 alone (Eq. Hand17 with l = 0, where no Y_lm weighting is needed) from real-to-complex
     transforms, for meshes too large for the full-m path.  Each stored mode of the half grid

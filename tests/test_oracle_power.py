@@ -240,3 +240,37 @@ def test_rfft_monopole_equals_full_grid(small_survey, interlace, assign):
     p0, cnt, sc = P.power_monopole_rfft(spec, g, r, kb)
     np.testing.assert_array_equal(cnt, a["nmodes"])
     np.testing.assert_allclose(p0, a["P"][0], rtol=1e-12, atol=1e-12 * sc["N0"])
+
+
+@pytest.mark.parametrize("interlace,assign", [(0, 2), (1, 3)])
+def test_cross_with_itself_is_auto_plus_shot(small_survey, interlace, assign):
+    """The cross multipoles of a tracer with itself equal its auto multipoles with the shot noise
+    N_0 added back to the monopole (same fields, I22^AA = I22^A)."""
+    g, r, origin = small_survey
+    spec = _survey_spec(20, 1000.0, origin, assign, interlace)
+    kb = (0.0, 0.02, 4)
+    auto = P.power_multipoles(spec, g, r, kb, (0, 2, 4))
+    cross = P.cross_power_multipoles(spec, g, r, g, r, kb, (0, 2, 4))
+    n0 = auto["scalars"]["N0"]
+    scale = np.abs(auto["P"][0]) + n0
+    for ell in (0, 2, 4):
+        want = auto["P"][ell] + (n0 if ell == 0 else 0.0) * (auto["nmodes"] > 0)
+        assert np.max(np.abs(cross["P"][ell] - want) / scale) < 1e-12
+
+
+def test_cross_is_symmetric_for_a_global_line_of_sight():
+    """With a fixed line of sight F_l = L_l(mu) F_0 for both tracers, so P_l^AB = P_l^BA."""
+    from synthetic import make_periodic_catalog
+
+    a = make_periodic_catalog(5000, 500.0, 16, seed=91)
+    b = make_periodic_catalog(3000, 500.0, 16, seed=92)
+    spec = dict(n=20, box=500.0, origin=(0.0, 0.0, 0.0), assign=3, interlace=1, los="global",
+                los_dir=(0.0, 0.0, 1.0), periodic=1)
+    kb = (0.0, 0.03, 5)
+    ab = P.cross_power_multipoles(spec, a, None, b, None, kb, (0, 2, 4))
+    ba = P.cross_power_multipoles(spec, b, None, a, None, kb, (0, 2, 4))
+    scale = np.max(np.abs(ab["P"][0]))
+    for ell in (0, 2, 4):
+        assert np.max(np.abs(ab["P"][ell] - ba["P"][ell])) < 1e-12 * scale
+    # and it is not the auto spectrum of either
+    assert np.max(np.abs(ab["P"][0] - P.power_multipoles(spec, a, None, kb, (0,))["P"][0])) > 1e-3 * scale
