@@ -170,6 +170,21 @@ npc_status npc_power_multipoles(npc_ctx* ctx, const npc_mesh_spec* mesh, const n
 /* Number of doubles written by npc_power_multipoles for this request (0 if the masks are bad). */
 int64_t npc_power_out_len(const npc_kbins* bins, uint32_t ell_mask, uint32_t modified_mask);
 
+/* Cross multipoles of two tracers A and B (multi-tracer spectra, which the paper's toolkit
+ * measures alongside the auto spectra; Sec. 6) -----------------------------------------------
+ * P_l^AB(k) = (2l+1)/I22^AB <Re F_0^A(k) F_l^B*(k)>_bin with F_l^B the m >= 0 Yamamoto field of
+ * tracer B (its line of sight: observer to B's grid points, or the global los), F_0^A the FKP field
+ * of A, I22^AB = sqrt(I22^A I22^B), and no shot noise subtracted (the tracers share no object).
+ * Both tracers use the same mesh spec; randoms_a and randoms_b are both NULL (periodic box) or both
+ * given (survey).  ell_mask: bits 0, 2, 4.  Cost: B's transforms plus one per phase for A.
+ * Output as npc_power_multipoles with modified_mask = 0 (length npc_power_out_len(bins, ell_mask,
+ * 0)), the 8 trailing scalars being [alpha_A, I22^AB, alpha_B, 0, I22^A, I22^B, sum w_A, sum w_B].
+ * Errors: as npc_power_multipoles; NPC_ERR_NUMERIC for an empty catalogue of either tracer. */
+npc_status npc_cross_power_multipoles(npc_ctx* ctx, const npc_mesh_spec* mesh, const npc_catalog* data_a,
+                                      const npc_catalog* randoms_a, const npc_catalog* data_b,
+                                      const npc_catalog* randoms_b, const npc_kbins* bins, uint32_t ell_mask,
+                                      npc_precision prec, double* out, int32_t out_on_device);
+
 /* Bispectrum multipoles (Sec. 2.2 Eq. bi_sco; Sec. 4 Eq. new_bispec; Sec. 5.4 shot noise) ------
  * Periodic box (mesh->periodic = 1, randoms = NULL) with a global line of sight (mesh->los = 1) for l = 2;
  * survey geometry (mesh->periodic = 0, randoms required) for the monopoles B_0 and B_000 only,

@@ -237,7 +237,7 @@ def power_multipoles(spec, data, randoms, kbins, ells=(0, 2, 4), modified=(), me
 
 def cross_power_multipoles(spec, data_a, randoms_a, data_b, randoms_b, kbins, ells=(0, 2, 4)):
     """Cross multipoles of two tracers A and B (multi-tracer spectra; the paper's toolkit measures
-    auto and cross spectra, Sec. 7, without printing the cross form).  Readings: the Y_lm weighting
+    auto and cross spectra, Sec. 6, without printing the cross form).  Readings: the Y_lm weighting
     (line of sight) sits on tracer B, P_l^AB = (2l+1)/I22^AB <Re F_0^A F_l^B*>_bin with F_l^B the
     Hand+17 field of B; the normalisation I22^AB = sqrt(I22^A I22^B) (exact when the two
     selections n w have the same shape); no shot noise is subtracted (disjoint tracers share no

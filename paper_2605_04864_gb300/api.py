@@ -136,6 +136,35 @@ def power_multipoles(data, randoms, n, box, origin=(0.0, 0.0, 0.0), assign=3, in
     return unpack_power(buf, kbins[2], ells, modified)
 
 
+def cross_power_multipoles(data_a, randoms_a, data_b, randoms_b, n, box, origin=(0.0, 0.0, 0.0), assign=3,
+                           interlace=1, kbins=(0.0, 0.01, 10), ells=(0, 2, 4), precision="mixed", periodic=None,
+                           los_dir=None, observer=(0.0, 0.0, 0.0), device=0, out=None):
+    """Cross multipoles P_l^AB of tracers A and B (line of sight on B, no shot noise).  Returns a
+    dict of NumPy arrays (scalars: alpha_A, I22_AB, alpha_B, 0, I22_A, I22_B, sum w_A, sum w_B), or
+    fills the device tensor ``out``."""
+    keep = _Keep()
+    if periodic is None:
+        periodic = randoms_a is None
+    spec = make_spec(n, box, origin, assign, interlace, periodic, los_dir, observer)
+    kb = B.npc_kbins(float(kbins[0]), float(kbins[1]), int(kbins[2]))
+    emask = sum(1 << int(l) for l in ells)
+    length = max(int(B.npc_power_out_len(C.byref(kb), emask, 0)), 1)
+    da, db = make_catalog(data_a, keep), make_catalog(data_b, keep)
+    ra, rb = make_catalog(randoms_a, keep), make_catalog(randoms_b, keep)
+    ctx = context(device)
+    args = (ctx, C.byref(spec), C.byref(da), C.byref(ra) if ra else None, C.byref(db),
+            C.byref(rb) if rb else None, C.byref(kb), emask, _prec(precision))
+    if out is not None:
+        B.check(B.npc_cross_power_multipoles(*args, C.c_void_p(out.data_ptr()), 1), ctx)
+        return out
+    buf = np.zeros(length)
+    B.check(B.npc_cross_power_multipoles(*args, buf.ctypes.data_as(C.c_void_p), 0), ctx)
+    res = unpack_power(buf, kbins[2], ells, ())
+    raw = buf[-8:]
+    res["scalars"] = dict(zip(("alpha_a", "I22_ab", "alpha_b", "zero", "I22_a", "I22_b", "sum_w_a", "sum_w_b"), raw))
+    return res
+
+
 def unpack_power(buf, nbins, ells, modified):
     buf = np.asarray(buf)
     res = {"k_eff": buf[0:nbins].copy(), "nmodes": buf[nbins:2 * nbins].copy(), "P": {}, "Pmod": {}}

@@ -65,6 +65,9 @@ _sig = {
                                        _P(npc_kbins), C.c_uint32, C.c_uint32, C.c_int, C.c_void_p,
                                        C.c_int32]),
     "npc_power_out_len": (C.c_int64, [_P(npc_kbins), C.c_uint32, C.c_uint32]),
+    "npc_cross_power_multipoles": (C.c_int, [C.c_void_p, _P(npc_mesh_spec), _P(npc_catalog), _P(npc_catalog),
+                                             _P(npc_catalog), _P(npc_catalog), _P(npc_kbins), C.c_uint32, C.c_int,
+                                             C.c_void_p, C.c_int32]),
     "npc_bispectrum": (C.c_int, [C.c_void_p, _P(npc_mesh_spec), _P(npc_catalog), _P(npc_catalog),
                                  _P(npc_kbins), C.c_uint32, C.c_uint32, C.c_int32, C.c_int, C.c_void_p,
                                  C.c_int32]),

@@ -286,9 +286,9 @@ npc_status finish_output(npc_ctx* ctx, const double* dev, double* out, int64_t l
 }
 
 // The estimator after validation, staging and the catalogue scalars (device output `dev_out`).
-npc_status power_core(npc_ctx* ctx, const npc_mesh_spec& ms, const DevCatalog& d, const DevCatalog* r,
-                      const npc_kbins& kb, uint32_t ell_mask, uint32_t modified_mask, int prec, const double* sc,
-                      double* dev_out) {
+// Field list and pass parameters of one P_l measurement (m >= 0 fields per phase, Table 1).
+static PowerPlan make_power_plan(npc_ctx* ctx, const npc_mesh_spec& ms, const npc_kbins& kb, uint32_t ell_mask,
+                                 uint32_t modified_mask) {
   const npc_mesh_spec* mesh = &ms;
   const npc_kbins* bins = &kb;
   const int n = mesh->n;
@@ -345,18 +345,71 @@ npc_status power_core(npc_ctx* ctx, const npc_mesh_spec& ms, const DevCatalog& d
   ctx->stats.n_transforms = ntr;
   ctx->stats.n_r2c_equivalent = nr2c;
   ctx->stats.n_phases = nphase;
+  return plan;
+}
 
+npc_status power_core(npc_ctx* ctx, const npc_mesh_spec& ms, const DevCatalog& d, const DevCatalog* r,
+                      const npc_kbins& kb, uint32_t ell_mask, uint32_t modified_mask, int prec, const double* sc,
+                      double* dev_out) {
+  const PowerPlan plan = make_power_plan(ctx, ms, kb, ell_mask, modified_mask);
+  const int n = ms.n;
+  const int nphase = plan.nphase;
+  const Geom g = make_geom(ms);
   const size_t rs = prec == NPC_PREC_FP64 ? 8 : 4;
   const size_t ncell = (size_t)n * n * n;
   void *ma, *mb = nullptr, *half;
   NPC_TRY(ws_get(ctx, "mesh.a", rs * ncell, &ma));
   if (nphase == 2) NPC_TRY(ws_get(ctx, "mesh.b", rs * ncell, &mb));
-  NPC_TRY(ws_get(ctx, "half", 2 * rs * (size_t)fl.nf * (n / 2) * n * n, &half));
+  NPC_TRY(ws_get(ctx, "half", 2 * rs * (size_t)plan.fl.nf * (n / 2) * n * n, &half));
   NPC_TRY(stage_mark(ctx, "alloc"));
-  NPC_TRY(launch_paint(ctx, d, r, *mesh, 1, prec, sc, ma, mb));
+  NPC_TRY(launch_paint(ctx, d, r, ms, 1, prec, sc, ma, mb));
   NPC_TRY(stage_mark(ctx, "paint_fold"));
   NPC_TRY(run_forward_transforms(ctx, prec, plan, g, ma, mb, half));
-  NPC_TRY(run_power_contract(ctx, prec, plan, *mesh, *bins, half, sc, dev_out));
+  NPC_TRY(run_power_contract(ctx, prec, plan, ms, kb, half, sc, dev_out));
+  return NPC_OK;
+}
+
+// Cross multipoles: tracer B's m >= 0 fields and tracer A's F_0 (one field per phase) transformed
+// into one half-spectrum buffer, then one contraction of Re[F_0^A F_l^B*].
+static npc_status power_cross_core(npc_ctx* ctx, const npc_mesh_spec& ms, const DevCatalog& da,
+                                   const DevCatalog* ra, const DevCatalog& db, const DevCatalog* rb,
+                                   const npc_kbins& kb, uint32_t ell_mask, int prec, const double* sca,
+                                   const double* scb, const double* scx, double* dev_out) {
+  PowerPlan plan = make_power_plan(ctx, ms, kb, ell_mask, 0);
+  const int nfb = plan.fl.nf;
+  PowerPlan plan_a = plan;
+  plan_a.fl.nf = 0;
+  for (int ph = 0; ph < plan.nphase; ++ph) {
+    Comp c;
+    c.phase = (int8_t)ph; c.ell = 0; c.m = 0; c.part = PART_ONE;
+    plan_a.fl.f[plan_a.fl.nf++] = c;
+  }
+  if (nfb + plan_a.fl.nf > NPC_MAX_FIELDS) return set_err(ctx, NPC_ERR_UNSUPPORTED, "cross: too many fields");
+  const int n = ms.n;
+  const Geom g = make_geom(ms);
+  const size_t rs = prec == NPC_PREC_FP64 ? 8 : 4;
+  const size_t ncell = (size_t)n * n * n;
+  const size_t fbytes = 2 * rs * (size_t)(n / 2) * n * n;   // one field's half spectrum
+  void *ma, *mb = nullptr, *half;
+  NPC_TRY(ws_get(ctx, "mesh.a", rs * ncell, &ma));
+  if (plan.nphase == 2) NPC_TRY(ws_get(ctx, "mesh.b", rs * ncell, &mb));
+  NPC_TRY(ws_get(ctx, "half", fbytes * (size_t)(nfb + plan_a.fl.nf), &half));
+  NPC_TRY(stage_mark(ctx, "alloc"));
+  NPC_TRY(launch_paint(ctx, db, rb, ms, 1, prec, scb, ma, mb));
+  NPC_TRY(stage_mark(ctx, "paint_fold"));
+  NPC_TRY(run_forward_transforms(ctx, prec, plan, g, ma, mb, half));
+  NPC_TRY(launch_paint(ctx, da, ra, ms, 1, prec, sca, ma, mb));
+  NPC_TRY(stage_mark(ctx, "paint_fold_a"));
+  NPC_TRY(run_forward_transforms(ctx, prec, plan_a, g, ma, mb, (char*)half + fbytes * nfb));
+  for (int f = 0; f < plan_a.fl.nf; ++f) {
+    Comp c = plan_a.fl.f[f];
+    c.tracer = 1;
+    plan.fl.f[plan.fl.nf++] = c;
+  }
+  plan.cross = 1;
+  ctx->stats.n_transforms += 1;
+  ctx->stats.n_r2c_equivalent += 1;
+  NPC_TRY(run_power_contract(ctx, prec, plan, ms, kb, half, scx, dev_out));
   return NPC_OK;
 }
 
@@ -521,6 +574,53 @@ npc_status npc_power_multipoles(npc_ctx* ctx, const npc_mesh_spec* mesh, const n
   double* dev_out = out;
   if (!out_on_device) NPC_TRY(ws_get(ctx, "power.out", sizeof(double) * out_len, (void**)&dev_out));
   NPC_TRY(power_core(ctx, *mesh, d, randoms ? &r : nullptr, *bins, ell_mask, modified_mask, prec, sc, dev_out));
+  NPC_TRY(finish_output(ctx, dev_out, out, out_len, out_on_device));
+  NPC_TRY(stage_mark(ctx, "download"));
+  return end_call(ctx);
+}
+
+npc_status npc_cross_power_multipoles(npc_ctx* ctx, const npc_mesh_spec* mesh, const npc_catalog* data_a,
+                                      const npc_catalog* randoms_a, const npc_catalog* data_b,
+                                      const npc_catalog* randoms_b, const npc_kbins* bins, uint32_t ell_mask,
+                                      npc_precision prec, double* out, int32_t out_on_device) {
+  if (!ctx) return NPC_ERR_INVALID_ARG;
+  begin_call(ctx);
+  NPC_TRY(check_spec(ctx, mesh));
+  NPC_TRY(check_bins(ctx, bins));
+  if (!out) return set_err(ctx, NPC_ERR_INVALID_ARG, "out is NULL");
+  const int64_t out_len = npc_power_out_len(bins, ell_mask, 0);
+  if (out_len == 0) return set_err(ctx, NPC_ERR_INVALID_ARG, "ell_mask must use bits 0,2,4");
+  if (prec != NPC_PREC_FP64 && prec != NPC_PREC_MIXED) return set_err(ctx, NPC_ERR_INVALID_ARG, "bad precision");
+  if (prec == NPC_PREC_FP64 && mesh->n > 256) return set_err(ctx, NPC_ERR_UNSUPPORTED, "FP64 precision supports n <= 256");
+  NPC_TRY(check_catalog(ctx, data_a, "data_a", false));
+  NPC_TRY(check_catalog(ctx, data_b, "data_b", false));
+  if (mesh->periodic) {
+    if (randoms_a || randoms_b) return set_err(ctx, NPC_ERR_INVALID_ARG, "periodic box takes no randoms");
+  } else {
+    if (!randoms_a || !randoms_b) return set_err(ctx, NPC_ERR_INVALID_ARG, "survey geometry needs both randoms");
+    NPC_TRY(check_catalog(ctx, randoms_a, "randoms_a", true));
+    NPC_TRY(check_catalog(ctx, randoms_b, "randoms_b", true));
+    if (randoms_a->n == 0 || randoms_b->n == 0) return set_err(ctx, NPC_ERR_NUMERIC, "empty random catalogue");
+  }
+  if (data_a->n == 0 || data_b->n == 0) return set_err(ctx, NPC_ERR_NUMERIC, "empty data catalogue (I22 = 0)");
+  NPC_CUDA(ctx, cudaSetDevice(ctx->device));
+  DevCatalog da, ra, db, rb;
+  NPC_TRY(stage_catalog(ctx, data_a, "data", &da));
+  if (randoms_a) NPC_TRY(stage_catalog(ctx, randoms_a, "rand", &ra));
+  NPC_TRY(stage_catalog(ctx, data_b, "data_b", &db));
+  if (randoms_b) NPC_TRY(stage_catalog(ctx, randoms_b, "rand_b", &rb));
+  double* sc;
+  NPC_TRY(ws_get(ctx, "scalars.cross", sizeof(double) * SC_COUNT * 3, (void**)&sc));
+  double *sca = sc, *scb = sc + SC_COUNT, *scx = sc + 2 * SC_COUNT;
+  NPC_TRY(stage_mark(ctx, "upload"));
+  NPC_TRY(launch_catalog_scalars(ctx, da, randoms_a ? &ra : nullptr, mesh->box, sca));
+  NPC_TRY(launch_catalog_scalars(ctx, db, randoms_b ? &rb : nullptr, mesh->box, scb));
+  NPC_TRY(launch_cross_scalars(ctx, sca, scb, scx));
+  NPC_TRY(stage_mark(ctx, "scalars"));
+  double* dev_out = out;
+  if (!out_on_device) NPC_TRY(ws_get(ctx, "power.out", sizeof(double) * out_len, (void**)&dev_out));
+  NPC_TRY(power_cross_core(ctx, *mesh, da, randoms_a ? &ra : nullptr, db, randoms_b ? &rb : nullptr, *bins, ell_mask,
+                           prec, sca, scb, scx, dev_out));
   NPC_TRY(finish_output(ctx, dev_out, out, out_len, out_on_device));
   NPC_TRY(stage_mark(ctx, "download"));
   return end_call(ctx);

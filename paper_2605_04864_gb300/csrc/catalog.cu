@@ -596,7 +596,28 @@ npc_status paint_impl(npc_ctx* ctx, const DevCatalog& d, const DevCatalog* r, co
   return launch_fold<T>(ctx, tiles, g, nphase, sc, sub, mesh_a, mesh_b);
 }
 
+// Scalars of a cross spectrum from those of tracers A and B: the normalisation sqrt(I22^A I22^B)
+// in the I22 slot, no shot noise, and the tracers' own values for the output (layout in npc.h).
+__global__ void k_cross_scalars(const double* __restrict__ sa, const double* __restrict__ sb, double* __restrict__ sx) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int i = 0; i < SC_COUNT; ++i) sx[i] = 0.0;
+  sx[SC_ALPHA] = sa[SC_ALPHA];
+  sx[SC_I22] = sqrt(sa[SC_I22] * sb[SC_I22]);
+  sx[SC_I33] = sb[SC_ALPHA];
+  sx[SC_N0] = 0.0;
+  sx[SC_S3] = sa[SC_I22];
+  sx[SC_SUMWG] = sb[SC_I22];
+  sx[SC_SUMWR] = sa[SC_SUMWG];
+  sx[SC_SUMW2] = sb[SC_SUMWG];
+}
+
 }  // namespace
+
+npc_status launch_cross_scalars(npc_ctx* ctx, const double* sa, const double* sb, double* sx) {
+  k_cross_scalars<<<1, 32, 0, ctx->stream>>>(sa, sb, sx);
+  NPC_LAUNCH(ctx);
+  return NPC_OK;
+}
 
 npc_status launch_catalog_scalars(npc_ctx* ctx, const DevCatalog& d, const DevCatalog* r, double box,
                                   double* dev_scalars) {

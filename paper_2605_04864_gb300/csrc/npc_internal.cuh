@@ -129,6 +129,7 @@ struct Comp {          // one real field: mesh phase x weight function
   int8_t phase;        // 0 or 1
   int8_t ell, m;       // Y_l^m (m >= 0)
   int8_t part;         // PART_RE / PART_IM of Y_l^m, PART_ONE (global LOS), PART_ZERO
+  int8_t tracer = 0;   // 1: F_0 of the first tracer A of a cross spectrum (the others are B's)
 };
 
 constexpr int NPC_MAX_FIELDS = 40;  // real fields per call (2 phases x 15 for l <= 4, + spare)
@@ -258,6 +259,8 @@ struct DevCatalog {   // catalogue resident on the device
 
 npc_status launch_catalog_scalars(npc_ctx* ctx, const DevCatalog& d, const DevCatalog* r, double box,
                                   double* dev_scalars);
+// Cross-spectrum scalars from tracers A and B (output slots documented with npc_cross_power_multipoles).
+npc_status launch_cross_scalars(npc_ctx* ctx, const double* sa, const double* sb, double* sx);
 
 // Paint the FKP field (weight_power 1) or the N-field (2) on 1 or 2 interlacing phases.
 // meshes: nphase pointers to n^3 arrays of T (layout [z][y][x]).
@@ -282,6 +285,7 @@ struct PowerPlan {
   int assign;
   int kz_keep;          // forward passes keep kz < kz_keep (0: all, n/2)
   int row_n2max;        // > 0: the y pass may skip rows (ky, kz) with ky^2 + kz^2 above it
+  int cross;            // 1: cross spectrum, P_l = Re<F_0^A F_l^B*> with A's fields marked `tracer`
 };
 
 // Catalogue -> P_l after validation, staging and the catalogue scalars `sc` (api.cu).

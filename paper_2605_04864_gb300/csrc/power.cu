@@ -401,7 +401,9 @@ struct ContractParams {
   int nf;
   FieldCoef fc[NPC_MAX_FIELDS];
   int ny;                       // Y table rows: 0, 3 (l = 2) or 8 (l = 2 and 4)
-  int nacc;                     // F accumulators (1..3)
+  int nacc;                     // F accumulators: nacc_b of F_0, F_2, F_4, then F_0^A if cross
+  int nacc_b;
+  int acc_a;                    // accumulator of F_0^A (cross spectra), -1 otherwise
   int nphase;
   int nrounds;                  // rounds of G field rows
   int phase_pure;               // 1: every group sees one mesh phase only (group parity when nphase = 2)
@@ -577,40 +579,36 @@ k_fft_x_contract(const cplx<T>* __restrict__ half, const ContractParams P, const
       for (int s = 0; s < MAX_SUMS; ++s) vals[s] = T(0);
       if (bin >= 0) {
         const T wgt = kz > 0 ? T(2) : T(1);
-        C F0 = cmk(T(0), T(0)), F2 = cmk(T(0), T(0)), F4 = cmk(T(0), T(0));
-        if (P.phase_pure) {
-          // groups of phase a (even g, or all with one phase) and of phase b (odd g), summed in g order
-          C B0 = cmk(T(0), T(0)), B2 = cmk(T(0), T(0)), B4 = cmk(T(0), T(0));
-          const int gstep = P.nphase == 2 ? 2 : 1;
-          for (int gg = 0; gg < G; gg += gstep) {
+        C F0 = cmk(T(0), T(0)), F2 = cmk(T(0), T(0)), F4 = cmk(T(0), T(0)), FA = cmk(T(0), T(0));
+        // sum of the group accumulators g0, g0 + gstep, ... in g order
+        auto gsum = [&](int g0, int gstep, C& s0, C& s2, C& s4, C& sa) {
+          for (int gg = g0; gg < G; gg += gstep) {
             const C* fg = facc + (size_t)gg * P.nacc * N + j;
-            F0 = cadd(F0, fg[0]);
-            if (P.nacc > 1) F2 = cadd(F2, fg[N]);
-            if (P.nacc > 2) F4 = cadd(F4, fg[2 * N]);
+            s0 = cadd(s0, fg[0]);
+            if (P.nacc_b > 1) s2 = cadd(s2, fg[N]);
+            if (P.nacc_b > 2) s4 = cadd(s4, fg[2 * N]);
+            if (P.acc_a >= 0) sa = cadd(sa, fg[(size_t)P.acc_a * N]);
           }
+        };
+        if (P.phase_pure) {
+          // groups of phase a (even g, or all with one phase) and of phase b (odd g)
+          gsum(0, P.nphase == 2 ? 2 : 1, F0, F2, F4, FA);
           const T faj = fa[j];
           F0 = cscale(F0, faj);
           F2 = cscale(F2, faj);
           F4 = cscale(F4, faj);
+          FA = cscale(FA, faj);
           if (P.nphase == 2) {
-            for (int gg = 1; gg < G; gg += 2) {
-              const C* fg = facc + (size_t)gg * P.nacc * N + j;
-              B0 = cadd(B0, fg[0]);
-              if (P.nacc > 1) B2 = cadd(B2, fg[N]);
-              if (P.nacc > 2) B4 = cadd(B4, fg[2 * N]);
-            }
+            C B0 = cmk(T(0), T(0)), B2 = cmk(T(0), T(0)), B4 = cmk(T(0), T(0)), BA = cmk(T(0), T(0));
+            gsum(1, 2, B0, B2, B4, BA);
             const C fbj = fb[j];
             F0 = cadd(F0, cmul(B0, fbj));
             F2 = cadd(F2, cmul(B2, fbj));
             F4 = cadd(F4, cmul(B4, fbj));
+            FA = cadd(FA, cmul(BA, fbj));
           }
         } else {
-          for (int gg = 0; gg < G; ++gg) {
-            const C* fg = facc + (size_t)gg * P.nacc * N + j;
-            F0 = cadd(F0, fg[0]);
-            if (P.nacc > 1) F2 = cadd(F2, fg[N]);
-            if (P.nacc > 2) F4 = cadd(F4, fg[2 * N]);
-          }
+          gsum(0, 1, F0, F2, F4, FA);
         }
         const T fi = T(i);
         const T kk = sqrt(fi * fi + fjy * fjy + fkz * fkz);
@@ -625,7 +623,8 @@ k_fft_x_contract(const cplx<T>* __restrict__ half, const ContractParams P, const
           T v = T(0);
           if (s < P.nell) {
             const C b = sel(P.ell_list[s]);
-            v = wgt * (F0.x * b.x + F0.y * b.y);
+            const C a = P.acc_a >= 0 ? FA : F0;   // cross: F_0 of tracer A against F_l of B
+            v = wgt * (a.x * b.x + a.y * b.y);
           } else if (s < P.nell + P.nll) {
             const C a = sel(P.lla[s - P.nell]), b = sel(P.llb[s - P.nell]);
             v = wgt * (a.x * b.x + a.y * b.y);
@@ -877,10 +876,21 @@ npc_status contract_impl(npc_ctx* ctx, const PowerPlan& plan, const npc_mesh_spe
   P.nf = plan.fl.nf;
   P.nphase = plan.nphase;
   P.ny = 0;
+  int req_internal = plan.ells_mask;
+  if (plan.mod_mask) req_internal |= 1 | 4 | 16;
+  P.need2 = (req_internal & 4) ? 1 : 0;
+  P.need4 = (req_internal & 16) ? 1 : 0;
+  P.nacc_b = plan.global_los ? 1 : (P.need4 ? 3 : (P.need2 ? 2 : 1));
+  P.acc_a = plan.cross ? P.nacc_b : -1;
+  P.nacc = P.nacc_b + (plan.cross ? 1 : 0);
+  if (plan.cross && plan.mod_mask)
+    return set_err(ctx, NPC_ERR_UNSUPPORTED, "cross spectra: no modified multipoles");
   for (int f = 0; f < plan.fl.nf; ++f) {
     const Comp c = plan.fl.f[f];
     FieldCoef fc;
-    fc.acc = (int8_t)(c.ell / 2);
+    fc.acc = (int8_t)(c.tracer ? P.acc_a : c.ell / 2);
+    if (c.tracer && (!plan.cross || c.part != PART_ONE))
+      return set_err(ctx, NPC_ERR_INVALID_ARG, "x pass: tracer-A field must be an unweighted F_0");
     fc.phase = c.phase;
     fc.part = c.part;
     fc.yidx = -1;
@@ -931,8 +941,6 @@ npc_status contract_impl(npc_ctx* ctx, const PowerPlan& plan, const npc_mesh_spe
   }
   P.nbins = kb.nbins;
   P.nell = 0;
-  int req_internal = plan.ells_mask;
-  if (plan.mod_mask) req_internal |= 1 | 4 | 16;
   for (int l = 0; l <= 4; l += 2)
     if (req_internal & (1 << l)) P.ell_list[P.nell++] = l;
   P.nll = 0;
@@ -940,9 +948,6 @@ npc_status contract_impl(npc_ctx* ctx, const PowerPlan& plan, const npc_mesh_spe
   if (plan.mod_mask & ((1 << 6) | (1 << 8))) { P.lla[P.nll] = 4; P.llb[P.nll] = 2; P.nll++; }
   if (plan.mod_mask & (1 << 8)) { P.lla[P.nll] = 4; P.llb[P.nll] = 4; P.nll++; }
   P.nsum = P.nell + P.nll + 2;
-  P.need2 = (req_internal & 4) ? 1 : 0;
-  P.need4 = (req_internal & 16) ? 1 : 0;
-  P.nacc = plan.global_los ? 1 : (P.need4 ? 3 : (P.need2 ? 2 : 1));
   P.global_los = plan.global_los;
   for (int a = 0; a < 3; ++a) P.los[a] = plan.los[a];
   P.assign = plan.assign;
