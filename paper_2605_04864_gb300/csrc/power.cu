@@ -215,14 +215,19 @@ template <typename T> struct ZGeom {
   T dz;                     // z step between consecutive elements of a thread (TPF cells)
 };
 
+// Keeps a value where it is computed: the per-pair factors below must not be hoisted out of the
+// pair loop (all fifteen pairs' factors would then stay live in registers).
+__device__ __forceinline__ void keep_here(float& x) { asm volatile("" : "+f"(x)); }
+__device__ __forceinline__ void keep_here(double& x) { asm volatile("" : "+d"(x)); }
+
 template <typename T, int N, int TX, int L, int M, int KIND>
 __device__ __forceinline__ void std_inputs(cplx<T> (&v)[8], const T* tileA, const T* tileB, int c, int t,
                                            const ZGeom<T>& zg, const YNorm& nrm) {
   constexpr int TPF = N / 8;
+  if constexpr (KIND == 0) {
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int z = t + q * TPF;
-    if constexpr (KIND == 0) {
+    for (int q = 0; q < 8; ++q) {
+      const int z = t + q * TPF;
       const T fa = tileA[z * TX + c], fb = tileB[z * TX + c];
       if constexpr (L == 0) {
         v[q] = cmk(fa, fb);
@@ -240,14 +245,30 @@ __device__ __forceinline__ void std_inputs(cplx<T> (&v)[8], const T* tileA, cons
         }
         v[q] = cmk(fa * ya, fb * yb);
       }
-    } else {
-      constexpr int ph = KIND - 1;
-      const T f = (ph ? tileB : tileA)[z * TX + c];
+    }
+  } else {
+    // Y_lm(xhat) = norm Q(uz) (px + i py)^m / r^m: the column factor norm (px + i py)^m is formed
+    // once per pair, each element needs 1/r, uz and the power r^-m
+    constexpr int ph = KIND - 1;
+    T cr = ynorm<T>(nrm, L * (L + 1) / 2 + M), ci = T(0);
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+      const T nr = cr * zg.px[ph] - ci * zg.py[ph];
+      ci = cr * zg.py[ph] + ci * zg.px[ph];
+      cr = nr;
+    }
+    keep_here(cr);
+    keep_here(ci);
+    const T* tile = ph ? tileB : tileA;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int z = t + q * TPF;
       const T pz = zg.pz0[ph] + T(q) * zg.dz;
       const T inv = rsqrt(zg.pxy2[ph] + pz * pz);
-      T re, im;
-      ylm_ct<T, L, M>(zg.px[ph] * inv, zg.py[ph] * inv, pz * inv, nrm, re, im);
-      v[q] = cmk(f * re, f * im);
+      T s = tile[z * TX + c] * ylm_q<T, L, M>(pz * inv);
+#pragma unroll
+      for (int j = 0; j < M; ++j) s *= inv;
+      v[q] = cmk(s * cr, s * ci);
     }
   }
 }
@@ -308,16 +329,19 @@ k_fwd_z_std(const T* __restrict__ mesh_a, const T* __restrict__ mesh_b, cplx<T>*
 #pragma unroll
     for (int q = 0; q < 8; ++q) work[(t + q * TPF) * TX + c] = v[q];
     __syncthreads();
-    for (int i = tid; i < KZ * TX; i += blockDim.x) {
-      const int kz = i / TX, cc = i % TX;
-      const C z1 = work[kz * TX + cc];
-      const C z2 = cconj(work[((N - kz) % N) * TX + cc]);
-      const C a = cscale(cadd(z1, z2), T(0.5));
-      const C d = csub(z1, z2);
-      const C b = cmk(T(0.5) * d.y, T(-0.5) * d.x);
-      const size_t gi = ((size_t)kz * N + y) * N + x0 + cc;
-      half[(size_t)(2 * p) * fstride + gi] = a;
-      half[(size_t)(2 * p + 1) * fstride + gi] = b;
+    // split the packed pair into its two half spectra; thread tid owns (kz0 + j KZSTEP, cc)
+    {
+      constexpr int KZSTEP = ColCfg<N>::THREADS / TX;
+      const int kz0 = tid / TX, cc = tid % TX;
+      C* o0 = half + (size_t)(2 * p) * fstride + ((size_t)kz0 * N + y) * N + x0 + cc;
+      C* o1 = o0 + fstride;
+      for (int kz = kz0; kz < KZ; kz += KZSTEP, o0 += (size_t)KZSTEP * N * N, o1 += (size_t)KZSTEP * N * N) {
+        const C z1 = work[kz * TX + cc];
+        const C z2 = cconj(work[(kz == 0 ? 0 : N - kz) * TX + cc]);
+        *o0 = cscale(cadd(z1, z2), T(0.5));
+        const C d = csub(z1, z2);
+        *o1 = cmk(T(0.5) * d.y, T(-0.5) * d.x);
+      }
     }
     __syncthreads();
   }
