@@ -218,6 +218,8 @@ def bispectrum(spec, data, randoms, kbins, scoc_ells=(0, 2), tripo_ells=(0, 2), 
         if shot == "fft":
             res["shot_B_fft"] = S.fft_method_shot_noise(spec, X0, nf[0], kbins, tri, sc["I33"], sc["S3"],
                                                         scoc_ells)
+            res["shot_BB_fft"] = S.compressed_fft_method_shot(spec, X0, nf[0], kbins, prs, sc["I33"], sc["S3"],
+                                                              tripo_ells)
     return res
 
 

@@ -40,6 +40,12 @@ back once, hence the -2.  ``fft_method_shot_noise`` enumerates the triplets (the
 out; tiny meshes).  Pinned by the exact identity it must satisfy: for uncompensated fields of at
 most two objects every closed triplet draws two legs from one object, so the raw estimator equals
 N_fft; with three objects the difference is the sum over distinct triples (tests).
+
+The same construction for the compressed B_l0l (l on the k3 leg, q3 = -q1 - q2 over all modes):
+  Ta = sum L_l(mu3) X_0(q3) N_0^*(q3),  Tb = sum L_l(mu3) X_0(q2) N_0^*(q2),
+  Tc = sum L_l(mu3) X_0(q1) N_0^*(q1),  Td = sum L_l(mu3)      over q1 in b_i, q2 in b_j,
+  N_fft(i,j) = (2l+1)/(I33 N_i N_j) Re[Ta + Tb + Tc - 2 S Td]
+(``compressed_fft_method_shot``), pinned by the same two- and three-object identities.
 """
 from __future__ import annotations
 
@@ -157,4 +163,32 @@ def fft_method_shot_noise(spec, X0, N0, kbins, tri, i33, s3, ells):
         tot = np.real(t["t23"] + t["t12"] + t["t13"]) - 2.0 * s3 * t["ntl"]
         with np.errstate(invalid="ignore", divide="ignore"):
             res[ell] = np.where(t["nt"] > 0, (2 * ell + 1) * tot / (i33 * np.where(t["nt"] > 0, t["nt"], 1)), 0.0)
+    return res
+
+
+def compressed_fft_method_shot(spec, X0, N0, kbins, prs, i33, s3, ells):
+    """N_fft(i, j) of the compressed B_l0l for every pair and each l in ells, by enumerating the
+    (q1, q2) pairs with q3 = -q1 - q2 taken on the grid as the estimator does."""
+    from .bispec import _mode_lists
+
+    n = spec["n"]
+    b, lists = _mode_lists(spec, kbins)
+    cnt = np.array([len(x) for x in lists], dtype=np.float64)
+    xn = X0 * np.conj(N0)
+    res = {}
+    for ell in ells:
+        lmu = H.legendre(ell, _mu(spec))
+        out = []
+        for i, j in prs:
+            q1, q2 = lists[i], lists[j]
+            q3 = (-(q1[:, None, :] + q2[None, :, :])) % n
+            i1, i2 = q1 % n, q2 % n
+            l3 = lmu[q3[..., 0], q3[..., 1], q3[..., 2]]
+            ta = np.sum(l3 * xn[q3[..., 0], q3[..., 1], q3[..., 2]])
+            tb = np.sum(l3 * xn[i2[:, 0], i2[:, 1], i2[:, 2]][None, :])
+            tc = np.sum(l3 * xn[i1[:, 0], i1[:, 1], i1[:, 2]][:, None])
+            td = np.sum(l3)
+            den = i33 * cnt[i] * cnt[j]
+            out.append((2 * ell + 1) * np.real(ta + tb + tc - 2.0 * s3 * td) / den if den > 0 else 0.0)
+        res[ell] = np.array(out)
     return res

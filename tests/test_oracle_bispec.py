@@ -255,3 +255,63 @@ def test_fft_shot_leaves_the_distinct_triples(ell):
     distinct = _distinct_triple_part(spec, pos, w, kb, tri, ell)
     scale = np.max(np.abs(raw))
     np.testing.assert_allclose(raw - sn, distinct, rtol=0, atol=1e-11 * scale)
+
+
+def _distinct_pair_part(spec, pos, w, kbins, prs, ell):
+    """(2l+1)/(N_i N_j) sum over q1 in b_i, q2 in b_j (q3 = -q1-q2 on the grid) of L_l(mu3)
+    sum_{a, b, c distinct} w_a w_b w_c e^{-i(q1.x_a + q2.x_b + q3.x_c)}, by explicit loops."""
+    from oracle import harmonics as Hm
+
+    n, box = spec["n"], spec["box"]
+    kf = 2 * pi / box
+    b, _ = M.bin_index(n, box, *kbins)
+    ii = M.int_freqs(n)
+    modes = [[] for _ in range(kbins[2])]
+    for a in range(n):
+        for c in range(n):
+            for e in range(n):
+                if b[a, c, e] >= 0:
+                    modes[b[a, c, e]].append((ii[a], ii[c], ii[e]))
+    out = []
+    for i, j in prs:
+        tot = 0.0
+        for q1 in modes[i]:
+            for q2 in modes[j]:
+                q3 = tuple(int(ii[(-q1[d] - q2[d]) % n]) for d in range(3))
+                r = np.sqrt(sum(x * x for x in q3))
+                l3 = float(Hm.legendre(ell, q3[2] / r if r > 0 else 0.0))
+                s = 0.0
+                for xa in range(len(w)):
+                    for xb in range(len(w)):
+                        for xc in range(len(w)):
+                            if len({xa, xb, xc}) < 3:
+                                continue
+                            ph = sum(kf * (q1[d] * pos[xa][d] + q2[d] * pos[xb][d] + q3[d] * pos[xc][d])
+                                     for d in range(3))
+                            s += w[xa] * w[xb] * w[xc] * np.cos(ph)
+                tot += l3 * s
+        out.append((2 * ell + 1) * tot / (len(modes[i]) * len(modes[j])))
+    return np.array(out)
+
+
+@pytest.mark.parametrize("ell", [0, 2])
+@pytest.mark.parametrize("nobj", [2, 3])
+def test_compressed_fft_shot_object_identities(ell, nobj):
+    """Compressed B_l0l: with two objects the raw estimator equals the FFT-method shot noise; with
+    three, the difference is the distinct-triple sum (explicit loops)."""
+    from oracle import shot as S
+
+    spec = _periodic_spec(16, 100.0)   # k_max = 3.5 k_f < n k_f / 4: q1 + q2 stays off the Nyquist planes
+    kf = 2 * pi / 100.0
+    kb = (0.5 * kf, 1.0 * kf, 3)
+    prs = B.pairs(kb)
+    pos = [(13.7, 42.1, 77.3), (61.2, 5.9, 30.4), (88.8, 70.2, 12.6)][:nobj]
+    w = [0.8, 1.7, 1.1][:nobj]
+    X, N = _object_fields(spec, pos, w)
+    Xl = B.los_field(spec, X, ell)
+    raw, _, _ = B.compressed_fft(spec, X, Xl, kb, prs, 1.0, ell)
+    s3 = sum(x ** 3 for x in w)
+    sn = S.compressed_fft_method_shot(spec, X, N, kb, prs, 1.0, s3, [ell])[ell]
+    scale = np.max(np.abs(raw))
+    want = 0.0 if nobj == 2 else _distinct_pair_part(spec, pos, w, kb, prs, ell)
+    np.testing.assert_allclose(raw - sn, want, rtol=0, atol=1e-11 * scale)
