@@ -195,10 +195,10 @@ npc_status npc_cross_power_multipoles(npc_ctx* ctx, const npc_mesh_spec* mesh, c
  * scoc_ell_mask: bits 0, 2 request B_0, B_2 (l on the first, smallest side).
  * tripo_ell_mask: bits 0, 2 request the compressed B_000, B_202.
  * shot: 1 subtracts the analytic shot noise (Sec. 5.4, thin-shell integrals) and reports it;
- *   2 uses the FFT method for B_l instead (Sec. 5.4.2: the exact sums over the closed triplets of the
- *   two-object terms, sum_x I_a I_b G_c with the shell fields G_c of X_0 N_0^* and L_2-weighted
- *   indicators for l = 2, about twice the triple-product work; B_l0l keeps the analytic form);
- *   0 leaves the raw estimates.
+ *   2 uses the FFT method instead (Sec. 5.4.2): the exact sums of the two-object terms over the
+ *   closed triplets of B_l (sum_x I_a I_b G_c with shell fields G_c of X_0 N_0^*, L_2-weighted
+ *   indicators for l = 2) and over the bin pairs of B_l0l (full-range fields of L_l X_0 N_0^* and of
+ *   L_l), about twice the triple-product work; 0 leaves the raw estimates.
  * Output `out` (float64), length from npc_bispectrum_layout():
  *   [ns][ntri]  B_l          [ns][ntri]  shot noise of B_l      [ntri] N_T (closed triplets)
  *   [nt][npair] B_l0l        [nt][npair] shot noise of B_l0l    [nbins] N_modes

@@ -405,9 +405,9 @@ struct TripleArgs {
   int npair;
   int ncol;         // used columns
   int nstage;       // distinct fields staged per chunk
-  int stage_field[3 * NB_MAX + 2];  // R index of staged slot s
+  int stage_field[3 * NB_MAX + 8];  // R index of staged slot s
   int a_slot[2][NB_MAX];            // staged slot of A_i per family
-  int b_slot[NB_MAX];               // staged slot of B_j
+  int b_slot[2][NB_MAX];            // staged slot of B_j per family
   int c_slot[TRI_COLS];             // staged slot of column c (-1: zero column)
   int nf_cols;                      // columns 0 .. nf_cols-1 are F_k (k = column), the rest G^(l)
   int64_t ncell;
@@ -456,7 +456,7 @@ k_triple(const float* __restrict__ R, const TripleArgs A, const int* __restrict_
         const int fam = r / A.npair, p = row_pair[r % A.npair];
         const int pij = pair_ij[p];
         sa[mt][h] = A.a_slot[fam][pij & 0xffff];
-        sb[mt][h] = A.b_slot[pij >> 16];
+        sb[mt][h] = A.b_slot[fam][pij >> 16];
         orow[mt][h] = fam * A.npair + p;
       }
     }
@@ -563,7 +563,7 @@ k_triple_f64(const double* __restrict__ R, const TripleArgs A, const int* __rest
   double acc = 0.0;
   if (cs >= 0) {
     const double* fa = R + (size_t)A.stage_field[A.a_slot[fam][pij & 0xffff]] * A.ncell;
-    const double* fb = R + (size_t)A.stage_field[A.b_slot[pij >> 16]] * A.ncell;
+    const double* fb = R + (size_t)A.stage_field[A.b_slot[fam][pij >> 16]] * A.ncell;
     const double* fc = R + (size_t)A.stage_field[cs] * A.ncell;
     const int64_t per = (A.ncell + gridDim.x - 1) / gridDim.x;
     const int64_t beg = (int64_t)blockIdx.x * per, end = min(A.ncell, beg + per);
@@ -597,15 +597,18 @@ struct FinalArgs {
   double kmin, dk;
   int part_nw_cross;    // partial records of the cross-spectrum kernel
   // FFT-method shot noise (shot = 2): partials of sum_x I_a I_b G_c (family 0) and
-  // sum_x I2_a I_b G_c (family 1) in s1, of sum_x I_a I_b G2_c in s2; columns c = 0 .. nb-1
-  int s1_nparts, s1_nrows, s2_nparts, s2_nrows;
+  // sum_x I2_a I_b G_c (family 1) in s1 (columns c < nb; then, for the compressed multipoles e,
+  // sum_x I_a I_b SF_e at nb + e and sum_x I_a I_b LF_e at nb + ntripo + e), of sum_x I_a I_b G2_c
+  // in s2 (nb columns), of sum_x I_a G_b LF_e (family 0) and sum_x G_a I_b LF_e (family 1) in s3
+  int s1_nparts, s1_nrows, s1_ncol, s2_nparts, s2_nrows, s3_nparts, s3_nrows, s3_ncol;
 };
 
 __global__ void k_bispec_finalize(const int* __restrict__ tri, const int* __restrict__ pair_ij,
                                   const double* __restrict__ part_main, const double* __restrict__ nt_sums,
                                   const double* __restrict__ cross_m, const double* __restrict__ cross_q,
                                   const double* __restrict__ part_s1, const double* __restrict__ part_s2,
-                                  const double* __restrict__ nt2_sums, const FinalArgs F,
+                                  const double* __restrict__ part_s3, const double* __restrict__ nt2_sums,
+                                  const FinalArgs F,
                                   const double* __restrict__ sc, double* __restrict__ out) {
   const int nb = F.nb;
   const double i33 = sc[SC_I33], s3 = sc[SC_S3];
@@ -632,11 +635,14 @@ __global__ void k_bispec_finalize(const int* __restrict__ tri, const int* __rest
     return p + b - a;
   };
   // sum over CTAs of an FFT-method partial (family fam, pair p, column c)
-  auto shot_sum = [&](const double* part, int nparts, int nrows, int fam, int p, int c) {
+  auto shot_sum = [&](const double* part, int nparts, int nrows, int ncol, int fam, int p, int c) {
     double v = 0;
-    for (int q = 0; q < nparts; ++q) v += part[((size_t)q * nrows + fam * F.npair + p) * nb + c];
+    for (int q = 0; q < nparts; ++q) v += part[((size_t)q * nrows + fam * F.npair + p) * ncol + c];
     return v;
   };
+  auto ps1 = [&](int fam, int p, int c) { return shot_sum(part_s1, F.s1_nparts, F.s1_nrows, F.s1_ncol, fam, p, c); };
+  auto ps2 = [&](int fam, int p, int c) { return shot_sum(part_s2, F.s2_nparts, F.s2_nrows, nb, fam, p, c); };
+  auto ps3 = [&](int fam, int p, int c) { return shot_sum(part_s3, F.s3_nparts, F.s3_nrows, F.s3_ncol, fam, p, c); };
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int nthreads = gridDim.x * blockDim.x;
   for (int t = tid; t < F.ntri; t += nthreads) {
@@ -662,14 +668,10 @@ __global__ void k_bispec_finalize(const int* __restrict__ tri, const int* __rest
         const int pik = pair_index(i, k), pjk = pair_index(j, k);
         double tsum, ntl;
         if (l == 0) {
-          tsum = shot_sum(part_s1, F.s1_nparts, F.s1_nrows, 0, pjk, i) +
-                 shot_sum(part_s1, F.s1_nparts, F.s1_nrows, 0, p, k) +
-                 shot_sum(part_s1, F.s1_nparts, F.s1_nrows, 0, pik, j);
+          tsum = ps1(0, pjk, i) + ps1(0, p, k) + ps1(0, pik, j);
           ntl = snt;
         } else {
-          tsum = shot_sum(part_s2, F.s2_nparts, F.s2_nrows, 0, pjk, i) +
-                 shot_sum(part_s1, F.s1_nparts, F.s1_nrows, 1, p, k) +
-                 shot_sum(part_s1, F.s1_nparts, F.s1_nrows, 1, pik, j);
+          tsum = ps2(0, pjk, i) + ps1(1, p, k) + ps1(1, pik, j);
           ntl = nt2_sums[(size_t)p * nb + k];
         }
         sn = (2 * l + 1) * (tsum - 2.0 * s3 * ntl) / (i33 * snt);
@@ -691,7 +693,12 @@ __global__ void k_bispec_finalize(const int* __restrict__ tri, const int* __rest
       for (int c = 0; c < F.nparts; ++c) sg += part_main[((size_t)c * F.nrows + p) * F.ncol + nb + e];
       const double raw = (ni > 0 && nj > 0) ? (2 * l + 1) * sg / (i33 * ni * nj * (double)F.ncell) : 0.0;
       double sn = 0.0;
-      if (F.shot && ni > 0 && nj > 0) {
+      if (F.shot == 2 && ni > 0 && nj > 0) {
+        // FFT method: Ta + Tb + Tc - 2 S Td over the (q1, q2) pairs of the two bins
+        const double ta = ps1(0, p, nb + e), td = ps1(0, p, nb + F.ntripo + e);
+        const double tb = ps3(0, p, e), tc = ps3(1, p, e);
+        sn = (2 * l + 1) * (ta + tb + tc - 2.0 * s3 * td) / (i33 * ni * nj * (double)F.ncell);
+      } else if (F.shot && ni > 0 && nj > 0) {
         const double ci = centre(i), cj = centre(j);
         const double sgn = (l % 2) ? -1.0 : 1.0;
         double v = (l == 0 ? s3 : 0.0);
@@ -1037,7 +1044,10 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
   int ng = 0;
   if (wantG0) { add(0, 0, -1, KG, 3); ng++; }
   if (wantG2) { add(0, 1, -1, KG, 3); ng++; }
-  int iS0 = -1, iS2 = -1, iI2 = -1;
+  int iS0 = -1, iS2 = -1, iI2 = -1, iSF = -1, iLF = -1;
+  int ntl = 0, tls[2] = {0, 0};   // compressed multipoles requested
+  for (int l = 0; l <= 2; l += 2)
+    if (tripo_mask & (1 << l)) tls[ntl++] = l;
   if (fftshot) {
     iS0 = (int)fl.size();
     for (int b = 0; b < nb; ++b) add(2, 0, b, Ks, 4);            // sum_{q in b} X_0 N_0^* e^{iqx}
@@ -1046,6 +1056,12 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
       for (int b = 0; b < nb; ++b) add(2, 1, b, Ks, 5);          // the same with L_2(mu)
       iI2 = (int)fl.size();
       for (int b = 0; b < nb; ++b) add(1, 1, b, Ks, 6);          // L_2(mu) indicators
+    }
+    if (ntl > 0) {   // compressed estimator: full-range fields of L_l X_0 N_0^* and of L_l
+      iSF = (int)fl.size();
+      for (int e = 0; e < ntl; ++e) add(2, tls[e] == 2 ? 1 : 0, -1, KG, 7);
+      iLF = (int)fl.size();
+      for (int e = 0; e < ntl; ++e) add(1, tls[e] == 2 ? 1 : 0, -1, KG, 8);
     }
   }
   const int nfield = (int)fl.size();
@@ -1154,11 +1170,11 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
     for (int q = 0; q < TRI_COLS; ++q) a.c_slot[q] = -1;
     a.nf_cols = nb;
     if (indicator) {
-      for (int b = 0; b < nb; ++b) a.a_slot[0][b] = a.b_slot[b] = a.c_slot[b] = stage_of(iI + b);
+      for (int b = 0; b < nb; ++b) a.a_slot[0][b] = a.b_slot[0][b] = a.b_slot[1][b] = a.c_slot[b] = stage_of(iI + b);
       a.nrows = npair;
       a.ncol = nb;
     } else {
-      for (int b = 0; b < nb; ++b) a.a_slot[0][b] = a.b_slot[b] = a.c_slot[b] = stage_of(b);
+      for (int b = 0; b < nb; ++b) a.a_slot[0][b] = a.b_slot[0][b] = a.b_slot[1][b] = a.c_slot[b] = stage_of(b);
       if (want2)
         for (int b = 0; b < nb; ++b) a.a_slot[1][b] = stage_of(iF2 + b);
       for (int l = 0; l < ng; ++l) a.c_slot[nb + l] = stage_of(iG + l);
@@ -1184,7 +1200,7 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
     for (int q = 0; q < TRI_COLS; ++q) a.c_slot[q] = -1;
     for (int b = 0; b < nb; ++b) {
       a.a_slot[0][b] = stage_of(fieldA0 + b);
-      a.b_slot[b] = stage_of(iI + b);
+      a.b_slot[0][b] = a.b_slot[1][b] = stage_of(iI + b);
       a.c_slot[b] = stage_of(fieldC + b);
     }
     if (fieldA1 >= 0)
@@ -1193,9 +1209,43 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
     a.nrows = npair * (fieldA1 >= 0 ? 2 : 1);
     a.ncol = nb;
   };
-  TripleArgs ts1{}, ts2{}, tn2{};
+  TripleArgs ts1{}, ts2{}, tn2{}, ts3{};
   if (fftshot) {
     setup_shot(ts1, iI, want2 ? iI2 : -1, iS0);   // sum I_a I_b S0_c and sum I2_a I_b S0_c
+    if (ntl > 0) {
+      // compressed estimator, same I_a I_b rows: columns nb + e: sum I_a I_b SF_l (Ta),
+      // nb + ntl + e: sum I_a I_b LF_l (Td)
+      auto stage_of = [&](int field) {
+        for (int q = 0; q < ts1.nstage; ++q)
+          if (ts1.stage_field[q] == field) return q;
+        ts1.stage_field[ts1.nstage] = field;
+        return ts1.nstage++;
+      };
+      for (int e = 0; e < ntl; ++e) {
+        ts1.c_slot[nb + e] = stage_of(iSF + e);
+        ts1.c_slot[nb + ntl + e] = stage_of(iLF + e);
+      }
+      ts1.ncol = nb + 2 * ntl;
+      // rows (I_a, S0_b) and (S0_a, I_b), columns LF_l: Tb and Tc
+      ts3 = TripleArgs{};
+      ts3.npair = npair;
+      ts3.ncell = (int64_t)ncs;
+      auto stage3 = [&](int field) {
+        for (int q = 0; q < ts3.nstage; ++q)
+          if (ts3.stage_field[q] == field) return q;
+        ts3.stage_field[ts3.nstage] = field;
+        return ts3.nstage++;
+      };
+      for (int q = 0; q < TRI_COLS; ++q) ts3.c_slot[q] = -1;
+      for (int b = 0; b < nb; ++b) {
+        ts3.a_slot[0][b] = ts3.b_slot[1][b] = stage3(iI + b);
+        ts3.b_slot[0][b] = ts3.a_slot[1][b] = stage3(iS0 + b);
+      }
+      for (int e = 0; e < ntl; ++e) ts3.c_slot[e] = stage3(iLF + e);
+      ts3.nf_cols = 0;
+      ts3.nrows = 2 * npair;
+      ts3.ncol = ntl;
+    }
     if (want2) setup_shot(ts2, iI, -1, iS2);      // sum I_a I_b S2_c
     if (want2) setup_shot(tn2, iI2, -1, iI);      // sum I2_a I_b I_c (cached)
   }
@@ -1247,16 +1297,21 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
   }
   NPC_TRY(launch(ta, grid, part));
   NPC_TRY(stage_mark(ctx, "triple"));
-  double *part_s1 = nullptr, *part_s2 = nullptr;
-  int gs1 = 0, gs2 = 0;
+  double *part_s1 = nullptr, *part_s2 = nullptr, *part_s3 = nullptr;
+  int gs1 = 0, gs2 = 0, gs3 = 0;
   if (fftshot) {
     gs1 = grid_for(ts1);
-    NPC_TRY(ws_get(ctx, "bis.s1part", sizeof(double) * (size_t)gs1 * ts1.nrows * nb, (void**)&part_s1));
+    NPC_TRY(ws_get(ctx, "bis.s1part", sizeof(double) * (size_t)gs1 * ts1.nrows * ts1.ncol, (void**)&part_s1));
     NPC_TRY(launch(ts1, gs1, part_s1));
     if (want2) {
       gs2 = grid_for(ts2);
       NPC_TRY(ws_get(ctx, "bis.s2part", sizeof(double) * (size_t)gs2 * ts2.nrows * nb, (void**)&part_s2));
       NPC_TRY(launch(ts2, gs2, part_s2));
+    }
+    if (ntl > 0) {
+      gs3 = grid_for(ts3);
+      NPC_TRY(ws_get(ctx, "bis.s3part", sizeof(double) * (size_t)gs3 * ts3.nrows * ts3.ncol, (void**)&part_s3));
+      NPC_TRY(launch(ts3, gs3, part_s3));
     }
     NPC_TRY(stage_mark(ctx, "shot_triple"));
   }
@@ -1283,11 +1338,15 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
   fa.dk = kb.dk;
   fa.s1_nparts = gs1;
   fa.s1_nrows = ts1.nrows;
+  fa.s1_ncol = ts1.ncol;
   fa.s2_nparts = gs2;
   fa.s2_nrows = ts2.nrows;
+  fa.s3_nparts = gs3;
+  fa.s3_nrows = ts3.nrows;
+  fa.s3_ncol = ts3.ncol;
   k_bispec_finalize<<<std::max(1, (std::max(ntri, npair) + 127) / 128), 128, 0, ctx->stream>>>(
       (const int*)(dtab + t_tri), (const int*)(dtab + t_pij), part, nt_sums, cross_m, cross_q, part_s1, part_s2,
-      nt2_sums, fa, sc, dev_out);
+      part_s3, nt2_sums, fa, sc, dev_out);
   NPC_LAUNCH(ctx);
   NPC_TRY(stage_mark(ctx, "finalize"));
   (void)out_len;

@@ -101,9 +101,10 @@ def test_fft_method_shot_noise_periodic(api, prec, tol):
         assert np.max(e) < tol, ("B", l, np.max(e))
         e = np.abs(res["shot_B"][l] - orc["shot_B_fft"][l]) / np.maximum(np.abs(orc["shot_B_fft"][l]), scale_t)
         assert np.max(e) < tol, ("shot_B_fft", l, np.max(e))
-    scale_p = np.abs(orc["BB"][0]) + np.abs(orc["shot_BB"][0])
-    e = np.abs(res["shot_BB"][0] - orc["shot_BB"][0]) / np.maximum(np.abs(orc["shot_BB"][0]), scale_p)
-    assert np.max(e) < tol
+    scale_p = np.abs(orc["BB"][0]) + np.abs(orc["shot_BB_fft"][0])
+    for l in (0, 2):
+        e = np.abs(res["shot_BB"][l] - orc["shot_BB_fft"][l]) / np.maximum(np.abs(orc["shot_BB_fft"][l]), scale_p)
+        assert np.max(e) < tol, ("shot_BB_fft", l, np.max(e))
     # the exact and thin-shell forms estimate the same noise: close for the monopole, not equal
     d = np.abs(orc["shot_B_fft"][0] - orc["shot_B"][0]) / np.abs(orc["shot_B"][0])
     assert 0 < np.max(d) < 0.2
@@ -117,13 +118,16 @@ def test_fft_method_shot_noise_survey_monopole(api):
     g, r, origin = make_survey_catalogs(20000, 200000, box, 900.0, 32, seed=73, fkp_p0=1e4)
     kf = 2 * np.pi / box
     kb = (2 * kf, 1.5 * kf, 3)
-    res = api.bispectrum(g, n=32, box=box, kbins=kb, scoc_ells=(0,), tripo_ells=(), precision="fp64",
+    res = api.bispectrum(g, n=32, box=box, kbins=kb, scoc_ells=(0,), tripo_ells=(0,), precision="fp64",
                          origin=origin, randoms=r, shot="fft")
     spec = dict(n=32, box=box, origin=tuple(origin), assign=3, interlace=1, los="global",
                 los_dir=(0.0, 0.0, 1.0), periodic=0)
-    orc = OB.bispectrum(spec, g, r, kb, (0,), (), shot="fft")
+    orc = OB.bispectrum(spec, g, r, kb, (0,), (0,), shot="fft")
     scale = np.abs(orc["B"][0]) + np.abs(orc["shot_B_fft"][0])
     e = np.abs(res["shot_B"][0] - orc["shot_B_fft"][0]) / np.maximum(np.abs(orc["shot_B_fft"][0]), scale)
+    assert np.max(e) < 1e-10
+    scale = np.abs(orc["BB"][0]) + np.abs(orc["shot_BB_fft"][0])
+    e = np.abs(res["shot_BB"][0] - orc["shot_BB_fft"][0]) / np.maximum(np.abs(orc["shot_BB_fft"][0]), scale)
     assert np.max(e) < 1e-10
 
 
