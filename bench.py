@@ -303,7 +303,7 @@ def bispec_leg(args, world, rank, barrier, max_over_ranks):
                        "assign": "TSC", "interlace": True},
             "stages_ms": stages, "gpu_launches": launches * args.steps,
             "fft_method_shot": {"value": world * ntri.value * nmult / (ms_fft / 1e3), "ms_per_step": ms_fft,
-                                "note": "shot noise of B_l by the FFT method (exact triplet sums)"},
+                                "note": "shot noise of B_l and B_l0l by the FFT method (exact sums of the two-object terms)"},
             "triple_product": "3xTF32 split hi+lo tensor-core products (mma.sync m16n8k8), FP32 within 128-cell chunks, FP64 across chunks"}
 
 

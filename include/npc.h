@@ -187,8 +187,12 @@ npc_status npc_cross_power_multipoles(npc_ctx* ctx, const npc_mesh_spec* mesh, c
 
 /* Bispectrum multipoles (Sec. 2.2 Eq. bi_sco; Sec. 4 Eq. new_bispec; Sec. 5.4 shot noise) ------
  * Periodic box (mesh->periodic = 1, randoms = NULL) with a global line of sight (mesh->los = 1) for l = 2;
- * survey geometry (mesh->periodic = 0, randoms required) for the monopoles B_0 and B_000 only,
- * which do not depend on the line of sight.
+ * survey geometry (mesh->periodic = 0, randoms required): the monopoles need no line of sight; for
+ * l = 2 either the global one (los = 1) or the line of sight from mesh->observer to each grid point
+ * (los = 0), where X_2 is the Yamamoto field of Eq. hand from Y_2m-weighted transforms (the
+ * compressed B_202 carries it on the k3 leg) and the analytic shot noise uses the Yamamoto N-field
+ * and the catalogue moments sum_p w_p^3 Y_2m(xhat_p) for its self term (shot = 2 is not available
+ * there: NPC_ERR_UNSUPPORTED).
  * Triangles: bins i <= j <= k closing at their centres, c_k <= c_i + c_j, c_b = kmin+(b+1/2)dk,
  * in lexicographic (i, j, k) order; pairs: i <= j in lexicographic order.  The largest bin edge
  * must not exceed k_N/2 (the closure would alias otherwise), else NPC_ERR_UNSUPPORTED.

@@ -193,18 +193,28 @@ def compressed_explicit(spec, meshes, kbins, prs, i33, ell):
 
 
 def bispectrum(spec, data, randoms, kbins, scoc_ells=(0, 2), tripo_ells=(0, 2), shot=True):
-    """Full oracle measurement (global line of sight): B_l, N_T, compressed B_l0l, shot noise
-    (analytic; shot="fft" adds the FFT-method shot noise of B_l as ``shot_B_fft``)."""
+    """Full oracle measurement: B_l, N_T, compressed B_l0l, shot noise (analytic; shot="fft" adds
+    the FFT-method shot noise as ``shot_B_fft`` / ``shot_BB_fft``, global line of sight only).
+    spec["los"] = "global": X_l = L_l(qhat . los) X_0; otherwise (survey geometry, line of sight to
+    each grid point from spec["observer"]) X_l is the Yamamoto field F_l of Eq. hand."""
     from . import power as P
     from . import shot as S
 
     sc = P.catalog_scalars(data, randoms, spec["box"])
     meshes = P.fkp_meshes(spec, data, randoms, sc)
-    fields, _ = P.fields_plain(spec, meshes, [0])
-    X0 = fields[0]
+    ells = sorted(set(scoc_ells) | set(tripo_ells) | {0})
+    endpoint = spec.get("los", "endpoint") != "global"
+    if endpoint:
+        # survey geometry with the line of sight to each grid point: X_l is the Yamamoto field
+        fields, _ = P.fields_plain(spec, meshes, ells)
+        X0 = fields[0]
+        Xl = {ell: fields[ell] for ell in ells}
+    else:
+        fields, _ = P.fields_plain(spec, meshes, [0])
+        X0 = fields[0]
+        Xl = {ell: los_field(spec, X0, ell) for ell in ells}
     tri = triangles(kbins)
     prs = pairs(kbins)
-    Xl = {ell: los_field(spec, X0, ell) for ell in set(scoc_ells) | set(tripo_ells)}
     B, nt, raw = scoccimarro_fft(spec, X0, Xl, kbins, tri, sc["I33"], scoc_ells)
     BB = {}
     for ell in tripo_ells:
@@ -212,9 +222,13 @@ def bispectrum(spec, data, randoms, kbins, scoc_ells=(0, 2), tripo_ells=(0, 2), 
     res = dict(tri=tri, pairs=prs, B=B, NT=nt, BB=BB, raw=raw, scalars=sc)
     if shot:
         nmeshes = P.fkp_meshes(spec, data, randoms, sc, weight_power=2)
-        nf, _ = P.fields_plain(spec, nmeshes, [0])
+        nf, _ = P.fields_plain(spec, nmeshes, ells if endpoint else [0])
+        survey = None
+        if endpoint:
+            survey = {ell: dict(Xl=Xl[ell], Nl=nf[ell], moments=S.ylm_moments(spec, data, randoms, sc["alpha"], ell))
+                      for ell in ells}
         res["shot_B"], res["shot_BB"], res["shot_parts"] = S.analytic_shot_noise(
-            spec, X0, nf[0], kbins, tri, prs, sc, scoc_ells, tripo_ells)
+            spec, X0, nf[0], kbins, tri, prs, sc, scoc_ells, tripo_ells, survey)
         if shot == "fft":
             res["shot_B_fft"] = S.fft_method_shot_noise(spec, X0, nf[0], kbins, tri, sc["I33"], sc["S3"],
                                                         scoc_ells)

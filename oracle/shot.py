@@ -64,15 +64,49 @@ def _mu(spec):
         return np.where(kk > 0, (kx * d[0] + ky * d[1] + kz * d[2]) / np.where(kk > 0, kk, 1.0), 0.0)
 
 
-def shell_terms(spec, X0, N0, kbins, ell, s3):
-    """(H_l, Q_l, N_mode) on the given bins."""
+def shell_terms(spec, X0, N0, kbins, ell, s3, survey=None):
+    """(H_l, Q_l, N_mode) on the given bins.
+
+    Global line of sight: X_l = L_l(mu) X_0 and F_l^w = L_l(mu) N_0, so H_l = Q_l with the self term
+    S <L_l(mu)>.  Survey geometry (``survey`` = dict(Xl, Nl, moments)): Q_l = <Re X_l N_0^*> - S_l,
+    H_l = <Re X_0 N_l^*> - S_l with X_l, N_l the Yamamoto fields of the FKP and N-fields, and the
+    self term S_l(k) = sum_p c_p <L_l(qhat . xhat_p)>_k = 4 pi/(2l+1) sum_m <Y_lm(qhat)>_k C_lm^*,
+    C_lm = sum_p c_p Y_lm(xhat_p), c_p = w^3 (data), -alpha^3 w^3 (randoms), xhat_p the direction of
+    object p from the observer (reading: the objects' own directions)."""
     b, _ = M.bin_index(spec["n"], spec["box"], *kbins)
     nb = kbins[2]
-    lmu = H.legendre(ell, _mu(spec))
-    cross, cnt = M.bin_average(lmu * np.real(X0 * np.conj(N0)), b, nb)
-    lavg, _ = M.bin_average(lmu, b, nb)
-    hval = cross - s3 * lavg
-    return hval, hval.copy(), cnt
+    if survey is None:
+        lmu = H.legendre(ell, _mu(spec))
+        cross, cnt = M.bin_average(lmu * np.real(X0 * np.conj(N0)), b, nb)
+        lavg, _ = M.bin_average(lmu, b, nb)
+        hval = cross - s3 * lavg
+        return hval, hval.copy(), cnt
+    (kx, ky, kz), _ = M.kvectors(spec["n"], spec["box"])
+    kh = np.stack(np.broadcast_arrays(kx, ky, kz), axis=-1)
+    self_t = np.zeros(nb)
+    for m in range(-ell, ell + 1):
+        y = H.ylm(ell, m, kh)
+        yr, _ = M.bin_average(np.real(y), b, nb)
+        yi, _ = M.bin_average(np.imag(y), b, nb)
+        cm = survey["moments"][m]
+        self_t += 4.0 * np.pi / (2 * ell + 1) * np.real((yr + 1j * yi) * np.conj(cm))
+    q, cnt = M.bin_average(np.real(survey["Xl"] * np.conj(N0)), b, nb)
+    h, _ = M.bin_average(np.real(X0 * np.conj(survey["Nl"])), b, nb)
+    return h - self_t, q - self_t, cnt
+
+
+def ylm_moments(spec, data, randoms, alpha, ell):
+    """C_lm = sum_g w^3 Y_lm(xhat_g) - alpha^3 sum_r w^3 Y_lm(xhat_r) for m = -l .. l, xhat the
+    direction from the observer."""
+    obs = np.asarray(spec.get("observer", (0.0, 0.0, 0.0)), dtype=np.float64)
+    out = {}
+    for m in range(-ell, ell + 1):
+        v = np.sum(np.asarray(data.w, np.float64) ** 3 * H.ylm(ell, m, np.asarray(data.pos, np.float64) - obs))
+        if randoms is not None:
+            v -= alpha ** 3 * np.sum(np.asarray(randoms.w, np.float64) ** 3
+                                     * H.ylm(ell, m, np.asarray(randoms.pos, np.float64) - obs))
+        out[m] = v
+    return out
 
 
 def qgrid(kbins):
@@ -83,7 +117,8 @@ def qgrid(kbins):
     return (0.0, dk, nq)
 
 
-def analytic_shot_noise(spec, X0, N0, kbins, tri, prs, sc, scoc_ells, tripo_ells):
+def analytic_shot_noise(spec, X0, N0, kbins, tri, prs, sc, scoc_ells, tripo_ells, survey=None):
+    """survey: None (global line of sight) or dict ell -> dict(Xl, Nl, moments) (see shell_terms)."""
     kmin, dk, nb = kbins
     c = np.array([kmin + (b + 0.5) * dk for b in range(nb)])
     i33, s3 = sc["I33"], sc["S3"]
@@ -91,8 +126,9 @@ def analytic_shot_noise(spec, X0, N0, kbins, tri, prs, sc, scoc_ells, tripo_ells
     cq = np.array([(m + 0.5) * dk for m in range(qb[2])])
     shot_B, shot_BB, parts = {}, {}, {}
     for ell in sorted(set(scoc_ells) | set(tripo_ells)):
-        hl, ql, _ = shell_terms(spec, X0, N0, kbins, ell, s3)
-        hq, qq, nq = shell_terms(spec, X0, N0, qb, ell, s3)
+        sv = None if survey is None else survey[ell]
+        hl, ql, _ = shell_terms(spec, X0, N0, kbins, ell, s3, sv)
+        hq, qq, nq = shell_terms(spec, X0, N0, qb, ell, s3, sv)
         parts[ell] = dict(H=hl, Q=ql, Qq=qq, Nq=nq)
         if ell in scoc_ells:
             out = np.empty(len(tri))

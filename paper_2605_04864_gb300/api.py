@@ -215,13 +215,14 @@ def stage_times(device=0, cap=64):
 
 def bispectrum(data, n, box, kbins, scoc_ells=(0, 2), tripo_ells=(0, 2), shot=True, assign=3, interlace=1,
                los_dir=(0.0, 0.0, 1.0), precision="mixed", origin=(0.0, 0.0, 0.0), device=0, out=None,
-               randoms=None):
+               randoms=None, observer=(0.0, 0.0, 0.0)):
     """Scoccimarro B_l and compressed B_l0l: periodic box with a global line of sight, or (with
-    ``randoms``) survey geometry for the monopoles.  shot: False/0 raw, True/1 analytic shot noise,
-    "fft"/2 the FFT-method shot noise for B_l (analytic for B_l0l)."""
+    ``randoms``) survey geometry, where ``los_dir=None`` puts the line of sight from ``observer``
+    to each grid point (Yamamoto X_2).  shot: False/0 raw, True/1 analytic shot noise, "fft"/2 the
+    FFT-method shot noise."""
     keep = _Keep()
     shot = 2 if shot == "fft" else int(shot)
-    spec = make_spec(n, box, origin, assign, interlace, 1 if randoms is None else 0, los_dir)
+    spec = make_spec(n, box, origin, assign, interlace, 1 if randoms is None else 0, los_dir, observer)
     kb = B.npc_kbins(float(kbins[0]), float(kbins[1]), int(kbins[2]))
     sm = sum(1 << int(l) for l in scoc_ells)
     tm = sum(1 << int(l) for l in tripo_ells)

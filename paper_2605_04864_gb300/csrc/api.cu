@@ -671,8 +671,10 @@ npc_status npc_bispectrum(npc_ctx* ctx, const npc_mesh_spec* mesh, const npc_cat
     if (mesh->los != 1 && !mono)
       return set_err(ctx, NPC_ERR_UNSUPPORTED, "bispectrum: l = 2 needs a global line of sight");
   } else {
-    // survey geometry: the monopoles B_0 and B_000 do not depend on the line of sight
-    if (!mono) return set_err(ctx, NPC_ERR_UNSUPPORTED, "bispectrum: survey geometry supports l = 0 only");
+    // survey geometry: the monopoles need no line of sight; l = 2 takes the global one (los = 1) or
+    // the line of sight to each grid point (Yamamoto X_2), the latter with the analytic shot noise
+    if (!mono && mesh->los != 1 && shot == 2)
+      return set_err(ctx, NPC_ERR_UNSUPPORTED, "bispectrum: FFT-method shot noise of l = 2 needs a global line of sight");
     if (!randoms) return set_err(ctx, NPC_ERR_INVALID_ARG, "survey geometry needs randoms");
     NPC_TRY(check_catalog(ctx, randoms, "randoms", true));
     if (randoms->n == 0) return set_err(ctx, NPC_ERR_NUMERIC, "empty random catalogue");

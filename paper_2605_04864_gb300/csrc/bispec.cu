@@ -109,6 +109,162 @@ k_fft_x_combine(const cplx<T>* __restrict__ half, int nout, int nphase, int KZ, 
 }
 
 // ------------------------------------------------------------------------------------------
+// 2b. survey geometry with the line of sight to each grid point (l = 2): the x pass assembles
+//     X_0 and the Yamamoto field X_2 = 4 pi/5 [Y_20 A_20 + 2 sum_{m=1,2} (ReY_2m A_2m + ImY_2m B_2m)]
+//     (khat at the mode; Eq. hand with the m < 0 terms folded onto m > 0) from the twelve fields of
+//     the standard l <= 2 layout, interlaced and compensated.  Field order (phase a, b):
+//     0 a, 1 b: F;  2 a, 3 b: F Y_20;  4, 5: a Re/Im F Y_21;  6, 7: b Re/Im F Y_21;
+//     8, 9: a Re/Im F Y_22;  10, 11: b Re/Im F Y_22;  without interlacing the six fields
+//     F, F Y_20, Re/Im F Y_21, Re/Im F Y_22 in that order.
+// ------------------------------------------------------------------------------------------
+template <typename T, int N>
+__global__ void __launch_bounds__(BT)
+k_fft_x_assemble2(const cplx<T>* __restrict__ half, int nphase, int KZ, int KY, int assign, const YNorm nrm,
+                  const cplx<T>* __restrict__ tw_g, cplx<T>* __restrict__ X0o, cplx<T>* __restrict__ X2o) {
+  using C = cplx<T>;
+  constexpr int TPF = N / 8;
+  constexpr int G = BT / TPF > 0 ? BT / TPF : 1;
+  constexpr int NP = row_pad_len<N>();
+  constexpr int NFMAX = 12;
+  const int NF = nphase == 2 ? 12 : 6;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  C* phs = tw + N;
+  C* rows = phs + N;
+  T* winv = reinterpret_cast<T*>(rows + (size_t)(NFMAX + RowGroups<N, BT>::NBUF) * NP);
+  const int tid = threadIdx.x;
+  for (int i = tid; i < N; i += blockDim.x) {
+    tw[i] = tw_g[i];
+    const T a = T(M_PI) * T(i - N / 2) / T(N);
+    phs[i] = cmk(cos(a), sin(a));
+  }
+  for (int i = tid; i <= N / 2; i += blockDim.x) winv[i] = T(1) / sinc_p<T>(T(M_PI) * T(i) / T(N), assign);
+  __syncthreads();
+  const int g = tid / TPF, t = tid % TPF;
+  const int nyr = 2 * KY + 1;
+  const int nrows = KZ * nyr;
+  const size_t fstride = (size_t)KZ * N * N;
+  const T c2 = T(4.0 * M_PI / 5.0);
+  // component c (F, F Y_20, Re/Im F Y_21, Re/Im F Y_22): field of phase a and of phase b
+  constexpr int IA2[6] = {0, 2, 4, 5, 8, 9}, IB2[6] = {1, 3, 6, 7, 10, 11};
+  const T n20 = ynorm<T>(nrm, 3), n21 = ynorm<T>(nrm, 4), n22 = ynorm<T>(nrm, 5);
+  for (int r = blockIdx.x; r < nrows; r += gridDim.x) {
+    const int kz = r / nyr;
+    const int jy = r % nyr - KY;
+    const int ky = jy < 0 ? jy + N : jy;
+    for (int f0 = 0; f0 < NF; f0 += G) {
+      const int f = f0 + g;
+      const bool live = g < G && f < NF;
+      C v[8];
+      if (live) {
+        const C* src = half + (size_t)f * fstride + ((size_t)kz * N + ky) * N;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = src[t + q * TPF];
+      } else {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = cmk(T(0), T(0));
+      }
+      RowView<C> rv{rows + (size_t)(live ? f : NFMAX + g) * NP};
+      fft_block<N, -1>(v, t, tw, rv, RowSync<N, BT>::make(g));
+      if (live) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) rv.st(t + q * TPF, v[q]);
+      }
+    }
+    __syncthreads();
+    for (int kx = tid; kx < N; kx += blockDim.x) {
+      const int i = kx < N / 2 ? kx : kx - N;
+      const int ai = i < 0 ? -i : i, aj = jy < 0 ? -jy : jy;
+      const T iw = winv[ai] * winv[aj] * winv[kz];
+      const int jp = RowView<C>::idx(kx);
+      const C ph = cmul(cmul(phs[i + N / 2], phs[jy + N / 2]), phs[kz + N / 2]);
+      auto comb = [&](int c) {   // interlaced (two phases), compensated component c
+        if (nphase == 1) return cscale(rows[(size_t)c * NP + jp], iw);
+        const C x = cadd(rows[(size_t)IA2[c] * NP + jp], cmul(ph, rows[(size_t)IB2[c] * NP + jp]));
+        return cscale(x, T(0.5) * iw);
+      };
+      // Y_2m(khat): norm Q(uz) (ux + i uy)^m
+      const T fi = T(i), fj = T(jy), fk = T(kz);
+      const T r2 = fi * fi + fj * fj + fk * fk;
+      const T inv = r2 > T(0) ? rsqrt(r2) : T(0);
+      const T ux = fi * inv, uy = fj * inv, uz = r2 > T(0) ? fk * inv : T(1);
+      const T y20 = n20 * (T(1.5) * uz * uz - T(0.5));
+      const C e1 = cmk(ux, uy);
+      const C y21 = cscale(e1, n21 * T(-3) * uz);
+      const C y22 = cscale(cmul(e1, e1), n22 * T(3));
+      C x2 = cscale(comb(1), y20);
+      x2 = cadd(x2, cscale(comb(2), T(2) * y21.x));
+      x2 = cadd(x2, cscale(comb(3), T(2) * y21.y));
+      x2 = cadd(x2, cscale(comb(4), T(2) * y22.x));
+      x2 = cadd(x2, cscale(comb(5), T(2) * y22.y));
+      const size_t o = ((size_t)kz * N + ky) * N + kx;
+      X0o[o] = comb(0);
+      X2o[o] = cscale(x2, c2);
+    }
+    __syncthreads();
+  }
+}
+
+// Catalogue moments of the survey self term: c_p Y_2m(xhat_p) for m = 0, 1, 2 as five reals
+// (Y_20, Re Y_21, Im Y_21, Re Y_22, Im Y_22), c_p = w_p^3, per-block float64 partials in a fixed
+// order; xhat_p from the observer.
+constexpr int YM_BLOCKS = 512, YM_THREADS = 256;
+template <typename P>
+__global__ void __launch_bounds__(YM_THREADS)
+k_cat_ylm2(const P* __restrict__ pos, const P* __restrict__ w, int64_t n, double ox, double oy, double oz,
+           const YNorm nrm, double* __restrict__ part) {
+  __shared__ double sh[5][YM_THREADS];
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t beg = (int64_t)blockIdx.x * chunk, end = min(n, beg + chunk);
+  double a[5] = {0, 0, 0, 0, 0};
+  const double n20 = nrm.v[3], n21 = nrm.v[4], n22 = nrm.v[5];
+  for (int64_t i = beg + threadIdx.x; i < end; i += blockDim.x) {
+    const double x = (double)pos[3 * i] - ox, y = (double)pos[3 * i + 1] - oy, z = (double)pos[3 * i + 2] - oz;
+    const double r2 = x * x + y * y + z * z;
+    if (!(r2 > 0)) continue;
+    const double inv = 1.0 / sqrt(r2);
+    const double ux = x * inv, uy = y * inv, uz = z * inv;
+    const double wi = w ? (double)w[i] : 1.0;
+    const double c = wi * wi * wi;
+    a[0] += c * n20 * (1.5 * uz * uz - 0.5);
+    a[1] += c * n21 * (-3.0 * uz) * ux;
+    a[2] += c * n21 * (-3.0 * uz) * uy;
+    a[3] += c * n22 * 3.0 * (ux * ux - uy * uy);
+    a[4] += c * n22 * 3.0 * (2.0 * ux * uy);
+  }
+  for (int k = 0; k < 5; ++k) sh[k][threadIdx.x] = a[k];
+  __syncthreads();
+  for (int off = YM_THREADS / 2; off > 0; off >>= 1) {
+    if (threadIdx.x < off)
+      for (int k = 0; k < 5; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x < 5) part[blockIdx.x * 5 + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+// C_2m = data sums - alpha^3 random sums, fixed order (one warp)
+__global__ void k_cat_ylm2_final(const double* __restrict__ pd, const double* __restrict__ pr, int nblk,
+                                 int have_randoms, const double* __restrict__ sc, double* __restrict__ mom) {
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x >= 32) return;
+  double d[5] = {0, 0, 0, 0, 0}, r[5] = {0, 0, 0, 0, 0};
+  for (int b = lane; b < nblk; b += 32)
+    for (int k = 0; k < 5; ++k) {
+      d[k] += pd[b * 5 + k];
+      if (have_randoms) r[k] += pr[b * 5 + k];
+    }
+  for (int k = 0; k < 5; ++k)
+    for (int off = 16; off > 0; off >>= 1) {
+      d[k] += __shfl_down_sync(0xffffffffu, d[k], off);
+      r[k] += __shfl_down_sync(0xffffffffu, r[k], off);
+    }
+  if (lane == 0) {
+    const double a = sc[SC_ALPHA];
+    for (int k = 0; k < 5; ++k) mom[k] = d[k] - a * a * a * r[k];
+  }
+}
+
+// ------------------------------------------------------------------------------------------
 // Warp-segmented accumulation of NS sums into per-warp float64 partials (runs of consecutive
 // lanes with equal bin; deterministic for a fixed thread-to-mode map).
 // ------------------------------------------------------------------------------------------
@@ -199,7 +355,7 @@ k_bin_cross(const cplx<T>* __restrict__ X0, const cplx<T>* __restrict__ XN, int 
 // 4. shell-filtered inverse transforms
 // ------------------------------------------------------------------------------------------
 struct ShellField {
-  int8_t src;     // 0: X_0, 1: ones (indicator), 2: X_0 N_0^* (FFT-method shot noise)
+  int8_t src;     // 0: X_0, 1: ones (indicator), 2: X_0 N_0^* (FFT-method shot noise), 3: X_2 (survey)
   int8_t mult;    // 0: 1, 1: L_2(mu)
   int16_t bin;    // >= 0: modes of this bin; -1: all modes with n2 <= n2cap
   int K;          // kz <= K, |ky| <= K
@@ -213,7 +369,8 @@ struct ShellField {
 // frequency i = kx' (kx' < NS/2) or kx' - NS, read from the n-grid spectrum X0.
 template <typename T, int NS>
 __global__ void __launch_bounds__(BT)
-k_shell_x(const cplx<T>* __restrict__ X0, const cplx<T>* __restrict__ XN, int KZX, int nfine,
+k_shell_x(const cplx<T>* __restrict__ X0, const cplx<T>* __restrict__ XN, const cplx<T>* __restrict__ X2, int KZX,
+          int nfine,
           const ShellField* __restrict__ fields, int nfields, int Kmax, const int16_t* __restrict__ tab, int n2cap,
           double lx, double ly, double lz, const cplx<T>* __restrict__ tw_g, cplx<T>* __restrict__ T1) {
   using C = cplx<T>;
@@ -224,7 +381,8 @@ k_shell_x(const cplx<T>* __restrict__ X0, const cplx<T>* __restrict__ XN, int KZ
   C* tw = reinterpret_cast<C*>(smem_raw);
   C* xrow = tw + NS;                  // X_0 row
   C* xnrow = xrow + NS;               // X_0 N_0^* row (when XN is given)
-  T* l2row = reinterpret_cast<T*>(xnrow + NS);  // L_2(mu) per kx
+  C* x2row = xnrow + NS;              // Yamamoto X_2 row (when X2 is given)
+  T* l2row = reinterpret_cast<T*>(x2row + NS);  // L_2(mu) per kx
   int* binrow = reinterpret_cast<int*>(l2row + NS);  // bin per kx (-1 excluded), n2 per kx
   int* n2row = binrow + NS;
   C* bufs = reinterpret_cast<C*>(n2row + NS);   // NBUF x NP
@@ -247,6 +405,7 @@ k_shell_x(const cplx<T>* __restrict__ X0, const cplx<T>* __restrict__ XN, int KZ
       const size_t src = ((size_t)kz * nfine + ky) * nfine + fx;
       xrow[kx] = (inrange && kz < KZX) ? X0[src] : cmk(T(0), T(0));
       if (XN) xnrow[kx] = (inrange && kz < KZX) ? cmul(X0[src], cconj(XN[src])) : cmk(T(0), T(0));
+      if (X2) x2row[kx] = (inrange && kz < KZX) ? X2[src] : cmk(T(0), T(0));
       const T kk = sqrt(T(n2));
       const T mu = n2 > 0 ? (T(i) * T(lx) + T(jy) * T(ly) + T(kz) * T(lz)) / kk : T(0);
       l2row[kx] = T(1.5) * mu * mu - T(0.5);
@@ -271,7 +430,7 @@ k_shell_x(const cplx<T>* __restrict__ X0, const cplx<T>* __restrict__ XN, int KZ
         if (live) {
           const bool in = sf.bin >= 0 ? (binrow[kx] == sf.bin) : (n2row[kx] >= 0);
           if (in) {
-            a = sf.src == 0 ? xrow[kx] : (sf.src == 2 ? xnrow[kx] : cmk(T(1), T(0)));
+            a = sf.src == 0 ? xrow[kx] : (sf.src == 2 ? xnrow[kx] : (sf.src == 3 ? x2row[kx] : cmk(T(1), T(0))));
             if (sf.mult) a = cscale(a, l2row[kx]);
           }
         }
@@ -584,6 +743,65 @@ __device__ double g_ell_dev(int l, double t) {
   return (2.0 * t * (5.0 * t * t - 3.0) + 3.0 * (t * t - 1.0) * (t * t - 1.0) * lg) / (16.0 * t * t * t);
 }
 
+// Survey l = 2 shell sums: per bin [w Re X0 N0*, w Re X2 N0*, w Re X0 N2*, w, w Y_20, w Re Y_21,
+// w Im Y_21, w Re Y_22, w Im Y_22] on the k-bins and on the unit-width k3 shells.
+constexpr int NCS = 9;
+template <typename T, int N>
+__global__ void __launch_bounds__(BT)
+k_bin_cross_survey(const cplx<T>* __restrict__ X0, const cplx<T>* __restrict__ X2, const cplx<T>* __restrict__ N0,
+                   const cplx<T>* __restrict__ N2, int KY, const YNorm nrm, const int16_t* __restrict__ tab_m, int nbm,
+                   const int16_t* __restrict__ tab_q, int nbq, int n2max, double* __restrict__ part_m,
+                   double* __restrict__ part_q) {
+  using C = cplx<T>;
+  constexpr int NW = BT / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double* pm = part_m + ((size_t)blockIdx.x * NW + warp) * nbm * NCS;
+  double* pq = part_q + ((size_t)blockIdx.x * NW + warp) * nbq * NCS;
+  const int nyr = 2 * KY + 1;
+  const int nrows = (KY + 1) * nyr;
+  const T n20 = ynorm<T>(nrm, 3), n21 = ynorm<T>(nrm, 4), n22 = ynorm<T>(nrm, 5);
+  for (int r = blockIdx.x; r < nrows; r += gridDim.x) {
+    const int kz = r / nyr;
+    const int jy = r % nyr - KY;
+    const int ky = jy < 0 ? jy + N : jy;
+    for (int jb = warp * 32; jb < N; jb += blockDim.x) {
+      const int j = jb + lane;
+      const int i = j < N / 2 ? j : j - N;
+      const int n2 = i * i + jy * jy + kz * kz;
+      int bm = -1, bq = -1;
+      T vals[NCS];
+#pragma unroll
+      for (int s = 0; s < NCS; ++s) vals[s] = T(0);
+      if (j < N && n2 > 0 && n2 <= n2max && i != -N / 2 && jy != -N / 2) {
+        bm = tab_m[n2];
+        bq = tab_q[n2];
+        const size_t idx = ((size_t)kz * N + ky) * N + j;
+        const C a0 = X0[idx], a2 = X2[idx], b0 = N0[idx], b2 = N2[idx];
+        const T inv = rsqrt(T(n2));
+        const T ux = T(i) * inv, uy = T(jy) * inv, uz = T(kz) * inv;
+        const T w = kz > 0 ? T(2) : T(1);
+        vals[0] = w * (a0.x * b0.x + a0.y * b0.y);
+        vals[1] = w * (a2.x * b0.x + a2.y * b0.y);
+        vals[2] = w * (a0.x * b2.x + a0.y * b2.y);
+        vals[3] = w;
+        vals[4] = w * n20 * (T(1.5) * uz * uz - T(0.5));
+        vals[5] = w * n21 * T(-3) * uz * ux;
+        vals[6] = w * n21 * T(-3) * uz * uy;
+        vals[7] = w * n22 * T(3) * (ux * ux - uy * uy);
+        vals[8] = w * n22 * T(3) * (T(2) * ux * uy);
+      }
+      T vm[NCS], vq[NCS];
+#pragma unroll
+      for (int s = 0; s < NCS; ++s) {
+        vm[s] = bm >= 0 ? vals[s] : T(0);
+        vq[s] = bq >= 0 ? vals[s] : T(0);
+      }
+      seg_accumulate<T, NCS>(lane, bm, vm, pm);
+      seg_accumulate<T, NCS>(lane, bq, vq, pq);
+    }
+  }
+}
+
 struct FinalArgs {
   int nb, ntri, npair, nq;
   int nscoc, scoc_l[2];
@@ -601,14 +819,16 @@ struct FinalArgs {
   // sum_x I_a I_b SF_e at nb + e and sum_x I_a I_b LF_e at nb + ntripo + e), of sum_x I_a I_b G2_c
   // in s2 (nb columns), of sum_x I_a G_b LF_e (family 0) and sum_x G_a I_b LF_e (family 1) in s3
   int s1_nparts, s1_nrows, s1_ncol, s2_nparts, s2_nrows, s3_nparts, s3_nrows, s3_ncol;
+  int survey;           // 1: survey l = 2 shell sums (NCS per bin) and catalogue moments
+  int ncs;              // sums per bin in cross_m / cross_q
 };
 
 __global__ void k_bispec_finalize(const int* __restrict__ tri, const int* __restrict__ pair_ij,
                                   const double* __restrict__ part_main, const double* __restrict__ nt_sums,
                                   const double* __restrict__ cross_m, const double* __restrict__ cross_q,
-                                  const double* __restrict__ part_s1, const double* __restrict__ part_s2,
-                                  const double* __restrict__ part_s3, const double* __restrict__ nt2_sums,
-                                  const FinalArgs F,
+                                  const double* __restrict__ mom, const double* __restrict__ part_s1,
+                                  const double* __restrict__ part_s2, const double* __restrict__ part_s3,
+                                  const double* __restrict__ nt2_sums, const FinalArgs F,
                                   const double* __restrict__ sc, double* __restrict__ out) {
   const int nb = F.nb;
   const double i33 = sc[SC_I33], s3 = sc[SC_S3];
@@ -616,19 +836,25 @@ __global__ void k_bispec_finalize(const int* __restrict__ tri, const int* __rest
   const size_t oB = 0, oSB = (size_t)F.nscoc * F.ntri, oNT = 2 * (size_t)F.nscoc * F.ntri;
   const size_t oBB = oNT + F.ntri, oSBB = oBB + (size_t)F.ntripo * F.npair;
   const size_t oNM = oSBB + (size_t)F.ntripo * F.npair, oSC = oNM + nb;
-  auto cross = [&](const double* cr, int b, int s) { return cr[(size_t)b * NCROSS + s]; };
+  auto cross = [&](const double* cr, int b, int s) { return cr[(size_t)b * F.ncs + s]; };
+  auto count = [&](const double* cr, int b) { return cross(cr, b, F.survey ? 3 : 2); };
   auto centre = [&](int b) { return F.kmin + (b + 0.5) * F.dk; };
-  // H_l(k) = <Re X N*> L_l - S3 <L_l> on the k-bins (l = 0, 2); Q_l on the k3 shells (same form)
-  auto Hm = [&](int l, int b) {
-    const double n = cross(cross_m, b, 2);
+  // H_l(k) = <Re X_0 N_l*> - S_l and Q_l(k) = <Re X_l N_0*> - S_l on a bin set (k-bins or k3 shells).
+  // Global line of sight: both are <L_l Re X_0 N_0*> - S3 <L_l>.  Survey l = 2: the self term
+  // S_2 = 4 pi/5 sum_m <Y_2m(qhat)> C_2m^* from the catalogue moments C_2m.
+  auto shell_term = [&](const double* cr, int l, int b, bool q) {
+    const double n = count(cr, b);
     if (n <= 0) return 0.0;
-    return l == 0 ? (cross(cross_m, b, 0) - s3 * n) / n : (cross(cross_m, b, 1) - s3 * cross(cross_m, b, 3)) / n;
+    if (l == 0) return (cross(cr, b, 0) - s3 * n) / n;
+    if (!F.survey) return (cross(cr, b, 1) - s3 * cross(cr, b, 3)) / n;
+    const double* c = cr + (size_t)b * F.ncs;
+    const double self = 4.0 * M_PI / 5.0 * (c[4] * mom[0] + 2.0 * (c[5] * mom[1] + c[6] * mom[2] + c[7] * mom[3] +
+                                                                   c[8] * mom[4]));
+    return ((q ? c[1] : c[2]) - self) / n;
   };
-  auto Hq = [&](int l, int b) {
-    const double n = cross(cross_q, b, 2);
-    if (n <= 0) return 0.0;
-    return l == 0 ? (cross(cross_q, b, 0) - s3 * n) / n : (cross(cross_q, b, 1) - s3 * cross(cross_q, b, 3)) / n;
-  };
+  auto Hm = [&](int l, int b) { return shell_term(cross_m, l, b, false); };
+  auto Qm = [&](int l, int b) { return shell_term(cross_m, l, b, true); };
+  auto Qq = [&](int l, int b) { return shell_term(cross_q, l, b, true); };
   auto pair_index = [&](int a, int b) {   // a <= b
     int p = 0;
     for (int c = 0; c < a; ++c) p += nb - c;
@@ -678,7 +904,7 @@ __global__ void k_bispec_finalize(const int* __restrict__ tri, const int* __rest
       } else if (F.shot && snt > 0) {
         const double L12 = l == 0 ? 1.0 : 1.5 * c12 * c12 - 0.5;
         const double L13 = l == 0 ? 1.0 : 1.5 * c13 * c13 - 0.5;
-        sn = (2 * l + 1) / i33 * ((l == 0 ? s3 : 0.0) + Hm(l, i) + L12 * Hm(l, j) + L13 * Hm(l, k));
+        sn = (2 * l + 1) / i33 * ((l == 0 ? s3 : 0.0) + Qm(l, i) + L12 * Hm(l, j) + L13 * Hm(l, k));
       }
       out[oB + (size_t)e * F.ntri + t] = raw - sn;
       out[oSB + (size_t)e * F.ntri + t] = sn;
@@ -686,7 +912,7 @@ __global__ void k_bispec_finalize(const int* __restrict__ tri, const int* __rest
   }
   for (int p = tid; p < F.npair; p += nthreads) {
     const int i = pair_ij[p] & 0xffff, j = pair_ij[p] >> 16;
-    const double ni = cross(cross_m, i, 2), nj = cross(cross_m, j, 2);
+    const double ni = count(cross_m, i), nj = count(cross_m, j);
     for (int e = 0; e < F.ntripo; ++e) {
       const int l = F.tripo_l[e];
       double sg = 0;
@@ -708,9 +934,9 @@ __global__ void k_bispec_finalize(const int* __restrict__ tri, const int* __rest
         double num = 0, den = 0;
         for (int m = 0; m < F.nq; ++m) {
           const double cm = (m + 0.5) * F.dk;
-          const double nm = cross(cross_q, m, 2);
+          const double nm = count(cross_q, m);
           if (cm >= lo - 1e-9 * F.dk && cm <= hi + 1e-9 * F.dk && nm > 0) {
-            num += nm / cm * Hq(l, m);
+            num += nm / cm * Qq(l, m);
             den += nm / cm;
           }
         }
@@ -721,18 +947,18 @@ __global__ void k_bispec_finalize(const int* __restrict__ tri, const int* __rest
       out[oSBB + (size_t)e * F.npair + p] = sn;
     }
   }
-  for (int b = tid; b < nb; b += nthreads) out[oNM + b] = cross(cross_m, b, 2);
+  for (int b = tid; b < nb; b += nthreads) out[oNM + b] = count(cross_m, b);
   if (tid < 8) out[oSC + tid] = sc[tid];
 }
 
 // reduce per-warp cross partials into [bin][NCROSS] in a fixed order
 // one warp per (bin, sum): strided lane sums then a fixed shuffle tree (reproducible order)
-__global__ void k_cross_reduce(const double* __restrict__ part, int nrec, int nb, double* __restrict__ out) {
+__global__ void k_cross_reduce(const double* __restrict__ part, int nrec, int nb, int ns, double* __restrict__ out) {
   const int lane = threadIdx.x & 31;
   const int wpb = blockDim.x / 32;
-  for (int e = blockIdx.x * wpb + (threadIdx.x >> 5); e < nb * NCROSS; e += gridDim.x * wpb) {
+  for (int e = blockIdx.x * wpb + (threadIdx.x >> 5); e < nb * ns; e += gridDim.x * wpb) {
     double s = 0;
-    for (int r = lane; r < nrec; r += 32) s += part[(size_t)r * nb * NCROSS + e];
+    for (int r = lane; r < nrec; r += 32) s += part[(size_t)r * nb * ns + e];
     for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
     if (lane == 0) out[e] = s;
   }
@@ -795,6 +1021,7 @@ int shell_grid_size(int need, int n, bool fp64) {
 struct ShellLaunch {
   const void* X;
   const void* XN;   // N-field spectrum for src = 2 fields, or null
+  const void* X2;   // Yamamoto X_2 for src = 3 fields, or null
   int KZX, nfine;
   const ShellField* fields;
   int nfield, Kmax;
@@ -816,13 +1043,14 @@ npc_status shell_passes(npc_ctx* ctx, const ShellLaunch& sl, cplx<T>* T1, cplx<T
   NPC_TRY(get_twiddles(ctx, NS, sizeof(T) == 8 ? NPC_PREC_FP64 : NPC_PREC_MIXED, &twp));
   const C* tw = (const C*)twp;
   {
-    const size_t smem = sizeof(C) * (3 * NS + (size_t)RowGroups<NS, BT>::NBUF * row_pad_len<NS>()) +
+    const size_t smem = sizeof(C) * (4 * NS + (size_t)RowGroups<NS, BT>::NBUF * row_pad_len<NS>()) +
                         sizeof(T) * NS + sizeof(int) * 2 * NS;
     auto kern = k_shell_x<T, NS>;
     NPC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int nrows = (sl.Kmax + 1) * (2 * sl.Kmax + 1);
     kern<<<std::min(nrows, ctx->num_sms * 4), BT, smem, ctx->stream>>>(
-        (const C*)sl.X, (const C*)sl.XN, sl.KZX, sl.nfine, sl.fields, sl.nfield, sl.Kmax, sl.tab, sl.n2cap, sl.l[0],
+        (const C*)sl.X, (const C*)sl.XN, (const C*)sl.X2, sl.KZX, sl.nfine, sl.fields, sl.nfield, sl.Kmax, sl.tab,
+        sl.n2cap, sl.l[0],
         sl.l[1], sl.l[2], tw, T1);
     NPC_LAUNCH(ctx);
   }
@@ -890,6 +1118,9 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
     const double ll = std::sqrt(m.los_dir[0] * m.los_dir[0] + m.los_dir[1] * m.los_dir[1] + m.los_dir[2] * m.los_dir[2]);
     for (int a = 0; a < 3; ++a) l3[a] = m.los_dir[a] / ll;
   }
+  // survey geometry with the line of sight to each grid point and an l = 2 request: Yamamoto X_2
+  // from the Y_2m-weighted transforms instead of L_2(khat . los) X_0
+  const bool yam = !m.periodic && m.los != 1 && (((scoc_mask | tripo_mask) & 4) != 0);
 
   // 1. paint + forward transforms of F and N fields
   const size_t rs = sizeof(T);
@@ -900,39 +1131,66 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
   PowerPlan plan{};
   plan.n = N;
   plan.nphase = nphase;
-  plan.global_los = 1;
+  plan.global_los = yam ? 0 : 1;
   plan.assign = m.assign;
   plan.kz_keep = KZ;
   plan.fl.nf = 0;
-  for (int ph = 0; ph < nphase; ++ph) {
+  auto push = [&](int ph, int l, int mm, int part) {
     Comp c;
-    c.phase = (int8_t)ph; c.ell = 0; c.m = 0; c.part = PART_ONE;
+    c.phase = (int8_t)ph; c.ell = (int8_t)l; c.m = (int8_t)mm; c.part = (int8_t)part;
     plan.fl.f[plan.fl.nf++] = c;
+  };
+  if (!yam) {
+    for (int ph = 0; ph < nphase; ++ph) push(ph, 0, 0, PART_ONE);
+  } else if (nphase == 2) {   // the standard interlaced l <= 2 layout (k_fft_x_assemble2 order)
+    push(0, 0, 0, PART_ONE); push(1, 0, 0, PART_ONE);
+    push(0, 2, 0, PART_RE); push(1, 2, 0, PART_RE);
+    push(0, 2, 1, PART_RE); push(0, 2, 1, PART_IM); push(1, 2, 1, PART_RE); push(1, 2, 1, PART_IM);
+    push(0, 2, 2, PART_RE); push(0, 2, 2, PART_IM); push(1, 2, 2, PART_RE); push(1, 2, 2, PART_IM);
+  } else {
+    push(0, 0, 0, PART_ONE); push(0, 2, 0, PART_RE);
+    push(0, 2, 1, PART_RE); push(0, 2, 1, PART_IM); push(0, 2, 2, PART_RE); push(0, 2, 2, PART_IM);
   }
+  const Geom gyam = make_geom(m);   // observer-relative grid points for the Y weighting
+  const Geom& gfwd = yam ? gyam : geo;
   const int prec = sizeof(T) == 8 ? NPC_PREC_FP64 : NPC_PREC_MIXED;
-  const size_t halfbytes = sizeof(C) * (size_t)nphase * KZ * N * N;
+  const size_t halfbytes = sizeof(C) * (size_t)plan.fl.nf * KZ * N * N;
   NPC_TRY(ws_get(ctx, "half", 2 * halfbytes, &half));
   C* halfF = (C*)half;
   C* halfN = (C*)((char*)half + halfbytes);
   NPC_TRY(stage_mark(ctx, "alloc"));
   NPC_TRY(launch_paint(ctx, d, r, m, 1, prec, sc, ma, mb));
   NPC_TRY(stage_mark(ctx, "paint_fold"));
-  NPC_TRY(run_forward_transforms(ctx, prec, plan, geo, ma, mb, halfF));
+  NPC_TRY(run_forward_transforms(ctx, prec, plan, gfwd, ma, mb, halfF));
   if (shot) {
     NPC_TRY(launch_paint(ctx, d, r, m, 2, prec, sc, ma, mb));
-    NPC_TRY(run_forward_transforms(ctx, prec, plan, geo, ma, mb, halfN));
+    NPC_TRY(run_forward_transforms(ctx, prec, plan, gfwd, ma, mb, halfN));
   }
   NPC_TRY(stage_mark(ctx, "forward_yz"));
 
   const void* twf;
   NPC_TRY(get_twiddles(ctx, N, prec, &twf));
   const C* tw = (const C*)twf;
-  // 2. x pass + combine into X0 (and XN)
+  // 2. x pass + combine into X0 (and XN); survey l = 2 also X2 (and N2) at X + 2 xfs (+ 3 xfs)
   C* X;
   const int nout = shot ? 2 : 1;
   const size_t xfs = (size_t)KZ * N * N;
-  NPC_TRY(ws_get(ctx, "bis.X", sizeof(C) * xfs * nout, (void**)&X));
-  {
+  NPC_TRY(ws_get(ctx, "bis.X", sizeof(C) * xfs * (yam ? 4 : nout), (void**)&X));
+  if (yam) {
+    const size_t smem =
+        sizeof(C) * (2 * N + (size_t)(12 + RowGroups<N, BT>::NBUF) * row_pad_len<N>()) + sizeof(T) * (N / 2 + 2);
+    auto kern = k_fft_x_assemble2<T, N>;
+    NPC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int nrows = KZ * (2 * K2 + 1);
+    const int grid = std::min(nrows, ctx->num_sms * 4);
+    const YNorm nrm = ylm_norm_table();
+    kern<<<grid, BT, smem, ctx->stream>>>(halfF, nphase, KZ, K2, m.assign, nrm, tw, X, X + 2 * xfs);
+    NPC_LAUNCH(ctx);
+    if (shot) {
+      kern<<<grid, BT, smem, ctx->stream>>>(halfN, nphase, KZ, K2, m.assign, nrm, tw, X + xfs, X + 3 * xfs);
+      NPC_LAUNCH(ctx);
+    }
+  } else {
     constexpr int TPF = N / 8;
     constexpr int G = BT / TPF > 0 ? BT / TPF : 1;
     const int nf = nphase * nout;
@@ -956,25 +1214,56 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
   NPC_TRY(get_bin_table(ctx, N, m.box, kb, &tab_m, 2));
   npc_kbins qb{0.0, kb.dk, nq};
   NPC_TRY(get_bin_table(ctx, N, m.box, qb, &tab_q, 3));
-  double *cross_m, *cross_q;
-  NPC_TRY(ws_get(ctx, "bis.cross", sizeof(double) * NCROSS * (nb + nq), (void**)&cross_m));
-  cross_q = cross_m + (size_t)NCROSS * nb;
+  const int nsum_c = yam ? NCS : NCROSS;   // shell sums per bin
+  double *cross_m, *cross_q, *mom = nullptr;
+  NPC_TRY(ws_get(ctx, "bis.cross", sizeof(double) * nsum_c * (nb + nq) + sizeof(double) * 8, (void**)&cross_m));
+  cross_q = cross_m + (size_t)nsum_c * nb;
+  if (yam) mom = cross_q + (size_t)nsum_c * nq;
   {
     const int nrows = (K2 + 1) * (2 * K2 + 1);
     const int grid = std::min(nrows, ctx->num_sms * 2);
     const int nw = BT / 32;
     double* part;
     const size_t np = (size_t)grid * nw;
-    NPC_TRY(ws_get(ctx, "bis.crosspart", sizeof(double) * np * NCROSS * (nb + nq), (void**)&part));
-    NPC_CUDA(ctx, cudaMemsetAsync(part, 0, sizeof(double) * np * NCROSS * (nb + nq), ctx->stream));
+    NPC_TRY(ws_get(ctx, "bis.crosspart", sizeof(double) * np * nsum_c * (nb + nq), (void**)&part));
+    NPC_CUDA(ctx, cudaMemsetAsync(part, 0, sizeof(double) * np * nsum_c * (nb + nq), ctx->stream));
     const C* XN = shot ? X + xfs : X;
-    k_bin_cross<T, N><<<grid, BT, 0, ctx->stream>>>(X, XN, KZ, K2, l3[0], l3[1], l3[2], tab_m, nb, tab_q, nq, n2cap,
-                                                   part, part + np * NCROSS * nb);
+    if (yam) {
+      const C* N2 = shot ? X + 3 * xfs : X + 2 * xfs;
+      k_bin_cross_survey<T, N><<<grid, BT, 0, ctx->stream>>>(X, X + 2 * xfs, XN, N2, K2, ylm_norm_table(), tab_m, nb,
+                                                            tab_q, nq, n2cap, part, part + np * NCS * nb);
+    } else {
+      k_bin_cross<T, N><<<grid, BT, 0, ctx->stream>>>(X, XN, KZ, K2, l3[0], l3[1], l3[2], tab_m, nb, tab_q, nq, n2cap,
+                                                     part, part + np * NCROSS * nb);
+    }
     NPC_LAUNCH(ctx);
-    k_cross_reduce<<<(nb * NCROSS + 3) / 4, 128, 0, ctx->stream>>>(part, (int)np, nb, cross_m);
+    k_cross_reduce<<<(nb * nsum_c + 3) / 4, 128, 0, ctx->stream>>>(part, (int)np, nb, nsum_c, cross_m);
     NPC_LAUNCH(ctx);
-    k_cross_reduce<<<(nq * NCROSS + 3) / 4, 128, 0, ctx->stream>>>(part + np * NCROSS * nb, (int)np, nq, cross_q);
+    k_cross_reduce<<<(nq * nsum_c + 3) / 4, 128, 0, ctx->stream>>>(part + np * nsum_c * nb, (int)np, nq, nsum_c,
+                                                                 cross_q);
     NPC_LAUNCH(ctx);
+    if (yam && shot) {
+      // catalogue moments C_2m of the self term (data, then randoms scaled by -alpha^3)
+      double* pm;
+      NPC_TRY(ws_get(ctx, "bis.ympart", sizeof(double) * 5 * YM_BLOCKS * 2, (void**)&pm));
+      const YNorm nrm = ylm_norm_table();
+      auto moments = [&](const DevCatalog& c, double* out) {
+        if (c.dtype == 1)
+          k_cat_ylm2<double><<<YM_BLOCKS, YM_THREADS, 0, ctx->stream>>>(
+              (const double*)c.pos, (const double*)c.w, c.n, m.observer[0], m.observer[1], m.observer[2], nrm, out);
+        else
+          k_cat_ylm2<float><<<YM_BLOCKS, YM_THREADS, 0, ctx->stream>>>(
+              (const float*)c.pos, (const float*)c.w, c.n, m.observer[0], m.observer[1], m.observer[2], nrm, out);
+      };
+      moments(d, pm);
+      NPC_LAUNCH(ctx);
+      if (r) {
+        moments(*r, pm + 5 * YM_BLOCKS);
+        NPC_LAUNCH(ctx);
+      }
+      k_cat_ylm2_final<<<1, 32, 0, ctx->stream>>>(pm, pm + 5 * YM_BLOCKS, YM_BLOCKS, r ? 1 : 0, sc, mom);
+      NPC_LAUNCH(ctx);
+    }
   }
   NPC_TRY(stage_mark(ctx, "shot_shells"));
 
@@ -1036,14 +1325,14 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
     ffam.push_back(fam);
   };
   for (int b = 0; b < nb; ++b) add(0, 0, b, Ks, 0);              // F0_b: R index b
-  if (want2) for (int b = 0; b < nb; ++b) add(0, 1, b, Ks, 1);   // F2_b: R index nb + b
+  if (want2) for (int b = 0; b < nb; ++b) add(yam ? 3 : 0, yam ? 0 : 1, b, Ks, 1);   // F2_b: R index nb + b
   const int iF2 = want2 ? nb : -1;
   const int iI = (int)fl.size();
   if (need_nt || fftshot) for (int b = 0; b < nb; ++b) add(1, 0, b, Ks, 2);   // I_b
   const int iG = (int)fl.size();
   int ng = 0;
   if (wantG0) { add(0, 0, -1, KG, 3); ng++; }
-  if (wantG2) { add(0, 1, -1, KG, 3); ng++; }
+  if (wantG2) { add(yam ? 3 : 0, yam ? 0 : 1, -1, KG, 3); ng++; }
   int iS0 = -1, iS2 = -1, iI2 = -1, iSF = -1, iLF = -1;
   int ntl = 0, tls[2] = {0, 0};   // compressed multipoles requested
   for (int l = 0; l <= 2; l += 2)
@@ -1134,6 +1423,7 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
     ShellLaunch sl{};
     sl.X = X;
     sl.XN = fftshot ? (const void*)(X + xfs) : nullptr;
+    sl.X2 = yam ? (const void*)(X + 2 * xfs) : nullptr;
     sl.KZX = KZ;
     sl.nfine = N;
     sl.fields = dfields;
@@ -1341,11 +1631,13 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
   fa.s1_ncol = ts1.ncol;
   fa.s2_nparts = gs2;
   fa.s2_nrows = ts2.nrows;
+  fa.survey = yam ? 1 : 0;
+  fa.ncs = nsum_c;
   fa.s3_nparts = gs3;
   fa.s3_nrows = ts3.nrows;
   fa.s3_ncol = ts3.ncol;
   k_bispec_finalize<<<std::max(1, (std::max(ntri, npair) + 127) / 128), 128, 0, ctx->stream>>>(
-      (const int*)(dtab + t_tri), (const int*)(dtab + t_pij), part, nt_sums, cross_m, cross_q, part_s1, part_s2,
+      (const int*)(dtab + t_tri), (const int*)(dtab + t_pij), part, nt_sums, cross_m, cross_q, mom, part_s1, part_s2,
       part_s3, nt2_sums, fa, sc, dev_out);
   NPC_LAUNCH(ctx);
   NPC_TRY(stage_mark(ctx, "finalize"));

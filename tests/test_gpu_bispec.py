@@ -131,6 +131,25 @@ def test_fft_method_shot_noise_survey_monopole(api):
     assert np.max(e) < 1e-10
 
 
+@pytest.mark.parametrize("assign,interlace,prec,tol", [(3, 1, "fp64", 1e-10), (2, 0, "fp64", 1e-10),
+                                                      (3, 1, "mixed", 1e-4)])
+def test_survey_l2_endpoint_line_of_sight(api, assign, interlace, prec, tol):
+    """Survey geometry with the line of sight to each grid point: Yamamoto X_2 (Y_2m-weighted
+    transforms), B_0, B_2, B_000, B_202 and their analytic shot noise with the survey self term."""
+    from synthetic import make_survey_catalogs
+
+    box = 600.0
+    g, r, origin = make_survey_catalogs(20000, 200000, box, 900.0, 32, seed=75, fkp_p0=1e4)
+    kf = 2 * np.pi / box
+    kb = (2 * kf, 1.5 * kf, 4)   # k_max = 8 k_f = k_N/2 at 32^3
+    res = api.bispectrum(g, n=32, box=box, kbins=kb, assign=assign, interlace=interlace, precision=prec,
+                         origin=origin, randoms=r, los_dir=None, observer=(0.0, 0.0, 0.0))
+    spec = dict(n=32, box=box, origin=tuple(origin), assign=assign, interlace=interlace, los="endpoint",
+                observer=(0.0, 0.0, 0.0), periodic=0)
+    orc = OB.bispectrum(spec, g, r, kb, (0, 2), (0, 2), shot=True)
+    _check(res, orc, tol)
+
+
 def test_mixed_19_bins_805_triangles_128(api):
     """The 19-bin / 805-triangle layout of the 256^3 workload on a 128^3 mesh of the same box
     (k_max = 0.2 = k_N/2), float32 transforms: <= 1e-4."""
@@ -166,6 +185,13 @@ def test_bispectrum_rejects(api):
     with pytest.raises(B.NpcError) as ei:        # odd multipole
         api.bispectrum(cat, n=32, box=300.0, kbins=(0.02, 0.02, 4), scoc_ells=(1,))
     assert ei.value.status == 1
+    from synthetic import make_survey_catalogs
+
+    g, r, origin = make_survey_catalogs(2000, 20000, 600.0, 900.0, 16, seed=77)
+    with pytest.raises(B.NpcError) as ei:        # FFT-method l = 2 shot noise with the endpoint line of sight
+        api.bispectrum(g, n=32, box=600.0, kbins=(0.03, 0.02, 3), origin=origin, randoms=r, los_dir=None,
+                       shot="fft")
+    assert ei.value.status == 4
 
 
 @pytest.mark.slow

@@ -315,3 +315,29 @@ def test_compressed_fft_shot_object_identities(ell, nobj):
     scale = np.max(np.abs(raw))
     want = 0.0 if nobj == 2 else _distinct_pair_part(spec, pos, w, kb, prs, ell)
     np.testing.assert_allclose(raw - sn, want, rtol=0, atol=1e-11 * scale)
+
+
+def test_survey_l2_tends_to_global_los_for_a_distant_observer():
+    """Survey geometry (Yamamoto X_2 with the line of sight to each grid point, the self term from
+    the objects' own directions) equals the global-LOS form in the limit of a distant observer,
+    where every direction is the box's (1,1,1)/sqrt(3): B_2, B_202 and their analytic shot noise."""
+    box, dist = 600.0, 1.0e8
+    g, r, origin = make_survey_catalogs(3000, 30000, box, dist, 12, seed=23, fkp_p0=1e4, dtype=np.float64)
+    kb = (0.011, 0.0135, 3)
+    common = dict(n=20, box=box, origin=tuple(origin), assign=3, interlace=1)
+    surv = B.bispectrum(dict(common, los="endpoint", observer=(0.0, 0.0, 0.0)), g, r, kb, (0, 2), (0, 2))
+    d = np.ones(3) / np.sqrt(3.0)
+    glob = B.bispectrum(dict(common, los="global", los_dir=tuple(d)), g, r, kb, (0, 2), (0, 2))
+    st = np.abs(glob["B"][0]) + np.abs(glob["shot_B"][0])
+    sp = np.abs(glob["BB"][0]) + np.abs(glob["shot_BB"][0])
+    for key, scale in (("B", st), ("shot_B", st), ("BB", sp), ("shot_BB", sp)):
+        for ell in (0, 2):
+            err = np.abs(surv[key][ell] - glob[key][ell]) / scale
+            assert np.max(err) < 1e-5, (key, ell, np.max(err))
+    # and a nearby observer changes B_2 (the line of sight varies across the box)
+    g2, r2, origin2 = make_survey_catalogs(3000, 30000, box, 900.0, 12, seed=23, fkp_p0=1e4, dtype=np.float64)
+    near = B.bispectrum(dict(common, origin=tuple(origin2), los="endpoint", observer=(0.0, 0.0, 0.0)), g2, r2,
+                        kb, (2,), (), shot=False)
+    nearg = B.bispectrum(dict(common, origin=tuple(origin2), los="global", los_dir=tuple(d)), g2, r2, kb, (2,), (),
+                         shot=False)
+    assert np.max(np.abs(near["B"][2] - nearg["B"][2])) > 1e-3 * np.max(np.abs(nearg["B"][2]))
