@@ -12,7 +12,8 @@ Follows Sec. 2.1 and Sec. 3 of the paper:
   observer to the grid point (endpoint line of sight), or the fixed line of sight for a global LOS;
   interlaced as 1/2 [S_a + e^{i H (kx+ky+kz)/2} S_b] and divided by W(k) (Eq. compensation).
 * Hand+17 form (Eq. hand): F_l(k) = 4 pi/(2l+1) sum_{m=-l}^{l} Y_l^{m*}(khat) S_l^m(k)
-  -- 2l+1 transforms; P_l = (2l+1)/I22 <Re F_0 F_l^*>_bin - delta_l0 N_0 (Eq. Hand17).
+  -- 2l+1 transforms; P_l = (2l+1)/I22 <Re F_0 F_l^*>_bin - delta_l0 N_0 (Eq. Hand17); for odd l
+  the imaginary part (Sec. 2.1: odd multipoles replace the real part by the imaginary part).
 * Symmetric form (Eqs. new_F_ell, pk_final): G_l = 4 pi/(2l+1) [f^0 + 2 sum_{m>=1} f^m] with
   f^m = Y_l^{m*}(khat) S_l^m -- l+1 transforms; P_l^E = Re[(2l+1)/I22 <F_0 G_l^*>] - N_l.
 * Space inversion (Eq. F_and_new_G): F_l(k) = 1/2 [G_l(k) + (-1)^l G_l^*(-k)], grid index
@@ -161,6 +162,11 @@ PLB_COEFFS = {
 }
 
 
+def _part(ell, z):
+    """Re z for even l, Im z for odd l (the odd-multipole estimator of Sec. 2.1)."""
+    return np.imag(z) if ell % 2 else np.real(z)
+
+
 def n_shot_two_index(ell, ellp, n0):
     """N_ll' = (2(l+l')+1) N_0 <L_l L_l'> over directions = (2(l+l')+1) N_0 delta_ll'/(2l+1)."""
     if ell != ellp:
@@ -187,7 +193,7 @@ def power_from_fields(spec, fields, kbins, ells, scalars, modified=(), fields_ki
     internal = sorted(set(ells) | ({0, 2, 4} if modified else set()))
     pl = {}
     for ell in internal:
-        v = np.real(f0 * np.conj(fields[ell]))
+        v = _part(ell, f0 * np.conj(fields[ell]))
         mean, _ = M.bin_average(v, b, nb)
         pl[ell] = np.where(empty, 0.0, (2 * ell + 1) / i22 * mean - (n0 if ell == 0 else 0.0))
     for ell in ells:
@@ -255,7 +261,7 @@ def cross_power_multipoles(spec, data_a, randoms_a, data_b, randoms_b, kbins, el
     empty = cnt == 0
     res = {"P": {}, "k_eff": kmean, "nmodes": cnt, "I22": i22, "scalars_a": sa, "scalars_b": sb}
     for ell in ells:
-        mean, _ = M.bin_average(np.real(fa[0] * np.conj(fb[ell])), b, nb)
+        mean, _ = M.bin_average(_part(ell, fa[0] * np.conj(fb[ell])), b, nb)
         res["P"][ell] = np.where(empty, 0.0, (2 * ell + 1) / i22 * mean)
     return res
 

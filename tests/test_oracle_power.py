@@ -274,3 +274,54 @@ def test_cross_is_symmetric_for_a_global_line_of_sight():
         assert np.max(np.abs(ab["P"][ell] - ba["P"][ell])) < 1e-12 * scale
     # and it is not the auto spectrum of either
     assert np.max(np.abs(ab["P"][0] - P.power_multipoles(spec, a, None, kb, (0,))["P"][0])) > 1e-3 * scale
+
+
+def test_odd_multipoles_symmetric_equals_hand17(small_survey):
+    """Odd l (Sec. 2.1: the imaginary part): Im<F_0 G_l^*> from the l+1 transforms equals
+    Im<F_0 F_l^*> of the Hand+17 sum over 2l+1 transforms."""
+    g, r, origin = small_survey
+    spec = _survey_spec(20, 1000.0, origin, 3, 1)
+    kb = (0.0, 0.02, 4)
+    a = P.power_multipoles(spec, g, r, kb, (0, 1, 3), method="plain")
+    b = P.power_multipoles(spec, g, r, kb, (0, 1, 3), method="symmetric")
+    scale = np.abs(a["P"][0]) + a["scalars"]["N0"]
+    for ell in (1, 3):
+        assert np.max(np.abs(a["P"][ell])) > 1e-6 * np.max(scale)   # wide-angle odd terms are not zero
+        assert np.max(np.abs(a["P"][ell] - b["P"][ell]) / scale) < 1e-13
+
+
+def test_odd_cross_multipoles_of_a_shifted_copy():
+    """Tracer B = tracer A moved by two cells along the line of sight (periodic box): F^B = e^{-i k.d}
+    F^A exactly, so P_l^AB = (2l+1)/I22 <|F^A|^2 L_l(mu) cos(k_z d)> (even l) and the same with
+    sin(k_z d) (odd l), and the odd auto multipoles vanish."""
+    from types import SimpleNamespace
+
+    from synthetic import make_periodic_catalog
+
+    box, n = 500.0, 20
+    a = make_periodic_catalog(4000, box, 16, seed=93, dtype=np.float64)
+    d = 2 * box / n
+    b = SimpleNamespace(pos=a.pos.copy(), w=a.w, nbar=a.nbar)
+    b.pos[:, 2] = np.mod(b.pos[:, 2] + d, box)
+    spec = dict(n=n, box=box, origin=(0.0, 0.0, 0.0), assign=3, interlace=1, los="global",
+                los_dir=(0.0, 0.0, 1.0), periodic=1)
+    kb = (0.0, 0.04, 4)
+    ells = (0, 1, 2, 3, 4)
+    cross = P.cross_power_multipoles(spec, a, None, b, None, kb, ells)
+    sc = P.catalog_scalars(a, None, box)
+    f0 = P.fields_plain(spec, P.fkp_meshes(spec, a, None, sc), [0])[0][0]
+    bidx, _ = M.bin_index(n, box, *kb)
+    (kx, ky, kz), _ = M.kvectors(n, box)
+    kk = np.sqrt(kx * kx + ky * ky + kz * kz)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        mu = np.where(kk > 0, kz / np.where(kk > 0, kk, 1.0), 0.0)
+    scale = np.max(np.abs(cross["P"][0]))
+    for ell in ells:
+        ph = np.sin(kz * d) if ell % 2 else np.cos(kz * d)
+        want, _ = M.bin_average(np.abs(f0) ** 2 * H.legendre(ell, mu) * ph, bidx, kb[2])
+        want = (2 * ell + 1) / sc["I22"] * want
+        assert np.max(np.abs(cross["P"][ell] - want)) < 1e-9 * scale, ell
+    assert np.max(np.abs(cross["P"][1])) > 1e-3 * scale
+    auto = P.power_multipoles(spec, a, None, kb, (0, 1, 3))
+    for ell in (1, 3):
+        assert np.max(np.abs(auto["P"][ell])) < 1e-12 * np.max(np.abs(auto["P"][0]))
