@@ -150,8 +150,10 @@ npc_status npc_catalog_scalars_noalloc(const npc_catalog* data, const npc_catalo
                                        double* out_device, void* cuda_stream, char* err, size_t errlen);
 
 /* Power-spectrum multipoles (Sec. 2.1 Eq. pk_final; Sec. 3 Eqs. Plnew, Pllp) ------------------
- * ell_mask: bit l requests P_l, l in {0, 2, 4}.  modified_mask: bits 4, 6, 8 request P_4b, P_6b,
- * P_8b (these need the l = 2 and l = 4 fields and are computed from them; Eq. Plnew).
+ * ell_mask: bit l requests P_l, l in {0, 1, 2, 3, 4}; odd l take the imaginary part of
+ * <F_0 F_l^*> (Sec. 2.1), which vanishes for an auto spectrum with a global line of sight.
+ * modified_mask: bits 4, 6, 8 request P_4b, P_6b, P_8b (these need the l = 2 and l = 4 fields and
+ * are computed from them; Eq. Plnew).
  * Output `out` (float64), length npc_power_out_len(), rows of nbins:
  *   [0]            k_eff  = mean |k| over the modes of the bin
  *   [1]            N_modes (number of full-grid modes in the bin)
@@ -176,9 +178,10 @@ int64_t npc_power_out_len(const npc_kbins* bins, uint32_t ell_mask, uint32_t mod
  * tracer B (its line of sight: observer to B's grid points, or the global los), F_0^A the FKP field
  * of A, I22^AB = sqrt(I22^A I22^B), and no shot noise subtracted (the tracers share no object).
  * Both tracers use the same mesh spec; randoms_a and randoms_b are both NULL (periodic box) or both
- * given (survey).  ell_mask: bits 0, 2, 4.  Cost: B's transforms plus one per phase for A.
+ * given (survey).  ell_mask: bits 0 .. 4.  Cost: B's transforms plus one per phase for A.
  * Output as npc_power_multipoles with modified_mask = 0 (length npc_power_out_len(bins, ell_mask,
  * 0)), the 8 trailing scalars being [alpha_A, I22^AB, alpha_B, 0, I22^A, I22^B, sum w_A, sum w_B].
+ * ell_mask may include the odd bits 1, 3 (imaginary part, as for npc_power_multipoles).
  * Errors: as npc_power_multipoles; NPC_ERR_NUMERIC for an empty catalogue of either tracer. */
 npc_status npc_cross_power_multipoles(npc_ctx* ctx, const npc_mesh_spec* mesh, const npc_catalog* data_a,
                                       const npc_catalog* randoms_a, const npc_catalog* data_b,
@@ -321,6 +324,18 @@ npc_status npc_paint_mesh(npc_ctx* ctx, const npc_mesh_spec* spec, const npc_cat
 npc_status npc_paint_adjoint(npc_ctx* ctx, const npc_mesh_spec* spec, const npc_catalog* data,
                              const void* grad_mesh, npc_precision prec, void* grad_pos,
                              void* grad_w);
+
+/* Single-purpose forms (float32 meshes, NPC_PREC_MIXED, device memory, host cotangents):
+ *   npc_power_vjp   = npc_mesh_multipoles_vjp with b0 = 0 (dl_dp[e][b] for the requested l);
+ *   npc_bispec0_vjp = npc_mesh_multipoles_vjp with ell_mask = 0, b0 = 1;
+ *   npc_tsc_adjoint = npc_paint_adjoint for TSC (spec->assign = 3, else NPC_ERR_INVALID_ARG),
+ *                     positions only (grad_pos of the catalogue's dtype). */
+npc_status npc_power_vjp(npc_ctx* ctx, const float* delta, const npc_mesh_spec* spec, const npc_kbins* bins,
+                         uint32_t ell_mask, double i22, const double* dl_dp, float* dl_ddelta);
+npc_status npc_bispec0_vjp(npc_ctx* ctx, const float* delta, const npc_mesh_spec* spec, const npc_kbins* bins,
+                           double i33, const double* dl_db0, float* dl_ddelta);
+npc_status npc_tsc_adjoint(npc_ctx* ctx, const npc_mesh_spec* spec, const npc_catalog* data, const float* grad_mesh,
+                           void* grad_pos);
 
 #ifdef __cplusplus
 }

@@ -94,6 +94,11 @@ _sig = {
     "npc_paint_mesh": (C.c_int, [C.c_void_p, _P(npc_mesh_spec), _P(npc_catalog), C.c_int, C.c_void_p]),
     "npc_paint_adjoint": (C.c_int, [C.c_void_p, _P(npc_mesh_spec), _P(npc_catalog), C.c_void_p, C.c_int,
                                     C.c_void_p, C.c_void_p]),
+    "npc_power_vjp": (C.c_int, [C.c_void_p, C.c_void_p, _P(npc_mesh_spec), _P(npc_kbins), C.c_uint32, C.c_double,
+                                C.c_void_p, C.c_void_p]),
+    "npc_bispec0_vjp": (C.c_int, [C.c_void_p, C.c_void_p, _P(npc_mesh_spec), _P(npc_kbins), C.c_double,
+                                  C.c_void_p, C.c_void_p]),
+    "npc_tsc_adjoint": (C.c_int, [C.c_void_p, _P(npc_mesh_spec), _P(npc_catalog), C.c_void_p, C.c_void_p]),
     "npc_stage_times": (C.c_int, [C.c_void_p, C.c_char_p, _P(C.c_double), _P(C.c_int32), C.c_int32,
                                   _P(C.c_int32)]),
 }

@@ -1221,4 +1221,27 @@ npc_status npc_paint_adjoint(npc_ctx* ctx, const npc_mesh_spec* spec, const npc_
   return end_call(ctx);
 }
 
+// Single-purpose forms of the calls above (float32 meshes, device memory)
+npc_status npc_power_vjp(npc_ctx* ctx, const float* delta, const npc_mesh_spec* spec, const npc_kbins* bins,
+                         uint32_t ell_mask, double i22, const double* dl_dp, float* dl_ddelta) {
+  return npc_mesh_multipoles_vjp(ctx, spec, delta, bins, ell_mask, 0, i22, 1.0, dl_dp, nullptr, 0,
+                                 NPC_PREC_MIXED, dl_ddelta);
+}
+
+npc_status npc_bispec0_vjp(npc_ctx* ctx, const float* delta, const npc_mesh_spec* spec, const npc_kbins* bins,
+                           double i33, const double* dl_db0, float* dl_ddelta) {
+  return npc_mesh_multipoles_vjp(ctx, spec, delta, bins, 0, 1, 1.0, i33, nullptr, dl_db0, 0, NPC_PREC_MIXED,
+                                 dl_ddelta);
+}
+
+npc_status npc_tsc_adjoint(npc_ctx* ctx, const npc_mesh_spec* spec, const npc_catalog* data, const float* grad_mesh,
+                           void* grad_pos) {
+  if (spec && spec->assign != 3) {
+    if (ctx) begin_call(ctx);
+    return ctx ? set_err(ctx, NPC_ERR_INVALID_ARG, "npc_tsc_adjoint needs spec->assign = 3 (TSC)")
+               : NPC_ERR_INVALID_ARG;
+  }
+  return npc_paint_adjoint(ctx, spec, data, grad_mesh, NPC_PREC_MIXED, grad_pos, nullptr);
+}
+
 }  // extern "C"

@@ -310,6 +310,9 @@ static PowerPlan make_power_plan(npc_ctx* ctx, const npc_mesh_spec& ms, const np
     const double r2 = (kmax / kf) * (kmax / kf);
     const double full = 3.0 * (n / 2) * (n / 2);
     plan.row_n2max = r2 >= full ? 0 : (int)std::floor(r2) + 1;
+    // planes kz > sqrt(row_n2max) hold no binned row: the forward passes stop below them
+    if (plan.row_n2max > 0)
+      plan.kz_keep = std::min(n / 2, (int)std::floor(std::sqrt((double)plan.row_n2max)) + 1);
   }
   int need = (int)ell_mask | 1;
   if (modified_mask) need |= 1 | 4 | 16;
@@ -319,14 +322,14 @@ static PowerPlan make_power_plan(npc_ctx* ctx, const npc_mesh_spec& ms, const np
   auto push = [&](int ph, int l, int m, int part) {
     Comp c;
     c.phase = (int8_t)ph; c.ell = (int8_t)l; c.m = (int8_t)m; c.part = (int8_t)part;
-    fl.f[fl.nf++] = c;
+    if (fl.nf < NPC_MAX_FIELDS) fl.f[fl.nf++] = c;   // 2 x 25 at most for l <= 4: always room
   };
   if (mesh->los == 1) {
     for (int ph = 0; ph < nphase; ++ph) push(ph, 0, 0, PART_ONE);
     ntr = 1;
     nr2c = 1;
   } else {
-    for (int l = 0; l <= 4; l += 2) {
+    for (int l = 0; l <= 4; ++l) {
       if (!(need & (1 << l))) continue;
       for (int m = 0; m <= l; ++m) {
         for (int ph = 0; ph < nphase; ++ph) {
@@ -389,7 +392,8 @@ static npc_status power_cross_core(npc_ctx* ctx, const npc_mesh_spec& ms, const 
   const Geom g = make_geom(ms);
   const size_t rs = prec == NPC_PREC_FP64 ? 8 : 4;
   const size_t ncell = (size_t)n * n * n;
-  const size_t fbytes = 2 * rs * (size_t)(n / 2) * n * n;   // one field's half spectrum
+  const int kzp = plan.kz_keep > 0 ? plan.kz_keep : n / 2;
+  const size_t fbytes = 2 * rs * (size_t)kzp * n * n;   // one field's half spectrum (kz < kzp)
   void *ma, *mb = nullptr, *half;
   NPC_TRY(ws_get(ctx, "mesh.a", rs * ncell, &ma));
   if (plan.nphase == 2) NPC_TRY(ws_get(ctx, "mesh.b", rs * ncell, &mb));
@@ -532,9 +536,9 @@ npc_status npc_catalog_scalars(npc_ctx* ctx, const npc_catalog* data, const npc_
 
 int64_t npc_power_out_len(const npc_kbins* bins, uint32_t ell_mask, uint32_t modified_mask) {
   if (!bins || bins->nbins < 1) return 0;
-  if ((ell_mask & ~0x15u) || (modified_mask & ~0x150u) || (ell_mask == 0 && modified_mask == 0)) return 0;
+  if ((ell_mask & ~0x1Fu) || (modified_mask & ~0x150u) || (ell_mask == 0 && modified_mask == 0)) return 0;
   int rows = 2;
-  for (int l = 0; l <= 4; l += 2) rows += (ell_mask >> l) & 1;
+  for (int l = 0; l <= 4; ++l) rows += (ell_mask >> l) & 1;
   for (int l = 4; l <= 8; l += 2) rows += (modified_mask >> l) & 1;
   return (int64_t)rows * bins->nbins + 8;
 }
@@ -549,7 +553,7 @@ npc_status npc_power_multipoles(npc_ctx* ctx, const npc_mesh_spec* mesh, const n
   if (!out) return set_err(ctx, NPC_ERR_INVALID_ARG, "out is NULL");
   const int64_t out_len = npc_power_out_len(bins, ell_mask, modified_mask);
   if (out_len == 0)
-    return set_err(ctx, NPC_ERR_INVALID_ARG, "ell_mask must use bits 0,2,4 and modified_mask bits 4,6,8");
+    return set_err(ctx, NPC_ERR_INVALID_ARG, "ell_mask must use bits 0..4 and modified_mask bits 4,6,8");
   if (prec != NPC_PREC_FP64 && prec != NPC_PREC_MIXED) return set_err(ctx, NPC_ERR_INVALID_ARG, "bad precision");
   if (prec == NPC_PREC_FP64 && mesh->n > 256) return set_err(ctx, NPC_ERR_UNSUPPORTED, "FP64 precision supports n <= 256");
   NPC_TRY(check_catalog(ctx, data, "data", false));
@@ -589,7 +593,7 @@ npc_status npc_cross_power_multipoles(npc_ctx* ctx, const npc_mesh_spec* mesh, c
   NPC_TRY(check_bins(ctx, bins));
   if (!out) return set_err(ctx, NPC_ERR_INVALID_ARG, "out is NULL");
   const int64_t out_len = npc_power_out_len(bins, ell_mask, 0);
-  if (out_len == 0) return set_err(ctx, NPC_ERR_INVALID_ARG, "ell_mask must use bits 0,2,4");
+  if (out_len == 0) return set_err(ctx, NPC_ERR_INVALID_ARG, "ell_mask must use bits 0..4");
   if (prec != NPC_PREC_FP64 && prec != NPC_PREC_MIXED) return set_err(ctx, NPC_ERR_INVALID_ARG, "bad precision");
   if (prec == NPC_PREC_FP64 && mesh->n > 256) return set_err(ctx, NPC_ERR_UNSUPPORTED, "FP64 precision supports n <= 256");
   NPC_TRY(check_catalog(ctx, data_a, "data_a", false));

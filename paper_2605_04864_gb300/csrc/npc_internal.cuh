@@ -132,7 +132,7 @@ struct Comp {          // one real field: mesh phase x weight function
   int8_t tracer = 0;   // 1: F_0 of the first tracer A of a cross spectrum (the others are B's)
 };
 
-constexpr int NPC_MAX_FIELDS = 40;  // real fields per call (2 phases x 15 for l <= 4, + spare)
+constexpr int NPC_MAX_FIELDS = 56;  // real fields per call (2 phases x 25 for l = 0 .. 4, + tracer A)
 
 struct FieldList {
   int nf;                     // number of real fields

@@ -30,7 +30,7 @@
 namespace {
 
 constexpr int CONTRACT_THREADS = 256;
-constexpr int MAX_SUMS = 8;
+constexpr int MAX_SUMS = 10;
 
 template <int N> struct ColCfg {
   static constexpr int TX = N >= 1024 ? 4 : (N >= 512 ? 8 : 16);  // TX <= N
@@ -179,11 +179,18 @@ k_fwd_z_single(const T* __restrict__ mesh, cplx<T>* __restrict__ half, const cpl
 // a/b whose real and imaginary parts share one Y evaluation.  Pairs are a prefix of
 //   (0,0,0) (2,0,0) (2,1,1) (2,1,2) (2,2,1) (2,2,2) (4,0,0) (4,1,1) (4,1,2) ... (4,4,1) (4,4,2).
 // ---------------------------------------------------------------------------------------------
-// Polynomial factor Q_lm(uz) of Y_lm = norm_lm Q_lm(uz) (ux + i uy)^m, l <= 4.
+// Polynomial factor Q_lm(uz) of Y_lm = norm_lm Q_lm(uz) (ux + i uy)^m, l <= 4: the associated
+// Legendre function with its (-1)^m phase, divided by sin^m(theta).
 template <typename T, int L, int M>
 __device__ __forceinline__ T ylm_q(T uz) {
   const T z2 = uz * uz;
   if constexpr (L == 0) return T(1);
+  else if constexpr (L == 1 && M == 0) return uz;
+  else if constexpr (L == 1 && M == 1) return T(-1);
+  else if constexpr (L == 3 && M == 0) return T(0.5) * uz * (T(5) * z2 - T(3));
+  else if constexpr (L == 3 && M == 1) return T(-1.5) * (T(5) * z2 - T(1));
+  else if constexpr (L == 3 && M == 2) return T(15) * uz;
+  else if constexpr (L == 3 && M == 3) return T(-15);
   else if constexpr (L == 2 && M == 0) return T(1.5) * z2 - T(0.5);
   else if constexpr (L == 2 && M == 1) return T(-3) * uz;
   else if constexpr (L == 2 && M == 2) return T(3);
@@ -415,9 +422,11 @@ template <typename T> __device__ __forceinline__ T coef_scale(const FieldCoef& c
 template <> __device__ __forceinline__ float coef_scale<float>(const FieldCoef& c) { return c.scale_f; }
 template <> __device__ __forceinline__ double coef_scale<double>(const FieldCoef& c) { return c.scale_d; }
 
-// Row Y table: Y_lm(khat) in the fixed order (2,0) (2,1) (2,2) (4,0) (4,1) (4,2) (4,3) (4,4).
-constexpr int MAX_YTAB = 8;
-__host__ __device__ constexpr int ytab_index(int l, int m) { return l == 2 ? m : 3 + m; }
+// Row Y table: Y_lm(khat) in the fixed order (2,0) (2,1) (2,2) (4,0) .. (4,4) (1,0) (1,1) (3,0) .. (3,3).
+constexpr int MAX_YTAB = 14;
+__host__ __device__ constexpr int ytab_index(int l, int m) {
+  return l == 2 ? m : (l == 4 ? 3 + m : (l == 1 ? 8 + m : 10 + m));
+}
 // Field slots of the x pass: slot[r * G + g] is the field row group g transforms in round r.
 constexpr int MAX_SLOTS = 256;
 
@@ -434,11 +443,16 @@ struct ContractParams {
   int8_t slot[MAX_SLOTS];       // field per (round, group), -1 for none
   int nbins, nsum;
   int row_n2max;                // rows (ky, kz) with ky^2 + kz^2 above this hold no binned mode
+  int KZ;                       // planes kz < KZ stored per field by the forward passes
   int nell;
-  int ell_list[3];
+  int ell_list[5];
   int nll;
   int lla[3], llb[3];
   int need2, need4;
+  int need_mask;                // multipoles l whose F_l the binning forms (bit l)
+  int acc_of[5];                // accumulator of F_l (tracer B), -1 if none
+  int ymask;                    // Y table groups evaluated per row: bit l for l = 1 .. 4
+  int even_layout;              // acc_of = {0, -1, 1 or -1, -1, 2 or -1}: the fixed even-l layout
   int global_los;
   double los[3];
   int assign;
@@ -490,7 +504,7 @@ k_fft_x_contract(const cplx<T>* __restrict__ half, const ContractParams P, const
   for (int i = tid; i <= N / 2; i += blockDim.x) winv[i] = T(1) / sinc_pow<T>(T(M_PI) * T(i) / T(N), P.assign);
   __syncthreads();
   double* mypart = part + ((size_t)blockIdx.x * NW + warp) * P.nbins * P.nsum;
-  const int nrows = (N / 2) * N;
+  const int nrows = P.KZ * N;
   const int g = tid / TPF, t = tid % TPF;
   const bool ingroup = g < G;
   const T half_or_one = P.nphase == 2 ? T(0.5) : T(1);
@@ -518,10 +532,20 @@ k_fft_x_contract(const cplx<T>* __restrict__ half, const ContractParams P, const
         const T inv = r2 > T(0) ? rsqrt(r2) : T(0);
         const T ux = fi * inv, uy = fj * inv, uz = r2 > T(0) ? fk * inv : T(1);
         T re, im;
+        if (P.ymask & 2) {
+          ylm_ct<T, 1, 0>(ux, uy, uz, nrm, re, im); ytab[8 * N + kx] = cmk(re, im);
+          ylm_ct<T, 1, 1>(ux, uy, uz, nrm, re, im); ytab[9 * N + kx] = cmk(re, im);
+        }
+        if (P.ymask & 8) {
+          ylm_ct<T, 3, 0>(ux, uy, uz, nrm, re, im); ytab[10 * N + kx] = cmk(re, im);
+          ylm_ct<T, 3, 1>(ux, uy, uz, nrm, re, im); ytab[11 * N + kx] = cmk(re, im);
+          ylm_ct<T, 3, 2>(ux, uy, uz, nrm, re, im); ytab[12 * N + kx] = cmk(re, im);
+          ylm_ct<T, 3, 3>(ux, uy, uz, nrm, re, im); ytab[13 * N + kx] = cmk(re, im);
+        }
         ylm_ct<T, 2, 0>(ux, uy, uz, nrm, re, im); ytab[0 * N + kx] = cmk(re, im);
         ylm_ct<T, 2, 1>(ux, uy, uz, nrm, re, im); ytab[1 * N + kx] = cmk(re, im);
         ylm_ct<T, 2, 2>(ux, uy, uz, nrm, re, im); ytab[2 * N + kx] = cmk(re, im);
-        if (P.ny > 3) {
+        if (P.ymask & 16) {
           ylm_ct<T, 4, 0>(ux, uy, uz, nrm, re, im); ytab[3 * N + kx] = cmk(re, im);
           ylm_ct<T, 4, 1>(ux, uy, uz, nrm, re, im); ytab[4 * N + kx] = cmk(re, im);
           ylm_ct<T, 4, 2>(ux, uy, uz, nrm, re, im); ytab[5 * N + kx] = cmk(re, im);
@@ -534,7 +558,7 @@ k_fft_x_contract(const cplx<T>* __restrict__ half, const ContractParams P, const
     __syncthreads();
     C v[8], vn[8], racc[8];
     int cur = -1;   // accumulator held in racc
-    const size_t fstride = (size_t)(N / 2) * N * N;
+    const size_t fstride = (size_t)P.KZ * N * N;
     const size_t roff = ((size_t)kz * N + ky) * N;
     int f = ingroup ? P.slot[g] : -1;
     if (f >= 0) {
@@ -603,52 +627,72 @@ k_fft_x_contract(const cplx<T>* __restrict__ half, const ContractParams P, const
       for (int s = 0; s < MAX_SUMS; ++s) vals[s] = T(0);
       if (bin >= 0) {
         const T wgt = kz > 0 ? T(2) : T(1);
-        C F0 = cmk(T(0), T(0)), F2 = cmk(T(0), T(0)), F4 = cmk(T(0), T(0)), FA = cmk(T(0), T(0));
-        // sum of the group accumulators g0, g0 + gstep, ... in g order
-        auto gsum = [&](int g0, int gstep, C& s0, C& s2, C& s4, C& sa) {
+        // accumulators summed over the groups: phase a (even g, or all with one phase) and phase b
+        C Aa[6], Ab[6];
+#pragma unroll
+        for (int a = 0; a < 6; ++a) Aa[a] = Ab[a] = cmk(T(0), T(0));
+        auto gsum = [&](int g0, int gstep, C (&acc)[6]) {
           for (int gg = g0; gg < G; gg += gstep) {
             const C* fg = facc + (size_t)gg * P.nacc * N + j;
-            s0 = cadd(s0, fg[0]);
-            if (P.nacc_b > 1) s2 = cadd(s2, fg[N]);
-            if (P.nacc_b > 2) s4 = cadd(s4, fg[2 * N]);
-            if (P.acc_a >= 0) sa = cadd(sa, fg[(size_t)P.acc_a * N]);
+#pragma unroll
+            for (int a = 0; a < 6; ++a)
+              if (a < P.nacc) acc[a] = cadd(acc[a], fg[(size_t)a * N]);
           }
         };
         if (P.phase_pure) {
-          // groups of phase a (even g, or all with one phase) and of phase b (odd g)
-          gsum(0, P.nphase == 2 ? 2 : 1, F0, F2, F4, FA);
+          gsum(0, P.nphase == 2 ? 2 : 1, Aa);
           const T faj = fa[j];
-          F0 = cscale(F0, faj);
-          F2 = cscale(F2, faj);
-          F4 = cscale(F4, faj);
-          FA = cscale(FA, faj);
+#pragma unroll
+          for (int a = 0; a < 6; ++a) Aa[a] = cscale(Aa[a], faj);
           if (P.nphase == 2) {
-            C B0 = cmk(T(0), T(0)), B2 = cmk(T(0), T(0)), B4 = cmk(T(0), T(0)), BA = cmk(T(0), T(0));
-            gsum(1, 2, B0, B2, B4, BA);
+            gsum(1, 2, Ab);
             const C fbj = fb[j];
-            F0 = cadd(F0, cmul(B0, fbj));
-            F2 = cadd(F2, cmul(B2, fbj));
-            F4 = cadd(F4, cmul(B4, fbj));
-            FA = cadd(FA, cmul(BA, fbj));
+#pragma unroll
+            for (int a = 0; a < 6; ++a) Aa[a] = cadd(Aa[a], cmul(Ab[a], fbj));
           }
         } else {
-          gsum(0, 1, F0, F2, F4, FA);
+          gsum(0, 1, Aa);
+        }
+        auto pick = [&](int k) {   // accumulator k (runtime index kept out of local memory)
+          C r = cmk(T(0), T(0));
+#pragma unroll
+          for (int a = 0; a < 6; ++a)
+            if (k == a) r = Aa[a];
+          return r;
+        };
+        const C F0 = Aa[0];
+        C F1, F2, F3, F4, FA;
+        if (P.even_layout) {   // accumulators F_0, F_2, F_4 (when present) at 0, 1, 2, then F_0^A
+          F1 = F3 = cmk(T(0), T(0));
+          F2 = Aa[1];
+          F4 = Aa[2];
+          FA = P.acc_a == 1 ? Aa[1] : (P.acc_a == 2 ? Aa[2] : Aa[3]);
+        } else {
+          F1 = pick(P.acc_of[1]);
+          F2 = pick(P.acc_of[2]);
+          F3 = pick(P.acc_of[3]);
+          F4 = pick(P.acc_of[4]);
+          FA = pick(P.acc_a);
         }
         const T fi = T(i);
         const T kk = sqrt(fi * fi + fjy * fjy + fkz * fkz);
         if (P.global_los) {
           const T mu = (fi * T(P.los[0]) + fjy * T(P.los[1]) + fkz * T(P.los[2])) / kk;
-          if (P.need2) F2 = cscale(F0, legendre_p<T>(2, mu));
-          if (P.need4) F4 = cscale(F0, legendre_p<T>(4, mu));
+          if (P.need_mask & 2) F1 = cscale(F0, legendre_p<T>(1, mu));
+          if (P.need_mask & 4) F2 = cscale(F0, legendre_p<T>(2, mu));
+          if (P.need_mask & 8) F3 = cscale(F0, legendre_p<T>(3, mu));
+          if (P.need_mask & 16) F4 = cscale(F0, legendre_p<T>(4, mu));
         }
-        auto sel = [&](int l) { return l == 0 ? F0 : (l == 2 ? F2 : F4); };
+        auto sel = [&](int l) { return l == 0 ? F0 : (l == 1 ? F1 : (l == 2 ? F2 : (l == 3 ? F3 : F4))); };
 #pragma unroll
         for (int s = 0; s < MAX_SUMS; ++s) {
           T v = T(0);
           if (s < P.nell) {
-            const C b = sel(P.ell_list[s]);
+            const int l = P.ell_list[s];
+            const C b = sel(l);
             const C a = P.acc_a >= 0 ? FA : F0;   // cross: F_0 of tracer A against F_l of B
-            v = wgt * (a.x * b.x + a.y * b.y);
+            // even l: Re a b^*; odd l: Im a b^* (Sec. 2.1, odd multipoles)
+            v = wgt * ((l & 1) ? (a.y * b.x - a.x * b.y) : (a.x * b.x + a.y * b.y));
           } else if (s < P.nell + P.nll) {
             const C a = sel(P.lla[s - P.nell]), b = sel(P.llb[s - P.nell]);
             v = wgt * (a.x * b.x + a.y * b.y);
@@ -694,7 +738,7 @@ k_fft_x_contract(const cplx<T>* __restrict__ half, const ContractParams P, const
 
 struct FinalParams {
   int nbins, nsum, nparts;
-  int nell, ell_list[3];
+  int nell, ell_list[5];
   int nll, lla[3], llb[3];
   int nmod, mod_list[3];
   int out_rows;          // 2 + requested P_l + requested P_lb
@@ -729,12 +773,12 @@ k_power_finalize(const double* __restrict__ part, const FinalParams F, const dou
     const bool ok = cnt > 0;
     out[0 * nb + b] = ok ? S[F.nsum - 1] / cnt : 0.0;
     out[1 * nb + b] = cnt;
-    double Pl[5] = {0, 0, 0, 0, 0};   // index l/2
+    double Pl[5] = {0, 0, 0, 0, 0};   // index l
     int row = 2;
     for (int e = 0; e < F.nell; ++e) {
       const int l = F.ell_list[e];
       const double v = ok ? (2 * l + 1) / i22 * S[e] / cnt - (l == 0 ? n0 : 0.0) : 0.0;
-      Pl[l / 2] = v;
+      Pl[l] = v;
       if (F.req_mask & (1 << l)) out[(row++) * nb + b] = v;
     }
     double P22 = 0, P42 = 0, P44 = 0;
@@ -750,10 +794,10 @@ k_power_finalize(const double* __restrict__ part, const FinalParams F, const dou
       const int lb = F.mod_list[e];
       double v = 0.0;
       if (ok) {
-        if (lb == 4) v = 35.0 / 18.0 * P22 - Pl[1] - 3.5 * Pl[0];
-        if (lb == 6) v = 11.0 / 5.0 * P42 - 52.0 / 63.0 * Pl[2] - 286.0 / 175.0 * Pl[1];
+        if (lb == 4) v = 35.0 / 18.0 * P22 - Pl[2] - 3.5 * Pl[0];
+        if (lb == 6) v = 11.0 / 5.0 * P42 - 52.0 / 63.0 * Pl[4] - 286.0 / 175.0 * Pl[2];
         if (lb == 8)
-          v = 1287.0 / 490.0 * P44 - 374.0 / 245.0 * P42 - 3553.0 / 15435.0 * Pl[2] - 1326.0 / 8575.0 * Pl[1] -
+          v = 1287.0 / 490.0 * P44 - 374.0 / 245.0 * P42 - 3553.0 / 15435.0 * Pl[4] - 1326.0 / 8575.0 * Pl[2] -
               2431.0 / 490.0 * Pl[0];
       }
       out[(row++) * nb + b] = v;
@@ -904,15 +948,32 @@ npc_status contract_impl(npc_ctx* ctx, const PowerPlan& plan, const npc_mesh_spe
   if (plan.mod_mask) req_internal |= 1 | 4 | 16;
   P.need2 = (req_internal & 4) ? 1 : 0;
   P.need4 = (req_internal & 16) ? 1 : 0;
-  P.nacc_b = plan.global_los ? 1 : (P.need4 ? 3 : (P.need2 ? 2 : 1));
+  P.need_mask = req_internal | 1;
+  // accumulators: one per multipole with fields of tracer B (in l order), then F_0^A
+  for (int l = 0; l <= 4; ++l) P.acc_of[l] = -1;
+  P.nacc_b = 0;
+  if (plan.global_los) {
+    P.acc_of[0] = 0;
+    P.nacc_b = 1;
+  } else {
+    for (int l = 0; l <= 4; ++l) {
+      bool has = false;
+      for (int f = 0; f < plan.fl.nf; ++f) has |= !plan.fl.f[f].tracer && plan.fl.f[f].ell == l;
+      if (has) P.acc_of[l] = P.nacc_b++;
+    }
+  }
   P.acc_a = plan.cross ? P.nacc_b : -1;
   P.nacc = P.nacc_b + (plan.cross ? 1 : 0);
+  if (P.nacc > 6) return set_err(ctx, NPC_ERR_UNSUPPORTED, "x pass: at most 6 accumulators");
+  P.even_layout = (P.acc_of[1] < 0 && P.acc_of[3] < 0 && (P.acc_of[2] == 1 || P.acc_of[2] < 0) &&
+                   (P.acc_of[4] == 2 || P.acc_of[4] < 0) && (P.acc_a < 0 || P.acc_a <= 3)) ? 1 : 0;
   if (plan.cross && plan.mod_mask)
     return set_err(ctx, NPC_ERR_UNSUPPORTED, "cross spectra: no modified multipoles");
+  P.ymask = 0;
   for (int f = 0; f < plan.fl.nf; ++f) {
     const Comp c = plan.fl.f[f];
     FieldCoef fc;
-    fc.acc = (int8_t)(c.tracer ? P.acc_a : c.ell / 2);
+    fc.acc = (int8_t)(c.tracer ? P.acc_a : (plan.global_los ? 0 : P.acc_of[c.ell]));
     if (c.tracer && (!plan.cross || c.part != PART_ONE))
       return set_err(ctx, NPC_ERR_INVALID_ARG, "x pass: tracer-A field must be an unweighted F_0");
     fc.phase = c.phase;
@@ -921,10 +982,11 @@ npc_status contract_impl(npc_ctx* ctx, const PowerPlan& plan, const npc_mesh_spe
     fc.scale_d = 1.0;
     fc.scale_f = 1.0f;
     if (c.part == PART_RE || c.part == PART_IM) {
-      if ((c.ell != 2 && c.ell != 4) || c.m < 0 || c.m > c.ell)
+      if (c.ell < 1 || c.ell > 4 || c.m < 0 || c.m > c.ell)
         return set_err(ctx, NPC_ERR_UNSUPPORTED, "Y_%d%d field in the x pass", c.ell, c.m);
       fc.yidx = (int8_t)ytab_index(c.ell, c.m);
-      P.ny = std::max(P.ny, c.ell == 4 ? 8 : 3);
+      P.ymask |= 1 << c.ell;
+      P.ny = std::max(P.ny, (P.ymask & 10) ? 14 : ((P.ymask & 16) ? 8 : 3));
       fc.scale_d = 4.0 * M_PI / (2 * c.ell + 1) * (c.m > 0 ? 2.0 : 1.0);
       fc.scale_f = (float)fc.scale_d;
     }
@@ -965,13 +1027,14 @@ npc_status contract_impl(npc_ctx* ctx, const PowerPlan& plan, const npc_mesh_spe
   }
   P.nbins = kb.nbins;
   P.nell = 0;
-  for (int l = 0; l <= 4; l += 2)
+  for (int l = 0; l <= 4; ++l)
     if (req_internal & (1 << l)) P.ell_list[P.nell++] = l;
   P.nll = 0;
   if (plan.mod_mask & (1 << 4)) { P.lla[P.nll] = 2; P.llb[P.nll] = 2; P.nll++; }
   if (plan.mod_mask & ((1 << 6) | (1 << 8))) { P.lla[P.nll] = 4; P.llb[P.nll] = 2; P.nll++; }
   if (plan.mod_mask & (1 << 8)) { P.lla[P.nll] = 4; P.llb[P.nll] = 4; P.nll++; }
   P.nsum = P.nell + P.nll + 2;
+  P.KZ = plan.kz_keep > 0 ? std::min(plan.kz_keep, N / 2) : N / 2;
   P.global_los = plan.global_los;
   for (int a = 0; a < 3; ++a) P.los[a] = plan.los[a];
   P.assign = plan.assign;
@@ -993,7 +1056,7 @@ npc_status contract_impl(npc_ctx* ctx, const PowerPlan& plan, const npc_mesh_spe
   int per_sm = 0;
   NPC_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, CONTRACT_THREADS, smem));
   if (per_sm < 1) return set_err(ctx, NPC_ERR_UNSUPPORTED, "contraction does not fit on an SM (%zu B smem)", smem);
-  const int nrows = (N / 2) * N;
+  const int nrows = P.KZ * N;
   const int grid = std::min(nrows, per_sm * ctx->num_sms);
   const int nw = CONTRACT_THREADS / 32;
   const size_t nparts = (size_t)grid * nw;
@@ -1018,7 +1081,7 @@ npc_status contract_impl(npc_ctx* ctx, const PowerPlan& plan, const npc_mesh_spe
   for (int lb = 4; lb <= 8; lb += 2)
     if (plan.mod_mask & (1 << lb)) F.mod_list[F.nmod++] = lb;
   int nreq = 0;
-  for (int l = 0; l <= 4; l += 2) nreq += (plan.ells_mask >> l) & 1;
+  for (int l = 0; l <= 4; ++l) nreq += (plan.ells_mask >> l) & 1;
   F.out_rows = 2 + nreq + F.nmod;
   F.req_mask = plan.ells_mask;
   k_power_finalize<<<std::min(P.nbins, 1024), FIN_THREADS, 0, ctx->stream>>>(part, F, sc, dev_out);

@@ -378,3 +378,48 @@ def test_full_size_1024(mods):
     assert fd == pytest.approx(an, rel=2e-3)
     del g, v
     torch.cuda.empty_cache()
+
+
+def test_single_purpose_entry_points(mods):
+    """npc_power_vjp, npc_bispec0_vjp and npc_tsc_adjoint equal the general calls bit for bit."""
+    A, _, B = mods
+    n, box = 32, 400.0
+    m, cat = _oracle_mesh(n, box, 20000, seed=171)
+    mesh = _dev(m, torch.float32)
+    kb = (0.02, 0.02, 5)
+    i22, i33 = 1.7e3, 2.3e5
+    rng = np.random.default_rng(5)
+    dldp = {l: rng.standard_normal(kb[2]) for l in (0, 2)}
+    dldb = rng.standard_normal(kb[2])
+    spec = A.make_spec(n, box, (0, 0, 0), 3, 0, 1, (0.0, 0.0, 1.0))
+    kbs = B.npc_kbins(*kb)
+    h = A.context(0)
+    g_ref = _vjp(mods, mesh, box, kb, (0, 2), False, i22, i33, dldp, None, "mixed")
+    g = torch.empty_like(mesh)
+    dp = np.ascontiguousarray(np.stack([dldp[0], dldp[2]]))
+    B.check(B.npc_power_vjp(h, C.c_void_p(mesh.data_ptr()), C.byref(spec), C.byref(kbs), 5, i22,
+                            dp.ctypes.data_as(C.c_void_p), C.c_void_p(g.data_ptr())), h)
+    torch.cuda.synchronize()
+    assert torch.equal(g, g_ref)
+    g_ref = _vjp(mods, mesh, box, kb, (), True, i22, i33, {}, dldb, "mixed")
+    db = np.ascontiguousarray(dldb)
+    B.check(B.npc_bispec0_vjp(h, C.c_void_p(mesh.data_ptr()), C.byref(spec), C.byref(kbs), i33,
+                              db.ctypes.data_as(C.c_void_p), C.c_void_p(g.data_ptr())), h)
+    torch.cuda.synchronize()
+    assert torch.equal(g, g_ref)
+    # TSC adjoint against the general paint adjoint
+    pos = torch.tensor(cat.pos, dtype=torch.float32, device="cuda")
+    w = torch.tensor(cat.w, dtype=torch.float32, device="cuda")
+    from types import SimpleNamespace
+
+    keep = A._Keep()
+    dc = A.make_catalog(SimpleNamespace(pos=pos, w=w, nbar=None), keep)
+    gp_ref = torch.zeros_like(pos)
+    gw = torch.zeros_like(w)
+    B.check(B.npc_paint_adjoint(h, C.byref(spec), C.byref(dc), C.c_void_p(mesh.data_ptr()), A._prec("mixed"),
+                                C.c_void_p(gp_ref.data_ptr()), C.c_void_p(gw.data_ptr())), h)
+    gp = torch.zeros_like(pos)
+    B.check(B.npc_tsc_adjoint(h, C.byref(spec), C.byref(dc), C.c_void_p(mesh.data_ptr()), C.c_void_p(gp.data_ptr())),
+            h)
+    torch.cuda.synchronize()
+    assert torch.equal(gp, gp_ref)

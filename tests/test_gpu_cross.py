@@ -87,4 +87,25 @@ def test_cross_rejects(api):
     with pytest.raises(RuntimeError):
         api.cross_power_multipoles(a, None, g, r, n=32, box=500.0, kbins=(0.0, 0.02, 4))   # one randoms only
     with pytest.raises(RuntimeError):
-        api.cross_power_multipoles(a, None, a, None, n=32, box=500.0, kbins=(0.0, 0.02, 4), ells=(1,))
+        api.cross_power_multipoles(a, None, a, None, n=32, box=500.0, kbins=(0.0, 0.02, 4), ells=(5,))
+
+
+def test_odd_cross_of_a_shifted_copy(api):
+    """Cross multipoles of a tracer and its copy moved two cells along the line of sight: the odd
+    P_1, P_3 (imaginary part) and the even ones against the oracle, periodic, global LOS."""
+    from types import SimpleNamespace
+
+    box, n = 500.0, 32
+    a = make_periodic_catalog(30000, box, 32, seed=141, dtype=np.float64)
+    b = SimpleNamespace(pos=a.pos.copy(), w=a.w, nbar=a.nbar)
+    b.pos[:, 2] = np.mod(b.pos[:, 2] + 2 * box / n, box)
+    kb = (0.0, 0.02, 8)
+    res = api.cross_power_multipoles(a, None, b, None, n=n, box=box, kbins=kb, ells=(0, 1, 2, 3, 4),
+                                     precision="fp64", los_dir=(0.0, 0.0, 1.0))
+    spec = dict(n=n, box=box, origin=(0.0, 0.0, 0.0), assign=3, interlace=1, los="global",
+                los_dir=(0.0, 0.0, 1.0), periodic=1)
+    orc = P.cross_power_multipoles(spec, a, None, b, None, kb, (0, 1, 2, 3, 4))
+    scale = _scale(orc)
+    for l in (0, 1, 2, 3, 4):
+        assert np.max(p_error(res["P"][l], orc["P"][l], scale)) < 1e-12, l
+    assert np.max(np.abs(orc["P"][1]) / scale) > 1e-3

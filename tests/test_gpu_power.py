@@ -207,3 +207,17 @@ def test_full_size_512_monopole(api):
     np.testing.assert_array_equal(res["nmodes"], cnt)
     e = p_error(res["P"][0], p0, np.abs(p0) + sc["N0"])
     assert np.max(e) < 1e-5, np.max(e)
+
+
+@pytest.mark.parametrize("prec,tol,n", [("fp64", 1e-12, 32), ("mixed", 1e-5, 64)])
+def test_odd_multipoles_survey(api, prec, tol, n):
+    """Odd P_1, P_3 (imaginary part, Sec. 2.1) with the endpoint line of sight, together with the
+    even ones and the modified multipoles (ten sums per bin)."""
+    g, r, origin = make_survey_catalogs(20000, 200000, 1000.0, 1200.0, 24, seed=61, fkp_p0=1e4)
+    kb = (0.0, 0.015, 8)
+    res = api.power_multipoles(g, r, n=n, box=1000.0, origin=origin, kbins=kb, ells=(0, 1, 2, 3, 4),
+                               modified=(4, 6, 8), precision=prec)
+    orc = _oracle(g, r, origin, n, 1000.0, 3, 1, kb, (0, 1, 2, 3, 4), (4, 6, 8))
+    _compare(res, orc, (0, 1, 2, 3, 4), (4, 6, 8), tol)
+    scale = np.abs(orc["P"][0]) + orc["scalars"]["N0"]
+    assert np.max(np.abs(orc["P"][1]) / scale) > 1e-6   # the odd terms measured are not all zero
