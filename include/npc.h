@@ -153,12 +153,14 @@ npc_status npc_catalog_scalars_noalloc(const npc_catalog* data, const npc_catalo
  * ell_mask: bit l requests P_l, l in {0, 1, 2, 3, 4}; odd l take the imaginary part of
  * <F_0 F_l^*> (Sec. 2.1), which vanishes for an auto spectrum with a global line of sight.
  * modified_mask: bits 4, 6, 8 request P_4b, P_6b, P_8b (these need the l = 2 and l = 4 fields and
- * are computed from them; Eq. Plnew).
+ * are computed from them; Eq. Plnew); bits 16, 17, 18 request the two-index multipoles P_22, P_42,
+ * P_44 themselves (Eq. Pllp, shot noise N_ll' subtracted).
  * Output `out` (float64), length npc_power_out_len(), rows of nbins:
  *   [0]            k_eff  = mean |k| over the modes of the bin
  *   [1]            N_modes (number of full-grid modes in the bin)
  *   [2 .. 2+nl)    P_l for the requested l in increasing order, shot noise subtracted (l = 0)
  *   [.. + nm)      P_4b, P_6b, P_8b for the requested ones in increasing order
+ *   [.. + nll)     P_22, P_42, P_44 for the requested ones in that order
  *   then 8 scalars as in npc_catalog_scalars.
  * Empty bins report k_eff = N_modes = P = 0.  data->n may be 0 only for a survey (randoms give
  * a zero field and P_0 = -N0); a periodic box needs data->n > 0 (else NPC_ERR_NUMERIC).

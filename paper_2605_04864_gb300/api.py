@@ -113,8 +113,9 @@ def _prec(p):
 
 def power_multipoles(data, randoms, n, box, origin=(0.0, 0.0, 0.0), assign=3, interlace=1, kbins=(0.0, 0.01, 10),
                      ells=(0, 2, 4), modified=(), precision="mixed", periodic=None, los_dir=None,
-                     observer=(0.0, 0.0, 0.0), device=0, out=None):
-    """Yamamoto P_l (and P_lb).  Returns a dict of NumPy arrays, or fills the device tensor ``out``."""
+                     observer=(0.0, 0.0, 0.0), device=0, out=None, two_index=()):
+    """Yamamoto P_l (and P_lb; ``two_index`` lists (l, l') of P_22, P_42, P_44 to report).  Returns
+    a dict of NumPy arrays, or fills the device tensor ``out``."""
     keep = _Keep()
     if periodic is None:
         periodic = randoms is None
@@ -122,6 +123,8 @@ def power_multipoles(data, randoms, n, box, origin=(0.0, 0.0, 0.0), assign=3, in
     kb = B.npc_kbins(float(kbins[0]), float(kbins[1]), int(kbins[2]))
     emask = sum(1 << int(l) for l in ells)
     mmask = sum(1 << int(l) for l in modified)
+    ll_bits = {(2, 2): 16, (4, 2): 17, (4, 4): 18}
+    mmask += sum(1 << ll_bits[tuple(p)] for p in two_index)
     length = max(int(B.npc_power_out_len(C.byref(kb), emask, mmask)), 1)  # the library rejects bad requests
     d = make_catalog(data, keep)
     r = make_catalog(randoms, keep)
@@ -133,7 +136,7 @@ def power_multipoles(data, randoms, n, box, origin=(0.0, 0.0, 0.0), assign=3, in
     buf = np.zeros(length)
     B.check(B.npc_power_multipoles(ctx, C.byref(spec), C.byref(d), C.byref(r) if r else None, C.byref(kb),
                                    emask, mmask, _prec(precision), buf.ctypes.data_as(C.c_void_p), 0), ctx)
-    return unpack_power(buf, kbins[2], ells, modified)
+    return unpack_power(buf, kbins[2], ells, modified, two_index)
 
 
 def cross_power_multipoles(data_a, randoms_a, data_b, randoms_b, n, box, origin=(0.0, 0.0, 0.0), assign=3,
@@ -165,9 +168,9 @@ def cross_power_multipoles(data_a, randoms_a, data_b, randoms_b, n, box, origin=
     return res
 
 
-def unpack_power(buf, nbins, ells, modified):
+def unpack_power(buf, nbins, ells, modified, two_index=()):
     buf = np.asarray(buf)
-    res = {"k_eff": buf[0:nbins].copy(), "nmodes": buf[nbins:2 * nbins].copy(), "P": {}, "Pmod": {}}
+    res = {"k_eff": buf[0:nbins].copy(), "nmodes": buf[nbins:2 * nbins].copy(), "P": {}, "Pmod": {}, "Pll": {}}
     row = 2
     for l in sorted(ells):
         res["P"][l] = buf[row * nbins:(row + 1) * nbins].copy()
@@ -175,6 +178,10 @@ def unpack_power(buf, nbins, ells, modified):
     for l in sorted(modified):
         res["Pmod"][l] = buf[row * nbins:(row + 1) * nbins].copy()
         row += 1
+    for p in ((2, 2), (4, 2), (4, 4)):
+        if p in {tuple(q) for q in two_index}:
+            res["Pll"][p] = buf[row * nbins:(row + 1) * nbins].copy()
+            row += 1
     sc = buf[row * nbins:row * nbins + 8]
     res["scalars"] = dict(zip(("alpha", "I22", "I33", "N0", "S3", "sum_wg", "sum_wr", "sum_w2"), sc))
     return res

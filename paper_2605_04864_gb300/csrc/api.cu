@@ -536,10 +536,11 @@ npc_status npc_catalog_scalars(npc_ctx* ctx, const npc_catalog* data, const npc_
 
 int64_t npc_power_out_len(const npc_kbins* bins, uint32_t ell_mask, uint32_t modified_mask) {
   if (!bins || bins->nbins < 1) return 0;
-  if ((ell_mask & ~0x1Fu) || (modified_mask & ~0x150u) || (ell_mask == 0 && modified_mask == 0)) return 0;
+  if ((ell_mask & ~0x1Fu) || (modified_mask & ~0x70150u) || (ell_mask == 0 && modified_mask == 0)) return 0;
   int rows = 2;
   for (int l = 0; l <= 4; ++l) rows += (ell_mask >> l) & 1;
   for (int l = 4; l <= 8; l += 2) rows += (modified_mask >> l) & 1;
+  for (int b = 16; b <= 18; ++b) rows += (modified_mask >> b) & 1;
   return (int64_t)rows * bins->nbins + 8;
 }
 
@@ -553,7 +554,7 @@ npc_status npc_power_multipoles(npc_ctx* ctx, const npc_mesh_spec* mesh, const n
   if (!out) return set_err(ctx, NPC_ERR_INVALID_ARG, "out is NULL");
   const int64_t out_len = npc_power_out_len(bins, ell_mask, modified_mask);
   if (out_len == 0)
-    return set_err(ctx, NPC_ERR_INVALID_ARG, "ell_mask must use bits 0..4 and modified_mask bits 4,6,8");
+    return set_err(ctx, NPC_ERR_INVALID_ARG, "ell_mask must use bits 0..4 and modified_mask bits 4,6,8,16,17,18");
   if (prec != NPC_PREC_FP64 && prec != NPC_PREC_MIXED) return set_err(ctx, NPC_ERR_INVALID_ARG, "bad precision");
   if (prec == NPC_PREC_FP64 && mesh->n > 256) return set_err(ctx, NPC_ERR_UNSUPPORTED, "FP64 precision supports n <= 256");
   NPC_TRY(check_catalog(ctx, data, "data", false));

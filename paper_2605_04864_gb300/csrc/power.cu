@@ -741,7 +741,8 @@ struct FinalParams {
   int nell, ell_list[5];
   int nll, lla[3], llb[3];
   int nmod, mod_list[3];
-  int out_rows;          // 2 + requested P_l + requested P_lb
+  int out_rows;          // 2 + requested P_l + requested P_lb + requested P_ll'
+  int ll_req;            // output P_22 (bit 0), P_42 (bit 1), P_44 (bit 2)
   int req_mask;          // requested P_l (bits)
 };
 
@@ -802,6 +803,10 @@ k_power_finalize(const double* __restrict__ part, const FinalParams F, const dou
       }
       out[(row++) * nb + b] = v;
     }
+    // the two-index spectra themselves (Eq. Pllp), when requested: P_22, P_42, P_44
+    if (F.ll_req & 1) out[(row++) * nb + b] = P22;
+    if (F.ll_req & 2) out[(row++) * nb + b] = P42;
+    if (F.ll_req & 4) out[(row++) * nb + b] = P44;
   }
   if (blockIdx.x == 0 && threadIdx.x < 8) out[(size_t)F.out_rows * nb + threadIdx.x] = sc[threadIdx.x];
 }
@@ -1030,9 +1035,9 @@ npc_status contract_impl(npc_ctx* ctx, const PowerPlan& plan, const npc_mesh_spe
   for (int l = 0; l <= 4; ++l)
     if (req_internal & (1 << l)) P.ell_list[P.nell++] = l;
   P.nll = 0;
-  if (plan.mod_mask & (1 << 4)) { P.lla[P.nll] = 2; P.llb[P.nll] = 2; P.nll++; }
-  if (plan.mod_mask & ((1 << 6) | (1 << 8))) { P.lla[P.nll] = 4; P.llb[P.nll] = 2; P.nll++; }
-  if (plan.mod_mask & (1 << 8)) { P.lla[P.nll] = 4; P.llb[P.nll] = 4; P.nll++; }
+  if (plan.mod_mask & ((1 << 4) | (1 << 16))) { P.lla[P.nll] = 2; P.llb[P.nll] = 2; P.nll++; }
+  if (plan.mod_mask & ((1 << 6) | (1 << 8) | (1 << 17))) { P.lla[P.nll] = 4; P.llb[P.nll] = 2; P.nll++; }
+  if (plan.mod_mask & ((1 << 8) | (1 << 18))) { P.lla[P.nll] = 4; P.llb[P.nll] = 4; P.nll++; }
   P.nsum = P.nell + P.nll + 2;
   P.KZ = plan.kz_keep > 0 ? std::min(plan.kz_keep, N / 2) : N / 2;
   P.global_los = plan.global_los;
@@ -1082,7 +1087,8 @@ npc_status contract_impl(npc_ctx* ctx, const PowerPlan& plan, const npc_mesh_spe
     if (plan.mod_mask & (1 << lb)) F.mod_list[F.nmod++] = lb;
   int nreq = 0;
   for (int l = 0; l <= 4; ++l) nreq += (plan.ells_mask >> l) & 1;
-  F.out_rows = 2 + nreq + F.nmod;
+  F.ll_req = (plan.mod_mask >> 16) & 7;
+  F.out_rows = 2 + nreq + F.nmod + ((F.ll_req & 1) + ((F.ll_req >> 1) & 1) + ((F.ll_req >> 2) & 1));
   F.req_mask = plan.ells_mask;
   k_power_finalize<<<std::min(P.nbins, 1024), FIN_THREADS, 0, ctx->stream>>>(part, F, sc, dev_out);
   NPC_LAUNCH(ctx);

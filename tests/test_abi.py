@@ -46,6 +46,8 @@ def test_host_only_calls():
     assert B.npc_power_out_len(C.byref(kb), 0b10101, (1 << 4) | (1 << 8)) == 7 * 20 + 8
     assert B.npc_power_out_len(C.byref(kb), 0b10, 0) == 3 * 20 + 8   # odd l (imaginary part)
     assert B.npc_power_out_len(C.byref(kb), 0b100000, 0) == 0   # l = 5 rejected
+    assert B.npc_power_out_len(C.byref(kb), 1, (1 << 16) | (1 << 18)) == 5 * 20 + 8   # P_22, P_44
+    assert B.npc_power_out_len(C.byref(kb), 1, 1 << 19) == 0
     st = B.npc_create(C.byref(C.c_void_p()), 0, None)
     assert st in (0, 1, 3)  # no device here: invalid device or CUDA error, never a crash
     assert B.npc_destroy(None) == 0

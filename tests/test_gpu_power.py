@@ -221,3 +221,20 @@ def test_odd_multipoles_survey(api, prec, tol, n):
     _compare(res, orc, (0, 1, 2, 3, 4), (4, 6, 8), tol)
     scale = np.abs(orc["P"][0]) + orc["scalars"]["N0"]
     assert np.max(np.abs(orc["P"][1]) / scale) > 1e-6   # the odd terms measured are not all zero
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("mixed", 1e-5)])
+def test_two_index_multipoles(api, prec, tol):
+    """P_22, P_42, P_44 of Eq. Pllp reported next to the modified multipoles, alone and together."""
+    g, r, origin = make_survey_catalogs(20000, 200000, 800.0, 1300.0, 24, seed=63, fkp_p0=1e4)
+    kb = (0.0, 0.015, 8)
+    orc = _oracle(g, r, origin, 32, 800.0, 3, 1, kb, (0, 2, 4), (4, 6, 8))
+    scale = np.abs(orc["P"][0]) + orc["scalars"]["N0"]
+    res = api.power_multipoles(g, r, n=32, box=800.0, origin=origin, kbins=kb, ells=(0, 2), modified=(6,),
+                               two_index=((2, 2), (4, 2), (4, 4)), precision=prec)
+    for p in ((2, 2), (4, 2), (4, 4)):
+        assert np.max(p_error(res["Pll"][p], orc["Pll"][p], scale)) < tol, p
+    assert np.max(p_error(res["Pmod"][6], orc["Pmod"][6], scale)) < tol
+    only = api.power_multipoles(g, r, n=32, box=800.0, origin=origin, kbins=kb, ells=(0,), two_index=((4, 4),),
+                                precision=prec)
+    assert np.max(p_error(only["Pll"][(4, 4)], orc["Pll"][(4, 4)], scale)) < tol
