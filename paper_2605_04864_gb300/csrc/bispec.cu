@@ -552,7 +552,7 @@ constexpr int NB_MAX = 24;
 constexpr int TRI_CHUNK = 256;          // cells staged per chunk
 constexpr int TRI_FLUSH = 16;           // chunks between FP64 flushes
 constexpr int TRI_WARPS = 8;
-constexpr int TRI_MT = 3;               // m tiles (16 rows) per warp -> 384 rows per CTA
+constexpr int TRI_MT = 2;               // m tiles (16 rows) per warp -> 256 rows per CTA, 2 CTAs per SM
 constexpr int TRI_NT_MAX = 4;           // n tiles (8 cols) -> up to 32 columns (3 when <= 24 are used)
 constexpr int TRI_ROWS = TRI_WARPS * TRI_MT * 16;
 constexpr int TRI_COLS = TRI_NT_MAX * 8;
@@ -595,7 +595,7 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], 
 // B b0 (k t, col g), b1 (k t+4, col g); D d0, d1 (row g, cols 2t, 2t+1), d2, d3 (row g+8, ...),
 // with g = lane/4 and t = lane%4.
 template <int TRI_NT>
-__global__ void __launch_bounds__(TRI_WARPS * 32, 1)
+__global__ void __launch_bounds__(TRI_WARPS * 32, 2)
 k_triple(const float* __restrict__ R, const TripleArgs A, const int* __restrict__ pair_ij,
          const int* __restrict__ row_pair, double* __restrict__ part) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1541,7 +1541,7 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
   }
   auto grid_for = [&](const TripleArgs& a) {
     const int ng_ = (a.nrows + TRI_ROWS - 1) / TRI_ROWS;
-    return sizeof(T) == 4 ? std::max(1, ctx->num_sms / ng_) : ctx->num_sms * 4;
+    return sizeof(T) == 4 ? std::max(1, 2 * ctx->num_sms / ng_) : ctx->num_sms * 4;   // 2 CTAs per SM
   };
   const int grid = grid_for(ta);
   double* part;
