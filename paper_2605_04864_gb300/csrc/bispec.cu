@@ -552,9 +552,10 @@ constexpr int NB_MAX = 24;
 constexpr int TRI_CHUNK = 256;          // cells staged per chunk
 constexpr int TRI_FLUSH = 16;           // chunks between FP64 flushes
 constexpr int TRI_WARPS = 8;
-constexpr int TRI_MT = 2;               // m tiles (16 rows) per warp -> 256 rows per CTA, 2 CTAs per SM
+// m tiles (16 rows) per warp, a template parameter: 1 (128 rows per CTA, 3 CTAs per SM) when the
+// staged fields are few, else 2 (256 rows per CTA, 2 CTAs per SM)
 constexpr int TRI_NT_MAX = 4;           // n tiles (8 cols) -> up to 32 columns (3 when <= 24 are used)
-constexpr int TRI_ROWS = TRI_WARPS * TRI_MT * 16;
+template <int MT> constexpr int tri_rows() { return TRI_WARPS * MT * 16; }
 constexpr int TRI_COLS = TRI_NT_MAX * 8;
 constexpr int TRI_SPAD = TRI_CHUNK + 4; // staging row stride (floats): 8 rows x 4 cells of an operand
                                         // fragment fall on 32 distinct banks
@@ -588,14 +589,14 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// grid = (cell ranges, row groups of TRI_ROWS); block = TRI_WARPS warps; TRI_NT n tiles of 8
+// grid = (cell ranges, row groups of tri_rows<MT>()); block = TRI_WARPS warps; TRI_NT n tiles of 8
 // columns (3 when the F_k and G^(l) columns fit in 24).  Rows run in the order row_pair (pairs
 // sorted by their larger bin j) and are written back to their pair index.
 // Fragment layouts of m16n8k8 (tf32): A a0 (row g, k t), a1 (g+8, t), a2 (g, t+4), a3 (g+8, t+4);
 // B b0 (k t, col g), b1 (k t+4, col g); D d0, d1 (row g, cols 2t, 2t+1), d2, d3 (row g+8, ...),
 // with g = lane/4 and t = lane%4.
-template <int TRI_NT>
-__global__ void __launch_bounds__(TRI_WARPS * 32, 2)
+template <int TRI_NT, int TRI_MT>
+__global__ void __launch_bounds__(TRI_WARPS * 32, TRI_MT == 1 ? 3 : 2)
 k_triple(const float* __restrict__ R, const TripleArgs A, const int* __restrict__ pair_ij,
          const int* __restrict__ row_pair, double* __restrict__ part) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -603,7 +604,7 @@ k_triple(const float* __restrict__ R, const TripleArgs A, const int* __restrict_
   double* dacc = reinterpret_cast<double*>(stage + (size_t)A.nstage * TRI_SPAD);  // [tid][NACC]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = lane >> 2, t = lane & 3;
-  const int rowbase = blockIdx.y * TRI_ROWS + warp * TRI_MT * 16;
+  const int rowbase = blockIdx.y * tri_rows<TRI_MT>() + warp * TRI_MT * 16;
   int sa[TRI_MT][2], sb[TRI_MT][2], orow[TRI_MT][2];
 #pragma unroll
   for (int mt = 0; mt < TRI_MT; ++mt) {
@@ -1539,9 +1540,12 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
     if (want2) setup_shot(ts2, iI, -1, iS2);      // sum I_a I_b S2_c
     if (want2) setup_shot(tn2, iI2, -1, iI);      // sum I2_a I_b I_c (cached)
   }
+  // one m tile per warp (3 CTAs per SM) while the staged fields leave room for three CTAs
+  auto tri_mt = [&](const TripleArgs& a) { return a.nstage <= 47 ? 1 : 2; };
   auto grid_for = [&](const TripleArgs& a) {
-    const int ng_ = (a.nrows + TRI_ROWS - 1) / TRI_ROWS;
-    return sizeof(T) == 4 ? std::max(1, 2 * ctx->num_sms / ng_) : ctx->num_sms * 4;   // 2 CTAs per SM
+    const int mt = tri_mt(a), rows = TRI_WARPS * mt * 16;
+    const int ng_ = (a.nrows + rows - 1) / rows;
+    return sizeof(T) == 4 ? std::max(1, (mt == 1 ? 3 : 2) * ctx->num_sms / ng_) : ctx->num_sms * 4;
   };
   const int grid = grid_for(ta);
   double* part;
@@ -1549,17 +1553,18 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
                  (void**)&part));
   auto launch = [&](const TripleArgs& a, int grid, double* part) -> npc_status {
     if constexpr (sizeof(T) == 4) {
-      const int groups = (a.nrows + TRI_ROWS - 1) / TRI_ROWS;
+      const int mt = tri_mt(a), rows = TRI_WARPS * mt * 16;
+      const int groups = (a.nrows + rows - 1) / rows;
       auto run = [&](auto kern, int nt) -> npc_status {
         const size_t smem = sizeof(float) * (size_t)a.nstage * TRI_SPAD +
-                            sizeof(double) * (size_t)TRI_WARPS * 32 * TRI_MT * nt * 4;
+                            sizeof(double) * (size_t)TRI_WARPS * 32 * mt * nt * 4;
         NPC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         kern<<<dim3(grid, groups), TRI_WARPS * 32, smem, ctx->stream>>>(
             (const float*)R, a, (const int*)(dtab + t_pij), (const int*)(dtab + t_rowp), part);
         return NPC_OK;
       };
-      if (a.ncol <= 24) NPC_TRY(run(k_triple<3>, 3));
-      else NPC_TRY(run(k_triple<4>, 4));
+      if (a.ncol <= 24) NPC_TRY(mt == 1 ? run(k_triple<3, 1>, 3) : run(k_triple<3, 2>, 3));
+      else NPC_TRY(mt == 1 ? run(k_triple<4, 1>, 4) : run(k_triple<4, 2>, 4));
     } else {
       const int outs = a.nrows * a.ncol;
       k_triple_f64<<<dim3(grid, (outs + 255) / 256), 256, 0, ctx->stream>>>((const double*)R, a,
