@@ -40,24 +40,28 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-def _src_hash():
+def _src_hash(files=None):
+    """Hash of the CUDA sources (all of csrc/, or the listed repo-relative files)."""
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_2605_04864_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
-        with open(os.path.join(csrc, fn), "rb") as f:
-            h.update(fn.encode())
+    if files is None:
+        csrc = os.path.join("paper_2605_04864_gb300", "csrc")
+        files = [os.path.join(csrc, fn) for fn in sorted(os.listdir(os.path.join(ROOT, csrc)))]
+    for rel in files:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(os.path.basename(rel).encode())
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
 def _traffic(kernel):
-    """DRAM bytes per launch from a committed ncu summary, if it was taken on the current source."""
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on the current source of
+    the kernel (its translation unit and the headers it includes, as listed in the record)."""
     p = os.path.join(ROOT, "profiles", "dram_traffic.json")
     try:
         with open(p) as f:
             d = json.load(f)
         rec = d.get(WORKLOAD, {}).get(kernel)
-        if rec and rec.get("src_hash") == _src_hash():
+        if rec and rec.get("src_hash") == _src_hash(rec.get("src_files")):
             return float(rec["bytes_per_launch"])
     except Exception:
         pass

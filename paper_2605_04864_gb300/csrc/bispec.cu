@@ -822,6 +822,7 @@ struct FinalArgs {
   int s1_nparts, s1_nrows, s1_ncol, s2_nparts, s2_nrows, s3_nparts, s3_nrows, s3_ncol;
   int survey;           // 1: survey l = 2 shell sums (NCS per bin) and catalogue moments
   int ncs;              // sums per bin in cross_m / cross_q
+  int ntri_blocks;      // leading 32-thread blocks that take the triangles (then one per pair)
 };
 
 __global__ void k_bispec_finalize(const int* __restrict__ tri, const int* __restrict__ pair_ij,
@@ -870,8 +871,62 @@ __global__ void k_bispec_finalize(const int* __restrict__ tri, const int* __rest
   auto ps1 = [&](int fam, int p, int c) { return shot_sum(part_s1, F.s1_nparts, F.s1_nrows, F.s1_ncol, fam, p, c); };
   auto ps2 = [&](int fam, int p, int c) { return shot_sum(part_s2, F.s2_nparts, F.s2_nrows, nb, fam, p, c); };
   auto ps3 = [&](int fam, int p, int c) { return shot_sum(part_s3, F.s3_nparts, F.s3_nrows, F.s3_ncol, fam, p, c); };
+  // pair p (lanes of one warp): compressed multipoles and their shot noise
+  auto finalize_pair = [&](int p, int lane) {
+    const int i = pair_ij[p] & 0xffff, j = pair_ij[p] >> 16;
+    const double ni = count(cross_m, i), nj = count(cross_m, j);
+    for (int e = 0; e < F.ntripo; ++e) {
+      const int l = F.tripo_l[e];
+      double sg = 0;
+      for (int c = 0; c < F.nparts; ++c) sg += part_main[((size_t)c * F.nrows + p) * F.ncol + nb + e];
+      const double raw = (ni > 0 && nj > 0) ? (2 * l + 1) * sg / (i33 * ni * nj * (double)F.ncell) : 0.0;
+      double sn = 0.0;
+      if (F.shot == 2 && ni > 0 && nj > 0) {
+        // FFT method: Ta + Tb + Tc - 2 S Td over the (q1, q2) pairs of the two bins
+        const double ta = ps1(0, p, nb + e), td = ps1(0, p, nb + F.ntripo + e);
+        const double tb = ps3(0, p, e), tc = ps3(1, p, e);
+        sn = (2 * l + 1) * (ta + tb + tc - 2.0 * s3 * td) / (i33 * ni * nj * (double)F.ncell);
+      } else if (F.shot && ni > 0 && nj > 0) {
+        const double ci = centre(i), cj = centre(j);
+        const double sgn = (l % 2) ? -1.0 : 1.0;
+        double v = (l == 0 ? s3 : 0.0);
+        v += sgn * g_ell_dev(l, ci / cj) * Hm(l, i);
+        v += sgn * g_ell_dev(l, cj / ci) * Hm(l, j);
+        // k3-shell average of Q_l over the shells the pair closes on: lanes take shells m = lane,
+        // lane + 32, ..., then a fixed shuffle tree
+        const double lo = fabs(ci - cj) + 0.5 * F.dk, hi = ci + cj - 0.5 * F.dk;
+        double num = 0, den = 0;
+        for (int m = lane; m < F.nq; m += 32) {
+          const double cm = (m + 0.5) * F.dk;
+          const double nm = count(cross_q, m);
+          if (cm >= lo - 1e-9 * F.dk && cm <= hi + 1e-9 * F.dk && nm > 0) {
+            num += nm / cm * Qq(l, m);
+            den += nm / cm;
+          }
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+          num += __shfl_xor_sync(0xffffffffu, num, off);
+          den += __shfl_xor_sync(0xffffffffu, den, off);
+        }
+        if (den > 0) v += num / den;
+        sn = (2 * l + 1) / i33 * v;
+      }
+      if (lane == 0) {
+        out[oBB + (size_t)e * F.npair + p] = raw - sn;
+        out[oSBB + (size_t)e * F.npair + p] = sn;
+      }
+    }
+  };
+  // blocks [0, ntb) take the triangles, one per thread; block ntb + p takes pair p as one warp
+  // (FP64 arithmetic is scarce on this part, so the per-pair shell sums are spread over the lanes)
+  const int ntb = F.ntri_blocks;
+  if ((int)blockIdx.x >= ntb) {
+    const int p = blockIdx.x - ntb, lane = threadIdx.x;
+    if (p < F.npair) finalize_pair(p, lane);
+    return;
+  }
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-  const int nthreads = gridDim.x * blockDim.x;
+  const int nthreads = ntb * blockDim.x;
   for (int t = tid; t < F.ntri; t += nthreads) {
     const int i = tri[3 * t], j = tri[3 * t + 1], k = tri[3 * t + 2];
     const int p = pair_index(i, j);
@@ -911,43 +966,6 @@ __global__ void k_bispec_finalize(const int* __restrict__ tri, const int* __rest
       out[oSB + (size_t)e * F.ntri + t] = sn;
     }
   }
-  for (int p = tid; p < F.npair; p += nthreads) {
-    const int i = pair_ij[p] & 0xffff, j = pair_ij[p] >> 16;
-    const double ni = count(cross_m, i), nj = count(cross_m, j);
-    for (int e = 0; e < F.ntripo; ++e) {
-      const int l = F.tripo_l[e];
-      double sg = 0;
-      for (int c = 0; c < F.nparts; ++c) sg += part_main[((size_t)c * F.nrows + p) * F.ncol + nb + e];
-      const double raw = (ni > 0 && nj > 0) ? (2 * l + 1) * sg / (i33 * ni * nj * (double)F.ncell) : 0.0;
-      double sn = 0.0;
-      if (F.shot == 2 && ni > 0 && nj > 0) {
-        // FFT method: Ta + Tb + Tc - 2 S Td over the (q1, q2) pairs of the two bins
-        const double ta = ps1(0, p, nb + e), td = ps1(0, p, nb + F.ntripo + e);
-        const double tb = ps3(0, p, e), tc = ps3(1, p, e);
-        sn = (2 * l + 1) * (ta + tb + tc - 2.0 * s3 * td) / (i33 * ni * nj * (double)F.ncell);
-      } else if (F.shot && ni > 0 && nj > 0) {
-        const double ci = centre(i), cj = centre(j);
-        const double sgn = (l % 2) ? -1.0 : 1.0;
-        double v = (l == 0 ? s3 : 0.0);
-        v += sgn * g_ell_dev(l, ci / cj) * Hm(l, i);
-        v += sgn * g_ell_dev(l, cj / ci) * Hm(l, j);
-        const double lo = fabs(ci - cj) + 0.5 * F.dk, hi = ci + cj - 0.5 * F.dk;
-        double num = 0, den = 0;
-        for (int m = 0; m < F.nq; ++m) {
-          const double cm = (m + 0.5) * F.dk;
-          const double nm = count(cross_q, m);
-          if (cm >= lo - 1e-9 * F.dk && cm <= hi + 1e-9 * F.dk && nm > 0) {
-            num += nm / cm * Qq(l, m);
-            den += nm / cm;
-          }
-        }
-        if (den > 0) v += num / den;
-        sn = (2 * l + 1) / i33 * v;
-      }
-      out[oBB + (size_t)e * F.npair + p] = raw - sn;
-      out[oSBB + (size_t)e * F.npair + p] = sn;
-    }
-  }
   for (int b = tid; b < nb; b += nthreads) out[oNM + b] = count(cross_m, b);
   if (tid < 8) out[oSC + tid] = sc[tid];
 }
@@ -962,6 +980,30 @@ __global__ void k_cross_reduce(const double* __restrict__ part, int nrec, int nb
     for (int r = lane; r < nrec; r += 32) s += part[(size_t)r * nb * ns + e];
     for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
     if (lane == 0) out[e] = s;
+  }
+}
+
+// Sum of per-CTA partials part[q][e] over q for every entry e.  A block takes 32 consecutive
+// entries (one per lane, so every load of a warp is contiguous) and splits the CTAs q over its
+// PR_SLICES warps (slice y sums q = y, y + PR_SLICES, ...); the slice sums are then added in slice
+// order, so the result does not depend on scheduling.
+constexpr int PR_SLICES = 16;
+__global__ void __launch_bounds__(32 * PR_SLICES) k_part_reduce(const double* __restrict__ part, int nparts,
+                                                                int64_t nent, double* __restrict__ out) {
+  __shared__ double sl[PR_SLICES][33];
+  const int lane = threadIdx.x & 31, y = threadIdx.x >> 5;
+  const int64_t e = (int64_t)blockIdx.x * 32 + lane;
+  double s = 0.0;
+  if (e < nent) {
+#pragma unroll 4
+    for (int q = y; q < nparts; q += PR_SLICES) s += part[(size_t)q * nent + e];
+  }
+  sl[y][lane] = s;
+  __syncthreads();
+  if (y == 0 && e < nent) {
+    double t = 0.0;
+    for (int r = 0; r < PR_SLICES; ++r) t += sl[r][lane];
+    out[e] = t;
   }
 }
 
@@ -1611,7 +1653,22 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
     NPC_TRY(stage_mark(ctx, "shot_triple"));
   }
 
-  // 6. finalize
+  // 6. finalize: the per-CTA partials are summed first (one coalesced pass each), then combined
+  auto reduce_parts = [&](const char* name, const double* p, int nparts, int64_t nent, double** out) -> npc_status {
+    NPC_TRY(ws_get(ctx, name, sizeof(double) * std::max<int64_t>(nent, 1), (void**)out));
+    const int64_t blocks = (nent + 31) / 32;
+    if (blocks > INT32_MAX) return NPC_ERR_INVALID_ARG;
+    k_part_reduce<<<(unsigned)std::max<int64_t>(1, blocks), 32 * PR_SLICES, 0, ctx->stream>>>(p, nparts, nent, *out);
+    NPC_LAUNCH(ctx);
+    return NPC_OK;
+  };
+  double *red_main = nullptr, *red_s1 = nullptr, *red_s2 = nullptr, *red_s3 = nullptr;
+  NPC_TRY(reduce_parts("bis.red.main", part, grid, (int64_t)ta.nrows * ta.ncol, &red_main));
+  if (fftshot) {
+    NPC_TRY(reduce_parts("bis.red.s1", part_s1, gs1, (int64_t)ts1.nrows * ts1.ncol, &red_s1));
+    if (want2) NPC_TRY(reduce_parts("bis.red.s2", part_s2, gs2, (int64_t)ts2.nrows * nb, &red_s2));
+    if (ntl > 0) NPC_TRY(reduce_parts("bis.red.s3", part_s3, gs3, (int64_t)ts3.nrows * ts3.ncol, &red_s3));
+  }
   FinalArgs fa{};
   fa.nb = nb;
   fa.ntri = ntri;
@@ -1624,26 +1681,27 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
   for (int l = 0; l <= 2; l += 2)
     if (tripo_mask & (1 << l)) fa.tripo_l[fa.ntripo++] = l;
   fa.shot = shot;
-  fa.nparts = grid;
+  fa.nparts = 1;   // partials already summed over the CTAs
   fa.nrows = ta.nrows;
   fa.ncol = ta.ncol;
   fa.has2 = want2 ? 1 : 0;
   fa.ncell = (int64_t)ncs;
   fa.kmin = kb.kmin;
   fa.dk = kb.dk;
-  fa.s1_nparts = gs1;
+  fa.s1_nparts = gs1 > 0 ? 1 : 0;
   fa.s1_nrows = ts1.nrows;
   fa.s1_ncol = ts1.ncol;
-  fa.s2_nparts = gs2;
+  fa.s2_nparts = gs2 > 0 ? 1 : 0;
   fa.s2_nrows = ts2.nrows;
   fa.survey = yam ? 1 : 0;
   fa.ncs = nsum_c;
-  fa.s3_nparts = gs3;
+  fa.s3_nparts = gs3 > 0 ? 1 : 0;
   fa.s3_nrows = ts3.nrows;
   fa.s3_ncol = ts3.ncol;
-  k_bispec_finalize<<<std::max(1, (std::max(ntri, npair) + 127) / 128), 128, 0, ctx->stream>>>(
-      (const int*)(dtab + t_tri), (const int*)(dtab + t_pij), part, nt_sums, cross_m, cross_q, mom, part_s1, part_s2,
-      part_s3, nt2_sums, fa, sc, dev_out);
+  fa.ntri_blocks = (std::max(std::max(ntri, nb), 8) + 31) / 32;
+  k_bispec_finalize<<<fa.ntri_blocks + npair, 32, 0, ctx->stream>>>(
+      (const int*)(dtab + t_tri), (const int*)(dtab + t_pij), red_main, nt_sums, cross_m, cross_q, mom, red_s1, red_s2,
+      red_s3, nt2_sums, fa, sc, dev_out);
   NPC_LAUNCH(ctx);
   NPC_TRY(stage_mark(ctx, "finalize"));
   (void)out_len;
