@@ -1,0 +1,128 @@
+"""Pins for oracle.sugiyama (the TripoSH B_{l1 l2 L} of Eq. sugi_estimator)."""
+import numpy as np
+import pytest
+
+from oracle import bispec as B
+from oracle import harmonics as H
+from oracle import power as P
+from oracle import sugiyama as S
+from synthetic import Catalog, make_periodic_catalog
+
+KB = (0.02, 0.02, 3)   # k_max = 0.08 < k_N/2 = 0.084 at n = 16, L = 300
+MULTIPOLES = [(0, 0, 0), (1, 1, 0), (1, 1, 2), (2, 0, 2), (0, 2, 2), (2, 2, 0), (2, 2, 2), (2, 2, 4)]
+TILT = (1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0)
+
+
+def _spec(n, los_dir=(0.0, 0.0, 1.0)):
+    return dict(n=n, box=300.0, origin=(0.0, 0.0, 0.0), assign=3, interlace=1, los="global",
+                los_dir=los_dir, periodic=1)
+
+
+@pytest.fixture(scope="module")
+def cat():
+    return make_periodic_catalog(4000, 300.0, 16, seed=11)
+
+
+def _setup(cat, los_dir, n=16):
+    spec = _spec(n, los_dir)
+    sc = P.catalog_scalars(cat, None, 300.0)
+    return spec, sc, P.fkp_meshes(spec, cat, None, sc)
+
+
+def _scale(res):
+    return np.max(np.abs(res[(0, 0, 0)]))
+
+
+def test_valid_multipoles():
+    assert S.valid_multipole(2, 0, 2) and S.valid_multipole(1, 1, 2) and S.valid_multipole(2, 2, 4)
+    assert not S.valid_multipole(1, 0, 0) and not S.valid_multipole(2, 0, 0) and not S.valid_multipole(2, 2, 1)
+
+
+@pytest.mark.parametrize("los_dir", [(0.0, 0.0, 1.0), TILT])
+def test_fft_against_mode_pair_enumeration(cat, los_dir):
+    """sum_x F F G equals the explicit (q1, q2) sum (the Kronecker delta of the closure) exactly."""
+    spec, sc, meshes = _setup(cat, los_dir)
+    res = S.sugiyama_fft(spec, meshes, KB, MULTIPOLES, sc["I33"])
+    prs = [(0, 0), (0, 2), (2, 1), (1, 2), (2, 2)]
+    for mp in [(0, 0, 0), (1, 1, 2), (2, 0, 2), (0, 2, 2), (2, 2, 2), (2, 2, 4)]:
+        brute = S.sugiyama_brute(spec, meshes, KB, mp, sc["I33"], prs)
+        got = np.array([res[mp][i, j] for i, j in prs])
+        assert np.max(np.abs(got - brute)) < 1e-11 * _scale(res), mp
+
+
+@pytest.mark.parametrize("los_dir", [(0.0, 0.0, 1.0), TILT])
+def test_ll0_against_legendre_form(cat, los_dir):
+    """B_{l l 0}: the m-sum with 3j symbols collapses to the Legendre polynomial of the angle between
+    q1 and q2 (addition theorem), independent of the line of sight."""
+    spec, sc, meshes = _setup(cat, los_dir)
+    res = S.sugiyama_fft(spec, meshes, KB, [(0, 0, 0), (1, 1, 0), (2, 2, 0)], sc["I33"])
+    prs = [(i, j) for i in range(3) for j in range(3)]
+    for ell in (0, 1, 2):
+        leg = S.legendre_ll0(spec, meshes, KB, ell, sc["I33"], prs)
+        got = np.array([res[(ell, ell, 0)][i, j] for i, j in prs])
+        assert np.max(np.abs(got - leg)) < 1e-11 * _scale(res), ell
+
+
+def test_monopole_equals_compressed_monopole(cat):
+    """Sec. 6: the compressed estimator's B_000 coincides with Sugiyama's B_000."""
+    spec, sc, meshes = _setup(cat, (0.0, 0.0, 1.0))
+    res = S.sugiyama_fft(spec, meshes, KB, [(0, 0, 0)], sc["I33"])
+    X0 = P.fields_plain(spec, meshes, [0])[0][0]
+    prs = B.pairs(KB)
+    comp, _, _ = B.compressed_fft(spec, X0, X0, KB, prs, sc["I33"], 0)
+    got = np.array([res[(0, 0, 0)][i, j] for i, j in prs])
+    np.testing.assert_allclose(np.real(got), comp, rtol=1e-11, atol=1e-13 * np.max(np.abs(comp)))
+
+
+@pytest.mark.parametrize("los_dir", [(0.0, 0.0, 1.0), TILT])
+def test_halved_sum_and_reality(cat, los_dir):
+    """Eq. sym_sugi: the paired sub-configurations are complex conjugates, so the boxed half-sum
+    (eta = 2, real part) equals the full sum, which is real."""
+    spec, sc, meshes = _setup(cat, los_dir)
+    mps = [(1, 1, 2), (2, 0, 2), (2, 2, 2), (2, 2, 4)]
+    full = S.sugiyama_fft(spec, meshes, KB, mps + [(0, 0, 0)], sc["I33"])
+    half = S.sugiyama_halved(spec, meshes, KB, mps, sc["I33"])
+    for mp in mps:
+        assert np.max(np.abs(np.imag(full[mp]))) < 1e-12 * _scale(full), mp
+        assert np.max(np.abs(np.real(full[mp]) - half[mp])) < 1e-12 * _scale(full), mp
+
+
+def test_cyclic_axis_permutation(cat):
+    """A cyclic permutation of the axes is a rotation: applied to the catalogue and the line of
+    sight together it leaves every B_{l1 l2 L} unchanged (the tilted line of sight makes every
+    G_L^M with M != 0 contribute)."""
+    spec, sc, meshes = _setup(cat, TILT)
+    res = S.sugiyama_fft(spec, meshes, KB, MULTIPOLES, sc["I33"])
+    rot = Catalog(np.ascontiguousarray(cat.pos[:, [1, 2, 0]]), cat.w, cat.nbar)
+    spec_r, sc_r, meshes_r = _setup(rot, (TILT[1], TILT[2], TILT[0]))
+    res_r = S.sugiyama_fft(spec_r, meshes_r, KB, MULTIPOLES, sc_r["I33"])
+    for mp in MULTIPOLES:
+        assert np.max(np.abs(res[mp] - res_r[mp])) < 1e-11 * _scale(res), mp
+    # and the multipoles with l > 0 do depend on the line of sight
+    spec_z, sc_z, meshes_z = _setup(cat, (0.0, 0.0, 1.0))
+    res_z = S.sugiyama_fft(spec_z, meshes_z, KB, [(0, 0, 0), (2, 0, 2)], sc_z["I33"])
+    assert np.max(np.abs(res_z[(2, 0, 2)] - res[(2, 0, 2)])) > 1e-3 * _scale(res)
+
+
+def test_l0l_reduces_to_legendre_shell_along_z(cat):
+    """Line of sight along z: only M = 0 survives and B_l0l = (2l+1)/(I33 N_i N_j n^3)
+    sum_x F_l(x; k_i) F_0(x; k_j) G(x), with F_l the shell of L_l(mu) X and G the full-range X."""
+    spec, sc, meshes = _setup(cat, (0.0, 0.0, 1.0))
+    res = S.sugiyama_fft(spec, meshes, KB, [(0, 0, 0), (2, 0, 2)], sc["I33"])
+    n = spec["n"]
+    X0 = P.fields_plain(spec, meshes, [0])[0][0]
+    f0 = B.shell_fields(spec, X0, KB)
+    f2 = B.shell_fields(spec, B.los_field(spec, X0, 2), KB)
+    g = np.real(np.fft.ifftn(X0)) * n**3
+    cnt = S.mode_counts(spec, KB)
+    for i in range(3):
+        for j in range(3):
+            want = 5.0 * np.sum(f2[i] * f0[j] * g) / (n**3 * sc["I33"] * cnt[i] * cnt[j])
+            assert abs(res[(2, 0, 2)][i, j] - want) < 1e-11 * _scale(res)
+
+
+def test_wigner_coefficients_of_the_l0l_collapse():
+    """H N (l 0 l; 0 0 0) = 2l + 1: the normalisation the reduction above relies on."""
+    for ell in range(5):
+        hN = H.wigner3j(ell, 0, ell, 0, 0, 0) * (2 * ell + 1) ** 2
+        assert abs(hN * H.wigner3j(ell, 0, ell, 0, 0, 0) - (2 * ell + 1)) < 1e-12
