@@ -301,6 +301,35 @@ def bispec_leg(args, world, rank, barrier, max_over_ranks):
     torch.cuda.synchronize()
     barrier()
     ms_fft = max_over_ranks(s.elapsed_time(e)) / args.steps
+    # Sugiyama TripoSH multipoles on the same catalogue (every (k1, k2) bin pair, raw estimator)
+    mps = [(0, 0, 0), (1, 1, 0), (1, 1, 2), (2, 0, 2), (2, 2, 0), (2, 2, 2)]
+    nbn = w["nbins"]
+    sout = torch.zeros(len(mps) * nbn * nbn + nbn + 8, dtype=torch.float64, device="cuda")
+    kws = dict(n=w["n"], box=w["box"], kbins=kb, multipoles=mps, precision=w["precision"], out=sout)
+    for _ in range(args.warmup):
+        api.bispectrum_sugiyama(cd, **kws)
+    torch.cuda.synchronize()
+    barrier()
+    s.record()
+    for _ in range(args.steps):
+        api.bispectrum_sugiyama(cd, **kws)
+    e.record()
+    torch.cuda.synchronize()
+    barrier()
+    ms_sug = max_over_ranks(s.elapsed_time(e)) / args.steps
+    api.set_profiling(True)
+    sacc = {}
+    for _ in range(max(1, args.steps // 4)):
+        api.bispectrum_sugiyama(cd, **kws)
+        for name, t, _ in api.stage_times():
+            a = sacc.setdefault(name, [0.0, 0])
+            a[0] += t
+            a[1] += 1
+    api.set_profiling(False)
+    sugiyama = {"multipoles": mps, "bin_pairs": nbn * nbn, "ms_per_step": ms_sug,
+                "value": world * len(mps) * nbn * nbn / (ms_sug / 1e3), "unit": "multipole values/s",
+                "stages_ms": {k: round(v[0] / v[1], 4) for k, v in sacc.items()},
+                "note": "TripoSH B_l1l2L (raw) for all 361 (k1, k2) pairs, global line of sight"}
     plain = None
     if not args.no_plain and rank == 0:
         # the plain float64 form (full inverse transforms, direct float64 triangle sums), compared
@@ -332,6 +361,7 @@ def bispec_leg(args, world, rank, barrier, max_over_ranks):
                        "assign": "TSC", "interlace": True},
             "stages_ms": stages, "gpu_launches": launches * args.steps,
             "plain_gpu": plain,
+            "sugiyama": sugiyama,
             "fft_method_shot": {"value": world * ntri.value * nmult / (ms_fft / 1e3), "ms_per_step": ms_fft,
                                 "note": "shot noise of B_l and B_l0l by the FFT method (exact sums of the two-object terms)"},
             "triple_product": "3xTF32 split hi+lo tensor-core products (mma.sync m16n8k8), FP32 within 128-cell chunks, FP64 across chunks"}

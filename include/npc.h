@@ -224,6 +224,31 @@ npc_status npc_bispectrum_layout(const npc_kbins* bins, uint32_t scoc_ell_mask,
 npc_status npc_bispectrum_triangles(const npc_kbins* bins, int32_t* tri, int64_t cap,
                                     int64_t* ntri);
 
+/* Sugiyama TripoSH bispectrum multipoles B_{l1 l2 L}(k1, k2) (Sec. 4.2, Eq. sugi_estimator with the
+ * fields of Eq. F_and_G), raw estimator (no shot noise subtracted), global line of sight
+ * (mesh->periodic = 1, or survey geometry with randoms and mesh->los = 1):
+ *   B(i, j) = H N / (I33 N_i N_j) sum_{m1 m2 M} (l1 l2 L; m1 m2 M) <F_l1^m1(x; k_i) F_l2^m2(x; k_j) G_L^M(x)>_x
+ * with F_l^m(x; k) = sum_{q in bin k} e^{iqx} y_l^{m*}(qhat) X(q), H = (l1 l2 L; 0 0 0),
+ * N = (2l1+1)(2l2+1)(2L+1), y = sqrt(4 pi/(2l+1)) Y, X the compensated interlaced spectrum and
+ * <.>_x the mean over the grid.  In the frame whose third axis is the line of sight only M = 0
+ * remains, G_L^0 is the full-range field of X for every L, and the m, -m sub-configurations pair up
+ * (Eq. sym_sugi): the library evaluates sum_{m=0..min(l1,l2)} of the real parts of F_l1^m F_l2^{m*} G
+ * as shell-field triple products on the tensor cores, every (k_i, k_j) bin pair at once.
+ * multipoles: nmult (1..16) triples (l1, l2, L), 0 <= l1, l2 <= 4, |l1 - l2| <= L <= l1 + l2, L and
+ *   l1 + l2 even (the plane-parallel symmetry about the line of sight); else NPC_ERR_INVALID_ARG.  Bins and mesh limits as npc_bispectrum (at most
+ *   24 bins, largest bin edge <= k_N/2).  Survey geometry with the line of sight to each grid point
+ *   (mesh->los = 0): NPC_ERR_UNSUPPORTED.
+ * Output `out` (float64, host or device as out_on_device), length npc_bispectrum_sugiyama_len():
+ *   [nmult][nbins][nbins] B (k1 = bin i the row, k2 = bin j the column), [nbins] N_modes,
+ *   then 8 scalars as in npc_catalog_scalars.
+ * Errors as npc_bispectrum. */
+npc_status npc_bispectrum_sugiyama(npc_ctx* ctx, const npc_mesh_spec* mesh, const npc_catalog* data,
+                                   const npc_catalog* randoms, const npc_kbins* bins, int32_t nmult,
+                                   const int32_t* multipoles, npc_precision prec, double* out,
+                                   int32_t out_on_device);
+/* Output length of npc_bispectrum_sugiyama: nmult * nbins^2 + nbins + 8 (-1 for bad arguments). */
+int64_t npc_bispectrum_sugiyama_len(const npc_kbins* bins, int32_t nmult);
+
 /* Batches of measurements --------------------------------------------------------------------------
  * Many mocks of uneven catalogue size and mesh, each measured as npc_power_multipoles (P_l for
  * ell_mask, no modified multipoles) and, when bispec_bins.nbins > 0, as npc_bispectrum with the

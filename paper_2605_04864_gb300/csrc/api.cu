@@ -656,6 +656,77 @@ npc_status npc_bispectrum_triangles(const npc_kbins* bins, int32_t* tri, int64_t
   return bispec_triangles(*bins, tri, cap, ntri);
 }
 
+int64_t npc_bispectrum_sugiyama_len(const npc_kbins* bins, int32_t nmult) {
+  if (!bins || bins->nbins < 1 || bins->nbins > 24 || nmult < 1 || nmult > NPC_SUGI_MAX) return -1;
+  const int64_t nb = bins->nbins;
+  return (int64_t)nmult * nb * nb + nb + 8;
+}
+
+npc_status npc_bispectrum_sugiyama(npc_ctx* ctx, const npc_mesh_spec* mesh, const npc_catalog* data,
+                                   const npc_catalog* randoms, const npc_kbins* bins, int32_t nmult,
+                                   const int32_t* multipoles, npc_precision prec, double* out,
+                                   int32_t out_on_device) {
+  if (!ctx) return NPC_ERR_INVALID_ARG;
+  begin_call(ctx);
+  NPC_TRY(check_spec(ctx, mesh));
+  NPC_TRY(check_bins(ctx, bins));
+  if (!out) return set_err(ctx, NPC_ERR_INVALID_ARG, "out is NULL");
+  if (!multipoles) return set_err(ctx, NPC_ERR_INVALID_ARG, "multipoles is NULL");
+  if (nmult < 1 || nmult > NPC_SUGI_MAX) return set_err(ctx, NPC_ERR_INVALID_ARG, "nmult must be 1..%d", NPC_SUGI_MAX);
+  if (bins->nbins > 24) return set_err(ctx, NPC_ERR_UNSUPPORTED, "bispectrum supports at most 24 bins");
+  SugiReq req{};
+  req.nmult = nmult;
+  for (int e = 0; e < nmult; ++e) {
+    const int l1 = multipoles[3 * e], l2 = multipoles[3 * e + 1], L = multipoles[3 * e + 2];
+    // L even: the plane-parallel symmetry about the line of sight (Sec. 4.2), so l1 + l2 is even too
+    if (l1 < 0 || l1 > 4 || l2 < 0 || l2 > 4 || L < std::abs(l1 - l2) || L > l1 + l2 || (L & 1) || ((l1 + l2) & 1))
+      return set_err(ctx, NPC_ERR_INVALID_ARG, "multipole (%d, %d, %d): need l1, l2 <= 4, |l1-l2| <= L <= l1+l2, "
+                     "L and l1+l2 even", l1, l2, L);
+    req.l1[e] = l1;
+    req.l2[e] = l2;
+    req.L[e] = L;
+  }
+  if (prec != NPC_PREC_FP64 && prec != NPC_PREC_MIXED) return set_err(ctx, NPC_ERR_INVALID_ARG, "bad precision");
+  if (mesh->periodic) {
+    if (randoms) return set_err(ctx, NPC_ERR_INVALID_ARG, "periodic box takes no randoms");
+  } else {
+    if (mesh->los != 1)
+      return set_err(ctx, NPC_ERR_UNSUPPORTED, "TripoSH multipoles need a global line of sight (los = 1)");
+    if (!randoms) return set_err(ctx, NPC_ERR_INVALID_ARG, "survey geometry needs randoms");
+    NPC_TRY(check_catalog(ctx, randoms, "randoms", true));
+    if (randoms->n == 0) return set_err(ctx, NPC_ERR_NUMERIC, "empty random catalogue");
+  }
+  const double kf = 2.0 * M_PI / mesh->box;
+  const double knyq = kf * mesh->n / 2.0;
+  const double kmax = bins->kmin + bins->nbins * bins->dk;
+  if (kmax > 0.5 * knyq)
+    return set_err(ctx, NPC_ERR_UNSUPPORTED, "largest bin edge %.4g exceeds k_N/2 = %.4g (closure would alias)", kmax,
+                   0.5 * knyq);
+  if (prec == NPC_PREC_FP64 && mesh->n > 256) return set_err(ctx, NPC_ERR_UNSUPPORTED, "FP64 precision supports n <= 256");
+  if (mesh->n > 512) return set_err(ctx, NPC_ERR_UNSUPPORTED, "bispectrum supports n <= 512");
+  NPC_TRY(check_catalog(ctx, data, "data", false));
+  if (data->n == 0) return set_err(ctx, NPC_ERR_NUMERIC, "empty data catalogue (I33 = 0)");
+  NPC_CUDA(ctx, cudaSetDevice(ctx->device));
+  const int64_t out_len = npc_bispectrum_sugiyama_len(bins, nmult);
+  ctx->stats.n_transforms = 1;
+  ctx->stats.n_r2c_equivalent = 1;
+  ctx->stats.n_phases = mesh->interlace ? 2 : 1;
+  DevCatalog d, r;
+  NPC_TRY(stage_catalog(ctx, data, "data", &d));
+  if (randoms) NPC_TRY(stage_catalog(ctx, randoms, "rand", &r));
+  double* sc;
+  NPC_TRY(ws_get(ctx, "scalars", sizeof(double) * SC_COUNT, (void**)&sc));
+  NPC_TRY(stage_mark(ctx, "upload"));
+  NPC_TRY(launch_catalog_scalars(ctx, d, randoms ? &r : nullptr, mesh->box, sc));
+  NPC_TRY(stage_mark(ctx, "scalars"));
+  double* dev_out = out;
+  if (!out_on_device) NPC_TRY(ws_get(ctx, "bis.out", sizeof(double) * out_len, (void**)&dev_out));
+  NPC_TRY(run_bispectrum_sugiyama(ctx, *mesh, *bins, req, prec, d, randoms ? &r : nullptr, sc, dev_out, out_len));
+  NPC_TRY(finish_output(ctx, dev_out, out, out_len, out_on_device));
+  NPC_TRY(stage_mark(ctx, "download"));
+  return end_call(ctx);
+}
+
 npc_status npc_bispectrum(npc_ctx* ctx, const npc_mesh_spec* mesh, const npc_catalog* data,
                           const npc_catalog* randoms, const npc_kbins* bins, uint32_t scoc_ell_mask,
                           uint32_t tripo_ell_mask, int32_t shot, npc_precision prec, double* out,

@@ -356,12 +356,52 @@ k_bin_cross(const cplx<T>* __restrict__ X0, const cplx<T>* __restrict__ XN, int 
 // ------------------------------------------------------------------------------------------
 struct ShellField {
   int8_t src;     // 0: X_0, 1: ones (indicator), 2: X_0 N_0^* (FFT-method shot noise), 3: X_2 (survey)
-  int8_t mult;    // 0: 1, 1: L_2(mu)
+  int8_t mult;    // 0: 1, 1: L_2(mu), 2: the TripoSH weight of (yl, ym, ypart)
   int16_t bin;    // >= 0: modes of this bin; -1: all modes with n2 <= n2cap
   int K;          // kz <= K, |ky| <= K
+  int8_t yl, ym;  // mult 2: the field is a part of F_l^m(x; k) = sum_q e^{iqx} y_l^{m*}(qhat) X(q), m >= 0
+  int8_t ypart;   // mult 2: 0 its real part, 1 its imaginary part
+  int8_t pad;
   int64_t off1;   // offset of this field in the x-pass output (complex elements)
   int64_t off2;   // offset in the y-pass output
 };
+
+// Orthonormal frame with e3 along the global line of sight; the TripoSH weights y_l^m(qhat) are
+// evaluated on the components (q.e1, q.e2, q.e3).
+struct LosFrame {
+  double e1[3], e2[3], e3[3];
+};
+
+// power-basis coefficients of the Legendre polynomials L_0 .. L_4
+__constant__ double c_legendre[5][5] = {{1.0, 0.0, 0.0, 0.0, 0.0},
+                                        {0.0, 1.0, 0.0, 0.0, 0.0},
+                                        {-0.5, 0.0, 1.5, 0.0, 0.0},
+                                        {0.0, -1.5, 0.0, 2.5, 0.0},
+                                        {0.375, 0.0, -3.75, 0.0, 4.375}};
+
+// Racah-normalised y_l^m = sqrt(4 pi/(2l+1)) Y_l^m for 0 <= m <= l <= 4 at the unit vector (x, y, z):
+// (-1)^m sqrt((l-m)!/(l+m)!) (d^m L_l/dmu^m)(z) (x + i y)^m, the Condon-Shortley phase included.
+template <typename T>
+__device__ __forceinline__ void ylm_frame(int l, int m, T x, T y, T z, T& re, T& im) {
+  T d = T(0), zp = T(1);
+  for (int k = m; k <= l; ++k) {
+    T f = T(c_legendre[l][k]);
+    for (int q = k - m + 1; q <= k; ++q) f *= T(q);   // k!/(k-m)!
+    d += f * zp;
+    zp *= z;
+  }
+  double ratio = 1.0;
+  for (int q = l - m + 1; q <= l + m; ++q) ratio *= q;
+  const T nrm = T((m & 1) ? -1.0 : 1.0) / sqrt(T(ratio));
+  T pr = T(1), pi = T(0);
+  for (int q = 0; q < m; ++q) {
+    const T t = pr * x - pi * y;
+    pi = pr * y + pi * x;
+    pr = t;
+  }
+  re = nrm * d * pr;
+  im = nrm * d * pi;
+}
 
 // x rows: for every (kz <= Kmax, |ky| <= Kmax) row, every field whose K covers it.  The shells and
 // their triple products are band-limited, so they run on a grid of NS <= n points per axis (the
@@ -372,7 +412,7 @@ __global__ void __launch_bounds__(BT)
 k_shell_x(const cplx<T>* __restrict__ X0, const cplx<T>* __restrict__ XN, const cplx<T>* __restrict__ X2, int KZX,
           int nfine,
           const ShellField* __restrict__ fields, int nfields, int Kmax, const int16_t* __restrict__ tab, int n2cap,
-          double lx, double ly, double lz, const cplx<T>* __restrict__ tw_g, cplx<T>* __restrict__ T1) {
+          const LosFrame fr, const cplx<T>* __restrict__ tw_g, cplx<T>* __restrict__ T1) {
   using C = cplx<T>;
   constexpr int TPF = NS / 8;
   constexpr int G = BT / TPF > 0 ? BT / TPF : 1;
@@ -407,7 +447,7 @@ k_shell_x(const cplx<T>* __restrict__ X0, const cplx<T>* __restrict__ XN, const 
       if (XN) xnrow[kx] = (inrange && kz < KZX) ? cmul(X0[src], cconj(XN[src])) : cmk(T(0), T(0));
       if (X2) x2row[kx] = (inrange && kz < KZX) ? X2[src] : cmk(T(0), T(0));
       const T kk = sqrt(T(n2));
-      const T mu = n2 > 0 ? (T(i) * T(lx) + T(jy) * T(ly) + T(kz) * T(lz)) / kk : T(0);
+      const T mu = n2 > 0 ? (T(i) * T(fr.e3[0]) + T(jy) * T(fr.e3[1]) + T(kz) * T(fr.e3[2])) / kk : T(0);
       l2row[kx] = T(1.5) * mu * mu - T(0.5);
       binrow[kx] = inrange ? tab[n2] : -1;
       n2row[kx] = inrange ? n2 : -1;
@@ -431,7 +471,26 @@ k_shell_x(const cplx<T>* __restrict__ X0, const cplx<T>* __restrict__ XN, const 
           const bool in = sf.bin >= 0 ? (binrow[kx] == sf.bin) : (n2row[kx] >= 0);
           if (in) {
             a = sf.src == 0 ? xrow[kx] : (sf.src == 2 ? xnrow[kx] : (sf.src == 3 ? x2row[kx] : cmk(T(1), T(0))));
-            if (sf.mult) a = cscale(a, l2row[kx]);
+            if (sf.mult == 1) {
+              a = cscale(a, l2row[kx]);
+            } else if (sf.mult == 2) {
+              // F_l^m = sum_q e^{iqx} (Re y - i Im y) X: for even l the real weights Re y (real part)
+              // and -Im y (imaginary part) are even in q; for odd l the parts are -i Im y X and
+              // -i Re y X.  Every weighted spectrum stays Hermitian, so each part is a real field.
+              const T ii = T(kx < NS / 2 ? kx : kx - NS), jj = T(jy), zz = T(kz);
+              const T inv = n2row[kx] > 0 ? T(1) / sqrt(T(n2row[kx])) : T(0);
+              const T ux = (ii * T(fr.e1[0]) + jj * T(fr.e1[1]) + zz * T(fr.e1[2])) * inv;
+              const T uy = (ii * T(fr.e2[0]) + jj * T(fr.e2[1]) + zz * T(fr.e2[2])) * inv;
+              const T uz = (ii * T(fr.e3[0]) + jj * T(fr.e3[1]) + zz * T(fr.e3[2])) * inv;
+              T yr, yi;
+              ylm_frame<T>(sf.yl, sf.ym, ux, uy, uz, yr, yi);
+              if (sf.yl & 1) {
+                const T w = sf.ypart ? yr : yi;
+                a = cmk(a.y * w, -a.x * w);
+              } else {
+                a = cscale(a, sf.ypart ? -yi : yr);
+              }
+            }
           }
         }
         v[q] = a;
@@ -970,6 +1029,25 @@ __global__ void k_bispec_finalize(const int* __restrict__ tri, const int* __rest
   if (tid < 8) out[oSC + tid] = sc[tid];
 }
 
+// TripoSH multipoles from the per-combination sums red[c][i][j] = sum_x A_i(x) G(x) C_j(x) (A, C the
+// parts of F_l1^m and F_l2^m of bins i and j): B_e(i, j) = sum_c coef[e][c] red[c][i][j] /
+// (I33 N_i N_j ncell), then the mode counts and the scalars.
+__global__ void k_sugi_finalize(const double* __restrict__ red, int ncombo, const double* __restrict__ coef,
+                                int nmult, int nb, const double* __restrict__ cross_m, int ncs,
+                                const double* __restrict__ sc, double ncell, double* __restrict__ out) {
+  const int nn = nb * nb;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthreads = gridDim.x * blockDim.x;
+  for (int o = tid; o < nmult * nn; o += nthreads) {
+    const int e = o / nn, ij = o % nn, i = ij / nb, j = ij % nb;
+    const double ni = cross_m[(size_t)i * ncs + 2], nj = cross_m[(size_t)j * ncs + 2];
+    double s = 0.0;
+    for (int c = 0; c < ncombo; ++c) s += coef[(size_t)e * ncombo + c] * red[(size_t)c * nn + ij];
+    out[o] = (ni > 0 && nj > 0) ? s / (sc[SC_I33] * ni * nj * ncell) : 0.0;
+  }
+  for (int b = tid; b < nb; b += nthreads) out[(size_t)nmult * nn + b] = cross_m[(size_t)b * ncs + 2];
+  if (tid < 8) out[(size_t)nmult * nn + nb + tid] = sc[tid];
+}
+
 // reduce per-warp cross partials into [bin][NCROSS] in a fixed order
 // one warp per (bin, sum): strided lane sums then a fixed shuffle tree (reproducible order)
 __global__ void k_cross_reduce(const double* __restrict__ part, int nrec, int nb, int ns, double* __restrict__ out) {
@@ -1026,6 +1104,29 @@ __global__ void k_nt_reduce(const double* __restrict__ part, int nparts, int npa
 // ------------------------------------------------------------------------------------------
 // host helpers
 // ------------------------------------------------------------------------------------------
+// Wigner 3j symbol for integer arguments by the Racah formula (float64; the factorials stay exact
+// for the arguments used here, j1 + j2 + j3 + 1 <= 17)
+static double wigner3j_host(int j1, int j2, int j3, int m1, int m2, int m3) {
+  if (m1 + m2 + m3 != 0 || j3 < std::abs(j1 - j2) || j3 > j1 + j2) return 0.0;
+  if (std::abs(m1) > j1 || std::abs(m2) > j2 || std::abs(m3) > j3) return 0.0;
+  auto fact = [](int n) {
+    double f = 1.0;
+    for (int q = 2; q <= n; ++q) f *= q;
+    return f;
+  };
+  const double tri = fact(j1 + j2 - j3) * fact(j1 - j2 + j3) * fact(-j1 + j2 + j3) / fact(j1 + j2 + j3 + 1);
+  const double pre =
+      std::sqrt(tri * fact(j1 + m1) * fact(j1 - m1) * fact(j2 + m2) * fact(j2 - m2) * fact(j3 + m3) * fact(j3 - m3));
+  const int tmin = std::max(0, std::max(j2 - j3 - m1, j1 - j3 + m2));
+  const int tmax = std::min(j1 + j2 - j3, std::min(j1 - m1, j2 + m2));
+  double sum = 0.0;
+  for (int t = tmin; t <= tmax; ++t)
+    sum += ((t & 1) ? -1.0 : 1.0) / (fact(t) * fact(j3 - j2 + t + m1) * fact(j3 - j1 + t - m2) *
+                                     fact(j1 + j2 - j3 - t) * fact(j1 - t - m1) * fact(j2 - t + m2));
+  const int ph = j1 - j2 - m3;
+  return ((ph % 2) != 0 ? -1.0 : 1.0) * pre * sum;
+}
+
 struct Tri {
   std::vector<int> tri;   // [ntri][3]
   std::vector<int> pij;   // pair (i | j << 16), lexicographic i <= j
@@ -1070,7 +1171,7 @@ struct ShellLaunch {
   int nfield, Kmax;
   const int16_t* tab;
   int n2cap;
-  double l[3];
+  LosFrame frame;
   const int* plane_f;
   const int* plane_kz;
   int nplanes;
@@ -1093,8 +1194,7 @@ npc_status shell_passes(npc_ctx* ctx, const ShellLaunch& sl, cplx<T>* T1, cplx<T
     const int nrows = (sl.Kmax + 1) * (2 * sl.Kmax + 1);
     kern<<<std::min(nrows, ctx->num_sms * 4), BT, smem, ctx->stream>>>(
         (const C*)sl.X, (const C*)sl.XN, (const C*)sl.X2, sl.KZX, sl.nfine, sl.fields, sl.nfield, sl.Kmax, sl.tab,
-        sl.n2cap, sl.l[0],
-        sl.l[1], sl.l[2], tw, T1);
+        sl.n2cap, sl.frame, tw, T1);
     NPC_LAUNCH(ctx);
   }
   constexpr int TX = BCol<NS>::TX;
@@ -1136,7 +1236,7 @@ npc_status shell_dispatch(npc_ctx* ctx, int NS, const ShellLaunch& sl, cplx<T>* 
 template <typename T, int N>
 npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb, int scoc_mask, int tripo_mask,
                        int shot, const DevCatalog& d, const DevCatalog* r, double* sc, double* dev_out,
-                       int64_t out_len) {
+                       int64_t out_len, const SugiReq* sug = nullptr) {
   using C = cplx<T>;
   const double kf = 2.0 * M_PI / m.box;
   const double kmax = kb.kmin + kb.nbins * kb.dk;
@@ -1161,6 +1261,24 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
     const double ll = std::sqrt(m.los_dir[0] * m.los_dir[0] + m.los_dir[1] * m.los_dir[1] + m.los_dir[2] * m.los_dir[2]);
     for (int a = 0; a < 3; ++a) l3[a] = m.los_dir[a] / ll;
   }
+  // frame of the TripoSH weights: e3 the line of sight, e1 from x (or y when the line of sight is
+  // close to x) with its e3 component removed, e2 = e3 x e1 (x, y, z themselves for a line of sight
+  // along z)
+  LosFrame frame{};
+  {
+    double a[3] = {std::fabs(l3[0]) < 0.9 ? 1.0 : 0.0, std::fabs(l3[0]) < 0.9 ? 0.0 : 1.0, 0.0};
+    const double ad = a[0] * l3[0] + a[1] * l3[1];
+    double e1[3] = {a[0] - ad * l3[0], a[1] - ad * l3[1], a[2] - ad * l3[2]};
+    const double n1 = std::sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+    for (int q = 0; q < 3; ++q) {
+      frame.e1[q] = e1[q] / n1;
+      frame.e3[q] = l3[q];
+    }
+    frame.e2[0] = l3[1] * frame.e1[2] - l3[2] * frame.e1[1];
+    frame.e2[1] = l3[2] * frame.e1[0] - l3[0] * frame.e1[2];
+    frame.e2[2] = l3[0] * frame.e1[1] - l3[1] * frame.e1[0];
+  }
+  const bool sugi = sug != nullptr;
   // survey geometry with the line of sight to each grid point and an l = 2 request: Yamamoto X_2
   // from the Y_2m-weighted transforms instead of L_2(khat . los) X_0
   const bool yam = !m.periodic && m.los != 1 && (((scoc_mask | tripo_mask) & 4) != 0);
@@ -1312,7 +1430,7 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
 
   // 4. shell fields
   const bool want2 = (scoc_mask & 4) != 0;
-  const bool wantG0 = (tripo_mask & 1) != 0, wantG2 = (tripo_mask & 4) != 0;
+  const bool wantG0 = (tripo_mask & 1) != 0 || sugi, wantG2 = (tripo_mask & 4) != 0;
   // grid of the shell fields and triple products: shells reach |q_i| <= K and the full fields
   // |q_i| <= K2, so a closed triple sums to at most 3K (2K + K2 with the compressed estimator) per
   // axis; any grid of more points has no aliasing and gives the same sums up to (n/NS)^3, which
@@ -1343,7 +1461,7 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
   const std::string ntname = slot_name(ctx, "bis.ntsums");
   NPC_TRY(ws_get(ctx, ntname.c_str(), sizeof(double) * npair * nb, (void**)&nt_sums));
   auto it = ctx->host_cache_keys.find(ntname);
-  const bool need_nt = it == ctx->host_cache_keys.end() || it->second != ntkey;
+  const bool need_nt = !sugi && (it == ctx->host_cache_keys.end() || it->second != ntkey);
 
   // FFT-method shot noise: the l = 2 triplet count sum_x L_2 I_i I_j I_k is cached like N_T
   const bool fftshot = shot == 2;
@@ -1394,6 +1512,35 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
       for (int e = 0; e < ntl; ++e) add(2, tls[e] == 2 ? 1 : 0, -1, KG, 7);
       iLF = (int)fl.size();
       for (int e = 0; e < ntl; ++e) add(1, tls[e] == 2 ? 1 : 0, -1, KG, 8);
+    }
+  }
+  // TripoSH shell fields: the parts of F_l^m(x; k_b), 0 <= m <= min(l1, l2), of every l requested
+  // (F_0^0 is F0_b above); sfield[l][m][part] = R index of bin 0, or -1
+  int sfield[5][5][2];
+  for (int l = 0; l < 5; ++l)
+    for (int mm = 0; mm < 5; ++mm) sfield[l][mm][0] = sfield[l][mm][1] = -1;
+  if (sugi) {
+    sfield[0][0][0] = 0;
+    int fam = 20;
+    for (int e = 0; e < sug->nmult; ++e) {
+      const int l1 = sug->l1[e], l2 = sug->l2[e], mmax = std::min(l1, l2);
+      for (int side = 0; side < 2; ++side) {
+        const int l = side ? l2 : l1;
+        for (int mm = 0; mm <= mmax; ++mm)
+          for (int part = 0; part < 2; ++part) {
+            // m = 0: the imaginary part of an even-l field and the real part of an odd-l one vanish
+            if (mm == 0 && part == ((l & 1) ? 0 : 1)) continue;
+            if (sfield[l][mm][part] >= 0) continue;
+            sfield[l][mm][part] = (int)fl.size();
+            for (int b = 0; b < nb; ++b) {
+              add(0, 2, b, Ks, fam);
+              fl.back().yl = (int8_t)l;
+              fl.back().ym = (int8_t)mm;
+              fl.back().ypart = (int8_t)part;
+            }
+            ++fam;
+          }
+      }
     }
   }
   const int nfield = (int)fl.size();
@@ -1451,6 +1598,47 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
     return ja != jb ? ja < jb : (tr.pij[a] & 0xffff) < (tr.pij[b] & 0xffff);
   });
   const size_t t_rowp = push_bytes(row_pair.data(), sizeof(int) * row_pair.size());
+  // TripoSH: combinations (l1, l2, m >= 0, part) and their weight in each multipole.  With
+  // F_l^{-m} = (-1)^{l+m} F_l^{m*} (Eq. sugi_F_and_G), G_L^M = delta_M0 G in the line-of-sight frame
+  // and (l1 l2 L; -m m 0) = (l1 l2 L; m -m 0) for even l1 + l2 + L, the m and -m sub-configurations
+  // both contribute (-1)^{l2+m} (l1 l2 L; m -m 0) sum_x (Re F1 Re F2 + Im F1 Im F2) G: real part of
+  // the product (Eq. sym_sugi).
+  struct SCombo {
+    int l1, l2, m, part;
+  };
+  std::vector<SCombo> combos;
+  std::vector<double> scoef;
+  size_t t_spij = 0, t_srow = 0, t_scoef = 0;
+  if (sugi) {
+    auto combo_of = [&](int l1, int l2, int mm, int part) {
+      for (size_t c = 0; c < combos.size(); ++c)
+        if (combos[c].l1 == l1 && combos[c].l2 == l2 && combos[c].m == mm && combos[c].part == part) return (int)c;
+      combos.push_back(SCombo{l1, l2, mm, part});
+      return (int)combos.size() - 1;
+    };
+    std::vector<std::vector<std::pair<int, double>>> terms(sug->nmult);
+    for (int e = 0; e < sug->nmult; ++e) {
+      const int l1 = sug->l1[e], l2 = sug->l2[e], L = sug->L[e], mmax = std::min(l1, l2);
+      const double hN = wigner3j_host(l1, l2, L, 0, 0, 0) * (2 * l1 + 1) * (2 * l2 + 1) * (2 * L + 1);
+      for (int mm = -mmax; mm <= mmax; ++mm) {
+        const double w = hN * wigner3j_host(l1, l2, L, mm, -mm, 0) * (((l2 + mm) & 1) ? -1.0 : 1.0);
+        const int am = std::abs(mm);
+        for (int part = 0; part < 2; ++part) {
+          if (am == 0 && part == ((l1 & 1) ? 0 : 1)) continue;   // the vanishing part at m = 0
+          terms[e].push_back({combo_of(l1, l2, am, part), w});
+        }
+      }
+    }
+    scoef.assign((size_t)sug->nmult * combos.size(), 0.0);
+    for (int e = 0; e < sug->nmult; ++e)
+      for (const auto& tw : terms[e]) scoef[(size_t)e * combos.size() + tw.first] += tw.second;
+    // rows b: A = the l1 part of bin b, B = G (pair (b, 0)); columns: the l2 parts of every bin
+    std::vector<int> sp(nb);
+    for (int b = 0; b < nb; ++b) sp[b] = b;
+    t_spij = push_bytes(sp.data(), sizeof(int) * nb);
+    t_srow = push_bytes(sp.data(), sizeof(int) * nb);
+    t_scoef = push_bytes(scoef.data(), sizeof(double) * scoef.size());
+  }
   char* dtab;
   NPC_TRY(ws_table(ctx, need_nt ? "bis.tables.nt" : "bis.tables", tables, tables.data(), tables.size(),
                    (void**)&dtab));
@@ -1474,7 +1662,7 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
     sl.Kmax = Kshell;
     sl.tab = tab_shell;
     sl.n2cap = n2cap;
-    for (int a = 0; a < 3; ++a) sl.l[a] = l3[a];
+    sl.frame = frame;
     sl.plane_f = (const int*)(dtab + t_pf);
     sl.plane_kz = (const int*)(dtab + t_pk);
     sl.nplanes = (int)plane_f.size();
@@ -1593,7 +1781,7 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
   double* part;
   NPC_TRY(ws_get(ctx, "bis.tripart", sizeof(double) * (size_t)grid * std::max(ta.nrows, tn.nrows) * TRI_COLS,
                  (void**)&part));
-  auto launch = [&](const TripleArgs& a, int grid, double* part) -> npc_status {
+  auto launch_tab = [&](const TripleArgs& a, int grid, double* part, size_t tp, size_t trp) -> npc_status {
     if constexpr (sizeof(T) == 4) {
       const int mt = tri_mt(a), rows = TRI_WARPS * mt * 16;
       const int groups = (a.nrows + rows - 1) / rows;
@@ -1602,7 +1790,7 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
                             sizeof(double) * (size_t)TRI_WARPS * 32 * mt * nt * 4;
         NPC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         kern<<<dim3(grid, groups), TRI_WARPS * 32, smem, ctx->stream>>>(
-            (const float*)R, a, (const int*)(dtab + t_pij), (const int*)(dtab + t_rowp), part);
+            (const float*)R, a, (const int*)(dtab + tp), (const int*)(dtab + trp), part);
         return NPC_OK;
       };
       if (a.ncol <= 24) NPC_TRY(mt == 1 ? run(k_triple<3, 1>, 3) : run(k_triple<3, 2>, 3));
@@ -1610,11 +1798,56 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
     } else {
       const int outs = a.nrows * a.ncol;
       k_triple_f64<<<dim3(grid, (outs + 255) / 256), 256, 0, ctx->stream>>>((const double*)R, a,
-                                                                             (const int*)(dtab + t_pij), part);
+                                                                             (const int*)(dtab + tp), part);
+      (void)trp;
     }
     NPC_LAUNCH(ctx);
     return NPC_OK;
   };
+  auto launch = [&](const TripleArgs& a, int grid, double* part) { return launch_tab(a, grid, part, t_pij, t_rowp); };
+  if (sugi) {
+    // one product per combination: rows F_l1^m part (bin i) x G, columns F_l2^m part (bin j)
+    const int ncombo = (int)combos.size();
+    std::vector<TripleArgs> targs(ncombo);
+    for (int c = 0; c < ncombo; ++c) {
+      TripleArgs& a = targs[c];
+      a = TripleArgs{};
+      a.npair = nb;
+      a.ncell = (int64_t)ncs;
+      auto stage_of = [&](int field) {
+        for (int q = 0; q < a.nstage; ++q)
+          if (a.stage_field[q] == field) return q;
+        a.stage_field[a.nstage] = field;
+        return a.nstage++;
+      };
+      for (int q = 0; q < TRI_COLS; ++q) a.c_slot[q] = -1;
+      const SCombo& cb = combos[c];
+      for (int b = 0; b < nb; ++b) a.a_slot[0][b] = stage_of(sfield[cb.l1][cb.m][cb.part] + b);
+      a.b_slot[0][0] = stage_of(iG);
+      for (int b = 0; b < nb; ++b) a.c_slot[b] = stage_of(sfield[cb.l2][cb.m][cb.part] + b);
+      a.nf_cols = nb;
+      a.nrows = nb;
+      a.ncol = nb;
+    }
+    const int gsug = grid_for(targs[0]);
+    const size_t per = (size_t)gsug * nb * nb;
+    double *spart, *sred;
+    NPC_TRY(ws_get(ctx, "bis.sugpart", sizeof(double) * per * ncombo, (void**)&spart));
+    NPC_TRY(ws_get(ctx, "bis.sugred", sizeof(double) * (size_t)nb * nb * ncombo, (void**)&sred));
+    for (int c = 0; c < ncombo; ++c) NPC_TRY(launch_tab(targs[c], gsug, spart + c * per, t_spij, t_srow));
+    NPC_TRY(stage_mark(ctx, "triple"));
+    for (int c = 0; c < ncombo; ++c) {
+      k_part_reduce<<<(nb * nb + 31) / 32, 32 * PR_SLICES, 0, ctx->stream>>>(spart + c * per, gsug, (int64_t)nb * nb,
+                                                                            sred + (size_t)c * nb * nb);
+      NPC_LAUNCH(ctx);
+    }
+    k_sugi_finalize<<<std::max(1, (sug->nmult * nb * nb + 127) / 128), 128, 0, ctx->stream>>>(
+        sred, ncombo, (const double*)(dtab + t_scoef), sug->nmult, nb, cross_m, nsum_c, sc, (double)ncs, dev_out);
+    NPC_LAUNCH(ctx);
+    NPC_TRY(stage_mark(ctx, "finalize"));
+    (void)out_len;
+    return NPC_OK;
+  }
   if (need_nt) {
     NPC_TRY(launch(tn, grid, part));
     k_nt_reduce<<<(npair * nb + 127) / 128, 128, 0, ctx->stream>>>(part, grid, npair, nb, nb, (double)ncs, 1,
@@ -1710,19 +1943,20 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
 
 template <typename T>
 npc_status bispec_dispatch(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb, int sm, int tm, int shot,
-                           const DevCatalog& d, const DevCatalog* r, double* sc, double* out, int64_t len) {
+                           const DevCatalog& d, const DevCatalog* r, double* sc, double* out, int64_t len,
+                           const SugiReq* sug = nullptr) {
   switch (m.n) {
-    case 16: return bispec_impl<T, 16>(ctx, m, kb, sm, tm, shot, d, r, sc, out, len);
-    case 32: return bispec_impl<T, 32>(ctx, m, kb, sm, tm, shot, d, r, sc, out, len);
-    case 64: return bispec_impl<T, 64>(ctx, m, kb, sm, tm, shot, d, r, sc, out, len);
-    case 128: return bispec_impl<T, 128>(ctx, m, kb, sm, tm, shot, d, r, sc, out, len);
-    case 256: return bispec_impl<T, 256>(ctx, m, kb, sm, tm, shot, d, r, sc, out, len);
-    case 48: return bispec_impl<T, 48>(ctx, m, kb, sm, tm, shot, d, r, sc, out, len);
-    case 96: return bispec_impl<T, 96>(ctx, m, kb, sm, tm, shot, d, r, sc, out, len);
-    case 192: return bispec_impl<T, 192>(ctx, m, kb, sm, tm, shot, d, r, sc, out, len);
+    case 16: return bispec_impl<T, 16>(ctx, m, kb, sm, tm, shot, d, r, sc, out, len, sug);
+    case 32: return bispec_impl<T, 32>(ctx, m, kb, sm, tm, shot, d, r, sc, out, len, sug);
+    case 64: return bispec_impl<T, 64>(ctx, m, kb, sm, tm, shot, d, r, sc, out, len, sug);
+    case 128: return bispec_impl<T, 128>(ctx, m, kb, sm, tm, shot, d, r, sc, out, len, sug);
+    case 256: return bispec_impl<T, 256>(ctx, m, kb, sm, tm, shot, d, r, sc, out, len, sug);
+    case 48: return bispec_impl<T, 48>(ctx, m, kb, sm, tm, shot, d, r, sc, out, len, sug);
+    case 96: return bispec_impl<T, 96>(ctx, m, kb, sm, tm, shot, d, r, sc, out, len, sug);
+    case 192: return bispec_impl<T, 192>(ctx, m, kb, sm, tm, shot, d, r, sc, out, len, sug);
   }
   if constexpr (sizeof(T) == 4) {
-    if (m.n == 512) return bispec_impl<T, 512>(ctx, m, kb, sm, tm, shot, d, r, sc, out, len);
+    if (m.n == 512) return bispec_impl<T, 512>(ctx, m, kb, sm, tm, shot, d, r, sc, out, len, sug);
   }
   return set_err(ctx, NPC_ERR_UNSUPPORTED, "bispectrum mesh size %d not supported at this precision", m.n);
 }
@@ -1735,6 +1969,13 @@ npc_status run_bispectrum(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins&
   if (prec == NPC_PREC_FP64)
     return bispec_dispatch<double>(ctx, m, kb, scoc_mask, tripo_mask, shot, d, r, sc, out, len);
   return bispec_dispatch<float>(ctx, m, kb, scoc_mask, tripo_mask, shot, d, r, sc, out, len);
+}
+
+npc_status run_bispectrum_sugiyama(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb, const SugiReq& req,
+                                   int prec, const DevCatalog& d, const DevCatalog* r, double* sc, double* out,
+                                   int64_t len) {
+  if (prec == NPC_PREC_FP64) return bispec_dispatch<double>(ctx, m, kb, 1, 0, 0, d, r, sc, out, len, &req);
+  return bispec_dispatch<float>(ctx, m, kb, 1, 0, 0, d, r, sc, out, len, &req);
 }
 
 int64_t bispec_counts(const npc_kbins& kb, int64_t* ntri, int64_t* npair) {

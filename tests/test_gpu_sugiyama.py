@@ -1,0 +1,114 @@
+"""GPU parity: npc_bispectrum_sugiyama (TripoSH B_{l1 l2 L}, through the C ABI) against the FP64
+oracle, which sums every (m1, m2, M) sub-configuration in the catalogue's own frame."""
+import numpy as np
+import pytest
+
+from helpers import ensure_built
+from oracle import power as P
+from oracle import sugiyama as OS
+from synthetic import make_periodic_catalog
+
+pytestmark = pytest.mark.gpu
+
+LOW = [(0, 0, 0), (1, 1, 0), (1, 1, 2), (2, 0, 2), (0, 2, 2), (2, 2, 0), (2, 2, 2), (2, 2, 4)]
+HIGH = [(0, 0, 0), (3, 1, 2), (1, 3, 4), (3, 3, 0), (4, 0, 4), (4, 2, 2), (2, 4, 6), (4, 4, 8), (3, 3, 6)]
+TILT = (1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0)
+
+
+@pytest.fixture(scope="module")
+def api():
+    ensure_built()
+    from paper_2605_04864_gb300 import api as A
+
+    return A
+
+
+def _spec(n, box, los_dir, periodic=1, origin=(0.0, 0.0, 0.0)):
+    return dict(n=n, box=box, origin=origin, assign=3, interlace=1, los="global", los_dir=los_dir,
+                periodic=periodic)
+
+
+def _oracle(spec, cat, randoms, kb, mps):
+    sc = P.catalog_scalars(cat, randoms, spec["box"])
+    meshes = P.fkp_meshes(spec, cat, randoms, sc)
+    return OS.sugiyama_fft(spec, meshes, kb, mps, sc["I33"]), OS.mode_counts(spec, kb)
+
+
+def _check(res, orc, cnt, mps, tol):
+    """Error relative to the B_000 scale of the same bin pair."""
+    np.testing.assert_array_equal(res["nmodes"], cnt)
+    scale = np.abs(np.real(orc[(0, 0, 0)]))
+    for mp in mps:
+        got, want = res["B"][mp], np.real(orc[mp])
+        e = np.abs(got - want) / np.maximum(np.abs(want), scale)
+        assert np.max(e) < tol, (mp, np.max(e))
+
+
+@pytest.mark.parametrize("mps", [LOW, HIGH], ids=["l<=2", "l<=4"])
+@pytest.mark.parametrize("los_dir", [(0.0, 0.0, 1.0), TILT], ids=["z", "tilted"])
+def test_fp64_periodic(api, mps, los_dir):
+    cat = make_periodic_catalog(20000, 300.0, 32, seed=81)
+    kb = (0.02, 0.02, 5)   # k_max = 0.12 < k_N/2 = 0.168
+    res = api.bispectrum_sugiyama(cat, n=32, box=300.0, kbins=kb, multipoles=mps, los_dir=los_dir,
+                                  precision="fp64")
+    orc, cnt = _oracle(_spec(32, 300.0, los_dir), cat, None, kb, mps)
+    _check(res, orc, cnt, mps, 1e-10)
+
+
+@pytest.mark.parametrize("n", [64, 48])
+def test_mixed_periodic(api, n):
+    """Float32 shell fields and 3xTF32 tensor-core products; a radix-3 mesh as well."""
+    box = 600.0 if n == 64 else 450.0
+    cat = make_periodic_catalog(60000, box, 32, seed=83)
+    kf = 2 * np.pi / box
+    kb = (2 * kf, 1.5 * kf, 6)   # k_max = 11 k_f < k_N/2 = n k_f / 4
+    mps = [(0, 0, 0), (1, 1, 2), (2, 0, 2), (2, 2, 2)]
+    res = api.bispectrum_sugiyama(cat, n=n, box=box, kbins=kb, multipoles=mps, los_dir=TILT, precision="mixed")
+    orc, cnt = _oracle(_spec(n, box, TILT), cat, None, kb, mps)
+    _check(res, orc, cnt, mps, 1e-4)
+
+
+def test_survey_geometry_global_line_of_sight(api):
+    """FKP field with randoms and a global line of sight."""
+    from synthetic import make_survey_catalogs
+
+    box = 600.0
+    g, r, origin = make_survey_catalogs(20000, 200000, box, 900.0, 32, seed=85, fkp_p0=1e4)
+    kf = 2 * np.pi / box
+    kb = (2 * kf, 1.5 * kf, 4)   # k_max = 8 k_f = k_N/2 at 32^3
+    mps = [(0, 0, 0), (2, 0, 2), (1, 1, 2)]
+    res = api.bispectrum_sugiyama(g, n=32, box=box, kbins=kb, multipoles=mps, los_dir=TILT, precision="fp64",
+                                  origin=origin, randoms=r)
+    orc, cnt = _oracle(_spec(32, box, TILT, periodic=0, origin=tuple(origin)), g, r, kb, mps)
+    _check(res, orc, cnt, mps, 1e-10)
+
+
+def test_monopole_matches_the_compressed_estimator(api):
+    """B_000 of the two estimators coincide (Sec. 6): the library's two paths agree."""
+    cat = make_periodic_catalog(20000, 300.0, 32, seed=87)
+    kb = (0.02, 0.02, 5)
+    sug = api.bispectrum_sugiyama(cat, n=32, box=300.0, kbins=kb, multipoles=[(0, 0, 0)], precision="fp64")
+    comp = api.bispectrum(cat, n=32, box=300.0, kbins=kb, scoc_ells=(0,), tripo_ells=(0,), shot=False,
+                          precision="fp64")
+    prs = [(i, j) for i in range(5) for j in range(i, 5)]
+    got = np.array([sug["B"][(0, 0, 0)][i, j] for i, j in prs])
+    np.testing.assert_allclose(got, comp["BB"][0], rtol=1e-10, atol=1e-12 * np.max(np.abs(got)))
+
+
+def test_rejects(api):
+    cat = make_periodic_catalog(2000, 300.0, 16, seed=89)
+    kb = (0.02, 0.02, 5)
+    with pytest.raises(RuntimeError):   # odd l1 + l2 + L
+        api.bispectrum_sugiyama(cat, n=32, box=300.0, kbins=kb, multipoles=[(1, 0, 0)])
+    with pytest.raises(RuntimeError):   # odd L (odd-parity multipole)
+        api.bispectrum_sugiyama(cat, n=32, box=300.0, kbins=kb, multipoles=[(1, 0, 1)])
+    with pytest.raises(RuntimeError):   # l above 4
+        api.bispectrum_sugiyama(cat, n=32, box=300.0, kbins=kb, multipoles=[(5, 5, 0)])
+    with pytest.raises(RuntimeError):   # aliasing closure
+        api.bispectrum_sugiyama(cat, n=32, box=300.0, kbins=(0.02, 0.02, 8), multipoles=[(0, 0, 0)])
+    from synthetic import make_survey_catalogs
+
+    g, r, origin = make_survey_catalogs(2000, 20000, 600.0, 900.0, 16, seed=91, fkp_p0=1e4)
+    with pytest.raises(RuntimeError):   # survey geometry with the line of sight to each grid point
+        api.bispectrum_sugiyama(g, n=32, box=600.0, kbins=(0.02, 0.01, 3), multipoles=[(2, 0, 2)], origin=origin,
+                                randoms=r, los_dir=None)
