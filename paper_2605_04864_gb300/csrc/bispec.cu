@@ -407,7 +407,7 @@ __device__ __forceinline__ void ylm_frame(int l, int m, T x, T y, T z, T& re, T&
 // their triple products are band-limited, so they run on a grid of NS <= n points per axis (the
 // smallest with no aliasing of the closed triples); row kx' of the NS grid holds the integer
 // frequency i = kx' (kx' < NS/2) or kx' - NS, read from the n-grid spectrum X0.
-template <typename T, int NS>
+template <typename T, int NS, bool YW>
 __global__ void __launch_bounds__(BT)
 k_shell_x(const cplx<T>* __restrict__ X0, const cplx<T>* __restrict__ XN, const cplx<T>* __restrict__ X2, int KZX,
           int nfine,
@@ -471,9 +471,9 @@ k_shell_x(const cplx<T>* __restrict__ X0, const cplx<T>* __restrict__ XN, const 
           const bool in = sf.bin >= 0 ? (binrow[kx] == sf.bin) : (n2row[kx] >= 0);
           if (in) {
             a = sf.src == 0 ? xrow[kx] : (sf.src == 2 ? xnrow[kx] : (sf.src == 3 ? x2row[kx] : cmk(T(1), T(0))));
-            if (sf.mult == 1) {
-              a = cscale(a, l2row[kx]);
-            } else if (sf.mult == 2) {
+            if (sf.mult == 1) a = cscale(a, l2row[kx]);
+            // (YW: the call holds TripoSH fields; the other calls compile without this branch)
+            if (YW && sf.mult == 2) {
               // F_l^m = sum_q e^{iqx} (Re y - i Im y) X: for even l the real weights Re y (real part)
               // and -Im y (imaginary part) are even in q; for odd l the parts are -i Im y X and
               // -i Re y X.  Every weighted spectrum stays Hermitian, so each part is a real field.
@@ -654,7 +654,10 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], 
 // Fragment layouts of m16n8k8 (tf32): A a0 (row g, k t), a1 (g+8, t), a2 (g, t+4), a3 (g+8, t+4);
 // B b0 (k t, col g), b1 (k t+4, col g); D d0, d1 (row g, cols 2t, 2t+1), d2, d3 (row g+8, ...),
 // with g = lane/4 and t = lane%4.
-template <int TRI_NT, int TRI_MT>
+// SK (split over cells): every warp takes the same TRI_MT m tiles (the whole row group) and its own
+// TRI_CHUNK / TRI_WARPS cells of each staged chunk; the warps' FP64 sums are added in warp order at
+// the end.  For products with few rows (at most 16 TRI_MT), where the row split would leave warps idle.
+template <int TRI_NT, int TRI_MT, bool SK = false>
 __global__ void __launch_bounds__(TRI_WARPS * 32, TRI_MT == 1 ? 3 : 2)
 k_triple(const float* __restrict__ R, const TripleArgs A, const int* __restrict__ pair_ij,
          const int* __restrict__ row_pair, double* __restrict__ part) {
@@ -663,7 +666,7 @@ k_triple(const float* __restrict__ R, const TripleArgs A, const int* __restrict_
   double* dacc = reinterpret_cast<double*>(stage + (size_t)A.nstage * TRI_SPAD);  // [tid][NACC]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = lane >> 2, t = lane & 3;
-  const int rowbase = blockIdx.y * tri_rows<TRI_MT>() + warp * TRI_MT * 16;
+  const int rowbase = SK ? blockIdx.y * TRI_MT * 16 : blockIdx.y * tri_rows<TRI_MT>() + warp * TRI_MT * 16;
   int sa[TRI_MT][2], sb[TRI_MT][2], orow[TRI_MT][2];
 #pragma unroll
   for (int mt = 0; mt < TRI_MT; ++mt) {
@@ -708,7 +711,9 @@ k_triple(const float* __restrict__ R, const TripleArgs A, const int* __restrict_
       stage[(size_t)sl * TRI_SPAD + c] = c < nc ? R[(size_t)A.stage_field[sl] * A.ncell + c0 + c] : 0.f;
     }
     __syncthreads();
-    for (int kk = 0; kk < TRI_CHUNK; kk += 8) {
+    constexpr int KPW = SK ? TRI_CHUNK / TRI_WARPS : TRI_CHUNK;   // cells of the chunk per warp
+    const int kbeg = SK ? warp * KPW : 0;
+    for (int kk = kbeg; kk < kbeg + KPW; kk += 8) {
       uint32_t bh[TRI_NT][2], bl[TRI_NT][2];
 #pragma unroll
       for (int nt = 0; nt < TRI_NT; ++nt) {
@@ -752,6 +757,16 @@ k_triple(const float* __restrict__ R, const TripleArgs A, const int* __restrict_
             myacc[e] += (double)d[mt][nt][q];
             d[mt][nt][q] = 0.f;
           }
+    }
+  }
+  if constexpr (SK) {
+    // add the warps' sums in warp order (warp 0's own sums first); warp 0 writes them
+    __syncthreads();
+    if (warp != 0) return;
+    for (int q = 0; q < NACC; ++q) {
+      double v = 0.0;
+      for (int w = 0; w < TRI_WARPS; ++w) v += dacc[(size_t)(w * 32 + lane) * NACC + q];
+      myacc[q] = v;
     }
   }
   // this CTA's partial sums as part[cta][row][col]
@@ -1172,6 +1187,7 @@ struct ShellLaunch {
   const int16_t* tab;
   int n2cap;
   LosFrame frame;
+  int has_yw;       // some field carries a TripoSH weight (mult 2)
   const int* plane_f;
   const int* plane_kz;
   int nplanes;
@@ -1189,7 +1205,7 @@ npc_status shell_passes(npc_ctx* ctx, const ShellLaunch& sl, cplx<T>* T1, cplx<T
   {
     const size_t smem = sizeof(C) * (4 * NS + (size_t)RowGroups<NS, BT>::NBUF * row_pad_len<NS>()) +
                         sizeof(T) * NS + sizeof(int) * 2 * NS;
-    auto kern = k_shell_x<T, NS>;
+    auto kern = sl.has_yw ? k_shell_x<T, NS, true> : k_shell_x<T, NS, false>;
     NPC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int nrows = (sl.Kmax + 1) * (2 * sl.Kmax + 1);
     kern<<<std::min(nrows, ctx->num_sms * 4), BT, smem, ctx->stream>>>(
@@ -1663,6 +1679,7 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
     sl.tab = tab_shell;
     sl.n2cap = n2cap;
     sl.frame = frame;
+    sl.has_yw = sugi ? 1 : 0;
     sl.plane_f = (const int*)(dtab + t_pf);
     sl.plane_kz = (const int*)(dtab + t_pk);
     sl.nplanes = (int)plane_f.size();
@@ -1793,8 +1810,18 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
             (const float*)R, a, (const int*)(dtab + tp), (const int*)(dtab + trp), part);
         return NPC_OK;
       };
-      if (a.ncol <= 24) NPC_TRY(mt == 1 ? run(k_triple<3, 1>, 3) : run(k_triple<3, 2>, 3));
-      else NPC_TRY(mt == 1 ? run(k_triple<4, 1>, 4) : run(k_triple<4, 2>, 4));
+      if (a.nrows <= 32 && a.ncol <= 24) {
+        // few rows: all warps on the same two m tiles, each on its own cells
+        const size_t smem = sizeof(float) * (size_t)a.nstage * TRI_SPAD + sizeof(double) * (size_t)TRI_WARPS * 32 * 2 * 3 * 4;
+        auto kern = k_triple<3, 2, true>;
+        NPC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kern<<<dim3(grid, 1), TRI_WARPS * 32, smem, ctx->stream>>>((const float*)R, a, (const int*)(dtab + tp),
+                                                                   (const int*)(dtab + trp), part);
+      } else if (a.ncol <= 24) {
+        NPC_TRY(mt == 1 ? run(k_triple<3, 1>, 3) : run(k_triple<3, 2>, 3));
+      } else {
+        NPC_TRY(mt == 1 ? run(k_triple<4, 1>, 4) : run(k_triple<4, 2>, 4));
+      }
     } else {
       const int outs = a.nrows * a.ncol;
       k_triple_f64<<<dim3(grid, (outs + 255) / 256), 256, 0, ctx->stream>>>((const double*)R, a,
@@ -1829,7 +1856,8 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
       a.nrows = nb;
       a.ncol = nb;
     }
-    const int gsug = grid_for(targs[0]);
+    // float: the split-over-cells product with two CTAs per SM (few rows); float64: as the others
+    const int gsug = sizeof(T) == 4 ? 2 * ctx->num_sms : grid_for(targs[0]);
     const size_t per = (size_t)gsug * nb * nb;
     double *spart, *sred;
     NPC_TRY(ws_get(ctx, "bis.sugpart", sizeof(double) * per * ncombo, (void**)&spart));
