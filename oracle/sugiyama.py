@@ -17,7 +17,23 @@ survey geometry: observer to the grid point).  ``sugiyama_fft`` evaluates every 
 (m1, m2, M) with m1 + m2 + M = 0, in the catalogue's own coordinate frame; no pairing of
 sub-configurations and no rotation of the line of sight onto an axis is used.
 
-The raw estimator is reported: no shot-noise term is subtracted.
+Analytic shot noise (Sec. 5.4, global line of sight; ``analytic_shot_noise``), four terms:
+  i = j = k:        delta_{l1 0} delta_{l2 0} delta_{L 0} S / I33
+  i != j = k (k1):  delta_{l1 L} delta_{l2 0} (2L+1)/I33 H_L(k1)
+  i = k != j (k2):  delta_{l2 L} delta_{l1 0} (2L+1)/I33 H_L(k2)
+  i = j != k:       H N / I33 * sum_m w_m q_{l1 l2 L}(c_i, c_j, c_m) Q_L(k_m) / sum_m w_m
+over the shells m of width dk centred at c_m = (m + 1/2) dk with c_m in [|c_i - c_j| + dk/2,
+c_i + c_j - dk/2], w_m = N_mode(m)/c_m (the mode-count weighting of the compressed estimator's
+analytic shot noise), H_L and Q_L the shell terms of ``oracle.shot`` (global line of sight: both
+<L_L(mu) Re X N^*> - S <L_L(mu)>), and
+  q_{l1 l2 L}(k1, k2, k3) = sum_n (-1)^n cL_l1^n(cos t13) cL_l2^{-n}(cos t23) (l1 l2 L; n -n 0)
+(Lemma 1 and Eq. q_ells) with cos t13 = (k2^2 - k1^2 - k3^2)/(2 k1 k3) and cos t23 = (k1^2 - k2^2 -
+k3^2)/(2 k2 k3) for k1 + k2 + k3 = 0.  Reading: cL_l^n are the Racah-normalised associated Legendre
+functions, y_l^n at azimuth 0, sqrt((l-n)!/(l+n)!) L_l^n for n >= 0 and (-1)^n cL_l^{|n|} for n < 0
+(with the unnormalised L_l^n the closed form misses the ring average whenever l1 != l2 and n != 0).
+Pinned by tests/test_oracle_sugiyama.py: the closed form against a direct quadrature of the ring
+average of sum_m (l1 l2 L; m -m 0) y_l1^{m*}(k1hat) y_l2^{-m*}(k2hat) around k3 (= q L_L(mu3)), and
+the monopole B_000 shot noise against the compressed estimator's analytic B_000 shot noise.
 
 Pinned by tests/test_oracle_sugiyama.py: the explicit (q1, q2) enumeration of the same sum in
 Fourier space (brute force, tiny meshes); the l l 0 multipoles against the Legendre form that the
@@ -211,11 +227,82 @@ def legendre_ll0(spec, meshes, kbins, ell, i33, prs):
     return np.array(out)
 
 
-def bispectrum_sugiyama(spec, data, randoms, kbins, multipoles):
-    """Full oracle measurement: {(l1, l2, L): real (nb, nb) array}, mode counts and scalars."""
+def racah_assoc_legendre(ell, n, x):
+    """cL_l^n(x) = y_l^n at polar cosine x and azimuth 0 (Racah-normalised associated Legendre)."""
+    from math import factorial, sqrt
+
+    an = abs(n)
+    v = sqrt(factorial(ell - an) / factorial(ell + an)) * H.assoc_legendre(ell, an, x)
+    return v if n >= 0 else (-1.0) ** an * v
+
+
+def q_ring(l1, l2, L, k1, k2, k3):
+    """q_{l1 l2 L}(k1, k2, k3) of Lemma 1 (Eq. q_ells) for the triangle k1 + k2 + k3 = 0."""
+    c13 = (k2 * k2 - k1 * k1 - k3 * k3) / (2.0 * k1 * k3)
+    c23 = (k1 * k1 - k2 * k2 - k3 * k3) / (2.0 * k2 * k3)
+    c13, c23 = min(1.0, max(-1.0, c13)), min(1.0, max(-1.0, c23))
+    s = 0.0
+    for n in range(-min(l1, l2), min(l1, l2) + 1):
+        s += (-1.0) ** n * float(racah_assoc_legendre(l1, n, c13)) * float(racah_assoc_legendre(l2, -n, c23)) \
+            * H.wigner3j(l1, l2, L, n, -n, 0)
+    return s
+
+
+def analytic_shot_noise(spec, X0, N0, kbins, multipoles, sc):
+    """Sec. 5.4 analytic shot noise of every multipole on every (k_i, k_j) pair (global line of
+    sight).  Returns {(l1, l2, L): (nb, nb)}."""
+    from . import shot as SH
+
+    kmin, dk, nb = kbins
+    cen = np.array([kmin + (b + 0.5) * dk for b in range(nb)])
+    qb = SH.qgrid(kbins)
+    cq = np.array([(m + 0.5) * dk for m in range(qb[2])])
+    i33, s3 = sc["I33"], sc["S3"]
+    Ls = sorted({L for _, _, L in multipoles})
+    Hk = {L: SH.shell_terms(spec, X0, N0, kbins, L, s3)[0] for L in Ls}
+    Qs = {}
+    for L in Ls:
+        _, Qs[L], nq = SH.shell_terms(spec, X0, N0, qb, L, s3)
+    out = {}
+    for l1, l2, L in multipoles:
+        hN = H.wigner3j(l1, l2, L, 0, 0, 0) * (2 * l1 + 1) * (2 * l2 + 1) * (2 * L + 1)
+        sn = np.zeros((nb, nb))
+        for i in range(nb):
+            for j in range(nb):
+                v = 0.0
+                if l1 == 0 and l2 == 0 and L == 0:
+                    v += s3 / i33
+                if l1 == L and l2 == 0:
+                    v += (2 * L + 1) / i33 * Hk[L][i]
+                if l2 == L and l1 == 0:
+                    v += (2 * L + 1) / i33 * Hk[L][j]
+                lo = abs(cen[i] - cen[j]) + 0.5 * dk
+                hi = cen[i] + cen[j] - 0.5 * dk
+                num = den = 0.0
+                for m in range(qb[2]):
+                    if lo - 1e-9 * dk <= cq[m] <= hi + 1e-9 * dk and nq[m] > 0:
+                        w = nq[m] / cq[m]
+                        num += w * q_ring(l1, l2, L, cen[i], cen[j], cq[m]) * Qs[L][m]
+                        den += w
+                if den > 0:
+                    v += hN / i33 * num / den
+                sn[i, j] = v
+        out[(l1, l2, L)] = sn
+    return out
+
+
+def bispectrum_sugiyama(spec, data, randoms, kbins, multipoles, shot=False):
+    """Full oracle measurement: {(l1, l2, L): real (nb, nb) array} (raw), the analytic shot noise
+    when ``shot``, mode counts and scalars."""
     sc = P.catalog_scalars(data, randoms, spec["box"])
     meshes = P.fkp_meshes(spec, data, randoms, sc)
     res = sugiyama_fft(spec, meshes, kbins, multipoles, sc["I33"])
-    return dict(B={k: np.real(v) for k, v in res.items()},
-                imag=max(float(np.max(np.abs(np.imag(v)))) for v in res.values()),
-                counts=mode_counts(spec, kbins), scalars=sc)
+    out = dict(B={k: np.real(v) for k, v in res.items()},
+               imag=max(float(np.max(np.abs(np.imag(v)))) for v in res.values()),
+               counts=mode_counts(spec, kbins), scalars=sc)
+    if shot:
+        nmeshes = P.fkp_meshes(spec, data, randoms, sc, weight_power=2)
+        X0, _ = spectra(spec, meshes, [])
+        N0, _ = spectra(spec, nmeshes, [])
+        out["shot"] = analytic_shot_noise(spec, X0, N0, kbins, multipoles, sc)
+    return out

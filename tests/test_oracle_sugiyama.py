@@ -126,3 +126,58 @@ def test_wigner_coefficients_of_the_l0l_collapse():
     for ell in range(5):
         hN = H.wigner3j(ell, 0, ell, 0, 0, 0) * (2 * ell + 1) ** 2
         assert abs(hN * H.wigner3j(ell, 0, ell, 0, 0, 0) - (2 * ell + 1)) < 1e-12
+
+
+def _ring_quadrature(l1, l2, L, k1, k2, k3, u3, ng=2048):
+    """Mean over the ring of k1 around k3 (k1 + k2 + k3 = 0) of
+    sum_m (l1 l2 L; m -m 0) y_l1^{m*}(k1hat) y_l2^{-m*}(k2hat), by direct quadrature."""
+    u3 = u3 / np.linalg.norm(u3)
+    c13 = (k2 * k2 - k1 * k1 - k3 * k3) / (2 * k1 * k3)
+    a = np.array([1.0, 0.0, 0.0]) if abs(u3[0]) < 0.9 else np.array([0.0, 1.0, 0.0])
+    e1 = a - a.dot(u3) * u3
+    e1 /= np.linalg.norm(e1)
+    e2 = np.cross(u3, e1)
+    g = np.arange(ng) * 2 * np.pi / ng
+    kv1 = k1 * (c13 * u3[None, :] + np.sqrt(1 - c13 * c13) * (np.cos(g)[:, None] * e1 + np.sin(g)[:, None] * e2))
+    kv2 = -kv1 - k3 * u3[None, :]
+    tot = 0.0 + 0.0j
+    for m in range(-min(l1, l2), min(l1, l2) + 1):
+        w = H.wigner3j(l1, l2, L, m, -m, 0)
+        tot += w * np.mean(np.conj(H.ylm_racah(l1, m, kv1)) * np.conj(H.ylm_racah(l2, -m, kv2)))
+    return tot
+
+
+@pytest.mark.parametrize("mp", [(0, 0, 0), (2, 0, 2), (1, 1, 2), (2, 2, 2), (3, 1, 2), (4, 2, 2), (1, 3, 4),
+                                (2, 4, 6), (4, 4, 8)])
+def test_lemma1_closed_form_against_ring_quadrature(mp):
+    """The ring average of the m-sum around k3 equals q_{l1 l2 L}(k1, k2, k3) L_L(mu3) (Lemma 1 with
+    the Racah-normalised associated Legendre functions)."""
+    rng = np.random.default_rng(7)
+    done = 0
+    while done < 4:
+        k1, k2, k3 = rng.uniform(0.04, 0.12, 3)
+        if not abs(k1 - k2) < k3 < k1 + k2:
+            continue
+        u3 = rng.normal(size=3)
+        ring = _ring_quadrature(*mp, k1, k2, k3, u3)
+        pred = S.q_ring(*mp, k1, k2, k3) * H.legendre(mp[2], u3[2] / np.linalg.norm(u3))
+        assert abs(ring.imag) < 1e-12 and abs(ring.real - pred) < 1e-12, (mp, ring, pred)
+        done += 1
+
+
+def test_monopole_shot_noise_equals_the_compressed_one(cat):
+    """B_000: the TripoSH analytic shot noise (S + H_0(k1) + H_0(k2) + <Q_0>)/I33 equals the
+    compressed estimator's analytic B_000 shot noise (g_0 = 1)."""
+    from oracle import shot as SH
+
+    spec, sc, meshes = _setup(cat, (0.0, 0.0, 1.0))
+    nmeshes = P.fkp_meshes(spec, cat, None, sc, weight_power=2)
+    X0 = P.fields_plain(spec, meshes, [0])[0][0]
+    N0 = P.fields_plain(spec, nmeshes, [0])[0][0]
+    sn = S.analytic_shot_noise(spec, X0, N0, KB, [(0, 0, 0), (2, 0, 2)], sc)
+    prs = B.pairs(KB)
+    _, bb, _ = SH.analytic_shot_noise(spec, X0, N0, KB, B.triangles(KB), prs, sc, (0,), (0,))
+    got = np.array([sn[(0, 0, 0)][i, j] for i, j in prs])
+    np.testing.assert_allclose(got, bb[0], rtol=1e-12)
+    # symmetric in (k1, k2) for l1 = l2
+    np.testing.assert_allclose(sn[(0, 0, 0)], sn[(0, 0, 0)].T, rtol=1e-12)
