@@ -225,7 +225,7 @@ npc_status npc_bispectrum_triangles(const npc_kbins* bins, int32_t* tri, int64_t
                                     int64_t* ntri);
 
 /* Sugiyama TripoSH bispectrum multipoles B_{l1 l2 L}(k1, k2) (Sec. 4.2, Eq. sugi_estimator with the
- * fields of Eq. F_and_G), raw estimator (no shot noise subtracted), global line of sight
+ * fields of Eq. F_and_G), global line of sight
  * (mesh->periodic = 1, or survey geometry with randoms and mesh->los = 1):
  *   B(i, j) = H N / (I33 N_i N_j) sum_{m1 m2 M} (l1 l2 L; m1 m2 M) <F_l1^m1(x; k_i) F_l2^m2(x; k_j) G_L^M(x)>_x
  * with F_l^m(x; k) = sum_{q in bin k} e^{iqx} y_l^{m*}(qhat) X(q), H = (l1 l2 L; 0 0 0),
@@ -238,15 +238,23 @@ npc_status npc_bispectrum_triangles(const npc_kbins* bins, int32_t* tri, int64_t
  *   l1 + l2 even (the plane-parallel symmetry about the line of sight); else NPC_ERR_INVALID_ARG.  Bins and mesh limits as npc_bispectrum (at most
  *   24 bins, largest bin edge <= k_N/2).  Survey geometry with the line of sight to each grid point
  *   (mesh->los = 0): NPC_ERR_UNSUPPORTED.
+ * shot: 0 raw estimates; 1 subtracts the analytic shot noise of Sec. 5.4 and reports it:
+ *   delta_{l1 0} delta_{l2 0} delta_{L 0} S/I33 (three legs from one object), delta_{l1 L} delta_{l2 0}
+ *   (2L+1) H_L(k1)/I33 and delta_{l2 L} delta_{l1 0} (2L+1) H_L(k2)/I33 (two), and for legs 1, 2 from
+ *   one object the thin-shell ring average of Lemma 1, H N/I33 sum_k3 w q_{l1 l2 L}(k1, k2, k3)
+ *   Q_L(k3) / sum_k3 w over the shells of width dk that close the pair (w = N_mode/k3), with
+ *   H_L = Q_L = <L_L(mu) Re X N^*> - S <L_L(mu)> on the k-bins and the k3 shells (N the w^2 field)
+ *   and q built from Racah-normalised associated Legendre functions.
  * Output `out` (float64, host or device as out_on_device), length npc_bispectrum_sugiyama_len():
- *   [nmult][nbins][nbins] B (k1 = bin i the row, k2 = bin j the column), [nbins] N_modes,
- *   then 8 scalars as in npc_catalog_scalars.
- * Errors as npc_bispectrum. */
+ *   [nmult][nbins][nbins] B (k1 = bin i the row, k2 = bin j the column; raw minus shot noise),
+ *   [nmult][nbins][nbins] shot noise (zeros when shot = 0), [nbins] N_modes, then 8 scalars as in
+ *   npc_catalog_scalars.
+ * Errors as npc_bispectrum; shot other than 0 or 1: NPC_ERR_INVALID_ARG. */
 npc_status npc_bispectrum_sugiyama(npc_ctx* ctx, const npc_mesh_spec* mesh, const npc_catalog* data,
                                    const npc_catalog* randoms, const npc_kbins* bins, int32_t nmult,
-                                   const int32_t* multipoles, npc_precision prec, double* out,
-                                   int32_t out_on_device);
-/* Output length of npc_bispectrum_sugiyama: nmult * nbins^2 + nbins + 8 (-1 for bad arguments). */
+                                   const int32_t* multipoles, int32_t shot, npc_precision prec,
+                                   double* out, int32_t out_on_device);
+/* Output length of npc_bispectrum_sugiyama: 2 nmult nbins^2 + nbins + 8 (-1 for bad arguments). */
 int64_t npc_bispectrum_sugiyama_len(const npc_kbins* bins, int32_t nmult);
 
 /* Batches of measurements --------------------------------------------------------------------------

@@ -249,12 +249,13 @@ def bispectrum(data, n, box, kbins, scoc_ells=(0, 2), tripo_ells=(0, 2), shot=Tr
     return unpack_bispectrum(buf, kbins, scoc_ells, tripo_ells)
 
 
-def bispectrum_sugiyama(data, n, box, kbins, multipoles=((0, 0, 0), (2, 0, 2)), assign=3, interlace=1,
+def bispectrum_sugiyama(data, n, box, kbins, multipoles=((0, 0, 0), (2, 0, 2)), shot=False, assign=3, interlace=1,
                         los_dir=(0.0, 0.0, 1.0), precision="mixed", origin=(0.0, 0.0, 0.0), device=0, out=None,
                         randoms=None):
-    """Sugiyama TripoSH multipoles B_{l1 l2 L}(k1, k2) for every bin pair (raw, no shot noise),
-    global line of sight ``los_dir``; periodic box, or survey geometry with ``randoms``.
-    Returns {"B": {(l1, l2, L): (nb, nb) array, row k1, column k2}, "nmodes", "scalars"}."""
+    """Sugiyama TripoSH multipoles B_{l1 l2 L}(k1, k2) for every bin pair, global line of sight
+    ``los_dir``; periodic box, or survey geometry with ``randoms``.  shot: subtract the analytic
+    shot noise.  Returns {"B": {(l1, l2, L): (nb, nb) array, row k1, column k2}, "shot": {...},
+    "nmodes", "scalars"}."""
     keep = _Keep()
     spec = make_spec(n, box, origin, assign, interlace, 1 if randoms is None else 0, los_dir, (0.0, 0.0, 0.0))
     kb = B.npc_kbins(float(kbins[0]), float(kbins[1]), int(kbins[2]))
@@ -267,22 +268,23 @@ def bispectrum_sugiyama(data, n, box, kbins, multipoles=((0, 0, 0), (2, 0, 2)), 
     ctx = context(device)
     if out is not None:
         B.check(B.npc_bispectrum_sugiyama(ctx, C.byref(spec), C.byref(d), rp, C.byref(kb), len(mps), arr,
-                                          _prec(precision), C.c_void_p(out.data_ptr()), 1), ctx)
+                                          int(shot), _prec(precision), C.c_void_p(out.data_ptr()), 1), ctx)
         return out
     buf = np.zeros(max(int(length), 1))
     B.check(B.npc_bispectrum_sugiyama(ctx, C.byref(spec), C.byref(d), rp, C.byref(kb), len(mps), arr,
-                                      _prec(precision), buf.ctypes.data_as(C.c_void_p), 0), ctx)
+                                      int(shot), _prec(precision), buf.ctypes.data_as(C.c_void_p), 0), ctx)
     return unpack_sugiyama(buf, kbins, mps)
 
 
 def unpack_sugiyama(buf, kbins, multipoles):
     nb = int(kbins[2])
     buf = np.asarray(buf)
-    res = {"B": {}}
+    res = {"B": {}, "shot": {}}
     o = 0
-    for mp in multipoles:
-        res["B"][tuple(mp)] = buf[o:o + nb * nb].reshape(nb, nb).copy()
-        o += nb * nb
+    for key in ("B", "shot"):
+        for mp in multipoles:
+            res[key][tuple(mp)] = buf[o:o + nb * nb].reshape(nb, nb).copy()
+            o += nb * nb
     res["nmodes"] = buf[o:o + nb].copy()
     o += nb
     res["scalars"] = dict(zip(("alpha", "I22", "I33", "N0", "S3", "sum_wg", "sum_wr", "sum_w2"), buf[o:o + 8]))

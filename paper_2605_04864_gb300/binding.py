@@ -75,8 +75,8 @@ _sig = {
                                         _P(C.c_int64), _P(C.c_int64)]),
     "npc_bispectrum_triangles": (C.c_int, [_P(npc_kbins), _P(C.c_int32), C.c_int64, _P(C.c_int64)]),
     "npc_bispectrum_sugiyama": (C.c_int, [C.c_void_p, _P(npc_mesh_spec), _P(npc_catalog), _P(npc_catalog),
-                                          _P(npc_kbins), C.c_int32, _P(C.c_int32), C.c_int, C.c_void_p,
-                                          C.c_int32]),
+                                          _P(npc_kbins), C.c_int32, _P(C.c_int32), C.c_int32, C.c_int,
+                                          C.c_void_p, C.c_int32]),
     "npc_bispectrum_sugiyama_len": (C.c_int64, [_P(npc_kbins), C.c_int32]),
     "npc_catalog_scalars_noalloc": (C.c_int, [_P(npc_catalog), _P(npc_catalog), C.c_double, C.c_void_p,
                                               C.c_void_p, C.c_char_p, C.c_size_t]),

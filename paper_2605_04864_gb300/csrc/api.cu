@@ -659,12 +659,12 @@ npc_status npc_bispectrum_triangles(const npc_kbins* bins, int32_t* tri, int64_t
 int64_t npc_bispectrum_sugiyama_len(const npc_kbins* bins, int32_t nmult) {
   if (!bins || bins->nbins < 1 || bins->nbins > 24 || nmult < 1 || nmult > NPC_SUGI_MAX) return -1;
   const int64_t nb = bins->nbins;
-  return (int64_t)nmult * nb * nb + nb + 8;
+  return 2 * (int64_t)nmult * nb * nb + nb + 8;
 }
 
 npc_status npc_bispectrum_sugiyama(npc_ctx* ctx, const npc_mesh_spec* mesh, const npc_catalog* data,
                                    const npc_catalog* randoms, const npc_kbins* bins, int32_t nmult,
-                                   const int32_t* multipoles, npc_precision prec, double* out,
+                                   const int32_t* multipoles, int32_t shot, npc_precision prec, double* out,
                                    int32_t out_on_device) {
   if (!ctx) return NPC_ERR_INVALID_ARG;
   begin_call(ctx);
@@ -687,6 +687,7 @@ npc_status npc_bispectrum_sugiyama(npc_ctx* ctx, const npc_mesh_spec* mesh, cons
     req.L[e] = L;
   }
   if (prec != NPC_PREC_FP64 && prec != NPC_PREC_MIXED) return set_err(ctx, NPC_ERR_INVALID_ARG, "bad precision");
+  if (shot != 0 && shot != 1) return set_err(ctx, NPC_ERR_INVALID_ARG, "shot must be 0 or 1");
   if (mesh->periodic) {
     if (randoms) return set_err(ctx, NPC_ERR_INVALID_ARG, "periodic box takes no randoms");
   } else {
@@ -721,7 +722,8 @@ npc_status npc_bispectrum_sugiyama(npc_ctx* ctx, const npc_mesh_spec* mesh, cons
   NPC_TRY(stage_mark(ctx, "scalars"));
   double* dev_out = out;
   if (!out_on_device) NPC_TRY(ws_get(ctx, "bis.out", sizeof(double) * out_len, (void**)&dev_out));
-  NPC_TRY(run_bispectrum_sugiyama(ctx, *mesh, *bins, req, prec, d, randoms ? &r : nullptr, sc, dev_out, out_len));
+  NPC_TRY(run_bispectrum_sugiyama(ctx, *mesh, *bins, req, shot, prec, d, randoms ? &r : nullptr, sc, dev_out,
+                                  out_len));
   NPC_TRY(finish_output(ctx, dev_out, out, out_len, out_on_device));
   NPC_TRY(stage_mark(ctx, "download"));
   return end_call(ctx);

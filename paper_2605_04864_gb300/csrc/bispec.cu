@@ -299,8 +299,10 @@ __device__ __forceinline__ void seg_accumulate(int lane, int bin, const T (&vals
 //    on two bin sets (the k-bins and the unit-width k3 shells), modes with |ky|, kz <= KY.
 // ------------------------------------------------------------------------------------------
 constexpr int NCROSS = 4;
+// with the TripoSH shot noise: also w L_l Re X_0 N_0^*, w L_l for l = 4, 6, 8 at 4 + 2 (l/2 - 2) + {0, 1}
+constexpr int NCROSS_S = 10;
 
-template <typename T, int N>
+template <typename T, int N, int NC = NCROSS>
 __global__ void __launch_bounds__(BT)
 k_bin_cross(const cplx<T>* __restrict__ X0, const cplx<T>* __restrict__ XN, int KZ, int KY, double lx, double ly,
             double lz, const int16_t* __restrict__ tab_m, int nbm, const int16_t* __restrict__ tab_q, int nbq,
@@ -308,8 +310,8 @@ k_bin_cross(const cplx<T>* __restrict__ X0, const cplx<T>* __restrict__ XN, int 
   using C = cplx<T>;
   constexpr int NW = BT / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double* pm = part_m + ((size_t)blockIdx.x * NW + warp) * nbm * NCROSS;
-  double* pq = part_q + ((size_t)blockIdx.x * NW + warp) * nbq * NCROSS;
+  double* pm = part_m + ((size_t)blockIdx.x * NW + warp) * nbm * NC;
+  double* pq = part_q + ((size_t)blockIdx.x * NW + warp) * nbq * NC;
   const int nyr = 2 * KY + 1;
   const int nrows = (KY + 1) * nyr;
   const size_t fstride = (size_t)KZ * N * N;
@@ -323,7 +325,9 @@ k_bin_cross(const cplx<T>* __restrict__ X0, const cplx<T>* __restrict__ XN, int 
       const int i = j < N / 2 ? j : j - N;
       const int n2 = i * i + jy * jy + kz * kz;
       int bm = -1, bq = -1;
-      T vals[NCROSS] = {T(0), T(0), T(0), T(0)};
+      T vals[NC];
+#pragma unroll
+      for (int q = 0; q < NC; ++q) vals[q] = T(0);
       if (j < N && n2 > 0 && n2 <= n2max && i != -N / 2 && jy != -N / 2) {
         bm = tab_m[n2];
         bq = tab_q[n2];
@@ -338,15 +342,30 @@ k_bin_cross(const cplx<T>* __restrict__ X0, const cplx<T>* __restrict__ XN, int 
         vals[1] = w * l2 * cr;
         vals[2] = w;
         vals[3] = w * l2;
-      }
-      T vm[NCROSS], vq[NCROSS];
+        if constexpr (NC > NCROSS) {
+          // L_3 .. L_8 by the three-term recurrence (l+1) L_{l+1} = (2l+1) mu L_l - l L_{l-1}
+          T lm1 = mu, lc = l2;
 #pragma unroll
-      for (int s = 0; s < NCROSS; ++s) {
+          for (int l = 2; l < 8; ++l) {
+            const T ln = (T(2 * l + 1) * mu * lc - T(l) * lm1) / T(l + 1);
+            lm1 = lc;
+            lc = ln;
+            if (l + 1 == 4 || l + 1 == 6 || l + 1 == 8) {
+              const int o = 4 + 2 * ((l + 1) / 2 - 2);
+              vals[o] = w * lc * cr;
+              vals[o + 1] = w * lc;
+            }
+          }
+        }
+      }
+      T vm[NC], vq[NC];
+#pragma unroll
+      for (int s = 0; s < NC; ++s) {
         vm[s] = bm >= 0 ? vals[s] : T(0);
         vq[s] = bq >= 0 ? vals[s] : T(0);
       }
-      seg_accumulate<T, NCROSS>(lane, bm, vm, pm);
-      seg_accumulate<T, NCROSS>(lane, bq, vq, pq);
+      seg_accumulate<T, NC>(lane, bm, vm, pm);
+      seg_accumulate<T, NC>(lane, bq, vq, pq);
     }
   }
 }
@@ -1044,23 +1063,80 @@ __global__ void k_bispec_finalize(const int* __restrict__ tri, const int* __rest
   if (tid < 8) out[oSC + tid] = sc[tid];
 }
 
+// Racah-normalised associated Legendre function cL_l^n(x): y_l^n at polar cosine x, azimuth 0
+// (for n < 0, (-1)^n cL_l^{|n|})
+__device__ double racah_assoc(int l, int n, double x) {
+  double re, im;
+  const int an = n < 0 ? -n : n;
+  ylm_frame<double>(l, an, sqrt(fmax(0.0, 1.0 - x * x)), 0.0, x, re, im);
+  return (n < 0 && (an & 1)) ? -re : re;
+}
+
+// per multipole: l1, l2, L, H N, then (l1 l2 L; n -n 0) for n = -4 .. 4
+constexpr int SUGI_DESC = 13;
+
 // TripoSH multipoles from the per-combination sums red[c][i][j] = sum_x A_i(x) G(x) C_j(x) (A, C the
-// parts of F_l1^m and F_l2^m of bins i and j): B_e(i, j) = sum_c coef[e][c] red[c][i][j] /
-// (I33 N_i N_j ncell), then the mode counts and the scalars.
+// parts of F_l1^m and F_l2^m of bins i and j): raw(i, j) = sum_c coef[e][c] red[c][i][j] /
+// (I33 N_i N_j ncell).  shot: the analytic shot noise of Sec. 5.4, global line of sight,
+//   delta_{l1 0} delta_{l2 0} delta_{L 0} S + delta_{l1 L} delta_{l2 0} (2L+1) H_L(k_i)
+//   + delta_{l2 L} delta_{l1 0} (2L+1) H_L(k_j) + H N sum_m w_m q(c_i, c_j, c_m) Q_L(m) / sum_m w_m,
+// all over I33, with H_L, Q_L = (sum w L_L Re X N^* - S sum w L_L) / N_mode on the k-bins and on the
+// k3 shells of width dk, w_m = N_mode(m)/c_m over the shells closing the pair, and Lemma 1's
+//   q(k1, k2, k3) = sum_n (-1)^n cL_l1^n(cos t13) cL_l2^{-n}(cos t23) (l1 l2 L; n -n 0).
+// Output: [nmult][nb][nb] raw - shot, [nmult][nb][nb] shot, the mode counts, the scalars.
 __global__ void k_sugi_finalize(const double* __restrict__ red, int ncombo, const double* __restrict__ coef,
-                                int nmult, int nb, const double* __restrict__ cross_m, int ncs,
+                                const double* __restrict__ desc, int nmult, int nb, const double* __restrict__ cross_m,
+                                const double* __restrict__ cross_q, int nq, int ncs, int shot, double dk, double kmin,
                                 const double* __restrict__ sc, double ncell, double* __restrict__ out) {
   const int nn = nb * nb;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthreads = gridDim.x * blockDim.x;
+  const double i33 = sc[SC_I33], s3 = sc[SC_S3];
+  auto shell = [&](const double* cr, int L, int b) {
+    const double* c = cr + (size_t)b * ncs;
+    const double n = c[2];
+    if (n <= 0) return 0.0;
+    const int ix = L == 0 ? 0 : (L == 2 ? 1 : 4 + 2 * (L / 2 - 2));
+    const int iw = L == 0 ? 2 : (L == 2 ? 3 : ix + 1);
+    return (c[ix] - s3 * c[iw]) / n;
+  };
   for (int o = tid; o < nmult * nn; o += nthreads) {
     const int e = o / nn, ij = o % nn, i = ij / nb, j = ij % nb;
     const double ni = cross_m[(size_t)i * ncs + 2], nj = cross_m[(size_t)j * ncs + 2];
     double s = 0.0;
     for (int c = 0; c < ncombo; ++c) s += coef[(size_t)e * ncombo + c] * red[(size_t)c * nn + ij];
-    out[o] = (ni > 0 && nj > 0) ? s / (sc[SC_I33] * ni * nj * ncell) : 0.0;
+    const double raw = (ni > 0 && nj > 0) ? s / (i33 * ni * nj * ncell) : 0.0;
+    double sn = 0.0;
+    if (shot && ni > 0 && nj > 0) {
+      const double* d = desc + (size_t)e * SUGI_DESC;
+      const int l1 = (int)d[0], l2 = (int)d[1], L = (int)d[2];
+      double v = 0.0;
+      if (l1 == 0 && l2 == 0 && L == 0) v += s3;
+      if (l1 == L && l2 == 0) v += (2 * L + 1) * shell(cross_m, L, i);
+      if (l2 == L && l1 == 0) v += (2 * L + 1) * shell(cross_m, L, j);
+      const double ci = kmin + (i + 0.5) * dk, cj = kmin + (j + 0.5) * dk;
+      const double lo = fabs(ci - cj) + 0.5 * dk, hi = ci + cj - 0.5 * dk;
+      const int nmin = l1 < l2 ? l1 : l2;
+      double num = 0.0, den = 0.0;
+      for (int m = 0; m < nq; ++m) {
+        const double cm = (m + 0.5) * dk;
+        const double nm = cross_q[(size_t)m * ncs + 2];
+        if (cm < lo - 1e-9 * dk || cm > hi + 1e-9 * dk || nm <= 0) continue;
+        const double c13 = fmin(1.0, fmax(-1.0, (cj * cj - ci * ci - cm * cm) / (2.0 * ci * cm)));
+        const double c23 = fmin(1.0, fmax(-1.0, (ci * ci - cj * cj - cm * cm) / (2.0 * cj * cm)));
+        double q = 0.0;
+        for (int n = -nmin; n <= nmin; ++n)
+          q += ((n & 1) ? -1.0 : 1.0) * racah_assoc(l1, n, c13) * racah_assoc(l2, -n, c23) * d[4 + n + 4];
+        num += nm / cm * q * shell(cross_q, L, m);
+        den += nm / cm;
+      }
+      if (den > 0) v += d[3] * num / den;
+      sn = v / i33;
+    }
+    out[o] = raw - sn;
+    out[(size_t)nmult * nn + o] = sn;
   }
-  for (int b = tid; b < nb; b += nthreads) out[(size_t)nmult * nn + b] = cross_m[(size_t)b * ncs + 2];
-  if (tid < 8) out[(size_t)nmult * nn + nb + tid] = sc[tid];
+  for (int b = tid; b < nb; b += nthreads) out[(size_t)2 * nmult * nn + b] = cross_m[(size_t)b * ncs + 2];
+  if (tid < 8) out[(size_t)2 * nmult * nn + nb + tid] = sc[tid];
 }
 
 // reduce per-warp cross partials into [bin][NCROSS] in a fixed order
@@ -1391,7 +1467,7 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
   NPC_TRY(get_bin_table(ctx, N, m.box, kb, &tab_m, 2));
   npc_kbins qb{0.0, kb.dk, nq};
   NPC_TRY(get_bin_table(ctx, N, m.box, qb, &tab_q, 3));
-  const int nsum_c = yam ? NCS : NCROSS;   // shell sums per bin
+  const int nsum_c = yam ? NCS : (sugi ? NCROSS_S : NCROSS);   // shell sums per bin
   double *cross_m, *cross_q, *mom = nullptr;
   NPC_TRY(ws_get(ctx, "bis.cross", sizeof(double) * nsum_c * (nb + nq) + sizeof(double) * 8, (void**)&cross_m));
   cross_q = cross_m + (size_t)nsum_c * nb;
@@ -1409,6 +1485,9 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
       const C* N2 = shot ? X + 3 * xfs : X + 2 * xfs;
       k_bin_cross_survey<T, N><<<grid, BT, 0, ctx->stream>>>(X, X + 2 * xfs, XN, N2, K2, ylm_norm_table(), tab_m, nb,
                                                             tab_q, nq, n2cap, part, part + np * NCS * nb);
+    } else if (sugi) {
+      k_bin_cross<T, N, NCROSS_S><<<grid, BT, 0, ctx->stream>>>(X, XN, KZ, K2, l3[0], l3[1], l3[2], tab_m, nb, tab_q,
+                                                               nq, n2cap, part, part + np * NCROSS_S * nb);
     } else {
       k_bin_cross<T, N><<<grid, BT, 0, ctx->stream>>>(X, XN, KZ, K2, l3[0], l3[1], l3[2], tab_m, nb, tab_q, nq, n2cap,
                                                      part, part + np * NCROSS * nb);
@@ -1624,7 +1703,7 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
   };
   std::vector<SCombo> combos;
   std::vector<double> scoef;
-  size_t t_spij = 0, t_srow = 0, t_scoef = 0;
+  size_t t_spij = 0, t_srow = 0, t_scoef = 0, t_sdesc = 0;
   if (sugi) {
     auto combo_of = [&](int l1, int l2, int mm, int part) {
       for (size_t c = 0; c < combos.size(); ++c)
@@ -1654,6 +1733,17 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
     t_spij = push_bytes(sp.data(), sizeof(int) * nb);
     t_srow = push_bytes(sp.data(), sizeof(int) * nb);
     t_scoef = push_bytes(scoef.data(), sizeof(double) * scoef.size());
+    std::vector<double> sdesc((size_t)sug->nmult * SUGI_DESC, 0.0);
+    for (int e = 0; e < sug->nmult; ++e) {
+      const int l1 = sug->l1[e], l2 = sug->l2[e], L = sug->L[e];
+      double* dd = sdesc.data() + (size_t)e * SUGI_DESC;
+      dd[0] = l1;
+      dd[1] = l2;
+      dd[2] = L;
+      dd[3] = wigner3j_host(l1, l2, L, 0, 0, 0) * (2 * l1 + 1) * (2 * l2 + 1) * (2 * L + 1);
+      for (int n = -4; n <= 4; ++n) dd[4 + n + 4] = wigner3j_host(l1, l2, L, n, -n, 0);
+    }
+    t_sdesc = push_bytes(sdesc.data(), sizeof(double) * sdesc.size());
   }
   char* dtab;
   NPC_TRY(ws_table(ctx, need_nt ? "bis.tables.nt" : "bis.tables", tables, tables.data(), tables.size(),
@@ -1869,8 +1959,10 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
                                                                             sred + (size_t)c * nb * nb);
       NPC_LAUNCH(ctx);
     }
-    k_sugi_finalize<<<std::max(1, (sug->nmult * nb * nb + 127) / 128), 128, 0, ctx->stream>>>(
-        sred, ncombo, (const double*)(dtab + t_scoef), sug->nmult, nb, cross_m, nsum_c, sc, (double)ncs, dev_out);
+    // 32-thread blocks: the shot-noise sums are float64 work, spread over many SMs
+    k_sugi_finalize<<<std::max(1, (sug->nmult * nb * nb + 31) / 32), 32, 0, ctx->stream>>>(
+        sred, ncombo, (const double*)(dtab + t_scoef), (const double*)(dtab + t_sdesc), sug->nmult, nb, cross_m,
+        cross_q, nq, nsum_c, shot ? 1 : 0, kb.dk, kb.kmin, sc, (double)ncs, dev_out);
     NPC_LAUNCH(ctx);
     NPC_TRY(stage_mark(ctx, "finalize"));
     (void)out_len;
@@ -2000,10 +2092,10 @@ npc_status run_bispectrum(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins&
 }
 
 npc_status run_bispectrum_sugiyama(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb, const SugiReq& req,
-                                   int prec, const DevCatalog& d, const DevCatalog* r, double* sc, double* out,
-                                   int64_t len) {
-  if (prec == NPC_PREC_FP64) return bispec_dispatch<double>(ctx, m, kb, 1, 0, 0, d, r, sc, out, len, &req);
-  return bispec_dispatch<float>(ctx, m, kb, 1, 0, 0, d, r, sc, out, len, &req);
+                                   int shot, int prec, const DevCatalog& d, const DevCatalog* r, double* sc,
+                                   double* out, int64_t len) {
+  if (prec == NPC_PREC_FP64) return bispec_dispatch<double>(ctx, m, kb, 1, 0, shot, d, r, sc, out, len, &req);
+  return bispec_dispatch<float>(ctx, m, kb, 1, 0, shot, d, r, sc, out, len, &req);
 }
 
 int64_t bispec_counts(const npc_kbins& kb, int64_t* ntri, int64_t* npair) {

@@ -317,13 +317,14 @@ npc_status run_bispectrum(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins&
 int64_t bispec_counts(const npc_kbins& kb, int64_t* ntri, int64_t* npair);
 
 // Sugiyama TripoSH multipoles B_{l1 l2 L} requested from the bispectrum pipeline (global line of
-// sight): output [nmult][nb][nb], then the mode count of every bin, then the SC_COUNT scalars
+// sight): output [nmult][nb][nb] estimate, [nmult][nb][nb] shot noise, the mode count of every
+// bin, then 8 scalars
 constexpr int NPC_SUGI_MAX = 16;
 struct SugiReq {
   int nmult;
   int l1[NPC_SUGI_MAX], l2[NPC_SUGI_MAX], L[NPC_SUGI_MAX];
 };
 npc_status run_bispectrum_sugiyama(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb, const SugiReq& req,
-                                   int prec, const DevCatalog& d, const DevCatalog* r, double* sc, double* out,
-                                   int64_t len);
+                                   int shot, int prec, const DevCatalog& d, const DevCatalog* r, double* sc,
+                                   double* out, int64_t len);
 npc_status bispec_triangles(const npc_kbins& kb, int32_t* tri, int64_t cap, int64_t* ntri);

@@ -49,7 +49,7 @@ def test_host_only_calls():
     assert B.npc_power_out_len(C.byref(kb), 1, (1 << 16) | (1 << 18)) == 5 * 20 + 8   # P_22, P_44
     assert B.npc_power_out_len(C.byref(kb), 1, 1 << 19) == 0
     kb19 = B.npc_kbins(0.01, 0.01, 19)
-    assert B.npc_bispectrum_sugiyama_len(C.byref(kb19), 3) == 3 * 19 * 19 + 19 + 8
+    assert B.npc_bispectrum_sugiyama_len(C.byref(kb19), 3) == 2 * 3 * 19 * 19 + 19 + 8
     assert B.npc_bispectrum_sugiyama_len(C.byref(kb19), 0) == -1
     kb25 = B.npc_kbins(0.01, 0.01, 25)
     assert B.npc_bispectrum_sugiyama_len(C.byref(kb25), 1) == -1   # at most 24 bins

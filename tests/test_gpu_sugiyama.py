@@ -83,16 +83,37 @@ def test_survey_geometry_global_line_of_sight(api):
     _check(res, orc, cnt, mps, 1e-10)
 
 
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 1e-4)])
+def test_analytic_shot_noise(api, prec, tol):
+    """Sec. 5.4 analytic shot noise (S, H_L on k1 and k2, Lemma 1's ring average over the k3 shells)
+    against the oracle; the estimate is the raw sum minus it."""
+    cat = make_periodic_catalog(20000, 300.0, 32, seed=93)
+    kb = (0.02, 0.02, 5)
+    mps = [(0, 0, 0), (2, 0, 2), (0, 2, 2), (1, 1, 2), (2, 2, 2), (3, 1, 2), (4, 2, 2), (4, 4, 8)]
+    res = api.bispectrum_sugiyama(cat, n=32, box=300.0, kbins=kb, multipoles=mps, shot=True, los_dir=TILT,
+                                  precision=prec)
+    spec = _spec(32, 300.0, TILT)
+    orc = OS.bispectrum_sugiyama(spec, cat, None, kb, mps, shot=True)
+    scale = np.abs(orc["B"][(0, 0, 0)]) + np.abs(orc["shot"][(0, 0, 0)])
+    for mp in mps:
+        e = np.abs(res["shot"][mp] - orc["shot"][mp]) / np.maximum(np.abs(orc["shot"][mp]), scale)
+        assert np.max(e) < tol, ("shot", mp, np.max(e))
+        e = np.abs(res["B"][mp] + res["shot"][mp] - orc["B"][mp]) / np.maximum(np.abs(orc["B"][mp]), scale)
+        assert np.max(e) < tol, ("raw", mp, np.max(e))
+
+
 def test_monopole_matches_the_compressed_estimator(api):
     """B_000 of the two estimators coincide (Sec. 6): the library's two paths agree."""
     cat = make_periodic_catalog(20000, 300.0, 32, seed=87)
     kb = (0.02, 0.02, 5)
-    sug = api.bispectrum_sugiyama(cat, n=32, box=300.0, kbins=kb, multipoles=[(0, 0, 0)], precision="fp64")
-    comp = api.bispectrum(cat, n=32, box=300.0, kbins=kb, scoc_ells=(0,), tripo_ells=(0,), shot=False,
+    sug = api.bispectrum_sugiyama(cat, n=32, box=300.0, kbins=kb, multipoles=[(0, 0, 0)], shot=True,
+                                  precision="fp64")
+    comp = api.bispectrum(cat, n=32, box=300.0, kbins=kb, scoc_ells=(0,), tripo_ells=(0,), shot=True,
                           precision="fp64")
     prs = [(i, j) for i in range(5) for j in range(i, 5)]
-    got = np.array([sug["B"][(0, 0, 0)][i, j] for i, j in prs])
-    np.testing.assert_allclose(got, comp["BB"][0], rtol=1e-10, atol=1e-12 * np.max(np.abs(got)))
+    for key, ckey in (("B", "BB"), ("shot", "shot_BB")):
+        got = np.array([sug[key][(0, 0, 0)][i, j] for i, j in prs])
+        np.testing.assert_allclose(got, comp[ckey][0], rtol=1e-10, atol=1e-12 * np.max(np.abs(got)))
 
 
 def test_rejects(api):
@@ -104,6 +125,8 @@ def test_rejects(api):
         api.bispectrum_sugiyama(cat, n=32, box=300.0, kbins=kb, multipoles=[(1, 0, 1)])
     with pytest.raises(RuntimeError):   # l above 4
         api.bispectrum_sugiyama(cat, n=32, box=300.0, kbins=kb, multipoles=[(5, 5, 0)])
+    with pytest.raises(RuntimeError):   # the FFT-method shot noise is not offered for TripoSH
+        api.bispectrum_sugiyama(cat, n=32, box=300.0, kbins=kb, multipoles=[(0, 0, 0)], shot=2)
     with pytest.raises(RuntimeError):   # aliasing closure
         api.bispectrum_sugiyama(cat, n=32, box=300.0, kbins=(0.02, 0.02, 8), multipoles=[(0, 0, 0)])
     from synthetic import make_survey_catalogs
