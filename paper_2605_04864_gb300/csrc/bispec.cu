@@ -1088,8 +1088,10 @@ __global__ void k_sugi_finalize(const double* __restrict__ red, int ncombo, cons
                                 const double* __restrict__ desc, int nmult, int nb, const double* __restrict__ cross_m,
                                 const double* __restrict__ cross_q, int nq, int ncs, int shot, double dk, double kmin,
                                 const double* __restrict__ sc, double ncell, double* __restrict__ out) {
+  // one warp per output (e, i, j); the lanes share the k3 shells of the ring average
   const int nn = nb * nb;
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthreads = gridDim.x * blockDim.x;
+  const int lane = threadIdx.x & 31;
+  const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
   const double i33 = sc[SC_I33], s3 = sc[SC_S3];
   auto shell = [&](const double* cr, int L, int b) {
     const double* c = cr + (size_t)b * ncs;
@@ -1099,7 +1101,7 @@ __global__ void k_sugi_finalize(const double* __restrict__ red, int ncombo, cons
     const int iw = L == 0 ? 2 : (L == 2 ? 3 : ix + 1);
     return (c[ix] - s3 * c[iw]) / n;
   };
-  for (int o = tid; o < nmult * nn; o += nthreads) {
+  for (int o = wid; o < nmult * nn; o += nwarps) {
     const int e = o / nn, ij = o % nn, i = ij / nb, j = ij % nb;
     const double ni = cross_m[(size_t)i * ncs + 2], nj = cross_m[(size_t)j * ncs + 2];
     double s = 0.0;
@@ -1117,7 +1119,7 @@ __global__ void k_sugi_finalize(const double* __restrict__ red, int ncombo, cons
       const double lo = fabs(ci - cj) + 0.5 * dk, hi = ci + cj - 0.5 * dk;
       const int nmin = l1 < l2 ? l1 : l2;
       double num = 0.0, den = 0.0;
-      for (int m = 0; m < nq; ++m) {
+      for (int m = lane; m < nq; m += 32) {
         const double cm = (m + 0.5) * dk;
         const double nm = cross_q[(size_t)m * ncs + 2];
         if (cm < lo - 1e-9 * dk || cm > hi + 1e-9 * dk || nm <= 0) continue;
@@ -1129,14 +1131,22 @@ __global__ void k_sugi_finalize(const double* __restrict__ red, int ncombo, cons
         num += nm / cm * q * shell(cross_q, L, m);
         den += nm / cm;
       }
+      for (int off = 16; off > 0; off >>= 1) {   // fixed tree: the same sum on every lane
+        num += __shfl_xor_sync(0xffffffffu, num, off);
+        den += __shfl_xor_sync(0xffffffffu, den, off);
+      }
       if (den > 0) v += d[3] * num / den;
       sn = v / i33;
     }
-    out[o] = raw - sn;
-    out[(size_t)nmult * nn + o] = sn;
+    if (lane == 0) {
+      out[o] = raw - sn;
+      out[(size_t)nmult * nn + o] = sn;
+    }
   }
-  for (int b = tid; b < nb; b += nthreads) out[(size_t)2 * nmult * nn + b] = cross_m[(size_t)b * ncs + 2];
-  if (tid < 8) out[(size_t)2 * nmult * nn + nb + tid] = sc[tid];
+  if (blockIdx.x == 0) {
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) out[(size_t)2 * nmult * nn + b] = cross_m[(size_t)b * ncs + 2];
+    if (threadIdx.x < 8) out[(size_t)2 * nmult * nn + nb + threadIdx.x] = sc[threadIdx.x];
+  }
 }
 
 // reduce per-warp cross partials into [bin][NCROSS] in a fixed order
@@ -1959,8 +1969,8 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
                                                                             sred + (size_t)c * nb * nb);
       NPC_LAUNCH(ctx);
     }
-    // 32-thread blocks: the shot-noise sums are float64 work, spread over many SMs
-    k_sugi_finalize<<<std::max(1, (sug->nmult * nb * nb + 31) / 32), 32, 0, ctx->stream>>>(
+    // one 32-thread block (a warp) per output: the shot-noise sums are float64 work, spread over the SMs
+    k_sugi_finalize<<<std::max(1, sug->nmult * nb * nb), 32, 0, ctx->stream>>>(
         sred, ncombo, (const double*)(dtab + t_scoef), (const double*)(dtab + t_sdesc), sug->nmult, nb, cross_m,
         cross_q, nq, nsum_c, shot ? 1 : 0, kb.dk, kb.kmin, sc, (double)ncs, dev_out);
     NPC_LAUNCH(ctx);
