@@ -135,3 +135,28 @@ def test_rejects(api):
     with pytest.raises(RuntimeError):   # survey geometry with the line of sight to each grid point
         api.bispectrum_sugiyama(g, n=32, box=600.0, kbins=(0.02, 0.01, 3), multipoles=[(2, 0, 2)], origin=origin,
                                 randoms=r, los_dir=None)
+
+
+def test_max_bins_and_empty_bins(api):
+    """24 bins (the maximum; the staged fields then need two m tiles per warp) of half a fundamental
+    frequency from k = 0, so the first bins hold no modes and must report zero."""
+    box = 450.0
+    kf = 2 * np.pi / box
+    cat = make_periodic_catalog(40000, box, 32, seed=95)
+    kb = (0.0, 0.5 * kf, 24)   # k_max = 12 k_f = k_N/2 at 48^3
+    mps = [(0, 0, 0), (2, 0, 2), (1, 1, 2)]
+    res = api.bispectrum_sugiyama(cat, n=48, box=box, kbins=kb, multipoles=mps, shot=True, precision="mixed")
+    spec = _spec(48, box, (0.0, 0.0, 1.0))
+    orc = OS.bispectrum_sugiyama(spec, cat, None, kb, mps, shot=True)
+    cnt = orc["counts"]
+    assert cnt[0] == 0 and cnt[1] == 0   # |q| < k_f holds only the excluded DC mode
+    np.testing.assert_array_equal(res["nmodes"], cnt)
+    empty = (cnt[:, None] * cnt[None, :]) == 0
+    scale = np.abs(orc["B"][(0, 0, 0)]) + np.abs(orc["shot"][(0, 0, 0)])
+    for mp in mps:
+        assert np.all(res["B"][mp][empty] == 0) and np.all(res["shot"][mp][empty] == 0), mp
+        full = ~empty
+        e = np.abs(res["B"][mp] + res["shot"][mp] - orc["B"][mp])[full] / np.maximum(np.abs(orc["B"][mp]), scale)[full]
+        assert np.max(e) < 1e-4, ("raw", mp, np.max(e))
+        e = np.abs(res["shot"][mp] - orc["shot"][mp])[full] / np.maximum(np.abs(orc["shot"][mp]), scale)[full]
+        assert np.max(e) < 1e-4, ("shot", mp, np.max(e))
