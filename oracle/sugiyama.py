@@ -35,6 +35,11 @@ Pinned by tests/test_oracle_sugiyama.py: the closed form against a direct quadra
 average of sum_m (l1 l2 L; m -m 0) y_l1^{m*}(k1hat) y_l2^{-m*}(k2hat) around k3 (= q L_L(mu3)), and
 the monopole B_000 shot noise against the compressed estimator's analytic B_000 shot noise.
 
+FFT-method (exact) shot noise (Sec. 5.4.2; ``fft_method_shot_noise``): the three two-object terms
+and the pure term written out over the (q1, q2) mode pairs.  Pinned by the identity it must
+satisfy: for uncompensated fields of two point objects every closed triple draws two legs from one
+object, so the raw estimator equals it (tests, with a tilted line of sight).
+
 Pinned by tests/test_oracle_sugiyama.py: the explicit (q1, q2) enumeration of the same sum in
 Fourier space (brute force, tiny meshes); the l l 0 multipoles against the Legendre form that the
 addition theorem gives (no Y_lm or 3j involved); B_000 against the compressed estimator B_000
@@ -105,9 +110,13 @@ def sugiyama_fft(spec, meshes, kbins, multipoles, i33):
     """B_{l1 l2 L}(i, j) for every ordered bin pair (k1 = bin i, k2 = bin j), per multipole.
 
     Returns {(l1, l2, L): complex array (nb, nb)}; the imaginary part is zero up to rounding."""
+    X0, dn = spectra(spec, meshes, sorted({L for _, _, L in multipoles}))
+    return sugiyama_from_spectra(spec, X0, dn, kbins, multipoles, i33)
+
+
+def sugiyama_from_spectra(spec, X0, dn, kbins, multipoles, i33):
+    """The estimator from X(q) and dn_L^M(q)/W (the keys (L, M) of ``dn``)."""
     n = spec["n"]
-    Ls = sorted({L for _, _, L in multipoles})
-    X0, dn = spectra(spec, meshes, Ls)
     G = {key: np.fft.ifftn(v) * n**3 for key, v in dn.items()}
     cnt = mode_counts(spec, kbins)
     shells = {}
@@ -291,6 +300,54 @@ def analytic_shot_noise(spec, X0, N0, kbins, multipoles, sc):
     return out
 
 
+def fft_method_shot_noise(spec, X0, N0, kbins, multipoles, i33, s3):
+    """FFT-method (exact) shot noise (Sec. 5.4.2) of every multipole and bin pair, global line of
+    sight n, by enumerating the (q1, q2) mode pairs (q3 = -q1 - q2 on the grid):
+      H N / (I33 N_i N_j) Re sum_{m1 m2 M} (l1 l2 L; m1 m2 M) y_L^{M*}(n)
+        sum_{q1 in b_i, q2 in b_j} y_l1^{m1*}(q1) y_l2^{m2*}(q2) [XN(q3) + XN(q2) + XN(q1) - 2 S]
+    with XN = X N^*: legs 1, 2 from one object leave X N^* on q3, legs 1, 3 on q2, legs 2, 3 on q1;
+    each of the three contains the three-of-one-object part S once, the pure term once more.
+    Tiny meshes only.  Returns {(l1, l2, L): (nb, nb)}."""
+    n = spec["n"]
+    b, _ = M.bin_index(n, spec["box"], *kbins)
+    ii = M.int_freqs(n)
+    kf = 2.0 * np.pi / spec["box"]
+    d = np.asarray(spec["los_dir"], dtype=np.float64)
+    d = d / np.linalg.norm(d)
+    xn = X0 * np.conj(N0)
+    nb = kbins[2]
+    idx = [np.argwhere(b == i) for i in range(nb)]
+    qv = [np.stack([ii[t[:, 0]], ii[t[:, 1]], ii[t[:, 2]]], axis=1).astype(np.float64) for t in idx]
+    out = {}
+    for l1, l2, L in multipoles:
+        hN = H.wigner3j(l1, l2, L, 0, 0, 0) * (2 * l1 + 1) * (2 * l2 + 1) * (2 * L + 1)
+        sn = np.zeros((nb, nb))
+        for i in range(nb):
+            for j in range(nb):
+                if len(idx[i]) == 0 or len(idx[j]) == 0:
+                    continue
+                i1, i2 = idx[i], idx[j]
+                i3 = (-i1[:, None, :] - i2[None, :, :]) % n
+                t = (xn[i3[..., 0], i3[..., 1], i3[..., 2]] + xn[i2[:, 0], i2[:, 1], i2[:, 2]][None, :]
+                     + xn[i1[:, 0], i1[:, 1], i1[:, 2]][:, None] - 2.0 * s3)
+                acc = 0.0 + 0.0j
+                for m1 in range(-l1, l1 + 1):
+                    y1 = np.conj(H.ylm_racah(l1, m1, kf * qv[i]))
+                    for m2 in range(-l2, l2 + 1):
+                        Mm = -m1 - m2
+                        if abs(Mm) > L:
+                            continue
+                        w = H.wigner3j(l1, l2, L, m1, m2, Mm)
+                        if w == 0.0:
+                            continue
+                        y2 = np.conj(H.ylm_racah(l2, m2, kf * qv[j]))
+                        yL = np.conj(H.ylm_racah(L, Mm, d))
+                        acc += w * yL * np.sum(y1[:, None] * y2[None, :] * t)
+                sn[i, j] = hN * np.real(acc) / (i33 * len(i1) * len(i2))
+        out[(l1, l2, L)] = sn
+    return out
+
+
 def bispectrum_sugiyama(spec, data, randoms, kbins, multipoles, shot=False):
     """Full oracle measurement: {(l1, l2, L): real (nb, nb) array} (raw), the analytic shot noise
     when ``shot``, mode counts and scalars."""
@@ -304,5 +361,8 @@ def bispectrum_sugiyama(spec, data, randoms, kbins, multipoles, shot=False):
         nmeshes = P.fkp_meshes(spec, data, randoms, sc, weight_power=2)
         X0, _ = spectra(spec, meshes, [])
         N0, _ = spectra(spec, nmeshes, [])
-        out["shot"] = analytic_shot_noise(spec, X0, N0, kbins, multipoles, sc)
+        if shot == "fft":
+            out["shot"] = fft_method_shot_noise(spec, X0, N0, kbins, multipoles, sc["I33"], sc["S3"])
+        else:
+            out["shot"] = analytic_shot_noise(spec, X0, N0, kbins, multipoles, sc)
     return out

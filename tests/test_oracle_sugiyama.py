@@ -4,6 +4,7 @@ import pytest
 
 from oracle import bispec as B
 from oracle import harmonics as H
+from oracle import mesh as M
 from oracle import power as P
 from oracle import sugiyama as S
 from synthetic import Catalog, make_periodic_catalog
@@ -181,3 +182,26 @@ def test_monopole_shot_noise_equals_the_compressed_one(cat):
     np.testing.assert_allclose(got, bb[0], rtol=1e-12)
     # symmetric in (k1, k2) for l1 = l2
     np.testing.assert_allclose(sn[(0, 0, 0)], sn[(0, 0, 0)].T, rtol=1e-12)
+
+
+@pytest.mark.parametrize("los_dir", [(0.0, 0.0, 1.0), TILT])
+def test_fft_method_shot_equals_raw_for_two_objects(los_dir):
+    """Two point objects, uncompensated fields: every closed triple draws two legs from one object,
+    so the raw estimator equals the FFT-method shot noise (all three pair terms and the -2 S)."""
+    spec = _spec(16, los_dir)
+    (kx, ky, kz), _ = M.kvectors(16, 300.0)
+    pos, w = [(13.7, 142.1, 277.3), (161.2, 5.9, 30.4)], [0.8, 1.7]
+    X = np.zeros((16,) * 3, dtype=np.complex128)
+    N = np.zeros_like(X)
+    for p, wp in zip(pos, w):
+        e = np.exp(-1j * (kx * p[0] + ky * p[1] + kz * p[2]))
+        X += wp * e
+        N += wp * wp * e
+    d = np.asarray(los_dir) / np.linalg.norm(los_dir)
+    mps = [(0, 0, 0), (2, 0, 2), (0, 2, 2), (1, 1, 2), (2, 2, 2), (2, 2, 4)]
+    dn = {(L, Mm): np.conj(H.ylm_racah(L, Mm, d)) * X for L in (0, 2, 4) for Mm in range(-L, L + 1)}
+    raw = S.sugiyama_from_spectra(spec, X, dn, KB, mps, 1.0)
+    sn = S.fft_method_shot_noise(spec, X, N, KB, mps, 1.0, sum(x ** 3 for x in w))
+    scale = np.max(np.abs(raw[(0, 0, 0)]))
+    for mp in mps:
+        assert np.max(np.abs(np.real(raw[mp]) - sn[mp])) < 1e-11 * scale, mp
