@@ -244,12 +244,16 @@ npc_status npc_bispectrum_triangles(const npc_kbins* bins, int32_t* tri, int64_t
  *   one object the thin-shell ring average of Lemma 1, H N/I33 sum_k3 w q_{l1 l2 L}(k1, k2, k3)
  *   Q_L(k3) / sum_k3 w over the shells of width dk that close the pair (w = N_mode/k3), with
  *   H_L = Q_L = <L_L(mu) Re X N^*> - S <L_L(mu)> on the k-bins and the k3 shells (N the w^2 field)
- *   and q built from Racah-normalised associated Legendre functions.
+ *   and q built from Racah-normalised associated Legendre functions; 2 uses the FFT method of
+ *   Sec. 5.4.2 instead (exact): legs 1, 2 from one object as triple products of the y_l^m-weighted
+ *   indicator shells against the full-range field of X N^*, legs 1, 3 and 2, 3 and the pure term as
+ *   products of per-bin sums A_l^m = sum y_l^{m*}(qhat) and C_l^m = sum y_l^{m*}(qhat) X N^*,
+ *   shot = H N/(I33 N_i N_j) sum_m (l1 l2 L; m -m 0) Re[T12 + A1 C2 + C1 A2 - 2 S A1 A2].
  * Output `out` (float64, host or device as out_on_device), length npc_bispectrum_sugiyama_len():
  *   [nmult][nbins][nbins] B (k1 = bin i the row, k2 = bin j the column; raw minus shot noise),
  *   [nmult][nbins][nbins] shot noise (zeros when shot = 0), [nbins] N_modes, then 8 scalars as in
  *   npc_catalog_scalars.
- * Errors as npc_bispectrum; shot other than 0 or 1: NPC_ERR_INVALID_ARG. */
+ * Errors as npc_bispectrum; shot other than 0, 1 or 2: NPC_ERR_INVALID_ARG. */
 npc_status npc_bispectrum_sugiyama(npc_ctx* ctx, const npc_mesh_spec* mesh, const npc_catalog* data,
                                    const npc_catalog* randoms, const npc_kbins* bins, int32_t nmult,
                                    const int32_t* multipoles, int32_t shot, npc_precision prec,

@@ -253,10 +253,11 @@ def bispectrum_sugiyama(data, n, box, kbins, multipoles=((0, 0, 0), (2, 0, 2)), 
                         los_dir=(0.0, 0.0, 1.0), precision="mixed", origin=(0.0, 0.0, 0.0), device=0, out=None,
                         randoms=None):
     """Sugiyama TripoSH multipoles B_{l1 l2 L}(k1, k2) for every bin pair, global line of sight
-    ``los_dir``; periodic box, or survey geometry with ``randoms``.  shot: subtract the analytic
-    shot noise.  Returns {"B": {(l1, l2, L): (nb, nb) array, row k1, column k2}, "shot": {...},
+    ``los_dir``; periodic box, or survey geometry with ``randoms``.  shot: True/1 subtracts the
+    analytic shot noise, "fft"/2 the FFT-method (exact) one.  Returns {"B": {(l1, l2, L): (nb, nb) array, row k1, column k2}, "shot": {...},
     "nmodes", "scalars"}."""
     keep = _Keep()
+    shot = 2 if shot == "fft" else int(shot)
     spec = make_spec(n, box, origin, assign, interlace, 1 if randoms is None else 0, los_dir, (0.0, 0.0, 0.0))
     kb = B.npc_kbins(float(kbins[0]), float(kbins[1]), int(kbins[2]))
     mps = [tuple(int(v) for v in mp) for mp in multipoles]

@@ -687,7 +687,7 @@ npc_status npc_bispectrum_sugiyama(npc_ctx* ctx, const npc_mesh_spec* mesh, cons
     req.L[e] = L;
   }
   if (prec != NPC_PREC_FP64 && prec != NPC_PREC_MIXED) return set_err(ctx, NPC_ERR_INVALID_ARG, "bad precision");
-  if (shot != 0 && shot != 1) return set_err(ctx, NPC_ERR_INVALID_ARG, "shot must be 0 or 1");
+  if (shot < 0 || shot > 2) return set_err(ctx, NPC_ERR_INVALID_ARG, "shot must be 0, 1 or 2");
   if (mesh->periodic) {
     if (randoms) return set_err(ctx, NPC_ERR_INVALID_ARG, "periodic box takes no randoms");
   } else {

@@ -1074,6 +1074,8 @@ __device__ double racah_assoc(int l, int n, double x) {
 
 // per multipole: l1, l2, L, H N, then (l1 l2 L; n -n 0) for n = -4 .. 4
 constexpr int SUGI_DESC = 13;
+// per-bin lattice sums of the FFT-method shot noise: (Re A, Im A, Re C, Im C) for l <= 4, 0 <= m <= l
+constexpr int NSB = 60;
 
 // TripoSH multipoles from the per-combination sums red[c][i][j] = sum_x A_i(x) G(x) C_j(x) (A, C the
 // parts of F_l1^m and F_l2^m of bins i and j): raw(i, j) = sum_c coef[e][c] red[c][i][j] /
@@ -1084,9 +1086,16 @@ constexpr int SUGI_DESC = 13;
 // k3 shells of width dk, w_m = N_mode(m)/c_m over the shells closing the pair, and Lemma 1's
 //   q(k1, k2, k3) = sum_n (-1)^n cL_l1^n(cos t13) cL_l2^{-n}(cos t23) (l1 l2 L; n -n 0).
 // Output: [nmult][nb][nb] raw - shot, [nmult][nb][nb] shot, the mode counts, the scalars.
+// shot = 2, the FFT method (Sec. 5.4.2): red[ncombo + c] holds the products of the indicator parts
+// against the full-range X N^* field (legs 1, 2 from one object), sbins the per-bin sums A_l^m =
+// sum y_l^{m*} and C_l^m = sum y_l^{m*} X N^* (legs 1, 3 and legs 2, 3 from one object, and the pure
+// term): shot = [sum_c coef red_ind / ncell + H N sum_m (l1 l2 L; m -m 0) Re(A1^m C2^{-m} +
+// C1^m A2^{-m} - 2 S A1^m A2^{-m})] / (I33 N_i N_j), with A^{-m} = (-1)^m conj A^m and
+// C^{-m} = (-1)^{m+l} conj C^m.
 __global__ void k_sugi_finalize(const double* __restrict__ red, int ncombo, const double* __restrict__ coef,
                                 const double* __restrict__ desc, int nmult, int nb, const double* __restrict__ cross_m,
-                                const double* __restrict__ cross_q, int nq, int ncs, int shot, double dk, double kmin,
+                                const double* __restrict__ cross_q, int nq, int ncs, int shot,
+                                const double* __restrict__ sbins, double dk, double kmin,
                                 const double* __restrict__ sc, double ncell, double* __restrict__ out) {
   // one warp per output (e, i, j); the lanes share the k3 shells of the ring average
   const int nn = nb * nb;
@@ -1108,7 +1117,39 @@ __global__ void k_sugi_finalize(const double* __restrict__ red, int ncombo, cons
     for (int c = 0; c < ncombo; ++c) s += coef[(size_t)e * ncombo + c] * red[(size_t)c * nn + ij];
     const double raw = (ni > 0 && nj > 0) ? s / (i33 * ni * nj * ncell) : 0.0;
     double sn = 0.0;
-    if (shot && ni > 0 && nj > 0) {
+    if (shot == 2 && ni > 0 && nj > 0) {
+      const double* d = desc + (size_t)e * SUGI_DESC;
+      const int l1 = (int)d[0], l2 = (int)d[1];
+      double t12 = 0.0;
+      for (int c = 0; c < ncombo; ++c) t12 += coef[(size_t)e * ncombo + c] * red[(size_t)(ncombo + c) * nn + ij];
+      // A or C (k = 0 or 2) of (l, m) on bin b, m of either sign
+      auto get = [&](int l, int m, int b, int k, double& re, double& im) {
+        const int am = m < 0 ? -m : m;
+        const double* p = sbins + (size_t)b * NSB + 4 * (l * (l + 1) / 2 + am) + k;
+        re = p[0];
+        im = p[1];
+        if (m < 0) {
+          const int ph = am + (k == 2 ? l : 0);
+          im = -im;
+          if (ph & 1) {
+            re = -re;
+            im = -im;
+          }
+        }
+      };
+      double rest = 0.0;
+      const int mm = l1 < l2 ? l1 : l2;
+      for (int m = -mm; m <= mm; ++m) {
+        double a1r, a1i, c1r, c1i, a2r, a2i, c2r, c2i;
+        get(l1, m, i, 0, a1r, a1i);
+        get(l1, m, i, 2, c1r, c1i);
+        get(l2, -m, j, 0, a2r, a2i);
+        get(l2, -m, j, 2, c2r, c2i);
+        const double t = (a1r * c2r - a1i * c2i) + (c1r * a2r - c1i * a2i) - 2.0 * s3 * (a1r * a2r - a1i * a2i);
+        rest += d[4 + m + 4] * t;
+      }
+      sn = (t12 / ncell + d[3] * rest) / (i33 * ni * nj);
+    } else if (shot == 1 && ni > 0 && nj > 0) {
       const double* d = desc + (size_t)e * SUGI_DESC;
       const int l1 = (int)d[0], l2 = (int)d[1], L = (int)d[2];
       double v = 0.0;
@@ -1146,6 +1187,62 @@ __global__ void k_sugi_finalize(const double* __restrict__ red, int ncombo, cons
   if (blockIdx.x == 0) {
     for (int b = threadIdx.x; b < nb; b += blockDim.x) out[(size_t)2 * nmult * nn + b] = cross_m[(size_t)b * ncs + 2];
     if (threadIdx.x < 8) out[(size_t)2 * nmult * nn + nb + threadIdx.x] = sc[threadIdx.x];
+  }
+}
+
+// Per-bin lattice sums of the TripoSH FFT-method shot noise, for l <= 4 and 0 <= m <= l at index
+// 4 (l(l+1)/2 + m): Re A, Im A, Re C, Im C with A_l^m(b) = sum_{q in b} y_l^{m*}(qhat) and
+// C_l^m(b) = sum_{q in b} y_l^{m*}(qhat) X(q) N^*(q), y in the line-of-sight frame.  A row kz > 0 of
+// the half spectrum stands for q and -q: y^{m*}(-qhat) = (-1)^l y^{m*}(qhat), XN^*(-q) = conj XN^*(q).
+template <typename T, int N>
+__global__ void __launch_bounds__(BT)
+k_sugi_binsums(const cplx<T>* __restrict__ X0, const cplx<T>* __restrict__ XN, int KY, const LosFrame fr,
+               const int16_t* __restrict__ tab_m, int nbm, double* __restrict__ part) {
+  constexpr int NW = BT / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double* pm = part + ((size_t)blockIdx.x * NW + warp) * nbm * NSB;
+  const int nyr = 2 * KY + 1;
+  const int nrows = (KY + 1) * nyr;
+  for (int r = blockIdx.x; r < nrows; r += gridDim.x) {
+    const int kz = r / nyr;
+    const int jy = r % nyr - KY;
+    const int ky = jy < 0 ? jy + N : jy;
+    for (int jb = warp * 32; jb < N; jb += blockDim.x) {
+      const int j = jb + lane;
+      const int i = j < N / 2 ? j : j - N;
+      const int n2 = i * i + jy * jy + kz * kz;
+      int bm = -1;
+      T vals[NSB];
+#pragma unroll
+      for (int q = 0; q < NSB; ++q) vals[q] = T(0);
+      if (j < N && n2 > 0 && i != -N / 2 && jy != -N / 2) bm = tab_m[n2];
+      if (bm >= 0) {
+        const size_t idx = ((size_t)kz * N + ky) * N + j;
+        const cplx<T> a = X0[idx], b = XN[idx];
+        const T xr = a.x * b.x + a.y * b.y, xi = a.y * b.x - a.x * b.y;   // X N^*
+        const T inv = T(1) / sqrt(T(n2));
+        const T ii = T(i), jj = T(jy), zz = T(kz);
+        const T ux = (ii * T(fr.e1[0]) + jj * T(fr.e1[1]) + zz * T(fr.e1[2])) * inv;
+        const T uy = (ii * T(fr.e2[0]) + jj * T(fr.e2[1]) + zz * T(fr.e2[2])) * inv;
+        const T uz = (ii * T(fr.e3[0]) + jj * T(fr.e3[1]) + zz * T(fr.e3[2])) * inv;
+#pragma unroll
+        for (int l = 0; l <= 4; ++l)
+#pragma unroll
+          for (int m = 0; m <= l; ++m) {
+            T yr, yi;
+            ylm_frame<T>(l, m, ux, uy, uz, yr, yi);
+            const T sr = yr, si = -yi;   // y^{m*}
+            const T mir = kz > 0 ? ((l & 1) ? T(-1) : T(1)) : T(0);
+            const int o = 4 * (l * (l + 1) / 2 + m);
+            vals[o] = sr * (T(1) + mir);
+            vals[o + 1] = si * (T(1) + mir);
+            // y* XN + mir y* conj(XN)
+            vals[o + 2] = sr * xr - si * xi + mir * (sr * xr + si * xi);
+            vals[o + 3] = sr * xi + si * xr + mir * (si * xr - sr * xi);
+          }
+      }
+      seg_accumulate<T, NSB>(lane, bm, vals, pm);
+    }
   }
 }
 
@@ -1603,7 +1700,7 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
   int ntl = 0, tls[2] = {0, 0};   // compressed multipoles requested
   for (int l = 0; l <= 2; l += 2)
     if (tripo_mask & (1 << l)) tls[ntl++] = l;
-  if (fftshot) {
+  if (fftshot && !sugi) {
     iS0 = (int)fl.size();
     for (int b = 0; b < nb; ++b) add(2, 0, b, Ks, 4);            // sum_{q in b} X_0 N_0^* e^{iqx}
     if (want2) {
@@ -1621,9 +1718,9 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
   }
   // TripoSH shell fields: the parts of F_l^m(x; k_b), 0 <= m <= min(l1, l2), of every l requested
   // (F_0^0 is F0_b above); sfield[l][m][part] = R index of bin 0, or -1
-  int sfield[5][5][2];
+  int sfield[5][5][2], ifield[5][5][2], iXN = -1;   // ifield: the indicator versions (FFT-method shot noise)
   for (int l = 0; l < 5; ++l)
-    for (int mm = 0; mm < 5; ++mm) sfield[l][mm][0] = sfield[l][mm][1] = -1;
+    for (int mm = 0; mm < 5; ++mm) sfield[l][mm][0] = sfield[l][mm][1] = ifield[l][mm][0] = ifield[l][mm][1] = -1;
   if (sugi) {
     sfield[0][0][0] = 0;
     int fam = 20;
@@ -1646,6 +1743,26 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
             ++fam;
           }
       }
+    }
+    if (fftshot) {
+      // FFT-method shot noise: the same parts of the y-weighted indicator shells, and the
+      // full-range field of X N^*
+      ifield[0][0][0] = iI;
+      for (int l = 0; l < 5; ++l)
+        for (int mm = 0; mm < 5; ++mm)
+          for (int part = 0; part < 2; ++part) {
+            if (sfield[l][mm][part] < 0 || (l == 0 && mm == 0)) continue;
+            ifield[l][mm][part] = (int)fl.size();
+            for (int b = 0; b < nb; ++b) {
+              add(1, 2, b, Ks, fam);
+              fl.back().yl = (int8_t)l;
+              fl.back().ym = (int8_t)mm;
+              fl.back().ypart = (int8_t)part;
+            }
+            ++fam;
+          }
+      iXN = (int)fl.size();
+      add(2, 0, -1, KG, fam++);
     }
   }
   const int nfield = (int)fl.size();
@@ -1848,7 +1965,7 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
     a.ncol = nb;
   };
   TripleArgs ts1{}, ts2{}, tn2{}, ts3{};
-  if (fftshot) {
+  if (fftshot && !sugi) {
     setup_shot(ts1, iI, want2 ? iI2 : -1, iS0);   // sum I_a I_b S0_c and sum I2_a I_b S0_c
     if (ntl > 0) {
       // compressed estimator, same I_a I_b rows: columns nb + e: sum I_a I_b SF_l (Ta),
@@ -1934,9 +2051,11 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
   auto launch = [&](const TripleArgs& a, int grid, double* part) { return launch_tab(a, grid, part, t_pij, t_rowp); };
   if (sugi) {
     // one product per combination: rows F_l1^m part (bin i) x G, columns F_l2^m part (bin j)
+    // (FFT-method shot noise: the same products of the indicator parts against X N^*, rows ncombo..)
     const int ncombo = (int)combos.size();
-    std::vector<TripleArgs> targs(ncombo);
-    for (int c = 0; c < ncombo; ++c) {
+    const int nprod = fftshot ? 2 * ncombo : ncombo;
+    std::vector<TripleArgs> targs(nprod);
+    for (int c = 0; c < nprod; ++c) {
       TripleArgs& a = targs[c];
       a = TripleArgs{};
       a.npair = nb;
@@ -1948,10 +2067,13 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
         return a.nstage++;
       };
       for (int q = 0; q < TRI_COLS; ++q) a.c_slot[q] = -1;
-      const SCombo& cb = combos[c];
-      for (int b = 0; b < nb; ++b) a.a_slot[0][b] = stage_of(sfield[cb.l1][cb.m][cb.part] + b);
-      a.b_slot[0][0] = stage_of(iG);
-      for (int b = 0; b < nb; ++b) a.c_slot[b] = stage_of(sfield[cb.l2][cb.m][cb.part] + b);
+      const SCombo& cb = combos[c % ncombo];
+      const bool ind = c >= ncombo;
+      const int fa = ind ? ifield[cb.l1][cb.m][cb.part] : sfield[cb.l1][cb.m][cb.part];
+      const int fc = ind ? ifield[cb.l2][cb.m][cb.part] : sfield[cb.l2][cb.m][cb.part];
+      for (int b = 0; b < nb; ++b) a.a_slot[0][b] = stage_of(fa + b);
+      a.b_slot[0][0] = stage_of(ind ? iXN : iG);
+      for (int b = 0; b < nb; ++b) a.c_slot[b] = stage_of(fc + b);
       a.nf_cols = nb;
       a.nrows = nb;
       a.ncol = nb;
@@ -1960,19 +2082,34 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
     const int gsug = sizeof(T) == 4 ? 2 * ctx->num_sms : grid_for(targs[0]);
     const size_t per = (size_t)gsug * nb * nb;
     double *spart, *sred;
-    NPC_TRY(ws_get(ctx, "bis.sugpart", sizeof(double) * per * ncombo, (void**)&spart));
-    NPC_TRY(ws_get(ctx, "bis.sugred", sizeof(double) * (size_t)nb * nb * ncombo, (void**)&sred));
-    for (int c = 0; c < ncombo; ++c) NPC_TRY(launch_tab(targs[c], gsug, spart + c * per, t_spij, t_srow));
+    NPC_TRY(ws_get(ctx, "bis.sugpart", sizeof(double) * per * nprod, (void**)&spart));
+    NPC_TRY(ws_get(ctx, "bis.sugred", sizeof(double) * (size_t)nb * nb * nprod, (void**)&sred));
+    for (int c = 0; c < nprod; ++c) NPC_TRY(launch_tab(targs[c], gsug, spart + c * per, t_spij, t_srow));
     NPC_TRY(stage_mark(ctx, "triple"));
-    for (int c = 0; c < ncombo; ++c) {
+    for (int c = 0; c < nprod; ++c) {
       k_part_reduce<<<(nb * nb + 31) / 32, 32 * PR_SLICES, 0, ctx->stream>>>(spart + c * per, gsug, (int64_t)nb * nb,
                                                                             sred + (size_t)c * nb * nb);
+      NPC_LAUNCH(ctx);
+    }
+    double* sbins = nullptr;
+    if (fftshot) {
+      // per-bin lattice sums A_l^m and C_l^m of the pair terms with a free third leg
+      const int nrows = (K + 1) * (2 * K + 1);
+      const int g = std::min(nrows, ctx->num_sms * 2);
+      const size_t np = (size_t)g * (BT / 32);
+      double* bpart;
+      NPC_TRY(ws_get(ctx, "bis.sbpart", sizeof(double) * np * NSB * nb, (void**)&bpart));
+      NPC_CUDA(ctx, cudaMemsetAsync(bpart, 0, sizeof(double) * np * NSB * nb, ctx->stream));
+      NPC_TRY(ws_get(ctx, "bis.sbins", sizeof(double) * NSB * nb, (void**)&sbins));
+      k_sugi_binsums<T, N><<<g, BT, 0, ctx->stream>>>(X, X + xfs, K, frame, tab_m, nb, bpart);
+      NPC_LAUNCH(ctx);
+      k_cross_reduce<<<(nb * NSB + 3) / 4, 128, 0, ctx->stream>>>(bpart, (int)np, nb, NSB, sbins);
       NPC_LAUNCH(ctx);
     }
     // one 32-thread block (a warp) per output: the shot-noise sums are float64 work, spread over the SMs
     k_sugi_finalize<<<std::max(1, sug->nmult * nb * nb), 32, 0, ctx->stream>>>(
         sred, ncombo, (const double*)(dtab + t_scoef), (const double*)(dtab + t_sdesc), sug->nmult, nb, cross_m,
-        cross_q, nq, nsum_c, shot ? 1 : 0, kb.dk, kb.kmin, sc, (double)ncs, dev_out);
+        cross_q, nq, nsum_c, shot, sbins, kb.dk, kb.kmin, sc, (double)ncs, dev_out);
     NPC_LAUNCH(ctx);
     NPC_TRY(stage_mark(ctx, "finalize"));
     (void)out_len;

@@ -102,6 +102,24 @@ def test_analytic_shot_noise(api, prec, tol):
         assert np.max(e) < tol, ("raw", mp, np.max(e))
 
 
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 1e-4)])
+def test_fft_method_shot_noise(api, prec, tol):
+    """Sec. 5.4.2 FFT-method (exact) shot noise against the oracle's mode-pair enumeration, with a
+    tilted line of sight (every sub-configuration of the oracle contributes)."""
+    cat = make_periodic_catalog(20000, 300.0, 32, seed=97)
+    kb = (0.02, 0.02, 5)
+    mps = [(0, 0, 0), (2, 0, 2), (0, 2, 2), (1, 1, 2), (2, 2, 2), (3, 1, 2), (2, 2, 4)]
+    res = api.bispectrum_sugiyama(cat, n=32, box=300.0, kbins=kb, multipoles=mps, shot="fft", los_dir=TILT,
+                                  precision=prec)
+    orc = OS.bispectrum_sugiyama(_spec(32, 300.0, TILT), cat, None, kb, mps, shot="fft")
+    scale = np.abs(orc["B"][(0, 0, 0)]) + np.abs(orc["shot"][(0, 0, 0)])
+    for mp in mps:
+        e = np.abs(res["shot"][mp] - orc["shot"][mp]) / np.maximum(np.abs(orc["shot"][mp]), scale)
+        assert np.max(e) < tol, ("shot", mp, np.max(e))
+        e = np.abs(res["B"][mp] + res["shot"][mp] - orc["B"][mp]) / np.maximum(np.abs(orc["B"][mp]), scale)
+        assert np.max(e) < tol, ("raw", mp, np.max(e))
+
+
 def test_monopole_matches_the_compressed_estimator(api):
     """B_000 of the two estimators coincide (Sec. 6): the library's two paths agree."""
     cat = make_periodic_catalog(20000, 300.0, 32, seed=87)
@@ -125,8 +143,8 @@ def test_rejects(api):
         api.bispectrum_sugiyama(cat, n=32, box=300.0, kbins=kb, multipoles=[(1, 0, 1)])
     with pytest.raises(RuntimeError):   # l above 4
         api.bispectrum_sugiyama(cat, n=32, box=300.0, kbins=kb, multipoles=[(5, 5, 0)])
-    with pytest.raises(RuntimeError):   # the FFT-method shot noise is not offered for TripoSH
-        api.bispectrum_sugiyama(cat, n=32, box=300.0, kbins=kb, multipoles=[(0, 0, 0)], shot=2)
+    with pytest.raises(RuntimeError):   # no such shot-noise mode
+        api.bispectrum_sugiyama(cat, n=32, box=300.0, kbins=kb, multipoles=[(0, 0, 0)], shot=3)
     with pytest.raises(RuntimeError):   # aliasing closure
         api.bispectrum_sugiyama(cat, n=32, box=300.0, kbins=(0.02, 0.02, 8), multipoles=[(0, 0, 0)])
     from synthetic import make_survey_catalogs
