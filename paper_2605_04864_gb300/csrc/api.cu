@@ -33,6 +33,8 @@ npc_status ws_get(npc_ctx* ctx, const char* name, size_t bytes, void** out) {
     if (ctx->capturing)
       return set_err(ctx, NPC_ERR_INVALID_ARG, "workspace '%s' would grow during graph capture", name);
     ctx->ws_generation++;
+    // contents cached under this name (tables, triangle counts) do not survive a reallocation
+    ctx->host_cache_keys.erase(name);
     if (w.p) {
       cudaError_t e = cudaStreamSynchronize(ctx->stream);
       if (e != cudaSuccess) return set_err(ctx, NPC_ERR_CUDA, "sync before realloc: %s", cudaGetErrorString(e));
@@ -64,9 +66,9 @@ static bool table_cached(npc_ctx* ctx, const std::string& name0, const std::vect
 npc_status ws_table(npc_ctx* ctx, const std::string& name0, const std::vector<char>& key, const void* data,
                     size_t bytes, void** out) {
   const std::string name = slot_name(ctx, name0);
-  auto it = ctx->host_cache_keys.find(name);
   void* p;
-  NPC_TRY(ws_get(ctx, name.c_str(), bytes, &p));
+  NPC_TRY(ws_get(ctx, name.c_str(), bytes, &p));   // (a reallocation drops the cached key)
+  auto it = ctx->host_cache_keys.find(name);
   if (it == ctx->host_cache_keys.end() || it->second != key) {
     if (ctx->capturing)
       return set_err(ctx, NPC_ERR_INVALID_ARG, "table '%s' would be uploaded during graph capture", name.c_str());

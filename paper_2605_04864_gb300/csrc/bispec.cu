@@ -1659,9 +1659,9 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
   }
   const Tri tr = make_triangles(kb);
   const int ntri = (int)tr.tri.size() / 3, npair = (int)tr.pij.size();
-  double* nt_sums;
+  double* nt_sums = nullptr;
   const std::string ntname = slot_name(ctx, "bis.ntsums");
-  NPC_TRY(ws_get(ctx, ntname.c_str(), sizeof(double) * npair * nb, (void**)&nt_sums));
+  if (!sugi) NPC_TRY(ws_get(ctx, ntname.c_str(), sizeof(double) * npair * nb, (void**)&nt_sums));
   auto it = ctx->host_cache_keys.find(ntname);
   const bool need_nt = !sugi && (it == ctx->host_cache_keys.end() || it->second != ntkey);
 

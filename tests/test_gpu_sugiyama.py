@@ -178,3 +178,18 @@ def test_max_bins_and_empty_bins(api):
         assert np.max(e) < 1e-4, ("raw", mp, np.max(e))
         e = np.abs(res["shot"][mp] - orc["shot"][mp])[full] / np.maximum(np.abs(orc["shot"][mp]), scale)[full]
         assert np.max(e) < 1e-4, ("shot", mp, np.max(e))
+
+
+def test_cached_triangle_counts_survive_a_larger_call(api):
+    """N_T is cached per geometry; a TripoSH call with more bins grows the shared workspaces, after
+    which the smaller bispectrum must still report the same counts (a reallocated workspace drops
+    its cached contents)."""
+    cat = make_periodic_catalog(20000, 300.0, 32, seed=99)
+    kb = (0.02, 0.02, 5)
+    first = api.bispectrum(cat, n=32, box=300.0, kbins=kb, scoc_ells=(0,), tripo_ells=(0,), precision="fp64")
+    kf = 2 * np.pi / 300.0
+    api.bispectrum_sugiyama(cat, n=32, box=300.0, kbins=(0.0, 0.3 * kf, 24), multipoles=[(0, 0, 0)],
+                            precision="fp64")
+    again = api.bispectrum(cat, n=32, box=300.0, kbins=kb, scoc_ells=(0,), tripo_ells=(0,), precision="fp64")
+    np.testing.assert_array_equal(again["NT"], first["NT"])
+    np.testing.assert_array_equal(again["B"][0], first["B"][0])
