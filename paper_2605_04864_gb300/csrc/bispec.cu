@@ -378,7 +378,8 @@ struct ShellField {
   int8_t mult;    // 0: 1, 1: L_2(mu), 2: the TripoSH weight of (yl, ym, ypart)
   int16_t bin;    // >= 0: modes of this bin; -1: all modes with n2 <= n2cap
   int K;          // kz <= K, |ky| <= K
-  int8_t yl, ym;  // mult 2: the field is a part of F_l^m(x; k) = sum_q e^{iqx} y_l^{m*}(qhat) X(q), m >= 0
+  int8_t yl, ym;  // mult 2: the field is a part of sum_q e^{iqx} y_l^{m*}(qhat) S(q), m >= 0, S the source
+                  // (X: the TripoSH shell F_l^m; ones: its indicator for the FFT-method shot noise)
   int8_t ypart;   // mult 2: 0 its real part, 1 its imaginary part
   int8_t pad;
   int64_t off1;   // offset of this field in the x-pass output (complex elements)
