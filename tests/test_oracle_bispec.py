@@ -341,3 +341,17 @@ def test_survey_l2_tends_to_global_los_for_a_distant_observer():
     nearg = B.bispectrum(dict(common, origin=tuple(origin2), los="global", los_dir=tuple(d)), g2, r2, kb, (2,), (),
                          shot=False)
     assert np.max(np.abs(near["B"][2] - nearg["B"][2])) > 1e-3 * np.max(np.abs(nearg["B"][2]))
+
+
+def test_analytic_shot_noise_tracks_the_fft_method():
+    """The thin-shell analytic shot noise of B_l and B_l0l (Sec. 5.4.1, 5.4.3) against the exact
+    FFT-method sums (Sec. 5.4.2) on the same catalogue: within a few per cent of the monopole
+    shot-noise scale (median), larger only on the few triangles of thin low-k bins."""
+    spec = _periodic_spec(32, 300.0)
+    cat = make_periodic_catalog(20000, 300.0, 32, seed=5)
+    res = B.bispectrum(spec, cat, None, (0.02, 0.02, 5), (0, 2), (0, 2), shot="fft")
+    for key, fkey, med, mx in (("shot_B", "shot_B_fft", 0.03, 0.2), ("shot_BB", "shot_BB_fft", 0.02, 0.1)):
+        scale = np.abs(res[fkey][0])
+        for ell in (0, 2):
+            rel = np.abs(res[key][ell] - res[fkey][ell]) / scale
+            assert np.median(rel) < med and np.max(rel) < mx, (key, ell, np.median(rel), np.max(rel))
