@@ -225,3 +225,27 @@ def test_analytic_shot_noise_tracks_the_fft_method():
     for mp in mps:
         rel = np.abs(an[mp] - ff[mp]) / scale
         assert np.median(rel) < 0.03 and np.max(rel) < 0.12, (mp, np.median(rel), np.max(rel))
+
+
+def test_endpoint_line_of_sight_tends_to_global_for_a_distant_observer():
+    """Survey geometry (G_L^M from y_L^M-weighted transforms with the line of sight to each grid
+    point) equals the global-line-of-sight estimator when the observer is so far away that every
+    direction is the same; a nearby observer changes B_202."""
+    from synthetic import make_survey_catalogs
+
+    box, kb = 600.0, (0.011, 0.0135, 3)
+    mps = [(0, 0, 0), (2, 0, 2), (1, 1, 2), (2, 2, 2)]
+    d = np.ones(3) / np.sqrt(3.0)
+    res = {}
+    for dist in (1.0e8, 900.0):
+        g, r, origin = make_survey_catalogs(3000, 30000, box, dist, 12, seed=23, fkp_p0=1e4, dtype=np.float64)
+        common = dict(n=20, box=box, origin=tuple(origin), assign=3, interlace=1, periodic=0)
+        ep = S.bispectrum_sugiyama(dict(common, los="endpoint", observer=(0.0, 0.0, 0.0)), g, r, kb, mps)
+        gl = S.bispectrum_sugiyama(dict(common, los="global", los_dir=tuple(d)), g, r, kb, mps)
+        res[dist] = (ep, gl)
+    ep, gl = res[1.0e8]
+    scale = np.max(np.abs(gl["B"][(0, 0, 0)]))
+    for mp in mps:
+        assert np.max(np.abs(ep["B"][mp] - gl["B"][mp])) < 5e-5 * scale, mp   # directions vary by box/dist ~ 6e-6
+    ep, gl = res[900.0]
+    assert np.max(np.abs(ep["B"][(2, 0, 2)] - gl["B"][(2, 0, 2)])) > 1e-3 * np.max(np.abs(gl["B"][(2, 0, 2)]))
