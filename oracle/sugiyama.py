@@ -45,8 +45,9 @@ Fourier space (brute force, tiny meshes); the l l 0 multipoles against the Legen
 addition theorem gives (no Y_lm or 3j involved); B_000 against the compressed estimator B_000
 (Sec. 6: the two monopoles coincide); the half-sum over paired sub-configurations of the boxed
 estimator (Eq. sym_sugi); invariance under a cyclic permutation of the axes applied to the
-catalogue and the line of sight together; and, for a global line of sight along z, the reduction
-of B_l0l to (2l+1)/(I33 N_i N_j n^3) sum_x F_l(x; k_i) F_0(x; k_j) G(x) with F_l the L_l(mu) shell.
+catalogue and the line of sight together; for a global line of sight along z, the reduction of
+B_l0l to (2l+1)/(I33 N_i N_j n^3) sum_x F_l(x; k_i) F_0(x; k_j) G(x) with F_l the L_l(mu) shell; and,
+with the line of sight to each grid point, the global-line-of-sight result for a distant observer.
 """
 from __future__ import annotations
 
