@@ -237,5 +237,51 @@ def bispectrum(spec, data, randoms, kbins, scoc_ells=(0, 2), tripo_ells=(0, 2), 
     return res
 
 
+def cross_bispectrum(spec, tracers, kbins, scoc_ells=(0, 2), tripo_ells=(0,)):
+    """Multi-tracer bispectra, global line of sight, raw estimates: tracer t_1 on leg 1 (k1, which
+    carries the line of sight of B_l), t_2 on leg 2, t_3 on leg 3, ``tracers`` = three (data,
+    randoms) pairs (randoms None for a periodic box).
+      B_l^{123}(i,j,k)  = (2l+1)/(I33^{123} N_T) sum_closed L_l(mu1) X^1(q1) X^2(q2) X^3(q3)
+      B_l0l^{123}(i,j)  = (2l+1)/(I33^{123} N_i N_j) sum_{q1 in b_i, q2 in b_j} X^1(q1) X^2(q2)
+                          L_l(mu3) X^3(q3),  q3 = -q1 - q2
+    Readings (the paper's toolkit lists auto and cross bispectra without printing the cross form):
+    I33^{123} = (I33^1 I33^2 I33^3)^(1/3), exact when the three selections n w have the same shape;
+    no shot noise is subtracted (pairs of legs on the same tracer would carry one).  Pinned by:
+    three equal tracers give the auto estimator; a copy of tracer A translated by whole cells on
+    leg 3 multiplies each closed triple by the phase exp(-i q3.d) (explicit enumeration, tests)."""
+    from . import power as P
+
+    fields, i33 = [], 1.0
+    for data, rnd in tracers:
+        sc = P.catalog_scalars(data, rnd, spec["box"])
+        meshes = P.fkp_meshes(spec, data, rnd, sc)
+        fields.append(P.fields_plain(spec, meshes, [0])[0][0])
+        i33 *= sc["I33"]
+    i33 = i33 ** (1.0 / 3.0)
+    n = spec["n"]
+    tri = triangles(kbins)
+    prs = pairs(kbins)
+    ind = shell_fields(spec, None, kbins, ones=True)
+    nt = np.array([np.sum(ind[i] * ind[j] * ind[k]) for i, j, k in tri]) / n**3
+    f2 = shell_fields(spec, fields[1], kbins)
+    f3 = shell_fields(spec, fields[2], kbins)
+    B = {}
+    for ell in scoc_ells:
+        f1 = shell_fields(spec, los_field(spec, fields[0], ell), kbins)
+        s = np.array([np.sum(f1[i] * f2[j] * f3[k]) for i, j, k in tri]) / n**3
+        with np.errstate(invalid="ignore", divide="ignore"):
+            B[ell] = np.where(nt > 0, (2 * ell + 1) * s / (i33 * np.where(nt > 0, nt, 1.0)), 0.0)
+    f1 = shell_fields(spec, fields[0], kbins)
+    _, cnt = M.bin_average(np.zeros((n, n, n)), M.bin_index(n, spec["box"], *kbins)[0], kbins[2])
+    BB = {}
+    for ell in tripo_ells:
+        g = np.real(np.fft.ifftn(los_field(spec, fields[2], ell))) * n**3
+        s = np.array([np.sum(f1[i] * f2[j] * g) for i, j in prs]) / n**3
+        ni, nj = cnt[prs[:, 0]], cnt[prs[:, 1]]
+        with np.errstate(invalid="ignore", divide="ignore"):
+            BB[ell] = np.where(ni * nj > 0, (2 * ell + 1) * s / (i33 * ni * nj), 0.0)
+    return dict(tri=tri, pairs=prs, B=B, BB=BB, NT=nt, I33=i33, fields=fields)
+
+
 def all_pairs_product(nb):
     return list(itertools.product(range(nb), range(nb)))
