@@ -237,6 +237,42 @@ def bispectrum(spec, data, randoms, kbins, scoc_ells=(0, 2), tripo_ells=(0, 2), 
     return res
 
 
+def odd_multipoles(spec, data, randoms, kbins, ells=(1, 3)):
+    """Odd Scoccimarro multipoles B_1, B_3 (raw), l on leg 1: X_l is anti-Hermitian for odd l, so its
+    shell fields are imaginary, i A_b(x), and the closure sum is i sum_x A_i F_j F_k; B_l reports the
+    imaginary part, (2l+1)/(I33 N_T) sum_x A_i F_j F_k / n^3 (reading, as for the odd P_l of Sec. 2.1).
+    X_l is the Yamamoto field F_l of Eq. hand (line of sight to each grid point) in survey geometry,
+    L_l(qhat . los) X_0 with a global line of sight.  Pinned by: the enumeration of the closed
+    triples (global line of sight, tiny mesh) and the global-line-of-sight limit of a distant
+    observer (tests)."""
+    from . import power as P
+
+    sc = P.catalog_scalars(data, randoms, spec["box"])
+    meshes = P.fkp_meshes(spec, data, randoms, sc)
+    endpoint = spec.get("los", "endpoint") != "global"
+    if endpoint:
+        fields, _ = P.fields_plain(spec, meshes, sorted(set(ells) | {0}))
+        X0, Xl = fields[0], {ell: fields[ell] for ell in ells}
+    else:
+        X0 = P.fields_plain(spec, meshes, [0])[0][0]
+        Xl = {ell: los_field(spec, X0, ell) for ell in ells}
+    n = spec["n"]
+    b, _ = M.bin_index(n, spec["box"], *kbins)
+    tri = triangles(kbins)
+    f0 = shell_fields(spec, X0, kbins)
+    ind = shell_fields(spec, None, kbins, ones=True)
+    nt = np.array([np.sum(ind[i] * ind[j] * ind[k]) for i, j, k in tri]) / n**3
+    out = {}
+    for ell in ells:
+        a = np.empty((kbins[2], n, n, n))
+        for ib in range(kbins[2]):
+            a[ib] = np.imag(np.fft.ifftn(np.where(b == ib, Xl[ell], 0.0))) * n**3
+        s = np.array([np.sum(a[i] * f0[j] * f0[k]) for i, j, k in tri]) / n**3
+        with np.errstate(invalid="ignore", divide="ignore"):
+            out[ell] = np.where(nt > 0, (2 * ell + 1) * s / (sc["I33"] * np.where(nt > 0, nt, 1.0)), 0.0)
+    return dict(tri=tri, B=out, NT=nt, X0=X0, Xl=Xl, I33=sc["I33"])
+
+
 def cross_bispectrum(spec, tracers, kbins, scoc_ells=(0, 2), tripo_ells=(0,)):
     """Multi-tracer bispectra, global line of sight, raw estimates: tracer t_1 on leg 1 (k1, which
     carries the line of sight of B_l), t_2 on leg 2, t_3 on leg 3, ``tracers`` = three (data,

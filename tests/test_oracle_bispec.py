@@ -392,3 +392,48 @@ def test_cross_bispectrum_identities():
             want.append((2 * ell + 1) * np.real(np.sum(np.where(inb, v, 0.0))) / (cross["I33"] * nt) if nt > 0 else 0.0)
         scale = np.max(np.abs(auto["B"][0]))
         assert np.max(np.abs(cross["B"][ell] - np.array(want))) < 1e-10 * scale, ell
+
+
+def test_odd_multipoles_enumeration_and_distant_observer():
+    """B_1, B_3 (imaginary part of the closure sum with the odd field on leg 1): equal to the
+    explicit enumeration of the closed triples with a global line of sight, and, in survey geometry,
+    to the global-line-of-sight form when the observer is far away (a nearby one changes B_1)."""
+    from oracle import harmonics as Hm
+
+    n, box = 16, 300.0
+    kb = (0.02, 0.02, 3)
+    cat = make_periodic_catalog(4000, box, 16, seed=11)
+    spec = dict(_periodic_spec(n, box), los_dir=(1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0))
+    res = B.odd_multipoles(spec, cat, None, kb)
+    X = res["X0"]
+    b, lists = B._mode_lists(spec, kb)
+    d = np.asarray(spec["los_dir"])
+    for ell in (1, 3):
+        want = []
+        for (i, j, k), nt in zip(res["tri"], res["NT"]):
+            q1, q2 = lists[i], lists[j]
+            q3 = -(q1[:, None, :] + q2[None, :, :])
+            inb = (b[q3[..., 0] % n, q3[..., 1] % n, q3[..., 2] % n] == k) & np.all(np.abs(q3) < n // 2, axis=-1)
+            i1, i2, i3 = q1 % n, q2 % n, q3 % n
+            mu1 = (q1 @ d) / np.linalg.norm(q1, axis=1)
+            v = (Hm.legendre(ell, mu1) * X[i1[:, 0], i1[:, 1], i1[:, 2]])[:, None] * X[i2[:, 0], i2[:, 1], i2[:, 2]][None, :]
+            v = v * X[i3[..., 0], i3[..., 1], i3[..., 2]]
+            want.append((2 * ell + 1) * np.imag(np.sum(np.where(inb, v, 0.0))) / (res["I33"] * nt) if nt > 0 else 0.0)
+        scale = np.max(np.abs(res["B"][ell]))
+        assert scale > 0 and np.max(np.abs(res["B"][ell] - np.array(want))) < 1e-10 * scale, ell
+    # survey geometry: distant observer -> global line of sight along the box direction
+    boxs, kbs = 600.0, (0.011, 0.0135, 3)
+    dd = np.ones(3) / np.sqrt(3.0)
+    out = {}
+    for dist in (1.0e8, 900.0):
+        g, r, origin = make_survey_catalogs(3000, 30000, boxs, dist, 12, seed=23, fkp_p0=1e4, dtype=np.float64)
+        common = dict(n=20, box=boxs, origin=tuple(origin), assign=3, interlace=1, periodic=0)
+        ep = B.odd_multipoles(dict(common, los="endpoint", observer=(0.0, 0.0, 0.0)), g, r, kbs)
+        gl = B.odd_multipoles(dict(common, los="global", los_dir=tuple(dd)), g, r, kbs)
+        out[dist] = (ep, gl)
+    ep, gl = out[1.0e8]
+    for ell in (1, 3):
+        sc = np.max(np.abs(gl["B"][ell]))
+        assert np.max(np.abs(ep["B"][ell] - gl["B"][ell])) < 1e-4 * sc, ell
+    ep, gl = out[900.0]
+    assert np.max(np.abs(ep["B"][1] - gl["B"][1])) > 1e-2 * np.max(np.abs(gl["B"][1]))
