@@ -14,8 +14,11 @@ Modules
              symmetry-reduced form (Eqs. new_F_ell, pk_final), two-index P_ll' and the modified
              multipoles P_4b, P_6b, P_8b (Eqs. Plnew, Pllp).
   bispec     Scoccimarro B_l (Eq. bi_sco), brute-force triangle sums, the compressed TripoSH
-             estimator B_l0l (Eq. new_bispec) in its collapsed and explicit-3j forms.
-  shot       analytic bispectrum shot noise (Sec. 5.4).
+             estimator B_l0l (Eq. new_bispec) in its collapsed and explicit-3j forms, odd B_1, B_3,
+             multi-tracer bispectra.
+  sugiyama   Sugiyama TripoSH B_l1l2L (Eq. sugi_estimator) with every sub-configuration, its
+             analytic (Lemma 1) and FFT-method shot noise.
+  shot       analytic and FFT-method bispectrum shot noise (Sec. 5.4).
   adjoint    gradients of P_l and equilateral B_0 with respect to the density mesh.
 
 Parity status of each function is stated in its docstring ("pinned by ..." or "parity unpinned").
