@@ -667,6 +667,8 @@ npc_status launch_paint(npc_ctx* ctx, const DevCatalog& d, const DevCatalog* r, 
 // above, but its scratch (the per-block partial sums and the 16 scalar slots) lives in a
 // file-scope device array instead of context workspace, so the call allocates nothing.
 // ---------------------------------------------------------------------------------------------
+#include <cuda.h>
+
 #include <mutex>
 
 namespace {
@@ -682,7 +684,40 @@ static __device__ __align__(256) double g_noalloc_scratch[2 * NOALLOC_PART + SC_
 
 constexpr int NOALLOC_MAX_DEVICES = 64;
 std::mutex g_noalloc_mutex;
-double* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+
+// Address of the static array per device, remembered together with the identity of the context it
+// was looked up in: a cudaDeviceReset (or another context made current) gives the device a new
+// context in which the array may sit elsewhere, so a changed context id triggers a new look-up.
+struct NoallocSlot {
+  double* ptr = nullptr;
+  unsigned long long ctx_id = 0;
+  bool ctx_known = false;
+};
+NoallocSlot g_noalloc_slot[NOALLOC_MAX_DEVICES];
+
+// Identity of the calling thread's current context, through driver entry points the runtime hands
+// out (no link-time dependence on the driver library).  False when there is no current context or
+// the entry points are unavailable; the caller then looks the address up again on every call.
+bool current_context_id(unsigned long long* id) {
+  static decltype(&cuCtxGetCurrent) get_current = nullptr;
+  static decltype(&cuCtxGetId) get_id = nullptr;
+  static bool resolved = false;
+  if (!resolved) {
+    resolved = true;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", (void**)&get_current, 12000, cudaEnableDefault, &q1) !=
+            cudaSuccess || q1 != cudaDriverEntryPointSuccess)
+      get_current = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", (void**)&get_id, 12000, cudaEnableDefault, &q2) !=
+            cudaSuccess || q2 != cudaDriverEntryPointSuccess)
+      get_id = nullptr;
+    cudaGetLastError();
+  }
+  if (!get_current || !get_id) return false;
+  CUcontext c = nullptr;
+  if (get_current(&c) != CUDA_SUCCESS || !c) return false;
+  return get_id(c, id) == CUDA_SUCCESS;
+}
 
 npc_status noalloc_err(char* err, size_t errlen, npc_status s, const char* msg) {
   if (err && errlen) {
@@ -719,19 +754,26 @@ extern "C" npc_status npc_catalog_scalars_noalloc(const npc_catalog* data, const
   }
   double* scratch;
   {
-    // One-time set-up per device, with that device current: host code cannot take the address
-    // of a __device__ array directly, so ask the runtime for it.
+    // Set-up per device and context, with that device current: host code cannot take the address
+    // of a __device__ array directly, so ask the runtime for it (done on the first call on a
+    // device, and again only after that device's context has changed).
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_ptr[dev]) {
+    NoallocSlot& slot = g_noalloc_slot[dev];
+    unsigned long long id = 0;
+    const bool known = current_context_id(&id);
+    if (!slot.ptr || !known || !slot.ctx_known || slot.ctx_id != id) {
       void* p = nullptr;
       const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
       if (e != cudaSuccess || !p) {
         cudaGetLastError();
+        slot = NoallocSlot{};
         return noalloc_err(err, errlen, NPC_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed");
       }
-      g_noalloc_ptr[dev] = static_cast<double*>(p);
+      slot.ptr = static_cast<double*>(p);
+      // the look-up makes the device's primary context current when none was
+      slot.ctx_known = current_context_id(&slot.ctx_id);
     }
-    scratch = g_noalloc_ptr[dev];
+    scratch = slot.ptr;
   }
   cudaStream_t st = (cudaStream_t)cuda_stream;
   const int64_t nmax = std::max<int64_t>(data->n, randoms ? randoms->n : 0);
@@ -751,7 +793,9 @@ extern "C" npc_status npc_catalog_scalars_noalloc(const npc_catalog* data, const
       k_cat_partials<float><<<nblk, RED_THREADS, 0, st>>>((const float*)k->w, (const float*)k->nbar, k->n, part);
   }
   k_cat_final<<<1, 32, 0, st>>>(part_d, part_r, nblk, randoms ? 1 : 0, box, sc);
-  cudaError_t e = cudaGetLastError();
+  // peek, not get: an error that the caller's earlier asynchronous work left pending is reported
+  // as this call's failure but stays pending for the caller to read
+  cudaError_t e = cudaPeekAtLastError();
   if (e == cudaSuccess) e = cudaMemcpyAsync(out_device, sc, 8 * sizeof(double), cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return noalloc_err(err, errlen, NPC_ERR_CUDA, cudaGetErrorString(e));
   return NPC_OK;

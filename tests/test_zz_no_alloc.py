@@ -59,6 +59,42 @@ def test_noalloc_matches_context_entry_point(dtype):
     del keep1, keep2, keep3
 
 
+def test_noalloc_many_blocks():
+    """5.5e6 objects: the call reduces over more blocks (1,221) than the context call's fixed 1,024,
+    so the two trees differ; the results still agree to rounding, and two calls agree bit for bit."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    ensure_built()
+    from paper_2605_04864_gb300 import binding as B
+
+    torch.cuda.set_device(0)
+    g, r, _ = make_survey_catalogs(500_000, 5_000_000, 1500.0, 2000.0, 32, seed=93, fkp_p0=1e4)
+    dg, keep1 = _dev_catalog(B, g, torch, np.float32)
+    dr, keep2 = _dev_catalog(B, r, torch, np.float32)
+    ctx = C.c_void_p()
+    B.check(B.npc_create(C.byref(ctx), 0, None))
+    try:
+        ref = torch.zeros(8, dtype=torch.float64, device="cuda")
+        B.check(B.npc_catalog_scalars(ctx, C.byref(dg), C.byref(dr), 1500.0, C.c_void_p(ref.data_ptr()), 1), ctx)
+        torch.cuda.synchronize()
+        want = ref.cpu().numpy()
+        outs = []
+        for _ in range(2):
+            got = torch.full((8,), np.nan, dtype=torch.float64, device="cuda")
+            err = C.create_string_buffer(256)
+            st = B.npc_catalog_scalars_noalloc(C.byref(dg), C.byref(dr), 1500.0, C.c_void_p(got.data_ptr()),
+                                               None, err, 256)
+            assert st == 0, err.value
+            torch.cuda.synchronize()
+            outs.append(got.cpu().numpy())
+            np.testing.assert_allclose(outs[-1], want, rtol=1e-12, atol=0)
+        np.testing.assert_array_equal(outs[0], outs[1])
+    finally:
+        B.npc_destroy(ctx)
+    del keep1, keep2
+
+
 def test_noalloc_rejects_host_pointers_and_oversize():
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
