@@ -69,22 +69,24 @@ def fkp_meshes(spec, data, randoms, scalars, weight_power=1):
     weight_power = 1: F = sum_g w W - alpha sum_r w W (periodic: minus the mean).
     weight_power = 2: the N-field sum_g w^2 W + alpha^2 sum_r w^2 W used by the shot noise (Sec. 5.2).
     """
-    n, box, origin, assign = spec["n"], spec["box"], spec["origin"], spec["assign"]
     shifts = (0.0, 0.5) if spec.get("interlace", 0) else (0.0,)
-    out = []
-    for sh in shifts:
-        sg = M.grid_coords(data.pos, origin, box, n, sh)
-        wg = np.asarray(data.w, dtype=np.float64) ** weight_power
-        mesh = M.paint(sg, wg, n, assign)
-        if randoms is not None:
-            sr = M.grid_coords(randoms.pos, origin, box, n, sh)
-            coef = -scalars["alpha"] if weight_power == 1 else scalars["alpha"] ** 2
-            wr = coef * np.asarray(randoms.w, dtype=np.float64) ** weight_power
-            mesh = mesh + M.paint(sr, wr, n, assign)
-        elif weight_power == 1:
-            mesh = mesh - _fsum(wg) / n**3
-        out.append(mesh)
-    return out
+    return [fkp_mesh_phase(spec, data, randoms, scalars, sh, weight_power) for sh in shifts]
+
+
+def fkp_mesh_phase(spec, data, randoms, scalars, shift, weight_power=1):
+    """One phase of ``fkp_meshes``: grid coordinates shifted by ``shift`` cells (0 or 1/2)."""
+    n, box, origin, assign = spec["n"], spec["box"], spec["origin"], spec["assign"]
+    sg = M.grid_coords(data.pos, origin, box, n, shift)
+    wg = np.asarray(data.w, dtype=np.float64) ** weight_power
+    mesh = M.paint(sg, wg, n, assign)
+    if randoms is not None:
+        sr = M.grid_coords(randoms.pos, origin, box, n, shift)
+        coef = -scalars["alpha"] if weight_power == 1 else scalars["alpha"] ** 2
+        wr = coef * np.asarray(randoms.w, dtype=np.float64) ** weight_power
+        mesh = mesh + M.paint(sr, wr, n, assign)
+    elif weight_power == 1:
+        mesh = mesh - _fsum(wg) / n**3
+    return mesh
 
 
 def _xhat_dirs(spec, shift_cells):
@@ -311,3 +313,178 @@ def direct_dft(pos, weights, kvecs, origin):
     x = np.asarray(pos, dtype=np.float64) - np.asarray(origin, dtype=np.float64)
     ph = np.asarray(kvecs) @ x.T
     return np.exp(-1j * ph) @ np.asarray(weights, dtype=np.float64)
+
+
+class HalfSpectrumPower:
+    """Symmetric-form multipoles (Eqs. new_F_ell, F_and_new_G, pk_final, Pllp, Plnew) evaluated on
+    the half Fourier grid of real-to-complex transforms, for meshes too large for the full-grid
+    forms above (the 512^3 survey workload).
+
+    For m >= 0 the weighted field F(x) Y_l^m(xhat) is split into its real and imaginary parts, whose
+    transforms A_l^m, B_l^m are Hermitian, so S_l^m = A_l^m + i B_l^m.  Inserting G_l of
+    Eq. new_F_ell into the space inversion of Eq. F_and_new_G, with Y_l^m(-khat) = (-1)^l Y_l^m(khat)
+    (Eq. sph_prop) and S_l^m(-k)^* = A_l^m(k) - i B_l^m(k), gives at every mode
+        F_l(k) = 4 pi/(2l+1) [Y_l^0 A_l^0 + 2 sum_{m>=1} (Re Y_l^m(khat) A_l^m + Im Y_l^m(khat) B_l^m)],
+    which obeys F_l(-k) = (-1)^l F_l(k)^*.  Hence for a mode pair (k, -k) both members carry the
+    same Re F_0 F_l^* (even l), Im F_0 F_l^* (odd l) and Re F_l F_l'^*: a stored mode with
+    0 < k_z < k_N stands for two modes of the full grid, a mode of the k_z = 0 plane for one (that
+    plane holds both members of each pair); the Nyquist planes and DC are excluded as in
+    ``mesh.bin_index``.  Interlacing and the compensation 1/W are per-mode factors, so each phase
+    accumulates its own F_l before the phases are combined.  Same outputs as ``power_multipoles``.
+
+    The work is a fixed list of stages (``stages()``): catalogue scalars and the painting of each
+    interlacing phase, then one stage per phase and (l, m >= 0) pair (the Y_l^m-weighted transforms
+    and their accumulation), then the phase combination and the binning.  ``workers`` is passed to
+    scipy.fft.
+
+    Pinned by tests/test_oracle_power.py: equal to the full-grid Hand+17 form (Eq. hand) and to
+    the full-grid symmetric form to rounding, for even and odd l, the two-index and modified
+    multipoles, endpoint and global lines of sight, CIC and interlaced TSC, meshes of 2^k and
+    3 * 2^k cells."""
+
+    def __init__(self, spec, data, randoms, kbins, ells=(0, 2, 4), modified=(), two_index=(),
+                 workers=None):
+        self.spec, self.data, self.randoms, self.kbins = spec, data, randoms, kbins
+        self.ells = tuple(ells)
+        self.modified = tuple(modified)
+        self.two_index = tuple(tuple(p) for p in two_index)
+        self.workers = workers
+        need = set(self.ells) | {0}
+        if self.modified:
+            need |= {2, 4}
+        for a, c in self.two_index:
+            need |= {a, c}
+        self.need = sorted(need)
+        self.nph = 2 if spec.get("interlace", 0) else 1
+        self.meshes = [None] * self.nph
+        self.acc = [{} for _ in range(self.nph)]
+        self.dirs = None
+        self.result = None
+
+    # --- half-grid geometry -------------------------------------------------------------------
+    def _half_ints(self):
+        n = self.spec["n"]
+        ii = M.int_freqs(n)
+        iz = np.arange(n // 2 + 1)
+        return ii[:, None, None], ii[None, :, None], iz[None, None, :]
+
+    def _khat_half(self):
+        ix, iy, iz = self._half_ints()
+        return np.stack(np.broadcast_arrays(ix, iy, iz), axis=-1).astype(np.float64)
+
+    def _rfft(self, x):
+        import scipy.fft as sfft
+
+        return sfft.rfftn(x, workers=self.workers)
+
+    # --- stages --------------------------------------------------------------------------------
+    def stages(self):
+        out = []
+        for ph in range(self.nph):
+            out.append((f"paint phase {ph}", lambda ph=ph: self._paint(ph)))
+        for ph in range(self.nph):
+            last = None
+            for ell in self.need:
+                for m in range(0, ell + 1):
+                    last = (ell, m)
+            for ell in self.need:
+                for m in range(0, ell + 1):
+                    out.append((f"transform phase {ph} l={ell} m={m}",
+                                lambda ph=ph, ell=ell, m=m, fin=((ell, m) == last): self._transform(ph, ell, m, fin)))
+        out.append(("combine and bin", self._finish))
+        return out
+
+    def _paint(self, ph):
+        if ph == 0:
+            self.scalars = catalog_scalars(self.data, self.randoms, self.spec["box"])
+        self.meshes[ph] = fkp_mesh_phase(self.spec, self.data, self.randoms, self.scalars, 0.5 * ph)
+
+    def _transform(self, ph, ell, m, last):
+        if self.dirs is None:
+            self.dirs = _xhat_dirs(self.spec, 0.5 * ph)
+        y = H.ylm(ell, m, self.dirs)
+        mesh = self.meshes[ph]
+        kh = self._khat_half()
+        yk = H.ylm(ell, m, kh)
+        del kh
+        c = 4.0 * pi / (2 * ell + 1) * (1.0 if m == 0 else 2.0)
+        term = c * np.real(yk) * self._rfft(mesh * np.real(y))
+        if m > 0:
+            term += c * np.imag(yk) * self._rfft(mesh * np.imag(y))
+        del y, yk
+        if ell in self.acc[ph]:
+            self.acc[ph][ell] += term
+        else:
+            self.acc[ph][ell] = term
+        if last:
+            self.dirs = None
+            self.meshes[ph] = None
+
+    def _finish(self):
+        spec, n = self.spec, self.spec["n"]
+        ix, iy, iz = self._half_ints()
+        a = np.pi / n
+        p = spec["assign"]
+
+        def sinc_p(i):
+            x = a * i.astype(np.float64)
+            return np.where(i == 0, 1.0, np.sin(x) / np.where(i == 0, 1.0, x)) ** p
+
+        win = sinc_p(ix) * sinc_p(iy) * sinc_p(iz)
+        if self.nph == 2:
+            ph = np.exp(1j * a * (ix + iy + iz))
+            F = {ell: 0.5 * (self.acc[0][ell] + ph * self.acc[1][ell]) / win for ell in self.need}
+            del ph
+        else:
+            F = {ell: self.acc[0][ell] / win for ell in self.need}
+        self.acc = None
+        kmin, dk, nb = self.kbins
+        kf = 2.0 * np.pi / spec["box"]
+        n2 = (ix * ix + iy * iy + iz * iz).astype(np.float64)
+        kmag = kf * np.sqrt(n2)
+        b = np.floor((kmag - kmin) / dk)
+        ok = (b >= 0) & (b < nb) & (n2 > 0)
+        ok &= (ix != -(n // 2)) & (iy != -(n // 2)) & (iz != n // 2)
+        wgt = (np.where(iz == 0, 1.0, 2.0) * ok).ravel()
+        bb = np.where(ok, b, 0).astype(np.int64).ravel()
+        cnt = np.bincount(bb, weights=wgt, minlength=nb)
+        ksum = np.bincount(bb, weights=wgt * np.broadcast_to(kmag, ok.shape).ravel(), minlength=nb)
+        empty = cnt == 0
+        safe = np.where(empty, 1.0, cnt)
+
+        def bin_mean(v):
+            return np.bincount(bb, weights=wgt * v.ravel(), minlength=nb) / safe
+
+        sc = self.scalars
+        i22, n0 = sc["I22"], sc["N0"]
+        res = {"P": {}, "Pll": {}, "Pmod": {}, "k_eff": np.where(empty, 0.0, ksum / safe), "nmodes": cnt,
+               "scalars": sc}
+        internal = sorted(set(self.ells) | ({0, 2, 4} if self.modified else set()))
+        pl = {}
+        for ell in internal:
+            mean = bin_mean(_part(ell, F[0] * np.conj(F[ell])))
+            pl[ell] = np.where(empty, 0.0, (2 * ell + 1) / i22 * mean - (n0 if ell == 0 else 0.0))
+        for ell in self.ells:
+            res["P"][ell] = pl[ell]
+        need2 = set(self.two_index)
+        if self.modified:
+            need2 |= {(2, 2), (4, 2), (4, 4)}
+        for (l1, l2) in sorted(need2):
+            mean = bin_mean(np.real(F[l1] * np.conj(F[l2])))
+            res["Pll"][(l1, l2)] = np.where(empty, 0.0, (2 * (l1 + l2) + 1) / i22 * mean
+                                            - n_shot_two_index(l1, l2, n0))
+        for lb in self.modified:
+            acc = 0.0
+            for key, coef in PLB_COEFFS[lb].items():
+                acc = acc + float(coef) * (pl[key[1]] if key[0] == 0 else res["Pll"][key])
+            res["Pmod"][lb] = acc
+        self.result = res
+
+
+def power_multipoles_rfft(spec, data, randoms, kbins, ells=(0, 2, 4), modified=(), two_index=(),
+                          workers=None):
+    """Catalogue -> binned multipoles by ``HalfSpectrumPower`` (every stage in order)."""
+    run = HalfSpectrumPower(spec, data, randoms, kbins, ells, modified, two_index, workers)
+    for _, stage in run.stages():
+        stage()
+    return run.result

@@ -325,3 +325,49 @@ def test_odd_cross_multipoles_of_a_shifted_copy():
     auto = P.power_multipoles(spec, a, None, kb, (0, 1, 3))
     for ell in (1, 3):
         assert np.max(np.abs(auto["P"][ell])) < 1e-12 * np.max(np.abs(auto["P"][0]))
+
+
+@pytest.mark.parametrize("n,assign,interlace,los", [(24, 2, 0, "endpoint"), (32, 3, 1, "endpoint"),
+                                                    (48, 3, 1, "endpoint"), (32, 3, 1, "global")])
+def test_half_spectrum_form_equals_full_grid(small_survey, n, assign, interlace, los):
+    """The half-spectrum (real-to-complex) evaluation of the symmetric form gives, for every
+    multipole (even and odd l, the two-index P_ll' and the modified P_lb), the values of the
+    full-grid Hand+17 sum over all 2l+1 values of m (Eq. hand), and the same mode counts and k_eff:
+    meshes of 2^k and 3 * 2^k cells, CIC without and TSC with interlacing, both lines of sight."""
+    g, r, origin = small_survey
+    spec = _survey_spec(n, 1000.0, origin, assign, interlace)
+    if los == "global":
+        spec.update(los="global", los_dir=(1.0, 2.0, 2.0))
+    kb = (0.0, 0.01, int(np.pi * n / 1000.0 / 0.01))
+    ells = (0, 1, 2, 3, 4)
+    two = ((2, 2), (4, 2), (4, 4))
+    a = P.power_multipoles(spec, g, r, kb, ells, (4, 6, 8), method="plain")
+    b = P.power_multipoles_rfft(spec, g, r, kb, ells, (4, 6, 8), two_index=two)
+    np.testing.assert_array_equal(a["nmodes"], b["nmodes"])
+    np.testing.assert_allclose(a["k_eff"], b["k_eff"], rtol=1e-13, atol=0)
+    scale = np.abs(a["P"][0]) + a["scalars"]["N0"]
+    for ell in ells:
+        assert np.max(np.abs(a["P"][ell] - b["P"][ell]) / scale) < 1e-12, ell
+    for lb in (4, 6, 8):
+        assert np.max(np.abs(a["Pmod"][lb] - b["Pmod"][lb]) / scale) < 1e-12, lb
+    for key in two:
+        assert np.max(np.abs(a["Pll"][key] - b["Pll"][key]) / scale) < 1e-12, key
+    if los == "endpoint":
+        assert np.max(np.abs(b["P"][1]) / scale) > 1e-8     # the odd terms compared are not all zero
+
+
+def test_half_spectrum_stages_are_the_pipeline(small_survey):
+    """The stage list runs the painting of each phase, one stage per phase and (l, m >= 0), then
+    the binning: 2 + 2 * 9 + 1 stages for P_0,2,4 with interlacing (Table 1: 9 transforms per
+    phase), and running them one by one gives the function's result."""
+    g, r, origin = small_survey
+    spec = _survey_spec(16, 1000.0, origin, 3, 1)
+    kb = (0.0, 0.02, 2)
+    run = P.HalfSpectrumPower(spec, g, r, kb, (0, 2, 4), (4,))
+    st = run.stages()
+    assert len(st) == 2 + 2 * 9 + 1
+    for _, f in st:
+        f()
+    ref = P.power_multipoles_rfft(spec, g, r, kb, (0, 2, 4), (4,))
+    for ell in (0, 2, 4):
+        np.testing.assert_array_equal(run.result["P"][ell], ref["P"][ell])
