@@ -14,6 +14,7 @@ from .catalogs import (  # noqa: F401
     Catalog,
     make_survey_catalogs,
     make_periodic_catalog,
+    fingerprint,
 )
 from .configs import WORKLOADS, workload  # noqa: F401
 from .batch import batch_plan, base_catalogues  # noqa: F401

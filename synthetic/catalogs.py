@@ -131,3 +131,18 @@ def make_periodic_catalog(n_gal, box, n_gen, seed, kaiser=0.8, dtype=np.float32)
     pos = lognormal_positions(n_gal, box, n_gen, seed, kaiser=kaiser)
     nbar = n_gal / box**3
     return Catalog(pos.astype(dtype), np.ones(n_gal, dtype), np.full(n_gal, nbar, dtype))
+
+
+def fingerprint(*catalogs):
+    """SHA-256 of the catalogues' arrays (positions, weights, densities, in order): identifies the
+    exact inputs a stored set of expected values was computed from."""
+    import hashlib
+
+    h = hashlib.sha256()
+    for c in catalogs:
+        for a in (c.pos, c.w, c.nbar):
+            a = np.ascontiguousarray(a)
+            h.update(str(a.dtype).encode())
+            h.update(str(a.shape).encode())
+            h.update(a.tobytes())
+    return h.hexdigest()

@@ -2,7 +2,7 @@
 import numpy as np
 import pytest
 
-from helpers import ensure_built
+from helpers import ensure_built, golden_module, stored_or_live
 from oracle import bispec as OB
 from synthetic import make_periodic_catalog, workload
 
@@ -195,41 +195,44 @@ def test_bispectrum_rejects(api):
 
 
 @pytest.mark.slow
-def test_full_size_256_sampled_triangles(api):
-    """Full 256^3 workload (1e6 particles, 19 bins): B_0, B_2 and N_T of a few triangles the oracle
-    computes one by one from its own shell fields."""
-    w = workload("bispec_256")
-    cat = make_periodic_catalog(w["n_gal"], w["box"], w["n_gen"], seed=w["seed"])
+def test_full_size_256_all_triangles(api):
+    """The bench workload in full (256^3, 1e6 particles, 19 bins): all 805 closed triangles of B_0,
+    B_2 and N_T and all 190 pairs of B_000, B_202, with their analytic shot noise, against the
+    oracle (stored by tests/golden/make_full_size.py, re-evaluated here if this machine generates
+    different input bytes).  Float32 shell fields: the rounded triangle count can miss the exact
+    integer by about 1e-5 of itself for the largest shells; B within 1e-4 of the monopole scale."""
+    from synthetic import fingerprint
+
+    gm = golden_module()
+    w, cat, spec = gm.bispec_inputs()
+
+    def live():
+        o = gm.bispec_oracle(w, cat, spec)
+        return {"tri": o["tri"], "pairs": o["pairs"], "NT": o["NT"],
+                "B_raw": {str(l): v for l, v in o["B"].items()}, "shot_B": {str(l): v for l, v in o["shot_B"].items()},
+                "BB_raw": {str(l): v for l, v in o["BB"].items()},
+                "shot_BB": {str(l): v for l, v in o["shot_BB"].items()}}
+
+    orc, _ = stored_or_live(gm.BISPEC_FILE, fingerprint(cat), live)
     kb = (w["kmin"], w["dk"], w["nbins"])
     res = api.bispectrum(cat, n=256, box=w["box"], kbins=kb, precision="mixed")
-    spec = _spec(256, w["box"])
-    from oracle import power as P
-
-    sc = P.catalog_scalars(cat, None, w["box"])
-    meshes = P.fkp_meshes(spec, cat, None, sc)
-    X0 = P.fields_plain(spec, meshes, [0])[0][0]
-    del meshes
-    tri = res["tri"]
-    picks = [0, len(tri) // 2, len(tri) - 1]
-    bins = sorted({int(b) for t in picks for b in tri[t]})
-    from oracle import mesh as M
-
-    b_idx, _ = M.bin_index(256, w["box"], *kb)
-    X2 = OB.los_field(spec, X0, 2)
-    f0, f2, ind = {}, {}, {}
-    for b in bins:
-        mask = b_idx == b
-        f0[b] = np.real(np.fft.ifftn(np.where(mask, X0, 0))) * 256**3
-        f2[b] = np.real(np.fft.ifftn(np.where(mask, X2, 0))) * 256**3
-        ind[b] = np.real(np.fft.ifftn(mask.astype(float))) * 256**3
-    for t in picks:
-        i, j, k = (int(v) for v in tri[t])
-        nt = np.sum(ind[i] * ind[j] * ind[k])
-        b0 = np.sum(f0[i] * f0[j] * f0[k]) / (sc["I33"] * nt)
-        b2 = 5 * np.sum(f2[i] * f0[j] * f0[k]) / (sc["I33"] * nt)
-        # float32 shell fields: the rounded triangle count can be off by ~1e-5 of itself for the
-        # largest shells (it normalises B, whose tolerance is 1e-4)
-        assert res["NT"][t] == pytest.approx(nt / 256**3, rel=5e-5)
-        scale = abs(b0)
-        assert abs(res["B"][0][t] + res["shot_B"][0][t] - b0) < 1e-4 * max(abs(b0), scale)
-        assert abs(res["B"][2][t] + res["shot_B"][2][t] - b2) < 1e-4 * max(abs(b2), scale)
+    np.testing.assert_array_equal(res["tri"], np.asarray(orc["tri"]))
+    assert res["tri"].shape == (805, 3)
+    np.testing.assert_allclose(res["NT"], np.asarray(orc["NT"]), rtol=5e-5, atol=1e-6)
+    b0 = np.asarray(orc["B_raw"]["0"])
+    scale_t = np.abs(b0) + np.abs(np.asarray(orc["shot_B"]["0"]))
+    for l in (0, 2):
+        raw_o = np.asarray(orc["B_raw"][str(l)])
+        e = np.abs(res["B"][l] + res["shot_B"][l] - raw_o) / np.maximum(np.abs(raw_o), scale_t)
+        assert np.max(e) < 1e-4, ("B", l, np.max(e))
+        sh = np.asarray(orc["shot_B"][str(l)])
+        e = np.abs(res["shot_B"][l] - sh) / np.maximum(np.abs(sh), scale_t)
+        assert np.max(e) < 1e-4, ("shot_B", l, np.max(e))
+    scale_p = np.abs(np.asarray(orc["BB_raw"]["0"])) + np.abs(np.asarray(orc["shot_BB"]["0"]))
+    for l in (0, 2):
+        raw_o = np.asarray(orc["BB_raw"][str(l)])
+        e = np.abs(res["BB"][l] + res["shot_BB"][l] - raw_o) / np.maximum(np.abs(raw_o), scale_p)
+        assert np.max(e) < 1e-4, ("BB", l, np.max(e))
+        sh = np.asarray(orc["shot_BB"][str(l)])
+        e = np.abs(res["shot_BB"][l] - sh) / np.maximum(np.abs(sh), scale_p)
+        assert np.max(e) < 1e-4, ("shot_BB", l, np.max(e))

@@ -5,7 +5,7 @@ from types import SimpleNamespace
 import numpy as np
 import pytest
 
-from helpers import ensure_built, p_error
+from helpers import ensure_built, golden_module, p_error, stored_or_live
 from oracle import power as P
 from synthetic import make_periodic_catalog, make_survey_catalogs, workload
 
@@ -192,21 +192,37 @@ def test_invalid_arguments_rejected(api):
 
 
 @pytest.mark.slow
-def test_full_size_512_monopole(api):
-    """Full 512^3 workload (2e6 galaxies, 2e7 randoms, TSC interlaced): P_0 against the oracle,
-    which can afford the single l = 0 transform at this size; P_l binning counts exactly."""
-    w = workload("p024b_mixed_512")
-    g, r, origin = make_survey_catalogs(w["n_gal"], w["n_ran"], w["box"], w["distance"], w["n_gen"],
-                                        seed=w["seed"], fkp_p0=w["fkp_p0"])
+def test_full_size_512_all_multipoles(api):
+    """The bench workload in full (512^3, 2e6 galaxies + 2e7 randoms, TSC interlaced, FKP weights,
+    80 bins): every P_0, P_2, P_4, P_4b, P_6b, P_8b bin against the oracle's half-spectrum form,
+    whose values are stored by tests/golden/make_full_size.py (re-evaluated here if this machine
+    generates different input bytes); N_modes exactly, tolerance 1e-5 in the monopole-scale metric."""
+    from synthetic import fingerprint
+
+    gm = golden_module()
+    w, g, r, spec = gm.power_inputs()
+
+    def live():
+        res = gm.power_oracle(w, g, r, spec)
+        return {"k_eff": res["k_eff"], "nmodes": res["nmodes"], "P": {str(l): v for l, v in res["P"].items()},
+                "Pmod": {str(l): v for l, v in res["Pmod"].items()},
+                "scalars": {k: res["scalars"][k] for k in ("alpha", "I22", "N0")}}
+
+    orc, _ = stored_or_live(gm.POWER_FILE, fingerprint(g, r), live)
     kb = (w["kmin"], w["dk"], w["nbins"])
-    res = api.power_multipoles(g, r, n=512, box=w["box"], origin=origin, assign=3, interlace=1, kbins=kb,
+    res = api.power_multipoles(g, r, n=512, box=w["box"], origin=spec["origin"], assign=3, interlace=1, kbins=kb,
                                ells=(0, 2, 4), modified=(4, 6, 8), precision="mixed")
-    spec = dict(n=512, box=w["box"], origin=tuple(origin), assign=3, interlace=1, los="endpoint",
-                observer=(0.0, 0.0, 0.0))
-    p0, cnt, sc = P.power_monopole_rfft(spec, g, r, kb)
-    np.testing.assert_array_equal(res["nmodes"], cnt)
-    e = p_error(res["P"][0], p0, np.abs(p0) + sc["N0"])
-    assert np.max(e) < 1e-5, np.max(e)
+    np.testing.assert_array_equal(res["nmodes"], np.asarray(orc["nmodes"]))
+    np.testing.assert_allclose(res["k_eff"], np.asarray(orc["k_eff"]), rtol=1e-6, atol=1e-12)
+    for k in ("alpha", "I22", "N0"):
+        assert res["scalars"][k] == pytest.approx(orc["scalars"][k], rel=1e-12)
+    scale = np.abs(np.asarray(orc["P"]["0"])) + orc["scalars"]["N0"]
+    for l in (0, 2, 4):
+        e = p_error(res["P"][l], np.asarray(orc["P"][str(l)]), scale)
+        assert np.max(e) < 1e-5, (l, np.max(e))
+    for l in (4, 6, 8):
+        e = p_error(res["Pmod"][l], np.asarray(orc["Pmod"][str(l)]), scale)
+        assert np.max(e) < 1e-5, ("b", l, np.max(e))
 
 
 @pytest.mark.parametrize("prec,tol,n", [("fp64", 1e-12, 32), ("mixed", 1e-5, 64)])

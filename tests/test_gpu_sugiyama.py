@@ -3,7 +3,7 @@ oracle, which sums every (m1, m2, M) sub-configuration in the catalogue's own fr
 import numpy as np
 import pytest
 
-from helpers import ensure_built
+from helpers import ensure_built, golden_module, stored_or_live
 from oracle import power as P
 from oracle import sugiyama as OS
 from synthetic import make_periodic_catalog
@@ -193,3 +193,30 @@ def test_cached_triangle_counts_survive_a_larger_call(api):
     again = api.bispectrum(cat, n=32, box=300.0, kbins=kb, scoc_ells=(0,), tripo_ells=(0,), precision="fp64")
     np.testing.assert_array_equal(again["NT"], first["NT"])
     np.testing.assert_array_equal(again["B"][0], first["B"][0])
+
+
+@pytest.mark.slow
+def test_full_size_256_sample(api):
+    """The 256^3 bispectrum workload (1e6 particles, 19 bins, line of sight z): TripoSH B_000 and
+    B_202 on all 361 (k1, k2) pairs against the oracle's every-sub-configuration sum (stored by
+    tests/golden/make_full_size.py, re-evaluated here if this machine generates different input
+    bytes); tolerance 1e-4 of the B_000 scale of the pair."""
+    from synthetic import fingerprint
+
+    gm = golden_module()
+    w, cat, spec = gm.bispec_inputs()
+
+    def live():
+        res, cnt = gm.sugiyama_oracle(w, cat, spec)
+        return {"nmodes": cnt, "B_raw": {"".join(str(v) for v in mp): res[mp] for mp in gm.SUGIYAMA_MULTIPOLES}}
+
+    orc, _ = stored_or_live(gm.SUGIYAMA_FILE, fingerprint(cat), live)
+    kb = (w["kmin"], w["dk"], w["nbins"])
+    mps = list(gm.SUGIYAMA_MULTIPOLES)
+    res = api.bispectrum_sugiyama(cat, n=256, box=w["box"], kbins=kb, multipoles=mps, precision="mixed")
+    np.testing.assert_array_equal(res["nmodes"], np.asarray(orc["nmodes"]))
+    scale = np.abs(np.asarray(orc["B_raw"]["000"]))
+    for mp in mps:
+        want = np.asarray(orc["B_raw"]["".join(str(v) for v in mp)])
+        e = np.abs(res["B"][mp] - want) / np.maximum(np.abs(want), scale)
+        assert np.max(e) < 1e-4, (mp, np.max(e))
