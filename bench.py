@@ -193,50 +193,208 @@ def algorithmic_bytes(w, stage, nf):
     return 0
 
 
-def cpu_baseline(w, sample_n=128):
-    """The FP64 oracle as it stands on a bounded sample: same geometry, mesh sample_n^3 and the
-    particle counts scaled by (sample_n/n)^3 (same particles per cell); rate scaled to 512^3 by
-    (n/sample_n)^3 * log(n^3)/log(sample_n^3) (transform-dominated)."""
+def _cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def _power_spec(w, origin):
+    return dict(n=w["n"], box=w["box"], origin=tuple(float(v) for v in origin), assign=w["assign"],
+                interlace=w["interlace"], los="endpoint", observer=(0.0, 0.0, 0.0))
+
+
+def cpu_baseline(w, g, r, origin):
+    """The FP64 oracle's half-spectrum pipeline (oracle.power.HalfSpectrumPower: painting of each
+    interlacing phase, one stage per phase and (l, m >= 0) with its Y_lm-weighted real-to-complex
+    transforms, then interlacing, compensation and binning) on the bench's own catalogues at the full
+    512^3 configuration, scipy.fft with every available core.  A bounded sample of its stages is
+    timed: the painting of phase 0, one one-transform stage (l = 0, m = 0), one two-transform stage
+    (l = 2, m = 1) and the binning stage (run on accumulators of the full set's shapes: its cost does
+    not depend on the values).  The measurement's time is the sum over all stages of the timed
+    stage of the same kind (each phase paints the whole catalogue; m = 0 stages make one transform,
+    m > 0 stages two)."""
+    from oracle import power as P
+
+    cores = _cores()
+    spec = _power_spec(w, origin)
+    kb = (w["kmin"], w["dk"], w["nbins"])
+    run = P.HalfSpectrumPower(spec, g, r, kb, w["ells"], w["modified"], workers=cores)
+    stages = dict(run.stages())
+    timed = {}
+
+    def tick(name, f):
+        t0 = time.perf_counter()
+        f()
+        timed[name] = time.perf_counter() - t0
+
+    tick("paint", stages["paint phase 0"])
+    tick("transform_m0", stages["transform phase 0 l=0 m=0"])
+    tick("transform_m1", stages["transform phase 0 l=2 m=1"])
+    have = run.acc[0][2]
+    for ph in range(run.nph):
+        for ell in run.need:
+            run.acc[ph].setdefault(ell, have)
+    tick("bin", stages["combine and bin"])
+    n_m0 = run.nph * len(run.need)
+    n_m1 = run.nph * sum(ell for ell in run.need)
+    total = run.nph * timed["paint"] + n_m0 * timed["transform_m0"] + n_m1 * timed["transform_m1"] + timed["bin"]
+    desc = (f"oracle.power.HalfSpectrumPower (numpy/scipy float64) on the full workload ({w['n']}^3, "
+            f"{len(g.w)} galaxies + {len(r.w)} randoms); timed stages: painting of phase 0, one "
+            f"one-transform and one two-transform (l, m) stage of phase 0 and the binning stage "
+            f"({sum(timed.values()):.1f} s); measurement time = {run.nph} x painting + {n_m0} x "
+            f"one-transform + {n_m1} x two-transform stages + binning = {total:.1f} s; scipy.fft "
+            f"workers = {cores} (the elementwise numpy work runs on one core)")
+    return {"value": 1.0 / total, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
+            "sample_seconds": sum(timed.values()), "stage_seconds": {k: round(v, 3) for k, v in timed.items()},
+            "measurement_seconds": total}
+
+
+REFERENCE_MESH = 128
+
+
+def run_reference(args, w):
+    """The reference arm: the FP64 oracle (there is no reference implementation to install) timed on
+    the host cores, one full catalogue -> multipoles measurement per step, on a sample of the bench
+    workload small enough that the steps fit in a few minutes: the same survey geometry, FKP weights,
+    TSC interlacing and bins of 0.01 h/Mpc, on a 128^3 mesh with the objects scaled by (128/512)^3
+    (the same objects per cell).  The line names that sample in its config; its rate is the measured
+    rate of the sample, not scaled to 512^3."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
     import math
 
     from oracle import power as P
     from synthetic import make_survey_catalogs
 
-    f = (sample_n / w["n"]) ** 3
+    cores = _cores()
+    ns = REFERENCE_MESH
+    f = (ns / w["n"]) ** 3
     g, r, origin = make_survey_catalogs(int(w["n_gal"] * f), int(w["n_ran"] * f), w["box"], w["distance"],
-                                        min(w["n_gen"], sample_n), seed=w["seed"], fkp_p0=w["fkp_p0"])
-    spec = dict(n=sample_n, box=w["box"], origin=tuple(origin), assign=w["assign"], interlace=w["interlace"],
-                los="endpoint", observer=(0.0, 0.0, 0.0))
-    kn = math.pi * sample_n / w["box"]
-    kb = (w["kmin"], w["dk"], min(w["nbins"], int(kn / w["dk"])))
-    t0 = time.perf_counter()
-    P.power_multipoles(spec, g, r, kb, w["ells"], w["modified"], method="plain")
-    dt = time.perf_counter() - t0
-    scale = (w["n"] / sample_n) ** 3 * math.log(w["n"] ** 3) / math.log(sample_n ** 3)
-    return dt, scale, (f"oracle (numpy FP64, Hand+17 full-m) on a {sample_n}^3 mesh with "
-                       f"{len(g.w)} galaxies + {len(r.w)} randoms, same box; time x {scale:.1f} "
-                       f"(cells x log-ratio) to the 512^3 workload")
-
-
-def run_reference(args, w):
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
-        return
-    times, desc, scale = [], "", 1.0
+                                        min(w["n_gen"], ns), seed=w["seed"], fkp_p0=w["fkp_p0"])
+    spec = _power_spec(dict(w, n=ns), origin)
+    nb = min(w["nbins"], int(math.pi * ns / w["box"] / w["dk"]))
+    kb = (w["kmin"], w["dk"], nb)
+    times = []
     for i in range(args.warmup + args.steps):
-        dt, scale, desc = cpu_baseline(w, sample_n=64)
+        t0 = time.perf_counter()
+        P.power_multipoles_rfft(spec, g, r, kb, w["ells"], w["modified"], workers=cores)
+        dt = time.perf_counter() - t0
         if i >= args.warmup:
             times.append(dt)
-    per = sum(times) / len(times) * scale
-    value = 1.0 / per
+    tot = sum(times)
+    value = len(times) / tot
+    desc = (f"oracle.power.power_multipoles_rfft (numpy/scipy float64), one full measurement per step of the "
+            f"{w['n']}^3 workload sampled at {ns}^3 with {len(g.w)} galaxies + {len(r.w)} randoms (same box, "
+            f"geometry, weights and objects per cell; {nb} bins up to the sample's Nyquist); scipy.fft workers "
+            f"= {cores}; the rate is the sample's own, not scaled")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "mesh": w["n"], "n_gal": w["n_gal"], "n_ran": w["n_ran"],
-                       "global_batch": 1, "parallelism": "replicas"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot / len(times) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{WORKLOAD} sampled at {ns}^3", "mesh": ns, "n_gal": len(g.w),
+                       "n_ran": len(r.w), "nbins": nb, "global_batch": 1, "parallelism": "host cores"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def power_errors(w, g, r, ours, nb):
+    """Per-multipole error of the library's output against the FP64 oracle values stored for the
+    same inputs (tests/golden/full_size_p024b_mixed_512.json, written by the oracle), in the
+    monopole-scale metric |X - X_orc| / max(|X_orc|, |P_0,orc| + N_0); None when the stored values
+    were computed from other input bytes."""
+    import numpy as np
+
+    from synthetic import fingerprint
+
+    path = os.path.join(ROOT, "tests", "golden", "full_size_p024b_mixed_512.json")
+    if not os.path.exists(path):
+        return {"available": False, "reason": "no stored oracle values"}
+    with open(path) as f:
+        orc = json.load(f)
+    if orc.get("fingerprint") != fingerprint(g, r):
+        return {"available": False, "reason": "stored oracle values were computed from other input bytes"}
+    from paper_2605_04864_gb300 import api
+
+    res = api.unpack_power(ours, nb, w["ells"], w["modified"])
+    scale = np.abs(np.asarray(orc["P"]["0"])) + orc["scalars"]["N0"]
+    err = {}
+    for l in w["ells"]:
+        o = np.asarray(orc["P"][str(l)])
+        err[f"P{l}"] = float(np.max(np.abs(res["P"][l] - o) / np.maximum(np.abs(o), scale)))
+    for l in w["modified"]:
+        o = np.asarray(orc["Pmod"][str(l)])
+        err[f"P{l}b"] = float(np.max(np.abs(res["Pmod"][l] - o) / np.maximum(np.abs(o), scale)))
+    return {"available": True, "metric": "max over bins of |X - X_orc| / max(|X_orc|, |P_0,orc| + N_0)",
+            "tolerance": 1e-5, "oracle": orc.get("oracle"), "max": err}
+
+
+def _tf32_peak():
+    """Dense tf32 tensor peak: the measured bf16 burst figure times the nominal tf32 / bf16 ratio
+    (1.1 / 2.25 PFLOP/s dense)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]) * 1.1 / 2.25, "measured bf16 x nominal tf32/bf16"
+    except Exception:
+        return 1900.0 * 1.1 / 2.25, "fallback bf16 x nominal tf32/bf16"
+
+
+def bispec_errors(cat, res):
+    """Error of every B_0, B_2 triangle and B_000, B_202 pair (raw estimate and analytic shot noise)
+    against the FP64 oracle values stored for the same catalogue (tests/golden/full_size_bispec_256.json,
+    written by the oracle), relative to the monopole scale |B_0,orc| + |N_0,orc| of the same
+    triangle or pair; None when the stored values were computed from other input bytes."""
+    import numpy as np
+
+    from synthetic import fingerprint
+
+    path = os.path.join(ROOT, "tests", "golden", "full_size_bispec_256.json")
+    if not os.path.exists(path):
+        return {"available": False, "reason": "no stored oracle values"}
+    with open(path) as f:
+        orc = json.load(f)
+    if orc.get("fingerprint") != fingerprint(cat):
+        return {"available": False, "reason": "stored oracle values were computed from other input bytes"}
+    a = lambda v: np.asarray(v)
+    out = {}
+    st = a(orc["B_raw"]["0"]).__abs__() + a(orc["shot_B"]["0"]).__abs__()
+    sp = a(orc["BB_raw"]["0"]).__abs__() + a(orc["shot_BB"]["0"]).__abs__()
+    for l in (0, 2):
+        o = a(orc["B_raw"][str(l)])
+        out[f"B{l}"] = float(np.max(np.abs(res["B"][l] + res["shot_B"][l] - o) / np.maximum(np.abs(o), st)))
+        o = a(orc["shot_B"][str(l)])
+        out[f"shot_B{l}"] = float(np.max(np.abs(res["shot_B"][l] - o) / np.maximum(np.abs(o), st)))
+        o = a(orc["BB_raw"][str(l)])
+        out[f"B{l}0{l}"] = float(np.max(np.abs(res["BB"][l] + res["shot_BB"][l] - o) / np.maximum(np.abs(o), sp)))
+        o = a(orc["shot_BB"][str(l)])
+        out[f"shot_B{l}0{l}"] = float(np.max(np.abs(res["shot_BB"][l] - o) / np.maximum(np.abs(o), sp)))
+    return {"available": True, "metric": "max over triangles (pairs) of |X - X_orc| / max(|X_orc|, |B_0,orc| + |N_0,orc|)",
+            "tolerance": 1e-4, "max": out}
+
+
+BISPEC_SAMPLE_BINS = 5
+
+
+def bispec_cpu_baseline(w, cat):
+    """The FP64 oracle (oracle.bispec.bispectrum with its analytic shot noise) on the bench's own
+    256^3 catalogue, restricted to the first BISPEC_SAMPLE_BINS k-bins (a bounded sample: the full
+    19-bin set takes the oracle several minutes); rate in the leg's unit over the sample's triangles."""
+    from oracle import bispec as OB
+
+    kb = (w["kmin"], w["dk"], BISPEC_SAMPLE_BINS)
+    spec = dict(n=w["n"], box=w["box"], origin=(0.0, 0.0, 0.0), assign=w["assign"], interlace=w["interlace"],
+                los="global", los_dir=(0.0, 0.0, 1.0), periodic=1)
+    t0 = time.perf_counter()
+    res = OB.bispectrum(spec, cat, None, kb, w["scoc_ells"], w["tripo_ells"], shot=True)
+    dt = time.perf_counter() - t0
+    ntri = len(res["tri"])
+    return {"value": ntri * len(w["scoc_ells"]) / dt, "unit": "triangles/s", "cores": 1, "kind": "oracle",
+            "sample": f"oracle.bispec.bispectrum (numpy float64, analytic shot noise, B_0, B_2, B_000, B_202) on the "
+                      f"full {w['n']}^3 catalogue with the first {BISPEC_SAMPLE_BINS} of {w['nbins']} bins "
+                      f"({ntri} triangles, {dt:.1f} s); numpy's transforms run on one core",
+            "sample_seconds": dt}
 
 
 def bispec_leg(args, world, rank, barrier, max_over_ranks):
@@ -301,6 +459,36 @@ def bispec_leg(args, world, rank, barrier, max_over_ranks):
     torch.cuda.synchronize()
     barrier()
     ms_fft = max_over_ranks(s.elapsed_time(e)) / args.steps
+    # end to end: pinned host catalogue in, host arrays out (the public Python call), every step
+    pin = lambda a: torch.from_numpy(a).pin_memory()
+    ch = SimpleNamespace(pos=pin(cat.pos), w=pin(cat.w), nbar=pin(cat.nbar))
+    kwh = {k: v for k, v in kw.items() if k != "out"}
+    api.bispectrum(ch, **kwh)
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        host_res = api.bispectrum(ch, **kwh)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e = {"value": world * ntri.value * nmult * args.steps / e2e_s, "unit": "triangles/s",
+           "h2d_bytes_per_step": sum(t.numel() * t.element_size() for t in (ch.pos, ch.w, ch.nbar)),
+           "d2h_bytes_per_step": length.value * 8, "ms_per_step": e2e_s / args.steps * 1e3}
+    # the dense triple-product contraction: tensor-bound (float32 shell fields split into tf32 hi + lo)
+    st = api.last_stats()
+    tri_ms, tri_nl, tri_rep = acc.get("triple", [0.0, 0, 1])
+    tri_launch_ms = tri_ms / max(tri_nl, 1)
+    tri_flops = st["contraction_flops"] / max(st["contraction_launches"], 1)
+    tf32_peak, tf32_src = _tf32_peak()
+    achieved = tri_flops / (tri_launch_ms / 1e3) / 1e12
+    roofline = {"bound": "tensor", "kernel": "triple", "achieved": achieved, "peak": tf32_peak, "unit": "TFLOP/s",
+                "frac": achieved / tf32_peak, "traffic": None, "peak_source": tf32_src,
+                "flops_per_launch": tri_flops, "launch_ms": tri_launch_ms,
+                "issued_frac": 3 * achieved / tf32_peak,
+                "note": "useful multiply-adds 2 x rows x columns x cells of the 128^3 shell grid; the split "
+                        "precision issues three tensor products per useful one (issued_frac)"}
+    errs = bispec_errors(cat, host_res) if rank == 0 else None
     # Sugiyama TripoSH multipoles on the same catalogue (every (k1, k2) bin pair, raw estimator)
     mps = [(0, 0, 0), (1, 1, 0), (1, 1, 2), (2, 0, 2), (2, 2, 0), (2, 2, 2)]
     nbn = w["nbins"]
@@ -360,6 +548,8 @@ def bispec_leg(args, world, rank, barrier, max_over_ranks):
             "config": {"workload": "bispec_256", "mesh": w["n"], "n_gal": w["n_gal"], "nbins": w["nbins"],
                        "assign": "TSC", "interlace": True},
             "stages_ms": stages, "gpu_launches": launches * args.steps,
+            "roofline": roofline, "e2e": e2e, "err_vs_fp64": errs,
+            "cpu_baseline": bispec_cpu_baseline(w, cat) if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None,
             "plain_gpu": plain,
             "sugiyama": sugiyama,
             "fft_method_shot": {"value": world * ntri.value * nmult / (ms_fft / 1e3), "ms_per_step": ms_fft,
@@ -771,6 +961,7 @@ def power_leg(args, w, world, local, rank, barrier, max_over_ranks):
                        "l2": "inputs larger than L2 (catalogues 440 MB, meshes 2x537 MB, spectra 16 GB)"},
             "roofline": roofline, "stages_ms": stages, "e2e": e2e, "gpu_launches": launches * args.steps,
             "clocks": clocks, "step_ms": step_stats}
+    line["err_vs_fp64"] = power_errors(w, g, r, out.cpu().numpy(), w["nbins"]) if rank == 0 else None
     # the plain GPU form (float64 cuFFT, Hand+17 full-m fields, atomic painting) beside it
     if not args.no_plain:
         ours = out.cpu().numpy()
@@ -864,9 +1055,8 @@ def main():
     if not args.no_batch:
         line["batch"] = batch_leg(args, world, rank, barrier, max_over_ranks)
     if rank == 0 and not args.no_power and not args.no_cpu_baseline and world == 1:
-        dt, scale, desc = cpu_baseline(w)
-        line["cpu_baseline"] = {"value": 1.0 / (dt * scale), "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": desc, "sample_seconds": dt}
+        g, r, origin = make_inputs(w, 0)
+        line["cpu_baseline"] = cpu_baseline(w, g, r, origin)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

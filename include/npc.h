@@ -107,6 +107,12 @@ typedef struct {
   int32_t n_phases;            /* 1 or 2 (interlacing) */
   int32_t n_kernel_launches;   /* kernels enqueued by the call */
   int64_t workspace_bytes;     /* device workspace held by the context after the call */
+  double contraction_flops;    /* bispectrum calls: multiply-add work of the dense triple-product
+                                  contractions the call launched, 2 x rows x columns x cells summed
+                                  over the launches (the useful products; the tensor cores issue
+                                  three per product for the split precision) */
+  int32_t contraction_launches;/* number of those launches */
+  int32_t reserved;
 } npc_stats;
 npc_status npc_last_stats(npc_ctx* ctx, npc_stats* out);
 
@@ -134,18 +140,24 @@ npc_status npc_catalog_scalars(npc_ctx* ctx, const npc_catalog* data, const npc_
  * The paper has no counterpart to this call; it exists for callers that cannot allocate device
  * memory (a host framework that owns all device memory through its own pool, a plugin that is
  * only handed device pointers, a latency-bound loop that must not pay an allocation's implicit
- * synchronisation).  It computes the same out[0..7] as npc_catalog_scalars, but needs no context
- * and allocates nothing: its scratch (per-block partial sums) is a static device array of
- * 786,560 bytes that every device which loads the library holds until the process exits.
+ * synchronisation).  It computes out[0..7] as npc_catalog_scalars defines them, but needs no
+ * context and allocates nothing: its scratch (per-block partial sums) is a static device array of
+ * 786,560 bytes that every device which loads the library holds until the process exits.  Its
+ * reduction tree depends on n (one block per 4,096 objects, where the context call always sums
+ * 1,024 fixed blocks), so the two calls agree to rounding (about 1e-12 relative), not bit for
+ * bit; repeated calls on the same inputs are bitwise identical.
  *   - data / randoms: device pointers only (on_device = 1), at most 33,554,432 objects each,
  *     otherwise NPC_ERR_INVALID_ARG with a message in `err`; randoms == NULL means a periodic box.
  *   - out_device: 8 doubles of device memory; the call is asynchronous on `cuda_stream` (NULL:
  *     the legacy default stream) and runs on the calling thread's current device.
  *   - err / errlen: optional buffer for a NUL-terminated message.
- * The first call on each device looks up the address of the static array on that device; make
- * that first call before any stream capture.  Every call reuses the same array and leaves the
- * last call's partial sums in it; calls whose work can overlap on one device (concurrent streams
- * or threads) race on it and must be serialised by the caller. */
+ * The first call on each device looks up the address of the static array on that device (again
+ * after that device's context changes, e.g. after cudaDeviceReset); make that first call before
+ * any stream capture.  Every call reuses the same array and leaves the last call's partial sums
+ * in it; calls whose work can overlap on one device (concurrent streams or threads) race on it and
+ * must be serialised by the caller.  A launch failure is returned as NPC_ERR_CUDA, and so is an
+ * error that earlier asynchronous work left pending (it is not cleared: cudaGetLastError still
+ * returns it afterwards). */
 npc_status npc_catalog_scalars_noalloc(const npc_catalog* data, const npc_catalog* randoms, double box,
                                        double* out_device, void* cuda_stream, char* err, size_t errlen);
 

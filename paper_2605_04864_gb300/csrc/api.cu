@@ -265,12 +265,16 @@ npc_status stage_mark(npc_ctx* ctx, const char* name) {
 
 void begin_call(npc_ctx* ctx) {
   ctx->launches = 0;
+  ctx->contraction_flops = 0.0;
+  ctx->contraction_launches = 0;
   ctx->last_error.clear();
   stage_begin(ctx);
 }
 
 npc_status end_call(npc_ctx* ctx) {
   ctx->stats.n_kernel_launches = ctx->launches;
+  ctx->stats.contraction_flops = ctx->contraction_flops;
+  ctx->stats.contraction_launches = ctx->contraction_launches;
   int64_t tot = 0;
   for (auto& kv : ctx->ws) tot += (int64_t)kv.second.bytes;
   ctx->stats.workspace_bytes = tot;

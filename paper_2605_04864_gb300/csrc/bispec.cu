@@ -2017,6 +2017,8 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
   NPC_TRY(ws_get(ctx, "bis.tripart", sizeof(double) * (size_t)grid * std::max(ta.nrows, tn.nrows) * TRI_COLS,
                  (void**)&part));
   auto launch_tab = [&](const TripleArgs& a, int grid, double* part, size_t tp, size_t trp) -> npc_status {
+    ctx->contraction_flops += 2.0 * a.nrows * a.ncol * (double)a.ncell;
+    ctx->contraction_launches += 1;
     if constexpr (sizeof(T) == 4) {
       const int mt = tri_mt(a), rows = TRI_WARPS * mt * 16;
       const int groups = (a.nrows + rows - 1) / rows;

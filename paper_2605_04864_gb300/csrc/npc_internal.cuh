@@ -166,6 +166,8 @@ struct npc_ctx {
   std::string last_error;
   npc_stats stats{};
   int launches = 0;
+  double contraction_flops = 0.0;   // dense triple-product work of the current call
+  int contraction_launches = 0;
   // stage profiling (events recorded on `stream` at stage boundaries when enabled)
   bool profile = false;
   std::vector<cudaEvent_t> ev_pool;
