@@ -374,7 +374,7 @@ def bispec_errors(cat, res):
             "tolerance": 1e-4, "max": out}
 
 
-BISPEC_SAMPLE_BINS = 5
+BISPEC_SAMPLE_BINS = 4
 
 
 def bispec_cpu_baseline(w, cat):

@@ -116,6 +116,22 @@ typedef struct {
 } npc_stats;
 npc_status npc_last_stats(npc_ctx* ctx, npc_stats* out);
 
+/* Device status of the context (no counterpart in the paper: an operational check).  Kernels
+ * whose waits on other threads of their block are bounded (the tensor-core triple products of
+ * npc_bispectrum) record NPC_ERR_TIMEOUT in a device word of the context when a wait gives up; the
+ * block then waits (with a fixed bound) for its copies and products in flight, frees its tensor
+ * memory and exits, so the context stays usable.  Calls that return host output check the word
+ * themselves and return its code; after calls with device output, npc_device_status synchronises
+ * the context's stream, returns the recorded code (NPC_OK if none) and clears it. */
+npc_status npc_device_status(npc_ctx* ctx);
+/* Bound of those waits in GPU clock cycles (<= 0: the default, 2^31 cycles, about a second).  A
+ * bound far below the work's latency makes the waits give up: tests use it to exercise the
+ * NPC_ERR_TIMEOUT path without any fault. */
+npc_status npc_set_wait_limit(npc_ctx* ctx, long long cycles);
+/* Implementation switches for comparison runs: "tcgen05_triple" (default 1) selects the tcgen05
+ * tensor-core path of the bispectrum triple products; 0 selects the warp-level mma.sync path. */
+npc_status npc_set_option(npc_ctx* ctx, const char* name, int64_t value);
+
 /* Stage timing.  With profiling on, every call records CUDA events on the context's stream at its
  * stage boundaries (a few events per call, no synchronisation).  npc_stage_times() waits for the
  * stream, then reports the stages of the last call: names[i] (NUL-terminated, 32 bytes each),

@@ -204,6 +204,22 @@ def last_stats(device=0):
     return {k: getattr(st, k) for k, _ in B.npc_stats._fields_}
 
 
+def set_option(name, value, device=0):
+    """Implementation switch of the context (npc_set_option), e.g. ("tcgen05_triple", 0)."""
+    B.check(B.npc_set_option(context(device), name.encode(), int(value)), context(device))
+
+
+def set_wait_limit(cycles, device=0):
+    """Bound of the device-side waits in clock cycles (<= 0: the default); see npc_set_wait_limit."""
+    B.check(B.npc_set_wait_limit(context(device), int(cycles)))
+
+
+def device_status(device=0):
+    """npc_device_status: raises NpcError when a bounded device wait gave up since the last check."""
+    ctx = context(device)
+    B.check(B.npc_device_status(ctx), ctx)
+
+
 def set_profiling(on=True, device=0):
     B.check(B.npc_set_profiling(context(device), 1 if on else 0))
 

@@ -60,6 +60,9 @@ _sig = {
     "npc_last_error": (C.c_int, [C.c_void_p, C.c_char_p, C.c_size_t]),
     "npc_version": (C.c_char_p, []),
     "npc_last_stats": (C.c_int, [C.c_void_p, _P(npc_stats)]),
+    "npc_device_status": (C.c_int, [C.c_void_p]),
+    "npc_set_wait_limit": (C.c_int, [C.c_void_p, C.c_longlong]),
+    "npc_set_option": (C.c_int, [C.c_void_p, C.c_char_p, C.c_int64]),
     "npc_catalog_scalars": (C.c_int, [C.c_void_p, _P(npc_catalog), _P(npc_catalog), C.c_double,
                                       C.c_void_p, C.c_int32]),
     "npc_power_multipoles": (C.c_int, [C.c_void_p, _P(npc_mesh_spec), _P(npc_catalog), _P(npc_catalog),

@@ -265,6 +265,7 @@ npc_status stage_mark(npc_ctx* ctx, const char* name) {
 
 void begin_call(npc_ctx* ctx) {
   ctx->launches = 0;
+  ctx->bounded_waits = false;
   ctx->contraction_flops = 0.0;
   ctx->contraction_launches = 0;
   ctx->last_error.clear();
@@ -288,7 +289,21 @@ npc_status finish_output(npc_ctx* ctx, const double* dev, double* out, int64_t l
   }
   NPC_CUDA(ctx, cudaMemcpyAsync(out, dev, sizeof(double) * len, cudaMemcpyDeviceToHost, ctx->stream));
   NPC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (ctx->bounded_waits) return check_device_status(ctx);
   return NPC_OK;
+}
+
+npc_status check_device_status(npc_ctx* ctx) {
+  if (!ctx->dev_status) return NPC_OK;
+  int word = 0;
+  NPC_CUDA(ctx, cudaMemcpyAsync(&word, ctx->dev_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  NPC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (word == 0) return NPC_OK;
+  // tables and counts cached by the failed call may be incomplete: recompute them next time
+  ctx->host_cache_keys.clear();
+  NPC_CUDA(ctx, cudaMemsetAsync(ctx->dev_status, 0, sizeof(int), ctx->stream));
+  NPC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return set_err(ctx, (npc_status)word, "a bounded device-side wait gave up (results of that call are invalid)");
 }
 
 // The estimator after validation, staging and the catalogue scalars (device output `dev_out`).
@@ -464,8 +479,36 @@ npc_status npc_create(npc_ctx** out, int device, void* cuda_stream) {
     c->own_stream = true;
   }
   cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (cudaMalloc(&c->dev_status, 16) != cudaSuccess || cudaMemset(c->dev_status, 0, 16) != cudaSuccess) {
+    cudaGetLastError();
+    if (c->dev_status) cudaFree(c->dev_status);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return NPC_ERR_OOM;
+  }
   *out = c;
   return NPC_OK;
+}
+
+npc_status npc_device_status(npc_ctx* ctx) {
+  if (!ctx) return NPC_ERR_INVALID_ARG;
+  cudaSetDevice(ctx->device);
+  return check_device_status(ctx);
+}
+
+npc_status npc_set_wait_limit(npc_ctx* ctx, long long cycles) {
+  if (!ctx) return NPC_ERR_INVALID_ARG;
+  ctx->wait_limit = cycles;
+  return NPC_OK;
+}
+
+npc_status npc_set_option(npc_ctx* ctx, const char* name, int64_t value) {
+  if (!ctx || !name) return NPC_ERR_INVALID_ARG;
+  if (std::strcmp(name, "tcgen05_triple") == 0) {
+    ctx->use_tcgen05 = value != 0;
+    return NPC_OK;
+  }
+  return set_err(ctx, NPC_ERR_INVALID_ARG, "unknown option '%s'", name);
 }
 
 npc_status npc_destroy(npc_ctx* ctx) {
@@ -476,6 +519,7 @@ npc_status npc_destroy(npc_ctx* ctx) {
   for (auto& kv : ctx->ws)
     if (kv.second.p) cudaFree(kv.second.p);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+  if (ctx->dev_status) cudaFree(ctx->dev_status);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
   return NPC_OK;

@@ -826,6 +826,8 @@ k_triple_f64(const double* __restrict__ R, const TripleArgs A, const int* __rest
   part[((size_t)blockIdx.x * A.nrows + r) * A.ncol + c] = acc;
 }
 
+#include "triple_tc.cuh"
+
 // ------------------------------------------------------------------------------------------
 // 6. normalisation and analytic shot noise (one thread per triangle / pair)
 // ------------------------------------------------------------------------------------------
@@ -2020,6 +2022,23 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
     ctx->contraction_flops += 2.0 * a.nrows * a.ncol * (double)a.ncell;
     ctx->contraction_launches += 1;
     if constexpr (sizeof(T) == 4) {
+      if (ctx->use_tcgen05 && a.nrows > 32 && a.ncol <= tc::NCOL && a.ncell % tc::CHUNK == 0) {
+        // tensor-core (tcgen05) path: up to three 128-row tiles per CTA
+        const int nt = std::min(3, (a.nrows + 127) / 128);
+        const int groups = (a.nrows + nt * 128 - 1) / (nt * 128);
+        const size_t smem = tc_triple_smem(a.nstage);
+        auto go = [&](auto kern) -> npc_status {
+          NPC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+          kern<<<dim3(grid, groups), nt * 128 + 32, smem, ctx->stream>>>(
+              (const float*)R, a, (const int*)(dtab + tp), (const int*)(dtab + trp), part, ctx->dev_status,
+              wait_cycles(ctx));
+          return NPC_OK;
+        };
+        NPC_TRY(nt == 1 ? go(k_triple_tc<1>) : nt == 2 ? go(k_triple_tc<2>) : go(k_triple_tc<3>));
+        ctx->bounded_waits = true;
+        NPC_LAUNCH(ctx);
+        return NPC_OK;
+      }
       const int mt = tri_mt(a), rows = TRI_WARPS * mt * 16;
       const int groups = (a.nrows + rows - 1) / rows;
       auto run = [&](auto kern, int nt) -> npc_status {

@@ -168,6 +168,13 @@ struct npc_ctx {
   int launches = 0;
   double contraction_flops = 0.0;   // dense triple-product work of the current call
   int contraction_launches = 0;
+  // device status word written by kernels whose waits are bounded (0 = fine, else an npc_status),
+  // the wait bound they are given (clock cycles) and whether the current call launched one
+  int* dev_status = nullptr;
+  long long wait_limit = 0;          // <= 0: the default bound
+  bool bounded_waits = false;
+  // triple products on the tcgen05 tensor cores (off: the mma.sync path), for comparison runs
+  bool use_tcgen05 = true;
   // stage profiling (events recorded on `stream` at stage boundaries when enabled)
   bool profile = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -187,6 +194,14 @@ struct npc_ctx {
   std::map<int, int> ytx;              // tuned columns per CTA of the y pass, per (n * 2 + fp64)
   cudaStream_t batch_hub = nullptr;    // stream the batch graphs are captured on and launched from
 };
+
+// default bound of a device-side wait: about one second at the GPU's clock
+constexpr long long NPC_DEFAULT_WAIT_CYCLES = 1ll << 31;
+inline long long wait_cycles(const npc_ctx* ctx) {
+  return ctx->wait_limit > 0 ? ctx->wait_limit : NPC_DEFAULT_WAIT_CYCLES;
+}
+// reads (and clears) the device status word after a synchronisation of the context's stream
+npc_status check_device_status(npc_ctx* ctx);
 
 // releases branch contexts, graphs and the batch stream (batch.cu)
 void destroy_batch_state(npc_ctx* ctx);

@@ -1,0 +1,367 @@
+// Triple products over cells on the 5th-generation tensor cores (tcgen05, TMEM accumulators).
+//
+// The contraction of Eq. bi_sco / Eq. new_bispec in real space,
+//     D[row, col] = sum_x A_i(x) B_j(x) C_col(x)      (row = pair (i, j) of a family, col = k or G),
+// is a GEMM with M = rows, N = columns (<= 32) and K = cells.  Per CTA:
+//   * NT row tiles of 128 rows (thread = row, four warps per tile), one control warp;
+//   * the staged fields of a chunk of 128 cells arrive by bulk asynchronous copies (the TMA unit,
+//     one 512-byte copy per field) into a ring of TC_NBUF shared-memory buffers, completed on an
+//     mbarrier with a transaction count;
+//   * each producer thread forms its row's pair products P = A_i B_j for 32 cells (one A stage),
+//     splits them into tf32 hi + lo and writes both straight into tensor memory (tcgen05.st): the A
+//     operand never passes through shared memory;
+//   * the producers also write the column operand (hi and lo) into shared memory in the canonical
+//     K-major layout without swizzle (8 x 16-byte core matrices);
+//   * one thread issues, per 8-cell k step and row tile, the three products hi*hi + hi*lo + lo*hi
+//     (tcgen05.mma kind::tf32, M = 128, N = 32, A from tensor memory, B from a shared-memory
+//     descriptor) into an FP32 accumulator in tensor memory, and commits each A stage to an
+//     mbarrier that frees its buffers;
+//   * every TC_FLUSH A stages (4096 cells) the producers read the accumulator back (tcgen05.ld),
+//     add it into float64 registers, and the next products start a fresh accumulator;
+//   * at the end each producer writes its row's float64 sums as the CTA's partials
+//     part[cta][row][col], reduced in a fixed order by the same kernels as the other paths.
+// Every wait is bounded (clock64 against `limit`); on expiry the kernel records NPC_ERR_TIMEOUT in
+// the device status word, the other roles leave their loops, the control thread waits (with a fixed
+// bound) for its copies and products in flight, and the allocating warp frees tensor memory.
+#pragma once
+
+#include <cstdint>
+
+namespace tc {
+
+constexpr int CHUNK = 128;        // cells per bulk-copy chunk (512 bytes per staged field)
+constexpr int SROW = CHUNK + 4;   // floats between staged field rows: 16-byte aligned, and rows
+                                  // fall 16 bytes apart modulo 128 (conflict-light 16-byte reads)
+constexpr int NBUF = 3;           // chunk buffers in flight
+constexpr int AST = 32;           // cells per A stage (four k steps of 8)
+constexpr int FLUSH = 128;        // A stages between float64 flushes
+constexpr int NCOL = 32;          // MMA N (columns, padded)
+constexpr int BTILE = 1024;       // bytes of one k step of the column operand (32 x 8 tf32)
+constexpr long long DRAIN_LIMIT = 1ll << 31;  // cycles a clean-up wait may take
+
+// column of tensor memory holding A stage `sb` (0/1), row tile `t`, part hl (0 hi, 1 lo)
+__device__ __forceinline__ uint32_t col_a(int sb, int t, int hl, int nt) { return (uint32_t)(((sb * nt + t) * 2 + hl) * AST); }
+__device__ __forceinline__ uint32_t col_d(int t, int nt) { return (uint32_t)(2 * nt * 2 * AST + t * NCOL); }
+
+__host__ __device__ constexpr uint32_t tmem_cols(int nt) {
+  return (nt * (4 * AST + NCOL)) <= 256 ? 256u : 512u;
+}
+
+// instruction descriptor: D f32, A and B tf32, both K-major, N = 32, M = 128
+constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NCOL >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase of parity `parity`.  Gives up (false) when another role has aborted
+// or after `limit` cycles, in which case it records the timeout and raises the CTA's abort flag.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit, volatile int* abort,
+                                          int* status) {
+  if (mbar_test(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_test(bar, parity)) {
+    if (*abort) return false;
+    if (clock64() - t0 > limit) {
+      *abort = 1;
+      atomicCAS(status, 0, (int)NPC_ERR_TIMEOUT);
+      return false;
+    }
+  }
+  return true;
+}
+
+// clean-up wait: fixed bound, no abort check
+__device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_test(bar, parity))
+    if (clock64() - t0 > DRAIN_LIMIT) return;
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+      "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+        "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr)
+      : "memory");
+}
+
+// shared-memory matrix descriptor, canonical K-major layout without swizzle: core matrices of
+// 8 rows x 16 bytes (rows 16 bytes apart), `lbo` bytes between core matrices along K, `sbo` bytes
+// between 8-row groups along M/N; bit 46 is the descriptor version of this architecture.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint32_t a, uint64_t bdesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(
+          d),
+      "r"(a), "l"(bdesc), "r"(IDESC), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+// hi = v with the 13 low mantissa bits cleared (what the tensor core reads of a tf32 operand),
+// lo = v - hi exactly; the product keeps about 21 bits (hi*hi + hi*lo + lo*hi)
+__device__ __forceinline__ void split(float v, uint32_t& hi, uint32_t& lo) {
+  hi = __float_as_uint(v) & 0xffffe000u;
+  lo = __float_as_uint(v - __uint_as_float(hi));
+}
+
+struct Smem {
+  uint64_t full_tma[NBUF];  // chunk buffer filled (transaction count)
+  uint64_t full_a[2];       // A stage written by every producer warp
+  uint64_t empty_a[2];      // products of an A stage complete (tcgen05.commit)
+  uint64_t drain;           // clean-up commit
+  uint32_t tmem_base;
+  int abort;
+};
+
+}  // namespace tc
+
+// grid = (CTAs over the cells, row groups of NT x 128 rows); block = NT x 128 producers + one
+// control warp.  Requires ncell % 128 == 0, ncol <= 32; dynamic shared memory = tc_triple_smem().
+template <int NT>
+__global__ void __launch_bounds__(NT * 128 + 32, 1)
+k_triple_tc(const float* __restrict__ R, const __grid_constant__ TripleArgs A, const int* __restrict__ pair_ij,
+            const int* __restrict__ row_pair, double* __restrict__ part, int* status, long long limit) {
+  using namespace tc;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* buf = reinterpret_cast<float*>(smem_raw);                                   // [NBUF][nstage][SROW]
+  const size_t buf_bytes = (size_t)NBUF * A.nstage * SROW * sizeof(float);
+  unsigned char* btile = smem_raw + ((buf_bytes + 1023) & ~(size_t)1023);            // [2 sb][2 hl][4 k][1 KB]
+  Smem* sm = reinterpret_cast<Smem*>(btile + 2 * 2 * 4 * BTILE);
+  volatile int* abort = &sm->abort;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int ctrl = NT * 4;  // control warp index
+  constexpr uint32_t NCOLS = tmem_cols(NT);
+
+  // cell range of this CTA, in whole chunks
+  const int64_t nchunk_all = A.ncell / CHUNK;
+  const int64_t per = (nchunk_all + gridDim.x - 1) / gridDim.x;
+  const int64_t c_beg = min((int64_t)blockIdx.x * per, nchunk_all);
+  const int64_t c_end = min(c_beg + per, nchunk_all);
+  const int nchunk = (int)(c_end - c_beg);
+  const int nst = nchunk * (CHUNK / AST);
+  const int64_t cell0 = c_beg * CHUNK;
+
+  if (warp == ctrl) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sm->tmem_base)),
+                 "r"(NCOLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    if (lane == 0) {
+      for (int b = 0; b < NBUF; ++b) mbar_init(&sm->full_tma[b], 1);
+      for (int b = 0; b < 2; ++b) {
+        mbar_init(&sm->full_a[b], NT * 4);
+        mbar_init(&sm->empty_a[b], 1);
+      }
+      mbar_init(&sm->drain, 1);
+      sm->abort = 0;
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+  }
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = sm->tmem_base;
+
+  if (warp == ctrl) {
+    if (lane == 0) {
+      // ---- control thread: bulk copies of the staged fields, and the tensor-core products ----
+      int issued = 0;
+      auto issue = [&](int c) {
+        const int b = c % NBUF;
+        mbar_arrive_tx(&sm->full_tma[b], (uint32_t)(A.nstage * CHUNK * sizeof(float)));
+        for (int s = 0; s < A.nstage; ++s)
+          bulk_g2s(buf + ((size_t)b * A.nstage + s) * SROW,
+                   R + (size_t)A.stage_field[s] * A.ncell + cell0 + (int64_t)c * CHUNK, CHUNK * sizeof(float),
+                   &sm->full_tma[b]);
+      };
+      for (; issued < min(NBUF, nchunk); ++issued) issue(issued);
+      const uint32_t bt0 = smem_u32(btile);
+      bool ok = true;
+      int s = 0;
+      for (; s < nst; ++s) {
+        const int sb = s & 1;
+        if (!mbar_wait(&sm->full_a[sb], (uint32_t)((s >> 1) & 1), limit, abort, status)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const bool fresh = (s % FLUSH) == 0;
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+          const uint32_t d = tbase + col_d(t, NT);
+#pragma unroll
+          for (int j = 0; j < AST / 8; ++j) {
+            const uint32_t ahi = tbase + col_a(sb, t, 0, NT) + 8 * j;
+            const uint32_t alo = tbase + col_a(sb, t, 1, NT) + 8 * j;
+            const uint64_t bh = sdesc(bt0 + (uint32_t)(((sb * 2 + 0) * 4 + j) * BTILE), 128, 256);
+            const uint64_t bl = sdesc(bt0 + (uint32_t)(((sb * 2 + 1) * 4 + j) * BTILE), 128, 256);
+            mma_tf32(d, ahi, bh, (fresh && j == 0) ? 0u : 1u);
+            mma_tf32(d, ahi, bl, 1u);
+            mma_tf32(d, alo, bh, 1u);
+          }
+        }
+        mma_commit(&sm->empty_a[sb]);
+        // the last A stage of chunk c has been read by every producer: its buffer is free
+        if ((s % (CHUNK / AST)) == CHUNK / AST - 1 && issued < nchunk) issue(issued++);
+      }
+      if (!ok) {
+        // clean up: every product issued so far, and every copy in flight, must finish before
+        // tensor memory is freed and the CTA exits
+        mma_commit(&sm->drain);
+        mbar_drain(&sm->drain, 0);
+        for (int c = max(0, issued - NBUF); c < issued; ++c) mbar_drain(&sm->full_tma[c % NBUF], (uint32_t)((c / NBUF) & 1));
+      }
+    }
+    __syncwarp();
+  } else {
+    // ---- producers: thread = row ----
+    const int t = warp >> 2, q = warp & 3;
+    const int row = blockIdx.y * (NT * 128) + t * 128 + q * 32 + lane;
+    int sa = -1, sbs = -1, orow = -1;
+    if (row < A.nrows) {
+      const int fam = row / A.npair, p = row_pair[row % A.npair];
+      const int pij = pair_ij[p];
+      sa = A.a_slot[fam][pij & 0xffff];
+      sbs = A.b_slot[fam][pij >> 16];
+      orow = fam * A.npair + p;
+    }
+    // the column operand: this warp writes the core matrices cm = warp, warp + 4 NT, ... (< 32);
+    // cm % 4 = warp % 4 is the 8-column group, lane / 4 the column within it, lane % 4 the cell
+    const int ncol_here = q * 8 + (lane >> 2);
+    const int cslot = ncol_here < A.ncol ? A.c_slot[ncol_here] : -1;
+    const uint32_t lane_addr = tbase + ((uint32_t)(q * 32) << 16);
+    double acc[NCOL];
+#pragma unroll
+    for (int c = 0; c < NCOL; ++c) acc[c] = 0.0;
+    for (int s = 0; s < nst; ++s) {
+      const int sb = s & 1;
+      const int c = s / (CHUNK / AST);
+      const int o = (s % (CHUNK / AST)) * AST;
+      const int b = c % NBUF;
+      if ((s % (CHUNK / AST)) == 0 && !mbar_wait(&sm->full_tma[b], (uint32_t)((c / NBUF) & 1), limit, abort, status))
+        break;
+      if (s >= 2 && !mbar_wait(&sm->empty_a[sb], (uint32_t)(((s - 2) >> 1) & 1), limit, abort, status)) break;
+      tc_fence_after();
+      const float* stage = buf + (size_t)b * A.nstage * SROW;
+      // A operand: pair products of this row, hi and lo, 16 cells per store
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        uint32_t vh[16], vl[16];
+        if (sa >= 0) {
+          const float4* pa = reinterpret_cast<const float4*>(stage + (size_t)sa * SROW + o + 16 * h);
+          const float4* pb = reinterpret_cast<const float4*>(stage + (size_t)sbs * SROW + o + 16 * h);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float4 x = pa[u], y = pb[u];
+            split(x.x * y.x, vh[4 * u + 0], vl[4 * u + 0]);
+            split(x.y * y.y, vh[4 * u + 1], vl[4 * u + 1]);
+            split(x.z * y.z, vh[4 * u + 2], vl[4 * u + 2]);
+            split(x.w * y.w, vh[4 * u + 3], vl[4 * u + 3]);
+          }
+        } else {
+#pragma unroll
+          for (int u = 0; u < 16; ++u) vh[u] = vl[u] = 0u;
+        }
+        tmem_st16(lane_addr + col_a(sb, t, 0, NT) + 16 * h, vh);
+        tmem_st16(lane_addr + col_a(sb, t, 1, NT) + 16 * h, vl);
+      }
+      // B operand: core matrices of 8 columns x 4 cells, k step j = cm / 8, K half kh = (cm / 4) % 2
+      for (int cm = warp; cm < 32; cm += NT * 4) {
+        const int j = cm >> 3, kh = (cm >> 2) & 1;
+        const int cell = o + 8 * j + 4 * kh + (lane & 3);
+        const float v = cslot >= 0 ? stage[(size_t)cslot * SROW + cell] : 0.f;
+        uint32_t hi, lo;
+        split(v, hi, lo);
+        const size_t off = (size_t)q * 256 + kh * 128 + (lane >> 2) * 16 + (lane & 3) * 4;
+        *reinterpret_cast<uint32_t*>(btile + ((sb * 2 + 0) * 4 + j) * BTILE + off) = hi;
+        *reinterpret_cast<uint32_t*>(btile + ((sb * 2 + 1) * 4 + j) * BTILE + off) = lo;
+      }
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      fence_async_smem();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sm->full_a[sb]);
+      if ((s % FLUSH) == FLUSH - 1 || s == nst - 1) {
+        if (!mbar_wait(&sm->empty_a[sb], (uint32_t)((s >> 1) & 1), limit, abort, status)) break;
+        tc_fence_after();
+        uint32_t v[NCOL];
+        tmem_ld32(lane_addr + col_d(t, NT), v);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int cc = 0; cc < NCOL; ++cc) acc[cc] += (double)__uint_as_float(v[cc]);
+        tc_fence_before();
+      }
+    }
+    if (orow >= 0 && !*abort) {
+      double* dst = part + ((size_t)blockIdx.x * A.nrows + orow) * A.ncol;
+#pragma unroll
+      for (int cc = 0; cc < NCOL; ++cc)
+        if (cc < A.ncol) dst[cc] = acc[cc];
+    }
+  }
+  __syncthreads();
+  if (warp == ctrl) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(NCOLS) : "memory");
+  }
+}
+
+// dynamic shared memory of k_triple_tc for `nstage` staged fields
+inline size_t tc_triple_smem(int nstage) {
+  const size_t buf = (size_t)tc::NBUF * nstage * tc::SROW * sizeof(float);
+  return ((buf + 1023) & ~(size_t)1023) + 2 * 2 * 4 * tc::BTILE + sizeof(tc::Smem);
+}

@@ -194,6 +194,51 @@ def test_bispectrum_rejects(api):
     assert ei.value.status == 4
 
 
+def test_tensor_core_paths_agree(api):
+    """The tcgen05 triple products (tf32 hi + lo split, TMEM accumulators) against the warp-level
+    mma.sync path on the same shell fields: both carry about 21 bits per product, so they agree
+    far inside the 1e-4 bispectrum tolerance; N_T (integer counts) is identical."""
+    cat = make_periodic_catalog(60000, 600.0, 32, seed=45)
+    kf = 2 * np.pi / 600.0
+    kb = (2 * kf, 1.5 * kf, 7)
+    a = api.bispectrum(cat, n=64, box=600.0, kbins=kb, precision="mixed")
+    try:
+        api.set_option("tcgen05_triple", 0)
+        b = api.bispectrum(cat, n=64, box=600.0, kbins=kb, precision="mixed")
+    finally:
+        api.set_option("tcgen05_triple", 1)
+    np.testing.assert_array_equal(a["NT"], b["NT"])
+    scale = np.abs(b["B"][0] + b["shot_B"][0]) + np.abs(b["shot_B"][0])
+    for l in (0, 2):
+        assert np.max(np.abs(a["B"][l] - b["B"][l]) / scale) < 1e-5, l
+    sp = np.abs(b["BB"][0] + b["shot_BB"][0]) + np.abs(b["shot_BB"][0])
+    for l in (0, 2):
+        assert np.max(np.abs(a["BB"][l] - b["BB"][l]) / sp) < 1e-5, l
+
+
+def test_bounded_wait_timeout_is_reported_and_the_context_recovers(api):
+    """A wait bound far below the work's latency makes the triple-product kernel's waits give up:
+    the call returns NPC_ERR_TIMEOUT (no fault, no hang), and with the default bound the next call
+    on the same context gives the same result as before."""
+    from paper_2605_04864_gb300 import binding as B
+
+    cat = make_periodic_catalog(30000, 400.0, 32, seed=47)
+    kb = (0.02, 0.02, 6)
+    ref = api.bispectrum(cat, n=64, box=400.0, kbins=kb, precision="mixed")
+    try:
+        api.set_wait_limit(1)
+        with pytest.raises(B.NpcError) as ei:
+            api.bispectrum(cat, n=64, box=400.0, kbins=kb, precision="mixed")
+        assert ei.value.status == 5
+    finally:
+        api.set_wait_limit(0)
+    api.device_status()
+    again = api.bispectrum(cat, n=64, box=400.0, kbins=kb, precision="mixed")
+    for l in (0, 2):
+        np.testing.assert_array_equal(again["B"][l], ref["B"][l])
+    np.testing.assert_array_equal(again["NT"], ref["NT"])
+
+
 @pytest.mark.slow
 def test_full_size_256_all_triangles(api):
     """The bench workload in full (256^3, 1e6 particles, 19 bins): all 805 closed triangles of B_0,
