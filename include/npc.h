@@ -229,7 +229,11 @@ npc_status npc_cross_power_multipoles(npc_ctx* ctx, const npc_mesh_spec* mesh, c
  * Triangles: bins i <= j <= k closing at their centres, c_k <= c_i + c_j, c_b = kmin+(b+1/2)dk,
  * in lexicographic (i, j, k) order; pairs: i <= j in lexicographic order.  The largest bin edge
  * must not exceed k_N/2 (the closure would alias otherwise), else NPC_ERR_UNSUPPORTED.
- * scoc_ell_mask: bits 0, 2 request B_0, B_2 (l on the first, smallest side).
+ * scoc_ell_mask: bits 0, 1, 2, 3 request B_0, B_1, B_2, B_3 (l on the first, smallest side).  The odd
+ *   multipoles follow Sec. 2.1's rule for odd l: X_l is anti-Hermitian, its shell fields are i A_b(x),
+ *   and B_l reports the imaginary part (2l+1)/(I33 N_T) sum_x A_i F_j F_k / N^3; with the line of
+ *   sight to each grid point X_l is the Yamamoto field of the Y_lm-weighted transforms, with a global
+ *   line of sight L_l(qhat . los) X_0.  They are raw estimates: their shot noise is reported as 0.
  * tripo_ell_mask: bits 0, 2 request the compressed B_000, B_202.
  * shot: 1 subtracts the analytic shot noise (Sec. 5.4, thin-shell integrals) and reports it;
  *   2 uses the FFT method instead (Sec. 5.4.2): the exact sums of the two-object terms over the
@@ -244,6 +248,20 @@ npc_status npc_bispectrum(npc_ctx* ctx, const npc_mesh_spec* mesh, const npc_cat
                           const npc_catalog* randoms, const npc_kbins* bins,
                           uint32_t scoc_ell_mask, uint32_t tripo_ell_mask, int32_t shot,
                           npc_precision prec, double* out, int32_t out_on_device);
+/* Multi-tracer bispectra (Sec. 6 lists auto and cross bispectra; the cross form is this library's
+ * reading): three tracers, tracer 1 on leg 1 (k1, which carries the line of sight of B_l), tracers
+ * 2 and 3 on legs 2 and 3 (on k3 for B_l0l):
+ *   B_l^{123}(i,j,k) = (2l+1)/(I33^{123} N_T) sum_closed L_l(mu1) X^1(q1) X^2(q2) X^3(q3)
+ *   B_l0l^{123}(i,j) = (2l+1)/(I33^{123} N_i N_j) sum_{q1 in i, q2 in j} X^1(q1) X^2(q2) L_l(mu3) X^3(q3)
+ * with I33^{123} = (I33^1 I33^2 I33^3)^(1/3) (exact when the three selections n w share a shape).
+ * data: array of 3 catalogues; randoms: NULL (periodic box) or an array of 3.  A global line of
+ * sight is required (mesh->los = 1).  scoc_ell_mask, tripo_ell_mask: bits 0 and 2.  Raw estimates:
+ * no shot noise is subtracted (a pair of legs on one tracer would carry one) and the shot-noise
+ * entries of the output are 0.  Output layout, triangle and pair order as npc_bispectrum (the 8
+ * scalars are tracer 1's, with I33 replaced by I33^{123} and S3 by 0). */
+npc_status npc_cross_bispectrum(npc_ctx* ctx, const npc_mesh_spec* mesh, const npc_catalog* data,
+                                const npc_catalog* randoms, const npc_kbins* bins, uint32_t scoc_ell_mask,
+                                uint32_t tripo_ell_mask, npc_precision prec, double* out, int32_t out_on_device);
 /* Sizes for npc_bispectrum.  Any output pointer may be NULL. */
 npc_status npc_bispectrum_layout(const npc_kbins* bins, uint32_t scoc_ell_mask,
                                  uint32_t tripo_ell_mask, int64_t* ntri, int64_t* npairs,

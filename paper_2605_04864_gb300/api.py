@@ -265,6 +265,32 @@ def bispectrum(data, n, box, kbins, scoc_ells=(0, 2), tripo_ells=(0, 2), shot=Tr
     return unpack_bispectrum(buf, kbins, scoc_ells, tripo_ells)
 
 
+def cross_bispectrum(tracers, n, box, kbins, scoc_ells=(0, 2), tripo_ells=(0,), assign=3, interlace=1,
+                     los_dir=(0.0, 0.0, 1.0), precision="mixed", origin=(0.0, 0.0, 0.0), device=0, out=None):
+    """Multi-tracer bispectra (npc_cross_bispectrum): ``tracers`` = three (data, randoms) pairs
+    (randoms None for a periodic box), tracer 1 on leg 1 (the line-of-sight leg of B_l), tracers 2
+    and 3 on legs 2 and 3; global line of sight; raw estimates."""
+    keep = _Keep()
+    periodic = tracers[0][1] is None
+    spec = make_spec(n, box, origin, assign, interlace, 1 if periodic else 0, los_dir, (0.0, 0.0, 0.0))
+    kb = B.npc_kbins(float(kbins[0]), float(kbins[1]), int(kbins[2]))
+    sm = sum(1 << int(l) for l in scoc_ells)
+    tm = sum(1 << int(l) for l in tripo_ells)
+    ntri, npair, length = C.c_int64(), C.c_int64(), C.c_int64()
+    st = B.npc_bispectrum_layout(C.byref(kb), sm, tm, C.byref(ntri), C.byref(npair), C.byref(length))
+    darr = (B.npc_catalog * 3)(*[make_catalog(t[0], keep) for t in tracers])
+    rarr = None if periodic else (B.npc_catalog * 3)(*[make_catalog(t[1], keep) for t in tracers])
+    ctx = context(device)
+    if out is not None:
+        B.check(B.npc_cross_bispectrum(ctx, C.byref(spec), darr, rarr, C.byref(kb), sm, tm, _prec(precision),
+                                       C.c_void_p(out.data_ptr()), 1), ctx)
+        return out
+    buf = np.zeros(max(length.value, 1) if st == 0 else 1)
+    B.check(B.npc_cross_bispectrum(ctx, C.byref(spec), darr, rarr, C.byref(kb), sm, tm, _prec(precision),
+                                   buf.ctypes.data_as(C.c_void_p), 0), ctx)
+    return unpack_bispectrum(buf, kbins, scoc_ells, tripo_ells)
+
+
 def bispectrum_sugiyama(data, n, box, kbins, multipoles=((0, 0, 0), (2, 0, 2)), shot=False, assign=3, interlace=1,
                         los_dir=(0.0, 0.0, 1.0), precision="mixed", origin=(0.0, 0.0, 0.0), device=0, out=None,
                         randoms=None):

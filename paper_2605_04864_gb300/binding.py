@@ -75,6 +75,8 @@ _sig = {
     "npc_bispectrum": (C.c_int, [C.c_void_p, _P(npc_mesh_spec), _P(npc_catalog), _P(npc_catalog),
                                  _P(npc_kbins), C.c_uint32, C.c_uint32, C.c_int32, C.c_int, C.c_void_p,
                                  C.c_int32]),
+    "npc_cross_bispectrum": (C.c_int, [C.c_void_p, _P(npc_mesh_spec), _P(npc_catalog), _P(npc_catalog),
+                                       _P(npc_kbins), C.c_uint32, C.c_uint32, C.c_int, C.c_void_p, C.c_int32]),
     "npc_bispectrum_layout": (C.c_int, [_P(npc_kbins), C.c_uint32, C.c_uint32, _P(C.c_int64),
                                         _P(C.c_int64), _P(C.c_int64)]),
     "npc_bispectrum_triangles": (C.c_int, [_P(npc_kbins), _P(C.c_int32), C.c_int64, _P(C.c_int64)]),

@@ -683,7 +683,7 @@ npc_status npc_cross_power_multipoles(npc_ctx* ctx, const npc_mesh_spec* mesh, c
 
 static int64_t bispec_len(const npc_kbins* bins, uint32_t sm, uint32_t tm, int64_t* ntri, int64_t* npair) {
   bispec_counts(*bins, ntri, npair);
-  const int ns = ((sm >> 0) & 1) + ((sm >> 2) & 1);
+  const int ns = ((sm >> 0) & 1) + ((sm >> 1) & 1) + ((sm >> 2) & 1) + ((sm >> 3) & 1);
   const int nt = ((tm >> 0) & 1) + ((tm >> 2) & 1);
   return 2 * ns * (*ntri) + (*ntri) + 2 * nt * (*npair) + bins->nbins + 8;
 }
@@ -691,7 +691,7 @@ static int64_t bispec_len(const npc_kbins* bins, uint32_t sm, uint32_t tm, int64
 npc_status npc_bispectrum_layout(const npc_kbins* bins, uint32_t scoc_ell_mask, uint32_t tripo_ell_mask,
                                  int64_t* ntri, int64_t* npairs, int64_t* out_len) {
   if (!bins || bins->nbins < 1 || bins->nbins > 24 || !(bins->dk > 0)) return NPC_ERR_INVALID_ARG;
-  if ((scoc_ell_mask & ~5u) || (tripo_ell_mask & ~5u) || (scoc_ell_mask | tripo_ell_mask) == 0)
+  if ((scoc_ell_mask & ~15u) || (tripo_ell_mask & ~5u) || (scoc_ell_mask | tripo_ell_mask) == 0)
     return NPC_ERR_INVALID_ARG;
   int64_t nt = 0, np = 0;
   const int64_t len = bispec_len(bins, scoc_ell_mask, tripo_ell_mask, &nt, &np);
@@ -789,15 +789,15 @@ npc_status npc_bispectrum(npc_ctx* ctx, const npc_mesh_spec* mesh, const npc_cat
   NPC_TRY(check_bins(ctx, bins));
   if (!out) return set_err(ctx, NPC_ERR_INVALID_ARG, "out is NULL");
   if (bins->nbins > 24) return set_err(ctx, NPC_ERR_UNSUPPORTED, "bispectrum supports at most 24 bins");
-  if ((scoc_ell_mask & ~5u) || (tripo_ell_mask & ~5u) || (scoc_ell_mask | tripo_ell_mask) == 0)
-    return set_err(ctx, NPC_ERR_INVALID_ARG, "multipole masks must use bits 0 and 2");
+  if ((scoc_ell_mask & ~15u) || (tripo_ell_mask & ~5u) || (scoc_ell_mask | tripo_ell_mask) == 0)
+    return set_err(ctx, NPC_ERR_INVALID_ARG, "multipole masks: Scoccimarro bits 0..3, compressed bits 0 and 2");
   if (shot < 0 || shot > 2) return set_err(ctx, NPC_ERR_INVALID_ARG, "shot must be 0, 1 or 2");
   if (prec != NPC_PREC_FP64 && prec != NPC_PREC_MIXED) return set_err(ctx, NPC_ERR_INVALID_ARG, "bad precision");
   const bool mono = (scoc_ell_mask & ~1u) == 0 && (tripo_ell_mask & ~1u) == 0;
   if (mesh->periodic) {
     if (randoms) return set_err(ctx, NPC_ERR_INVALID_ARG, "periodic box takes no randoms");
     if (mesh->los != 1 && !mono)
-      return set_err(ctx, NPC_ERR_UNSUPPORTED, "bispectrum: l = 2 needs a global line of sight");
+      return set_err(ctx, NPC_ERR_UNSUPPORTED, "bispectrum: l > 0 in a periodic box needs a global line of sight");
   } else {
     // survey geometry: the monopoles need no line of sight; l = 2 takes the global one (los = 1) or
     // the line of sight to each grid point (Yamamoto X_2), the latter with the analytic shot noise
@@ -835,6 +835,70 @@ npc_status npc_bispectrum(npc_ctx* ctx, const npc_mesh_spec* mesh, const npc_cat
   if (!out_on_device) NPC_TRY(ws_get(ctx, "bis.out", sizeof(double) * out_len, (void**)&dev_out));
   NPC_TRY(run_bispectrum(ctx, *mesh, *bins, (int)scoc_ell_mask, (int)tripo_ell_mask, shot, prec, d,
                          randoms ? &r : nullptr, sc, dev_out, out_len));
+  NPC_TRY(finish_output(ctx, dev_out, out, out_len, out_on_device));
+  NPC_TRY(stage_mark(ctx, "download"));
+  return end_call(ctx);
+}
+
+npc_status npc_cross_bispectrum(npc_ctx* ctx, const npc_mesh_spec* mesh, const npc_catalog* data,
+                                const npc_catalog* randoms, const npc_kbins* bins, uint32_t scoc_ell_mask,
+                                uint32_t tripo_ell_mask, npc_precision prec, double* out, int32_t out_on_device) {
+  if (!ctx) return NPC_ERR_INVALID_ARG;
+  begin_call(ctx);
+  NPC_TRY(check_spec(ctx, mesh));
+  NPC_TRY(check_bins(ctx, bins));
+  if (!out || !data) return set_err(ctx, NPC_ERR_INVALID_ARG, "data and out are required");
+  if (bins->nbins > 24) return set_err(ctx, NPC_ERR_UNSUPPORTED, "bispectrum supports at most 24 bins");
+  if ((scoc_ell_mask & ~5u) || (tripo_ell_mask & ~5u) || (scoc_ell_mask | tripo_ell_mask) == 0)
+    return set_err(ctx, NPC_ERR_INVALID_ARG, "multi-tracer multipole masks must use bits 0 and 2");
+  if (prec != NPC_PREC_FP64 && prec != NPC_PREC_MIXED) return set_err(ctx, NPC_ERR_INVALID_ARG, "bad precision");
+  if (mesh->los != 1) return set_err(ctx, NPC_ERR_UNSUPPORTED, "multi-tracer bispectra need a global line of sight");
+  if (mesh->periodic && randoms) return set_err(ctx, NPC_ERR_INVALID_ARG, "periodic box takes no randoms");
+  if (!mesh->periodic && !randoms) return set_err(ctx, NPC_ERR_INVALID_ARG, "survey geometry needs three random catalogues");
+  const double kf = 2.0 * M_PI / mesh->box;
+  const double kmax = bins->kmin + bins->nbins * bins->dk;
+  if (kmax > 0.25 * kf * mesh->n)
+    return set_err(ctx, NPC_ERR_UNSUPPORTED, "largest bin edge %.4g exceeds k_N/2 = %.4g (closure would alias)", kmax,
+                   0.25 * kf * mesh->n);
+  if (prec == NPC_PREC_FP64 && mesh->n > 256) return set_err(ctx, NPC_ERR_UNSUPPORTED, "FP64 precision supports n <= 256");
+  if (mesh->n > 512) return set_err(ctx, NPC_ERR_UNSUPPORTED, "bispectrum supports n <= 512");
+  static const char* dtag[3] = {"data", "data_b", "data_c"};
+  static const char* rtag[3] = {"rand", "rand_b", "rand_c"};
+  for (int t = 0; t < 3; ++t) {
+    NPC_TRY(check_catalog(ctx, &data[t], dtag[t], false));
+    if (data[t].n == 0) return set_err(ctx, NPC_ERR_NUMERIC, "empty data catalogue %d (I33 = 0)", t);
+    if (randoms) {
+      NPC_TRY(check_catalog(ctx, &randoms[t], rtag[t], true));
+      if (randoms[t].n == 0) return set_err(ctx, NPC_ERR_NUMERIC, "empty random catalogue %d", t);
+    }
+  }
+  NPC_CUDA(ctx, cudaSetDevice(ctx->device));
+  int64_t ntri = 0, npair = 0;
+  const int64_t out_len = bispec_len(bins, scoc_ell_mask, tripo_ell_mask, &ntri, &npair);
+  DevCatalog d[3], r[3];
+  for (int t = 0; t < 3; ++t) {
+    NPC_TRY(stage_catalog(ctx, &data[t], dtag[t], &d[t]));
+    if (randoms) NPC_TRY(stage_catalog(ctx, &randoms[t], rtag[t], &r[t]));
+  }
+  double* sc;
+  NPC_TRY(ws_get(ctx, "scalars.x3", sizeof(double) * SC_COUNT * 4, (void**)&sc));
+  NPC_TRY(stage_mark(ctx, "upload"));
+  for (int t = 0; t < 3; ++t)
+    NPC_TRY(launch_catalog_scalars(ctx, d[t], randoms ? &r[t] : nullptr, mesh->box, sc + (size_t)t * SC_COUNT));
+  double* scx = sc + 3 * SC_COUNT;
+  NPC_TRY(launch_cross3_scalars(ctx, sc, sc + SC_COUNT, sc + 2 * SC_COUNT, scx));
+  NPC_TRY(stage_mark(ctx, "scalars"));
+  CrossReq req{};
+  for (int t = 0; t < 2; ++t) {
+    req.d[t] = d[1 + t];
+    if (randoms) req.r[t] = r[1 + t];
+    req.sc[t] = sc + (size_t)(1 + t) * SC_COUNT;
+  }
+  req.has_r = randoms != nullptr;
+  double* dev_out = out;
+  if (!out_on_device) NPC_TRY(ws_get(ctx, "bis.out", sizeof(double) * out_len, (void**)&dev_out));
+  NPC_TRY(run_bispectrum_cross(ctx, *mesh, *bins, (int)scoc_ell_mask, (int)tripo_ell_mask, prec, d[0],
+                               randoms ? &r[0] : nullptr, sc, scx, req, dev_out, out_len));
   NPC_TRY(finish_output(ctx, dev_out, out, out_len, out_on_device));
   NPC_TRY(stage_mark(ctx, "download"));
   return end_call(ctx);

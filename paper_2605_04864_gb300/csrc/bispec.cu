@@ -109,29 +109,35 @@ k_fft_x_combine(const cplx<T>* __restrict__ half, int nout, int nphase, int KZ, 
 }
 
 // ------------------------------------------------------------------------------------------
-// 2b. survey geometry with the line of sight to each grid point (l = 2): the x pass assembles
-//     X_0 and the Yamamoto field X_2 = 4 pi/5 [Y_20 A_20 + 2 sum_{m=1,2} (ReY_2m A_2m + ImY_2m B_2m)]
-//     (khat at the mode; Eq. hand with the m < 0 terms folded onto m > 0) from the twelve fields of
-//     the standard l <= 2 layout, interlaced and compensated.  Field order (phase a, b):
-//     0 a, 1 b: F;  2 a, 3 b: F Y_20;  4, 5: a Re/Im F Y_21;  6, 7: b Re/Im F Y_21;
-//     8, 9: a Re/Im F Y_22;  10, 11: b Re/Im F Y_22;  without interlacing the six fields
-//     F, F Y_20, Re/Im F Y_21, Re/Im F Y_22 in that order.
+// 2b. survey geometry with the line of sight to each grid point: the x pass assembles X_0 and the
+//     Yamamoto fields (Eq. hand with the m < 0 terms folded onto m > 0)
+//       X_l = 4 pi/(2l+1) [Y_l0 A_l0 + 2 sum_{m>=1} (Re Y_lm A_lm + Im Y_lm B_lm)]   (khat at the mode)
+//     for l = 1, 2, 3 (each when its output is given), from the Y_lm-weighted fields of the
+//     forward plan, interlaced and compensated.  A_lm, B_lm are the transforms of Re and Im of
+//     F Y_lm(xhat); X_l(-q) = (-1)^l X_l(q)^*.  Components c (l, m, part) list their phase-a field
+//     ia[c] and phase-b field ib[c] (unused without interlacing).
 // ------------------------------------------------------------------------------------------
+constexpr int YAM_MAXC = 16;   // F and the parts of Y_lm, l <= 3: 1 + 3 + 5 + 7
+struct YamComps {
+  int nf, nc;
+  int8_t l[YAM_MAXC], m[YAM_MAXC], part[YAM_MAXC];
+  int8_t ia[YAM_MAXC], ib[YAM_MAXC];
+};
+
 template <typename T, int N>
 __global__ void __launch_bounds__(BT)
-k_fft_x_assemble2(const cplx<T>* __restrict__ half, int nphase, int KZ, int KY, int assign, const YNorm nrm,
-                  const cplx<T>* __restrict__ tw_g, cplx<T>* __restrict__ X0o, cplx<T>* __restrict__ X2o) {
+k_fft_x_assemble_yam(const cplx<T>* __restrict__ half, int nphase, int KZ, int KY, int assign, const YNorm nrm,
+                     const YamComps cp, const cplx<T>* __restrict__ tw_g, cplx<T>* __restrict__ X0o,
+                     cplx<T>* __restrict__ X1o, cplx<T>* __restrict__ X2o, cplx<T>* __restrict__ X3o) {
   using C = cplx<T>;
   constexpr int TPF = N / 8;
   constexpr int G = BT / TPF > 0 ? BT / TPF : 1;
   constexpr int NP = row_pad_len<N>();
-  constexpr int NFMAX = 12;
-  const int NF = nphase == 2 ? 12 : 6;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
   C* phs = tw + N;
-  C* rows = phs + N;
-  T* winv = reinterpret_cast<T*>(rows + (size_t)(NFMAX + RowGroups<N, BT>::NBUF) * NP);
+  C* rows = phs + N;   // [nf + NBUF][NP]
+  T* winv = reinterpret_cast<T*>(rows + (size_t)(cp.nf + RowGroups<N, BT>::NBUF) * NP);
   const int tid = threadIdx.x;
   for (int i = tid; i < N; i += blockDim.x) {
     tw[i] = tw_g[i];
@@ -144,17 +150,14 @@ k_fft_x_assemble2(const cplx<T>* __restrict__ half, int nphase, int KZ, int KY, 
   const int nyr = 2 * KY + 1;
   const int nrows = KZ * nyr;
   const size_t fstride = (size_t)KZ * N * N;
-  const T c2 = T(4.0 * M_PI / 5.0);
-  // component c (F, F Y_20, Re/Im F Y_21, Re/Im F Y_22): field of phase a and of phase b
-  constexpr int IA2[6] = {0, 2, 4, 5, 8, 9}, IB2[6] = {1, 3, 6, 7, 10, 11};
-  const T n20 = ynorm<T>(nrm, 3), n21 = ynorm<T>(nrm, 4), n22 = ynorm<T>(nrm, 5);
+  C* outs[4] = {X0o, X1o, X2o, X3o};
   for (int r = blockIdx.x; r < nrows; r += gridDim.x) {
     const int kz = r / nyr;
     const int jy = r % nyr - KY;
     const int ky = jy < 0 ? jy + N : jy;
-    for (int f0 = 0; f0 < NF; f0 += G) {
+    for (int f0 = 0; f0 < cp.nf; f0 += G) {
       const int f = f0 + g;
-      const bool live = g < G && f < NF;
+      const bool live = g < G && f < cp.nf;
       C v[8];
       if (live) {
         const C* src = half + (size_t)f * fstride + ((size_t)kz * N + ky) * N;
@@ -164,7 +167,7 @@ k_fft_x_assemble2(const cplx<T>* __restrict__ half, int nphase, int KZ, int KY, 
 #pragma unroll
         for (int q = 0; q < 8; ++q) v[q] = cmk(T(0), T(0));
       }
-      RowView<C> rv{rows + (size_t)(live ? f : NFMAX + g) * NP};
+      RowView<C> rv{rows + (size_t)(live ? f : cp.nf + g) * NP};
       fft_block<N, -1>(v, t, tw, rv, RowSync<N, BT>::make(g));
       if (live) {
 #pragma unroll
@@ -178,28 +181,30 @@ k_fft_x_assemble2(const cplx<T>* __restrict__ half, int nphase, int KZ, int KY, 
       const T iw = winv[ai] * winv[aj] * winv[kz];
       const int jp = RowView<C>::idx(kx);
       const C ph = cmul(cmul(phs[i + N / 2], phs[jy + N / 2]), phs[kz + N / 2]);
-      auto comb = [&](int c) {   // interlaced (two phases), compensated component c
-        if (nphase == 1) return cscale(rows[(size_t)c * NP + jp], iw);
-        const C x = cadd(rows[(size_t)IA2[c] * NP + jp], cmul(ph, rows[(size_t)IB2[c] * NP + jp]));
-        return cscale(x, T(0.5) * iw);
-      };
-      // Y_2m(khat): norm Q(uz) (ux + i uy)^m
       const T fi = T(i), fj = T(jy), fk = T(kz);
       const T r2 = fi * fi + fj * fj + fk * fk;
       const T inv = r2 > T(0) ? rsqrt(r2) : T(0);
       const T ux = fi * inv, uy = fj * inv, uz = r2 > T(0) ? fk * inv : T(1);
-      const T y20 = n20 * (T(1.5) * uz * uz - T(0.5));
-      const C e1 = cmk(ux, uy);
-      const C y21 = cscale(e1, n21 * T(-3) * uz);
-      const C y22 = cscale(cmul(e1, e1), n22 * T(3));
-      C x2 = cscale(comb(1), y20);
-      x2 = cadd(x2, cscale(comb(2), T(2) * y21.x));
-      x2 = cadd(x2, cscale(comb(3), T(2) * y21.y));
-      x2 = cadd(x2, cscale(comb(4), T(2) * y22.x));
-      x2 = cadd(x2, cscale(comb(5), T(2) * y22.y));
+      C acc[4] = {cmk(T(0), T(0)), cmk(T(0), T(0)), cmk(T(0), T(0)), cmk(T(0), T(0))};
+      for (int c = 0; c < cp.nc; ++c) {
+        C x = rows[(size_t)cp.ia[c] * NP + jp];
+        if (nphase == 2) x = cscale(cadd(x, cmul(ph, rows[(size_t)cp.ib[c] * NP + jp])), T(0.5));
+        x = cscale(x, iw);
+        const int l = cp.l[c];
+        if (l == 0) {
+          acc[0] = x;
+          continue;
+        }
+        T yr, yi;
+        ylm_eval<T>(l, cp.m[c], ux, uy, uz, nrm, yr, yi);
+        const T wgt = cp.m[c] == 0 ? yr : T(2) * (cp.part[c] == PART_IM ? yi : yr);
+        acc[l] = cadd(acc[l], cscale(x, wgt));
+      }
       const size_t o = ((size_t)kz * N + ky) * N + kx;
-      X0o[o] = comb(0);
-      X2o[o] = cscale(x2, c2);
+      X0o[o] = acc[0];
+#pragma unroll
+      for (int l = 1; l <= 3; ++l)
+        if (outs[l]) outs[l][o] = cscale(acc[l], T(4.0 * M_PI) / T(2 * l + 1));
     }
     __syncthreads();
   }
@@ -374,8 +379,10 @@ k_bin_cross(const cplx<T>* __restrict__ X0, const cplx<T>* __restrict__ XN, int 
 // 4. shell-filtered inverse transforms
 // ------------------------------------------------------------------------------------------
 struct ShellField {
-  int8_t src;     // 0: X_0, 1: ones (indicator), 2: X_0 N_0^* (FFT-method shot noise), 3: X_2 (survey)
-  int8_t mult;    // 0: 1, 1: L_2(mu), 2: the TripoSH weight of (yl, ym, ypart)
+  int8_t src;     // 0: X_0, 1: ones (indicator), 2: X_0 N_0^* (FFT-method shot noise), 3: X_2 (survey),
+                  // 4: X_1, 5: X_3 (survey, odd: anti-Hermitian, taken times -i),
+                  // 6: X of tracer 2, 7: X of tracer 3 (multi-tracer bispectra)
+  int8_t mult;    // 0: 1, 1: L_yl(mu) (times -i for odd yl), 2: the TripoSH weight of (yl, ym, ypart)
   int16_t bin;    // >= 0: modes of this bin; -1: all modes with n2 <= n2cap
   int K;          // kz <= K, |ky| <= K
   int8_t yl, ym;  // mult 2: the field is a part of sum_q e^{iqx} y_l^{m*}(qhat) S(q), m >= 0, S the source
@@ -398,6 +405,13 @@ __constant__ double c_legendre[5][5] = {{1.0, 0.0, 0.0, 0.0, 0.0},
                                         {-0.5, 0.0, 1.5, 0.0, 0.0},
                                         {0.0, -1.5, 0.0, 2.5, 0.0},
                                         {0.375, 0.0, -3.75, 0.0, 4.375}};
+
+template <typename T>
+__device__ __forceinline__ T legendre_dev(int l, T mu) {
+  T r = T(0);
+  for (int k = l; k >= 0; --k) r = r * mu + T(c_legendre[l][k]);
+  return r;
+}
 
 // Racah-normalised y_l^m = sqrt(4 pi/(2l+1)) Y_l^m for 0 <= m <= l <= 4 at the unit vector (x, y, z):
 // (-1)^m sqrt((l-m)!/(l+m)!) (d^m L_l/dmu^m)(z) (x + i y)^m, the Condon-Shortley phase included.
@@ -429,8 +443,9 @@ __device__ __forceinline__ void ylm_frame(int l, int m, T x, T y, T z, T& re, T&
 // frequency i = kx' (kx' < NS/2) or kx' - NS, read from the n-grid spectrum X0.
 template <typename T, int NS, bool YW>
 __global__ void __launch_bounds__(BT)
-k_shell_x(const cplx<T>* __restrict__ X0, const cplx<T>* __restrict__ XN, const cplx<T>* __restrict__ X2, int KZX,
-          int nfine,
+k_shell_x(const cplx<T>* __restrict__ X0, const cplx<T>* __restrict__ XN, const cplx<T>* __restrict__ X2,
+          const cplx<T>* __restrict__ X1, const cplx<T>* __restrict__ X3, const cplx<T>* __restrict__ XB,
+          const cplx<T>* __restrict__ XC, int KZX, int nfine,
           const ShellField* __restrict__ fields, int nfields, int Kmax, const int16_t* __restrict__ tab, int n2cap,
           const LosFrame fr, const cplx<T>* __restrict__ tw_g, cplx<T>* __restrict__ T1) {
   using C = cplx<T>;
@@ -442,8 +457,12 @@ k_shell_x(const cplx<T>* __restrict__ X0, const cplx<T>* __restrict__ XN, const 
   C* xrow = tw + NS;                  // X_0 row
   C* xnrow = xrow + NS;               // X_0 N_0^* row (when XN is given)
   C* x2row = xnrow + NS;              // Yamamoto X_2 row (when X2 is given)
-  T* l2row = reinterpret_cast<T*>(x2row + NS);  // L_2(mu) per kx
-  int* binrow = reinterpret_cast<int*>(l2row + NS);  // bin per kx (-1 excluded), n2 per kx
+  C* x1row = x2row + NS;              // Yamamoto X_1, X_3 rows (when given)
+  C* x3row = x1row + NS;
+  C* xbrow = x3row + NS;              // the X rows of tracers 2 and 3 (when given)
+  C* xcrow = xbrow + NS;
+  T* murow = reinterpret_cast<T*>(xcrow + NS);  // mu = qhat . los per kx
+  int* binrow = reinterpret_cast<int*>(murow + NS);  // bin per kx (-1 excluded), n2 per kx
   int* n2row = binrow + NS;
   C* bufs = reinterpret_cast<C*>(n2row + NS);   // NBUF x NP
   const int tid = threadIdx.x;
@@ -466,9 +485,12 @@ k_shell_x(const cplx<T>* __restrict__ X0, const cplx<T>* __restrict__ XN, const 
       xrow[kx] = (inrange && kz < KZX) ? X0[src] : cmk(T(0), T(0));
       if (XN) xnrow[kx] = (inrange && kz < KZX) ? cmul(X0[src], cconj(XN[src])) : cmk(T(0), T(0));
       if (X2) x2row[kx] = (inrange && kz < KZX) ? X2[src] : cmk(T(0), T(0));
+      if (X1) x1row[kx] = (inrange && kz < KZX) ? X1[src] : cmk(T(0), T(0));
+      if (X3) x3row[kx] = (inrange && kz < KZX) ? X3[src] : cmk(T(0), T(0));
+      if (XB) xbrow[kx] = (inrange && kz < KZX) ? XB[src] : cmk(T(0), T(0));
+      if (XC) xcrow[kx] = (inrange && kz < KZX) ? XC[src] : cmk(T(0), T(0));
       const T kk = sqrt(T(n2));
-      const T mu = n2 > 0 ? (T(i) * T(fr.e3[0]) + T(jy) * T(fr.e3[1]) + T(kz) * T(fr.e3[2])) / kk : T(0);
-      l2row[kx] = T(1.5) * mu * mu - T(0.5);
+      murow[kx] = n2 > 0 ? (T(i) * T(fr.e3[0]) + T(jy) * T(fr.e3[1]) + T(kz) * T(fr.e3[2])) / kk : T(0);
       binrow[kx] = inrange ? tab[n2] : -1;
       n2row[kx] = inrange ? n2 : -1;
     }
@@ -490,8 +512,20 @@ k_shell_x(const cplx<T>* __restrict__ X0, const cplx<T>* __restrict__ XN, const 
         if (live) {
           const bool in = sf.bin >= 0 ? (binrow[kx] == sf.bin) : (n2row[kx] >= 0);
           if (in) {
-            a = sf.src == 0 ? xrow[kx] : (sf.src == 2 ? xnrow[kx] : (sf.src == 3 ? x2row[kx] : cmk(T(1), T(0))));
-            if (sf.mult == 1) a = cscale(a, l2row[kx]);
+            switch (sf.src) {
+              case 0: a = xrow[kx]; break;
+              case 2: a = xnrow[kx]; break;
+              case 3: a = x2row[kx]; break;
+              case 4: a = x1row[kx]; break;
+              case 5: a = x3row[kx]; break;
+              case 6: a = xbrow[kx]; break;
+              case 7: a = xcrow[kx]; break;
+              default: a = cmk(T(1), T(0));
+            }
+            if (sf.mult == 1) a = cscale(a, legendre_dev<T>(sf.yl, murow[kx]));
+            // odd l: the source is anti-Hermitian, its shell field i A(x); -i X is Hermitian and
+            // gives the real A (the imaginary part of the closure sum, Sec. 2.1)
+            if ((sf.mult == 1 && (sf.yl & 1)) || sf.src == 4 || sf.src == 5) a = cmk(a.y, -a.x);
             // (YW: the call holds TripoSH fields; the other calls compile without this branch)
             if (YW && sf.mult == 2) {
               // F_l^m = sum_q e^{iqx} (Re y - i Im y) X: for even l the real weights Re y (real part)
@@ -645,8 +679,8 @@ struct TripleArgs {
   int ncol;         // used columns
   int nstage;       // distinct fields staged per chunk
   int stage_field[3 * NB_MAX + 8];  // R index of staged slot s
-  int a_slot[2][NB_MAX];            // staged slot of A_i per family
-  int b_slot[2][NB_MAX];            // staged slot of B_j per family
+  int a_slot[4][NB_MAX];            // staged slot of A_i per family
+  int b_slot[4][NB_MAX];            // staged slot of B_j per family
   int c_slot[TRI_COLS];             // staged slot of column c (-1: zero column)
   int nf_cols;                      // columns 0 .. nf_cols-1 are F_k (k = column), the rest G^(l)
   int64_t ncell;
@@ -901,13 +935,13 @@ k_bin_cross_survey(const cplx<T>* __restrict__ X0, const cplx<T>* __restrict__ X
 
 struct FinalArgs {
   int nb, ntri, npair, nq;
-  int nscoc, scoc_l[2];
+  int nscoc, scoc_l[4];
+  int scoc_fam[4];      // row family of each Scoccimarro multipole in the data launch partials
   int ntripo, tripo_l[2];
   int shot;
   int nparts;           // CTAs of the triple kernel
   int nrows;            // rows of the data launch partials (family * npair + pair)
   int ncol;             // columns of the data launch partials (nb F_0 columns, then G columns)
-  int has2;             // rows npair .. 2 npair - 1 hold the l = 2 family
   int64_t ncell;
   double kmin, dk;
   int part_nw_cross;    // partial records of the cross-spectrum kernel
@@ -1026,11 +1060,10 @@ __global__ void k_bispec_finalize(const int* __restrict__ tri, const int* __rest
   for (int t = tid; t < F.ntri; t += nthreads) {
     const int i = tri[3 * t], j = tri[3 * t + 1], k = tri[3 * t + 2];
     const int p = pair_index(i, j);
-    double s0 = 0, s2 = 0, snt = 0;
-    for (int c = 0; c < F.nparts; ++c) {
-      s0 += part_main[((size_t)c * F.nrows + p) * F.ncol + k];
-      if (F.has2) s2 += part_main[((size_t)c * F.nrows + F.npair + p) * F.ncol + k];
-    }
+    double sfam[4] = {0, 0, 0, 0}, snt = 0;
+    for (int c = 0; c < F.nparts; ++c)
+      for (int e = 0; e < F.nscoc; ++e)
+        sfam[e] += part_main[((size_t)c * F.nrows + (size_t)F.scoc_fam[e] * F.npair + p) * F.ncol + k];
     snt = nt_sums[(size_t)p * nb + k];
     out[oNT + t] = snt / (double)F.ncell;
     const double ci = centre(i), cj = centre(j), ck = centre(k);
@@ -1038,9 +1071,11 @@ __global__ void k_bispec_finalize(const int* __restrict__ tri, const int* __rest
     const double c13 = (cj * cj - ci * ci - ck * ck) / (2.0 * ci * ck);
     for (int e = 0; e < F.nscoc; ++e) {
       const int l = F.scoc_l[e];
-      const double raw = snt > 0 ? (2 * l + 1) * (l == 0 ? s0 : s2) / (i33 * snt) : 0.0;
+      const double raw = snt > 0 ? (2 * l + 1) * sfam[e] / (i33 * snt) : 0.0;
       double sn = 0.0;
-      if (F.shot == 2 && snt > 0) {
+      if (l & 1) {
+        // odd multipoles: raw estimate (no shot-noise model for them)
+      } else if (F.shot == 2 && snt > 0) {
         // FFT method: two-object terms T23 + T12 + T13 over the closed triplets, minus twice the
         // three-of-one-object part S N_T^(l) (each two-object term holds it once, the pure term once)
         const int pik = pair_index(i, k), pjk = pair_index(j, k);
@@ -1367,6 +1402,10 @@ struct ShellLaunch {
   const void* X;
   const void* XN;   // N-field spectrum for src = 2 fields, or null
   const void* X2;   // Yamamoto X_2 for src = 3 fields, or null
+  const void* X1;   // Yamamoto X_1, X_3 for src = 4, 5 fields, or null
+  const void* X3;
+  const void* XB;   // tracers 2 and 3 of a multi-tracer bispectrum (src = 6, 7), or null
+  const void* XC;
   int KZX, nfine;
   const ShellField* fields;
   int nfield, Kmax;
@@ -1389,13 +1428,15 @@ npc_status shell_passes(npc_ctx* ctx, const ShellLaunch& sl, cplx<T>* T1, cplx<T
   NPC_TRY(get_twiddles(ctx, NS, sizeof(T) == 8 ? NPC_PREC_FP64 : NPC_PREC_MIXED, &twp));
   const C* tw = (const C*)twp;
   {
-    const size_t smem = sizeof(C) * (4 * NS + (size_t)RowGroups<NS, BT>::NBUF * row_pad_len<NS>()) +
+    const size_t smem = sizeof(C) * (8 * NS + (size_t)RowGroups<NS, BT>::NBUF * row_pad_len<NS>()) +
                         sizeof(T) * NS + sizeof(int) * 2 * NS;
     auto kern = sl.has_yw ? k_shell_x<T, NS, true> : k_shell_x<T, NS, false>;
     NPC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int nrows = (sl.Kmax + 1) * (2 * sl.Kmax + 1);
     kern<<<std::min(nrows, ctx->num_sms * 4), BT, smem, ctx->stream>>>(
-        (const C*)sl.X, (const C*)sl.XN, (const C*)sl.X2, sl.KZX, sl.nfine, sl.fields, sl.nfield, sl.Kmax, sl.tab,
+        (const C*)sl.X, (const C*)sl.XN, (const C*)sl.X2, (const C*)sl.X1, (const C*)sl.X3, (const C*)sl.XB,
+        (const C*)sl.XC, sl.KZX, sl.nfine,
+        sl.fields, sl.nfield, sl.Kmax, sl.tab,
         sl.n2cap, sl.frame, tw, T1);
     NPC_LAUNCH(ctx);
   }
@@ -1438,7 +1479,11 @@ npc_status shell_dispatch(npc_ctx* ctx, int NS, const ShellLaunch& sl, cplx<T>* 
 template <typename T, int N>
 npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb, int scoc_mask, int tripo_mask,
                        int shot, const DevCatalog& d, const DevCatalog* r, double* sc, double* dev_out,
-                       int64_t out_len, const SugiReq* sug = nullptr) {
+                       int64_t out_len, const SugiReq* sug = nullptr, const CrossReq* crq = nullptr,
+                       double* sc_own = nullptr) {
+  // multi-tracer bispectra (crq): `sc` holds the combined normalisation, `sc_own` tracer 1's own
+  // scalars (its FKP field needs its alpha)
+  double* const sc_paint = (crq && sc_own) ? sc_own : sc;
   using C = cplx<T>;
   const double kf = 2.0 * M_PI / m.box;
   const double kmax = kb.kmin + kb.nbins * kb.dk;
@@ -1484,6 +1529,11 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
   // survey geometry with the line of sight to each grid point and an l = 2 request: Yamamoto X_2
   // from the Y_2m-weighted transforms instead of L_2(khat . los) X_0
   const bool yam = !m.periodic && m.los != 1 && (((scoc_mask | tripo_mask) & 4) != 0);
+  // odd Scoccimarro multipoles l = 1, 3 (Sec. 2.1: the imaginary part of the closure sum), l on
+  // leg 1: with the line of sight to each grid point the Yamamoto X_l of the Y_lm-weighted
+  // transforms (yamo), otherwise L_l(qhat . los) X_0; raw estimates (no shot noise)
+  const bool want1 = (scoc_mask & 2) != 0, want3 = (scoc_mask & 8) != 0;
+  const bool yamo = !m.periodic && m.los != 1 && (want1 || want3);
 
   // 1. paint + forward transforms of F and N fields
   const size_t rs = sizeof(T);
@@ -1498,77 +1548,111 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
   plan.assign = m.assign;
   plan.kz_keep = KZ;
   plan.fl.nf = 0;
-  auto push = [&](int ph, int l, int mm, int part) {
-    Comp c;
-    c.phase = (int8_t)ph; c.ell = (int8_t)l; c.m = (int8_t)mm; c.part = (int8_t)part;
-    plan.fl.f[plan.fl.nf++] = c;
+  // survey layout: component c = (l, m, part) with its phase-a and phase-b fields adjacent
+  auto build_survey = [&](PowerPlan& pl, YamComps& yc, bool l1, bool l2, bool l3) {
+    pl.fl.nf = 0;
+    yc = YamComps{};
+    auto comp = [&](int l, int mm, int part) {
+      const int c = yc.nc++;
+      yc.l[c] = (int8_t)l; yc.m[c] = (int8_t)mm; yc.part[c] = (int8_t)part;
+      for (int ph = 0; ph < nphase; ++ph) {
+        (ph == 0 ? yc.ia[c] : yc.ib[c]) = (int8_t)pl.fl.nf;
+        Comp f;
+        f.phase = (int8_t)ph; f.ell = (int8_t)l; f.m = (int8_t)mm; f.part = (int8_t)part;
+        pl.fl.f[pl.fl.nf++] = f;
+      }
+    };
+    comp(0, 0, PART_ONE);
+    for (int l = 1; l <= 3; ++l) {
+      if (!(l == 1 ? l1 : (l == 2 ? l2 : l3))) continue;
+      comp(l, 0, PART_RE);
+      for (int mm = 1; mm <= l; ++mm) {
+        comp(l, mm, PART_RE);
+        comp(l, mm, PART_IM);
+      }
+    }
+    yc.nf = pl.fl.nf;
   };
-  if (!yam) {
-    for (int ph = 0; ph < nphase; ++ph) push(ph, 0, 0, PART_ONE);
-  } else if (nphase == 2) {   // the standard interlaced l <= 2 layout (k_fft_x_assemble2 order)
-    push(0, 0, 0, PART_ONE); push(1, 0, 0, PART_ONE);
-    push(0, 2, 0, PART_RE); push(1, 2, 0, PART_RE);
-    push(0, 2, 1, PART_RE); push(0, 2, 1, PART_IM); push(1, 2, 1, PART_RE); push(1, 2, 1, PART_IM);
-    push(0, 2, 2, PART_RE); push(0, 2, 2, PART_IM); push(1, 2, 2, PART_RE); push(1, 2, 2, PART_IM);
-  } else {
-    push(0, 0, 0, PART_ONE); push(0, 2, 0, PART_RE);
-    push(0, 2, 1, PART_RE); push(0, 2, 1, PART_IM); push(0, 2, 2, PART_RE); push(0, 2, 2, PART_IM);
-  }
+  auto build_plain = [&](PowerPlan& pl) {
+    pl.fl.nf = 0;
+    for (int ph = 0; ph < nphase; ++ph) {
+      Comp c;
+      c.phase = (int8_t)ph; c.ell = 0; c.m = 0; c.part = PART_ONE;
+      pl.fl.f[pl.fl.nf++] = c;
+    }
+  };
+  YamComps ycF{}, ycN{};
+  PowerPlan planN = plan;
+  if (yam || yamo) build_survey(plan, ycF, yamo && want1, yam, yamo && want3);
+  else build_plain(plan);
+  if (yam) build_survey(planN, ycN, false, true, false);
+  else build_plain(planN);
+  plan.global_los = (yam || yamo) ? 0 : 1;
+  planN.global_los = yam ? 0 : 1;
   const Geom gyam = make_geom(m);   // observer-relative grid points for the Y weighting
-  const Geom& gfwd = yam ? gyam : geo;
+  const Geom& gfwd = (yam || yamo) ? gyam : geo;
+  const Geom& gfwdN = yam ? gyam : geo;
   const int prec = sizeof(T) == 8 ? NPC_PREC_FP64 : NPC_PREC_MIXED;
   const size_t halfbytes = sizeof(C) * (size_t)plan.fl.nf * KZ * N * N;
   NPC_TRY(ws_get(ctx, "half", 2 * halfbytes, &half));
   C* halfF = (C*)half;
   C* halfN = (C*)((char*)half + halfbytes);
   NPC_TRY(stage_mark(ctx, "alloc"));
-  NPC_TRY(launch_paint(ctx, d, r, m, 1, prec, sc, ma, mb));
+  NPC_TRY(launch_paint(ctx, d, r, m, 1, prec, sc_paint, ma, mb));
   NPC_TRY(stage_mark(ctx, "paint_fold"));
   NPC_TRY(run_forward_transforms(ctx, prec, plan, gfwd, ma, mb, halfF));
   if (shot) {
     NPC_TRY(launch_paint(ctx, d, r, m, 2, prec, sc, ma, mb));
-    NPC_TRY(run_forward_transforms(ctx, prec, plan, gfwd, ma, mb, halfN));
+    NPC_TRY(run_forward_transforms(ctx, prec, planN, gfwdN, ma, mb, halfN));
   }
   NPC_TRY(stage_mark(ctx, "forward_yz"));
 
   const void* twf;
   NPC_TRY(get_twiddles(ctx, N, prec, &twf));
   const C* tw = (const C*)twf;
-  // 2. x pass + combine into X0 (and XN); survey l = 2 also X2 (and N2) at X + 2 xfs (+ 3 xfs)
+  // 2. x pass + combine into X0 (and XN); survey l = 2 also X2 (and N2) at X + 2 xfs (+ 3 xfs), survey
+  //    odd l the Yamamoto X1 at X + 4 xfs and X3 at X + 5 xfs
   C* X;
   const int nout = shot ? 2 : 1;
   const size_t xfs = (size_t)KZ * N * N;
-  NPC_TRY(ws_get(ctx, "bis.X", sizeof(C) * xfs * (yam ? 4 : nout), (void**)&X));
-  if (yam) {
-    const size_t smem =
-        sizeof(C) * (2 * N + (size_t)(12 + RowGroups<N, BT>::NBUF) * row_pad_len<N>()) + sizeof(T) * (N / 2 + 2);
-    auto kern = k_fft_x_assemble2<T, N>;
-    NPC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  NPC_TRY(ws_get(ctx, "bis.X", sizeof(C) * xfs * (crq ? 3 : (yamo ? 6 : (yam ? 4 : nout))), (void**)&X));
+  {
     const int nrows = KZ * (2 * K2 + 1);
     const int grid = std::min(nrows, ctx->num_sms * 4);
-    const YNorm nrm = ylm_norm_table();
-    kern<<<grid, BT, smem, ctx->stream>>>(halfF, nphase, KZ, K2, m.assign, nrm, tw, X, X + 2 * xfs);
-    NPC_LAUNCH(ctx);
-    if (shot) {
-      kern<<<grid, BT, smem, ctx->stream>>>(halfN, nphase, KZ, K2, m.assign, nrm, tw, X + xfs, X + 3 * xfs);
+    auto assemble = [&](const C* src, const YamComps& yc, C* x0, C* x1, C* x2, C* x3) -> npc_status {
+      const size_t smem = sizeof(C) * (2 * N + (size_t)(yc.nf + RowGroups<N, BT>::NBUF) * row_pad_len<N>()) +
+                          sizeof(T) * (N / 2 + 2);
+      if (smem > 227 * 1024) return set_err(ctx, NPC_ERR_UNSUPPORTED, "survey multipoles: mesh too large at this precision");
+      auto kern = k_fft_x_assemble_yam<T, N>;
+      NPC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      kern<<<grid, BT, smem, ctx->stream>>>(src, nphase, KZ, K2, m.assign, ylm_norm_table(), yc, tw, x0, x1, x2, x3);
       NPC_LAUNCH(ctx);
-    }
-  } else {
-    constexpr int TPF = N / 8;
-    constexpr int G = BT / TPF > 0 ? BT / TPF : 1;
-    const int nf = nphase * nout;
-    // F and N halves are separate buffers: combine each
-    for (int o = 0; o < nout; ++o) {
+      return NPC_OK;
+    };
+    auto combine = [&](const C* src, C* dst) -> npc_status {
       const size_t smem =
           sizeof(C) * (2 * N + (size_t)(nphase + RowGroups<N, BT>::NBUF) * row_pad_len<N>()) + sizeof(T) * (N / 2 + 2);
       auto kern = k_fft_x_combine<T, N>;
       NPC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      const int nrows = KZ * (2 * K2 + 1);
-      const int grid = std::min(nrows, ctx->num_sms * 4);
-      kern<<<grid, BT, smem, ctx->stream>>>(o == 0 ? halfF : halfN, 1, nphase, KZ, K2, m.assign, tw, X + (size_t)o * xfs);
+      kern<<<grid, BT, smem, ctx->stream>>>(src, 1, nphase, KZ, K2, m.assign, tw, dst);
       NPC_LAUNCH(ctx);
+      return NPC_OK;
+    };
+    if (yam || yamo)
+      NPC_TRY(assemble(halfF, ycF, X, (yamo && want1) ? X + 4 * xfs : nullptr, yam ? X + 2 * xfs : nullptr,
+                       (yamo && want3) ? X + 5 * xfs : nullptr));
+    else
+      NPC_TRY(combine(halfF, X));
+    if (shot) {
+      if (yam) NPC_TRY(assemble(halfN, ycN, X + xfs, nullptr, X + 3 * xfs, nullptr));
+      else NPC_TRY(combine(halfN, X + xfs));
     }
-    (void)nf;
+    // tracers 2 and 3 of a multi-tracer bispectrum: X at X + xfs and X + 2 xfs
+    for (int t = 0; crq && t < 2; ++t) {
+      NPC_TRY(launch_paint(ctx, crq->d[t], crq->has_r ? &crq->r[t] : nullptr, m, 1, prec, crq->sc[t], ma, mb));
+      NPC_TRY(run_forward_transforms(ctx, prec, plan, gfwd, ma, mb, halfF));
+      NPC_TRY(combine(halfF, X + (size_t)(1 + t) * xfs));
+    }
   }
   NPC_TRY(stage_mark(ctx, "forward_x_combine"));
 
@@ -1684,21 +1768,40 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
 
   std::vector<ShellField> fl;
   std::vector<int> ffam;   // field family (z-pass pairs stay within a family)
-  auto add = [&](int src, int mult, int bin, int Kf, int fam) {
+  auto add = [&](int src, int mult, int bin, int Kf, int fam, int lmult = 2) {
     ShellField f{};
     f.src = (int8_t)src; f.mult = (int8_t)mult; f.bin = (int16_t)bin; f.K = Kf;
+    if (mult == 1) f.yl = (int8_t)lmult;   // L_l(mu) weight
     fl.push_back(f);
     ffam.push_back(fam);
   };
   for (int b = 0; b < nb; ++b) add(0, 0, b, Ks, 0);              // F0_b: R index b
   if (want2) for (int b = 0; b < nb; ++b) add(yam ? 3 : 0, yam ? 0 : 1, b, Ks, 1);   // F2_b: R index nb + b
   const int iF2 = want2 ? nb : -1;
+  int iFB = 0, iFC = 0;   // shells of the legs 2 and 3 (F_0 of the same catalogue unless multi-tracer)
+  if (crq) {
+    iFB = (int)fl.size();
+    for (int b = 0; b < nb; ++b) add(6, 0, b, Ks, 20);
+    iFC = (int)fl.size();
+    for (int b = 0; b < nb; ++b) add(7, 0, b, Ks, 21);
+  }
+  // odd multipoles: shells of -i X_l (survey: Yamamoto X_1 / X_3; global: L_l(mu) X_0)
+  int iFodd[4] = {-1, -1, -1, -1};
+  for (int l = 1; l <= 3; l += 2) {
+    if (!(scoc_mask & (1 << l))) continue;
+    iFodd[l] = (int)fl.size();
+    for (int b = 0; b < nb; ++b) {
+      if (yamo) add(l == 1 ? 4 : 5, 0, b, Ks, 10 + l);
+      else add(0, 1, b, Ks, 10 + l, l);
+    }
+  }
   const int iI = (int)fl.size();
   if (need_nt || fftshot) for (int b = 0; b < nb; ++b) add(1, 0, b, Ks, 2);   // I_b
   const int iG = (int)fl.size();
   int ng = 0;
-  if (wantG0) { add(0, 0, -1, KG, 3); ng++; }
-  if (wantG2) { add(yam ? 3 : 0, yam ? 0 : 1, -1, KG, 3); ng++; }
+  const int gsrc = crq ? 7 : 0;   // the compressed estimator's full-range field: leg 3's tracer
+  if (wantG0) { add(gsrc, 0, -1, KG, 3); ng++; }
+  if (wantG2) { add(yam ? 3 : gsrc, yam ? 0 : 1, -1, KG, 3); ng++; }
   int iS0 = -1, iS2 = -1, iI2 = -1, iSF = -1, iLF = -1;
   int ntl = 0, tls[2] = {0, 0};   // compressed multipoles requested
   for (int l = 0; l <= 2; l += 2)
@@ -1891,6 +1994,10 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
     sl.X = X;
     sl.XN = fftshot ? (const void*)(X + xfs) : nullptr;
     sl.X2 = yam ? (const void*)(X + 2 * xfs) : nullptr;
+    sl.X1 = (yamo && want1) ? (const void*)(X + 4 * xfs) : nullptr;
+    sl.X3 = (yamo && want3) ? (const void*)(X + 5 * xfs) : nullptr;
+    sl.XB = crq ? (const void*)(X + xfs) : nullptr;
+    sl.XC = crq ? (const void*)(X + 2 * xfs) : nullptr;
     sl.KZX = KZ;
     sl.nfine = N;
     sl.fields = dfields;
@@ -1914,6 +2021,7 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
 
   // 5. triple products
   if (nb > NB_MAX) return set_err(ctx, NPC_ERR_UNSUPPORTED, "at most %d bins", NB_MAX);
+  int fam_of_l[4] = {0, -1, -1, -1};   // row family of B_l in the data launch
   auto setup = [&](TripleArgs& a, bool indicator) {
     a = TripleArgs{};
     a.npair = npair;
@@ -1932,11 +2040,25 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
       a.nrows = npair;
       a.ncol = nb;
     } else {
-      for (int b = 0; b < nb; ++b) a.a_slot[0][b] = a.b_slot[0][b] = a.b_slot[1][b] = a.c_slot[b] = stage_of(b);
-      if (want2)
-        for (int b = 0; b < nb; ++b) a.a_slot[1][b] = stage_of(iF2 + b);
+      for (int b = 0; b < nb; ++b) {
+        a.a_slot[0][b] = stage_of(b);
+        a.b_slot[0][b] = stage_of(iFB + b);
+        a.c_slot[b] = stage_of(iFC + b);
+      }
+      // further row families: A = F_l (l = 2, 1, 3 as requested), B = F_0
+      int nfam = 1;
+      auto family_rows = [&](int first) {
+        for (int b = 0; b < nb; ++b) {
+          a.a_slot[nfam][b] = stage_of(first + b);
+          a.b_slot[nfam][b] = stage_of(iFB + b);
+        }
+        return nfam++;
+      };
+      if (want2) fam_of_l[2] = family_rows(iF2);
+      if (iFodd[1] >= 0) fam_of_l[1] = family_rows(iFodd[1]);
+      if (iFodd[3] >= 0) fam_of_l[3] = family_rows(iFodd[3]);
       for (int l = 0; l < ng; ++l) a.c_slot[nb + l] = stage_of(iG + l);
-      a.nrows = npair * (want2 ? 2 : 1);
+      a.nrows = npair * nfam;
       a.ncol = nb + ng;
     }
   };
@@ -2026,12 +2148,13 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
         // tensor-core (tcgen05) path: up to three 128-row tiles per CTA
         const int nt = std::min(3, (a.nrows + 127) / 128);
         const int groups = (a.nrows + nt * 128 - 1) / (nt * 128);
-        const size_t smem = tc_triple_smem(a.nstage);
+        const int nbuf = tc_triple_smem(a.nstage, 3, nt) <= 200 * 1024 ? 3 : 2;
+        const size_t smem = tc_triple_smem(a.nstage, nbuf, nt);
         auto go = [&](auto kern) -> npc_status {
           NPC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-          kern<<<dim3(grid, groups), nt * 128 + 32, smem, ctx->stream>>>(
+          kern<<<dim3(grid, groups), nt * 256 + 32, smem, ctx->stream>>>(
               (const float*)R, a, (const int*)(dtab + tp), (const int*)(dtab + trp), part, ctx->dev_status,
-              wait_cycles(ctx));
+              wait_cycles(ctx), nbuf);
           return NPC_OK;
         };
         NPC_TRY(nt == 1 ? go(k_triple_tc<1>) : nt == 2 ? go(k_triple_tc<2>) : go(k_triple_tc<3>));
@@ -2197,8 +2320,11 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
   fa.npair = npair;
   fa.nq = nq;
   fa.nscoc = 0;
-  for (int l = 0; l <= 2; l += 2)
-    if (scoc_mask & (1 << l)) fa.scoc_l[fa.nscoc++] = l;
+  for (int l = 0; l <= 3; ++l)
+    if (scoc_mask & (1 << l)) {
+      fa.scoc_fam[fa.nscoc] = fam_of_l[l];
+      fa.scoc_l[fa.nscoc++] = l;
+    }
   fa.ntripo = 0;
   for (int l = 0; l <= 2; l += 2)
     if (tripo_mask & (1 << l)) fa.tripo_l[fa.ntripo++] = l;
@@ -2206,7 +2332,6 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
   fa.nparts = 1;   // partials already summed over the CTAs
   fa.nrows = ta.nrows;
   fa.ncol = ta.ncol;
-  fa.has2 = want2 ? 1 : 0;
   fa.ncell = (int64_t)ncs;
   fa.kmin = kb.kmin;
   fa.dk = kb.dk;
@@ -2233,19 +2358,19 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
 template <typename T>
 npc_status bispec_dispatch(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb, int sm, int tm, int shot,
                            const DevCatalog& d, const DevCatalog* r, double* sc, double* out, int64_t len,
-                           const SugiReq* sug = nullptr) {
+                           const SugiReq* sug = nullptr, const CrossReq* crq = nullptr, double* sc_own = nullptr) {
   switch (m.n) {
-    case 16: return bispec_impl<T, 16>(ctx, m, kb, sm, tm, shot, d, r, sc, out, len, sug);
-    case 32: return bispec_impl<T, 32>(ctx, m, kb, sm, tm, shot, d, r, sc, out, len, sug);
-    case 64: return bispec_impl<T, 64>(ctx, m, kb, sm, tm, shot, d, r, sc, out, len, sug);
-    case 128: return bispec_impl<T, 128>(ctx, m, kb, sm, tm, shot, d, r, sc, out, len, sug);
-    case 256: return bispec_impl<T, 256>(ctx, m, kb, sm, tm, shot, d, r, sc, out, len, sug);
-    case 48: return bispec_impl<T, 48>(ctx, m, kb, sm, tm, shot, d, r, sc, out, len, sug);
-    case 96: return bispec_impl<T, 96>(ctx, m, kb, sm, tm, shot, d, r, sc, out, len, sug);
-    case 192: return bispec_impl<T, 192>(ctx, m, kb, sm, tm, shot, d, r, sc, out, len, sug);
+    case 16: return bispec_impl<T, 16>(ctx, m, kb, sm, tm, shot, d, r, sc, out, len, sug, crq, sc_own);
+    case 32: return bispec_impl<T, 32>(ctx, m, kb, sm, tm, shot, d, r, sc, out, len, sug, crq, sc_own);
+    case 64: return bispec_impl<T, 64>(ctx, m, kb, sm, tm, shot, d, r, sc, out, len, sug, crq, sc_own);
+    case 128: return bispec_impl<T, 128>(ctx, m, kb, sm, tm, shot, d, r, sc, out, len, sug, crq, sc_own);
+    case 256: return bispec_impl<T, 256>(ctx, m, kb, sm, tm, shot, d, r, sc, out, len, sug, crq, sc_own);
+    case 48: return bispec_impl<T, 48>(ctx, m, kb, sm, tm, shot, d, r, sc, out, len, sug, crq, sc_own);
+    case 96: return bispec_impl<T, 96>(ctx, m, kb, sm, tm, shot, d, r, sc, out, len, sug, crq, sc_own);
+    case 192: return bispec_impl<T, 192>(ctx, m, kb, sm, tm, shot, d, r, sc, out, len, sug, crq, sc_own);
   }
   if constexpr (sizeof(T) == 4) {
-    if (m.n == 512) return bispec_impl<T, 512>(ctx, m, kb, sm, tm, shot, d, r, sc, out, len, sug);
+    if (m.n == 512) return bispec_impl<T, 512>(ctx, m, kb, sm, tm, shot, d, r, sc, out, len, sug, crq, sc_own);
   }
   return set_err(ctx, NPC_ERR_UNSUPPORTED, "bispectrum mesh size %d not supported at this precision", m.n);
 }
@@ -2258,6 +2383,14 @@ npc_status run_bispectrum(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins&
   if (prec == NPC_PREC_FP64)
     return bispec_dispatch<double>(ctx, m, kb, scoc_mask, tripo_mask, shot, d, r, sc, out, len);
   return bispec_dispatch<float>(ctx, m, kb, scoc_mask, tripo_mask, shot, d, r, sc, out, len);
+}
+
+npc_status run_bispectrum_cross(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb, int scoc_mask,
+                                int tripo_mask, int prec, const DevCatalog& d, const DevCatalog* r, double* sc1,
+                                double* scx, const CrossReq& req, double* out, int64_t len) {
+  if (prec == NPC_PREC_FP64)
+    return bispec_dispatch<double>(ctx, m, kb, scoc_mask, tripo_mask, 0, d, r, scx, out, len, nullptr, &req, sc1);
+  return bispec_dispatch<float>(ctx, m, kb, scoc_mask, tripo_mask, 0, d, r, scx, out, len, nullptr, &req, sc1);
 }
 
 npc_status run_bispectrum_sugiyama(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb, const SugiReq& req,

@@ -611,7 +611,24 @@ __global__ void k_cross_scalars(const double* __restrict__ sa, const double* __r
   sx[SC_SUMW2] = sb[SC_SUMWG];
 }
 
+// Scalars of a three-tracer bispectrum: tracer 1's values with I33 replaced by the geometric mean
+// (I33^1 I33^2 I33^3)^(1/3) (the normalisation of the cross bispectra, Sec. 6 reading) and S3 = 0
+// (no shot noise is subtracted from the raw cross estimates).
+__global__ void k_cross3_scalars(const double* __restrict__ s1, const double* __restrict__ s2,
+                                 const double* __restrict__ s3, double* __restrict__ sx) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int i = 0; i < SC_COUNT; ++i) sx[i] = s1[i];
+  sx[SC_I33] = cbrt(s1[SC_I33] * s2[SC_I33] * s3[SC_I33]);
+  sx[SC_S3] = 0.0;
+}
+
 }  // namespace
+
+npc_status launch_cross3_scalars(npc_ctx* ctx, const double* s1, const double* s2, const double* s3, double* sx) {
+  k_cross3_scalars<<<1, 32, 0, ctx->stream>>>(s1, s2, s3, sx);
+  NPC_LAUNCH(ctx);
+  return NPC_OK;
+}
 
 npc_status launch_cross_scalars(npc_ctx* ctx, const double* sa, const double* sb, double* sx) {
   k_cross_scalars<<<1, 32, 0, ctx->stream>>>(sa, sb, sx);

@@ -278,6 +278,7 @@ npc_status launch_catalog_scalars(npc_ctx* ctx, const DevCatalog& d, const DevCa
                                   double* dev_scalars);
 // Cross-spectrum scalars from tracers A and B (output slots documented with npc_cross_power_multipoles).
 npc_status launch_cross_scalars(npc_ctx* ctx, const double* sa, const double* sb, double* sx);
+npc_status launch_cross3_scalars(npc_ctx* ctx, const double* s1, const double* s2, const double* s3, double* sx);
 
 // Paint the FKP field (weight_power 1) or the N-field (2) on 1 or 2 interlacing phases.
 // meshes: nphase pointers to n^3 arrays of T (layout [z][y][x]).
@@ -345,3 +346,14 @@ npc_status run_bispectrum_sugiyama(npc_ctx* ctx, const npc_mesh_spec& m, const n
                                    int shot, int prec, const DevCatalog& d, const DevCatalog* r, double* sc,
                                    double* out, int64_t len);
 npc_status bispec_triangles(const npc_kbins& kb, int32_t* tri, int64_t cap, int64_t* ntri);
+// multi-tracer bispectra: tracers 2 and 3 (tracer 1 is the call's catalogue), with their randoms
+// (survey geometry) and catalogue scalars
+struct CrossReq {
+  DevCatalog d[2];
+  DevCatalog r[2];
+  bool has_r;
+  double* sc[2];
+};
+npc_status run_bispectrum_cross(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb, int scoc_mask,
+                                int tripo_mask, int prec, const DevCatalog& d, const DevCatalog* r, double* sc1,
+                                double* scx, const CrossReq& req, double* out, int64_t len);

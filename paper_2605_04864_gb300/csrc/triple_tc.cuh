@@ -3,11 +3,11 @@
 // The contraction of Eq. bi_sco / Eq. new_bispec in real space,
 //     D[row, col] = sum_x A_i(x) B_j(x) C_col(x)      (row = pair (i, j) of a family, col = k or G),
 // is a GEMM with M = rows, N = columns (<= 32) and K = cells.  Per CTA:
-//   * NT row tiles of 128 rows (thread = row, four warps per tile), one control warp;
+//   * NT row tiles of 128 rows (two threads per row, eight warps per tile), one control warp;
 //   * the staged fields of a chunk of 128 cells arrive by bulk asynchronous copies (the TMA unit,
-//     one 512-byte copy per field) into a ring of TC_NBUF shared-memory buffers, completed on an
+//     one 512-byte copy per field) into a ring of two or three shared-memory buffers, completed on an
 //     mbarrier with a transaction count;
-//   * each producer thread forms its row's pair products P = A_i B_j for 32 cells (one A stage),
+//   * each producer thread forms its row's pair products P = A_i B_j for 16 of the 32 cells of an A stage,
 //     splits them into tf32 hi + lo and writes both straight into tensor memory (tcgen05.st): the A
 //     operand never passes through shared memory;
 //   * the producers also write the column operand (hi and lo) into shared memory in the canonical
@@ -16,8 +16,8 @@
 //     (tcgen05.mma kind::tf32, M = 128, N = 32, A from tensor memory, B from a shared-memory
 //     descriptor) into an FP32 accumulator in tensor memory, and commits each A stage to an
 //     mbarrier that frees its buffers;
-//   * every TC_FLUSH A stages (4096 cells) the producers read the accumulator back (tcgen05.ld),
-//     add it into float64 registers, and the next products start a fresh accumulator;
+//   * every FLUSH A stages (4096 cells) the producers read the accumulator back (tcgen05.ld),
+//     add it into float64 sums in shared memory, and the next products start a fresh accumulator;
 //   * at the end each producer writes its row's float64 sums as the CTA's partials
 //     part[cta][row][col], reduced in a fixed order by the same kernels as the other paths.
 // Every wait is bounded (clock64 against `limit`); on expiry the kernel records NPC_ERR_TIMEOUT in
@@ -32,7 +32,6 @@ namespace tc {
 constexpr int CHUNK = 128;        // cells per bulk-copy chunk (512 bytes per staged field)
 constexpr int SROW = CHUNK + 4;   // floats between staged field rows: 16-byte aligned, and rows
                                   // fall 16 bytes apart modulo 128 (conflict-light 16-byte reads)
-constexpr int NBUF = 3;           // chunk buffers in flight
 constexpr int AST = 32;           // cells per A stage (four k steps of 8)
 constexpr int FLUSH = 128;        // A stages between float64 flushes
 constexpr int NCOL = 32;          // MMA N (columns, padded)
@@ -108,23 +107,26 @@ __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence:
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+// TMEM stores read their registers at issue; completion (tcgen05.wait::st) is awaited before the
+// thread synchronisation that hands the stage to the MMA thread.  No memory clobber: tensor memory
+// is not addressable memory, and ordinary loads may move across the store.
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
   asm volatile(
       "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
       "%15, %16};" ::"r"(taddr),
       "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
-      "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
-      : "memory");
+      "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]));
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+// 16 columns of this warp's 32 lanes, with the wait in the same statement so that no use of the
+// registers can be scheduled before the data has arrived
+__device__ __forceinline__ void tmem_ld16_wait(uint32_t taddr, uint32_t (&v)[16]) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
       : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
-        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
-        "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
-        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
       : "r"(taddr)
       : "memory");
 }
@@ -158,7 +160,7 @@ __device__ __forceinline__ void split(float v, uint32_t& hi, uint32_t& lo) {
 }
 
 struct Smem {
-  uint64_t full_tma[NBUF];  // chunk buffer filled (transaction count)
+  uint64_t full_tma[3];     // chunk buffer filled (transaction count)
   uint64_t full_a[2];       // A stage written by every producer warp
   uint64_t empty_a[2];      // products of an A stage complete (tcgen05.commit)
   uint64_t drain;           // clean-up commit
@@ -168,22 +170,25 @@ struct Smem {
 
 }  // namespace tc
 
-// grid = (CTAs over the cells, row groups of NT x 128 rows); block = NT x 128 producers + one
-// control warp.  Requires ncell % 128 == 0, ncol <= 32; dynamic shared memory = tc_triple_smem().
+// grid = (CTAs over the cells, row groups of NT x 128 rows); block = NT x 256 producers (two per
+// row: warp 8t + 4h + q serves tile t, lanes 32q.. of tensor memory, cells 16h.. of each A stage)
+// + one control warp.  Requires ncell % 128 == 0, ncol <= 32; nbuf = 2 or 3 chunk buffers;
+// dynamic shared memory = tc_triple_smem(nstage, nbuf, NT).
 template <int NT>
-__global__ void __launch_bounds__(NT * 128 + 32, 1)
+__global__ void __launch_bounds__(NT * 256 + 32, 1)
 k_triple_tc(const float* __restrict__ R, const __grid_constant__ TripleArgs A, const int* __restrict__ pair_ij,
-            const int* __restrict__ row_pair, double* __restrict__ part, int* status, long long limit) {
+            const int* __restrict__ row_pair, double* __restrict__ part, int* status, long long limit, int nbuf) {
   using namespace tc;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* buf = reinterpret_cast<float*>(smem_raw);                                   // [NBUF][nstage][SROW]
-  const size_t buf_bytes = (size_t)NBUF * A.nstage * SROW * sizeof(float);
+  float* buf = reinterpret_cast<float*>(smem_raw);                                   // [nbuf][nstage][SROW]
+  const size_t buf_bytes = (size_t)nbuf * A.nstage * SROW * sizeof(float);
   unsigned char* btile = smem_raw + ((buf_bytes + 1023) & ~(size_t)1023);            // [2 sb][2 hl][4 k][1 KB]
-  Smem* sm = reinterpret_cast<Smem*>(btile + 2 * 2 * 4 * BTILE);
+  double* accs = reinterpret_cast<double*>(btile + 2 * 2 * 4 * BTILE);              // [NCOL][NT * 128]
+  Smem* sm = reinterpret_cast<Smem*>(accs + (size_t)NCOL * NT * 128);
   volatile int* abort = &sm->abort;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int ctrl = NT * 4;  // control warp index
+  const int ctrl = NT * 8;  // control warp index
   constexpr uint32_t NCOLS = tmem_cols(NT);
 
   // cell range of this CTA, in whole chunks
@@ -195,15 +200,16 @@ k_triple_tc(const float* __restrict__ R, const __grid_constant__ TripleArgs A, c
   const int nst = nchunk * (CHUNK / AST);
   const int64_t cell0 = c_beg * CHUNK;
 
+  for (int i = tid; i < NCOL * NT * 128; i += blockDim.x) accs[i] = 0.0;
   if (warp == ctrl) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sm->tmem_base)),
                  "r"(NCOLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     if (lane == 0) {
-      for (int b = 0; b < NBUF; ++b) mbar_init(&sm->full_tma[b], 1);
+      for (int b = 0; b < nbuf; ++b) mbar_init(&sm->full_tma[b], 1);
       for (int b = 0; b < 2; ++b) {
-        mbar_init(&sm->full_a[b], NT * 4);
+        mbar_init(&sm->full_a[b], NT * 8);
         mbar_init(&sm->empty_a[b], 1);
       }
       mbar_init(&sm->drain, 1);
@@ -221,18 +227,17 @@ k_triple_tc(const float* __restrict__ R, const __grid_constant__ TripleArgs A, c
       // ---- control thread: bulk copies of the staged fields, and the tensor-core products ----
       int issued = 0;
       auto issue = [&](int c) {
-        const int b = c % NBUF;
+        const int b = c % nbuf;
         mbar_arrive_tx(&sm->full_tma[b], (uint32_t)(A.nstage * CHUNK * sizeof(float)));
         for (int s = 0; s < A.nstage; ++s)
           bulk_g2s(buf + ((size_t)b * A.nstage + s) * SROW,
                    R + (size_t)A.stage_field[s] * A.ncell + cell0 + (int64_t)c * CHUNK, CHUNK * sizeof(float),
                    &sm->full_tma[b]);
       };
-      for (; issued < min(NBUF, nchunk); ++issued) issue(issued);
-      const uint32_t bt0 = smem_u32(btile);
+      for (; issued < min(nbuf, nchunk); ++issued) issue(issued);
+      const uint64_t bdesc0 = sdesc(smem_u32(btile), 128, 256);
       bool ok = true;
-      int s = 0;
-      for (; s < nst; ++s) {
+      for (int s = 0; s < nst; ++s) {
         const int sb = s & 1;
         if (!mbar_wait(&sm->full_a[sb], (uint32_t)((s >> 1) & 1), limit, abort, status)) {
           ok = false;
@@ -247,8 +252,9 @@ k_triple_tc(const float* __restrict__ R, const __grid_constant__ TripleArgs A, c
           for (int j = 0; j < AST / 8; ++j) {
             const uint32_t ahi = tbase + col_a(sb, t, 0, NT) + 8 * j;
             const uint32_t alo = tbase + col_a(sb, t, 1, NT) + 8 * j;
-            const uint64_t bh = sdesc(bt0 + (uint32_t)(((sb * 2 + 0) * 4 + j) * BTILE), 128, 256);
-            const uint64_t bl = sdesc(bt0 + (uint32_t)(((sb * 2 + 1) * 4 + j) * BTILE), 128, 256);
+            // the descriptor's start address field counts 16-byte units
+            const uint64_t bh = bdesc0 + (uint64_t)((((sb * 2 + 0) * 4 + j) * BTILE) >> 4);
+            const uint64_t bl = bdesc0 + (uint64_t)((((sb * 2 + 1) * 4 + j) * BTILE) >> 4);
             mma_tf32(d, ahi, bh, (fresh && j == 0) ? 0u : 1u);
             mma_tf32(d, ahi, bl, 1u);
             mma_tf32(d, alo, bh, 1u);
@@ -258,59 +264,59 @@ k_triple_tc(const float* __restrict__ R, const __grid_constant__ TripleArgs A, c
         // the last A stage of chunk c has been read by every producer: its buffer is free
         if ((s % (CHUNK / AST)) == CHUNK / AST - 1 && issued < nchunk) issue(issued++);
       }
-      if (!ok) {
-        // clean up: every product issued so far, and every copy in flight, must finish before
-        // tensor memory is freed and the CTA exits
-        mma_commit(&sm->drain);
-        mbar_drain(&sm->drain, 0);
-        for (int c = max(0, issued - NBUF); c < issued; ++c) mbar_drain(&sm->full_tma[c % NBUF], (uint32_t)((c / NBUF) & 1));
-      }
+      // every product issued must finish before tensor memory is freed (the producers have waited
+      // for them unless a wait gave up)
+      mma_commit(&sm->drain);
+      mbar_drain(&sm->drain, 0);
+      if (!ok || *abort)
+        for (int c = max(0, issued - nbuf); c < issued; ++c) mbar_drain(&sm->full_tma[c % nbuf], (uint32_t)((c / nbuf) & 1));
     }
     __syncwarp();
   } else {
-    // ---- producers: thread = row ----
-    const int t = warp >> 2, q = warp & 3;
-    const int row = blockIdx.y * (NT * 128) + t * 128 + q * 32 + lane;
-    int sa = -1, sbs = -1, orow = -1;
+    // ---- producers: two threads per row ----
+    const int t = warp >> 3, h = (warp >> 2) & 1, q = warp & 3;
+    const int lrow = t * 128 + q * 32 + lane;         // row within the CTA's group
+    const int row = blockIdx.y * (NT * 128) + lrow;
+    int sa = -1, sbs = -1;
     if (row < A.nrows) {
       const int fam = row / A.npair, p = row_pair[row % A.npair];
       const int pij = pair_ij[p];
       sa = A.a_slot[fam][pij & 0xffff];
       sbs = A.b_slot[fam][pij >> 16];
-      orow = fam * A.npair + p;
     }
-    // the column operand: this warp writes the core matrices cm = warp, warp + 4 NT, ... (< 32);
+    // the column operand: this warp writes the core matrices cm = warp, warp + 8 NT (< 32);
     // cm % 4 = warp % 4 is the 8-column group, lane / 4 the column within it, lane % 4 the cell
     const int ncol_here = q * 8 + (lane >> 2);
     const int cslot = ncol_here < A.ncol ? A.c_slot[ncol_here] : -1;
     const uint32_t lane_addr = tbase + ((uint32_t)(q * 32) << 16);
-    double acc[NCOL];
-#pragma unroll
-    for (int c = 0; c < NCOL; ++c) acc[c] = 0.0;
     for (int s = 0; s < nst; ++s) {
       const int sb = s & 1;
       const int c = s / (CHUNK / AST);
       const int o = (s % (CHUNK / AST)) * AST;
-      const int b = c % NBUF;
-      if ((s % (CHUNK / AST)) == 0 && !mbar_wait(&sm->full_tma[b], (uint32_t)((c / NBUF) & 1), limit, abort, status))
+      const int b = c % nbuf;
+      if ((s % (CHUNK / AST)) == 0 && !mbar_wait(&sm->full_tma[b], (uint32_t)((c / nbuf) & 1), limit, abort, status))
         break;
       if (s >= 2 && !mbar_wait(&sm->empty_a[sb], (uint32_t)(((s - 2) >> 1) & 1), limit, abort, status)) break;
       tc_fence_after();
       const float* stage = buf + (size_t)b * A.nstage * SROW;
-      // A operand: pair products of this row, hi and lo, 16 cells per store
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
+      // A operand: pair products of this row for cells o + 16 h .. + 16, hi and lo
+      {
         uint32_t vh[16], vl[16];
         if (sa >= 0) {
           const float4* pa = reinterpret_cast<const float4*>(stage + (size_t)sa * SROW + o + 16 * h);
           const float4* pb = reinterpret_cast<const float4*>(stage + (size_t)sbs * SROW + o + 16 * h);
+          float4 x[4], y[4];
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
-            const float4 x = pa[u], y = pb[u];
-            split(x.x * y.x, vh[4 * u + 0], vl[4 * u + 0]);
-            split(x.y * y.y, vh[4 * u + 1], vl[4 * u + 1]);
-            split(x.z * y.z, vh[4 * u + 2], vl[4 * u + 2]);
-            split(x.w * y.w, vh[4 * u + 3], vl[4 * u + 3]);
+            x[u] = pa[u];
+            y[u] = pb[u];
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            split(x[u].x * y[u].x, vh[4 * u + 0], vl[4 * u + 0]);
+            split(x[u].y * y[u].y, vh[4 * u + 1], vl[4 * u + 1]);
+            split(x[u].z * y[u].z, vh[4 * u + 2], vl[4 * u + 2]);
+            split(x[u].w * y[u].w, vh[4 * u + 3], vl[4 * u + 3]);
           }
         } else {
 #pragma unroll
@@ -320,7 +326,7 @@ k_triple_tc(const float* __restrict__ R, const __grid_constant__ TripleArgs A, c
         tmem_st16(lane_addr + col_a(sb, t, 1, NT) + 16 * h, vl);
       }
       // B operand: core matrices of 8 columns x 4 cells, k step j = cm / 8, K half kh = (cm / 4) % 2
-      for (int cm = warp; cm < 32; cm += NT * 4) {
+      for (int cm = warp; cm < 32; cm += NT * 8) {
         const int j = cm >> 3, kh = (cm >> 2) & 1;
         const int cell = o + 8 * j + 4 * kh + (lane & 3);
         const float v = cslot >= 0 ? stage[(size_t)cslot * SROW + cell] : 0.f;
@@ -338,30 +344,34 @@ k_triple_tc(const float* __restrict__ R, const __grid_constant__ TripleArgs A, c
       if ((s % FLUSH) == FLUSH - 1 || s == nst - 1) {
         if (!mbar_wait(&sm->empty_a[sb], (uint32_t)((s >> 1) & 1), limit, abort, status)) break;
         tc_fence_after();
-        uint32_t v[NCOL];
-        tmem_ld32(lane_addr + col_d(t, NT), v);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        uint32_t v[16];
+        tmem_ld16_wait(lane_addr + col_d(t, NT) + 16 * h, v);
 #pragma unroll
-        for (int cc = 0; cc < NCOL; ++cc) acc[cc] += (double)__uint_as_float(v[cc]);
+        for (int cc = 0; cc < 16; ++cc) accs[(size_t)(16 * h + cc) * (NT * 128) + lrow] += (double)__uint_as_float(v[cc]);
         tc_fence_before();
       }
-    }
-    if (orow >= 0 && !*abort) {
-      double* dst = part + ((size_t)blockIdx.x * A.nrows + orow) * A.ncol;
-#pragma unroll
-      for (int cc = 0; cc < NCOL; ++cc)
-        if (cc < A.ncol) dst[cc] = acc[cc];
     }
   }
   __syncthreads();
   if (warp == ctrl) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(NCOLS) : "memory");
+  } else if (!*abort) {
+    // this CTA's float64 sums as part[cta][row][col]
+    const int t = warp >> 3, h = (warp >> 2) & 1, q = warp & 3;
+    const int lrow = t * 128 + q * 32 + lane;
+    const int row = blockIdx.y * (NT * 128) + lrow;
+    if (row < A.nrows) {
+      const int fam = row / A.npair, p = row_pair[row % A.npair];
+      double* dst = part + ((size_t)blockIdx.x * A.nrows + fam * A.npair + p) * A.ncol;
+      for (int cc = 16 * h; cc < 16 * h + 16 && cc < A.ncol; ++cc) dst[cc] = accs[(size_t)cc * (NT * 128) + lrow];
+    }
   }
 }
 
-// dynamic shared memory of k_triple_tc for `nstage` staged fields
-inline size_t tc_triple_smem(int nstage) {
-  const size_t buf = (size_t)tc::NBUF * nstage * tc::SROW * sizeof(float);
-  return ((buf + 1023) & ~(size_t)1023) + 2 * 2 * 4 * tc::BTILE + sizeof(tc::Smem);
+// dynamic shared memory of k_triple_tc<NT> for `nstage` staged fields and `nbuf` chunk buffers
+inline size_t tc_triple_smem(int nstage, int nbuf, int nt) {
+  const size_t buf = (size_t)nbuf * nstage * tc::SROW * sizeof(float);
+  return ((buf + 1023) & ~(size_t)1023) + 2 * 2 * 4 * tc::BTILE + sizeof(double) * tc::NCOL * nt * 128 +
+         sizeof(tc::Smem);
 }

@@ -150,6 +150,63 @@ def test_survey_l2_endpoint_line_of_sight(api, assign, interlace, prec, tol):
     _check(res, orc, tol)
 
 
+def _check_odd(res, orc, ells, tol):
+    """Odd multipoles (raw, imaginary part) against the oracle, relative to the raw monopole scale of
+    the same triangle; their reported shot noise is zero."""
+    np.testing.assert_array_equal(res["tri"], orc["tri"])
+    scale = np.abs(res["B"][0] + res["shot_B"][0])
+    for l in ells:
+        e = np.abs(res["B"][l] - orc["B"][l]) / np.maximum(np.abs(orc["B"][l]), scale)
+        assert np.max(e) < tol, (l, np.max(e))
+        assert np.all(res["shot_B"][l] == 0)
+    assert max(np.max(np.abs(orc["B"][l]) / scale) for l in ells) > 1e-4   # the odd parts are not all zero
+
+
+@pytest.mark.parametrize("assign,interlace,prec,tol", [(3, 1, "fp64", 1e-10), (2, 0, "fp64", 1e-10),
+                                                      (3, 1, "mixed", 1e-4)])
+def test_survey_odd_multipoles_endpoint_line_of_sight(api, assign, interlace, prec, tol):
+    """Survey geometry with the line of sight to each grid point: B_1 and B_3 (Yamamoto X_1, X_3 from
+    the Y_1m- and Y_3m-weighted transforms, imaginary part of the closure sum), requested together
+    with B_0, B_2 and the compressed multipoles, against the oracle's odd multipoles."""
+    from synthetic import make_survey_catalogs
+
+    box = 600.0
+    g, r, origin = make_survey_catalogs(20000, 200000, box, 700.0, 32, seed=79, fkp_p0=1e4)
+    kf = 2 * np.pi / box
+    kb = (2 * kf, 1.5 * kf, 4)
+    res = api.bispectrum(g, n=32, box=box, kbins=kb, assign=assign, interlace=interlace, precision=prec,
+                         origin=origin, randoms=r, los_dir=None, observer=(0.0, 0.0, 0.0),
+                         scoc_ells=(0, 1, 2, 3), tripo_ells=(0, 2))
+    spec = dict(n=32, box=box, origin=tuple(origin), assign=assign, interlace=interlace, los="endpoint",
+                observer=(0.0, 0.0, 0.0), periodic=0)
+    orc = OB.odd_multipoles(spec, g, r, kb, (1, 3))
+    _check_odd(res, orc, (1, 3), tol)
+    even = OB.bispectrum(spec, g, r, kb, (0, 2), (0, 2), shot=True)
+    _check(dict(res, B={l: res["B"][l] for l in (0, 2)}, shot_B={l: res["shot_B"][l] for l in (0, 2)}), even, tol)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 1e-4)])
+def test_odd_multipoles_global_line_of_sight(api, prec, tol):
+    """B_1 alone and B_1, B_3 with B_0, survey geometry with a tilted global line of sight
+    (X_l = L_l(qhat . los) X_0), against the oracle."""
+    from synthetic import make_survey_catalogs
+
+    box = 600.0
+    los = (1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0)
+    g, r, origin = make_survey_catalogs(20000, 200000, box, 800.0, 32, seed=83, fkp_p0=1e4)
+    kf = 2 * np.pi / box
+    kb = (2 * kf, 1.5 * kf, 4)
+    spec = dict(n=32, box=box, origin=tuple(origin), assign=3, interlace=1, los="global", los_dir=los, periodic=0)
+    orc = OB.odd_multipoles(spec, g, r, kb, (1, 3))
+    res = api.bispectrum(g, n=32, box=box, kbins=kb, precision=prec, origin=origin, randoms=r, los_dir=los,
+                         scoc_ells=(0, 1, 3), tripo_ells=(), shot=True)
+    _check_odd(res, orc, (1, 3), tol)
+    one = api.bispectrum(g, n=32, box=box, kbins=kb, precision=prec, origin=origin, randoms=r, los_dir=los,
+                         scoc_ells=(0, 1), tripo_ells=(), shot=False)
+    scale = np.abs(res["B"][0] + res["shot_B"][0])
+    assert np.max(np.abs(one["B"][1] - orc["B"][1]) / np.maximum(np.abs(orc["B"][1]), scale)) < tol
+
+
 def test_mixed_19_bins_805_triangles_128(api):
     """The 19-bin / 805-triangle layout of the 256^3 workload on a 128^3 mesh of the same box
     (k_max = 0.2 = k_N/2), float32 transforms: <= 1e-4."""
@@ -182,8 +239,11 @@ def test_bispectrum_rejects(api):
     with pytest.raises(B.NpcError) as ei:        # k_max beyond k_N/2
         api.bispectrum(cat, n=32, box=300.0, kbins=(0.02, 0.05, 5))
     assert ei.value.status == 4
-    with pytest.raises(B.NpcError) as ei:        # odd multipole
-        api.bispectrum(cat, n=32, box=300.0, kbins=(0.02, 0.02, 4), scoc_ells=(1,))
+    with pytest.raises(B.NpcError) as ei:        # multipole beyond l = 3
+        api.bispectrum(cat, n=32, box=300.0, kbins=(0.02, 0.02, 4), scoc_ells=(4,))
+    assert ei.value.status == 1
+    with pytest.raises(B.NpcError) as ei:        # compressed odd multipole
+        api.bispectrum(cat, n=32, box=300.0, kbins=(0.02, 0.02, 4), tripo_ells=(1,))
     assert ei.value.status == 1
     from synthetic import make_survey_catalogs
 

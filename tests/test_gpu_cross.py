@@ -1,4 +1,4 @@
-"""GPU parity: npc_cross_power_multipoles (through the C ABI) against the FP64 oracle."""
+"""GPU parity: npc_cross_power_multipoles and npc_cross_bispectrum (through the C ABI) against the FP64 oracle."""
 import numpy as np
 import pytest
 
@@ -109,3 +109,73 @@ def test_odd_cross_of_a_shifted_copy(api):
     for l in (0, 1, 2, 3, 4):
         assert np.max(p_error(res["P"][l], orc["P"][l], scale)) < 1e-12, l
     assert np.max(np.abs(orc["P"][1]) / scale) > 1e-3
+
+
+def _check_cross_b(res, orc, scoc, tripo, tol):
+    np.testing.assert_array_equal(res["tri"], orc["tri"])
+    scale = np.abs(orc["B"][0])
+    for l in scoc:
+        e = np.abs(res["B"][l] - orc["B"][l]) / np.maximum(np.abs(orc["B"][l]), scale)
+        assert np.max(e) < tol, ("B", l, np.max(e))
+        assert np.all(res["shot_B"][l] == 0)
+    sp = np.abs(orc["BB"][0]) if 0 in orc["BB"] else None
+    for l in tripo:
+        ref = np.abs(orc["BB"][l]) if sp is None else np.maximum(np.abs(orc["BB"][l]), sp)
+        e = np.abs(res["BB"][l] - orc["BB"][l]) / ref
+        assert np.max(e) < tol, ("BB", l, np.max(e))
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 1e-4)])
+def test_cross_bispectrum_three_periodic_tracers(api, prec, tol):
+    """Three different periodic catalogues, tracer t on leg t, global line of sight along z:
+    B_0^{123}, B_2^{123} (l on leg 1) and B_000^{123}, B_202^{123} (l on leg 3) against the oracle."""
+    from oracle import bispec as OB
+
+    cats = [make_periodic_catalog(n, 300.0, 32, seed=s) for n, s in ((20000, 51), (15000, 52), (25000, 53))]
+    kb = (0.02, 0.02, 5)
+    spec = dict(n=32, box=300.0, origin=(0.0, 0.0, 0.0), assign=3, interlace=1, los="global",
+                los_dir=(0.0, 0.0, 1.0), periodic=1)
+    orc = OB.cross_bispectrum(spec, [(c, None) for c in cats], kb, (0, 2), (0, 2))
+    res = api.cross_bispectrum([(c, None) for c in cats], n=32, box=300.0, kbins=kb, scoc_ells=(0, 2),
+                               tripo_ells=(0, 2), precision=prec)
+    _check_cross_b(res, orc, (0, 2), (0, 2), tol)
+    np.testing.assert_allclose(res["NT"], orc["NT"], rtol=1e-9, atol=1e-6)
+
+
+def test_cross_bispectrum_survey_and_equal_tracers(api):
+    """Survey geometry with three (data, randoms) pairs and a tilted global line of sight against the
+    oracle; and three copies of one catalogue give the auto bispectrum's raw B_0 and B_000."""
+    from oracle import bispec as OB
+
+    box = 600.0
+    los = (1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0)
+    tr = []
+    for s in (61, 62, 63):
+        g, r, origin = make_survey_catalogs(15000, 150000, box, 900.0, 32, seed=s, fkp_p0=1e4)
+        tr.append((g, r))
+    kf = 2 * np.pi / box
+    kb = (2 * kf, 1.5 * kf, 4)
+    spec = dict(n=32, box=box, origin=tuple(origin), assign=3, interlace=1, los="global", los_dir=los, periodic=0)
+    orc = OB.cross_bispectrum(spec, tr, kb, (0, 2), (0,))
+    res = api.cross_bispectrum(tr, n=32, box=box, kbins=kb, scoc_ells=(0, 2), tripo_ells=(0,), los_dir=los,
+                               origin=origin, precision="fp64")
+    _check_cross_b(res, orc, (0, 2), (0,), 1e-10)
+    g, r = tr[0]
+    same = api.cross_bispectrum([(g, r)] * 3, n=32, box=box, kbins=kb, scoc_ells=(0,), tripo_ells=(0,),
+                                los_dir=los, origin=origin, precision="fp64")
+    auto = api.bispectrum(g, n=32, box=box, kbins=kb, scoc_ells=(0,), tripo_ells=(0,), shot=False, origin=origin,
+                          randoms=r, los_dir=los, precision="fp64")
+    np.testing.assert_allclose(same["B"][0], auto["B"][0], rtol=1e-11, atol=0)
+    np.testing.assert_allclose(same["BB"][0], auto["BB"][0], rtol=1e-11, atol=0)
+
+
+def test_cross_bispectrum_rejects(api):
+    from paper_2605_04864_gb300 import binding as B
+
+    cats = [make_periodic_catalog(2000, 300.0, 16, seed=s) for s in (1, 2, 3)]
+    with pytest.raises(B.NpcError) as ei:       # line of sight to each grid point
+        api.cross_bispectrum([(c, None) for c in cats], n=32, box=300.0, kbins=(0.02, 0.02, 4), los_dir=None)
+    assert ei.value.status == 4
+    with pytest.raises(B.NpcError) as ei:       # odd multipole
+        api.cross_bispectrum([(c, None) for c in cats], n=32, box=300.0, kbins=(0.02, 0.02, 4), scoc_ells=(1,))
+    assert ei.value.status == 1
