@@ -131,6 +131,9 @@ npc_status npc_set_wait_limit(npc_ctx* ctx, long long cycles);
 /* Implementation switches for comparison runs: "tcgen05_triple" (default 1) selects the tcgen05
  * tensor-core path of the bispectrum triple products; 0 selects the warp-level mma.sync path. */
 npc_status npc_set_option(npc_ctx* ctx, const char* name, int64_t value);
+/* Current value of an option: "tcgen05_triple" as above (npc_batch_tune sets it to the faster path
+ * for the batch it times), "batch_branches" (0: not tuned). */
+npc_status npc_get_option(npc_ctx* ctx, const char* name, int64_t* value);
 
 /* Stage timing.  With profiling on, every call records CUDA events on the context's stream at its
  * stage boundaries (a few events per call, no synchronisation).  npc_stage_times() waits for the
@@ -271,8 +274,8 @@ npc_status npc_bispectrum_triangles(const npc_kbins* bins, int32_t* tri, int64_t
                                     int64_t* ntri);
 
 /* Sugiyama TripoSH bispectrum multipoles B_{l1 l2 L}(k1, k2) (Sec. 4.2, Eq. sugi_estimator with the
- * fields of Eq. F_and_G), global line of sight
- * (mesh->periodic = 1, or survey geometry with randoms and mesh->los = 1):
+ * fields of Eq. F_and_G).  Global line of sight (mesh->periodic = 1, or survey geometry with randoms
+ * and mesh->los = 1):
  *   B(i, j) = H N / (I33 N_i N_j) sum_{m1 m2 M} (l1 l2 L; m1 m2 M) <F_l1^m1(x; k_i) F_l2^m2(x; k_j) G_L^M(x)>_x
  * with F_l^m(x; k) = sum_{q in bin k} e^{iqx} y_l^{m*}(qhat) X(q), H = (l1 l2 L; 0 0 0),
  * N = (2l1+1)(2l2+1)(2L+1), y = sqrt(4 pi/(2l+1)) Y, X the compensated interlaced spectrum and
@@ -280,10 +283,18 @@ npc_status npc_bispectrum_triangles(const npc_kbins* bins, int32_t* tri, int64_t
  * remains, G_L^0 is the full-range field of X for every L, and the m, -m sub-configurations pair up
  * (Eq. sym_sugi): the library evaluates sum_{m=0..min(l1,l2)} of the real parts of F_l1^m F_l2^{m*} G
  * as shell-field triple products on the tensor cores, every (k_i, k_j) bin pair at once.
- * multipoles: nmult (1..16) triples (l1, l2, L), 0 <= l1, l2 <= 4, |l1 - l2| <= L <= l1 + l2, L and
- *   l1 + l2 even (the plane-parallel symmetry about the line of sight); else NPC_ERR_INVALID_ARG.  Bins and mesh limits as npc_bispectrum (at most
- *   24 bins, largest bin edge <= k_N/2).  Survey geometry with the line of sight to each grid point
- *   (mesh->los = 0): NPC_ERR_UNSUPPORTED.
+ * Survey geometry with the line of sight to each grid point (mesh->los = 0, randoms required): the
+ *   full sum over (m1, m2, M = -m1-m2) in the catalogue frame, G_L^M(x) = sum_q e^{iqx} dn_L^M(q)/W(q)
+ *   with dn_L^M the interlaced transform of F(x) y_L^{M*}(xhat) (xhat from mesh->observer to the grid
+ *   point), from the transforms of F Re Y_LM and F Im Y_LM for M >= 0 (G_L^{-M} = (-1)^M G_L^{M*});
+ *   every sub-configuration becomes real triple products of the parts of F_l1^|m1|, F_l2^|m2| and
+ *   G_L^|M|.  For l1 + l2 odd (odd L) the sum is imaginary and its imaginary part is reported (the
+ *   rule of Sec. 2.1 for odd multipoles).  Raw estimates only there (shot = 0, else
+ *   NPC_ERR_UNSUPPORTED).
+ * multipoles: nmult (1..16) triples (l1, l2, L), 0 <= l1, l2 <= 4, |l1 - l2| <= L <= l1 + l2; with a
+ *   global line of sight L and l1 + l2 even (the plane-parallel symmetry about it), with the line of
+ *   sight to each grid point l1 + l2 + L even and L <= 4; else NPC_ERR_INVALID_ARG.  Bins and mesh
+ *   limits as npc_bispectrum (at most 24 bins, largest bin edge <= k_N/2).
  * shot: 0 raw estimates; 1 subtracts the analytic shot noise of Sec. 5.4 and reports it:
  *   delta_{l1 0} delta_{l2 0} delta_{L 0} S/I33 (three legs from one object), delta_{l1 L} delta_{l2 0}
  *   (2L+1) H_L(k1)/I33 and delta_{l2 L} delta_{l1 0} (2L+1) H_L(k2)/I33 (two), and for legs 1, 2 from
@@ -338,9 +349,12 @@ int64_t npc_batch_layout(int32_t nitems, const npc_batch_item* items, uint32_t e
  * block.  Asynchronous on the context's stream.  flags: 0 or NPC_BATCH_GRAPH. */
 npc_status npc_batch_run(npc_ctx* ctx, int32_t nitems, const npc_batch_item* items, uint32_t ell_mask,
                          npc_precision prec, double* out_device, int32_t flags);
-/* Autotuner: times, on this batch, the columns per CTA of the y transform pass for every mesh size
- * and then the number of concurrent branches (graph replays), keeps the fastest choices in the
- * context and reports the branch count.  Runs the batch several times (out_device is overwritten). */
+/* Autotuner: times, on this batch, the columns per CTA of the y transform pass for every mesh size,
+ * then the number of concurrent branches (graph replays), then the triple-product path of the
+ * bispectra (tcgen05 tiles of 128 rows or warp-level tiles of 16 rows, option "tcgen05_triple"),
+ * keeps the fastest choices in the context and reports the branch count.  Runs the batch several
+ * times (out_device is overwritten).  After a batch, npc_device_status also checks the bounded
+ * waits of the batch's branch contexts. */
 npc_status npc_batch_tune(npc_ctx* ctx, int32_t nitems, const npc_batch_item* items, uint32_t ell_mask,
                           npc_precision prec, double* out_device, int32_t* branches);
 /* Autotuner of the transform passes for mesh size n: times the valid column-tile widths of the

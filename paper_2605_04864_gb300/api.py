@@ -209,6 +209,13 @@ def set_option(name, value, device=0):
     B.check(B.npc_set_option(context(device), name.encode(), int(value)), context(device))
 
 
+def get_option(name, device=0):
+    """Current value of a context option (npc_get_option)."""
+    v = C.c_int64()
+    B.check(B.npc_get_option(context(device), name.encode(), C.byref(v)), context(device))
+    return v.value
+
+
 def set_wait_limit(cycles, device=0):
     """Bound of the device-side waits in clock cycles (<= 0: the default); see npc_set_wait_limit."""
     B.check(B.npc_set_wait_limit(context(device), int(cycles)))

@@ -63,6 +63,7 @@ _sig = {
     "npc_device_status": (C.c_int, [C.c_void_p]),
     "npc_set_wait_limit": (C.c_int, [C.c_void_p, C.c_longlong]),
     "npc_set_option": (C.c_int, [C.c_void_p, C.c_char_p, C.c_int64]),
+    "npc_get_option": (C.c_int, [C.c_void_p, C.c_char_p, _P(C.c_int64)]),
     "npc_catalog_scalars": (C.c_int, [C.c_void_p, _P(npc_catalog), _P(npc_catalog), C.c_double,
                                       C.c_void_p, C.c_int32]),
     "npc_power_multipoles": (C.c_int, [C.c_void_p, _P(npc_mesh_spec), _P(npc_catalog), _P(npc_catalog),

@@ -493,6 +493,11 @@ npc_status npc_create(npc_ctx** out, int device, void* cuda_stream) {
 npc_status npc_device_status(npc_ctx* ctx) {
   if (!ctx) return NPC_ERR_INVALID_ARG;
   cudaSetDevice(ctx->device);
+  // the batch executor's branch contexts first (their kernels run on their own streams)
+  for (npc_ctx* sub : ctx->subs) {
+    const npc_status st = check_device_status(sub);
+    if (st != NPC_OK) return set_err(ctx, st, "%s", sub->last_error.c_str());
+  }
   return check_device_status(ctx);
 }
 
@@ -506,6 +511,19 @@ npc_status npc_set_option(npc_ctx* ctx, const char* name, int64_t value) {
   if (!ctx || !name) return NPC_ERR_INVALID_ARG;
   if (std::strcmp(name, "tcgen05_triple") == 0) {
     ctx->use_tcgen05 = value != 0;
+    return NPC_OK;
+  }
+  return set_err(ctx, NPC_ERR_INVALID_ARG, "unknown option '%s'", name);
+}
+
+npc_status npc_get_option(npc_ctx* ctx, const char* name, int64_t* value) {
+  if (!ctx || !name || !value) return NPC_ERR_INVALID_ARG;
+  if (std::strcmp(name, "tcgen05_triple") == 0) {
+    *value = ctx->use_tcgen05 ? 1 : 0;
+    return NPC_OK;
+  }
+  if (std::strcmp(name, "batch_branches") == 0) {
+    *value = ctx->batch_branches;
     return NPC_OK;
   }
   return set_err(ctx, NPC_ERR_INVALID_ARG, "unknown option '%s'", name);
@@ -726,12 +744,17 @@ npc_status npc_bispectrum_sugiyama(npc_ctx* ctx, const npc_mesh_spec* mesh, cons
   if (bins->nbins > 24) return set_err(ctx, NPC_ERR_UNSUPPORTED, "bispectrum supports at most 24 bins");
   SugiReq req{};
   req.nmult = nmult;
+  // survey geometry with the line of sight to each grid point: G_L^M for every M (L <= 4)
+  const bool endpoint = !mesh->periodic && mesh->los != 1;
   for (int e = 0; e < nmult; ++e) {
     const int l1 = multipoles[3 * e], l2 = multipoles[3 * e + 1], L = multipoles[3 * e + 2];
-    // L even: the plane-parallel symmetry about the line of sight (Sec. 4.2), so l1 + l2 is even too
-    if (l1 < 0 || l1 > 4 || l2 < 0 || l2 > 4 || L < std::abs(l1 - l2) || L > l1 + l2 || (L & 1) || ((l1 + l2) & 1))
+    // global line of sight: L even (the plane-parallel symmetry about it, Sec. 4.2), so l1 + l2 is
+    // even too; endpoint line of sight: l1 + l2 + L even (H_l1l2L != 0), L <= 4
+    const bool bad_parity = endpoint ? (((l1 + l2 + L) & 1) || L > 4) : ((L & 1) || ((l1 + l2) & 1));
+    if (l1 < 0 || l1 > 4 || l2 < 0 || l2 > 4 || L < std::abs(l1 - l2) || L > l1 + l2 || bad_parity)
       return set_err(ctx, NPC_ERR_INVALID_ARG, "multipole (%d, %d, %d): need l1, l2 <= 4, |l1-l2| <= L <= l1+l2, "
-                     "L and l1+l2 even", l1, l2, L);
+                     "L and l1+l2 even (global line of sight) or l1+l2+L even and L <= 4 (line of sight to each "
+                     "grid point)", l1, l2, L);
     req.l1[e] = l1;
     req.l2[e] = l2;
     req.L[e] = L;
@@ -741,8 +764,9 @@ npc_status npc_bispectrum_sugiyama(npc_ctx* ctx, const npc_mesh_spec* mesh, cons
   if (mesh->periodic) {
     if (randoms) return set_err(ctx, NPC_ERR_INVALID_ARG, "periodic box takes no randoms");
   } else {
-    if (mesh->los != 1)
-      return set_err(ctx, NPC_ERR_UNSUPPORTED, "TripoSH multipoles need a global line of sight (los = 1)");
+    if (endpoint && shot != 0)
+      return set_err(ctx, NPC_ERR_UNSUPPORTED,
+                     "TripoSH with the line of sight to each grid point: raw estimates only (shot = 0)");
     if (!randoms) return set_err(ctx, NPC_ERR_INVALID_ARG, "survey geometry needs randoms");
     NPC_TRY(check_catalog(ctx, randoms, "randoms", true));
     if (randoms->n == 0) return set_err(ctx, NPC_ERR_NUMERIC, "empty random catalogue");

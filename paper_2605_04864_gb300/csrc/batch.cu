@@ -142,8 +142,10 @@ npc_status enqueue(npc_ctx* ctx, cudaStream_t hub, const std::vector<Item>& item
   return NPC_OK;
 }
 
-std::string batch_key(int nitems, const npc_batch_item* items, uint32_t ell_mask, int prec, int nb, const double* out) {
+std::string batch_key(int nitems, const npc_batch_item* items, uint32_t ell_mask, int prec, int nb, const double* out,
+                      bool tc) {
   std::string k;
+  k.push_back(tc ? 'T' : 'M');   // triple-product path baked into the captured kernels
   k.append((const char*)items, sizeof(npc_batch_item) * (size_t)nitems);
   k.append((const char*)&ell_mask, sizeof(ell_mask));
   k.append((const char*)&prec, sizeof(prec));
@@ -204,7 +206,11 @@ npc_status batch_exec(npc_ctx* ctx, int nitems, const npc_batch_item* items, uin
   int64_t total = 0;
   NPC_TRY(plan_items(ctx, nitems, items, ell_mask, prec, nb, &plan, &total));
   NPC_TRY(ensure_branches(ctx, nb));
-  for (int b = 0; b < nb; ++b) ctx->subs[b]->ytx = ctx->ytx;
+  for (int b = 0; b < nb; ++b) {
+    ctx->subs[b]->ytx = ctx->ytx;
+    ctx->subs[b]->use_tcgen05 = ctx->use_tcgen05;
+    ctx->subs[b]->wait_limit = ctx->wait_limit;
+  }
   cudaStream_t hub = hub_stream(ctx);
   if (!hub) return set_err(ctx, NPC_ERR_CUDA, "cannot create the batch stream");
   Events ev;
@@ -220,7 +226,7 @@ npc_status batch_exec(npc_ctx* ctx, int nitems, const npc_batch_item* items, uin
   int launches0 = 0;
   for (int b = 0; b < nb; ++b) launches0 += ctx->subs[b]->launches;
 
-  const std::string key = batch_key(nitems, items, ell_mask, prec, nb, out);
+  const std::string key = batch_key(nitems, items, ell_mask, prec, nb, out, ctx->use_tcgen05);
   auto git = ctx->graphs.find(key);
   bool replay = false;
   if (use_graph && git != ctx->graphs.end()) {
@@ -389,9 +395,32 @@ npc_status npc_batch_tune(npc_ctx* ctx, int32_t nitems, const npc_batch_item* it
       best_b = nb;
     }
   }
+  // 3. triple-product path of the bispectra (tcgen05 tiles of 128 rows, or warp-level mma.sync tiles
+  //    of 16 rows), timed on graph replays with the chosen branch count
+  float best_t = 1e30f;
+  bool best_tc = ctx->use_tcgen05;
+  for (int opt = 1; opt >= 0 && st == NPC_OK; --opt) {
+    ctx->use_tcgen05 = opt != 0;
+    st = batch_exec(ctx, nitems, items, ell_mask, prec, out_device, true, best_b);
+    if (st == NPC_OK) st = batch_exec(ctx, nitems, items, ell_mask, prec, out_device, true, best_b);
+    if (st != NPC_OK) break;
+    cudaEventRecord(e0, ctx->stream);
+    for (int rep = 0; rep < 2 && st == NPC_OK; ++rep)
+      st = batch_exec(ctx, nitems, items, ell_mask, prec, out_device, true, best_b);
+    cudaEventRecord(e1, ctx->stream);
+    if (st != NPC_OK) break;
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_t) {
+      best_t = ms;
+      best_tc = opt != 0;
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != NPC_OK) return st;
+  ctx->use_tcgen05 = best_tc;
   ctx->batch_branches = best_b;
   if (branches) *branches = best_b;
   return end_call(ctx);

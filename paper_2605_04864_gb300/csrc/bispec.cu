@@ -115,9 +115,11 @@ k_fft_x_combine(const cplx<T>* __restrict__ half, int nout, int nphase, int KZ, 
 //     for l = 1, 2, 3 (each when its output is given), from the Y_lm-weighted fields of the
 //     forward plan, interlaced and compensated.  A_lm, B_lm are the transforms of Re and Im of
 //     F Y_lm(xhat); X_l(-q) = (-1)^l X_l(q)^*.  Components c (l, m, part) list their phase-a field
-//     ia[c] and phase-b field ib[c] (unused without interlacing).
+//     ia[c] and phase-b field ib[c] (unused without interlacing).  With `comps` given the kernel
+//     stores every component's interlaced, compensated spectrum there instead (component c at
+//     comps + c KZ N^2): the y_L^M-weighted parts of the TripoSH field G_L^M.
 // ------------------------------------------------------------------------------------------
-constexpr int YAM_MAXC = 16;   // F and the parts of Y_lm, l <= 3: 1 + 3 + 5 + 7
+constexpr int YAM_MAXC = 25;   // F and the parts of Y_lm, l <= 4: 1 + 3 + 5 + 7 + 9
 struct YamComps {
   int nf, nc;
   int8_t l[YAM_MAXC], m[YAM_MAXC], part[YAM_MAXC];
@@ -128,7 +130,8 @@ template <typename T, int N>
 __global__ void __launch_bounds__(BT)
 k_fft_x_assemble_yam(const cplx<T>* __restrict__ half, int nphase, int KZ, int KY, int assign, const YNorm nrm,
                      const YamComps cp, const cplx<T>* __restrict__ tw_g, cplx<T>* __restrict__ X0o,
-                     cplx<T>* __restrict__ X1o, cplx<T>* __restrict__ X2o, cplx<T>* __restrict__ X3o) {
+                     cplx<T>* __restrict__ X1o, cplx<T>* __restrict__ X2o, cplx<T>* __restrict__ X3o,
+                     cplx<T>* __restrict__ comps) {
   using C = cplx<T>;
   constexpr int TPF = N / 8;
   constexpr int G = BT / TPF > 0 ? BT / TPF : 1;
@@ -186,10 +189,15 @@ k_fft_x_assemble_yam(const cplx<T>* __restrict__ half, int nphase, int KZ, int K
       const T inv = r2 > T(0) ? rsqrt(r2) : T(0);
       const T ux = fi * inv, uy = fj * inv, uz = r2 > T(0) ? fk * inv : T(1);
       C acc[4] = {cmk(T(0), T(0)), cmk(T(0), T(0)), cmk(T(0), T(0)), cmk(T(0), T(0))};
+      const size_t o = ((size_t)kz * N + ky) * N + kx;
       for (int c = 0; c < cp.nc; ++c) {
         C x = rows[(size_t)cp.ia[c] * NP + jp];
         if (nphase == 2) x = cscale(cadd(x, cmul(ph, rows[(size_t)cp.ib[c] * NP + jp])), T(0.5));
         x = cscale(x, iw);
+        if (comps) {
+          comps[(size_t)c * fstride + o] = x;
+          continue;
+        }
         const int l = cp.l[c];
         if (l == 0) {
           acc[0] = x;
@@ -200,7 +208,7 @@ k_fft_x_assemble_yam(const cplx<T>* __restrict__ half, int nphase, int KZ, int K
         const T wgt = cp.m[c] == 0 ? yr : T(2) * (cp.part[c] == PART_IM ? yi : yr);
         acc[l] = cadd(acc[l], cscale(x, wgt));
       }
-      const size_t o = ((size_t)kz * N + ky) * N + kx;
+      if (comps) continue;
       X0o[o] = acc[0];
 #pragma unroll
       for (int l = 1; l <= 3; ++l)
@@ -381,14 +389,15 @@ k_bin_cross(const cplx<T>* __restrict__ X0, const cplx<T>* __restrict__ XN, int 
 struct ShellField {
   int8_t src;     // 0: X_0, 1: ones (indicator), 2: X_0 N_0^* (FFT-method shot noise), 3: X_2 (survey),
                   // 4: X_1, 5: X_3 (survey, odd: anti-Hermitian, taken times -i),
-                  // 6: X of tracer 2, 7: X of tracer 3 (multi-tracer bispectra)
+                  // 6: X of tracer 2, 7: X of tracer 3 (multi-tracer bispectra),
+                  // 8: a stored component spectrum `comp` (TripoSH G_L^M parts, bin -1)
   int8_t mult;    // 0: 1, 1: L_yl(mu) (times -i for odd yl), 2: the TripoSH weight of (yl, ym, ypart)
   int16_t bin;    // >= 0: modes of this bin; -1: all modes with n2 <= n2cap
   int K;          // kz <= K, |ky| <= K
   int8_t yl, ym;  // mult 2: the field is a part of sum_q e^{iqx} y_l^{m*}(qhat) S(q), m >= 0, S the source
                   // (X: the TripoSH shell F_l^m; ones: its indicator for the FFT-method shot noise)
   int8_t ypart;   // mult 2: 0 its real part, 1 its imaginary part
-  int8_t pad;
+  int8_t comp;    // src 8: index of the stored component spectrum (TripoSH G_L^M parts)
   int64_t off1;   // offset of this field in the x-pass output (complex elements)
   int64_t off2;   // offset in the y-pass output
 };
@@ -445,7 +454,7 @@ template <typename T, int NS, bool YW>
 __global__ void __launch_bounds__(BT)
 k_shell_x(const cplx<T>* __restrict__ X0, const cplx<T>* __restrict__ XN, const cplx<T>* __restrict__ X2,
           const cplx<T>* __restrict__ X1, const cplx<T>* __restrict__ X3, const cplx<T>* __restrict__ XB,
-          const cplx<T>* __restrict__ XC, int KZX, int nfine,
+          const cplx<T>* __restrict__ XC, const cplx<T>* __restrict__ XCOMP, int KZX, int nfine,
           const ShellField* __restrict__ fields, int nfields, int Kmax, const int16_t* __restrict__ tab, int n2cap,
           const LosFrame fr, const cplx<T>* __restrict__ tw_g, cplx<T>* __restrict__ T1) {
   using C = cplx<T>;
@@ -520,6 +529,13 @@ k_shell_x(const cplx<T>* __restrict__ X0, const cplx<T>* __restrict__ XN, const 
               case 5: a = x3row[kx]; break;
               case 6: a = xbrow[kx]; break;
               case 7: a = xcrow[kx]; break;
+              case 8: {
+                const int ii = kx < NS / 2 ? kx : kx - NS;
+                const int fx = ii < 0 ? ii + nfine : ii;
+                a = kz < KZX ? XCOMP[(size_t)sf.comp * KZX * nfine * nfine + ((size_t)kz * nfine + ky) * nfine + fx]
+                             : cmk(T(0), T(0));
+                break;
+              }
               default: a = cmk(T(1), T(0));
             }
             if (sf.mult == 1) a = cscale(a, legendre_dev<T>(sf.yl, murow[kx]));
@@ -1406,6 +1422,7 @@ struct ShellLaunch {
   const void* X3;
   const void* XB;   // tracers 2 and 3 of a multi-tracer bispectrum (src = 6, 7), or null
   const void* XC;
+  const void* XCOMP;  // component spectra for src = 8 fields (KZX n^2 each), or null
   int KZX, nfine;
   const ShellField* fields;
   int nfield, Kmax;
@@ -1435,7 +1452,7 @@ npc_status shell_passes(npc_ctx* ctx, const ShellLaunch& sl, cplx<T>* T1, cplx<T
     const int nrows = (sl.Kmax + 1) * (2 * sl.Kmax + 1);
     kern<<<std::min(nrows, ctx->num_sms * 4), BT, smem, ctx->stream>>>(
         (const C*)sl.X, (const C*)sl.XN, (const C*)sl.X2, (const C*)sl.X1, (const C*)sl.X3, (const C*)sl.XB,
-        (const C*)sl.XC, sl.KZX, sl.nfine,
+        (const C*)sl.XC, (const C*)sl.XCOMP, sl.KZX, sl.nfine,
         sl.fields, sl.nfield, sl.Kmax, sl.tab,
         sl.n2cap, sl.frame, tw, T1);
     NPC_LAUNCH(ctx);
@@ -1526,6 +1543,13 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
     frame.e2[2] = l3[0] * frame.e1[1] - l3[1] * frame.e1[0];
   }
   const bool sugi = sug != nullptr;
+  // TripoSH with the line of sight to each grid point: G_L^M from y_L^M-weighted transforms and the
+  // full m1 + m2 + M = 0 sum in the catalogue frame (raw estimates)
+  const bool sugi_ep = sugi && m.los != 1 && !m.periodic;
+  int sugi_lmask = 0;   // L > 0 of the requested TripoSH multipoles
+  if (sugi_ep)
+    for (int e = 0; e < sug->nmult; ++e)
+      if (sug->L[e] > 0) sugi_lmask |= 1 << sug->L[e];
   // survey geometry with the line of sight to each grid point and an l = 2 request: Yamamoto X_2
   // from the Y_2m-weighted transforms instead of L_2(khat . los) X_0
   const bool yam = !m.periodic && m.los != 1 && (((scoc_mask | tripo_mask) & 4) != 0);
@@ -1549,7 +1573,7 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
   plan.kz_keep = KZ;
   plan.fl.nf = 0;
   // survey layout: component c = (l, m, part) with its phase-a and phase-b fields adjacent
-  auto build_survey = [&](PowerPlan& pl, YamComps& yc, bool l1, bool l2, bool l3) {
+  auto build_survey = [&](PowerPlan& pl, YamComps& yc, int lmask) {
     pl.fl.nf = 0;
     yc = YamComps{};
     auto comp = [&](int l, int mm, int part) {
@@ -1563,8 +1587,8 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
       }
     };
     comp(0, 0, PART_ONE);
-    for (int l = 1; l <= 3; ++l) {
-      if (!(l == 1 ? l1 : (l == 2 ? l2 : l3))) continue;
+    for (int l = 1; l <= 4; ++l) {
+      if (!(lmask & (1 << l))) continue;
       comp(l, 0, PART_RE);
       for (int mm = 1; mm <= l; ++mm) {
         comp(l, mm, PART_RE);
@@ -1583,14 +1607,15 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
   };
   YamComps ycF{}, ycN{};
   PowerPlan planN = plan;
-  if (yam || yamo) build_survey(plan, ycF, yamo && want1, yam, yamo && want3);
+  if (sugi_ep) build_survey(plan, ycF, sugi_lmask);
+  else if (yam || yamo) build_survey(plan, ycF, ((yamo && want1) ? 2 : 0) | (yam ? 4 : 0) | ((yamo && want3) ? 8 : 0));
   else build_plain(plan);
-  if (yam) build_survey(planN, ycN, false, true, false);
+  if (yam) build_survey(planN, ycN, 4);
   else build_plain(planN);
-  plan.global_los = (yam || yamo) ? 0 : 1;
+  plan.global_los = (yam || yamo || sugi_ep) ? 0 : 1;
   planN.global_los = yam ? 0 : 1;
   const Geom gyam = make_geom(m);   // observer-relative grid points for the Y weighting
-  const Geom& gfwd = (yam || yamo) ? gyam : geo;
+  const Geom& gfwd = (yam || yamo || sugi_ep) ? gyam : geo;
   const Geom& gfwdN = yam ? gyam : geo;
   const int prec = sizeof(T) == 8 ? NPC_PREC_FP64 : NPC_PREC_MIXED;
   const size_t halfbytes = sizeof(C) * (size_t)plan.fl.nf * KZ * N * N;
@@ -1615,17 +1640,19 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
   C* X;
   const int nout = shot ? 2 : 1;
   const size_t xfs = (size_t)KZ * N * N;
-  NPC_TRY(ws_get(ctx, "bis.X", sizeof(C) * xfs * (crq ? 3 : (yamo ? 6 : (yam ? 4 : nout))), (void**)&X));
+  NPC_TRY(ws_get(ctx, "bis.X",
+                 sizeof(C) * xfs * (sugi_ep ? ycF.nc : (crq ? 3 : (yamo ? 6 : (yam ? 4 : nout)))), (void**)&X));
   {
     const int nrows = KZ * (2 * K2 + 1);
     const int grid = std::min(nrows, ctx->num_sms * 4);
-    auto assemble = [&](const C* src, const YamComps& yc, C* x0, C* x1, C* x2, C* x3) -> npc_status {
+    auto assemble = [&](const C* src, const YamComps& yc, C* x0, C* x1, C* x2, C* x3, C* comps = nullptr) -> npc_status {
       const size_t smem = sizeof(C) * (2 * N + (size_t)(yc.nf + RowGroups<N, BT>::NBUF) * row_pad_len<N>()) +
                           sizeof(T) * (N / 2 + 2);
       if (smem > 227 * 1024) return set_err(ctx, NPC_ERR_UNSUPPORTED, "survey multipoles: mesh too large at this precision");
       auto kern = k_fft_x_assemble_yam<T, N>;
       NPC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      kern<<<grid, BT, smem, ctx->stream>>>(src, nphase, KZ, K2, m.assign, ylm_norm_table(), yc, tw, x0, x1, x2, x3);
+      kern<<<grid, BT, smem, ctx->stream>>>(src, nphase, KZ, K2, m.assign, ylm_norm_table(), yc, tw, x0, x1, x2, x3,
+                                            comps);
       NPC_LAUNCH(ctx);
       return NPC_OK;
     };
@@ -1638,7 +1665,9 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
       NPC_LAUNCH(ctx);
       return NPC_OK;
     };
-    if (yam || yamo)
+    if (sugi_ep)   // component c at X + c xfs; component 0 (the plain field) is X_0
+      NPC_TRY(assemble(halfF, ycF, X, nullptr, nullptr, nullptr, X));
+    else if (yam || yamo)
       NPC_TRY(assemble(halfF, ycF, X, (yamo && want1) ? X + 4 * xfs : nullptr, yam ? X + 2 * xfs : nullptr,
                        (yamo && want3) ? X + 5 * xfs : nullptr));
     else
@@ -1827,7 +1856,96 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
   int sfield[5][5][2], ifield[5][5][2], iXN = -1;   // ifield: the indicator versions (FFT-method shot noise)
   for (int l = 0; l < 5; ++l)
     for (int mm = 0; mm < 5; ++mm) sfield[l][mm][0] = sfield[l][mm][1] = ifield[l][mm][0] = ifield[l][mm][1] = -1;
-  if (sugi) {
+  // endpoint TripoSH: the real triple products of the full sub-configuration sum.  With
+  // F_l^{-m} = (-1)^{l+m} F_l^{m*}, G_L^{-M} = (-1)^M G_L^{M*} (both from the reality of F(x)) and
+  // G_L^M = c_L (G[Re] - i G[Im]), c_L = sqrt(4 pi/(2L+1)) (G[Re], G[Im] the fields of the transforms
+  // of F Re Y_LM and F Im Y_LM), every (m1, m2, M = -m1-m2) term is a product of the parts (real,
+  // imaginary) of the |m| fields, and Re(z1 z2 z3) = x1 x2 x3 - x1 y2 y3 - y1 x2 y3 - y1 y2 x3.
+  // For l1 + l2 odd (odd L) the sum is imaginary and its imaginary part is reported (the rule of
+  // Sec. 2.1 for odd multipoles): Im(z1 z2 z3) = x1 x2 y3 + x1 y2 x3 + y1 x2 x3 - y1 y2 y3.
+  struct EpKey {
+    int l1, a1, p1, l2, a2, p2, L, A3, p3;
+  };
+  std::vector<EpKey> ep_keys;
+  std::vector<std::vector<std::pair<int, double>>> ep_terms;
+  int gfield[5][5][2];
+  for (int l = 0; l < 5; ++l)
+    for (int mm = 0; mm < 5; ++mm) gfield[l][mm][0] = gfield[l][mm][1] = -1;
+  if (sugi_ep) {
+    ep_terms.resize(sug->nmult);
+    auto key_of = [&](const EpKey& k) {
+      for (size_t q = 0; q < ep_keys.size(); ++q) {
+        const EpKey& o = ep_keys[q];
+        if (o.l1 == k.l1 && o.a1 == k.a1 && o.p1 == k.p1 && o.l2 == k.l2 && o.a2 == k.a2 && o.p2 == k.p2 &&
+            o.L == k.L && o.A3 == k.A3 && o.p3 == k.p3)
+          return (int)q;
+      }
+      ep_keys.push_back(k);
+      return (int)ep_keys.size() - 1;
+    };
+    for (int e = 0; e < sug->nmult; ++e) {
+      const int l1 = sug->l1[e], l2 = sug->l2[e], L = sug->L[e];
+      const double hN = wigner3j_host(l1, l2, L, 0, 0, 0) * (2 * l1 + 1) * (2 * l2 + 1) * (2 * L + 1);
+      const double cL = L == 0 ? 1.0 : std::sqrt(4.0 * M_PI / (2 * L + 1));
+      for (int m1 = -l1; m1 <= l1; ++m1)
+        for (int m2 = -l2; m2 <= l2; ++m2) {
+          const int M = -m1 - m2;
+          if (std::abs(M) > L) continue;
+          const double w = wigner3j_host(l1, l2, L, m1, m2, M);
+          if (w == 0.0) continue;
+          const int a1 = std::abs(m1), a2 = std::abs(m2), A3 = std::abs(M);
+          const double s1 = (m1 < 0 && ((l1 + a1) & 1)) ? -1.0 : 1.0, t1 = m1 < 0 ? -1.0 : 1.0;
+          const double s2 = (m2 < 0 && ((l2 + a2) & 1)) ? -1.0 : 1.0, t2 = m2 < 0 ? -1.0 : 1.0;
+          const double s3 = (M < 0 && (A3 & 1)) ? -1.0 : 1.0, t3 = M < 0 ? -1.0 : 1.0;
+          const double base = hN * w * s1 * s2 * s3;
+          const bool imag = ((l1 + l2) & 1) != 0;
+          const int pr[4][3] = {{0, 0, 0}, {0, 1, 1}, {1, 0, 1}, {1, 1, 0}};
+          const int pi[4][3] = {{0, 0, 1}, {0, 1, 0}, {1, 0, 0}, {1, 1, 1}};
+          const double sgr[4] = {1.0, -t2 * t3, -t1 * t3, -t1 * t2};
+          const double sgi[4] = {t3, t2, t1, -t1 * t2 * t3};
+          const int (&pp)[4][3] = imag ? pi : pr;
+          const double* sg = imag ? sgi : sgr;
+          for (int q = 0; q < 4; ++q) {
+            const int p1 = pp[q][0], p2 = pp[q][1], p3 = pp[q][2];
+            if (a1 == 0 && p1 == ((l1 & 1) ? 0 : 1)) continue;   // vanishing part of an m = 0 shell
+            if (a2 == 0 && p2 == ((l2 & 1) ? 0 : 1)) continue;
+            if (A3 == 0 && p3 == 1) continue;                    // G_L^0 is real
+            const double gscale = p3 == 0 ? cL : -cL;
+            ep_terms[e].push_back({key_of(EpKey{l1, a1, p1, l2, a2, p2, L, A3, p3}), base * sg[q] * gscale});
+          }
+        }
+    }
+    // shells F_l^m parts (catalogue frame) and the G_L^M parts (full range, from the components)
+    sfield[0][0][0] = 0;
+    int fam = 20;
+    auto need_shell = [&](int l, int a, int p) {
+      if (sfield[l][a][p] >= 0) return;
+      sfield[l][a][p] = (int)fl.size();
+      for (int b = 0; b < nb; ++b) {
+        add(0, 2, b, Ks, fam);
+        fl.back().yl = (int8_t)l;
+        fl.back().ym = (int8_t)a;
+        fl.back().ypart = (int8_t)p;
+      }
+      ++fam;
+    };
+    for (const EpKey& k : ep_keys) {
+      need_shell(k.l1, k.a1, k.p1);
+      need_shell(k.l2, k.a2, k.p2);
+      if (k.L == 0) {
+        gfield[0][0][0] = iG;
+        continue;
+      }
+      if (gfield[k.L][k.A3][k.p3] >= 0) continue;
+      int comp = -1;
+      for (int c = 0; c < ycF.nc; ++c)
+        if (ycF.l[c] == k.L && ycF.m[c] == k.A3 && ycF.part[c] == (k.p3 ? PART_IM : PART_RE)) comp = c;
+      if (comp < 0) return set_err(ctx, NPC_ERR_INVALID_ARG, "TripoSH: missing y_L^M component");
+      gfield[k.L][k.A3][k.p3] = (int)fl.size();
+      add(8, 0, -1, KG, fam++);
+      fl.back().comp = (int8_t)comp;
+    }
+  } else if (sugi) {
     sfield[0][0][0] = 0;
     int fam = 20;
     for (int e = 0; e < sug->nmult; ++e) {
@@ -1933,10 +2051,23 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
   // the product (Eq. sym_sugi).
   struct SCombo {
     int l1, l2, m, part;
+    int fa = -1, fg = -1, fc = -1;   // endpoint TripoSH: the R indices of the three operands
   };
   std::vector<SCombo> combos;
   std::vector<double> scoef;
   size_t t_spij = 0, t_srow = 0, t_scoef = 0, t_sdesc = 0;
+  if (sugi_ep) {
+    for (const EpKey& k : ep_keys) {
+      SCombo cb{k.l1, k.l2, k.a1, k.p1};
+      cb.fa = sfield[k.l1][k.a1][k.p1];
+      cb.fg = gfield[k.L][k.A3][k.p3];
+      cb.fc = sfield[k.l2][k.a2][k.p2];
+      combos.push_back(cb);
+    }
+    scoef.assign((size_t)sug->nmult * combos.size(), 0.0);
+    for (int e = 0; e < sug->nmult; ++e)
+      for (const auto& tw : ep_terms[e]) scoef[(size_t)e * combos.size() + tw.first] += tw.second;
+  }
   if (sugi) {
     auto combo_of = [&](int l1, int l2, int mm, int part) {
       for (size_t c = 0; c < combos.size(); ++c)
@@ -1945,7 +2076,7 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
       return (int)combos.size() - 1;
     };
     std::vector<std::vector<std::pair<int, double>>> terms(sug->nmult);
-    for (int e = 0; e < sug->nmult; ++e) {
+    for (int e = 0; !sugi_ep && e < sug->nmult; ++e) {
       const int l1 = sug->l1[e], l2 = sug->l2[e], L = sug->L[e], mmax = std::min(l1, l2);
       const double hN = wigner3j_host(l1, l2, L, 0, 0, 0) * (2 * l1 + 1) * (2 * l2 + 1) * (2 * L + 1);
       for (int mm = -mmax; mm <= mmax; ++mm) {
@@ -1957,9 +2088,11 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
         }
       }
     }
-    scoef.assign((size_t)sug->nmult * combos.size(), 0.0);
-    for (int e = 0; e < sug->nmult; ++e)
-      for (const auto& tw : terms[e]) scoef[(size_t)e * combos.size() + tw.first] += tw.second;
+    if (!sugi_ep) {
+      scoef.assign((size_t)sug->nmult * combos.size(), 0.0);
+      for (int e = 0; e < sug->nmult; ++e)
+        for (const auto& tw : terms[e]) scoef[(size_t)e * combos.size() + tw.first] += tw.second;
+    }
     // rows b: A = the l1 part of bin b, B = G (pair (b, 0)); columns: the l2 parts of every bin
     std::vector<int> sp(nb);
     for (int b = 0; b < nb; ++b) sp[b] = b;
@@ -1998,6 +2131,7 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
     sl.X3 = (yamo && want3) ? (const void*)(X + 5 * xfs) : nullptr;
     sl.XB = crq ? (const void*)(X + xfs) : nullptr;
     sl.XC = crq ? (const void*)(X + 2 * xfs) : nullptr;
+    sl.XCOMP = sugi_ep ? (const void*)X : nullptr;
     sl.KZX = KZ;
     sl.nfine = N;
     sl.fields = dfields;
@@ -2214,10 +2348,10 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
       for (int q = 0; q < TRI_COLS; ++q) a.c_slot[q] = -1;
       const SCombo& cb = combos[c % ncombo];
       const bool ind = c >= ncombo;
-      const int fa = ind ? ifield[cb.l1][cb.m][cb.part] : sfield[cb.l1][cb.m][cb.part];
-      const int fc = ind ? ifield[cb.l2][cb.m][cb.part] : sfield[cb.l2][cb.m][cb.part];
+      const int fa = ind ? ifield[cb.l1][cb.m][cb.part] : (cb.fa >= 0 ? cb.fa : sfield[cb.l1][cb.m][cb.part]);
+      const int fc = ind ? ifield[cb.l2][cb.m][cb.part] : (cb.fc >= 0 ? cb.fc : sfield[cb.l2][cb.m][cb.part]);
       for (int b = 0; b < nb; ++b) a.a_slot[0][b] = stage_of(fa + b);
-      a.b_slot[0][0] = stage_of(ind ? iXN : iG);
+      a.b_slot[0][0] = stage_of(ind ? iXN : (cb.fg >= 0 ? cb.fg : iG));
       for (int b = 0; b < nb; ++b) a.c_slot[b] = stage_of(fc + b);
       a.nf_cols = nb;
       a.nrows = nb;

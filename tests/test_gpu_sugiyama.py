@@ -35,11 +35,13 @@ def _oracle(spec, cat, randoms, kb, mps):
 
 
 def _check(res, orc, cnt, mps, tol):
-    """Error relative to the B_000 scale of the same bin pair."""
+    """Error relative to the B_000 scale of the same bin pair.  For l1 + l2 odd (odd L, line of sight
+    to each grid point) the sum is imaginary and the library reports its imaginary part."""
     np.testing.assert_array_equal(res["nmodes"], cnt)
     scale = np.abs(np.real(orc[(0, 0, 0)]))
     for mp in mps:
-        got, want = res["B"][mp], np.real(orc[mp])
+        got = res["B"][mp]
+        want = np.imag(orc[mp]) if (mp[0] + mp[1]) % 2 else np.real(orc[mp])
         e = np.abs(got - want) / np.maximum(np.abs(want), scale)
         assert np.max(e) < tol, (mp, np.max(e))
 
@@ -150,8 +152,11 @@ def test_rejects(api):
     from synthetic import make_survey_catalogs
 
     g, r, origin = make_survey_catalogs(2000, 20000, 600.0, 900.0, 16, seed=91, fkp_p0=1e4)
-    with pytest.raises(RuntimeError):   # survey geometry with the line of sight to each grid point
-        api.bispectrum_sugiyama(g, n=32, box=600.0, kbins=(0.02, 0.01, 3), multipoles=[(2, 0, 2)], origin=origin,
+    with pytest.raises(RuntimeError):   # line of sight to each grid point: L above 4
+        api.bispectrum_sugiyama(g, n=32, box=600.0, kbins=(0.02, 0.01, 3), multipoles=[(4, 2, 6)], origin=origin,
+                                randoms=r, los_dir=None)
+    with pytest.raises(RuntimeError):   # line of sight to each grid point: odd l1 + l2 + L
+        api.bispectrum_sugiyama(g, n=32, box=600.0, kbins=(0.02, 0.01, 3), multipoles=[(1, 0, 0)], origin=origin,
                                 randoms=r, los_dir=None)
 
 
@@ -193,6 +198,42 @@ def test_cached_triangle_counts_survive_a_larger_call(api):
     again = api.bispectrum(cat, n=32, box=300.0, kbins=kb, scoc_ells=(0,), tripo_ells=(0,), precision="fp64")
     np.testing.assert_array_equal(again["NT"], first["NT"])
     np.testing.assert_array_equal(again["B"][0], first["B"][0])
+
+
+ENDPOINT = [(0, 0, 0), (2, 0, 2), (0, 2, 2), (1, 1, 0), (1, 1, 2), (2, 2, 2), (1, 0, 1), (2, 1, 1), (2, 1, 3)]
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 1e-4)])
+def test_survey_endpoint_line_of_sight(api, prec, tol):
+    """Survey geometry with the line of sight to each grid point: G_L^M for every M from the
+    y_L^M-weighted transforms, F_l^m in the catalogue frame and the full m1 + m2 + M = 0 sum,
+    including odd L (l1 + l2 + L even), against the oracle's sum over every sub-configuration."""
+    from synthetic import make_survey_catalogs
+
+    box = 600.0
+    g, r, origin = make_survey_catalogs(20000, 200000, box, 800.0, 32, seed=87, fkp_p0=1e4)
+    kf = 2 * np.pi / box
+    kb = (2 * kf, 1.5 * kf, 4)
+    spec = dict(n=32, box=box, origin=tuple(origin), assign=3, interlace=1, los="endpoint",
+                observer=(0.0, 0.0, 0.0), periodic=0)
+    res = api.bispectrum_sugiyama(g, n=32, box=box, kbins=kb, multipoles=ENDPOINT, los_dir=None, precision=prec,
+                                  origin=origin, randoms=r)
+    orc, cnt = _oracle(spec, g, r, kb, ENDPOINT)
+    _check(res, orc, cnt, ENDPOINT, tol)
+    # the odd-L multipoles measured are not all zero
+    scale = np.abs(np.real(orc[(0, 0, 0)]))
+    assert np.max(np.abs(np.imag(orc[(1, 0, 1)])) / scale) > 1e-4
+
+
+def test_endpoint_rejects_shot_noise(api):
+    from paper_2605_04864_gb300 import binding as B
+    from synthetic import make_survey_catalogs
+
+    g, r, origin = make_survey_catalogs(2000, 20000, 600.0, 900.0, 16, seed=89)
+    with pytest.raises(B.NpcError) as ei:
+        api.bispectrum_sugiyama(g, n=32, box=600.0, kbins=(0.03, 0.02, 3), multipoles=[(0, 0, 0)], los_dir=None,
+                                origin=origin, randoms=r, shot=True)
+    assert ei.value.status == 4
 
 
 @pytest.mark.slow
