@@ -657,12 +657,33 @@ def batch_leg(args, world, rank, barrier, max_over_ranks):
     launches = api.last_stats()["n_kernel_launches"]
     ms_eager = timed(False)
     nm = len(plan)
+    triple_path = "tcgen05" if api.get_option("tcgen05_triple") else "mma.sync"
+    plain = None
+    if not args.no_plain and rank == 0:
+        # the plain form of the same batch, mock by mock: float64 cuFFT Hand+17 P_0,2,4 and a float64
+        # B_0 by full inverse transforms and direct triangle sums (no tensor cores, no graph)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for it, m in zip(items, plan):
+            wpk = dict(n=m["n"], box=m["box"], assign=w["assign"], kmin=0.0, dk=w["dk"], nbins=m["pk_nbins"])
+            plain_gpu_power(it["data"], it["randoms"], m["origin"], wpk)
+            if m["bk_nbins"] > 0:
+                kbb = (w["bk_kmin"], w["dk"], m["bk_nbins"])
+                plain_gpu_bispec0_survey(it["data"], it["randoms"], m["origin"], m["n"], m["box"], kbb,
+                                         api.bispectrum_triangles(kbb))
+        torch.cuda.synchronize()
+        plain_s = time.perf_counter() - t0
+        plain = {"value": nm / plain_s, "unit": "mocks/s", "ms_per_batch": plain_s * 1e3,
+                 "method": "float64 torch.fft (cuFFT) Hand+17 P_0,2,4 and B_0 by full inverse transforms with direct "
+                           "float64 triangle sums, mock by mock (one pass, after the library's timed runs)",
+                 "speedup_of_graph": plain_s * 1e3 / ms_graph}
     del keep, items, arr, out
     torch.cuda.empty_cache()
     return {"metric": "mocks/s (96 survey mocks, 32 each at 128^3/192^3/256^3, P_0,2,4 + B_0 with shot noise)",
             "value": world * nm / (ms_graph / 1e3), "unit": "mocks/s", "ms_per_batch": ms_graph,
             "eager": {"value": world * nm / (ms_eager / 1e3), "ms_per_batch": ms_eager},
             "branches": branches, "tune_seconds": tune_s, "kernels_per_batch": launches,
+            "tuned_triple_path": triple_path, "plain_gpu": plain,
             "config": {"workload": "batch_96", "mocks": nm, "n_gal_total": sum(m["n_gal"] for m in plan),
                        "n_ran_total": sum(m["n_ran"] for m in plan), "precision": w["precision"]}}
 
@@ -846,6 +867,64 @@ def plain_gpu_bispec(cd, w, tri, dev="cuda"):
         out0[t] = S0[q, k] / (i33 * NT[q, k])
         out2[t] = 5.0 * S2[q, k] / (i33 * NT[q, k])
     return out0, out2
+
+
+def plain_gpu_bispec0_survey(gd, rd, origin, n, box, kb, tri, p=3, dev="cuda"):
+    """The plain GPU form of a survey-geometry B_0: float64 throughout, the FKP field data - alpha
+    randoms painted with float64 atomics on both interlacing phases, cuFFT through torch.fft, every
+    shell field F_b and indicator I_b by a full inverse transform, direct float64 triangle sums.
+    Returns the raw B_0 for ``tri``."""
+    import math
+
+    import torch
+
+    f64 = torch.float64
+    pg, wg = gd.pos.to(f64), gd.w.to(f64)
+    pr, wr, nr = rd.pos.to(f64), rd.w.to(f64), rd.nbar.to(f64)
+    alpha = wg.sum() / wr.sum()
+    i33 = alpha * (nr * nr * wr * wr * wr).sum()
+    o = torch.tensor(origin, dtype=f64, device=dev)
+
+    def paint(shift):
+        mesh = torch.zeros(n ** 3, dtype=f64, device=dev)
+        for pos, wt in ((pg, wg), (pr, -alpha * wr)):
+            s = (pos - o) * (n / box) + shift
+            i0 = torch.floor(s + 0.5) if p == 3 else torch.floor(s)
+            d = s - i0
+            taps = ([(-1, 0.5 * (0.5 - d) ** 2), (0, 0.75 - d * d), (1, 0.5 * (0.5 + d) ** 2)] if p == 3
+                    else [(0, 1.0 - d), (1, d)])
+            i0 = i0.long()
+            for ox, wx in taps:
+                ix = (i0[:, 0] + ox) % n
+                for oy, wy in taps:
+                    iy = (i0[:, 1] + oy) % n
+                    for oz, wz in taps:
+                        iz = (i0[:, 2] + oz) % n
+                        mesh.index_add_(0, (iz * n + iy) * n + ix, wt * wx[:, 0] * wy[:, 1] * wz[:, 2])
+        return mesh.view(n, n, n)
+
+    kfreq = torch.fft.fftfreq(n, d=1.0 / n).to(dev).to(f64)
+    kx = torch.arange(n // 2 + 1, dtype=f64, device=dev)
+    KZ, KY, KX = kfreq.view(n, 1, 1), kfreq.view(1, n, 1), kx.view(1, 1, -1)
+    kk = torch.sqrt(KX * KX + KY * KY + KZ * KZ)
+    sinc = lambda a: torch.where(a == 0, torch.ones_like(a), torch.sin(a) / torch.where(a == 0, torch.ones_like(a), a))
+    W = (sinc(math.pi * KX / n) * sinc(math.pi * KY / n) * sinc(math.pi * KZ / n)) ** p
+    phase = torch.exp(1j * math.pi * (KX + KY + KZ) / n)
+    X0 = 0.5 * (torch.fft.rfftn(paint(0.0)) + phase * torch.fft.rfftn(paint(0.5))) / W
+    nyq = (KX == n // 2) | (KY == -n // 2) | (KZ == -n // 2)
+    b = torch.floor((2 * math.pi / box * kk - kb[0]) / kb[1])
+    F0, I = [], []
+    for ib in range(kb[2]):
+        m = ((b == ib) & (~nyq) & (kk > 0)).to(f64)
+        F0.append(torch.fft.irfftn(X0 * m, s=(n, n, n)).flatten() * n ** 3)
+        I.append(torch.fft.irfftn(m.to(X0.dtype), s=(n, n, n)).flatten() * n ** 3)
+    F0, I = torch.stack(F0), torch.stack(I)
+    out = torch.zeros(len(tri), dtype=f64, device=dev)
+    for t, (i, j, k) in enumerate(tri):
+        s0 = torch.dot(F0[i] * F0[j], F0[k])
+        nt = torch.dot(I[i] * I[j], I[k])
+        out[t] = s0 / (i33 * nt)
+    return out
 
 
 def power_leg(args, w, world, local, rank, barrier, max_over_ranks):
