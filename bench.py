@@ -53,14 +53,14 @@ def _src_hash(files=None):
     return h.hexdigest()[:16]
 
 
-def _traffic(kernel):
+def _traffic(kernel, workload=WORKLOAD):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on the current source of
     the kernel (its translation unit and the headers it includes, as listed in the record)."""
     p = os.path.join(ROOT, "profiles", "dram_traffic.json")
     try:
         with open(p) as f:
             d = json.load(f)
-        rec = d.get(WORKLOAD, {}).get(kernel)
+        rec = d.get(workload, {}).get(kernel)
         if rec and rec.get("src_hash") == _src_hash(rec.get("src_files")):
             return float(rec["bytes_per_launch"])
     except Exception:
@@ -483,7 +483,7 @@ def bispec_leg(args, world, rank, barrier, max_over_ranks):
     tf32_peak, tf32_src = _tf32_peak()
     achieved = tri_flops / (tri_launch_ms / 1e3) / 1e12
     roofline = {"bound": "tensor", "kernel": "triple", "achieved": achieved, "peak": tf32_peak, "unit": "TFLOP/s",
-                "frac": achieved / tf32_peak, "traffic": None, "peak_source": tf32_src,
+                "frac": achieved / tf32_peak, "traffic": _traffic("triple", "bispec_256"), "peak_source": tf32_src,
                 "flops_per_launch": tri_flops, "launch_ms": tri_launch_ms,
                 "issued_frac": 3 * achieved / tf32_peak,
                 "note": "useful multiply-adds 2 x rows x columns x cells of the 128^3 shell grid; the split "

@@ -32,18 +32,24 @@ namespace tc {
 constexpr int CHUNK = 128;        // cells per bulk-copy chunk (512 bytes per staged field)
 constexpr int SROW = CHUNK + 4;   // floats between staged field rows: 16-byte aligned, and rows
                                   // fall 16 bytes apart modulo 128 (conflict-light 16-byte reads)
-constexpr int AST = 32;           // cells per A stage (four k steps of 8)
-constexpr int FLUSH = 128;        // A stages between float64 flushes
+// 32-cell stages, two in flight: 16-cell stages with three or four in flight measured 0.91 and
+// 0.89 ms against 0.79 ms at 256^3 (the per-stage hand-off costs more than the deeper ring saves)
+constexpr int AST = 32;           // cells per A stage (k steps of 8)
+constexpr int NSA = 2;            // A stages in flight (tensor-memory ring)
+constexpr int KSTEPS = AST / 8;
+constexpr int SPC = CHUNK / AST;  // A stages per chunk
+constexpr int CPT = AST / 2;      // cells per producer thread per A stage (two threads per row)
+constexpr int FLUSH = 4096 / AST; // A stages between float64 flushes (4096 cells)
 constexpr int NCOL = 32;          // MMA N (columns, padded)
 constexpr int BTILE = 1024;       // bytes of one k step of the column operand (32 x 8 tf32)
 constexpr long long DRAIN_LIMIT = 1ll << 31;  // cycles a clean-up wait may take
 
 // column of tensor memory holding A stage `sb` (0/1), row tile `t`, part hl (0 hi, 1 lo)
 __device__ __forceinline__ uint32_t col_a(int sb, int t, int hl, int nt) { return (uint32_t)(((sb * nt + t) * 2 + hl) * AST); }
-__device__ __forceinline__ uint32_t col_d(int t, int nt) { return (uint32_t)(2 * nt * 2 * AST + t * NCOL); }
+__device__ __forceinline__ uint32_t col_d(int t, int nt) { return (uint32_t)(NSA * nt * 2 * AST + t * NCOL); }
 
 __host__ __device__ constexpr uint32_t tmem_cols(int nt) {
-  return (nt * (4 * AST + NCOL)) <= 256 ? 256u : 512u;
+  return (nt * (2 * NSA * AST + NCOL)) <= 256 ? 256u : 512u;
 }
 
 // instruction descriptor: D f32, A and B tf32, both K-major, N = 32, M = 128
@@ -110,6 +116,10 @@ __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.a
 // TMEM stores read their registers at issue; completion (tcgen05.wait::st) is awaited before the
 // thread synchronisation that hands the stage to the MMA thread.  No memory clobber: tensor memory
 // is not addressable memory, and ordinary loads may move across the store.
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&v)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr), "r"(v[0]),
+               "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]));
+}
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
   asm volatile(
       "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
@@ -161,8 +171,8 @@ __device__ __forceinline__ void split(float v, uint32_t& hi, uint32_t& lo) {
 
 struct Smem {
   uint64_t full_tma[3];     // chunk buffer filled (transaction count)
-  uint64_t full_a[2];       // A stage written by every producer warp
-  uint64_t empty_a[2];      // products of an A stage complete (tcgen05.commit)
+  uint64_t full_a[NSA];     // A stage written by every producer warp
+  uint64_t empty_a[NSA];    // products of an A stage complete (tcgen05.commit)
   uint64_t drain;           // clean-up commit
   uint32_t tmem_base;
   int abort;
@@ -182,8 +192,8 @@ k_triple_tc(const float* __restrict__ R, const __grid_constant__ TripleArgs A, c
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* buf = reinterpret_cast<float*>(smem_raw);                                   // [nbuf][nstage][SROW]
   const size_t buf_bytes = (size_t)nbuf * A.nstage * SROW * sizeof(float);
-  unsigned char* btile = smem_raw + ((buf_bytes + 1023) & ~(size_t)1023);            // [2 sb][2 hl][4 k][1 KB]
-  double* accs = reinterpret_cast<double*>(btile + 2 * 2 * 4 * BTILE);              // [NCOL][NT * 128]
+  unsigned char* btile = smem_raw + ((buf_bytes + 1023) & ~(size_t)1023);     // [NSA sb][2 hl][KSTEPS k][1 KB]
+  double* accs = reinterpret_cast<double*>(btile + NSA * 2 * KSTEPS * BTILE);  // [NCOL][NT * 128]
   Smem* sm = reinterpret_cast<Smem*>(accs + (size_t)NCOL * NT * 128);
   volatile int* abort = &sm->abort;
 
@@ -197,7 +207,7 @@ k_triple_tc(const float* __restrict__ R, const __grid_constant__ TripleArgs A, c
   const int64_t c_beg = min((int64_t)blockIdx.x * per, nchunk_all);
   const int64_t c_end = min(c_beg + per, nchunk_all);
   const int nchunk = (int)(c_end - c_beg);
-  const int nst = nchunk * (CHUNK / AST);
+  const int nst = nchunk * SPC;
   const int64_t cell0 = c_beg * CHUNK;
 
   for (int i = tid; i < NCOL * NT * 128; i += blockDim.x) accs[i] = 0.0;
@@ -208,7 +218,7 @@ k_triple_tc(const float* __restrict__ R, const __grid_constant__ TripleArgs A, c
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     if (lane == 0) {
       for (int b = 0; b < nbuf; ++b) mbar_init(&sm->full_tma[b], 1);
-      for (int b = 0; b < 2; ++b) {
+      for (int b = 0; b < NSA; ++b) {
         mbar_init(&sm->full_a[b], NT * 8);
         mbar_init(&sm->empty_a[b], 1);
       }
@@ -238,8 +248,8 @@ k_triple_tc(const float* __restrict__ R, const __grid_constant__ TripleArgs A, c
       const uint64_t bdesc0 = sdesc(smem_u32(btile), 128, 256);
       bool ok = true;
       for (int s = 0; s < nst; ++s) {
-        const int sb = s & 1;
-        if (!mbar_wait(&sm->full_a[sb], (uint32_t)((s >> 1) & 1), limit, abort, status)) {
+        const int sb = s % NSA;
+        if (!mbar_wait(&sm->full_a[sb], (uint32_t)((s / NSA) & 1), limit, abort, status)) {
           ok = false;
           break;
         }
@@ -249,12 +259,12 @@ k_triple_tc(const float* __restrict__ R, const __grid_constant__ TripleArgs A, c
         for (int t = 0; t < NT; ++t) {
           const uint32_t d = tbase + col_d(t, NT);
 #pragma unroll
-          for (int j = 0; j < AST / 8; ++j) {
+          for (int j = 0; j < KSTEPS; ++j) {
             const uint32_t ahi = tbase + col_a(sb, t, 0, NT) + 8 * j;
             const uint32_t alo = tbase + col_a(sb, t, 1, NT) + 8 * j;
             // the descriptor's start address field counts 16-byte units
-            const uint64_t bh = bdesc0 + (uint64_t)((((sb * 2 + 0) * 4 + j) * BTILE) >> 4);
-            const uint64_t bl = bdesc0 + (uint64_t)((((sb * 2 + 1) * 4 + j) * BTILE) >> 4);
+            const uint64_t bh = bdesc0 + (uint64_t)((((sb * 2 + 0) * KSTEPS + j) * BTILE) >> 4);
+            const uint64_t bl = bdesc0 + (uint64_t)((((sb * 2 + 1) * KSTEPS + j) * BTILE) >> 4);
             mma_tf32(d, ahi, bh, (fresh && j == 0) ? 0u : 1u);
             mma_tf32(d, ahi, bl, 1u);
             mma_tf32(d, alo, bh, 1u);
@@ -262,7 +272,7 @@ k_triple_tc(const float* __restrict__ R, const __grid_constant__ TripleArgs A, c
         }
         mma_commit(&sm->empty_a[sb]);
         // the last A stage of chunk c has been read by every producer: its buffer is free
-        if ((s % (CHUNK / AST)) == CHUNK / AST - 1 && issued < nchunk) issue(issued++);
+        if ((s % SPC) == SPC - 1 && issued < nchunk) issue(issued++);
       }
       // every product issued must finish before tensor memory is freed (the producers have waited
       // for them unless a wait gave up)
@@ -290,29 +300,29 @@ k_triple_tc(const float* __restrict__ R, const __grid_constant__ TripleArgs A, c
     const int cslot = ncol_here < A.ncol ? A.c_slot[ncol_here] : -1;
     const uint32_t lane_addr = tbase + ((uint32_t)(q * 32) << 16);
     for (int s = 0; s < nst; ++s) {
-      const int sb = s & 1;
-      const int c = s / (CHUNK / AST);
-      const int o = (s % (CHUNK / AST)) * AST;
+      const int sb = s % NSA;
+      const int c = s / SPC;
+      const int o = (s % SPC) * AST;
       const int b = c % nbuf;
-      if ((s % (CHUNK / AST)) == 0 && !mbar_wait(&sm->full_tma[b], (uint32_t)((c / nbuf) & 1), limit, abort, status))
+      if ((s % SPC) == 0 && !mbar_wait(&sm->full_tma[b], (uint32_t)((c / nbuf) & 1), limit, abort, status))
         break;
-      if (s >= 2 && !mbar_wait(&sm->empty_a[sb], (uint32_t)(((s - 2) >> 1) & 1), limit, abort, status)) break;
+      if (s >= NSA && !mbar_wait(&sm->empty_a[sb], (uint32_t)(((s - NSA) / NSA) & 1), limit, abort, status)) break;
       tc_fence_after();
       const float* stage = buf + (size_t)b * A.nstage * SROW;
-      // A operand: pair products of this row for cells o + 16 h .. + 16, hi and lo
+      // A operand: pair products of this row for cells o + CPT h .. + CPT, hi and lo
       {
-        uint32_t vh[16], vl[16];
+        uint32_t vh[CPT], vl[CPT];
         if (sa >= 0) {
-          const float4* pa = reinterpret_cast<const float4*>(stage + (size_t)sa * SROW + o + 16 * h);
-          const float4* pb = reinterpret_cast<const float4*>(stage + (size_t)sbs * SROW + o + 16 * h);
-          float4 x[4], y[4];
+          const float4* pa = reinterpret_cast<const float4*>(stage + (size_t)sa * SROW + o + CPT * h);
+          const float4* pb = reinterpret_cast<const float4*>(stage + (size_t)sbs * SROW + o + CPT * h);
+          float4 x[CPT / 4], y[CPT / 4];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
+          for (int u = 0; u < CPT / 4; ++u) {
             x[u] = pa[u];
             y[u] = pb[u];
           }
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
+          for (int u = 0; u < CPT / 4; ++u) {
             split(x[u].x * y[u].x, vh[4 * u + 0], vl[4 * u + 0]);
             split(x[u].y * y[u].y, vh[4 * u + 1], vl[4 * u + 1]);
             split(x[u].z * y[u].z, vh[4 * u + 2], vl[4 * u + 2]);
@@ -320,21 +330,26 @@ k_triple_tc(const float* __restrict__ R, const __grid_constant__ TripleArgs A, c
           }
         } else {
 #pragma unroll
-          for (int u = 0; u < 16; ++u) vh[u] = vl[u] = 0u;
+          for (int u = 0; u < CPT; ++u) vh[u] = vl[u] = 0u;
         }
-        tmem_st16(lane_addr + col_a(sb, t, 0, NT) + 16 * h, vh);
-        tmem_st16(lane_addr + col_a(sb, t, 1, NT) + 16 * h, vl);
+        if constexpr (CPT == 16) {
+          tmem_st16(lane_addr + col_a(sb, t, 0, NT) + CPT * h, vh);
+          tmem_st16(lane_addr + col_a(sb, t, 1, NT) + CPT * h, vl);
+        } else {
+          tmem_st8(lane_addr + col_a(sb, t, 0, NT) + CPT * h, vh);
+          tmem_st8(lane_addr + col_a(sb, t, 1, NT) + CPT * h, vl);
+        }
       }
       // B operand: core matrices of 8 columns x 4 cells, k step j = cm / 8, K half kh = (cm / 4) % 2
-      for (int cm = warp; cm < 32; cm += NT * 8) {
+      for (int cm = warp; cm < 8 * KSTEPS; cm += NT * 8) {
         const int j = cm >> 3, kh = (cm >> 2) & 1;
         const int cell = o + 8 * j + 4 * kh + (lane & 3);
         const float v = cslot >= 0 ? stage[(size_t)cslot * SROW + cell] : 0.f;
         uint32_t hi, lo;
         split(v, hi, lo);
         const size_t off = (size_t)q * 256 + kh * 128 + (lane >> 2) * 16 + (lane & 3) * 4;
-        *reinterpret_cast<uint32_t*>(btile + ((sb * 2 + 0) * 4 + j) * BTILE + off) = hi;
-        *reinterpret_cast<uint32_t*>(btile + ((sb * 2 + 1) * 4 + j) * BTILE + off) = lo;
+        *reinterpret_cast<uint32_t*>(btile + ((sb * 2 + 0) * KSTEPS + j) * BTILE + off) = hi;
+        *reinterpret_cast<uint32_t*>(btile + ((sb * 2 + 1) * KSTEPS + j) * BTILE + off) = lo;
       }
       asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
       fence_async_smem();
@@ -342,7 +357,7 @@ k_triple_tc(const float* __restrict__ R, const __grid_constant__ TripleArgs A, c
       __syncwarp();
       if (lane == 0) mbar_arrive(&sm->full_a[sb]);
       if ((s % FLUSH) == FLUSH - 1 || s == nst - 1) {
-        if (!mbar_wait(&sm->empty_a[sb], (uint32_t)((s >> 1) & 1), limit, abort, status)) break;
+        if (!mbar_wait(&sm->empty_a[sb], (uint32_t)((s / NSA) & 1), limit, abort, status)) break;
         tc_fence_after();
         uint32_t v[16];
         tmem_ld16_wait(lane_addr + col_d(t, NT) + 16 * h, v);
@@ -372,6 +387,6 @@ k_triple_tc(const float* __restrict__ R, const __grid_constant__ TripleArgs A, c
 // dynamic shared memory of k_triple_tc<NT> for `nstage` staged fields and `nbuf` chunk buffers
 inline size_t tc_triple_smem(int nstage, int nbuf, int nt) {
   const size_t buf = (size_t)nbuf * nstage * tc::SROW * sizeof(float);
-  return ((buf + 1023) & ~(size_t)1023) + 2 * 2 * 4 * tc::BTILE + sizeof(double) * tc::NCOL * nt * 128 +
+  return ((buf + 1023) & ~(size_t)1023) + tc::NSA * 2 * tc::KSTEPS * tc::BTILE + sizeof(double) * tc::NCOL * nt * 128 +
          sizeof(tc::Smem);
 }
