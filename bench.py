@@ -554,7 +554,12 @@ def bispec_leg(args, world, rank, barrier, max_over_ranks):
             "sugiyama": sugiyama,
             "fft_method_shot": {"value": world * ntri.value * nmult / (ms_fft / 1e3), "ms_per_step": ms_fft,
                                 "note": "shot noise of B_l and B_l0l by the FFT method (exact sums of the two-object terms)"},
-            "triple_product": "3xTF32 split hi+lo tensor-core products (mma.sync m16n8k8), FP32 within 128-cell chunks, FP64 across chunks"}
+            "triple_product": ("3xTF32 split hi+lo tensor-core products: tcgen05.mma kind::tf32 M=128 N=32 with the "
+                               "pair products in tensor memory for launches of more than 32 rows, mma.sync m16n8k8 "
+                               "for the rest; FP32 within 4096-cell (tcgen05) or 128-cell chunks, FP64 across them"
+                               if api.get_option("tcgen05_triple") else
+                               "3xTF32 split hi+lo tensor-core products (mma.sync m16n8k8), FP32 within 128-cell "
+                               "chunks, FP64 across chunks")}
 
 
 def adjoint_leg(args, world, rank, barrier, max_over_ranks):
