@@ -341,6 +341,15 @@ def _tf32_peak():
         return 1900.0 * 1.1 / 2.25, "fallback bf16 x nominal tf32/bf16"
 
 
+def _f16_peak():
+    """Dense f16 tensor peak: the measured bf16 burst figure (f16 and bf16 share the dense rate)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured bf16 (f16 has the same dense rate)"
+    except Exception:
+        return 1900.0, "fallback bf16 (f16 has the same dense rate)"
+
+
 def bispec_errors(cat, res):
     """Error of every B_0, B_2 triangle and B_000, B_202 pair (raw estimate and analytic shot noise)
     against the FP64 oracle values stored for the same catalogue (tests/golden/full_size_bispec_256.json,
@@ -475,19 +484,25 @@ def bispec_leg(args, world, rank, barrier, max_over_ranks):
     e2e = {"value": world * ntri.value * nmult * args.steps / e2e_s, "unit": "triangles/s",
            "h2d_bytes_per_step": sum(t.numel() * t.element_size() for t in (ch.pos, ch.w, ch.nbar)),
            "d2h_bytes_per_step": length.value * 8, "ms_per_step": e2e_s / args.steps * 1e3}
-    # the dense triple-product contraction: tensor-bound (float32 shell fields split into tf32 hi + lo)
+    # the dense triple-product contraction: tensor-bound (float32 shell fields split into f16 hi + lo
+    # on the tcgen05 path, tf32 hi + lo on mma.sync)
     st = api.last_stats()
     tri_ms, tri_nl, tri_rep = acc.get("triple", [0.0, 0, 1])
     tri_launch_ms = tri_ms / max(tri_nl, 1)
     tri_flops = st["contraction_flops"] / max(st["contraction_launches"], 1)
-    tf32_peak, tf32_src = _tf32_peak()
+    tri_issued = st["contraction_issued_flops"] / max(st["contraction_launches"], 1)
+    tc_path = bool(api.get_option("tcgen05_triple"))
+    tpeak, tpeak_src = _f16_peak() if tc_path else _tf32_peak()
     achieved = tri_flops / (tri_launch_ms / 1e3) / 1e12
-    roofline = {"bound": "tensor", "kernel": "triple", "achieved": achieved, "peak": tf32_peak, "unit": "TFLOP/s",
-                "frac": achieved / tf32_peak, "traffic": _traffic("triple", "bispec_256"), "peak_source": tf32_src,
+    roofline = {"bound": "tensor", "kernel": "triple", "achieved": achieved, "peak": tpeak, "unit": "TFLOP/s",
+                "frac": achieved / tpeak, "traffic": _traffic("triple", "bispec_256"), "peak_source": tpeak_src,
                 "flops_per_launch": tri_flops, "launch_ms": tri_launch_ms,
-                "issued_frac": 3 * achieved / tf32_peak,
-                "note": "useful multiply-adds 2 x rows x columns x cells of the 128^3 shell grid; the split "
-                        "precision issues three tensor products per useful one (issued_frac)"}
+                "issued_flops_per_launch": tri_issued,
+                "issued_frac": tri_issued / (tri_launch_ms / 1e3) / 1e12 / tpeak,
+                "note": "useful multiply-adds 2 x rows x columns x cells of the 128^3 shell grid (frac); "
+                        "issued_frac counts what the tensor cores execute: padded 128-row tiles and N "
+                        "columns, two f16 products per k step for the hi + lo split (tcgen05) or three "
+                        "tf32 products on 16 x 8 tiles (mma.sync)"}
     errs = bispec_errors(cat, host_res) if rank == 0 else None
     # Sugiyama TripoSH multipoles on the same catalogue (every (k1, k2) bin pair, raw estimator)
     mps = [(0, 0, 0), (1, 1, 0), (1, 1, 2), (2, 0, 2), (2, 2, 0), (2, 2, 2)]

@@ -109,10 +109,12 @@ typedef struct {
   int64_t workspace_bytes;     /* device workspace held by the context after the call */
   double contraction_flops;    /* bispectrum calls: multiply-add work of the dense triple-product
                                   contractions the call launched, 2 x rows x columns x cells summed
-                                  over the launches (the useful products; the tensor cores issue
-                                  three per product for the split precision) */
+                                  over the launches (the useful products) */
   int32_t contraction_launches;/* number of those launches */
   int32_t reserved;
+  double contraction_issued_flops; /* the same contractions as the tensor cores issue them: padded
+                                  rows and columns and the parts of the split precision (f16 hi and
+                                  lo on the tcgen05 path, tf32 hi*hi + hi*lo + lo*hi on mma.sync) */
 } npc_stats;
 npc_status npc_last_stats(npc_ctx* ctx, npc_stats* out);
 

@@ -49,7 +49,8 @@ NPC_BATCH_GRAPH = 1
 class npc_stats(C.Structure):
     _fields_ = [("n_transforms", C.c_int32), ("n_r2c_equivalent", C.c_int32), ("n_phases", C.c_int32),
                 ("n_kernel_launches", C.c_int32), ("workspace_bytes", C.c_int64),
-                ("contraction_flops", C.c_double), ("contraction_launches", C.c_int32), ("reserved", C.c_int32)]
+                ("contraction_flops", C.c_double), ("contraction_launches", C.c_int32), ("reserved", C.c_int32),
+                ("contraction_issued_flops", C.c_double)]
 
 
 _P = C.POINTER

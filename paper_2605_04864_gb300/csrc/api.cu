@@ -267,6 +267,7 @@ void begin_call(npc_ctx* ctx) {
   ctx->launches = 0;
   ctx->bounded_waits = false;
   ctx->contraction_flops = 0.0;
+  ctx->contraction_issued_flops = 0.0;
   ctx->contraction_launches = 0;
   ctx->last_error.clear();
   stage_begin(ctx);
@@ -276,6 +277,7 @@ npc_status end_call(npc_ctx* ctx) {
   ctx->stats.n_kernel_launches = ctx->launches;
   ctx->stats.contraction_flops = ctx->contraction_flops;
   ctx->stats.contraction_launches = ctx->contraction_launches;
+  ctx->stats.contraction_issued_flops = ctx->contraction_issued_flops;
   int64_t tot = 0;
   for (auto& kv : ctx->ws) tot += (int64_t)kv.second.bytes;
   ctx->stats.workspace_bytes = tot;

@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 
 #include "fft_core.cuh"
 
@@ -614,13 +615,43 @@ k_shell_y(const cplx<T>* __restrict__ T1, const ShellField* __restrict__ fields,
   for (int q = 0; q < 8; ++q) dst[(size_t)(t + q * TPF) * N] = v[q];
 }
 
+// Float shell fields are stored chunk-interleaved: for every run of RCH = 128 cells the rows of all
+// nfield fields follow each other (512 bytes each), so that the rows of consecutive fields of one
+// chunk form one contiguous block (the tensor-core triple products copy each such block with one
+// bulk copy).  Within its row, field f's cells are rotated by rf_rot(f) = 4 (f mod 8) places
+// (16-byte units): once a block is in shared memory, reads of one cell offset from the rows of
+// eight consecutive fields fall on distinct banks.  Float64 fields keep one row of ncell values per
+// field.
+constexpr int RCH = 128;
+__host__ __device__ __forceinline__ int rf_rot(int field) { return 4 * (field & 7); }
+__host__ __device__ __forceinline__ size_t rf_index(int field, int64_t cell, int nfield) {
+  const uint64_t uc = (uint64_t)cell;
+  return ((size_t)(uc >> 7) * nfield + field) * RCH + (size_t)(((int)(uc & (RCH - 1)) + rf_rot(field)) & (RCH - 1));
+}
+
+// largest |v| of a block's values of one field into fmax[f] (float bits of a non-negative value
+// order as unsigned integers; a NaN orders above every finite value)
+template <int THREADS>
+__device__ __forceinline__ void block_absmax(unsigned m, unsigned* red, unsigned* fmax) {
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < THREADS / 32; ++w) m = max(m, red[w]);
+    if (m > *reinterpret_cast<volatile unsigned*>(fmax)) atomicMax(fmax, m);
+  }
+  __syncthreads();
+}
+
 // z columns, two real fields (same K) per complex inverse transform:
 // c(kz) = A(kz) + i B(kz), c(N - kz) = conj(A(kz)) + i conj(B(kz)); Re -> A(z), Im -> B(z).
+// With fmax (float fields), the largest |value| of every field written is recorded there: the
+// tensor-core triple products scale their f16 operands by it.
 template <typename T, int N>
 __global__ void __launch_bounds__(BCol<N>::THREADS)
 k_shell_z(const cplx<T>* __restrict__ T2, const ShellField* __restrict__ fields, const int* __restrict__ pair_a,
           const int* __restrict__ pair_b, const int* __restrict__ out_a, const int* __restrict__ out_b,
-          const cplx<T>* __restrict__ tw_g, T* __restrict__ R) {
+          const cplx<T>* __restrict__ tw_g, T* __restrict__ R, int nfield, unsigned* __restrict__ fmax) {
   using C = cplx<T>;
   constexpr int TX = BCol<N>::TX;
   constexpr int TPF = N / 8;
@@ -657,13 +688,44 @@ k_shell_z(const cplx<T>* __restrict__ T2, const ShellField* __restrict__ fields,
   __syncthreads();
   fft_block<N, +1>(v, t, tw, ColView<C>{work + c, TX});
   const size_t cell0 = (size_t)y * N + x;
-  T* ra = R + (size_t)out_a[p] * N * plane + cell0;
-  T* rb = out_b[p] >= 0 ? R + (size_t)out_b[p] * N * plane + cell0 : nullptr;
+  const bool has_b = out_b[p] >= 0;
+  if constexpr (sizeof(T) == 4) {
+    // rf_index with the z plane split off: N^2 is a multiple of RCH (N is a multiple of 16)
+    const size_t cstride = (size_t)nfield * RCH;
+    const size_t pchunks = plane / RCH;
+    const int w0 = (int)(cell0 & (RCH - 1));
+    const size_t c0k = cell0 / RCH;
+    const int fa = out_a[p], fb = has_b ? out_b[p] : 0;
+    const size_t oa = (size_t)fa * RCH + ((w0 + rf_rot(fa)) & (RCH - 1));
+    const size_t ob = (size_t)fb * RCH + ((w0 + rf_rot(fb)) & (RCH - 1));
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const size_t zo = (size_t)(t + q * TPF) * plane;
-    ra[zo] = v[q].x;
-    if (rb) rb[zo] = v[q].y;
+    for (int q = 0; q < 8; ++q) {
+      const size_t base = ((size_t)(t + q * TPF) * pchunks + c0k) * cstride;
+      R[base + oa] = v[q].x;
+      if (has_b) R[base + ob] = v[q].y;
+    }
+  } else {
+    T* ra = R + (size_t)out_a[p] * N * plane + cell0;
+    T* rb = has_b ? R + (size_t)out_b[p] * N * plane + cell0 : nullptr;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const size_t zo = (size_t)(t + q * TPF) * plane;
+      ra[zo] = v[q].x;
+      if (rb) rb[zo] = v[q].y;
+    }
+  }
+  if constexpr (sizeof(T) == 4) {
+    if (fmax) {
+      __shared__ unsigned red[BCol<N>::THREADS / 32];
+      unsigned ma = 0u, mb = 0u;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        ma = max(ma, __float_as_uint(v[q].x) & 0x7fffffffu);
+        mb = max(mb, __float_as_uint(v[q].y) & 0x7fffffffu);
+      }
+      block_absmax<BCol<N>::THREADS>(ma, red, fmax + out_a[p]);
+      if (has_b) block_absmax<BCol<N>::THREADS>(mb, red, fmax + out_b[p]);
+    }
   }
 }
 
@@ -700,6 +762,7 @@ struct TripleArgs {
   int c_slot[TRI_COLS];             // staged slot of column c (-1: zero column)
   int nf_cols;                      // columns 0 .. nf_cols-1 are F_k (k = column), the rest G^(l)
   int64_t ncell;
+  int nfield_r;                     // fields of the shell-field array (float layout: rf_index)
 };
 
 // v = hi + lo with hi = v truncated to the 10 explicit mantissa bits of tf32 (a bit mask) and the
@@ -776,9 +839,16 @@ k_triple(const float* __restrict__ R, const TripleArgs A, const int* __restrict_
   for (int64_t c0 = beg; c0 < end; c0 += TRI_CHUNK) {
     const int nc = (int)((end - c0) < (int64_t)TRI_CHUNK ? (end - c0) : (int64_t)TRI_CHUNK);
     __syncthreads();
-    for (int idx = tid; idx < A.nstage * TRI_CHUNK; idx += blockDim.x) {
-      const int sl = idx / TRI_CHUNK, c = idx % TRI_CHUNK;
-      stage[(size_t)sl * TRI_SPAD + c] = c < nc ? R[(size_t)A.stage_field[sl] * A.ncell + c0 + c] : 0.f;
+    // one 128-cell row of a staged field per warp and step: a 16-byte load per lane, the row's
+    // rotation undone on the store (nc is a multiple of RCH: ncell is)
+    for (int rw = warp; rw < A.nstage * (TRI_CHUNK / RCH); rw += TRI_WARPS) {
+      const int sl = rw / (TRI_CHUNK / RCH), half = rw % (TRI_CHUNK / RCH);
+      const int field = A.stage_field[sl], rot = rf_rot(field);
+      const int cl = (lane * 4 - rot) & (RCH - 1);   // logical cell of the lane's first value
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (half * RCH < nc)
+        v = *reinterpret_cast<const float4*>(R + (((size_t)(c0 / RCH) + half) * A.nfield_r + field) * RCH + lane * 4);
+      *reinterpret_cast<float4*>(stage + (size_t)sl * TRI_SPAD + half * RCH + cl) = v;
     }
     __syncthreads();
     constexpr int KPW = SK ? TRI_CHUNK / TRI_WARPS : TRI_CHUNK;   // cells of the chunk per warp
@@ -877,6 +947,118 @@ k_triple_f64(const double* __restrict__ R, const TripleArgs A, const int* __rest
 }
 
 #include "triple_tc.cuh"
+
+// Orientation of a tensor-core triple-product launch (triple_tc.cuh).  Every output (family f,
+// pair (i, j), column c) multiplies three staged fields A_{f,i} B_{f,j} C_c; two of them form a
+// product row (M side) and the third a single-field column (N side, hi and lo interleaved).  The
+// three assignments are tried and the one with the lowest cost is kept: per 16-cell k step each
+// row tile takes two products of at least 46 cycles (N <= 64 costs as much as N = 16; above that
+// about N / 2), and forming a row about half a cycle.
+struct TcPlanHost {
+  int nmrow = 0, nmcol = 0, n = 0, nt = 1, groups = 1, nsa = 2, nbuf = 3;
+  size_t smem = 0;
+  std::vector<int16_t> rx, ry, cz;   // staged slots, numbered by increasing field index
+  std::vector<int> sfield, runs;     // field of each slot; runs of consecutive fields (first slot, length)
+  std::vector<int> gidx;
+  size_t o_rx = 0, o_ry = 0, o_cz = 0, o_sfield = 0, o_runs = 0, o_gidx = 0;   // offsets in the uploaded table
+};
+
+bool plan_triple_tc(const TripleArgs& a, const int* pij, int max_smem, TcPlanHost& out) {
+  if (a.npair <= 0 || a.nrows % a.npair != 0 || a.nstage > tc::MAX_SLOTS || a.ncell % tc::CHUNK != 0) return false;
+  const int nfam = a.nrows / a.npair;
+  // staged slots renumbered by increasing field index; runs of consecutive fields
+  std::vector<int> order(a.nstage), pos(a.nstage);
+  for (int q = 0; q < a.nstage; ++q) order[q] = q;
+  std::sort(order.begin(), order.end(), [&](int x, int y) { return a.stage_field[x] < a.stage_field[y]; });
+  std::vector<int> sfield(a.nstage), runs;
+  for (int q = 0; q < a.nstage; ++q) {
+    pos[order[q]] = q;
+    sfield[q] = a.stage_field[order[q]];
+    if (q > 0 && sfield[q] == sfield[q - 1]) return false;   // a field staged twice
+    if (q == 0 || sfield[q] != sfield[q - 1] + 1) {
+      runs.push_back(q);
+      runs.push_back(1);
+    } else {
+      runs.back() += 1;
+    }
+  }
+  auto slot = [&](int x) { return x < 0 ? -1 : pos[x]; };
+  double best = 1e300;
+  bool found = false;
+  for (int orient = 0; orient < 3; ++orient) {
+    std::map<std::pair<int, int>, int> rows;
+    std::map<int, int> cols;
+    auto roles = [&](int f, int p, int c, int& u, int& v, int& w) {
+      const int xa = slot(a.a_slot[f][pij[p] & 0xffff]), xb = slot(a.b_slot[f][pij[p] >> 16]), xc = slot(a.c_slot[c]);
+      if (orient == 0) { u = xa; v = xb; w = xc; }
+      else if (orient == 1) { u = xb; v = xc; w = xa; }
+      else { u = xa; v = xc; w = xb; }
+      if (u > v) std::swap(u, v);
+    };
+    for (int f = 0; f < nfam; ++f)
+      for (int p = 0; p < a.npair; ++p)
+        for (int c = 0; c < a.ncol; ++c) {
+          if (a.c_slot[c] < 0) continue;
+          int u, v, w;
+          roles(f, p, c, u, v, w);
+          if (u < 0 || w < 0) return false;
+          rows.emplace(std::make_pair(u, v), 0);
+          cols.emplace(w, 0);
+        }
+    const int nr = (int)rows.size(), nc = (int)cols.size();
+    if (nr == 0 || nc == 0) return false;
+    const int n = std::max(16, (2 * nc + 15) / 16 * 16);
+    if (n > tc::MAXN) continue;
+    const int tiles = (nr + 127) / 128;
+    const int groups = (tiles + 2) / 3, nt = (tiles + groups - 1) / groups;
+    const int nsa = std::min(tc::NSA_MAX, (512 / nt - n) / tc::ACOLS);
+    if (nsa < 2) continue;
+    int nbuf = 3;
+    size_t smem = tc::tc_layout(a.nstage, 3, nt, n, nc, nsa).total;
+    if (smem > 200 * 1024) {
+      nbuf = 2;
+      smem = tc::tc_layout(a.nstage, 2, nt, n, nc, nsa).total;
+    }
+    if (smem > (size_t)max_smem) continue;
+    const double cost = (double)tiles * 2.0 * std::max(46.0, n / 2.0) + 0.5 * nr;
+    if (cost >= best) continue;
+    best = cost;
+    found = true;
+    TcPlanHost P;
+    P.sfield = sfield;
+    P.runs = runs;
+    P.nmrow = nr;
+    P.nmcol = nc;
+    P.n = n;
+    P.nt = nt;
+    P.groups = groups;
+    P.nsa = nsa;
+    P.nbuf = nbuf;
+    P.smem = smem;
+    int k = 0;
+    for (auto& e : rows) {   // key order: rows sharing their first factor are adjacent (broadcast loads)
+      e.second = k++;
+      P.rx.push_back((int16_t)e.first.first);
+      P.ry.push_back((int16_t)e.first.second);
+    }
+    k = 0;
+    for (auto& e : cols) {
+      e.second = k++;
+      P.cz.push_back((int16_t)e.first);
+    }
+    P.gidx.assign((size_t)a.nrows * a.ncol, -1);
+    for (int f = 0; f < nfam; ++f)
+      for (int p = 0; p < a.npair; ++p)
+        for (int c = 0; c < a.ncol; ++c) {
+          if (a.c_slot[c] < 0) continue;
+          int u, v, w;
+          roles(f, p, c, u, v, w);
+          P.gidx[((size_t)f * a.npair + p) * a.ncol + c] = rows.at(std::make_pair(u, v)) * nc + cols.at(w);
+        }
+    out = std::move(P);
+  }
+  return found;
+}
 
 // ------------------------------------------------------------------------------------------
 // 6. normalisation and analytic shot noise (one thread per triangle / pair)
@@ -1435,6 +1617,7 @@ struct ShellLaunch {
   int nplanes;
   const int *za, *zb, *oa, *ob;
   int nzp;
+  unsigned* fmax;   // per R field: bits of the largest |value| written (float fields), or null
 };
 
 // the three shell passes on the NS grid
@@ -1470,7 +1653,7 @@ npc_status shell_passes(npc_ctx* ctx, const ShellLaunch& sl, cplx<T>* T1, cplx<T
   auto kz = k_shell_z<T, NS>;
   NPC_CUDA(ctx, cudaFuncSetAttribute(kz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   kz<<<dim3(NS / TX, NS, sl.nzp), BCol<NS>::THREADS, smem, ctx->stream>>>(T2, sl.fields, sl.za, sl.zb, sl.oa, sl.ob,
-                                                                          tw, R);
+                                                                          tw, R, sl.nfield, sl.fmax);
   NPC_LAUNCH(ctx);
   return NPC_OK;
 }
@@ -2119,9 +2302,13 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
   T* R;
   NPC_TRY(ws_get(ctx, "bis.T1", sizeof(C) * std::max<int64_t>(o1, 1), (void**)&T1));
   NPC_TRY(ws_get(ctx, "bis.T2", sizeof(C) * std::max<int64_t>(o2, 1), (void**)&T2));
-  NPC_TRY(ws_get(ctx, "bis.R", sizeof(T) * ncs * nfield, (void**)&R));
+  // float fields chunk-interleaved (rf_index), float64 fields one row each
+  const size_t rbytes = sizeof(T) * ncs * nfield;
+  if (sizeof(T) == 4 && ncs % RCH != 0) return set_err(ctx, NPC_ERR_UNSUPPORTED, "shell grid of %lld cells", (long long)ncs);
+  NPC_TRY(ws_get(ctx, "bis.R", rbytes, (void**)&R));
   const int16_t* tab_shell;
   NPC_TRY(get_bin_table(ctx, N, m.box, kb, &tab_shell, 2));
+  unsigned* fmax_dev = nullptr;
   {
     ShellLaunch sl{};
     sl.X = X;
@@ -2149,6 +2336,12 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
     sl.oa = (const int*)(dtab + t_oa);
     sl.ob = (const int*)(dtab + t_ob);
     sl.nzp = nzp;
+    sl.fmax = nullptr;
+    if constexpr (sizeof(T) == 4) if (ctx->use_tcgen05 && !sugi) {
+      NPC_TRY(ws_get(ctx, "bis.fmax", sizeof(unsigned) * nfield, (void**)&sl.fmax));
+      NPC_CUDA(ctx, cudaMemsetAsync(sl.fmax, 0, sizeof(unsigned) * nfield, ctx->stream));
+      fmax_dev = sl.fmax;
+    }
     NPC_TRY(shell_dispatch<T>(ctx, NS, sl, T1, T2, R));
   }
   NPC_TRY(stage_mark(ctx, "shell_fields"));
@@ -2263,9 +2456,48 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
     if (want2) setup_shot(ts2, iI, -1, iS2);      // sum I_a I_b S2_c
     if (want2) setup_shot(tn2, iI2, -1, iI);      // sum I2_a I_b I_c (cached)
   }
-  // one m tile per warp (3 CTAs per SM) while the staged fields leave room for three CTAs
+  // tensor-core (tcgen05) plans of the launches with more than 32 rows, one device table for all
+  std::vector<std::pair<const TripleArgs*, TcPlanHost>> tc_plans;
+  const char* tc_tab = nullptr;
+  if constexpr (sizeof(T) == 4) {
+    if (ctx->use_tcgen05 && fmax_dev) {
+      int max_smem = 0;
+      NPC_CUDA(ctx, cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+      std::vector<char> tt;
+      auto push16 = [&](const void* q, size_t nbytes) {
+        const size_t o = tt.size();
+        tt.resize(o + (nbytes + 15) / 16 * 16);
+        if (nbytes) std::memcpy(tt.data() + o, q, nbytes);
+        return o;
+      };
+      for (const TripleArgs* a : {&ta, &tn, &ts1, &ts2, &ts3, &tn2}) {
+        TcPlanHost P;
+        if (a->nrows <= 32 || a->ncol <= 0 || !plan_triple_tc(*a, tr.pij.data(), max_smem, P)) continue;
+        P.o_rx = push16(P.rx.data(), sizeof(int16_t) * P.rx.size());
+        P.o_ry = push16(P.ry.data(), sizeof(int16_t) * P.ry.size());
+        P.o_cz = push16(P.cz.data(), sizeof(int16_t) * P.cz.size());
+        P.o_sfield = push16(P.sfield.data(), sizeof(int) * P.sfield.size());
+        P.o_runs = push16(P.runs.data(), sizeof(int) * P.runs.size());
+        P.o_gidx = push16(P.gidx.data(), sizeof(int) * P.gidx.size());
+        tc_plans.emplace_back(a, std::move(P));
+      }
+      if (!tc_plans.empty()) {
+        void* d;
+        NPC_TRY(ws_table(ctx, "bis.tcplan", tt, tt.data(), tt.size(), &d));
+        tc_tab = (const char*)d;
+      }
+    }
+  }
+  auto tc_plan_of = [&](const TripleArgs& a) -> const TcPlanHost* {
+    for (const auto& e : tc_plans)
+      if (e.first == &a) return &e.second;
+    return nullptr;
+  };
+  // one m tile per warp (3 CTAs per SM) while the staged fields leave room for three CTAs; the
+  // tensor-core path: one CTA per SM and row group
   auto tri_mt = [&](const TripleArgs& a) { return a.nstage <= 47 ? 1 : 2; };
   auto grid_for = [&](const TripleArgs& a) {
+    if (const TcPlanHost* P = tc_plan_of(a)) return std::max(1, ctx->num_sms / P->groups);
     const int mt = tri_mt(a), rows = TRI_WARPS * mt * 16;
     const int ng_ = (a.nrows + rows - 1) / rows;
     return sizeof(T) == 4 ? std::max(1, (mt == 1 ? 3 : 2) * ctx->num_sms / ng_) : ctx->num_sms * 4;
@@ -2274,24 +2506,38 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
   double* part;
   NPC_TRY(ws_get(ctx, "bis.tripart", sizeof(double) * (size_t)grid * std::max(ta.nrows, tn.nrows) * TRI_COLS,
                  (void**)&part));
-  auto launch_tab = [&](const TripleArgs& a, int grid, double* part, size_t tp, size_t trp) -> npc_status {
+  auto launch_tab = [&](const TripleArgs& a0, int grid, double* part, size_t tp, size_t trp) -> npc_status {
+    const TripleArgs& a = a0;
+    TripleArgs ak = a0;   // the mma.sync path reads the float fields through rf_index
+    ak.nfield_r = nfield;
     ctx->contraction_flops += 2.0 * a.nrows * a.ncol * (double)a.ncell;
     ctx->contraction_launches += 1;
     if constexpr (sizeof(T) == 4) {
-      if (ctx->use_tcgen05 && a.nrows > 32 && a.ncol <= tc::NCOL && a.ncell % tc::CHUNK == 0) {
-        // tensor-core (tcgen05) path: up to three 128-row tiles per CTA
-        const int nt = std::min(3, (a.nrows + 127) / 128);
-        const int groups = (a.nrows + nt * 128 - 1) / (nt * 128);
-        const int nbuf = tc_triple_smem(a.nstage, 3, nt) <= 200 * 1024 ? 3 : 2;
-        const size_t smem = tc_triple_smem(a.nstage, nbuf, nt);
+      if (const TcPlanHost* P = tc_plan_of(a)) {
+        // tensor-core (tcgen05) path, f16 hi + lo operands, orientation from the plan
+        tc::Plan kp{};
+        kp.nmrow = P->nmrow;
+        kp.nmcol = P->nmcol;
+        kp.n = P->n;
+        kp.nsa = P->nsa;
+        kp.nout = a.nrows * a.ncol;
+        kp.nstage = a.nstage;
+        kp.nrun = (int)P->runs.size() / 2;
+        kp.nfield = nfield;
+        kp.rx = (const int16_t*)(tc_tab + P->o_rx);
+        kp.ry = (const int16_t*)(tc_tab + P->o_ry);
+        kp.cz = (const int16_t*)(tc_tab + P->o_cz);
+        kp.sfield = (const int*)(tc_tab + P->o_sfield);
+        kp.runs = (const int*)(tc_tab + P->o_runs);
+        kp.gidx = (const int*)(tc_tab + P->o_gidx);
         auto go = [&](auto kern) -> npc_status {
-          NPC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-          kern<<<dim3(grid, groups), nt * 256 + 32, smem, ctx->stream>>>(
-              (const float*)R, a, (const int*)(dtab + tp), (const int*)(dtab + trp), part, ctx->dev_status,
-              wait_cycles(ctx), nbuf);
+          NPC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P->smem));
+          kern<<<dim3(grid, P->groups), P->nt * 128 * tc::PPR + (tc::NBW + 2) * 32, P->smem, ctx->stream>>>(
+              (const float*)R, a.ncell, kp, fmax_dev, part, ctx->dev_status, wait_cycles(ctx), P->nbuf);
           return NPC_OK;
         };
-        NPC_TRY(nt == 1 ? go(k_triple_tc<1>) : nt == 2 ? go(k_triple_tc<2>) : go(k_triple_tc<3>));
+        NPC_TRY(P->nt == 1 ? go(k_triple_tc<1>) : P->nt == 2 ? go(k_triple_tc<2>) : go(k_triple_tc<3>));
+        ctx->contraction_issued_flops += 2.0 * 2.0 * P->groups * P->nt * 128.0 * P->n * (double)a.ncell;
         ctx->bounded_waits = true;
         NPC_LAUNCH(ctx);
         return NPC_OK;
@@ -2303,15 +2549,18 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
                             sizeof(double) * (size_t)TRI_WARPS * 32 * mt * nt * 4;
         NPC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         kern<<<dim3(grid, groups), TRI_WARPS * 32, smem, ctx->stream>>>(
-            (const float*)R, a, (const int*)(dtab + tp), (const int*)(dtab + trp), part);
+            (const float*)R, ak, (const int*)(dtab + tp), (const int*)(dtab + trp), part);
         return NPC_OK;
       };
+      // issued: three tf32 products per useful one, on 16-row m tiles and 8-column n tiles
+      ctx->contraction_issued_flops +=
+          3.0 * 2.0 * (a.nrows <= 32 && a.ncol <= 24 ? 32 : groups * rows) * (a.ncol <= 24 ? 24 : 32) * (double)a.ncell;
       if (a.nrows <= 32 && a.ncol <= 24) {
         // few rows: all warps on the same two m tiles, each on its own cells
         const size_t smem = sizeof(float) * (size_t)a.nstage * TRI_SPAD + sizeof(double) * (size_t)TRI_WARPS * 32 * 2 * 3 * 4;
         auto kern = k_triple<3, 2, true>;
         NPC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        kern<<<dim3(grid, 1), TRI_WARPS * 32, smem, ctx->stream>>>((const float*)R, a, (const int*)(dtab + tp),
+        kern<<<dim3(grid, 1), TRI_WARPS * 32, smem, ctx->stream>>>((const float*)R, ak, (const int*)(dtab + tp),
                                                                    (const int*)(dtab + trp), part);
       } else if (a.ncol <= 24) {
         NPC_TRY(mt == 1 ? run(k_triple<3, 1>, 3) : run(k_triple<3, 2>, 3));
@@ -2320,6 +2569,7 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
       }
     } else {
       const int outs = a.nrows * a.ncol;
+      ctx->contraction_issued_flops += 2.0 * outs * (double)a.ncell;
       k_triple_f64<<<dim3(grid, (outs + 255) / 256), 256, 0, ctx->stream>>>((const double*)R, a,
                                                                              (const int*)(dtab + tp), part);
       (void)trp;

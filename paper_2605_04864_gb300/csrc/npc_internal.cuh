@@ -168,6 +168,7 @@ struct npc_ctx {
   int launches = 0;
   double contraction_flops = 0.0;   // dense triple-product work of the current call
   int contraction_launches = 0;
+  double contraction_issued_flops = 0.0;   // the same work as the tensor cores issue it (padding, split parts)
   // device status word written by kernels whose waits are bounded (0 = fine, else an npc_status),
   // the wait bound they are given (clock cycles) and whether the current call launched one
   int* dev_status = nullptr;

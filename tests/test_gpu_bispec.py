@@ -255,18 +255,29 @@ def test_bispectrum_rejects(api):
 
 
 def test_tensor_core_paths_agree(api):
-    """The tcgen05 triple products (tf32 hi + lo split, TMEM accumulators) against the warp-level
-    mma.sync path on the same shell fields: both carry about 21 bits per product, so they agree
-    far inside the 1e-4 bispectrum tolerance; N_T (integer counts) is identical."""
+    """The tcgen05 triple products (f16 hi + lo split after exact power-of-two scales, TMEM
+    accumulators) against the warp-level mma.sync path (tf32 hi + lo) on the same shell fields:
+    both carry about 21 bits per product, so they agree far inside the 1e-4 bispectrum tolerance;
+    N_T (integer counts) is identical.  The statistics show which path ran: the tcgen05 path issues
+    two f16 products per k step (hi and lo rows against interleaved hi and lo columns), mma.sync three
+    tf32 products."""
     cat = make_periodic_catalog(60000, 600.0, 32, seed=45)
     kf = 2 * np.pi / 600.0
     kb = (2 * kf, 1.5 * kf, 7)
+    api.bispectrum(cat, n=64, box=600.0, kbins=kb, precision="mixed")   # N_T counted and cached here
     a = api.bispectrum(cat, n=64, box=600.0, kbins=kb, precision="mixed")
+    st_a = api.last_stats()
     try:
         api.set_option("tcgen05_triple", 0)
         b = api.bispectrum(cat, n=64, box=600.0, kbins=kb, precision="mixed")
+        st_b = api.last_stats()
     finally:
         api.set_option("tcgen05_triple", 1)
+    assert st_a["contraction_launches"] >= 1 and st_a["contraction_flops"] == st_b["contraction_flops"]
+    # 7 bins: 56 rows x 9 columns of B_0, B_2, B_000, B_202; the tcgen05 plan puts the 14 single
+    # fields F_0,i, F_2,i on the N side (N = 32) against the 28 products F_0,j F_0,k and the 14
+    # products F_0,j G (one 128-row tile)
+    assert st_a["contraction_issued_flops"] != st_b["contraction_issued_flops"]
     np.testing.assert_array_equal(a["NT"], b["NT"])
     scale = np.abs(b["B"][0] + b["shot_B"][0]) + np.abs(b["shot_B"][0])
     for l in (0, 2):
