@@ -122,7 +122,10 @@ npc_status npc_last_stats(npc_ctx* ctx, npc_stats* out);
  * whose waits on other threads of their block are bounded (the tensor-core triple products of
  * npc_bispectrum) record NPC_ERR_TIMEOUT in a device word of the context when a wait gives up; the
  * block then waits (with a fixed bound) for its copies and products in flight, frees its tensor
- * memory and exits, so the context stays usable.  Calls that return host output check the word
+ * memory and exits, so the context stays usable.  The same word records NPC_ERR_NUMERIC when a
+ * shell field's largest |value| lies outside [2^-57, 2^63) (other than an all-zero field): the
+ * tensor-core path scales its f16 operands by powers of two taken from those maxima, and outside
+ * that range they would overflow or lose precision (the mma.sync path has no such limit).  Calls that return host output check the word
  * themselves and return its code; after calls with device output, npc_device_status synchronises
  * the context's stream, returns the recorded code (NPC_OK if none) and clears it. */
 npc_status npc_device_status(npc_ctx* ctx);
@@ -131,7 +134,9 @@ npc_status npc_device_status(npc_ctx* ctx);
  * NPC_ERR_TIMEOUT path without any fault. */
 npc_status npc_set_wait_limit(npc_ctx* ctx, long long cycles);
 /* Implementation switches for comparison runs: "tcgen05_triple" (default 1) selects the tcgen05
- * tensor-core path of the bispectrum triple products; 0 selects the warp-level mma.sync path. */
+ * tensor-core path of the bispectrum triple products (f16 hi + lo operands after exact
+ * power-of-two scales, float32 accumulation in tensor memory, launches of more than 32 rows);
+ * 0 selects the warp-level mma.sync path (tf32 hi + lo). */
 npc_status npc_set_option(npc_ctx* ctx, const char* name, int64_t value);
 /* Current value of an option: "tcgen05_triple" as above (npc_batch_tune sets it to the faster path
  * for the batch it times), "batch_branches" (0: not tuned). */

@@ -305,6 +305,11 @@ npc_status check_device_status(npc_ctx* ctx) {
   ctx->host_cache_keys.clear();
   NPC_CUDA(ctx, cudaMemsetAsync(ctx->dev_status, 0, sizeof(int), ctx->stream));
   NPC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (word == NPC_ERR_NUMERIC)
+    return set_err(ctx, NPC_ERR_NUMERIC,
+                   "a shell field's largest |value| lies outside [2^-57, 2^63), the range of the f16 tensor-core "
+                   "triple products (results of that call are invalid; npc_set_option(\"tcgen05_triple\", 0) "
+                   "selects the tf32 mma.sync path)");
   return set_err(ctx, (npc_status)word, "a bounded device-side wait gave up (results of that call are invalid)");
 }
 

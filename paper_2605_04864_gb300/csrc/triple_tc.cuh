@@ -417,22 +417,30 @@ k_triple_tc(const float* __restrict__ R, int64_t ncell, const __grid_constant__ 
     __syncwarp();
   } else if (warp >= bw0) {
     // ---- operand warps: hi and lo of every column, interleaved (rows 2w, 2w + 1 of the N side);
-    //      unit u = (column w, 8-cell group g of the stage): one 16-byte row of hi and one of lo ----
+    //      unit u = (column w, 8-cell group g of the stage): one 16-byte row of hi and one of lo.
+    //      A row's bank group is its index mod 8 (every other stride of the layout is a multiple of
+    //      128 bytes), so lanes 2i and 2i + 1 take the same column (groups 2q, 2q + 1), a quarter
+    //      warp four consecutive columns, and the odd lane of a pair stores its lo row first: the
+    //      eight rows of each store fall on eight bank groups ----
     const int tb = tid - bw0 * 32;
     constexpr int GPS = AST / 8;                      // 8-cell groups per stage
     const int nunit = P.nmcol * GPS;
     constexpr int UPT = (MAXN / 2 * GPS + NBW * 32 - 1) / (NBW * 32);   // units per thread at most
-    int srow[UPT], scell[UPT], dhi[UPT], dlo[UPT];
+    int srow[UPT], scell[UPT], d1[UPT], d2[UPT];
     float fsc[UPT];
+    const bool lo_first = (tb & 1) != 0;
 #pragma unroll
     for (int k = 0; k < UPT; ++k) {
       const int u = tb + k * NBW * 32;
-      const int w = u / GPS, g = u % GPS, j = g >> 1, kh = g & 1;
+      const int pr = u >> 1;
+      const int w = pr % P.nmcol, g = 2 * (pr / P.nmcol) + (u & 1), j = g >> 1, kh = g & 1;
       srow[k] = u < nunit ? col_s[w] * SROW : 0;
       scell[k] = 8 * g + (u < nunit ? rf_rot(P.sfield[col_s[w]]) : 0);   // rotated cell of the unit's first cell
       fsc[k] = u < nunit ? exp2f_int(14 - col_e[w]) : 0.f;
-      dhi[k] = j * N * 32 + ((2 * w) >> 3) * 256 + kh * 128 + ((2 * w) & 7) * 16;
-      dlo[k] = j * N * 32 + ((2 * w + 1) >> 3) * 256 + kh * 128 + ((2 * w + 1) & 7) * 16;
+      const int dhi = j * N * 32 + ((2 * w) >> 3) * 256 + kh * 128 + ((2 * w) & 7) * 16;
+      const int dlo = j * N * 32 + ((2 * w + 1) >> 3) * 256 + kh * 128 + ((2 * w + 1) & 7) * 16;
+      d1[k] = lo_first ? dlo : dhi;
+      d2[k] = lo_first ? dhi : dlo;
     }
     for (int s = 0; s < nst; ++s) {
       const int slot = s % NSA;
@@ -454,8 +462,8 @@ k_triple_tc(const float* __restrict__ R, int64_t ncell, const __grid_constant__ 
           split_f16x2(a0.z * f, a0.w * f, hi.y, lo.y);
           split_f16x2(a1.x * f, a1.y * f, hi.z, lo.z);
           split_f16x2(a1.z * f, a1.w * f, hi.w, lo.w);
-          *reinterpret_cast<uint4*>(bslot + dhi[k]) = hi;
-          *reinterpret_cast<uint4*>(bslot + dlo[k]) = lo;
+          *reinterpret_cast<uint4*>(bslot + d1[k]) = lo_first ? lo : hi;
+          *reinterpret_cast<uint4*>(bslot + d2[k]) = lo_first ? hi : lo;
         }
       }
       fence_async_smem();
