@@ -280,8 +280,55 @@ __device__ __forceinline__ void std_inputs(cplx<T> (&v)[8], const T* tileA, cons
   }
 }
 
+// The real column signal of the (L, M > 0) fields of mesh phase PH: Y_LM(xhat) = norm Q_LM(uz)
+// ((px + i py)/r)^M splits into s(z) = mesh(z) Q_LM(uz) r^-M, real, and the column factor
+// cr + i ci = norm (px + i py)^M, constant along z; the transforms of the fields' real and imaginary
+// parts are cr S(kz) and ci S(kz), S the transform of s.
+template <typename T, int N, int TX, int L, int M, int PH>
+__device__ __forceinline__ void std_real(T (&sv)[8], T& cr, T& ci, const T* tile, int c, int t, const ZGeom<T>& zg,
+                                         const YNorm& nrm) {
+  constexpr int TPF = N / 8;
+  cr = ynorm<T>(nrm, L * (L + 1) / 2 + M);
+  ci = T(0);
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+    const T nr = cr * zg.px[PH] - ci * zg.py[PH];
+    ci = cr * zg.py[PH] + ci * zg.px[PH];
+    cr = nr;
+  }
+  keep_here(cr);
+  keep_here(ci);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int z = t + q * TPF;
+    const T pz = zg.pz0[PH] + T(q) * zg.dz;
+    const T inv = rsqrt(zg.pxy2[PH] + pz * pz);
+    T v = tile[z * TX + c] * ylm_q<T, L, M>(pz * inv);
+#pragma unroll
+    for (int j = 0; j < M; ++j) v *= inv;
+    sv[q] = v;
+  }
+}
+
+// Phases a and b of one (L, M > 0): s_a + i s_b in one complex transform (two real signals), then
+// S_a(k) = (Z(k) + Z(N - k)^*) / 2 and S_b(k) = (Z(k) - Z(N - k)^*) / 2i give the four half spectra.
+template <typename T, int N, int TX, int L, int M>
+__device__ __forceinline__ void std_pair_ab(cplx<T> (&v)[8], T (&cf)[4], const T* tileA, const T* tileB, int c, int t,
+                                            const ZGeom<T>& zg, const YNorm& nrm) {
+  T sa[8], sb[8];
+  std_real<T, N, TX, L, M, 0>(sa, cf[0], cf[1], tileA, c, t, zg, nrm);
+  std_real<T, N, TX, L, M, 1>(sb, cf[2], cf[3], tileB, c, t, zg, nrm);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) v[q] = cmk(sa[q], sb[q]);
+}
+
+// float: the occupancy of the form without packed phase pairs (64 registers at 512 threads, at most
+// 80 otherwise), so that the pairs' extra live values do not cost CTAs per SM
+template <typename T, int N> constexpr int zstd_min_blocks() {
+  return sizeof(T) == 4 ? 65536 / (ColCfg<N>::THREADS * (ColCfg<N>::THREADS == 512 ? 64 : 80)) : 1;
+}
 template <typename T, int N>
-__global__ void __launch_bounds__(ColCfg<N>::THREADS)
+__global__ void __launch_bounds__(ColCfg<N>::THREADS, zstd_min_blocks<T, N>())
 k_fwd_z_std(const T* __restrict__ mesh_a, const T* __restrict__ mesh_b, cplx<T>* __restrict__ half, int npairs,
             const Geom g, const YNorm nrm, const cplx<T>* __restrict__ tw_g, int KZ) {
   using C = cplx<T>;
@@ -315,6 +362,43 @@ k_fwd_z_std(const T* __restrict__ mesh_a, const T* __restrict__ mesh_b, cplx<T>*
   const size_t fstride = (size_t)KZ * N * N;
   for (int p = 0; p < npairs; ++p) {
     C v[8];
+    // pairs 2k and 2k + 1 of an m > 0 harmonic (phase a, phase b): one transform for both
+    const bool ab = (p == 2 || p == 4 || p == 7 || p == 9 || p == 11 || p == 13) && p + 1 < npairs;
+    if (ab) {
+      T cf[4];   // cr, ci of phase a, then of phase b
+      switch (p) {
+        case 2: std_pair_ab<T, N, TX, 2, 1>(v, cf, tileA, tileB, c, t, zg, nrm); break;
+        case 4: std_pair_ab<T, N, TX, 2, 2>(v, cf, tileA, tileB, c, t, zg, nrm); break;
+        case 7: std_pair_ab<T, N, TX, 4, 1>(v, cf, tileA, tileB, c, t, zg, nrm); break;
+        case 9: std_pair_ab<T, N, TX, 4, 2>(v, cf, tileA, tileB, c, t, zg, nrm); break;
+        case 11: std_pair_ab<T, N, TX, 4, 3>(v, cf, tileA, tileB, c, t, zg, nrm); break;
+        default: std_pair_ab<T, N, TX, 4, 4>(v, cf, tileA, tileB, c, t, zg, nrm); break;
+      }
+      fft_block<N, -1>(v, t, tw, ColView<C>{work + c, TX});
+#pragma unroll
+      for (int q = 0; q < 8; ++q) work[(t + q * TPF) * TX + c] = v[q];
+      __syncthreads();
+      {
+        // thread tid owns (kz0 + j KZSTEP, cc) with cc = tid % TX = c: its column's factors
+        constexpr int KZSTEP = ColCfg<N>::THREADS / TX;
+        const int kz0 = tid / TX, cc = tid % TX;
+        C* o0 = half + (size_t)(2 * p) * fstride + ((size_t)kz0 * N + y) * N + x0 + cc;
+        for (int kz = kz0; kz < KZ; kz += KZSTEP, o0 += (size_t)KZSTEP * N * N) {
+          const C z1 = work[kz * TX + cc];
+          const C z2 = cconj(work[(kz == 0 ? 0 : N - kz) * TX + cc]);
+          const C sa = cscale(cadd(z1, z2), T(0.5));
+          const C d = csub(z1, z2);
+          const C sb = cmk(T(0.5) * d.y, T(-0.5) * d.x);
+          o0[0] = cscale(sa, cf[0]);
+          o0[fstride] = cscale(sa, cf[1]);
+          o0[2 * fstride] = cscale(sb, cf[2]);
+          o0[3 * fstride] = cscale(sb, cf[3]);
+        }
+      }
+      __syncthreads();
+      ++p;
+      continue;
+    }
     switch (p) {
       case 0: std_inputs<T, N, TX, 0, 0, 0>(v, tileA, tileB, c, t, zg, nrm); break;
       case 1: std_inputs<T, N, TX, 2, 0, 0>(v, tileA, tileB, c, t, zg, nrm); break;
