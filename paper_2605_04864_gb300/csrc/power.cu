@@ -701,91 +701,100 @@ k_fft_x_contract(const cplx<T>* __restrict__ half, const ContractParams P, const
     }
     __syncthreads();
     const T fjy = T(jy), fkz = T(kz);
-    for (int jb = warp * 32; jb < N; jb += blockDim.x) {
-      const int j = jb + lane;
-      const int i = j < N / 2 ? j : j - N;
+    // modes kx = jp and kx = -jp (index N - jp) have the same |k|, hence the same bin: a thread adds
+    // both before the warp-segmented scan (one scan and one set of run-end atomics per pair)
+    for (int jb = warp * 32; jb < N / 2; jb += blockDim.x) {
+      const int jp = jb + lane;
       int bin = -1;
-      if (j < N && i != -N / 2 && jy != -N / 2 && (i != 0 || jy != 0 || kz != 0)) bin = bintab[i * i + jy * jy + kz * kz];
       T vals[MAX_SUMS];
 #pragma unroll
       for (int s = 0; s < MAX_SUMS; ++s) vals[s] = T(0);
-      if (bin >= 0) {
-        const T wgt = kz > 0 ? T(2) : T(1);
-        // accumulators summed over the groups: phase a (even g, or all with one phase) and phase b
-        C Aa[6], Ab[6];
+#pragma unroll 1
+      for (int mir = 0; mir < 2; ++mir) {
+        const int j = mir ? N - jp : jp;
+        const int i = mir ? -jp : jp;
+        int mbin = -1;
+        if (jp < N / 2 && (mir == 0 || jp > 0) && jy != -N / 2 && (i != 0 || jy != 0 || kz != 0))
+          mbin = bintab[i * i + jy * jy + kz * kz];
+        if (mbin >= 0) {
+          bin = mbin;
+          const T wgt = kz > 0 ? T(2) : T(1);
+          // accumulators summed over the groups: phase a (even g, or all with one phase) and phase b
+          C Aa[6], Ab[6];
 #pragma unroll
-        for (int a = 0; a < 6; ++a) Aa[a] = Ab[a] = cmk(T(0), T(0));
-        auto gsum = [&](int g0, int gstep, C (&acc)[6]) {
-          for (int gg = g0; gg < G; gg += gstep) {
-            const C* fg = facc + (size_t)gg * P.nacc * N + j;
+          for (int a = 0; a < 6; ++a) Aa[a] = Ab[a] = cmk(T(0), T(0));
+          auto gsum = [&](int g0, int gstep, C (&acc)[6]) {
+            for (int gg = g0; gg < G; gg += gstep) {
+              const C* fg = facc + (size_t)gg * P.nacc * N + j;
+#pragma unroll
+              for (int a = 0; a < 6; ++a)
+                if (a < P.nacc) acc[a] = cadd(acc[a], fg[(size_t)a * N]);
+            }
+          };
+          if (P.phase_pure) {
+            gsum(0, P.nphase == 2 ? 2 : 1, Aa);
+            const T faj = fa[j];
+#pragma unroll
+            for (int a = 0; a < 6; ++a) Aa[a] = cscale(Aa[a], faj);
+            if (P.nphase == 2) {
+              gsum(1, 2, Ab);
+              const C fbj = fb[j];
+#pragma unroll
+              for (int a = 0; a < 6; ++a) Aa[a] = cadd(Aa[a], cmul(Ab[a], fbj));
+            }
+          } else {
+            gsum(0, 1, Aa);
+          }
+          auto pick = [&](int k) {   // accumulator k (runtime index kept out of local memory)
+            C r = cmk(T(0), T(0));
 #pragma unroll
             for (int a = 0; a < 6; ++a)
-              if (a < P.nacc) acc[a] = cadd(acc[a], fg[(size_t)a * N]);
+              if (k == a) r = Aa[a];
+            return r;
+          };
+          const C F0 = Aa[0];
+          C F1, F2, F3, F4, FA;
+          if (P.even_layout) {   // accumulators F_0, F_2, F_4 (when present) at 0, 1, 2, then F_0^A
+            F1 = F3 = cmk(T(0), T(0));
+            F2 = Aa[1];
+            F4 = Aa[2];
+            FA = P.acc_a == 1 ? Aa[1] : (P.acc_a == 2 ? Aa[2] : Aa[3]);
+          } else {
+            F1 = pick(P.acc_of[1]);
+            F2 = pick(P.acc_of[2]);
+            F3 = pick(P.acc_of[3]);
+            F4 = pick(P.acc_of[4]);
+            FA = pick(P.acc_a);
           }
-        };
-        if (P.phase_pure) {
-          gsum(0, P.nphase == 2 ? 2 : 1, Aa);
-          const T faj = fa[j];
-#pragma unroll
-          for (int a = 0; a < 6; ++a) Aa[a] = cscale(Aa[a], faj);
-          if (P.nphase == 2) {
-            gsum(1, 2, Ab);
-            const C fbj = fb[j];
-#pragma unroll
-            for (int a = 0; a < 6; ++a) Aa[a] = cadd(Aa[a], cmul(Ab[a], fbj));
+          const T fi = T(i);
+          const T kk = sqrt(fi * fi + fjy * fjy + fkz * fkz);
+          if (P.global_los) {
+            const T mu = (fi * T(P.los[0]) + fjy * T(P.los[1]) + fkz * T(P.los[2])) / kk;
+            if (P.need_mask & 2) F1 = cscale(F0, legendre_p<T>(1, mu));
+            if (P.need_mask & 4) F2 = cscale(F0, legendre_p<T>(2, mu));
+            if (P.need_mask & 8) F3 = cscale(F0, legendre_p<T>(3, mu));
+            if (P.need_mask & 16) F4 = cscale(F0, legendre_p<T>(4, mu));
           }
-        } else {
-          gsum(0, 1, Aa);
-        }
-        auto pick = [&](int k) {   // accumulator k (runtime index kept out of local memory)
-          C r = cmk(T(0), T(0));
+          auto sel = [&](int l) { return l == 0 ? F0 : (l == 1 ? F1 : (l == 2 ? F2 : (l == 3 ? F3 : F4))); };
 #pragma unroll
-          for (int a = 0; a < 6; ++a)
-            if (k == a) r = Aa[a];
-          return r;
-        };
-        const C F0 = Aa[0];
-        C F1, F2, F3, F4, FA;
-        if (P.even_layout) {   // accumulators F_0, F_2, F_4 (when present) at 0, 1, 2, then F_0^A
-          F1 = F3 = cmk(T(0), T(0));
-          F2 = Aa[1];
-          F4 = Aa[2];
-          FA = P.acc_a == 1 ? Aa[1] : (P.acc_a == 2 ? Aa[2] : Aa[3]);
-        } else {
-          F1 = pick(P.acc_of[1]);
-          F2 = pick(P.acc_of[2]);
-          F3 = pick(P.acc_of[3]);
-          F4 = pick(P.acc_of[4]);
-          FA = pick(P.acc_a);
-        }
-        const T fi = T(i);
-        const T kk = sqrt(fi * fi + fjy * fjy + fkz * fkz);
-        if (P.global_los) {
-          const T mu = (fi * T(P.los[0]) + fjy * T(P.los[1]) + fkz * T(P.los[2])) / kk;
-          if (P.need_mask & 2) F1 = cscale(F0, legendre_p<T>(1, mu));
-          if (P.need_mask & 4) F2 = cscale(F0, legendre_p<T>(2, mu));
-          if (P.need_mask & 8) F3 = cscale(F0, legendre_p<T>(3, mu));
-          if (P.need_mask & 16) F4 = cscale(F0, legendre_p<T>(4, mu));
-        }
-        auto sel = [&](int l) { return l == 0 ? F0 : (l == 1 ? F1 : (l == 2 ? F2 : (l == 3 ? F3 : F4))); };
-#pragma unroll
-        for (int s = 0; s < MAX_SUMS; ++s) {
-          T v = T(0);
-          if (s < P.nell) {
-            const int l = P.ell_list[s];
-            const C b = sel(l);
-            const C a = P.acc_a >= 0 ? FA : F0;   // cross: F_0 of tracer A against F_l of B
-            // even l: Re a b^*; odd l: Im a b^* (Sec. 2.1, odd multipoles)
-            v = wgt * ((l & 1) ? (a.y * b.x - a.x * b.y) : (a.x * b.x + a.y * b.y));
-          } else if (s < P.nell + P.nll) {
-            const C a = sel(P.lla[s - P.nell]), b = sel(P.llb[s - P.nell]);
-            v = wgt * (a.x * b.x + a.y * b.y);
-          } else if (s == P.nsum - 2) {
-            v = wgt;
-          } else if (s == P.nsum - 1) {
-            v = wgt * T(P.kf) * kk;
+          for (int s = 0; s < MAX_SUMS; ++s) {
+            T v = T(0);
+            if (s < P.nell) {
+              const int l = P.ell_list[s];
+              const C b = sel(l);
+              const C a = P.acc_a >= 0 ? FA : F0;   // cross: F_0 of tracer A against F_l of B
+              // even l: Re a b^*; odd l: Im a b^* (Sec. 2.1, odd multipoles)
+              v = wgt * ((l & 1) ? (a.y * b.x - a.x * b.y) : (a.x * b.x + a.y * b.y));
+            } else if (s < P.nell + P.nll) {
+              const C a = sel(P.lla[s - P.nell]), b = sel(P.llb[s - P.nell]);
+              v = wgt * (a.x * b.x + a.y * b.y);
+            } else if (s == P.nsum - 2) {
+              v = wgt;
+            } else if (s == P.nsum - 1) {
+              v = wgt * T(P.kf) * kk;
+            }
+            vals[s] += v;
           }
-          vals[s] = v;
         }
       }
       // warp-segmented inclusive scan over runs of consecutive lanes with equal bin; a run is
