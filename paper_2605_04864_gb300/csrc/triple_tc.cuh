@@ -242,6 +242,19 @@ __device__ __forceinline__ void split_f16x2(float v0, float v1, uint32_t& hi, ui
 __device__ __forceinline__ float exp2f_int(int e) { return __int_as_float((127 + e) << 23); }      // e in [-126, 127]
 __device__ __forceinline__ double exp2d_int(int e) { return __longlong_as_double((long long)(1023 + e) << 52); }
 
+// Position in a ring of `n` slots and the parity of the slot's current use (slot = i mod n,
+// parity = (i / n) mod 2 for the i-th use), advanced without divisions.
+struct Ring {
+  int slot = 0;
+  uint32_t par = 0;
+  __device__ __forceinline__ void next(int n) {
+    if (++slot == n) {
+      slot = 0;
+      par ^= 1u;
+    }
+  }
+};
+
 struct Smem {
   uint64_t full_tma[3];       // chunk buffer filled (transaction count)
   uint64_t chunk_free[3];     // chunk buffer read by every producer and operand warp
@@ -369,9 +382,10 @@ k_triple_tc(const float* __restrict__ R, int64_t ncell, const __grid_constant__ 
     if (lane == 0) {
       const uint32_t bytes = (uint32_t)(P.nstage * RCH * sizeof(float));
       int issued = 0;
-      for (int c = 0; c < nchunk; ++c) {
-        const int b = c % nbuf;
-        if (c >= nbuf && !mbar_wait(&sm->chunk_free[b], (uint32_t)((c / nbuf - 1) & 1), limit, abort, status)) break;
+      Ring bf;
+      for (int c = 0; c < nchunk; ++c, bf.next(nbuf)) {
+        const int b = bf.slot;
+        if (c >= nbuf && !mbar_wait(&sm->chunk_free[b], bf.par ^ 1u, limit, abort, status)) break;
         mbar_arrive_tx(&sm->full_tma[b], bytes);
         const size_t gchunk = (size_t)(c_beg + c);
         for (int r = 0; r < P.nrun; ++r) {
@@ -392,9 +406,10 @@ k_triple_tc(const float* __restrict__ R, int64_t ncell, const __grid_constant__ 
       const uint32_t idesc = idesc_f16(N);
       const uint64_t bd0 = sdesc(smem_u32(btile), 128, 256);
       const uint32_t bstep = (uint32_t)(N * 32) >> 4;   // one k step of the operand, in descriptor units
-      for (int s = 0; s < nst; ++s) {
-        const int slot = s % NSA;
-        if (!mbar_wait(&sm->full_a[slot], (uint32_t)((s / NSA) & 1), limit, abort, status)) break;
+      Ring st;
+      for (int s = 0; s < nst; ++s, st.next(NSA)) {
+        const int slot = st.slot;
+        if (!mbar_wait(&sm->full_a[slot], st.par, limit, abort, status)) break;
         tc_fence_after();
         const bool fresh = (s % FLUSH) == 0;
 #pragma unroll
@@ -442,13 +457,13 @@ k_triple_tc(const float* __restrict__ R, int64_t ncell, const __grid_constant__ 
       d1[k] = lo_first ? dlo : dhi;
       d2[k] = lo_first ? dhi : dlo;
     }
-    for (int s = 0; s < nst; ++s) {
-      const int slot = s % NSA;
-      const int c = s / SPC;
+    Ring st, bf;   // stage slot; chunk buffer (advanced after the chunk's last stage)
+    for (int s = 0; s < nst; ++s, st.next(NSA)) {
+      const int slot = st.slot;
       const int o = (s % SPC) * AST;
-      const int b = c % nbuf;
-      if ((s % SPC) == 0 && !warp_wait(&sm->full_tma[b], (uint32_t)((c / nbuf) & 1), limit, abort, status)) break;
-      if (s >= NSA && !warp_wait(&sm->empty_a[slot], (uint32_t)(((s - NSA) / NSA) & 1), limit, abort, status)) break;
+      const int b = bf.slot;
+      if ((s % SPC) == 0 && !warp_wait(&sm->full_tma[b], bf.par, limit, abort, status)) break;
+      if (s >= NSA && !warp_wait(&sm->empty_a[slot], st.par ^ 1u, limit, abort, status)) break;
       const float* stage = buf + (size_t)b * P.nstage * SROW;
       unsigned char* bslot = btile + (size_t)slot * KSTEPS * N * 32;
 #pragma unroll
@@ -472,6 +487,7 @@ k_triple_tc(const float* __restrict__ R, int64_t ncell, const __grid_constant__ 
         mbar_arrive(&sm->full_a[slot]);
         if ((s % SPC) == SPC - 1) mbar_arrive(&sm->chunk_free[b]);
       }
+      if ((s % SPC) == SPC - 1) bf.next(nbuf);
     }
   } else {
     // ---- producers: two threads per product row ----
@@ -490,14 +506,13 @@ k_triple_tc(const float* __restrict__ R, int64_t ncell, const __grid_constant__ 
     }
     if (h == 0) row_e[lrow] = eu;
     const uint32_t lane_addr = tbase + ((uint32_t)(q * 32) << 16);
-    for (int s = 0; s < nst; ++s) {
-      const int slot = s % NSA;
-      const int c = s / SPC;
+    Ring st, bf;   // stage slot; chunk buffer (advanced after the chunk's last stage)
+    for (int s = 0; s < nst; ++s, st.next(NSA)) {
+      const int slot = st.slot;
       const int o = (s % SPC) * AST;
-      const int b = c % nbuf;
-      if ((s % SPC) == 0 && !warp_wait(&sm->full_tma[b], (uint32_t)((c / nbuf) & 1), limit, abort, status))
-        break;
-      if (s >= NSA && !warp_wait(&sm->empty_a[slot], (uint32_t)(((s - NSA) / NSA) & 1), limit, abort, status)) break;
+      const int b = bf.slot;
+      if ((s % SPC) == 0 && !warp_wait(&sm->full_tma[b], bf.par, limit, abort, status)) break;
+      if (s >= NSA && !warp_wait(&sm->empty_a[slot], st.par ^ 1u, limit, abort, status)) break;
       tc_fence_after();
       const float* stage = buf + (size_t)b * P.nstage * SROW;
 #pragma unroll
@@ -530,8 +545,9 @@ k_triple_tc(const float* __restrict__ R, int64_t ncell, const __grid_constant__ 
         mbar_arrive(&sm->full_a[slot]);
         if ((s % SPC) == SPC - 1) mbar_arrive(&sm->chunk_free[b]);
       }
+      if ((s % SPC) == SPC - 1) bf.next(nbuf);
       if ((s % FLUSH) == FLUSH - 1 || s == nst - 1) {
-        if (!warp_wait(&sm->empty_a[slot], (uint32_t)((s / NSA) & 1), limit, abort, status)) break;
+        if (!warp_wait(&sm->empty_a[slot], st.par, limit, abort, status)) break;
         tc_fence_after();
         // this thread's share of the row's accumulators: columns [h N / PPR, (h + 1) N / PPR), pairs (hi, lo)
         for (int c8 = h * (N / PPR); c8 < (h + 1) * (N / PPR); c8 += 8) {
