@@ -701,21 +701,24 @@ k_fft_x_contract(const cplx<T>* __restrict__ half, const ContractParams P, const
     }
     __syncthreads();
     const T fjy = T(jy), fkz = T(kz);
-    // modes kx = jp and kx = -jp (index N - jp) have the same |k|, hence the same bin: a thread adds
-    // both before the warp-segmented scan (one scan and one set of run-end atomics per pair)
-    for (int jb = warp * 32; jb < N / 2; jb += blockDim.x) {
+    // modes kx = jp and kx = -jp (index N - jp) have the same |k|, hence the same bin: where a thread
+    // would bin two or more modes, it adds the mirror pair before the warp-segmented scan (one scan
+    // and one set of run-end atomics per pair); smaller rows keep one mode per thread
+    constexpr bool MIRROR = N >= 2 * CONTRACT_THREADS;
+    constexpr int NJ = MIRROR ? N / 2 : N;
+    for (int jb = warp * 32; jb < NJ; jb += blockDim.x) {
       const int jp = jb + lane;
       int bin = -1;
       T vals[MAX_SUMS];
 #pragma unroll
       for (int s = 0; s < MAX_SUMS; ++s) vals[s] = T(0);
 #pragma unroll 1
-      for (int mir = 0; mir < 2; ++mir) {
-        const int j = mir ? N - jp : jp;
-        const int i = mir ? -jp : jp;
+      for (int mir = 0; mir < (MIRROR ? 2 : 1); ++mir) {
+        const int j = MIRROR ? (mir ? N - jp : jp) : jp;
+        const int i = MIRROR ? (mir ? -jp : jp) : (jp < N / 2 ? jp : jp - N);
+        const bool in_row = MIRROR ? (jp < N / 2 && (mir == 0 || jp > 0)) : (jp < N && i != -N / 2);
         int mbin = -1;
-        if (jp < N / 2 && (mir == 0 || jp > 0) && jy != -N / 2 && (i != 0 || jy != 0 || kz != 0))
-          mbin = bintab[i * i + jy * jy + kz * kz];
+        if (in_row && jy != -N / 2 && (i != 0 || jy != 0 || kz != 0)) mbin = bintab[i * i + jy * jy + kz * kz];
         if (mbin >= 0) {
           bin = mbin;
           const T wgt = kz > 0 ? T(2) : T(1);

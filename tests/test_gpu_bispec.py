@@ -264,15 +264,17 @@ def test_tensor_core_paths_agree(api):
     cat = make_periodic_catalog(60000, 600.0, 32, seed=45)
     kf = 2 * np.pi / 600.0
     kb = (2 * kf, 1.5 * kf, 7)
-    api.bispectrum(cat, n=64, box=600.0, kbins=kb, precision="mixed")   # N_T counted and cached here
-    a = api.bispectrum(cat, n=64, box=600.0, kbins=kb, precision="mixed")
-    st_a = api.last_stats()
+    path = api.get_option("tcgen05_triple")
     try:
+        api.set_option("tcgen05_triple", 1)
+        api.bispectrum(cat, n=64, box=600.0, kbins=kb, precision="mixed")   # N_T counted and cached here
+        a = api.bispectrum(cat, n=64, box=600.0, kbins=kb, precision="mixed")
+        st_a = api.last_stats()
         api.set_option("tcgen05_triple", 0)
         b = api.bispectrum(cat, n=64, box=600.0, kbins=kb, precision="mixed")
         st_b = api.last_stats()
     finally:
-        api.set_option("tcgen05_triple", 1)
+        api.set_option("tcgen05_triple", path)
     assert st_a["contraction_launches"] >= 1 and st_a["contraction_flops"] == st_b["contraction_flops"]
     # 7 bins: 56 rows x 9 columns of B_0, B_2, B_000, B_202; the tcgen05 plan puts the 14 single
     # fields F_0,i, F_2,i on the N side (N = 32) against the 28 products F_0,j F_0,k and the 14
@@ -295,16 +297,21 @@ def test_bounded_wait_timeout_is_reported_and_the_context_recovers(api):
 
     cat = make_periodic_catalog(30000, 400.0, 32, seed=47)
     kb = (0.02, 0.02, 6)
-    ref = api.bispectrum(cat, n=64, box=400.0, kbins=kb, precision="mixed")
+    path = api.get_option("tcgen05_triple")
+    api.set_option("tcgen05_triple", 1)   # the bounded waits are the tensor-core kernel's
     try:
-        api.set_wait_limit(1)
-        with pytest.raises(B.NpcError) as ei:
-            api.bispectrum(cat, n=64, box=400.0, kbins=kb, precision="mixed")
-        assert ei.value.status == 5
+        ref = api.bispectrum(cat, n=64, box=400.0, kbins=kb, precision="mixed")
+        try:
+            api.set_wait_limit(1)
+            with pytest.raises(B.NpcError) as ei:
+                api.bispectrum(cat, n=64, box=400.0, kbins=kb, precision="mixed")
+            assert ei.value.status == 5
+        finally:
+            api.set_wait_limit(0)
+        api.device_status()
+        again = api.bispectrum(cat, n=64, box=400.0, kbins=kb, precision="mixed")
     finally:
-        api.set_wait_limit(0)
-    api.device_status()
-    again = api.bispectrum(cat, n=64, box=400.0, kbins=kb, precision="mixed")
+        api.set_option("tcgen05_triple", path)
     for l in (0, 2):
         np.testing.assert_array_equal(again["B"][l], ref["B"][l])
     np.testing.assert_array_equal(again["NT"], ref["NT"])
