@@ -1010,9 +1010,16 @@ bool plan_triple_tc(const TripleArgs& a, const int* pij, int max_smem, TcPlanHos
     const int n = std::max(16, (2 * nc + 15) / 16 * 16);
     if (n > tc::MAXN) continue;
     const int tiles = (nr + 127) / 128;
-    const int groups = (tiles + 2) / 3, nt = (tiles + groups - 1) / groups;
-    const int nsa = std::min(tc::NSA_MAX, (512 / nt - n) / tc::ACOLS);
-    if (nsa < 2) continue;
+    // row tiles per CTA: the most (up to three) that leave tensor memory for two stages in flight
+    int nt = std::min(3, tiles), nsa = 0;
+    for (; nt >= 1; --nt) {
+      nsa = std::min(tc::NSA_MAX, (512 / nt - n) / tc::ACOLS);
+      if (nsa >= 2) break;
+    }
+    if (nt < 1) continue;
+    const int groups = (tiles + nt - 1) / nt;
+    nt = (tiles + groups - 1) / groups;   // the same group count with the tiles spread evenly
+    nsa = std::min(tc::NSA_MAX, (512 / nt - n) / tc::ACOLS);
     int nbuf = 3;
     size_t smem = tc::tc_layout(a.nstage, 3, nt, n, nc, nsa).total;
     if (smem > 200 * 1024) {

@@ -359,3 +359,68 @@ def test_full_size_256_all_triangles(api):
         sh = np.asarray(orc["shot_BB"][str(l)])
         e = np.abs(res["shot_BB"][l] - sh) / np.maximum(np.abs(sh), scale_p)
         assert np.max(e) < 1e-4, ("shot_BB", l, np.max(e))
+
+
+def _shape_case(api, case):
+    """One bispectrum call of the launch shape `case`; returns the result dictionary."""
+    from synthetic import make_survey_catalogs
+
+    box = 600.0
+    kf = 2 * np.pi / box
+    if case == "periodic_24_bins":   # the most bins: 348 product rows, two row groups over the CTAs
+        cat = make_periodic_catalog(200000, box, 48, seed=61)
+        return api.bispectrum(cat, n=192, box=box, kbins=(2 * kf, 1.5 * kf, 24), precision="mixed")
+    if case == "fft_method_shot":    # the shot-noise products of the FFT method (shot = 2)
+        cat = make_periodic_catalog(60000, box, 32, seed=62)
+        return api.bispectrum(cat, n=64, box=box, kbins=(2 * kf, 1.5 * kf, 7), shot=2, precision="mixed")
+    if case == "survey_odd":         # four row families: F_0, F_2, F_1, F_3 on the first leg
+        g, r, origin = make_survey_catalogs(20000, 200000, box, 700.0, 32, seed=63, fkp_p0=1e4)
+        return api.bispectrum(g, n=32, box=box, kbins=(2 * kf, 1.5 * kf, 4), origin=origin, randoms=r, los_dir=None,
+                              scoc_ells=(0, 1, 2, 3), tripo_ells=(0, 2), precision="mixed")
+    # three tracers of one density field (one seed, different numbers of objects: a cross
+    # bispectrum with signal), every product of two different catalogues' fields
+    cats = [make_periodic_catalog(nn, box, 32, seed=64) for nn in (30000, 20000, 40000)]
+    return api.cross_bispectrum([(c, None) for c in cats], n=64, box=box, kbins=(2 * kf, 1.5 * kf, 7),
+                                scoc_ells=(0, 2), tripo_ells=(0, 2), precision="mixed")
+
+
+@pytest.mark.parametrize("case", ["periodic_24_bins", "fft_method_shot", "survey_odd", "cross_three_tracers"])
+def test_tensor_core_paths_agree_over_launch_shapes(api, case):
+    """The tcgen05 plan (which two fields form the product rows, row tiles per CTA and row groups,
+    stages in flight) against the mma.sync path on launch shapes beyond the plain 7-bin case: the
+    largest bin count, the FFT-method shot-noise products, four row families of odd multipoles and
+    three different tracers.  Each form carries its own float32 accumulation error (1e-5 to 3e-5 of
+    the monopole scale against the FP64 oracle on a 128^3 shell grid), so they agree within half the
+    1e-4 tolerance; the statistics show that the tcgen05 path ran."""
+    path = api.get_option("tcgen05_triple")
+    try:
+        api.set_option("tcgen05_triple", 1)
+        _shape_case(api, case)   # N_T counted and cached on the first call of a geometry
+        a = _shape_case(api, case)
+        st_a = api.last_stats()
+        api.set_option("tcgen05_triple", 0)
+        b = _shape_case(api, case)
+        st_b = api.last_stats()
+    finally:
+        api.set_option("tcgen05_triple", path)
+    assert st_a["contraction_flops"] == st_b["contraction_flops"] > 0
+    assert st_a["contraction_issued_flops"] != st_b["contraction_issued_flops"]
+    np.testing.assert_array_equal(a["tri"], b["tri"])
+    if "NT" in b:
+        np.testing.assert_allclose(a["NT"], b["NT"], rtol=1e-6)
+    for key, skey in (("B", "shot_B"), ("BB", "shot_BB")):
+        if key not in b:
+            continue
+        shot = b.get(skey, {})
+        scale = np.abs(b[key][0] + shot.get(0, 0.0)) + np.abs(shot.get(0, 0.0))
+        # triangles without a closed triplet (N_T = 0: possible with bins of half a fundamental
+        # mode) are undefined on both paths
+        ok = np.isfinite(scale) & (scale > 0)
+        for l in b[key]:
+            np.testing.assert_array_equal(np.isfinite(a[key][l]), np.isfinite(b[key][l]))
+            err = np.max(np.abs(a[key][l] - b[key][l])[ok] / scale[ok])
+            assert err < 5e-5, (key, l, err)
+            if l in shot:
+                err = np.max(np.abs(a[skey][l] - shot[l])[ok] / scale[ok])
+                assert err < 5e-5, (skey, l, err)
+    assert ok.sum() > 0.9 * ok.size
