@@ -963,7 +963,10 @@ struct TcPlanHost {
   size_t o_rx = 0, o_ry = 0, o_cz = 0, o_sfield = 0, o_runs = 0, o_gidx = 0;   // offsets in the uploaded table
 };
 
-bool plan_triple_tc(const TripleArgs& a, const int* pij, int max_smem, TcPlanHost& out) {
+// need_pk (optional, npair x nf_cols): the outputs of the first nf_cols columns that are read later
+// (1) or never (0, written as zero); columns from nf_cols on are always read.
+bool plan_triple_tc(const TripleArgs& a, const int* pij, int max_smem, TcPlanHost& out,
+                    const std::vector<char>* need_pk = nullptr) {
   if (a.npair <= 0 || a.nrows % a.npair != 0 || a.nstage > tc::MAX_SLOTS || a.ncell % tc::CHUNK != 0) return false;
   const int nfam = a.nrows / a.npair;
   // staged slots renumbered by increasing field index; runs of consecutive fields
@@ -995,10 +998,13 @@ bool plan_triple_tc(const TripleArgs& a, const int* pij, int max_smem, TcPlanHos
       else { u = xa; v = xc; w = xb; }
       if (u > v) std::swap(u, v);
     };
+    auto needed = [&](int p, int c) {
+      return a.c_slot[c] >= 0 && (!need_pk || c >= a.nf_cols || (*need_pk)[(size_t)p * a.nf_cols + c]);
+    };
     for (int f = 0; f < nfam; ++f)
       for (int p = 0; p < a.npair; ++p)
         for (int c = 0; c < a.ncol; ++c) {
-          if (a.c_slot[c] < 0) continue;
+          if (!needed(p, c)) continue;
           int u, v, w;
           roles(f, p, c, u, v, w);
           if (u < 0 || w < 0) return false;
@@ -1057,7 +1063,7 @@ bool plan_triple_tc(const TripleArgs& a, const int* pij, int max_smem, TcPlanHos
     for (int f = 0; f < nfam; ++f)
       for (int p = 0; p < a.npair; ++p)
         for (int c = 0; c < a.ncol; ++c) {
-          if (a.c_slot[c] < 0) continue;
+          if (!needed(p, c)) continue;
           int u, v, w;
           roles(f, p, c, u, v, w);
           P.gidx[((size_t)f * a.npair + p) * a.ncol + c] = rows.at(std::make_pair(u, v)) * nc + cols.at(w);
@@ -2477,9 +2483,22 @@ npc_status bispec_impl(npc_ctx* ctx, const npc_mesh_spec& m, const npc_kbins& kb
         if (nbytes) std::memcpy(tt.data() + o, q, nbytes);
         return o;
       };
+      // the data and N_T launches are read only at the closed triangles (i <= j <= k: pair (i, j),
+      // column k) and, for the data launch, at every pair's G columns: product rows that serve no
+      // closed triangle are not formed
+      std::vector<char> need_pk((size_t)npair * nb, 0);
+      {
+        std::vector<int> pidx((size_t)nb * nb, -1);
+        for (int q = 0; q < npair; ++q) pidx[(size_t)(tr.pij[q] & 0xffff) * nb + (tr.pij[q] >> 16)] = q;
+        for (size_t t = 0; t + 2 < tr.tri.size(); t += 3) {
+          const int q = pidx[(size_t)tr.tri[t] * nb + tr.tri[t + 1]];
+          if (q >= 0) need_pk[(size_t)q * nb + tr.tri[t + 2]] = 1;
+        }
+      }
       for (const TripleArgs* a : {&ta, &tn, &ts1, &ts2, &ts3, &tn2}) {
         TcPlanHost P;
-        if (a->nrows <= 32 || a->ncol <= 0 || !plan_triple_tc(*a, tr.pij.data(), max_smem, P)) continue;
+        const std::vector<char>* need = (a == &ta || a == &tn) && a->nf_cols == nb ? &need_pk : nullptr;
+        if (a->nrows <= 32 || a->ncol <= 0 || !plan_triple_tc(*a, tr.pij.data(), max_smem, P, need)) continue;
         P.o_rx = push16(P.rx.data(), sizeof(int16_t) * P.rx.size());
         P.o_ry = push16(P.ry.data(), sizeof(int16_t) * P.ry.size());
         P.o_cz = push16(P.cz.data(), sizeof(int16_t) * P.cz.size());
