@@ -152,6 +152,8 @@ struct PaintGeo {
   int n, bs, nb, ts;     // mesh cells, brick size, bricks per side, tile side (bs + 4)
   double o[3];           // origin
   double inv_h;          // n / box
+  float o_hi[3], o_lo[3];      // origin and n / box as float pairs (hi + lo) for the scatter's
+  float ih_hi, ih_lo;          // float fast path
 };
 
 __device__ __forceinline__ long long wrapi(long long i, int n) {
@@ -250,6 +252,45 @@ __device__ __forceinline__ uint32_t axis_meta(double s, int n, int bs, double* f
   return local | ((uint32_t)(ia - fb) << 5) | ((uint32_t)(ib - fb) << 6);
 }
 
+// The same decisions and fraction from a float position in float arithmetic: s = (x - origin) n/box
+// as a float pair (exact difference by two-sum, exact product error by fma; about 2^-46 relative),
+// its floor and the fraction s - floor(s) to float precision.  For TSC floor(s + 1/2) - floor(s) is
+// [frac >= 1/2] and floor(s + 1) - floor(s) = 1; for CIC the phase-a offset is 0 and the phase-b one
+// [frac >= 1/2], exactly as the float64 expressions give them.  Returns false (the caller takes the
+// float64 path) when |s| >= 2^22 or the fraction lies within 1e-6 of 0, 1/2 or 1, where the float64
+// rounding of s could decide differently.
+template <int ASSIGN>
+__device__ __forceinline__ bool axis_meta_fast(float x, float o_hi, float o_lo, float ih_hi, float ih_lo, int n, int bs,
+                                               float* frac, uint32_t* meta) {
+  const float d1 = __fsub_rn(x, o_hi);
+  const float bv = __fsub_rn(d1, x);
+  const float d2 = __fsub_rn(__fadd_rn(__fsub_rn(x, __fsub_rn(d1, bv)), __fsub_rn(-o_hi, bv)), o_lo);
+  // the rounded product is never fused into a later add: s2 carries its exact error
+  const float s1 = __fmul_rn(d1, ih_hi);
+  float s2 = fmaf(d1, ih_hi, -s1);
+  s2 = fmaf(d1, ih_lo, s2);
+  s2 = fmaf(d2, ih_hi, s2);
+  if (!(fabsf(s1) < 4194304.0f)) return false;
+  float f = floorf(s1);
+  float fr = __fadd_rn(__fsub_rn(s1, f), s2);
+  if (fr < 0.0f) {
+    f -= 1.0f;
+    fr += 1.0f;
+  } else if (fr >= 1.0f) {
+    f += 1.0f;
+    fr -= 1.0f;
+  }
+  const float tol = 1.0e-6f;
+  if (fr < tol || fr > 1.0f - tol || fabsf(fr - 0.5f) < tol) return false;
+  const int fb = (int)f;
+  const uint32_t half = fr >= 0.5f ? 1u : 0u;
+  const uint32_t local = (uint32_t)((((fb % n) + n) % n) % bs);
+  const uint32_t da = ASSIGN == 2 ? 0u : half, db = ASSIGN == 2 ? half : 1u;
+  *meta = local | (da << 5) | (db << 6);
+  *frac = fr;
+  return true;
+}
+
 // coefficient * w^power per particle; coef_kind: 0 -> 1, 1 -> -alpha, 2 -> +alpha^2
 template <int ASSIGN, typename P, typename R>
 __global__ void k_scatter(const P* __restrict__ pos, const P* __restrict__ w, int64_t n, int power,
@@ -259,10 +300,41 @@ __global__ void k_scatter(const P* __restrict__ pos, const P* __restrict__ w, in
   double coef = 1.0;
   if (coef_kind == 1) coef = -sc[SC_ALPHA];
   if (coef_kind == 2) coef = sc[SC_ALPHA] * sc[SC_ALPHA];
+  const float coef_f = (float)coef;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int b = brick[i];
     if (b < 0) continue;
+    const int dst = start[b] + rank[i];
+    if constexpr (sizeof(R) == 4 && sizeof(P) == 4) {
+      // float records from float positions: the float pair path, float64 only near a decision
+      uint32_t u[3];
+      float wcf;
+      {
+        const float wf = w ? (float)w[i] : 1.0f;
+        wcf = coef_f * (power == 2 ? wf * wf : wf);
+      }
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const float x = (float)pos[3 * i + a];
+        float frf;
+        uint32_t ma;
+        if (!axis_meta_fast<ASSIGN>(x, g.o_hi[a], g.o_lo[a], g.ih_hi, g.ih_lo, g.n, g.bs, &frf, &ma)) {
+          double frd;
+          ma = axis_meta<ASSIGN>(((double)x - g.o[a]) * g.inv_h, g.n, g.bs, &frd);
+          frf = (float)frd;
+        }
+        const uint32_t q = __float2uint_rz(frf * 16777216.0f);
+        u[a] = (q > 0xffffffu ? 0xffffffu : q) | ((ma & 255u) << 24);
+      }
+      typename RecOf<R>::type r;
+      r.x = __uint_as_float(u[0]);
+      r.y = __uint_as_float(u[1]);
+      r.z = __uint_as_float(u[2]);
+      r.w = wcf;
+      rec[dst] = r;
+      continue;
+    }
     const double wi = w ? (double)w[i] : 1.0;
     const double wc = coef * (power == 2 ? wi * wi : wi);
     double fr[3];
@@ -272,7 +344,6 @@ __global__ void k_scatter(const P* __restrict__ pos, const P* __restrict__ w, in
       const double s = ((double)pos[3 * i + a] - g.o[a]) * g.inv_h;
       m |= axis_meta<ASSIGN>(s, g.n, g.bs, &fr[a]) << (8 * a);
     }
-    const int dst = start[b] + rank[i];
     typename RecOf<R>::type r;
     if constexpr (sizeof(R) == 4) {
       // one 16-byte record: per axis the fraction in 24-bit fixed point (truncated, |error| < 2^-24
@@ -552,6 +623,12 @@ npc_status paint_impl(npc_ctx* ctx, const DevCatalog& d, const DevCatalog* r, co
   g.ts = g.bs + 4;
   for (int a = 0; a < 3; ++a) g.o[a] = m.origin[a];
   g.inv_h = (double)m.n / m.box;
+  for (int a = 0; a < 3; ++a) {
+    g.o_hi[a] = (float)g.o[a];
+    g.o_lo[a] = (float)(g.o[a] - (double)g.o_hi[a]);
+  }
+  g.ih_hi = (float)g.inv_h;
+  g.ih_lo = (float)(g.inv_h - (double)g.ih_hi);
   const int nphase = m.interlace ? 2 : 1;
   const int nbricks = g.nb * g.nb * g.nb;
   const int64_t ntot = d.n + (r ? r->n : 0);
