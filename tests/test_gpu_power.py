@@ -146,6 +146,33 @@ def test_particles_on_box_edges_and_outside(api):
     _compare(res, orc, (0, 2), (), 1e-12)
 
 
+@pytest.mark.parametrize("assign", [2, 3])
+def test_float_positions_on_cell_faces_mixed(api, assign):
+    """Float positions on cell faces, cell centres and the box faces (where the float-pair fraction is
+    within 1e-6 of an assignment decision and the float64 form decides), and a few float ulps off them
+    (where the float-pair form decides alone), paint as the oracle does in mixed precision."""
+    rng = np.random.default_rng(23 + assign)
+    box, n = 200.0, 32
+    h = box / n
+    for origin in [(0.0, 0.0, 0.0), (-18.75, 12.5, 3.125), (0.1, -0.3, 7.7)]:
+        o = np.array(origin)
+        pos = o + rng.random((20000, 3)) * box
+        pos[:12000] = o + rng.integers(-2, 2 * n + 2, size=(12000, 3)) * (h / 2)
+        pos[8000:9000, 0] = o[0]
+        pos[9000:10000, 1] = o[1] + box
+        pos = pos.astype(np.float32)
+        away = np.where(rng.random((2000, 3)) < 0.5, -np.inf, np.inf).astype(np.float32)
+        pos[10000:12000] = np.nextafter(pos[10000:12000], away)
+        nb = np.float32(20000 / box**3)
+        cat = SimpleNamespace(pos=pos, w=np.ones(20000, np.float32), nbar=np.full(20000, nb, np.float32))
+        kb = (0.0, 0.03, 8)
+        res = api.power_multipoles(cat, None, n=n, box=box, origin=origin, assign=assign, interlace=1,
+                                   kbins=kb, ells=(0, 2), precision="mixed", los_dir=(0, 0, 1))
+        spec = dict(n=n, box=box, origin=origin, assign=assign, interlace=1, los="global", los_dir=(0, 0, 1))
+        orc = P.power_multipoles(spec, cat, None, kb, (0, 2))
+        _compare(res, orc, (0, 2), (), 1e-5)
+
+
 def test_determinism_and_device_inputs(api):
     torch = pytest.importorskip("torch")
     g, r, origin = make_survey_catalogs(30000, 300000, 800.0, 1300.0, 32, seed=12, fkp_p0=1e4)
