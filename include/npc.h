@@ -73,7 +73,8 @@ typedef struct {
   const void* pos;     /* required when n > 0 */
   const void* w;       /* NULL: all weights 1 */
   const void* nbar;    /* NULL allowed only where nbar is not used (data catalogue, periodic) */
-  int64_t n;           /* number of objects, >= 0 */
+  int64_t n;           /* number of objects, 0 <= n < 2^31; a catalogue painted with its randoms
+                          needs data n + randoms n < 2^31 (NPC_ERR_UNSUPPORTED otherwise) */
   int32_t dtype;       /* 0 = float32, 1 = float64 (all three arrays) */
   int32_t on_device;   /* 1: device pointers on the context's device; 0: host pointers */
 } npc_catalog;

@@ -185,6 +185,16 @@ npc_status check_catalog(npc_ctx* ctx, const npc_catalog* c, const char* what, b
   return NPC_OK;
 }
 
+// A catalogue and its randoms are sorted into bricks together, with 32-bit offsets into one record
+// array: their sizes must sum below 2^31.
+npc_status check_painted_pair(npc_ctx* ctx, const npc_catalog* d, const npc_catalog* r) {
+  const int64_t tot = d->n + (r ? r->n : 0);
+  if (tot >= (int64_t)1 << 31)
+    return set_err(ctx, NPC_ERR_UNSUPPORTED, "data + randoms hold %lld objects; painting takes at most 2^31-1",
+                   (long long)tot);
+  return NPC_OK;
+}
+
 npc_status check_bins(npc_ctx* ctx, const npc_kbins* b) {
   if (!b) return set_err(ctx, NPC_ERR_INVALID_ARG, "k-bins are NULL");
   if (!(b->dk > 0.0) || !std::isfinite(b->dk) || !(b->kmin >= 0.0) || !std::isfinite(b->kmin))
@@ -638,6 +648,7 @@ npc_status npc_power_multipoles(npc_ctx* ctx, const npc_mesh_spec* mesh, const n
   } else {
     if (!randoms) return set_err(ctx, NPC_ERR_INVALID_ARG, "survey geometry needs randoms");
     NPC_TRY(check_catalog(ctx, randoms, "randoms", true));
+    NPC_TRY(check_painted_pair(ctx, data, randoms));
     if (randoms->n == 0) return set_err(ctx, NPC_ERR_NUMERIC, "empty random catalogue");
   }
   if (data->n == 0) return set_err(ctx, NPC_ERR_NUMERIC, "empty data catalogue (I22 = 0)");
@@ -680,6 +691,8 @@ npc_status npc_cross_power_multipoles(npc_ctx* ctx, const npc_mesh_spec* mesh, c
     if (!randoms_a || !randoms_b) return set_err(ctx, NPC_ERR_INVALID_ARG, "survey geometry needs both randoms");
     NPC_TRY(check_catalog(ctx, randoms_a, "randoms_a", true));
     NPC_TRY(check_catalog(ctx, randoms_b, "randoms_b", true));
+    NPC_TRY(check_painted_pair(ctx, data_a, randoms_a));
+    NPC_TRY(check_painted_pair(ctx, data_b, randoms_b));
     if (randoms_a->n == 0 || randoms_b->n == 0) return set_err(ctx, NPC_ERR_NUMERIC, "empty random catalogue");
   }
   if (data_a->n == 0 || data_b->n == 0) return set_err(ctx, NPC_ERR_NUMERIC, "empty data catalogue (I22 = 0)");
@@ -776,6 +789,7 @@ npc_status npc_bispectrum_sugiyama(npc_ctx* ctx, const npc_mesh_spec* mesh, cons
                      "TripoSH with the line of sight to each grid point: raw estimates only (shot = 0)");
     if (!randoms) return set_err(ctx, NPC_ERR_INVALID_ARG, "survey geometry needs randoms");
     NPC_TRY(check_catalog(ctx, randoms, "randoms", true));
+    NPC_TRY(check_painted_pair(ctx, data, randoms));
     if (randoms->n == 0) return set_err(ctx, NPC_ERR_NUMERIC, "empty random catalogue");
   }
   const double kf = 2.0 * M_PI / mesh->box;
@@ -836,6 +850,7 @@ npc_status npc_bispectrum(npc_ctx* ctx, const npc_mesh_spec* mesh, const npc_cat
       return set_err(ctx, NPC_ERR_UNSUPPORTED, "bispectrum: FFT-method shot noise of l = 2 needs a global line of sight");
     if (!randoms) return set_err(ctx, NPC_ERR_INVALID_ARG, "survey geometry needs randoms");
     NPC_TRY(check_catalog(ctx, randoms, "randoms", true));
+    NPC_TRY(check_painted_pair(ctx, data, randoms));
     if (randoms->n == 0) return set_err(ctx, NPC_ERR_NUMERIC, "empty random catalogue");
   }
   const double kf = 2.0 * M_PI / mesh->box;
@@ -900,6 +915,7 @@ npc_status npc_cross_bispectrum(npc_ctx* ctx, const npc_mesh_spec* mesh, const n
     if (data[t].n == 0) return set_err(ctx, NPC_ERR_NUMERIC, "empty data catalogue %d (I33 = 0)", t);
     if (randoms) {
       NPC_TRY(check_catalog(ctx, &randoms[t], rtag[t], true));
+      NPC_TRY(check_painted_pair(ctx, &data[t], &randoms[t]));
       if (randoms[t].n == 0) return set_err(ctx, NPC_ERR_NUMERIC, "empty random catalogue %d", t);
     }
   }

@@ -52,6 +52,7 @@ npc_status check_item(npc_ctx* ctx, const npc_batch_item& it, uint32_t ell_mask,
     if (it.randoms.n != 0) return set_err(ctx, NPC_ERR_INVALID_ARG, "item %d: periodic box takes no randoms", i);
   } else {
     NPC_TRY(check_catalog(ctx, &it.randoms, "randoms", true));
+    NPC_TRY(check_painted_pair(ctx, &it.data, &it.randoms));
     if (!it.randoms.on_device || it.randoms.n == 0)
       return set_err(ctx, NPC_ERR_INVALID_ARG, "item %d: survey needs a non-empty device random catalogue", i);
   }

@@ -632,6 +632,9 @@ npc_status paint_impl(npc_ctx* ctx, const DevCatalog& d, const DevCatalog* r, co
   const int nphase = m.interlace ? 2 : 1;
   const int nbricks = g.nb * g.nb * g.nb;
   const int64_t ntot = d.n + (r ? r->n : 0);
+  // brick starts and ranks are 32-bit offsets into one record array
+  if (ntot >= (int64_t)1 << 31)
+    return set_err(ctx, NPC_ERR_UNSUPPORTED, "painting takes at most 2^31-1 objects (data + randoms)");
   int *count, *start, *brick, *rank;
   uint32_t* meta;
   void* rec;

@@ -246,6 +246,7 @@ npc_status ws_table(npc_ctx* ctx, const std::string& name, const std::vector<cha
 // Shared host helpers of the public entry points (api.cu)
 npc_status check_spec(npc_ctx* ctx, const npc_mesh_spec* m);
 npc_status check_catalog(npc_ctx* ctx, const npc_catalog* c, const char* what, bool need_nbar);
+npc_status check_painted_pair(npc_ctx* ctx, const npc_catalog* d, const npc_catalog* r);
 npc_status check_bins(npc_ctx* ctx, const npc_kbins* b);
 struct DevCatalog;
 npc_status stage_catalog(npc_ctx* ctx, const npc_catalog* c, const char* tag, DevCatalog* out);

@@ -216,6 +216,26 @@ def test_invalid_arguments_rejected(api):
     with pytest.raises(B.NpcError) as ei:
         api.power_multipoles(g, r, n=32, box=300.0, origin=origin, kbins=kb, ells=(0,), periodic=1)
     assert ei.value.status == 1
+    # a catalogue and its randoms share one brick sort with 32-bit offsets: together they must hold
+    # fewer than 2^31 objects.  The declared counts are rejected before any array is read (the
+    # arrays behind them are the small ones above).
+    keep = api._Keep()
+    spec = api.make_spec(32, 300.0, origin, 3, 1, 0)
+    kbs = B.npc_kbins(*kb)
+    buf = np.zeros(64)
+    ctx = api.context(0)
+    for nd, nr in [((1 << 31) - 1, 1), (1 << 30, 1 << 30)]:
+        d, rr = api.make_catalog(g, keep), api.make_catalog(r, keep)
+        d.n, rr.n = nd, nr
+        st = B.npc_power_multipoles(ctx, C.byref(spec), C.byref(d), C.byref(rr), C.byref(kbs), 1, 0,
+                                    B.NPC_PREC_MIXED, buf.ctypes.data_as(C.c_void_p), 0)
+        assert st == 4, (nd, nr, st)
+        ga, ra = api.make_catalog(g, keep), api.make_catalog(r, keep)
+        st = B.npc_cross_power_multipoles(ctx, C.byref(spec), C.byref(ga), C.byref(ra), C.byref(d), C.byref(rr),
+                                          C.byref(kbs), 1, B.NPC_PREC_MIXED, buf.ctypes.data_as(C.c_void_p), 0)
+        assert st == 4, ("cross", nd, nr, st)
+    res = api.power_multipoles(g, r, n=32, box=300.0, origin=origin, kbins=kb, ells=(0,))
+    assert np.all(np.isfinite(res["P"][0]))
 
 
 @pytest.mark.slow
