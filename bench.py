@@ -569,9 +569,11 @@ def bispec_leg(args, world, rank, barrier, max_over_ranks):
             "sugiyama": sugiyama,
             "fft_method_shot": {"value": world * ntri.value * nmult / (ms_fft / 1e3), "ms_per_step": ms_fft,
                                 "note": "shot noise of B_l and B_l0l by the FFT method (exact sums of the two-object terms)"},
-            "triple_product": ("3xTF32 split hi+lo tensor-core products: tcgen05.mma kind::tf32 M=128 N=32 with the "
-                               "pair products in tensor memory for launches of more than 32 rows, mma.sync m16n8k8 "
-                               "for the rest; FP32 within 4096-cell (tcgen05) or 128-cell chunks, FP64 across them"
+            "triple_product": ("f16 hi+lo split after exact power-of-two scales: tcgen05.mma kind::f16 M=128 with the "
+                               "product rows written to tensor memory and the hi/lo columns packed along N, fields "
+                               "staged by bulk asynchronous copies, for launches of more than 32 rows (3xTF32 "
+                               "mma.sync m16n8k8 for the rest); FP32 within 4096-cell flushes (tcgen05, compensated "
+                               "sums) or 128-cell chunks (mma.sync), FP64 across them"
                                if api.get_option("tcgen05_triple") else
                                "3xTF32 split hi+lo tensor-core products (mma.sync m16n8k8), FP32 within 128-cell "
                                "chunks, FP64 across chunks")}
