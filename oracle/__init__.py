@@ -21,5 +21,8 @@ Modules
   shot       analytic and FFT-method bispectrum shot noise (Sec. 5.4).
   adjoint    gradients of P_l and equilateral B_0 with respect to the density mesh.
 
-Parity status of each function is stated in its docstring ("pinned by ..." or "parity unpinned").
+Each module's header names the tests that pin its functions and what they check, and a function's
+docstring does so where its pins differ from its module's; a function with no pin would say
+"parity unpinned" (none does: the analytic shot-noise forms, thin-shell approximations with no exact
+reference, are pinned statistically and against the exact FFT-method sums, as their headers say).
 """

@@ -19,6 +19,14 @@ the paper notes they contribute nothing, Appendix G), DC excluded, bin
 b = floor((k_f sqrt(i^2+j^2+l^2) - kmin)/dk), kept when 0 <= b < nbins (half-open bins).
 The paper writes the shell boundaries both with strict and with non-strict inequalities (Sec. 2.3
 and Appendix E); half-open is the reading used here.
+
+Pinned by tests/test_oracle_mesh.py: mode counts per thin shell equal the number of integer vectors
+of that length (enumerated; Legendre's three-square theorem for the empty shells), one bin over
+every |k| > 0 holds the (n - 1)^3 - 1 modes inside the Nyquist cube, and the CIC / TSC weights at
+grid points, half cells and quarter cells are the textbook values, conserve mass and reproduce the
+particle's position; by tests/test_oracle_power.py: the painted mesh's DFT equals the per-particle
+DFT (CIC on grid points exactly, compensated CIC / TSC at low k), the compensated Poisson spectrum
+equals the closed-form alias sum of the window, and interlacing removes the leading alias.
 """
 from __future__ import annotations
 
