@@ -24,7 +24,9 @@ Pinned by tests/test_oracle_mesh.py: mode counts per thin shell equal the number
 of that length (enumerated; Legendre's three-square theorem for the empty shells), one bin over
 every |k| > 0 holds the (n - 1)^3 - 1 modes inside the Nyquist cube, and the CIC / TSC weights at
 grid points, half cells and quarter cells are the textbook values, conserve mass and reproduce the
-particle's position; by tests/test_oracle_power.py: the painted mesh's DFT equals the per-particle
+particle's position, and the window W(k) is the Fourier transform of the painted kernel (the mesh
+DFT of one particle averaged over its offset in the cell, to the alias bound of that average); by
+tests/test_oracle_power.py: the painted mesh's DFT equals the per-particle
 DFT (CIC on grid points exactly, compensated CIC / TSC at low k), the compensated Poisson spectrum
 equals the closed-form alias sum of the window, and interlacing removes the leading alias.
 """

@@ -99,3 +99,25 @@ def test_assignment_conserves_mass_and_centre(assign):
         for a in range(3):
             marg = m.sum(axis=tuple(x for x in range(3) if x != a))
             assert float(marg @ idx) == pytest.approx(p[a], abs=1e-12)
+
+
+@pytest.mark.parametrize("assign", [2, 3])
+def test_window_is_the_fourier_transform_of_the_kernel(assign):
+    """Averaged over the particle's offset s within a cell, e^{i k.s} times the mesh DFT of one painted
+    particle is the continuous Fourier transform of the assignment kernel, prod_a sinc^p(k_a H / 2):
+    the compensation W(k) of Sec. 3.1.  By Poisson summation the M-point midpoint average over each
+    axis differs from it only by the aliases k + 2 pi M m / H (m != 0), at most
+    2 zeta(p) (pi (M - 1/2))^-p per axis; the tolerance is three times that (three axes)."""
+    n, mo = 8, 48
+    off = (np.arange(mo) + 0.5) / mo
+    s = np.stack(np.meshgrid(off, off, off, indexing="ij"), -1).reshape(-1, 3) + np.array([3.0, 2.0, 5.0])
+    w = M.window(n, assign)
+    zeta = {2: np.pi ** 2 / 6, 3: 1.2020569031595942}[assign]
+    tol = 3 * 2 * zeta * (np.pi * (mo - 0.5)) ** (-assign) * 1.01
+    for i in [(1, 0, 0), (2, 1, 0), (3, 3, 1), (-3, 2, -1), (1, 1, 1), (3, -3, 3), (0, 0, 2)]:
+        phase = s @ (2.0 * np.pi * np.array(i) / n)      # k.s with s in cells
+        mesh_c = M.paint(s, np.cos(phase), n, assign)
+        mesh_s = M.paint(s, np.sin(phase), n, assign)
+        j = tuple(v % n for v in i)
+        avg = (np.fft.fftn(mesh_c)[j] + 1j * np.fft.fftn(mesh_s)[j]) / len(s)
+        assert abs(avg - w[j]) < tol, (i, avg, w[j], tol)
