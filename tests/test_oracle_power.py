@@ -230,6 +230,28 @@ def test_catalog_scalars_uniform():
     assert per["N0"] == pytest.approx(1.0)
 
 
+@pytest.mark.parametrize("c", [1.0, 0.37])
+def test_catalog_scalars_are_the_density_integrals(c):
+    """I22 and I33 are the integrals of (nbar w)^2 and (nbar w)^3 over the volume (Secs. 2.1, 2.2):
+    for a uniform survey of volume V (nbar = N_g / V on every random) with constant weight c they are
+    nbar^2 c^2 V and nbar^3 c^3 V, the values the periodic-box forms give for the same data, and the
+    three-point self term is N_g c^3 (1 - alpha^2)."""
+    rng = np.random.default_rng(3)
+    ng, nr, box = 2000, 30000, 50.0
+    vol = box**3
+    nb = ng / vol
+    g = SimpleNamespace(pos=rng.random((ng, 3)) * box, w=np.full(ng, c), nbar=np.full(ng, nb))
+    r = SimpleNamespace(pos=rng.random((nr, 3)) * box, w=np.full(nr, c), nbar=np.full(nr, nb))
+    sur = P.catalog_scalars(g, r)
+    per = P.catalog_scalars(g, None, box=box)
+    alpha = ng / nr
+    assert sur["I22"] == pytest.approx(nb**2 * c**2 * vol, rel=1e-12)
+    assert sur["I33"] == pytest.approx(nb**3 * c**3 * vol, rel=1e-12)
+    assert per["I22"] == pytest.approx(nb**2 * c**2 * vol, rel=1e-12)
+    assert per["I33"] == pytest.approx(nb**3 * c**3 * vol, rel=1e-12)
+    assert sur["S3"] == pytest.approx(ng * c**3 * (1 - alpha**2), rel=1e-12)
+
+
 @pytest.mark.parametrize("interlace,assign", [(0, 2), (1, 3)])
 def test_rfft_monopole_equals_full_grid(small_survey, interlace, assign):
     """The half-grid monopole used for full-size checks equals the full-grid Hand+17 P_0."""
