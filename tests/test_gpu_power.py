@@ -173,6 +173,29 @@ def test_float_positions_on_cell_faces_mixed(api, assign):
         _compare(res, orc, (0, 2), (), 1e-5)
 
 
+@pytest.mark.parametrize("prec,tol", [("mixed", 1e-5), ("fp64", 1e-11)])
+def test_most_objects_in_one_cell(api, prec, tol):
+    """A degenerate catalogue: 250,000 of 300,000 objects at one point, so one brick holds almost the
+    whole catalogue (the largest per-brick count the painter's fixed-point scale has to absorb) and the
+    field is nearly a spike; P_0, P_2 as the oracle has them.  FP64 tolerance: the brick's taps are
+    rounded to multiples of 2^-e with 2^(61-e) > count x max w (count = 250,780 here, e = 43), and the
+    250,000 identical taps all round the same way, so each of the 27 cells of a phase may be off by
+    count x 2^-44 = 1.4e-8; divided by the compensation W > 0.5 in these bins and compared with
+    |F| = 2.5e5 that is at most 3e-12 of F, 6e-12 of P (1.7e-12 measured), hence 1e-11."""
+    rng = np.random.default_rng(61)
+    box, n = 200.0, 32
+    pos = rng.random((300000, 3)) * box
+    pos[:250000] = (37.3, 101.9, 150.2)
+    dt = np.float32 if prec == "mixed" else np.float64
+    cat = SimpleNamespace(pos=pos.astype(dt), w=np.ones(300000, dt), nbar=np.full(300000, 300000 / box**3, dt))
+    kb = (0.0, 0.03, 8)
+    res = api.power_multipoles(cat, None, n=n, box=box, origin=(0.0, 0.0, 0.0), assign=3, interlace=1,
+                               kbins=kb, ells=(0, 2), precision=prec, los_dir=(0, 0, 1))
+    spec = dict(n=n, box=box, origin=(0.0, 0.0, 0.0), assign=3, interlace=1, los="global", los_dir=(0, 0, 1))
+    orc = P.power_multipoles(spec, cat, None, kb, (0, 2))
+    _compare(res, orc, (0, 2), (), tol)
+
+
 def test_determinism_and_device_inputs(api):
     torch = pytest.importorskip("torch")
     g, r, origin = make_survey_catalogs(30000, 300000, 800.0, 1300.0, 32, seed=12, fkp_p0=1e4)
