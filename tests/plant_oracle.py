@@ -94,6 +94,22 @@ PLANTS += [
      "v += (2 * L + 1) / i33 * Hk[L][j]", 1),
     ("A1 adjoint factor 2 dropped", "oracle/adjoint.py", "Y = 2.0 * K * X / M.window(n, assign)",
      "Y = K * X / M.window(n, assign)", 1),
+    ("HS1 half spectrum m > 0 not doubled", "oracle/power.py",
+     "c = 4.0 * pi / (2 * ell + 1) * (1.0 if m == 0 else 2.0)", "c = 4.0 * pi / (2 * ell + 1) * 1.0", 1),
+    ("HS2 half spectrum imaginary part sign", "oracle/power.py",
+     "term += c * np.imag(yk) * self._rfft(mesh * np.imag(y))",
+     "term -= c * np.imag(yk) * self._rfft(mesh * np.imag(y))", 1),
+    ("HS3 half spectrum pair weight", "oracle/power.py", "wgt = (np.where(iz == 0, 1.0, 2.0) * ok).ravel()",
+     "wgt = (np.where(iz == 0, 2.0, 2.0) * ok).ravel()", 1),
+    ("HS4 half spectrum Nyquist plane kept", "oracle/power.py", "& (iz != n // 2)", "", 1),
+    ("HS5 half spectrum interlacing phase", "oracle/power.py", "ph = np.exp(1j * a * (ix + iy + iz))",
+     "ph = np.exp(-1j * a * (ix + iy + iz))", 1),
+    ("X1 cross I22 of tracer A only", "oracle/power.py", 'i22 = np.sqrt(sa["I22"] * sb["I22"])', 'i22 = sa["I22"]', 1),
+    ("X2 cross tracers swapped", "oracle/power.py", "_part(ell, fa[0] * np.conj(fb[ell]))",
+     "_part(ell, fb[0] * np.conj(fa[ell]))", 1),
+    ("L1 global line of sight not normalised", "oracle/bispec.py",
+     "    d = d / np.linalg.norm(d)\n    kk = np.sqrt(kx * kx + ky * ky + kz * kz)",
+     "    kk = np.sqrt(kx * kx + ky * ky + kz * kz)", 1),
 ]
 
 # Uncaught, and why: the first gives the same result for every input the oracle takes; the second

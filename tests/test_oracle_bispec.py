@@ -124,6 +124,21 @@ def test_triangle_count_thin_shell_limit():
     assert np.all(np.abs(ratios - 1) < 0.06)
 
 
+def test_global_line_of_sight_enters_by_direction_only():
+    """los_dir is a direction: (1, 2, 2) and (1/3, 2/3, 2/3) give the same B_0, B_2, B_000, B_202 and
+    analytic shot noise (B_2 is far from zero here, so the comparison is not empty)."""
+    cat = make_periodic_catalog(4000, 300.0, 16, seed=12)
+    kb = (0.02, 0.02, 5)
+    base = _periodic_spec(24, 300.0)
+    a = B.bispectrum(dict(base, los_dir=(1.0, 2.0, 2.0)), cat, None, kb, (0, 2), (0, 2))
+    b = B.bispectrum(dict(base, los_dir=(1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0)), cat, None, kb, (0, 2), (0, 2))
+    scale = np.max(np.abs(a["B"][0]))
+    assert np.max(np.abs(a["B"][2])) > 1e-2 * scale
+    for key in ("B", "BB", "shot_B", "shot_BB"):
+        for ell in (0, 2):
+            np.testing.assert_allclose(a[key][ell], b[key][ell], rtol=1e-10, atol=1e-10 * scale)
+
+
 @pytest.mark.slow
 def test_poisson_shot_noise_is_subtracted():
     """Uniform Poisson catalogues (no clustering): the raw monopole B_0 averages to the analytic

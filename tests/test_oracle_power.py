@@ -354,13 +354,16 @@ def test_odd_cross_multipoles_of_a_shifted_copy():
 def test_half_spectrum_form_equals_full_grid(small_survey, n, assign, interlace, los):
     """The half-spectrum (real-to-complex) evaluation of the symmetric form gives, for every
     multipole (even and odd l, the two-index P_ll' and the modified P_lb), the values of the
-    full-grid Hand+17 sum over all 2l+1 values of m (Eq. hand), and the same mode counts and k_eff:
-    meshes of 2^k and 3 * 2^k cells, CIC without and TSC with interlacing, both lines of sight."""
+    full-grid Hand+17 sum over all 2l+1 values of m (Eq. hand), and the same mode counts and k_eff,
+    in bins reaching the corners of the Fourier cube: meshes of 2^k and 3 * 2^k cells, CIC without
+    and TSC with interlacing, both lines of sight."""
     g, r, origin = small_survey
     spec = _survey_spec(n, 1000.0, origin, assign, interlace)
     if los == "global":
         spec.update(los="global", los_dir=(1.0, 2.0, 2.0))
-    kb = (0.0, 0.01, int(np.pi * n / 1000.0 / 0.01))
+    # bins up to sqrt(3) k_N: every mode of the cube has a bin, so the Nyquist planes that both
+    # forms leave out are compared too
+    kb = (0.0, 0.01, int(np.sqrt(3.0) * np.pi * n / 1000.0 / 0.01) + 1)
     ells = (0, 1, 2, 3, 4)
     two = ((2, 2), (4, 2), (4, 4))
     a = P.power_multipoles(spec, g, r, kb, ells, (4, 6, 8), method="plain")
