@@ -107,14 +107,30 @@ PLANTS += [
     ("X1 cross I22 of tracer A only", "oracle/power.py", 'i22 = np.sqrt(sa["I22"] * sb["I22"])', 'i22 = sa["I22"]', 1),
     ("X2 cross tracers swapped", "oracle/power.py", "_part(ell, fa[0] * np.conj(fb[ell]))",
      "_part(ell, fb[0] * np.conj(fa[ell]))", 1),
+    ("SV1 survey self-term moments with alpha^2", "oracle/shot.py", "v -= alpha ** 3 * np.sum(",
+     "v -= alpha ** 2 * np.sum(", 1),
+    ("TS1 TripoSH G field not conjugated", "oracle/sugiyama.py",
+     "lambda sh, L=L, Mm=Mm: np.conj(H.ylm_racah(L, Mm, P._xhat_dirs(spec, sh))))",
+     "lambda sh, L=L, Mm=Mm: H.ylm_racah(L, Mm, P._xhat_dirs(spec, sh)))", 1),
+    ("TS2 TripoSH shell weight not conjugated", "oracle/sugiyama.py",
+     "w = np.conj(H.ylm_racah(ell, m, P._khat(spec))) * X0", "w = H.ylm_racah(ell, m, P._khat(spec)) * X0", 1),
+    ("AD2 bispectrum adjoint 3 -> 2", "oracle/adjoint.py", "c = 3.0 * dldb[k] / (i33 * nt)",
+     "c = 2.0 * dldb[k] / (i33 * nt)", 1),
     ("L1 global line of sight not normalised", "oracle/bispec.py",
      "    d = d / np.linalg.norm(d)\n    kk = np.sqrt(kx * kx + ky * ky + kz * kz)",
      "    kk = np.sqrt(kx * kx + ky * ky + kz * kz)", 1),
 ]
 
-# Uncaught, and why: the first gives the same result for every input the oracle takes; the second
-# changes only a reading that no printed value fixes.
+# Uncaught, and why: the first two give the same result for every input the oracle takes; the
+# third changes only a reading that no printed value fixes; the fourth is a limit of the pins.
 EQUIVALENT = [
+    ("survey self term S_l not conjugated", "oracle/shot.py",
+     "the survey shot noise is formed for l = 0 (real Y_00 and C_00) and l = 2, where every bin is a "
+     "union of lattice shells invariant under the cube's symmetries, so <Y_2m>_k = 0 and S_2 = 0"),
+    ("survey Q_l built as H_l (line of sight on the wrong leg)", "oracle/shot.py",
+     "NOT PINNED beyond the distant-observer limit, where Q_l = H_l; without randoms N = w F and "
+     "Q_l = H_l exactly, so no few-object identity separates them, only a statistical test with "
+     "randoms near the observer"),
     ("(-1)^l dropped from the space inversion", "oracle/power.py",
      "F_l from G_l is formed only for the even l = 2, 4 of the two-index spectra, where (-1)^l = 1"),
     ("strict bin-centre closure c_k < c_i + c_j", "oracle/bispec.py",
