@@ -277,7 +277,9 @@ npc_status npc_cross_bispectrum(npc_ctx* ctx, const npc_mesh_spec* mesh, const n
 npc_status npc_bispectrum_layout(const npc_kbins* bins, uint32_t scoc_ell_mask,
                                  uint32_t tripo_ell_mask, int64_t* ntri, int64_t* npairs,
                                  int64_t* out_len);
-/* Triangle bin indices [ntri][3] (host memory, capacity `cap` triangles). */
+/* Triangle bin indices [ntri][3] in npc_bispectrum's order (host memory, capacity `cap` triangles).
+ * *ntri receives the count; tri = NULL only asks for it; cap below the count returns
+ * NPC_ERR_INVALID_ARG and writes nothing to tri. */
 npc_status npc_bispectrum_triangles(const npc_kbins* bins, int32_t* tri, int64_t cap,
                                     int64_t* ntri);
 
